@@ -1,0 +1,70 @@
+"""Exact stationary vectors by routes independent of the multigrid method.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU-baseline
+leg of bench.py may import this package; the product path never does.
+
+The result the method must reach (Section 1, Eq. (1.1); Section 2): the unique x > 0
+with A x = x, 1^T x = 1, for an irreducible column-stochastic A (Perron-Frobenius).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def from_degree(deg: np.ndarray) -> np.ndarray:
+    """Random walk with a_ij = 1/deg(j) on an undirected graph (uniform network and
+    planar-graph models of Section 5.1): A D 1 = D 1 with D = diag(deg), so x = deg / sum(deg)."""
+    deg = np.asarray(deg, dtype=np.float64)
+    return deg / deg.sum()
+
+
+def birth_death(birth: np.ndarray, death: np.ndarray) -> np.ndarray:
+    """Detailed balance x_k b_k = x_{k+1} d_{k+1}; evaluated in log space because the
+    entries span hundreds of orders of magnitude for long chains."""
+    birth = np.asarray(birth, dtype=np.float64)
+    death = np.asarray(death, dtype=np.float64)
+    n = len(birth)
+    logx = np.zeros(n)
+    if n > 1:
+        logx[1:] = np.cumsum(np.log(birth[:-1]) - np.log(death[1:]))
+    logx -= logx.max()
+    x = np.exp(logx)
+    return x / x.sum()
+
+
+def dense_nullspace(A_dense: np.ndarray) -> np.ndarray:
+    """Bordered dense solve: replace the last equation of (I - A) x = 0 by 1^T x = 1.
+    Nonsingular for irreducible A because the left null vector 1 of B has no zero entry."""
+    n = A_dense.shape[0]
+    M = np.eye(n) - A_dense
+    M[-1, :] = 1.0
+    rhs = np.zeros(n)
+    rhs[-1] = 1.0
+    return np.linalg.solve(M, rhs)
+
+
+def sparse_nullspace(A) -> np.ndarray:
+    """The same bordered system solved with SuperLU (scipy) for chains too large for dense LU."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    M = (sp.identity(n, format="csr") - A).tolil()
+    M[n - 1, :] = np.ones(n)
+    rhs = np.zeros(n)
+    rhs[-1] = 1.0
+    x = spla.spsolve(M.tocsc(), rhs)
+    return x / x.sum()
+
+
+def exact_stationary(chain) -> np.ndarray:
+    """Closed form where the model has one, else a direct solve."""
+    if "degree" in chain.meta:
+        return from_degree(chain.meta["degree"])
+    if chain.kind == "birth_death":
+        return birth_death(chain.meta["birth"], chain.meta["death"])
+    if chain.n <= 500:
+        return dense_nullspace(chain.dense())
+    return sparse_nullspace(chain.to_scipy())
