@@ -1,0 +1,250 @@
+/*
+ * bamg.h — C ABI of the GB300 Bootstrap AMG library for Markov chains.
+ *
+ * Computes the stationary vector x of an irreducible column-stochastic transition
+ * matrix A (A x = x, x > 0, 1^T x = 1; Section 1, Eq. (1.1)) by solving B x = 0 with
+ * B = I - A: a bootstrap setup (Section 1 steps 1-4; Algorithm 3, the multilevel
+ * eigensolver, followed by the rebuild of all P_l, B_l, T_l) and flexible GMRES
+ * preconditioned by a V(2,2) cycle (Section 4.2, Eq. (4.4)).
+ *
+ * Conventions for every entry point:
+ *  - A is column stochastic and a_ij is the probability of the transition j -> i, so
+ *    CSR row i lists the source states j.  Column indices of a row must be sorted
+ *    ascending and unique.  Self-loops are allowed (B keeps them on its diagonal).
+ *  - Integer index arrays are int32; floating arrays are FP64 unless a `dtype`
+ *    argument says otherwise (BAMG_F64 = double, BAMG_F32 = float).
+ *  - Pointers are device pointers unless the argument name starts with h_ or a flag
+ *    says the buffer lives in host memory.  The caller owns every buffer it passes;
+ *    the library never frees them and keeps no reference after the call returns.
+ *  - Test-vector blocks are "row interleaved": X[i * ld + k] is vector k at state i;
+ *    `ld` and `col0` must be multiples of 2 (FP64) or 4 (FP32) so rows load as
+ *    16-byte vectors, and X must be 16-byte aligned.
+ *  - Work is queued on `stream` (a cudaStream_t; NULL = the legacy default stream).
+ *    Entry points that return sizes or statuses synchronise that stream first.
+ *  - Every call returns BAMG_OK (0) or a negative code; bamg_last_error() returns a
+ *    message for the calling thread's last failure.  No call is thread-safe on the
+ *    same handle.
+ */
+#ifndef BAMG_H
+#define BAMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BAMG_OK = 0,
+    BAMG_EINVAL = -1,    /* bad argument, size or layout */
+    BAMG_ENOTSTOCH = -2, /* A not column stochastic (|colsum - 1| > 1e-12), a negative entry, or a_ii = 1 */
+    BAMG_ECUDA = -3,     /* CUDA runtime error */
+    BAMG_ENOMEM = -4,    /* device allocation failed */
+    BAMG_ENOCONV = -5,   /* tolerance not reached within max_it iterations */
+    BAMG_ETIMEOUT = -6,  /* a device-side loop hit its iteration cap */
+    BAMG_ENUMERIC = -7,  /* NaN/Inf, or a singular coarsest factor */
+    BAMG_ESIZE = -8,     /* output capacity too small; the needed size is returned */
+    BAMG_EOVERFLOW = -9  /* a fixed per-row capacity was exceeded (neighbourhood search) */
+};
+
+enum { BAMG_F64 = 0, BAMG_F32 = 1 };
+enum { BAMG_PREC_FP64 = 0, BAMG_PREC_MIXED = 1 };
+enum { BAMG_COARSEN_GRID = 0, BAMG_COARSEN_CR = 1 };
+
+/* Column-stochastic A.  `on_host` = 1: the three arrays are host memory and are
+ * copied to the device inside the call; 0: device memory. */
+typedef struct {
+    int32_t n, nnz;
+    const int32_t* row_ptr; /* n + 1 */
+    const int32_t* col;     /* nnz */
+    const double* val;      /* nnz */
+    int32_t on_host;
+} bamg_csr;
+
+/* A device CSR matrix used by the step entry points; `val` has the call's dtype. */
+typedef struct {
+    int32_t n, nnz;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const void* val;
+} bamg_mat;
+
+typedef struct {
+    double omega;       /* omega-Jacobi damping (Section 3: 0.7) */
+    int32_t nu_tv;      /* setup sweeps on the random test vectors */
+    int32_t nu_ev;      /* sweeps on interpolated eigenvector approximations */
+    int32_t nu_pre, nu_post; /* V(nu_pre, nu_post) cycle (Section 5.1: V(2,2)) */
+    int32_t caliber;    /* c: max non-zeros per interpolation row (Section 3.2; 2) */
+    int32_t z;          /* path length of the neighbourhoods, Eq. (3.5), 1..3 */
+    int32_t mmax;       /* candidates kept per fine point, closest first (<= 16) */
+    int32_t k_ev;       /* coarsest-level eigenvectors carried up (Section 5.1: 6) */
+    int32_t coarse_max; /* stop coarsening at n_l <= coarse_max (<= 64) */
+    int32_t gmres_m;    /* FGMRES restart length (<= 64) */
+    int32_t max_it;     /* total FGMRES iteration cap */
+    int32_t precision;  /* BAMG_PREC_FP64 or BAMG_PREC_MIXED (FP32 setup + V-cycle) */
+    int32_t coarsen;    /* BAMG_COARSEN_GRID (needs grid_nx, grid_ny) or BAMG_COARSEN_CR */
+    int32_t grid_nx, grid_ny; /* state (ix, iy) has index ix + iy * grid_nx */
+    uint64_t seed;      /* counter-based random numbers (SplitMix64) */
+    double tv_lo, tv_hi;/* initial test vectors uniform in [tv_lo, tv_hi) */
+    double ev_change_tol;/* an eigenvector joins the test set if |dlambda|/|lambda| exceeds this */
+    double ridge;       /* Tikhonov factor of the local LS systems, FP64 runs */
+    double ridge32;     /* the same for FP32 (mixed) runs */
+    double weight_floor;/* floor of ||B x||^2 in the LS weights */
+    double cr_theta;    /* compatible relaxation threshold (Section 3.1: 0.85) */
+    int32_t cr_nu;      /* CR sweeps per round (Section 3.1: 8) */
+    int32_t cr_max_rounds;
+    double cr_omega;
+    void* stream;       /* cudaStream_t for all work of the handle */
+} bamg_opts;
+
+typedef struct {
+    int32_t status;
+    int32_t iterations;   /* FGMRES iterations */
+    int32_t restarts;
+    int32_t true_checks;  /* true-residual evaluations */
+    double residual_l1;   /* ||B x||_1 / ||x||_1 of the returned x */
+    double setup_ms;      /* wall time of bamg_setup */
+    double solve_ms;      /* wall time of this bamg_solve */
+} bamg_stats;
+
+typedef struct bamg_handle bamg_handle;
+
+/* Fills *o with the paper's settings (Section 5.1) and the readings for the rest. */
+int bamg_default_opts(bamg_opts* o);
+
+/* Bootstrap setup (Section 1 steps 1-4; Algorithm 3 with mu = 1; rebuild).
+ * A: the transition matrix (copied; the caller may free it on return).
+ * r: number of random test vectors (1..24).  levels: maximum number of coarsenings.
+ * On success *h owns all device memory of the hierarchy until bamg_free(*h).
+ * Errors: EINVAL (sizes, r, options, grid dims), ENOTSTOCH, ENOMEM, ECUDA, ENUMERIC. */
+int bamg_setup(const bamg_csr* A, int r, int levels, const bamg_opts* o, bamg_handle** h);
+
+enum { BAMG_X_GUESS = 1, BAMG_X_HOST = 2 };
+/* Preconditioned flexible GMRES on B x = 0 (Section 4.2) until
+ * ||B x||_1 / ||x||_1 <= tol, then x is scaled to 1^T x = 1.
+ * x: n doubles, device memory unless flags has BAMG_X_HOST.  With BAMG_X_GUESS the
+ * incoming x is the initial guess, otherwise the setup's state-vector approximation
+ * (Section 4.1) is used.  st may be NULL.  Errors: ENOCONV (x holds the last iterate),
+ * ENUMERIC, ECUDA. */
+int bamg_solve(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st);
+
+/* Frees the handle and its device memory.  NULL is allowed. */
+void bamg_free(bamg_handle* h);
+
+/* Message of the calling thread's last failed call ("" if none).  Static storage. */
+const char* bamg_last_error(void);
+
+/* Number of kernels this library has launched in the process (all threads). */
+uint64_t bamg_launch_count(void);
+
+/* Levels of the hierarchy: *nlevels, and per level the size and non-zeros of B_l into
+ * h_n[], h_nnz[] (capacity 32 each, may be NULL); operator complexity sum nnz / nnz_0. */
+int bamg_hierarchy_info(const bamg_handle* h, int* nlevels, int64_t* h_n, int64_t* h_nnz, double* opc);
+
+enum {
+    BAMG_EXPORT_B = 0,   /* CSR of B_l: h_dst = [row_ptr (n+1) int32 | col (nnz) int32 | val (nnz) double] */
+    BAMG_EXPORT_T = 1,   /* T_l values on B_l's pattern (nnz doubles) */
+    BAMG_EXPORT_P = 2,   /* P_l as ELL: [pcol (n*c) int32 | pcnt (n) int32 | pval (n*c) double] */
+    BAMG_EXPORT_CF = 3,  /* cf (n bytes, 1 = coarse) */
+    BAMG_EXPORT_X = 4,   /* test-vector block, n * ld doubles (ld via bamg_hierarchy_layout) */
+    BAMG_EXPORT_PINV = 5,/* coarsest B_L^+ (n_L * n_L doubles, row-major) */
+    BAMG_EXPORT_XINIT = 6,/* the setup's state-vector approximation (n_0 doubles) */
+    BAMG_EXPORT_LAMBDA = 7 /* eigenvalue approximations of level l (nvec doubles) */
+};
+/* Copies one object of level l to host memory h_dst (converted to double).  Returns
+ * ESIZE with *h_bytes = the needed size when cap_bytes is too small. */
+int bamg_level_export(const bamg_handle* h, int level, int what, void* h_dst, int64_t cap_bytes, int64_t* h_bytes);
+
+/* Layout of the test-vector block of level l: leading dimension, random vectors r,
+ * eigenvector columns start (col0 of V) and count. */
+int bamg_hierarchy_layout(const bamg_handle* h, int level, int* ld, int* r, int* v_col0, int* nvec);
+
+/* ---------------------------------------------------------------------------------
+ * Hierarchy import (checkpoint/resume): builds a handle from a given hierarchy, all
+ * arrays in host memory, FP64.  Level l has B_l (CSR) and, for l < nlevels-1, P_l in
+ * CSR (n_l x n_{l+1}, at most `caliber` entries per row); Q_l is derived from P_l as
+ * in Section 4 (Q[I, i] = 1/|J_i|).  pinv is the coarsest B_L^+ (row-major), x_init the
+ * initial guess.  Used to run the solve phase on a hierarchy built elsewhere.
+ * --------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t n, nnz;
+    const int32_t* h_row_ptr; const int32_t* h_col; const double* h_val;  /* B_l */
+    int32_t p_nnz;
+    const int32_t* h_p_row_ptr; const int32_t* h_p_col; const double* h_p_val; /* P_l */
+} bamg_level_in;
+int bamg_import(int nlevels, const bamg_level_in* levels, const double* h_pinv, const double* h_x_init,
+                const bamg_opts* o, bamg_handle** h);
+
+/* z = C v: one V(nu_pre, nu_post) cycle of the handle's hierarchy on v (Eq. (4.4),
+ * zero initial guess, B_L^+ on the coarsest level).  v, z: n_0 device doubles. */
+int bamg_vcycle_apply(bamg_handle* h, const double* v, double* z);
+
+/* ---------------------------------------------------------------------------------
+ * Step entry points: one step of the setup on caller buffers (device memory).
+ * --------------------------------------------------------------------------------- */
+
+/* Initial test vectors (Section 5.1: uniform positive random entries):
+ * X[i*ld + col0 + k] = lo + (hi - lo) * u, u the (k * 2^40 + i + 1)-th SplitMix64 draw
+ * (Steele, Lea, Flood 2014) of `seed`, k < ncols, computed in FP64 then rounded to dtype. */
+int bamg_tv_init(int dtype, int n, int ncols, int ld, int col0, uint64_t seed, double lo, double hi,
+                 void* X, void* stream);
+
+/* nu omega-Jacobi sweeps (Section 3, Eq. (3.1), M = diag(B)/omega) on the columns
+ * [col0, col0 + ncols) of X: X <- X - omega D^{-1} (B X).  With T_val and d_lambda
+ * the sweeps solve (B - lambda_k T) x_k = 0 (Algorithm 3): D_k = diag(B) - lambda_k diag(T).
+ * T_val: values of T on B's pattern (NULL: T = I); d_lambda: ncols FP64 shifts (NULL: 0).
+ * work: scratch of n * ld elements of dtype.  B must store its diagonal. */
+int bamg_relax(int dtype, const bamg_mat* B, const void* T_val, const double* d_lambda, int ncols, int ld,
+               int col0, double omega, int nu, void* X, void* work, void* stream);
+
+/* LS weights of Section 3.2: scales each active column k of [col0, col0+ncols) to unit
+ * 2-norm and sets w_k = 1 / max(||B x_k||_2^2, floor), then divides the active weights by
+ * their maximum; inactive columns (d_active[k] = 0, or d_active NULL = all active) get 0.
+ * d_w: ncols doubles. */
+int bamg_tv_weights(int dtype, const bamg_mat* B, int ncols, int ld, int col0, const uint8_t* d_active,
+                    double floor, void* X, double* d_w, void* stream);
+
+/* Full coarsening (Section 5.1): cf[i] = 1 on states with even ix and even iy;
+ * cidx[i] = (ix/2) + (iy/2) * ((nx+1)/2) on coarse states, -1 on fine states. */
+int bamg_coarsen_grid(int nx, int ny, uint8_t* cf, int32_t* cidx, void* stream);
+
+/* Compatible-relaxation coarsening, Algorithm 1 (Section 3.1), on level `level` of the
+ * seed's random streams: an independent set of G(B) to start, then rounds of nu
+ * F-relaxation sweeps from U[1,2) starts adding an independent set of the slow points
+ * while rho_f > theta.  Writes cf, cidx; *h_nc = coarse count, *h_rounds = rounds. */
+int bamg_coarsen_cr(const bamg_mat* B, int level, uint64_t seed, double theta, int nu, double omega,
+                    int max_rounds, uint8_t* cf, int32_t* cidx, int* h_nc, int* h_rounds, void* stream);
+
+/* Least-squares interpolation rows (Section 3.2, Eq. (3.5), Eq. (3.6), Algorithm 2) for
+ * every fine point: candidates are the coarse points within path length z in G(B),
+ * ordered by (length, coarse index), at most mmax; greedy selection of up to c points,
+ * each step minimising Eq. (3.6) with the weights d_w over the ncols columns of X
+ * (from col 0).  Output P in ELL form: pcol[i*c + t] (coarse index), pval, pcnt[i];
+ * coarse points get the unit row.  Rows are sorted by coarse index. */
+int bamg_interp_ls(int dtype, const bamg_mat* B, const uint8_t* cf, const int32_t* cidx, const void* X,
+                   int ncols, int ld, const double* d_w, int z, int mmax, int c, double ridge,
+                   int32_t* pcol, void* pval, int32_t* pcnt, void* stream);
+
+/* Petrov-Galerkin products B_c = Q B P and T_c = Q T P (Section 1 step 3; Algorithm 3)
+ * with the averaging Q of Section 4 (Q[I,i] = 1/pcnt[i] for I in row i of P).
+ * T_val: T on B's pattern (NULL: T = I); T_c is returned on B_c's pattern.
+ * Output CSR with nc rows; cap = capacity of out_col/out_bv/out_tv.  *h_nnz = nnz(B_c);
+ * returns ESIZE (nothing written) when cap < nnz(B_c). */
+int bamg_galerkin(int dtype, const bamg_mat* B, const void* T_val, int nc, const int32_t* pcol,
+                  const void* pval, const int32_t* pcnt, int c, int32_t* out_row_ptr, int32_t* out_col,
+                  void* out_bv, void* out_tv, int64_t cap, int64_t* h_nnz, void* stream);
+
+/* Coarsest level (Algorithm 3, first branch): eigenpairs of B_L x = lambda T_L x of
+ * smallest |lambda| (dense n x n row-major FP64, n <= 64).  Complex pairs are returned
+ * as two real columns (Re v, Im v) sharing Re lambda; at most k_ev + 1 columns.
+ * d_lam[col], d_V (n x ncols, column-major, unit norm, <w, v> > 0 for w_i = i+1),
+ * d_kind[col] (0 real, 1 real part, 2 imaginary part); *h_nvec = columns written.
+ * The smallest eigenvalue is set to exactly 0.  With d_pinv != NULL also writes
+ * B_L^+ (row-major), the minimal-norm inverse of Section 4.2. */
+int bamg_coarse_eig(int n, const double* d_B, const double* d_T, int k_ev, double* d_lam, double* d_V,
+                    int32_t* d_kind, int* h_nvec, double* d_pinv, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BAMG_H */

@@ -1,0 +1,169 @@
+// Shared host/device helpers of the GB300 Bootstrap AMG library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/bamg.h"
+
+namespace bamg {
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void count_launch();
+void set_last_error(const std::string& msg);
+
+#define BAMG_CK(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            throw ::bamg::Error(e_ == cudaErrorMemoryAllocation ? BAMG_ENOMEM : BAMG_ECUDA,        \
+                                std::string(#call) + ": " + cudaGetErrorString(e_));               \
+        }                                                                                          \
+    } while (0)
+
+#define BAMG_REQUIRE(cond, code, msg)                                                              \
+    do {                                                                                           \
+        if (!(cond)) throw ::bamg::Error((code), (msg));                                           \
+    } while (0)
+
+// Every kernel of the library goes through this macro so the process-wide launch
+// counter is exact.
+#define BAMG_LAUNCH(kernel, grid, block, smem, stream, ...)                                        \
+    do {                                                                                           \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                                \
+        ::bamg::count_launch();                                                                    \
+        BAMG_CK(cudaGetLastError());                                                               \
+    } while (0)
+
+inline unsigned blocks_for(int64_t work, int per_block) {
+    int64_t b = (work + per_block - 1) / per_block;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+// Owning device buffer (cudaMalloc).  Persistent storage of a hierarchy.
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t n_) { alloc(n_); }
+    void alloc(size_t n_) {
+        release();
+        if (n_) BAMG_CK(cudaMalloc(&p, n_ * sizeof(T)));
+        n = n_;
+    }
+    void ensure(size_t n_) {
+        if (n_ > n) alloc(n_);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevBuf() { release(); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        release();
+        p = o.p;
+        n = o.n;
+        o.p = nullptr;
+        o.n = 0;
+        return *this;
+    }
+    T* get() const { return p; }
+};
+
+// Stream-ordered temporary (cudaMallocAsync / cudaFreeAsync).
+template <typename T>
+struct TmpBuf {
+    T* p = nullptr;
+    cudaStream_t s = nullptr;
+    TmpBuf(size_t n, cudaStream_t st) : s(st) {
+        if (n) BAMG_CK(cudaMallocAsync((void**)&p, n * sizeof(T), s));
+    }
+    ~TmpBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    TmpBuf(const TmpBuf&) = delete;
+    TmpBuf& operator=(const TmpBuf&) = delete;
+    T* get() const { return p; }
+};
+
+// ------------------------------------------------------------------ device helpers
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): state s + t * gamma, then the published
+// 64-bit finaliser.  Draw number (stream * 2^40 + idx + 1) of `seed`.
+__host__ __device__ __forceinline__ uint64_t splitmix64_output(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t counter_u64(uint64_t seed, uint64_t stream, uint64_t idx) {
+    uint64_t ctr = stream * (1ull << 40) + idx + 1ull;
+    return splitmix64_output(seed + ctr * 0x9E3779B97F4A7C15ull);
+}
+__device__ __forceinline__ double counter_uniform(uint64_t seed, uint64_t stream, uint64_t idx) {
+    return (double)(counter_u64(seed, stream, idx) >> 11) * 0x1.0p-53;
+}
+
+constexpr uint64_t STREAM_TV = 0;
+constexpr uint64_t STREAM_CR = 1ull << 22;
+constexpr uint64_t STREAM_MIS = 1ull << 23;
+
+// 16-byte vector of T: 2 doubles or 4 floats.
+template <typename T>
+struct V16;
+template <>
+struct V16<double> {
+    using type = double2;
+    static constexpr int W = 2;
+    __device__ static void load(const double* p, double* o) {
+        double2 v = *reinterpret_cast<const double2*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+    __device__ static void store(double* p, const double* o) { *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]); }
+};
+template <>
+struct V16<float> {
+    using type = float4;
+    static constexpr int W = 4;
+    __device__ static void load(const float* p, float* o) {
+        float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+    __device__ static void store(float* p, const float* o) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Multiply and add with rounding after each operation (no contraction into an FMA),
+// so that sums computed in the same order match a plain CPU evaluation bit for bit.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+// ------------------------------------------------------------------ host helpers
+void exclusive_scan(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s);  // d_out has n+1 entries
+int32_t read_int(const int32_t* d_p, cudaStream_t s);
+
+}  // namespace bamg

@@ -1,0 +1,223 @@
+// Compatible-relaxation coarsening, Algorithm 1 (Section 3.1): an independent set of
+// the graph of B to start, then rounds of nu F-relaxation sweeps (Eq. (3.2)) from random
+// starts in [1, 2); while the convergence estimate of Eq. (3.3) exceeds theta, an
+// independent set of the slow points joins C.  Independent sets use Luby's rule with
+// fixed SplitMix64 priorities: an undecided candidate enters when its key (priority,
+// index) beats every undecided neighbour's, after which its undecided neighbours leave.
+#include "kernels.cuh"
+
+namespace bamg {
+
+__global__ void k_tcount(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         int32_t* __restrict__ cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+        if (ci[p] != i) atomicAdd(cnt + ci[p], 1);
+}
+__global__ void k_tfill(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                        const int32_t* __restrict__ rpT, int32_t* __restrict__ cursor, int32_t* __restrict__ ciT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int j = ci[p];
+        if (j != i) ciT[rpT[j] + atomicAdd(cursor + j, 1)] = i;
+    }
+}
+
+__device__ __forceinline__ bool beats(uint64_t pi, int i, uint64_t pj, int j) { return pi > pj || (pi == pj && i > j); }
+
+__global__ void k_mis_step(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const int32_t* __restrict__ rpT, const int32_t* __restrict__ ciT,
+                           const uint8_t* __restrict__ und, uint8_t* __restrict__ win, uint64_t seed, uint64_t stream) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (!und[i]) {
+        win[i] = 0;
+        return;
+    }
+    const uint64_t pi = counter_u64(seed, stream, (uint64_t)i);
+    bool ok = true;
+    for (int p = rp[i]; p < rp[i + 1] && ok; ++p) {
+        const int j = ci[p];
+        if (j != i && und[j] && !beats(pi, i, counter_u64(seed, stream, (uint64_t)j), j)) ok = false;
+    }
+    for (int p = rpT[i]; p < rpT[i + 1] && ok; ++p) {
+        const int j = ciT[p];
+        if (und[j] && !beats(pi, i, counter_u64(seed, stream, (uint64_t)j), j)) ok = false;
+    }
+    win[i] = ok ? 1 : 0;
+}
+
+__global__ void k_mis_remove(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const int32_t* __restrict__ rpT, const int32_t* __restrict__ ciT,
+                             uint8_t* __restrict__ und, const uint8_t* __restrict__ win, uint8_t* __restrict__ chosen,
+                             int* __restrict__ left) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !und[i]) return;
+    if (win[i]) {
+        chosen[i] = 1;
+        und[i] = 0;
+        return;
+    }
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+        if (ci[p] != i && win[ci[p]]) {
+            und[i] = 0;
+            return;
+        }
+    for (int p = rpT[i]; p < rpT[i + 1]; ++p)
+        if (win[ciT[p]]) {
+            und[i] = 0;
+            return;
+        }
+    atomicAdd(left, 1);
+}
+
+// chosen |= independent set of the candidates (und on entry; consumed).
+static void independent_set(int n, const int32_t* rp, const int32_t* ci, const int32_t* rpT, const int32_t* ciT,
+                            uint8_t* und, uint8_t* chosen, uint64_t seed, uint64_t stream, cudaStream_t s) {
+    TmpBuf<uint8_t> win(n, s);
+    TmpBuf<int> left(1, s);
+    const unsigned g = blocks_for(n, 256);
+    for (int round = 0; round <= n; ++round) {
+        BAMG_CK(cudaMemsetAsync(left.get(), 0, sizeof(int), s));
+        BAMG_LAUNCH(k_mis_step, g, 256, 0, s, n, rp, ci, rpT, ciT, und, win.get(), seed, stream);
+        BAMG_LAUNCH(k_mis_remove, g, 256, 0, s, n, rp, ci, rpT, ciT, und, win.get(), chosen, left.get());
+        int h = 0;
+        BAMG_CK(cudaMemcpyAsync(&h, left.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        BAMG_CK(cudaStreamSynchronize(s));
+        if (h == 0) return;
+    }
+    throw Error(BAMG_ETIMEOUT, "independent set did not terminate");
+}
+
+__global__ void k_cr_start(int n, const uint8_t* __restrict__ cf, double* __restrict__ u, uint64_t seed,
+                           uint64_t stream) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) u[i] = cf[i] ? 0.0 : 1.0 + counter_uniform(seed, stream, (uint64_t)i);
+}
+
+template <typename T>
+__global__ void k_frelax(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const T* __restrict__ bv, const uint8_t* __restrict__ cf, const double* __restrict__ u,
+                         double* __restrict__ un, double omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (cf[i]) {
+        un[i] = 0.0;
+        return;
+    }
+    double s = 0.0, d = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int j = ci[p];
+        if (j == i) d = (double)bv[p];
+        if (!cf[j]) s += (double)bv[p] * u[j];
+    }
+    un[i] = u[i] - (omega * (1.0 / d)) * s;
+}
+
+__global__ void k_cr_norms(int n, const double* __restrict__ u0, const double* __restrict__ u,
+                           double* __restrict__ partial) {
+    __shared__ double sh[2][8];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double a = 0.0, b = 0.0;
+    if (i < n) {
+        a = u0[i] * u0[i];
+        b = u[i] * u[i];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sh[0][wid] = a;
+        sh[1][wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * 2 + threadIdx.x] = t;
+    }
+}
+__global__ void k_sum2(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+    const int q = threadIdx.x;
+    if (q >= 2) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * 2 + q];
+    out[q] = s;
+}
+
+__global__ void k_cr_slow(int n, const uint8_t* __restrict__ cf, const double* __restrict__ up,
+                          const double* __restrict__ u, double theta, uint8_t* __restrict__ cand) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    cand[i] = (!cf[i] && fabs(u[i]) / fabs(up[i]) > theta) ? 1 : 0;
+}
+
+__global__ void k_u8_to_i32(int n, const uint8_t* __restrict__ a, int32_t* __restrict__ b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+__global__ void k_cidx_from_scan(int n, const uint8_t* __restrict__ cf, const int32_t* __restrict__ sc,
+                                 int32_t* __restrict__ cidx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cidx[i] = cf[i] ? sc[i] : -1;
+}
+
+template <typename T>
+int coarsen_cr(const MatView<T>& B, int level, uint64_t seed, double theta, int nu, double omega, int max_rounds,
+               uint8_t* cf, int32_t* cidx, int* nc_out, cudaStream_t s) {
+    const int n = B.n;
+    const unsigned g = blocks_for(n, 256);
+    // transpose pattern for the undirected neighbourhoods
+    TmpBuf<int32_t> cnt(n, s), rpT(n + 1, s), cursor(n, s);
+    BAMG_CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * n, s));
+    BAMG_CK(cudaMemsetAsync(cursor.get(), 0, sizeof(int32_t) * n, s));
+    BAMG_LAUNCH(k_tcount, g, 256, 0, s, n, B.rp, B.ci, cnt.get());
+    exclusive_scan(cnt.get(), rpT.get(), n, s);
+    const int nT = read_int(rpT.get() + n, s);
+    TmpBuf<int32_t> ciT(nT > 0 ? nT : 1, s);
+    BAMG_LAUNCH(k_tfill, g, 256, 0, s, n, B.rp, B.ci, rpT.get(), cursor.get(), ciT.get());
+    TmpBuf<uint8_t> und(n, s), cand(n, s);
+    BAMG_CK(cudaMemsetAsync(cf, 0, n, s));
+    BAMG_CK(cudaMemsetAsync(und.get(), 1, n, s));
+    independent_set(n, B.rp, B.ci, rpT.get(), ciT.get(), und.get(), cf, seed, STREAM_MIS + ((uint64_t)level << 8), s);
+    TmpBuf<double> u0(n, s), ua(n, s), ub(n, s), norms(2, s), part((size_t)g * 2, s);
+    int rounds = 0;
+    double h[2];
+    for (;;) {
+        BAMG_LAUNCH(k_cr_start, g, 256, 0, s, n, cf, u0.get(), seed, STREAM_CR + ((uint64_t)level << 8) + rounds);
+        const double* cur = u0.get();
+        double* prev = nullptr;
+        double* bufs[2] = {ua.get(), ub.get()};
+        for (int k = 0; k < nu; ++k) {
+            double* nxt = bufs[k & 1];
+            BAMG_LAUNCH(k_frelax<T>, g, 256, 0, s, n, B.rp, B.ci, B.v, cf, cur, nxt, omega);
+            prev = const_cast<double*>(cur);
+            cur = nxt;
+        }
+        BAMG_LAUNCH(k_cr_norms, g, 256, 0, s, n, u0.get(), cur, part.get());
+        BAMG_LAUNCH(k_sum2, 1, 32, 0, s, (int)g, part.get(), norms.get());
+        BAMG_CK(cudaMemcpyAsync(h, norms.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+        BAMG_CK(cudaStreamSynchronize(s));
+        const double rho = std::pow(std::sqrt(h[1]) / std::sqrt(h[0]), 1.0 / nu);
+        if (!(rho > theta) || rounds >= max_rounds || h[0] == 0.0) break;
+        BAMG_LAUNCH(k_cr_slow, g, 256, 0, s, n, cf, prev, cur, theta, cand.get());
+        ++rounds;
+        independent_set(n, B.rp, B.ci, rpT.get(), ciT.get(), cand.get(), cf, seed,
+                        STREAM_MIS + ((uint64_t)level << 8) + rounds, s);
+    }
+    TmpBuf<int32_t> ci32(n, s), sc(n + 1, s);
+    BAMG_LAUNCH(k_u8_to_i32, g, 256, 0, s, n, cf, ci32.get());
+    exclusive_scan(ci32.get(), sc.get(), n, s);
+    BAMG_LAUNCH(k_cidx_from_scan, g, 256, 0, s, n, cf, sc.get(), cidx);
+    *nc_out = read_int(sc.get() + n, s);
+    return rounds;
+}
+
+template int coarsen_cr<float>(const MatView<float>&, int, uint64_t, double, int, double, int, uint8_t*, int32_t*,
+                               int*, cudaStream_t);
+template int coarsen_cr<double>(const MatView<double>&, int, uint64_t, double, int, double, int, uint8_t*, int32_t*,
+                                int*, cudaStream_t);
+
+}  // namespace bamg

@@ -1,0 +1,706 @@
+// Interpolation and coarse operators: full coarsening (Section 5.1), the coarse
+// neighbourhoods of Eq. (3.5), the greedy least-squares fit of Algorithm 2 / Eq. (3.6),
+// the averaging restriction Q of Section 4, and the Petrov-Galerkin products
+// B_{l+1} = Q B P, T_{l+1} = Q T P (Section 1 step 3, Algorithm 3).
+#include <cfloat>
+
+#include "kernels.cuh"
+
+namespace bamg {
+
+// ================================================================ scan
+constexpr int SCAN_T = 256, SCAN_I = 8, SCAN_B = SCAN_T * SCAN_I;
+
+__global__ void k_scan_local(const int32_t* __restrict__ in, int32_t* __restrict__ out, int n,
+                             int32_t* __restrict__ bsum) {
+    __shared__ int32_t wsum[SCAN_T / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_I;
+    int32_t v[SCAN_I];
+    int32_t tsum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_I; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        tsum += v[k];
+    }
+    int32_t x = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < SCAN_T / 32 ? wsum[lane] : 0;
+        int32_t incl = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane < SCAN_T / 32) wsum[lane] = incl - w;
+        if (lane == SCAN_T / 32 - 1) bsum[blockIdx.x] = incl;
+    }
+    __syncthreads();
+    int32_t run = x - tsum + wsum[warp];
+#pragma unroll
+    for (int k = 0; k < SCAN_I; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void k_scan_sums(int32_t* __restrict__ bsum, int nb, int32_t* __restrict__ total) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nb; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        const int32_t v = i < nb ? bsum[i] : 0;
+        int32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+            int32_t incl = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            wsum[lane] = incl - w;
+        }
+        __syncthreads();
+        const int32_t excl = carry + wsum[warp] + x - v;
+        __syncthreads();
+        if (i < nb) bsum[i] = excl;
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int32_t* __restrict__ out, int n, const int32_t* __restrict__ bsum) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += bsum[i / SCAN_B];
+}
+
+void exclusive_scan(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s) {
+    if (n <= 0) {
+        BAMG_CK(cudaMemsetAsync(d_out, 0, sizeof(int32_t), s));
+        return;
+    }
+    const int nb = (int)blocks_for(n, SCAN_B);
+    TmpBuf<int32_t> bsum(nb, s);
+    BAMG_LAUNCH(k_scan_local, nb, SCAN_T, 0, s, d_in, d_out, n, bsum.get());
+    BAMG_LAUNCH(k_scan_sums, 1, 1024, 0, s, bsum.get(), nb, d_out + n);
+    BAMG_LAUNCH(k_scan_add, blocks_for(n, 256), 256, 0, s, d_out, n, bsum.get());
+}
+
+int32_t read_int(const int32_t* d_p, cudaStream_t s) {
+    int32_t v = 0;
+    BAMG_CK(cudaMemcpyAsync(&v, d_p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BAMG_CK(cudaStreamSynchronize(s));
+    return v;
+}
+
+// ================================================================ coarsening
+__global__ void k_coarsen_grid(int nx, int ny, uint8_t* __restrict__ cf, int32_t* __restrict__ cidx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nx * ny) return;
+    const int ix = (int)(i % nx), iy = (int)(i / nx);
+    const bool c = (ix % 2 == 0) && (iy % 2 == 0);
+    cf[i] = c ? 1 : 0;
+    cidx[i] = c ? (ix / 2) + (iy / 2) * ((nx + 1) / 2) : -1;
+}
+void coarsen_grid(int nx, int ny, uint8_t* cf, int32_t* cidx, cudaStream_t s) {
+    BAMG_LAUNCH(k_coarsen_grid, blocks_for((int64_t)nx * ny, 256), 256, 0, s, nx, ny, cf, cidx);
+}
+
+__global__ void k_coarse_to_fine(int n, const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx,
+                                 int32_t* __restrict__ c2f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && cf[i]) c2f[cidx[i]] = i;
+}
+void coarse_to_fine(int n, const uint8_t* cf, const int32_t* cidx, int32_t* c2f, cudaStream_t s) {
+    if (n) BAMG_LAUNCH(k_coarse_to_fine, blocks_for(n, 256), 256, 0, s, n, cf, cidx, c2f);
+}
+
+// ================================================================ least-squares interpolation
+constexpr int LS_WARPS = 4;
+constexpr int VIS_CAP = 256;  // nodes visited by one neighbourhood search
+constexpr int MMAX = 16;
+constexpr int CMAX = 4;
+constexpr int KMAX = 32;
+
+// Solves the SPD system A x = b of order m <= CMAX by Cholesky; false if not SPD.
+template <typename T>
+__device__ __forceinline__ bool chol_solve(T (&A)[CMAX][CMAX], const T (&b)[CMAX], int m, T (&x)[CMAX]) {
+    T L[CMAX][CMAX];
+    T y[CMAX];
+#pragma unroll
+    for (int j = 0; j < CMAX; ++j) {
+        if (j < m) {
+            T s = A[j][j];
+#pragma unroll
+            for (int k = 0; k < CMAX; ++k)
+                if (k < j) s -= L[j][k] * L[j][k];
+            if (!(s > T(0))) return false;
+            const T d = sqrt(s);
+            L[j][j] = d;
+#pragma unroll
+            for (int i = 0; i < CMAX; ++i) {
+                if (i > j && i < m) {
+                    T t = A[i][j];
+#pragma unroll
+                    for (int k = 0; k < CMAX; ++k)
+                        if (k < j) t -= L[i][k] * L[j][k];
+                    L[i][j] = t / d;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < CMAX; ++j) {
+        if (j < m) {
+            T t = b[j];
+#pragma unroll
+            for (int k = 0; k < CMAX; ++k)
+                if (k < j) t -= L[j][k] * y[k];
+            y[j] = t / L[j][j];
+        }
+    }
+#pragma unroll
+    for (int j = CMAX - 1; j >= 0; --j) {
+        if (j < m) {
+            T t = y[j];
+#pragma unroll
+            for (int k = 0; k < CMAX; ++k)
+                if (k > j && k < m) t -= L[k][j] * x[k];
+            x[j] = t / L[j][j];
+        }
+    }
+    return true;
+}
+
+// One warp per point.  Fine points: breadth-first search to depth z over the row
+// pattern of B (edges i -> j for b_ij != 0, i != j), candidates = coarse points found,
+// ranked by (depth, coarse index) and cut to mmax; then the greedy steps of
+// Algorithm 2 with one lane per candidate: each lane forms its (|J|+1)-square weighted
+// normal equations (plus the Tikhonov term), solves them by Cholesky and evaluates the
+// functional of Eq. (3.6) directly; the lane with the smallest value (lowest slot on
+// ties) joins J.
+template <typename T>
+__global__ void __launch_bounds__(LS_WARPS * 32)
+    k_ls_fit(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const uint8_t* __restrict__ cf,
+             const int32_t* __restrict__ cidx, const T* __restrict__ X, int ncols, int ld, const double* __restrict__ w,
+             int z, int mmax, int c, double ridge, int32_t* __restrict__ pcol, T* __restrict__ pval,
+             int32_t* __restrict__ pcnt, int* __restrict__ err) {
+    __shared__ int s_vis[LS_WARPS][VIS_CAP];
+    __shared__ unsigned long long s_key[LS_WARPS][VIS_CAP];
+    __shared__ uint8_t s_dist[LS_WARPS][VIS_CAP];
+    __shared__ int s_cand[LS_WARPS][MMAX];
+    __shared__ T s_xi[LS_WARPS][KMAX];
+    __shared__ T s_xj[LS_WARPS][CMAX][KMAX];
+    __shared__ T s_w[KMAX];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < KMAX) s_w[threadIdx.x] = threadIdx.x < ncols ? (T)w[threadIdx.x] : T(0);
+    __syncthreads();
+    const int i = blockIdx.x * LS_WARPS + wid;
+    if (i >= n) return;
+    const int64_t prow = (int64_t)i * c;
+    if (cf[i]) {
+        if (lane < c) {
+            pcol[prow + lane] = lane == 0 ? cidx[i] : -1;
+            pval[prow + lane] = lane == 0 ? T(1) : T(0);
+        }
+        if (lane == 0) pcnt[i] = 1;
+        return;
+    }
+    // ---- neighbourhood search (Eq. (3.5))
+    int* vis = s_vis[wid];
+    uint8_t* dist = s_dist[wid];
+    if (lane == 0) {
+        vis[0] = i;
+        dist[0] = 0;
+    }
+    __syncwarp();
+    int nvis = 1, fs = 0, fe = 1;
+    bool ovf = false;
+    for (int d = 1; d <= z; ++d) {
+        for (int f = fs; f < fe; ++f) {
+            const int u = vis[f];
+            const int p0 = rp[u], p1 = rp[u + 1];
+            for (int base = p0; base < p1; base += 32) {
+                const int p = base + lane;
+                const int v = p < p1 ? ci[p] : -1;
+                bool isnew = v >= 0;
+                if (isnew)
+                    for (int q = 0; q < nvis; ++q)
+                        if (vis[q] == v) {
+                            isnew = false;
+                            break;
+                        }
+                const int key = isnew ? v : -1 - lane;
+                const unsigned grp = __match_any_sync(0xffffffffu, key);
+                const unsigned lt = (1u << lane) - 1u;
+                const bool leader = isnew && (grp & lt) == 0u;
+                const unsigned bal = __ballot_sync(0xffffffffu, leader);
+                const int pos = nvis + __popc(bal & lt);
+                if (leader && pos < VIS_CAP) {
+                    vis[pos] = v;
+                    dist[pos] = (uint8_t)d;
+                }
+                int added = __popc(bal);
+                if (nvis + added > VIS_CAP) {
+                    ovf = true;
+                    added = VIS_CAP - nvis;
+                }
+                nvis += added;
+                __syncwarp();
+            }
+        }
+        fs = fe;
+        fe = nvis;
+    }
+    // ---- candidates: coarse points ranked by (depth, coarse index)
+    unsigned long long* key = s_key[wid];
+    int ntot = 0;
+    for (int q0 = 1; q0 < nvis; q0 += 32) {
+        const int q = q0 + lane;
+        bool isc = false;
+        if (q < nvis) {
+            const int v = vis[q];
+            isc = cf[v] != 0;
+            key[q] = isc ? (((unsigned long long)dist[q] << 32) | (unsigned)cidx[v]) : ~0ull;
+        }
+        ntot += __popc(__ballot_sync(0xffffffffu, isc));
+    }
+    __syncwarp();
+    for (int q0 = 1; q0 < nvis; q0 += 32) {
+        const int q = q0 + lane;
+        if (q < nvis && key[q] != ~0ull) {
+            const unsigned long long kq = key[q];
+            int rank = 0;
+            for (int q2 = 1; q2 < nvis; ++q2) rank += key[q2] < kq;
+            if (rank < mmax) s_cand[wid][rank] = vis[q];
+        }
+    }
+    const int ncand = ntot < mmax ? ntot : mmax;
+    for (int k = lane; k < KMAX; k += 32) s_xi[wid][k] = k < ncols ? X[(int64_t)i * ld + k] : T(0);
+    __syncwarp();
+    // ---- greedy least squares (Algorithm 2)
+    const int node = lane < ncand ? s_cand[wid][lane] : -1;
+    const T* xs = node >= 0 ? X + (int64_t)node * ld : nullptr;
+    T gss = T(0), bs = T(0);
+    if (node >= 0)
+        for (int k = 0; k < ncols; ++k) {
+            const T wk = s_w[k], v = xs[k];
+            gss += wk * v * v;
+            bs += wk * v * s_xi[wid][k];
+        }
+    T gsj[CMAX], GJJ[CMAX][CMAX], bJ[CMAX], pbest[CMAX];
+    int J[CMAX];
+#pragma unroll
+    for (int a = 0; a < CMAX; ++a) {
+        gsj[a] = bJ[a] = pbest[a] = T(0);
+        J[a] = -1;
+#pragma unroll
+        for (int b = 0; b < CMAX; ++b) GJJ[a][b] = T(0);
+    }
+    bool used = false;
+    int nJ = 0;
+    const T INF = (T)INFINITY;
+#pragma unroll
+    for (int t = 0; t < CMAX; ++t) {
+        if (t >= c) break;
+        T L = INF;
+        T pl[CMAX];
+#pragma unroll
+        for (int a = 0; a < CMAX; ++a) pl[a] = T(0);
+        if (node >= 0 && !used) {
+            T A[CMAX][CMAX], rhs[CMAX];
+            T tr = gss;
+#pragma unroll
+            for (int a = 0; a < CMAX; ++a) {
+#pragma unroll
+                for (int b = 0; b < CMAX; ++b) A[a][b] = (a < t && b < t) ? GJJ[a][b] : T(0);
+                rhs[a] = a < t ? bJ[a] : T(0);
+                if (a < t) {
+                    A[a][t] = gsj[a];
+                    A[t][a] = gsj[a];
+                    tr += GJJ[a][a];
+                }
+            }
+            A[t][t] = gss;
+            rhs[t] = bs;
+            const T delta = (T)ridge * tr / (T)(t + 1);
+#pragma unroll
+            for (int a = 0; a < CMAX; ++a)
+                if (a <= t) A[a][a] += delta;
+            if (chol_solve<T>(A, rhs, t + 1, pl)) {
+                T acc = T(0);
+                for (int k = 0; k < ncols; ++k) {
+                    T r = s_xi[wid][k] - pl[t] * xs[k];
+#pragma unroll
+                    for (int a = 0; a < CMAX; ++a)
+                        if (a < t) r -= pl[a] * s_xj[wid][a][k];
+                    acc += s_w[k] * r * r;
+                }
+                L = (acc == acc) ? acc : INF;
+            }
+        }
+        T bestL = L;
+        int bestLane = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T oL = __shfl_xor_sync(0xffffffffu, bestL, o);
+            const int oLane = __shfl_xor_sync(0xffffffffu, bestLane, o);
+            if (oL < bestL || (oL == bestL && oLane < bestLane)) {
+                bestL = oL;
+                bestLane = oLane;
+            }
+        }
+        if (!(bestL < INF)) break;
+        const T w_gss = __shfl_sync(0xffffffffu, gss, bestLane);
+        const T w_bs = __shfl_sync(0xffffffffu, bs, bestLane);
+        const int w_node = __shfl_sync(0xffffffffu, node, bestLane);
+#pragma unroll
+        for (int a = 0; a < CMAX; ++a) {
+            const T g = __shfl_sync(0xffffffffu, gsj[a], bestLane);
+            const T pv = __shfl_sync(0xffffffffu, pl[a], bestLane);
+            if (a < t) {
+                GJJ[t][a] = g;
+                GJJ[a][t] = g;
+            }
+            pbest[a] = a <= t ? pv : T(0);
+        }
+        GJJ[t][t] = w_gss;
+        bJ[t] = w_bs;
+        J[t] = w_node;
+        nJ = t + 1;
+        if (lane == bestLane) used = true;
+        for (int k = lane; k < KMAX; k += 32) s_xj[wid][t][k] = k < ncols ? X[(int64_t)w_node * ld + k] : T(0);
+        __syncwarp();
+        if (node >= 0) {
+            T g = T(0);
+            for (int k = 0; k < ncols; ++k) g += s_w[k] * xs[k] * s_xj[wid][t][k];
+            gsj[t] = g;
+        }
+    }
+    if (lane == 0) {
+        int cols[CMAX];
+        T vals[CMAX];
+#pragma unroll
+        for (int a = 0; a < CMAX; ++a) {
+            cols[a] = a < nJ ? cidx[J[a]] : 0x7fffffff;
+            vals[a] = pbest[a];
+        }
+        for (int a = 1; a < nJ; ++a)
+            for (int b = a; b > 0 && cols[b - 1] > cols[b]; --b) {
+                int tc = cols[b];
+                cols[b] = cols[b - 1];
+                cols[b - 1] = tc;
+                T tv = vals[b];
+                vals[b] = vals[b - 1];
+                vals[b - 1] = tv;
+            }
+        for (int a = 0; a < c; ++a) {
+            pcol[prow + a] = a < nJ ? cols[a] : -1;
+            pval[prow + a] = a < nJ ? vals[a] : T(0);
+        }
+        pcnt[i] = nJ;
+        if (ovf) atomicOr(err, 1);
+    }
+}
+
+template <typename T>
+int interp_ls(int n, const int32_t* rp, const int32_t* ci, const uint8_t* cf, const int32_t* cidx, const T* X, int ncols,
+              int ld, const double* d_w, int z, int mmax, int c, double ridge, int32_t* pcol, T* pval, int32_t* pcnt,
+              cudaStream_t s) {
+    BAMG_REQUIRE(ncols >= 1 && ncols <= KMAX, BAMG_EINVAL, "interp_ls: 1 <= ncols <= 32");
+    BAMG_REQUIRE(c >= 1 && c <= CMAX, BAMG_EINVAL, "interp_ls: 1 <= caliber <= 4");
+    BAMG_REQUIRE(mmax >= 1 && mmax <= MMAX, BAMG_EINVAL, "interp_ls: 1 <= mmax <= 16");
+    BAMG_REQUIRE(z >= 1 && z <= 3, BAMG_EINVAL, "interp_ls: 1 <= z <= 3");
+    if (n == 0) return 0;
+    TmpBuf<int> err(1, s);
+    BAMG_CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    BAMG_LAUNCH(k_ls_fit<T>, blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, cf, cidx, X, ncols, ld, d_w, z,
+                mmax, c, ridge, pcol, pval, pcnt, err.get());
+    int h = 0;
+    BAMG_CK(cudaMemcpyAsync(&h, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CK(cudaStreamSynchronize(s));
+    return h ? BAMG_EOVERFLOW : 0;
+}
+
+// ================================================================ restriction Q
+__global__ void k_q_count(int n, int c, const int32_t* __restrict__ pcol, const int32_t* __restrict__ pcnt,
+                          int32_t* __restrict__ qcnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int t = 0; t < pcnt[i]; ++t) atomicAdd(qcnt + pcol[(int64_t)i * c + t], 1);
+}
+__global__ void k_q_fill(int n, int c, const int32_t* __restrict__ pcol, const int32_t* __restrict__ pcnt,
+                         const int32_t* __restrict__ qrp, int32_t* __restrict__ cursor, int32_t* __restrict__ qci) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int t = 0; t < pcnt[i]; ++t) {
+        const int I = pcol[(int64_t)i * c + t];
+        const int pos = atomicAdd(cursor + I, 1);
+        qci[qrp[I] + pos] = i;
+    }
+}
+// Sort each row by fine index (the fill order above is arbitrary) and set the
+// averaging weights 1/|J_i| (Section 4: identical entries per column, 1^T Q = 1^T).
+template <typename T>
+__global__ void k_q_sort(int nc, const int32_t* __restrict__ qrp, int32_t* __restrict__ qci, T* __restrict__ qv,
+                         const int32_t* __restrict__ pcnt) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    const int a = qrp[I], b = qrp[I + 1];
+    for (int p = a + 1; p < b; ++p) {
+        const int v = qci[p];
+        int q = p;
+        while (q > a && qci[q - 1] > v) {
+            qci[q] = qci[q - 1];
+            --q;
+        }
+        qci[q] = v;
+    }
+    for (int p = a; p < b; ++p) qv[p] = (T)(1.0 / (double)pcnt[qci[p]]);
+}
+
+template <typename T>
+void build_restriction(const EllView<T>& P, int nc, DevBuf<int32_t>& qrp, DevBuf<int32_t>& qci, DevBuf<T>& qv,
+                       cudaStream_t s) {
+    TmpBuf<int32_t> cnt(nc, s), cursor(nc, s);
+    BAMG_CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * nc, s));
+    BAMG_CK(cudaMemsetAsync(cursor.get(), 0, sizeof(int32_t) * nc, s));
+    BAMG_LAUNCH(k_q_count, blocks_for(P.n, 256), 256, 0, s, P.n, P.c, P.pcol, P.pcnt, cnt.get());
+    qrp.alloc(nc + 1);
+    exclusive_scan(cnt.get(), qrp.get(), nc, s);
+    const int nq = read_int(qrp.get() + nc, s);
+    qci.alloc(nq > 0 ? nq : 1);
+    qv.alloc(nq > 0 ? nq : 1);
+    BAMG_LAUNCH(k_q_fill, blocks_for(P.n, 256), 256, 0, s, P.n, P.c, P.pcol, P.pcnt, qrp.get(), cursor.get(), qci.get());
+    BAMG_LAUNCH(k_q_sort<T>, blocks_for(nc, 128), 128, 0, s, nc, qrp.get(), qci.get(), qv.get(), P.pcnt);
+}
+
+// ================================================================ Petrov-Galerkin
+// Every product Q[I,i] M[i,j] P[j,J] is enumerated in the order (i, j, slot) for each
+// coarse row I, rounded as ((q * m) * p); the products of one (I, J) are then summed in
+// that order.  This is the order of the plain definition, so a CPU evaluation of the
+// same sum in the same order gives the same bits.
+__global__ void k_gal_count(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
+                            const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const int32_t* __restrict__ pcnt, int32_t* __restrict__ np) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int s = 0;
+    for (int q = qrp[I]; q < qrp[I + 1]; ++q) {
+        const int i = qci[q];
+        for (int p = rp[i]; p < rp[i + 1]; ++p) s += pcnt[ci[p]];
+    }
+    np[I] = s;
+}
+
+template <typename T>
+__global__ void k_gal_expand(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
+                             const T* __restrict__ qv, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const T* __restrict__ bv, const T* __restrict__ tv, const int32_t* __restrict__ pcol,
+                             const T* __restrict__ pval, const int32_t* __restrict__ pcnt, int c,
+                             const int32_t* __restrict__ poff, int32_t* __restrict__ pJ, T* __restrict__ pvb,
+                             T* __restrict__ pvt) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int o = poff[I];
+    for (int q = qrp[I]; q < qrp[I + 1]; ++q) {
+        const int i = qci[q];
+        const T qq = qv[q];
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            const int j = ci[p];
+            const T qb = mul_rn(qq, bv[p]);
+            const T qt = tv ? mul_rn(qq, tv[p]) : (j == i ? qq : T(0));
+            const int cnt = pcnt[j];
+            for (int s = 0; s < cnt; ++s) {
+                const T pv = pval[(int64_t)j * c + s];
+                pJ[o] = pcol[(int64_t)j * c + s];
+                pvb[o] = mul_rn(qb, pv);
+                pvt[o] = mul_rn(qt, pv);
+                ++o;
+            }
+        }
+    }
+}
+
+constexpr int GAL_WARPS = 2;
+constexpr int GAL_CAP = 2048;
+
+template <typename T>
+__global__ void __launch_bounds__(GAL_WARPS * 32)
+    k_gal_reduce(int nc, const int32_t* __restrict__ poff, const int32_t* __restrict__ pJ, const T* __restrict__ pvb,
+                 const T* __restrict__ pvt, int32_t* __restrict__ ucnt, int32_t* __restrict__ uJ, T* __restrict__ ubv,
+                 T* __restrict__ utv, uint8_t* __restrict__ head) {
+    __shared__ unsigned long long s_keys[GAL_WARPS][GAL_CAP];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int I = blockIdx.x * GAL_WARPS + wid;
+    if (I >= nc) return;
+    const int o = poff[I], np = poff[I + 1] - o;
+    const unsigned lt = (1u << lane) - 1u;
+    if (np <= GAL_CAP) {
+        unsigned long long* keys = s_keys[wid];
+        int N = 32;
+        while (N < np) N <<= 1;
+        for (int e = lane; e < N; e += 32)
+            keys[e] = e < np ? (((unsigned long long)(unsigned)pJ[o + e] << 32) | (unsigned)e) : ~0ull;
+        __syncwarp();
+        for (int k = 2; k <= N; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int e = lane; e < N; e += 32) {
+                    const int pe = e ^ jj;
+                    if (pe > e) {
+                        const unsigned long long a = keys[e], b = keys[pe];
+                        const bool up = (e & k) == 0;
+                        if ((a > b) == up) {
+                            keys[e] = b;
+                            keys[pe] = a;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        int base = 0;
+        for (int e0 = 0; e0 < np; e0 += 32) {
+            const int e = e0 + lane;
+            const unsigned Je = e < np ? (unsigned)(keys[e] >> 32) : 0u;
+            const bool hd = e < np && (e == 0 || (unsigned)(keys[e - 1] >> 32) != Je);
+            const unsigned bal = __ballot_sync(0xffffffffu, hd);
+            if (hd) {
+                const int rank = base + __popc(bal & lt);
+                const int pos0 = (int)(keys[e] & 0xffffffffu);
+                T sb = pvb[o + pos0], st = pvt[o + pos0];
+                for (int e2 = e + 1; e2 < np && (unsigned)(keys[e2] >> 32) == Je; ++e2) {
+                    const int pos = (int)(keys[e2] & 0xffffffffu);
+                    sb = add_rn(sb, pvb[o + pos]);
+                    st = add_rn(st, pvt[o + pos]);
+                }
+                uJ[o + rank] = (int32_t)Je;
+                ubv[o + rank] = sb;
+                utv[o + rank] = st;
+            }
+            base += __popc(bal);
+        }
+        if (lane == 0) ucnt[I] = base;
+    } else {
+        // long rows: quadratic scan in global memory
+        for (int e = lane; e < np; e += 32) {
+            const int Je = pJ[o + e];
+            bool hd = true;
+            for (int e2 = 0; e2 < e; ++e2)
+                if (pJ[o + e2] == Je) {
+                    hd = false;
+                    break;
+                }
+            head[o + e] = hd ? 1 : 0;
+        }
+        __syncwarp();
+        int cnt = 0;
+        for (int e = lane; e < np; e += 32) {
+            if (!head[o + e]) continue;
+            ++cnt;
+            const int Je = pJ[o + e];
+            int rank = 0;
+            for (int e2 = 0; e2 < np; ++e2) rank += (head[o + e2] && pJ[o + e2] < Je);
+            T sb = pvb[o + e], st = pvt[o + e];
+            for (int e2 = e + 1; e2 < np; ++e2)
+                if (pJ[o + e2] == Je) {
+                    sb = add_rn(sb, pvb[o + e2]);
+                    st = add_rn(st, pvt[o + e2]);
+                }
+            uJ[o + rank] = Je;
+            ubv[o + rank] = sb;
+            utv[o + rank] = st;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        if (lane == 0) ucnt[I] = cnt;
+    }
+}
+
+template <typename T>
+__global__ void k_gal_compact(int nc, const int32_t* __restrict__ poff, const int32_t* __restrict__ ucnt,
+                              const int32_t* __restrict__ rpc, const int32_t* __restrict__ uJ, const T* __restrict__ ubv,
+                              const T* __restrict__ utv, int32_t* __restrict__ ci, T* __restrict__ bv,
+                              T* __restrict__ tv) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    const int o = poff[I], d = rpc[I];
+    for (int u = 0; u < ucnt[I]; ++u) {
+        ci[d + u] = uJ[o + u];
+        bv[d + u] = ubv[o + u];
+        tv[d + u] = utv[o + u];
+    }
+}
+
+template <typename T>
+void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int32_t* qci, const T* qv,
+              const EllView<T>& P, int nc, GalerkinOut<T>& out, cudaStream_t s) {
+    TmpBuf<int32_t> np(nc, s), poff(nc + 1, s);
+    BAMG_LAUNCH(k_gal_count, blocks_for(nc, 128), 128, 0, s, nc, qrp, qci, B.rp, B.ci, P.pcnt, np.get());
+    exclusive_scan(np.get(), poff.get(), nc, s);
+    const int total = read_int(poff.get() + nc, s);
+    BAMG_REQUIRE(total >= 0, BAMG_EINVAL, "galerkin: product count overflows int32");
+    const size_t tot = total > 0 ? (size_t)total : 1;
+    TmpBuf<int32_t> pJ(tot, s), uJ(tot, s), ucnt(nc, s);
+    TmpBuf<T> pvb(tot, s), pvt(tot, s), ubv(tot, s), utv(tot, s);
+    TmpBuf<uint8_t> head(tot, s);
+    BAMG_LAUNCH(k_gal_expand<T>, blocks_for(nc, 128), 128, 0, s, nc, qrp, qci, qv, B.rp, B.ci, B.v, T_val, P.pcol,
+                P.pval, P.pcnt, P.c, poff.get(), pJ.get(), pvb.get(), pvt.get());
+    BAMG_LAUNCH(k_gal_reduce<T>, blocks_for(nc, GAL_WARPS), GAL_WARPS * 32, 0, s, nc, poff.get(), pJ.get(), pvb.get(),
+                pvt.get(), ucnt.get(), uJ.get(), ubv.get(), utv.get(), head.get());
+    out.rp.alloc(nc + 1);
+    exclusive_scan(ucnt.get(), out.rp.get(), nc, s);
+    out.nnz = read_int(out.rp.get() + nc, s);
+    const size_t nz = out.nnz > 0 ? (size_t)out.nnz : 1;
+    out.ci.alloc(nz);
+    out.bv.alloc(nz);
+    out.tv.alloc(nz);
+    BAMG_LAUNCH(k_gal_compact<T>, blocks_for(nc, 128), 128, 0, s, nc, poff.get(), ucnt.get(), out.rp.get(), uJ.get(),
+                ubv.get(), utv.get(), out.ci.get(), out.bv.get(), out.tv.get());
+}
+
+template <typename T>
+__global__ void k_csr_to_dense(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const T* __restrict__ v, double* __restrict__ D) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) D[(int64_t)i * n + ci[p]] = (double)v[p];
+}
+template <typename T>
+void csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const T* v, double* D, cudaStream_t s) {
+    BAMG_CK(cudaMemsetAsync(D, 0, sizeof(double) * n * n, s));
+    if (n) BAMG_LAUNCH(k_csr_to_dense<T>, blocks_for(n, 64), 64, 0, s, n, rp, ci, v, D);
+}
+
+#define INST(T)                                                                                                     \
+    template int interp_ls<T>(int, const int32_t*, const int32_t*, const uint8_t*, const int32_t*, const T*, int,   \
+                              int, const double*, int, int, int, double, int32_t*, T*, int32_t*, cudaStream_t);     \
+    template void build_restriction<T>(const EllView<T>&, int, DevBuf<int32_t>&, DevBuf<int32_t>&, DevBuf<T>&,      \
+                                       cudaStream_t);                                                               \
+    template void galerkin<T>(const MatView<T>&, const T*, const int32_t*, const int32_t*, const T*,                \
+                              const EllView<T>&, int, GalerkinOut<T>&, cudaStream_t);                               \
+    template void csr_to_dense<T>(int, const int32_t*, const int32_t*, const T*, double*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace bamg

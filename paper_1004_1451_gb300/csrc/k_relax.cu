@@ -1,0 +1,519 @@
+// Relaxation and test-vector kernels: omega-Jacobi SpMM over row-interleaved blocks of
+// test vectors (Section 3, Eq. (3.1)), the shifted sweeps of Algorithm 3, the LS
+// weights of Section 3.2, Rayleigh-quotient updates, injection and prolongation of
+// vector blocks, and the construction of B = I - A.
+#include <cfloat>
+
+#include "kernels.cuh"
+
+namespace bamg {
+
+// ---------------------------------------------------------------- initial vectors
+template <typename T>
+__global__ void k_tv_init(int n, int ncols, int ld, int col0, uint64_t seed, double lo, double hi, T* X) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * ncols) return;
+    int i = (int)(t / ncols);
+    int k = (int)(t - (int64_t)i * ncols);
+    double u = counter_uniform(seed, STREAM_TV + (uint64_t)k, (uint64_t)i);
+    double v = __dadd_rn(lo, __dmul_rn(hi - lo, u));
+    X[(int64_t)i * ld + col0 + k] = (T)v;
+}
+
+template <typename T>
+void launch_tv_init(int n, int ncols, int ld, int col0, uint64_t seed, double lo, double hi, T* X, cudaStream_t s) {
+    int64_t work = (int64_t)n * ncols;
+    if (work == 0) return;
+    BAMG_LAUNCH(k_tv_init<T>, blocks_for(work, 256), 256, 0, s, n, ncols, ld, col0, seed, lo, hi, X);
+}
+
+// ---------------------------------------------------------------- diagonals
+template <typename T>
+__global__ void k_diag(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
+                       T* __restrict__ d) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T x = T(0);
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+        if (ci[p] == i) {
+            x = v[p];
+            break;
+        }
+    d[i] = x;
+}
+template <typename T>
+void launch_diag_vals(int n, const int32_t* rp, const int32_t* ci, const T* vals, T* d, cudaStream_t s) {
+    if (n) BAMG_LAUNCH(k_diag<T>, blocks_for(n, 256), 256, 0, s, n, rp, ci, vals, d);
+}
+template <typename T>
+void launch_diag(const MatView<T>& M, T* d, cudaStream_t s) {
+    launch_diag_vals<T>(M.n, M.rp, M.ci, M.v, d, s);
+}
+
+template <typename T>
+__global__ void k_reciprocal(int n, const T* d, T* dinv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dinv[i] = T(1) / d[i];
+}
+template <typename T>
+void launch_reciprocal(int n, const T* d, T* dinv, cudaStream_t s) {
+    if (n) BAMG_LAUNCH(k_reciprocal<T>, blocks_for(n, 256), 256, 0, s, n, d, dinv);
+}
+
+template <typename T>
+__global__ void k_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* tv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) tv[p] = (ci[p] == i) ? T(1) : T(0);
+}
+template <typename T>
+void launch_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* tv, cudaStream_t s) {
+    if (n) BAMG_LAUNCH(k_identity_on_pattern<T>, blocks_for(n, 256), 256, 0, s, n, rp, ci, tv);
+}
+
+// ---------------------------------------------------------------- omega-Jacobi SpMM
+// One thread owns one 16-byte chunk (W columns) of one row: it walks the row of B once,
+// gathering the matching chunk of each neighbour's test-vector row (contiguous in the
+// row-interleaved layout), so the W columns share every matrix load.
+template <typename T, bool SHIFT>
+__global__ void __launch_bounds__(256)
+    k_jacobi(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
+             const T* __restrict__ tv, const T* __restrict__ dB, const T* __restrict__ dinvB, const T* __restrict__ dT,
+             const double* __restrict__ lam, int ncols, const T* __restrict__ X, T* __restrict__ Y, int ld, int col0,
+             int nvec, T omega) {
+    constexpr int W = V16<T>::W;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int row = (int)(t / nvec);
+    if (row >= n) return;
+    int ch = (int)(t - (int64_t)row * nvec);
+    int off = col0 + ch * W;
+    T acc[W], accT[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) acc[e] = accT[e] = T(0);
+    const int p0 = rp[row], p1 = rp[row + 1];
+    for (int p = p0; p < p1; ++p) {
+        const int j = __ldg(ci + p);
+        T xv[W];
+        V16<T>::load(X + (int64_t)j * ld + off, xv);
+        const T b = __ldg(bv + p);
+#pragma unroll
+        for (int e = 0; e < W; ++e) acc[e] += b * xv[e];
+        if (SHIFT && tv != nullptr) {
+            const T tt = __ldg(tv + p);
+#pragma unroll
+            for (int e = 0; e < W; ++e) accT[e] += tt * xv[e];
+        }
+    }
+    T xs[W], y[W];
+    V16<T>::load(X + (int64_t)row * ld + off, xs);
+    if (SHIFT) {
+        const T db = dB[row];
+        const T dt = tv ? dT[row] : T(1);
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            const int c = ch * W + e;
+            const T l = c < ncols ? (T)lam[c] : T(0);
+            const T tx = tv ? accT[e] : xs[e];
+            const T r = acc[e] - l * tx;
+            const T d = db - l * dt;
+            y[e] = xs[e] - omega * r / d;
+        }
+    } else {
+        const T di = dinvB[row];
+#pragma unroll
+        for (int e = 0; e < W; ++e) y[e] = xs[e] - omega * (di * acc[e]);
+    }
+    V16<T>::store(Y + (int64_t)row * ld + off, y);
+}
+
+template <typename T>
+__global__ void k_copy_cols(int n, const T* __restrict__ src, T* __restrict__ dst, int ld, int col0, int nvec) {
+    constexpr int W = V16<T>::W;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int row = (int)(t / nvec);
+    if (row >= n) return;
+    int ch = (int)(t - (int64_t)row * nvec);
+    T v[W];
+    V16<T>::load(src + (int64_t)row * ld + col0 + ch * W, v);
+    V16<T>::store(dst + (int64_t)row * ld + col0 + ch * W, v);
+}
+
+template <typename T>
+void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, const T* dT, const double* d_lambda,
+           int ncols, int ld, int col0, T omega, int nu, T* X, T* work, cudaStream_t s) {
+    constexpr int W = V16<T>::W;
+    const int nvec = (ncols + W - 1) / W;
+    if (B.n == 0 || nvec == 0 || nu <= 0) return;
+    const int64_t work_items = (int64_t)B.n * nvec;
+    const unsigned grid = blocks_for(work_items, 256);
+    T* src = X;
+    T* dst = work;
+    for (int k = 0; k < nu; ++k) {
+        if (d_lambda)
+            BAMG_LAUNCH((k_jacobi<T, true>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda,
+                        ncols, src, dst, ld, col0, nvec, omega);
+        else
+            BAMG_LAUNCH((k_jacobi<T, false>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda,
+                        ncols, src, dst, ld, col0, nvec, omega);
+        T* t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != X) BAMG_LAUNCH(k_copy_cols<T>, grid, 256, 0, s, B.n, src, X, ld, col0, nvec);
+}
+
+// ---------------------------------------------------------------- column statistics
+// MODE 0: (sum x^2, sum (Bx)^2) per column; MODE 1: (sum x (Bx), sum x (Tx)).
+// Block (nvec x ny): threads own chunks of rows in a grid-stride loop; per-thread sums
+// in T, then a fixed-order tree in FP64 per block, then a fixed-order sum over blocks.
+template <typename T, int MODE>
+__global__ void k_colstats(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const T* __restrict__ bv, const T* __restrict__ tv, const T* __restrict__ X, int ld,
+                           int col0, int nvec, double* __restrict__ partial) {
+    constexpr int W = V16<T>::W;
+    extern __shared__ double sh[];
+    const int ch = threadIdx.x, ry = threadIdx.y, ny = blockDim.y;
+    const int off = col0 + ch * W;
+    T s0[W], s1[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) s0[e] = s1[e] = T(0);
+    for (int row = blockIdx.x * ny + ry; row < n; row += gridDim.x * ny) {
+        T acc[W], accT[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) acc[e] = accT[e] = T(0);
+        for (int p = rp[row]; p < rp[row + 1]; ++p) {
+            const int j = ci[p];
+            T xv[W];
+            V16<T>::load(X + (int64_t)j * ld + off, xv);
+            const T b = bv[p];
+#pragma unroll
+            for (int e = 0; e < W; ++e) acc[e] += b * xv[e];
+            if (MODE == 1 && tv != nullptr) {
+                const T tt = tv[p];
+#pragma unroll
+                for (int e = 0; e < W; ++e) accT[e] += tt * xv[e];
+            }
+        }
+        T xs[W];
+        V16<T>::load(X + (int64_t)row * ld + off, xs);
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            if (MODE == 0) {
+                s0[e] += xs[e] * xs[e];
+                s1[e] += acc[e] * acc[e];
+            } else {
+                s0[e] += xs[e] * acc[e];
+                s1[e] += xs[e] * (tv ? accT[e] : xs[e]);
+            }
+        }
+    }
+    const int base = (ry * nvec + ch) * 2 * W;
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        sh[base + e] = (double)s0[e];
+        sh[base + W + e] = (double)s1[e];
+    }
+    __syncthreads();
+    for (int stride = ny >> 1; stride > 0; stride >>= 1) {
+        if (ry < stride) {
+            const int o = ((ry + stride) * nvec + ch) * 2 * W;
+            for (int q = 0; q < 2 * W; ++q) sh[base + q] += sh[o + q];
+        }
+        __syncthreads();
+    }
+    if (ry == 0)
+        for (int q = 0; q < 2 * W; ++q) partial[(int64_t)blockIdx.x * (nvec * 2 * W) + ch * 2 * W + q] = sh[base + q];
+}
+
+__global__ void k_reduce_partials(int nblocks, int width, const double* __restrict__ partial, double* __restrict__ out) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= width) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * width + q];
+    out[q] = s;
+}
+
+template <typename T, int MODE>
+static void colstats(const MatView<T>& B, const T* T_val, const T* X, int ld, int col0, int ncols, double* d_sums,
+                     cudaStream_t s) {
+    constexpr int W = V16<T>::W;
+    const int nvec = (ncols + W - 1) / W;
+    int ny = 1;
+    while (ny * 2 * nvec <= 256) ny *= 2;
+    int nb = (int)blocks_for(B.n, ny);
+    if (nb > 512) nb = 512;
+    const int width = nvec * 2 * W;
+    TmpBuf<double> partial((size_t)nb * width, s);
+    size_t smem = (size_t)ny * nvec * 2 * W * sizeof(double);
+    BAMG_LAUNCH((k_colstats<T, MODE>), nb, dim3(nvec, ny), smem, s, B.n, B.rp, B.ci, B.v, T_val, X, ld, col0, nvec,
+                partial.get());
+    BAMG_LAUNCH(k_reduce_partials, blocks_for(width, 64), 64, 0, s, nb, width, partial.get(), d_sums);
+}
+
+// ---------------------------------------------------------------- LS weights
+__global__ void k_weights(int ncols, int W, const double* __restrict__ sums, const uint8_t* __restrict__ active,
+                          double floor, double* __restrict__ w, double* __restrict__ nrm) {
+    const int k = threadIdx.x;  // one warp, ncols <= 32
+    double m = 0.0, nk = 1.0;
+    if (k < ncols) {
+        const int ch = k / W, e = k - ch * W;
+        const double xx = sums[ch * 2 * W + e], bb = sums[ch * 2 * W + W + e];
+        const bool act = active ? active[k] != 0 : true;
+        if (act && xx > 0.0) {
+            nk = sqrt(xx);
+            m = 1.0 / fmax(bb / xx, floor);
+        }
+    }
+    double mx = m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (k < ncols) {
+        w[k] = mx > 0.0 ? m / mx : 0.0;
+        nrm[k] = nk;
+    }
+}
+
+template <typename T>
+__global__ void k_scale_cols(int n, T* __restrict__ X, int ld, int col0, int ncols, const double* __restrict__ nrm) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int row = (int)(t / ncols);
+    if (row >= n) return;
+    int k = (int)(t - (int64_t)row * ncols);
+    const double d = nrm[k];
+    if (d != 1.0) {
+        T* p = X + (int64_t)row * ld + col0 + k;
+        *p = (T)((double)*p / d);
+    }
+}
+
+template <typename T>
+void tv_weights(const MatView<T>& B, int ncols, int ld, int col0, const uint8_t* d_active, double floor, T* X,
+                double* d_w, cudaStream_t s) {
+    constexpr int W = V16<T>::W;
+    BAMG_REQUIRE(ncols >= 1 && ncols <= 32, BAMG_EINVAL, "tv_weights: 1 <= ncols <= 32");
+    const int nvec = (ncols + W - 1) / W;
+    TmpBuf<double> sums((size_t)nvec * 2 * W, s);
+    TmpBuf<double> nrm(32, s);
+    colstats<T, 0>(B, nullptr, X, ld, col0, ncols, sums.get(), s);
+    BAMG_LAUNCH(k_weights, 1, 32, 0, s, ncols, W, sums.get(), d_active, floor, d_w, nrm.get());
+    BAMG_LAUNCH(k_scale_cols<T>, blocks_for((int64_t)B.n * ncols, 256), 256, 0, s, B.n, X, ld, col0, ncols, nrm.get());
+}
+
+// ---------------------------------------------------------------- Rayleigh update
+__global__ void k_rayleigh(int ncols, int W, const double* __restrict__ sums, double tol, double* __restrict__ lam,
+                           uint8_t* __restrict__ sel) {
+    const int k = threadIdx.x;
+    if (k >= ncols) return;
+    const int ch = k / W, e = k - ch * W;
+    const double num = sums[ch * 2 * W + e], den = sums[ch * 2 * W + W + e];
+    const double old = lam[k];
+    const double nw = (k == 0) ? 0.0 : num / den;
+    const double change = fabs(nw - old) / fmax(fabs(old), 1e-300);
+    sel[k] = (k == 0 || change > tol) ? 1 : 0;
+    lam[k] = nw;
+}
+
+template <typename T>
+void rayleigh_update(const MatView<T>& B, const T* T_val, const T* X, int ncols, int ld, int col0, double tol,
+                     double* d_lam, uint8_t* d_sel, cudaStream_t s) {
+    constexpr int W = V16<T>::W;
+    const int nvec = (ncols + W - 1) / W;
+    TmpBuf<double> sums((size_t)nvec * 2 * W, s);
+    colstats<T, 1>(B, T_val, X, ld, col0, ncols, sums.get(), s);
+    BAMG_LAUNCH(k_rayleigh, 1, 32, 0, s, ncols, W, sums.get(), tol, d_lam, d_sel);
+}
+
+// ---------------------------------------------------------------- injection / prolongation
+template <typename T>
+__global__ void k_inject(int nc, const int32_t* __restrict__ c2f, const T* __restrict__ X, T* __restrict__ Xc, int ld,
+                         int col0, int nvec) {
+    constexpr int W = V16<T>::W;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int I = (int)(t / nvec);
+    if (I >= nc) return;
+    int ch = (int)(t - (int64_t)I * nvec);
+    T v[W];
+    V16<T>::load(X + (int64_t)c2f[I] * ld + col0 + ch * W, v);
+    V16<T>::store(Xc + (int64_t)I * ld + col0 + ch * W, v);
+}
+template <typename T>
+void inject_cols(int nc, const int32_t* c2f, const T* X, T* Xc, int ld, int col0, int ncols, cudaStream_t s) {
+    constexpr int W = V16<T>::W;
+    const int nvec = (ncols + W - 1) / W;
+    if (nc && nvec) BAMG_LAUNCH(k_inject<T>, blocks_for((int64_t)nc * nvec, 256), 256, 0, s, nc, c2f, X, Xc, ld, col0, nvec);
+}
+
+template <typename T>
+__global__ void k_prolong_cols(int n, int c, const int32_t* __restrict__ pcol, const T* __restrict__ pval,
+                               const int32_t* __restrict__ pcnt, const T* __restrict__ Xc, T* __restrict__ X, int ld,
+                               int col0, int nvec) {
+    constexpr int W = V16<T>::W;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = (int)(t / nvec);
+    if (i >= n) return;
+    int ch = (int)(t - (int64_t)i * nvec);
+    T acc[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) acc[e] = T(0);
+    const int cnt = pcnt[i];
+    for (int q = 0; q < cnt; ++q) {
+        const int J = pcol[(int64_t)i * c + q];
+        const T pv = pval[(int64_t)i * c + q];
+        T xv[W];
+        V16<T>::load(Xc + (int64_t)J * ld + col0 + ch * W, xv);
+#pragma unroll
+        for (int e = 0; e < W; ++e) acc[e] += pv * xv[e];
+    }
+    V16<T>::store(X + (int64_t)i * ld + col0 + ch * W, acc);
+}
+template <typename T>
+void prolong_cols(const EllView<T>& P, const T* Xc, T* X, int ld, int col0, int ncols, cudaStream_t s) {
+    constexpr int W = V16<T>::W;
+    const int nvec = (ncols + W - 1) / W;
+    if (P.n && nvec)
+        BAMG_LAUNCH(k_prolong_cols<T>, blocks_for((int64_t)P.n * nvec, 256), 256, 0, s, P.n, P.c, P.pcol, P.pval,
+                    P.pcnt, Xc, X, ld, col0, nvec);
+}
+
+// ---------------------------------------------------------------- conversions
+template <typename Tin, typename Tout>
+__global__ void k_convert(int64_t n, const Tin* a, Tout* b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (Tout)a[i];
+}
+template <typename Tin, typename Tout>
+void launch_convert(int64_t n, const Tin* a, Tout* b, cudaStream_t s) {
+    if (n > 0) BAMG_LAUNCH((k_convert<Tin, Tout>), blocks_for(n, 256), 256, 0, s, n, a, b);
+}
+template <typename Tin, typename Tout>
+__global__ void k_strided_to_vec(int n, const Tin* X, int ld, int col, Tout* y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (Tout)X[(int64_t)i * ld + col];
+}
+template <typename Tin, typename Tout>
+void launch_strided_to_vec(int n, const Tin* X, int ld, int col, Tout* y, cudaStream_t s) {
+    if (n) BAMG_LAUNCH((k_strided_to_vec<Tin, Tout>), blocks_for(n, 256), 256, 0, s, n, X, ld, col, y);
+}
+template <typename Tin, typename Tout>
+__global__ void k_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) X[(int64_t)i * ld + col] = (Tout)y[i];
+}
+template <typename Tin, typename Tout>
+void launch_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col, cudaStream_t s) {
+    if (n) BAMG_LAUNCH((k_vec_to_strided<Tin, Tout>), blocks_for(n, 256), 256, 0, s, n, y, X, ld, col);
+}
+
+// ---------------------------------------------------------------- B = I - A
+__global__ void k_count_B(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ v, int32_t* __restrict__ cnt, int* __restrict__ flags,
+                          double* __restrict__ colsum) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int f = 0;
+    bool has_diag = false;
+    const int p0 = rp[i], p1 = rp[i + 1];
+    if (p1 < p0) f |= 8;
+    for (int p = p0; p < p1; ++p) {
+        const int j = ci[p];
+        if (j < 0 || j >= n || (p > p0 && j <= ci[p - 1])) {
+            f |= 8;
+            continue;
+        }
+        const double a = v[p];
+        if (!(a >= 0.0)) f |= 1;
+        if (j == i) {
+            has_diag = true;
+            if (a >= 1.0) f |= 4;
+        }
+        atomicAdd(colsum + j, a);
+    }
+    cnt[i] = (p1 - p0) + (has_diag ? 0 : 1);
+    if (f) atomicOr(flags, f);
+}
+
+__global__ void k_fill_B(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const double* __restrict__ v, const int32_t* __restrict__ rpB, int32_t* __restrict__ ciB,
+                         double* __restrict__ vB) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int q = rpB[i];
+    bool done = false;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int j = ci[p];
+        if (!done && j > i) {
+            ciB[q] = i;
+            vB[q] = 1.0;
+            ++q;
+            done = true;
+        }
+        if (j == i) {
+            ciB[q] = i;
+            vB[q] = 1.0 - v[p];
+            done = true;
+        } else {
+            ciB[q] = j;
+            vB[q] = -v[p];
+        }
+        ++q;
+    }
+    if (!done) {
+        ciB[q] = i;
+        vB[q] = 1.0;
+    }
+}
+
+__global__ void k_check_colsum(int n, const double* __restrict__ colsum, int* __restrict__ flags) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n && !(fabs(colsum[j] - 1.0) <= 1e-12)) atomicOr(flags, 2);
+}
+
+int build_system_matrix(int n, int nnzA, const int32_t* rpA, const int32_t* ciA, const double* vA,
+                        DevBuf<int32_t>& rpB, DevBuf<int32_t>& ciB, DevBuf<double>& vB, cudaStream_t s) {
+    TmpBuf<int32_t> cnt(n, s);
+    TmpBuf<double> colsum(n, s);
+    TmpBuf<int> flags(1, s);
+    BAMG_CK(cudaMemsetAsync(colsum.get(), 0, sizeof(double) * n, s));
+    BAMG_CK(cudaMemsetAsync(flags.get(), 0, sizeof(int), s));
+    BAMG_LAUNCH(k_count_B, blocks_for(n, 256), 256, 0, s, n, rpA, ciA, vA, cnt.get(), flags.get(), colsum.get());
+    BAMG_LAUNCH(k_check_colsum, blocks_for(n, 256), 256, 0, s, n, colsum.get(), flags.get());
+    int h_flags = 0;
+    BAMG_CK(cudaMemcpyAsync(&h_flags, flags.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CK(cudaStreamSynchronize(s));
+    if (h_flags) return h_flags;
+    rpB.alloc(n + 1);
+    exclusive_scan(cnt.get(), rpB.get(), n, s);
+    const int nnzB = read_int(rpB.get() + n, s);
+    ciB.alloc(nnzB);
+    vB.alloc(nnzB);
+    BAMG_LAUNCH(k_fill_B, blocks_for(n, 256), 256, 0, s, n, rpA, ciA, vA, rpB.get(), ciB.get(), vB.get());
+    (void)nnzA;
+    return 0;
+}
+
+// ---------------------------------------------------------------- instantiations
+#define INST(T)                                                                                                    \
+    template void launch_tv_init<T>(int, int, int, int, uint64_t, double, double, T*, cudaStream_t);               \
+    template void launch_diag<T>(const MatView<T>&, T*, cudaStream_t);                                             \
+    template void launch_diag_vals<T>(int, const int32_t*, const int32_t*, const T*, T*, cudaStream_t);            \
+    template void launch_reciprocal<T>(int, const T*, T*, cudaStream_t);                                           \
+    template void launch_identity_on_pattern<T>(int, const int32_t*, const int32_t*, T*, cudaStream_t);            \
+    template void relax<T>(const MatView<T>&, const T*, const T*, const T*, const T*, const double*, int, int, int, \
+                           T, int, T*, T*, cudaStream_t);                                                          \
+    template void tv_weights<T>(const MatView<T>&, int, int, int, const uint8_t*, double, T*, double*, cudaStream_t); \
+    template void rayleigh_update<T>(const MatView<T>&, const T*, const T*, int, int, int, double, double*,         \
+                                     uint8_t*, cudaStream_t);                                                      \
+    template void inject_cols<T>(int, const int32_t*, const T*, T*, int, int, int, cudaStream_t);                  \
+    template void prolong_cols<T>(const EllView<T>&, const T*, T*, int, int, int, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+template void launch_convert<double, float>(int64_t, const double*, float*, cudaStream_t);
+template void launch_convert<float, double>(int64_t, const float*, double*, cudaStream_t);
+template void launch_convert<double, double>(int64_t, const double*, double*, cudaStream_t);
+template void launch_strided_to_vec<float, double>(int, const float*, int, int, double*, cudaStream_t);
+template void launch_strided_to_vec<double, double>(int, const double*, int, int, double*, cudaStream_t);
+template void launch_vec_to_strided<double, float>(int, const double*, float*, int, int, cudaStream_t);
+template void launch_vec_to_strided<double, double>(int, const double*, double*, int, int, cudaStream_t);
+
+}  // namespace bamg

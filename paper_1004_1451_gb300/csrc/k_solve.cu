@@ -1,0 +1,328 @@
+// Solve phase: the V(nu1, nu2) cycle whose error propagator is Eq. (4.4),
+// S^nu2 (I - P C_{l+1} Q B) S^nu1 with S = I - omega D^{-1} B and C_L = B_L^+, and the
+// FP64 pieces of flexible GMRES on B x = 0 (Section 4.2): sparse products with B,
+// classical Gram-Schmidt dots and updates, Givens rotations, the update x0 + Z y, and
+// the true residual ||B x||_1 / ||x||_1.
+#include "gmres_state.cuh"
+#include "kernels.cuh"
+
+namespace bamg {
+
+// ---------------------------------------------------------------- V-cycle kernels
+template <typename T>
+__global__ void k_smooth0(int n, const T* __restrict__ dinv, const T* __restrict__ b, T* __restrict__ x, T omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = (omega * dinv[i]) * b[i];
+}
+
+template <typename T>
+__global__ void k_smooth(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const T* __restrict__ bv, const T* __restrict__ dinv, const T* __restrict__ b,
+                         const T* __restrict__ x, T* __restrict__ y, T omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0);
+    for (int p = rp[i]; p < rp[i + 1]; ++p) s += bv[p] * x[ci[p]];
+    y[i] = x[i] + (omega * dinv[i]) * (b[i] - s);
+}
+
+template <typename T>
+__global__ void k_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                        const T* __restrict__ bv, const T* __restrict__ b, const T* __restrict__ x,
+                        T* __restrict__ r) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0);
+    for (int p = rp[i]; p < rp[i + 1]; ++p) s += bv[p] * x[ci[p]];
+    r[i] = b[i] - s;
+}
+
+template <typename T>
+__global__ void k_restrict(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
+                           const T* __restrict__ qv, const T* __restrict__ r, T* __restrict__ bc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    T s = T(0);
+    for (int q = qrp[I]; q < qrp[I + 1]; ++q) s += qv[q] * r[qci[q]];
+    bc[I] = s;
+}
+
+template <typename T>
+__global__ void k_prolong_add(int n, int c, const int32_t* __restrict__ pcol, const T* __restrict__ pval,
+                              const int32_t* __restrict__ pcnt, const T* __restrict__ ec, T* __restrict__ x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = T(0);
+    for (int t = 0; t < pcnt[i]; ++t) s += pval[(int64_t)i * c + t] * ec[pcol[(int64_t)i * c + t]];
+    x[i] = x[i] + s;
+}
+
+// Coarsest level: x = B_L^+ b, one warp per row.
+template <typename T>
+__global__ void k_dense_mv(int n, const T* __restrict__ A, const T* __restrict__ b, T* __restrict__ x) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    T s = T(0);
+    for (int c = lane; c < n; c += 32) s += A[(int64_t)row * n + c] * b[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = s;
+}
+
+template <typename T>
+__global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+template <typename T>
+void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int nu_pre, int nu_post, cudaStream_t s) {
+    const int L = (int)lv.size() - 1;
+    const T omega = (T)omega_d;
+    std::vector<T*> xcur(L + 1), xtmp(L + 1);
+    for (int l = 0; l < L; ++l) {
+        const VLevel<T>& v = lv[l];
+        const int n = v.B.n;
+        const unsigned g = blocks_for(n, 256);
+        T* x = v.x;
+        T* t = v.r;
+        if (nu_pre >= 1) {
+            BAMG_LAUNCH(k_smooth0<T>, g, 256, 0, s, n, v.dinv, v.b, x, omega);
+            for (int k = 1; k < nu_pre; ++k) {
+                BAMG_LAUNCH(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega);
+                T* q = x;
+                x = t;
+                t = q;
+            }
+        } else {
+            BAMG_CK(cudaMemsetAsync(x, 0, sizeof(T) * n, s));
+        }
+        BAMG_LAUNCH(k_resid<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.b, x, t);
+        const int nc = lv[l + 1].B.n;
+        BAMG_LAUNCH(k_restrict<T>, blocks_for(nc, 256), 256, 0, s, nc, v.qrp, v.qci, v.qv, t, lv[l + 1].b);
+        xcur[l] = x;
+        xtmp[l] = t;
+    }
+    {
+        const int n = lv[L].B.n;
+        BAMG_LAUNCH(k_dense_mv<T>, blocks_for(n, 4), 128, 0, s, n, pinv, lv[L].b, lv[L].x);
+        xcur[L] = lv[L].x;
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        const VLevel<T>& v = lv[l];
+        const int n = v.B.n;
+        const unsigned g = blocks_for(n, 256);
+        T* x = xcur[l];
+        T* t = xtmp[l];
+        BAMG_LAUNCH(k_prolong_add<T>, g, 256, 0, s, n, v.P.c, v.P.pcol, v.P.pval, v.P.pcnt, xcur[l + 1], x);
+        for (int k = 0; k < nu_post; ++k) {
+            BAMG_LAUNCH(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega);
+            T* q = x;
+            x = t;
+            t = q;
+        }
+        xcur[l] = x;
+    }
+    if (L > 0 && xcur[0] != lv[0].x) BAMG_LAUNCH(k_copy<T>, blocks_for(lv[0].B.n, 256), 256, 0, s, lv[0].B.n, xcur[0], lv[0].x);
+}
+
+// ---------------------------------------------------------------- FP64 Krylov pieces
+template <typename TX>
+__global__ void k_spmv64(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const double* __restrict__ bv, const TX* __restrict__ x, double* __restrict__ y, double alpha) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) s += bv[p] * (double)x[ci[p]];
+    y[i] = alpha * s;
+}
+void spmv_f64(const MatView<double>& B, const double* x, double* y, double alpha, cudaStream_t s) {
+    BAMG_LAUNCH(k_spmv64<double>, blocks_for(B.n, 256), 256, 0, s, B.n, B.rp, B.ci, B.v, x, y, alpha);
+}
+void spmv_f64_from_f32(const MatView<double>& B, const float* x, double* y, cudaStream_t s) {
+    BAMG_LAUNCH(k_spmv64<float>, blocks_for(B.n, 256), 256, 0, s, B.n, B.rp, B.ci, B.v, x, y, 1.0);
+}
+
+constexpr int DOT_ROWS = 2048;
+int dots_partial_blocks(int n) { return (int)blocks_for(n, DOT_ROWS); }
+
+__global__ void __launch_bounds__(256) k_dots_partial(int n, const double* __restrict__ V, int64_t ldv, int nv,
+                                                      const double* __restrict__ w, double* __restrict__ partial) {
+    __shared__ double sw[DOT_ROWS];
+    const int r0 = blockIdx.x * DOT_ROWS;
+    const int cnt = min(DOT_ROWS, n - r0);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sw[e] = w[r0 + e];
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = wid; q < nv; q += nw) {
+        const double* vq = V + (int64_t)q * ldv + r0;
+        double acc = 0.0;
+        for (int e = lane; e < cnt; e += 32) acc += vq[e] * sw[e];
+        acc = warp_sum(acc);
+        if (lane == 0) partial[(int64_t)blockIdx.x * nv + q] = acc;
+    }
+}
+
+__global__ void k_reduce_cols(int nb, int nv, const double* __restrict__ partial, double* __restrict__ h) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nv) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * nv + q];
+    h[q] = s;
+}
+
+void dots(int n, const double* V, int64_t ldv, int nv, const double* w, double* d_h, double* d_partial,
+          cudaStream_t s) {
+    const int nb = dots_partial_blocks(n);
+    BAMG_LAUNCH(k_dots_partial, nb, 256, 0, s, n, V, ldv, nv, w, d_partial);
+    BAMG_LAUNCH(k_reduce_cols, blocks_for(nv, 64), 64, 0, s, nb, nv, d_partial, d_h);
+}
+
+__global__ void k_update_minus(int n, const double* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ h,
+                               double* __restrict__ w) {
+    __shared__ double sh[GMRES_MMAX + 1];
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) sh[q] = h[q];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = w[i];
+    for (int q = 0; q < nv; ++q) s -= V[(int64_t)q * ldv + i] * sh[q];
+    w[i] = s;
+}
+void update_minus(int n, const double* V, int64_t ldv, int nv, const double* d_h, double* w, cudaStream_t s) {
+    BAMG_LAUNCH(k_update_minus, blocks_for(n, 256), 256, 0, s, n, V, ldv, nv, d_h, w);
+}
+
+template <typename TZ>
+__global__ void k_form_x(int n, const double* __restrict__ x0, const TZ* __restrict__ Z, int64_t ldz, int nz,
+                         const double* __restrict__ y, double* __restrict__ x) {
+    __shared__ double sy[GMRES_MMAX];
+    for (int q = threadIdx.x; q < nz; q += blockDim.x) sy[q] = y[q];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int q = 0; q < nz; ++q) s += (double)Z[(int64_t)q * ldz + i] * sy[q];
+    x[i] = x0[i] + s;
+}
+template <typename TZ>
+void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const double* d_y, double* x, cudaStream_t s) {
+    BAMG_LAUNCH(k_form_x<TZ>, blocks_for(n, 256), 256, 0, s, n, x0, Z, ldz, nz, d_y, x);
+}
+
+// sums of |Bx|, (Bx)^2, |x| and x over rows: per-block partials then a fixed-order sum.
+__global__ void __launch_bounds__(256) k_resnorm_partial(int n, const int32_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ ci, const double* __restrict__ bv,
+                                                         const double* __restrict__ x, double* __restrict__ partial) {
+    __shared__ double sh[4][8];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double a = 0.0, b2 = 0.0, c = 0.0, d = 0.0;
+    if (i < n) {
+        double s = 0.0;
+        for (int p = rp[i]; p < rp[i + 1]; ++p) s += bv[p] * x[ci[p]];
+        a = fabs(s);
+        b2 = s * s;
+        c = fabs(x[i]);
+        d = x[i];
+    }
+    a = warp_sum(a);
+    b2 = warp_sum(b2);
+    c = warp_sum(c);
+    d = warp_sum(d);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sh[0][wid] = a;
+        sh[1][wid] = b2;
+        sh[2][wid] = c;
+        sh[3][wid] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * 4 + threadIdx.x] = t;
+    }
+}
+void residual_norms(const MatView<double>& B, const double* x, double* d_out, double* d_partial, cudaStream_t s) {
+    const int nb = (int)blocks_for(B.n, 256);
+    BAMG_LAUNCH(k_resnorm_partial, nb, 256, 0, s, B.n, B.rp, B.ci, B.v, x, d_partial);
+    BAMG_LAUNCH(k_reduce_cols, 1, 64, 0, s, nb, 4, d_partial, d_out);
+}
+
+// y = x * num or x / num with num = d_num[num_idx] (a device scalar).
+__global__ void k_scale_vec(int n, const double* __restrict__ x, const double* __restrict__ d_num, int num_idx,
+                            int reciprocal, double* __restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = d_num[num_idx];
+    y[i] = reciprocal ? (a != 0.0 ? x[i] / a : 0.0) : x[i] * a;
+}
+void scale_vec(int n, double* x, const double* d_num, int num_idx, bool reciprocal, double* y, cudaStream_t s) {
+    BAMG_LAUNCH(k_scale_vec, blocks_for(n, 256), 256, 0, s, n, x, d_num, num_idx, reciprocal ? 1 : 0, y);
+}
+
+// Givens update of column j (Saad, Iterative Methods for Sparse Linear Systems, Alg. 6.9
+// as a rotation sequence): h = h1 + h2 from the two Gram-Schmidt passes, h_{j+1,j} =
+// sqrt(nrm2); previous rotations are applied, a new one annihilates h_{j+1,j}, and
+// |g_{j+1}| is the residual norm of the least-squares problem.
+__global__ void k_givens(double* __restrict__ st, int j, int m) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    GmresLayout L(m);
+    double col[GMRES_MMAX + 1];
+    for (int i = 0; i <= j; ++i) col[i] = st[L.h1 + i] + st[L.h2 + i];
+    const double hn = sqrt(st[L.nrm2]);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double c = st[L.cs + i], s = st[L.sn + i];
+        const double a = col[i], b = col[i + 1];
+        col[i] = c * a + s * b;
+        col[i + 1] = -s * a + c * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double den = hypot(a, b);
+    const double c = den == 0.0 ? 1.0 : a / den, s = den == 0.0 ? 0.0 : b / den;
+    st[L.cs + j] = c;
+    st[L.sn + j] = s;
+    col[j] = c * a + s * b;
+    const double gj = st[L.g + j];
+    st[L.g + j + 1] = -s * gj;
+    st[L.g + j] = c * gj;
+    for (int i = 0; i <= j; ++i) st[L.R + i + (int64_t)j * m] = col[i];
+    st[L.est] = fabs(st[L.g + j + 1]);
+    st[L.hn] = hn;
+}
+void gmres_arnoldi_step(double* d_state, int j, int m, cudaStream_t s) {
+    BAMG_LAUNCH(k_givens, 1, 32, 0, s, d_state, j, m);
+}
+
+// Start of a cycle: beta = ||r0||_2 from nrm2, g = beta e_1; hn = beta scales v_1.
+__global__ void k_gmres_init(double* __restrict__ st, int m) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    GmresLayout L(m);
+    const double beta = sqrt(st[L.nrm2]);
+    for (int i = 0; i <= m; ++i) st[L.g + i] = 0.0;
+    st[L.g] = beta;
+    st[L.hn] = beta;
+    st[L.est] = beta;
+}
+void gmres_init(double* d_state, int m, cudaStream_t s) { BAMG_LAUNCH(k_gmres_init, 1, 32, 0, s, d_state, m); }
+
+// y = R^{-1} g for the leading (j+1) x (j+1) block.
+__global__ void k_solve_y(double* __restrict__ st, int j, int m) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    GmresLayout L(m);
+    for (int r = j; r >= 0; --r) {
+        double s = st[L.g + r];
+        for (int q = r + 1; q <= j; ++q) s -= st[L.R + r + (int64_t)q * m] * st[L.y + q];
+        st[L.y + r] = s / st[L.R + r + (int64_t)r * m];
+    }
+}
+void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s) { BAMG_LAUNCH(k_solve_y, 1, 32, 0, s, d_state, j, m); }
+
+template void vcycle<float>(const std::vector<VLevel<float>>&, const float*, double, int, int, cudaStream_t);
+template void vcycle<double>(const std::vector<VLevel<double>>&, const double*, double, int, int, cudaStream_t);
+template void form_x<float>(int, const double*, const float*, int64_t, int, const double*, double*, cudaStream_t);
+template void form_x<double>(int, const double*, const double*, int64_t, int, const double*, double*, cudaStream_t);
+
+}  // namespace bamg

@@ -1,0 +1,134 @@
+// Host launchers of the device kernels (one translation unit per family).
+#pragma once
+
+#include "common.cuh"
+
+namespace bamg {
+
+template <typename T>
+struct MatView {
+    int n = 0, nnz = 0;
+    const int32_t* rp = nullptr;
+    const int32_t* ci = nullptr;
+    const T* v = nullptr;
+};
+
+// Interpolation in ELL form: row i has pcnt[i] <= c entries (pcol[i*c+t], pval[i*c+t]).
+template <typename T>
+struct EllView {
+    int n = 0, c = 0;
+    const int32_t* pcol = nullptr;
+    const T* pval = nullptr;
+    const int32_t* pcnt = nullptr;
+};
+
+// ------------------------------------------------------------------ k_relax.cu
+template <typename T>
+void launch_tv_init(int n, int ncols, int ld, int col0, uint64_t seed, double lo, double hi, T* X, cudaStream_t s);
+template <typename T>
+void launch_diag(const MatView<T>& M, T* d, cudaStream_t s);
+template <typename T>
+void launch_diag_vals(int n, const int32_t* rp, const int32_t* ci, const T* vals, T* d, cudaStream_t s);
+template <typename T>
+void launch_reciprocal(int n, const T* d, T* dinv, cudaStream_t s);
+template <typename T>
+void launch_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* tv, cudaStream_t s);
+// nu sweeps; T_val/dT/d_lambda may be null (no shift).  work: n*ld scratch.
+template <typename T>
+void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, const T* dT, const double* d_lambda,
+           int ncols, int ld, int col0, T omega, int nu, T* X, T* work, cudaStream_t s);
+// Normalise active columns and write LS weights (ncols doubles).
+template <typename T>
+void tv_weights(const MatView<T>& B, int ncols, int ld, int col0, const uint8_t* d_active, double floor, T* X,
+                double* d_w, cudaStream_t s);
+// Rayleigh quotients lambda_k = <Bx,x>/<Tx,x> (k >= 1; lambda_0 = 0), selection flags.
+template <typename T>
+void rayleigh_update(const MatView<T>& B, const T* T_val, const T* X, int ncols, int ld, int col0, double tol,
+                     double* d_lam, uint8_t* d_sel, cudaStream_t s);
+template <typename T>
+void inject_cols(int nc, const int32_t* c2f, const T* X, T* Xc, int ld, int col0, int ncols, cudaStream_t s);
+template <typename T>
+void prolong_cols(const EllView<T>& P, const T* Xc, T* X, int ld, int col0, int ncols, cudaStream_t s);
+template <typename Tin, typename Tout>
+void launch_convert(int64_t n, const Tin* a, Tout* b, cudaStream_t s);
+template <typename Tin, typename Tout>
+void launch_strided_to_vec(int n, const Tin* X, int ld, int col, Tout* y, cudaStream_t s);
+template <typename Tin, typename Tout>
+void launch_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col, cudaStream_t s);
+
+// Build B = I - A (diagonal always stored) from A (sorted CSR); checks column sums,
+// signs and a_ii < 1.  Returns the status flags (bit 0: negative entry, bit 1: colsum,
+// bit 2: a_ii = 1, bit 3: unsorted/out-of-range column).
+int build_system_matrix(int n, int nnzA, const int32_t* rpA, const int32_t* ciA, const double* vA,
+                        DevBuf<int32_t>& rpB, DevBuf<int32_t>& ciB, DevBuf<double>& vB, cudaStream_t s);
+
+// ------------------------------------------------------------------ k_interp.cu
+void coarsen_grid(int nx, int ny, uint8_t* cf, int32_t* cidx, cudaStream_t s);
+void coarse_to_fine(int n, const uint8_t* cf, const int32_t* cidx, int32_t* c2f, cudaStream_t s);
+// Returns an error flag (BAMG_EOVERFLOW if a neighbourhood search overflowed).
+template <typename T>
+int interp_ls(int n, const int32_t* rp, const int32_t* ci, const uint8_t* cf, const int32_t* cidx, const T* X, int ncols,
+              int ld, const double* d_w, int z, int mmax, int c, double ridge, int32_t* pcol, T* pval, int32_t* pcnt,
+              cudaStream_t s);
+// Q rows (CSR by coarse rows, sorted by fine index) from the ELL interpolation.
+template <typename T>
+void build_restriction(const EllView<T>& P, int nc, DevBuf<int32_t>& qrp, DevBuf<int32_t>& qci, DevBuf<T>& qv,
+                       cudaStream_t s);
+// Galerkin: outputs allocated by the callback once nnz is known.
+template <typename T>
+struct GalerkinOut {
+    DevBuf<int32_t> rp, ci;
+    DevBuf<T> bv, tv;
+    int nnz = 0;
+};
+template <typename T>
+void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int32_t* qci, const T* qv,
+              const EllView<T>& P, int nc, GalerkinOut<T>& out, cudaStream_t s);
+template <typename T>
+void csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const T* v, double* D, cudaStream_t s);
+
+// ------------------------------------------------------------------ k_cr.cu
+// Compatible relaxation coarsening (Algorithm 1).  Returns the number of rounds.
+template <typename T>
+int coarsen_cr(const MatView<T>& B, int level, uint64_t seed, double theta, int nu, double omega, int max_rounds,
+               uint8_t* cf, int32_t* cidx, int* nc_out, cudaStream_t s);
+
+// ------------------------------------------------------------------ k_coarse.cu
+// Eigenpairs of B x = lambda T x (dense FP64, n <= 64).  Returns the number of vector
+// columns written (<= k_ev + 1) or a negative status.
+int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_lam, double* d_V, int32_t* d_kind,
+               cudaStream_t s);
+// Minimal-norm inverse of the rank n-1 matrix B (dense FP64, row-major).
+int coarse_pinv(int n, const double* dB, double* dP, cudaStream_t s);
+
+// ------------------------------------------------------------------ k_solve.cu
+template <typename T>
+struct VLevel {  // one level of the V-cycle
+    MatView<T> B;
+    const T* dinv = nullptr;
+    EllView<T> P;                  // to the next coarser level
+    const int32_t* qrp = nullptr;  // Q by coarse rows
+    const int32_t* qci = nullptr;
+    const T* qv = nullptr;
+    T *b = nullptr, *x = nullptr, *r = nullptr;  // work vectors of n entries
+};
+template <typename T>
+void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega, int nu_pre, int nu_post, cudaStream_t s);
+
+void spmv_f64(const MatView<double>& B, const double* x, double* y, double alpha, cudaStream_t s);  // y = alpha B x
+void spmv_f64_from_f32(const MatView<double>& B, const float* x, double* y, cudaStream_t s);
+// Column dots h[q] = sum_i V[q*ldv + i] w[i], q < nv (deterministic two-level reduction).
+void dots(int n, const double* V, int64_t ldv, int nv, const double* w, double* d_h, double* d_partial,
+          cudaStream_t s);
+int dots_partial_blocks(int n);
+void update_minus(int n, const double* V, int64_t ldv, int nv, const double* d_h, double* w, cudaStream_t s);
+template <typename TZ>
+void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const double* d_y, double* x, cudaStream_t s);
+// sum |B x|, sum (B x)^2, sum |x|, sum x into d_out[4] (deterministic).
+void residual_norms(const MatView<double>& B, const double* x, double* d_out, double* d_partial, cudaStream_t s);
+void scale_vec(int n, double* x, const double* d_num, int num_idx, bool reciprocal, double* y, cudaStream_t s);
+void gmres_init(double* d_state, int m, cudaStream_t s);
+void gmres_arnoldi_step(double* d_state, int j, int m, cudaStream_t s);
+void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s);
+
+}  // namespace bamg

@@ -1,0 +1,783 @@
+// Host runtime of the library: the hierarchy, the bootstrap setup (Section 1 steps 1-4,
+// Algorithm 3 with mu = 1, then the rebuild from the enriched test sets), flexible GMRES
+// preconditioned by the V-cycle (Section 4.2), import/export, and the C ABI of bamg.h.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <type_traits>
+
+#include "gmres_state.cuh"
+#include "kernels.cuh"
+
+namespace bamg {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local std::string g_err;
+void set_last_error(const std::string& m) { g_err = m; }
+
+static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// active[k] = 1 for the random vectors, sel[q] for eigenvector column ldU + q, else 0.
+__global__ void k_active_mask(int r, int ldU, int nvec, int ld, const uint8_t* __restrict__ sel,
+                              uint8_t* __restrict__ active) {
+    const int k = threadIdx.x;
+    if (k >= ld) return;
+    uint8_t a = 0;
+    if (k < r) a = 1;
+    else if (k >= ldU && k - ldU < nvec) a = sel[k - ldU];
+    active[k] = a;
+}
+
+template <typename T>
+struct LevelT {
+    int n = 0, nnz = 0;
+    DevBuf<int32_t> rp, ci;
+    DevBuf<T> bv, tv;  // B_l and T_l (T on B's pattern)
+    DevBuf<T> dB, dT, dinv;
+    int nx = 0, ny = 0;
+    DevBuf<uint8_t> cf;
+    DevBuf<int32_t> cidx, c2f;
+    int nc = 0;
+    DevBuf<int32_t> pcol, pcnt;
+    DevBuf<T> pval;
+    DevBuf<int32_t> qrp, qci;
+    DevBuf<T> qv;
+    DevBuf<T> X;
+    DevBuf<double> w, lam;
+    DevBuf<uint8_t> sel;
+    DevBuf<T> vb, vx, vr;
+    MatView<T> B() const { return MatView<T>{n, nnz, rp.get(), ci.get(), bv.get()}; }
+    EllView<T> P(int c) const { return EllView<T>{n, c, pcol.get(), pval.get(), pcnt.get()}; }
+    void diagonals(cudaStream_t s) {
+        dB.alloc(n);
+        dT.alloc(n);
+        dinv.alloc(n);
+        launch_diag_vals<T>(n, rp.get(), ci.get(), bv.get(), dB.get(), s);
+        if (tv.get()) launch_diag_vals<T>(n, rp.get(), ci.get(), tv.get(), dT.get(), s);
+        launch_reciprocal<T>(n, dB.get(), dinv.get(), s);
+    }
+};
+
+struct SolverBase {
+    bamg_opts o{};
+    cudaStream_t s = nullptr;
+    double setup_ms = 0.0;
+    virtual ~SolverBase() {}
+    virtual int nlevels() const = 0;
+    virtual void level_size(int l, int64_t* n, int64_t* nnz) const = 0;
+    virtual void solve(double* x, int flags, double tol, bamg_stats* st) = 0;
+    virtual void vcycle_apply(const double* v, double* z) = 0;
+    virtual void export_obj(int level, int what, void* h_dst, int64_t cap, int64_t* bytes) = 0;
+    virtual void layout(int level, int* ld, int* r, int* v0, int* nvec) const = 0;
+};
+
+template <typename T>
+struct Solver : SolverBase {
+    std::vector<std::unique_ptr<LevelT<T>>> lv;
+    int r = 0, ldU = 0, ldV = 0, ld = 0, nvec = 0, nL = 0;
+    DevBuf<double> b64_own;  // FP64 values of B_0 when T = float
+    const double* b64 = nullptr;
+    DevBuf<double> pinv64;
+    DevBuf<T> pinvT;
+    DevBuf<double> x_init;
+    // Krylov workspace
+    int m = 0;
+    DevBuf<double> V, state, partial, x0, xw, rn;
+    DevBuf<T> Z, vin;
+    double* h_pin = nullptr;
+
+    ~Solver() override {
+        if (h_pin) cudaFreeHost(h_pin);
+    }
+    int nlevels() const override { return (int)lv.size(); }
+    void level_size(int l, int64_t* n, int64_t* nnz) const override {
+        *n = lv[l]->n;
+        *nnz = lv[l]->nnz;
+    }
+    void layout(int l, int* ld_, int* r_, int* v0, int* nv) const override {
+        (void)l;
+        if (ld_) *ld_ = ld;
+        if (r_) *r_ = r;
+        if (v0) *v0 = ldU;
+        if (nv) *nv = nvec;
+    }
+    MatView<double> B64() const { return MatView<double>{lv[0]->n, lv[0]->nnz, lv[0]->rp.get(), lv[0]->ci.get(), b64}; }
+    double ridge() const { return std::is_same<T, float>::value ? o.ridge32 : o.ridge; }
+
+    std::vector<VLevel<T>> vlevels(const T* b0, T* x0v) {
+        std::vector<VLevel<T>> v(lv.size());
+        for (size_t l = 0; l < lv.size(); ++l) {
+            LevelT<T>& L = *lv[l];
+            v[l].B = L.B();
+            v[l].dinv = L.dinv.get();
+            if (l + 1 < lv.size()) {
+                v[l].P = L.P(o.caliber);
+                v[l].qrp = L.qrp.get();
+                v[l].qci = L.qci.get();
+                v[l].qv = L.qv.get();
+            }
+            v[l].b = L.vb.get();
+            v[l].x = L.vx.get();
+            v[l].r = L.vr.get();
+        }
+        v[0].b = const_cast<T*>(b0);
+        v[0].x = x0v;
+        return v;
+    }
+
+    void alloc_vcycle_work() {
+        for (auto& L : lv) {
+            L->vb.alloc(L->n);
+            L->vx.alloc(L->n);
+            L->vr.alloc(L->n);
+        }
+    }
+
+    // --------------------------------------------------------------- interpolation step
+    // P_l by Algorithm 2 from the active columns of X_l, Q_l, and the Galerkin products
+    // into level l+1 (replacing its operators).
+    void build_level_operators(int l, const uint8_t* d_active, int ncols_w) {
+        LevelT<T>& c = *lv[l];
+        LevelT<T>& nx = *lv[l + 1];
+        c.w.alloc(ld);
+        BAMG_CK(cudaMemsetAsync(c.w.get(), 0, sizeof(double) * ld, s));
+        tv_weights<T>(c.B(), ncols_w, ld, 0, d_active, o.weight_floor, c.X.get(), c.w.get(), s);
+        c.pcol.alloc((size_t)c.n * o.caliber);
+        c.pval.alloc((size_t)c.n * o.caliber);
+        c.pcnt.alloc(c.n);
+        int e = interp_ls<T>(c.n, c.rp.get(), c.ci.get(), c.cf.get(), c.cidx.get(), c.X.get(), ld, ld, c.w.get(), o.z,
+                             o.mmax, o.caliber, ridge(), c.pcol.get(), c.pval.get(), c.pcnt.get(), s);
+        BAMG_REQUIRE(e == 0, BAMG_EOVERFLOW, "neighbourhood search exceeded its capacity of 256 visited states");
+        build_restriction<T>(c.P(o.caliber), c.nc, c.qrp, c.qci, c.qv, s);
+        GalerkinOut<T> go;
+        galerkin<T>(c.B(), c.tv.get(), c.qrp.get(), c.qci.get(), c.qv.get(), c.P(o.caliber), c.nc, go, s);
+        nx.n = c.nc;
+        nx.nnz = go.nnz;
+        nx.rp = std::move(go.rp);
+        nx.ci = std::move(go.ci);
+        nx.bv = std::move(go.bv);
+        nx.tv = std::move(go.tv);
+        nx.diagonals(s);
+    }
+
+    void split(int l) {
+        LevelT<T>& c = *lv[l];
+        c.cf.alloc(c.n);
+        c.cidx.alloc(c.n);
+        if (o.coarsen == BAMG_COARSEN_GRID) {
+            coarsen_grid(c.nx, c.ny, c.cf.get(), c.cidx.get(), s);
+            c.nc = ((c.nx + 1) / 2) * ((c.ny + 1) / 2);
+        } else {
+            int nc = 0;
+            coarsen_cr<T>(c.B(), l, o.seed, o.cr_theta, o.cr_nu, o.cr_omega, o.cr_max_rounds, c.cf.get(), c.cidx.get(),
+                          &nc, s);
+            c.nc = nc;
+        }
+        BAMG_REQUIRE(c.nc > 0 && c.nc < c.n, BAMG_ENUMERIC, "coarsening produced no coarse level");
+        c.c2f.alloc(c.nc);
+        coarse_to_fine(c.n, c.cf.get(), c.cidx.get(), c.c2f.get(), s);
+    }
+
+    // --------------------------------------------------------------- setup
+    void setup(const bamg_csr* A, int r_, int levels) {
+        auto t0 = std::chrono::steady_clock::now();
+        const int n = A->n;
+        r = r_;
+        // inputs on the device
+        const int32_t *rpA = A->row_ptr, *ciA = A->col;
+        const double* vA = A->val;
+        DevBuf<int32_t> hrp, hci;
+        DevBuf<double> hv;
+        if (A->on_host) {
+            hrp.alloc(n + 1);
+            hci.alloc(std::max(A->nnz, 1));
+            hv.alloc(std::max(A->nnz, 1));
+            BAMG_CK(cudaMemcpyAsync(hrp.get(), A->row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
+            BAMG_CK(cudaMemcpyAsync(hci.get(), A->col, sizeof(int32_t) * A->nnz, cudaMemcpyHostToDevice, s));
+            BAMG_CK(cudaMemcpyAsync(hv.get(), A->val, sizeof(double) * A->nnz, cudaMemcpyHostToDevice, s));
+            rpA = hrp.get();
+            ciA = hci.get();
+            vA = hv.get();
+        }
+        DevBuf<int32_t> rpB, ciB;
+        DevBuf<double> vB;
+        const int flags = build_system_matrix(n, A->nnz, rpA, ciA, vA, rpB, ciB, vB, s);
+        BAMG_REQUIRE(!(flags & 8), BAMG_EINVAL, "A: column indices must be sorted, unique and within [0, n)");
+        BAMG_REQUIRE(!(flags & 1), BAMG_ENOTSTOCH, "A has a negative entry");
+        BAMG_REQUIRE(!(flags & 4), BAMG_ENOTSTOCH, "A has a_ii = 1 (absorbing state)");
+        BAMG_REQUIRE(!(flags & 2), BAMG_ENOTSTOCH, "A is not column stochastic (|colsum - 1| > 1e-12)");
+        auto L0 = std::make_unique<LevelT<T>>();
+        L0->n = n;
+        L0->nnz = read_int(rpB.get() + n, s);
+        L0->rp = std::move(rpB);
+        L0->ci = std::move(ciB);
+        if constexpr (std::is_same<T, double>::value) {
+            L0->bv = std::move(vB);
+            b64 = L0->bv.get();
+        } else {
+            L0->bv.alloc(L0->nnz);
+            launch_convert<double, float>(L0->nnz, vB.get(), L0->bv.get(), s);
+            b64_own = std::move(vB);
+            b64 = b64_own.get();
+        }
+        L0->tv.alloc(L0->nnz);
+        launch_identity_on_pattern<T>(n, L0->rp.get(), L0->ci.get(), L0->tv.get(), s);
+        L0->diagonals(s);
+        L0->nx = o.grid_nx;
+        L0->ny = o.grid_ny;
+        constexpr int W = V16<T>::W;
+        ldU = round_up(r, W);
+        ldV = round_up(o.k_ev + 1, W);
+        ld = ldU + ldV;
+        BAMG_REQUIRE(ld <= 32, BAMG_EINVAL, "r + k_ev too large: padded test-vector block must be <= 32 columns");
+        L0->X.alloc((size_t)n * ld);
+        BAMG_CK(cudaMemsetAsync(L0->X.get(), 0, sizeof(T) * n * ld, s));
+        launch_tv_init<T>(n, r, ld, 0, o.seed, o.tv_lo, o.tv_hi, L0->X.get(), s);
+        lv.clear();
+        lv.push_back(std::move(L0));
+        const T omega = (T)o.omega;
+        // ---- first pass, down (Algorithm 3: relax U_l, P_l, Q_l, B_{l+1}, T_{l+1}, U_{l+1} = R U_l)
+        for (int l = 0; l < levels; ++l) {
+            LevelT<T>& c = *lv.back();
+            if (c.n <= o.coarse_max) break;
+            {
+                TmpBuf<T> work((size_t)c.n * ld, s);
+                relax<T>(c.B(), nullptr, c.dB.get(), c.dinv.get(), nullptr, nullptr, r, ld, 0, omega, o.nu_tv,
+                         c.X.get(), work.get(), s);
+            }
+            split(l);
+            auto nl = std::make_unique<LevelT<T>>();
+            nl->nx = (c.nx + 1) / 2;
+            nl->ny = (c.ny + 1) / 2;
+            lv.push_back(std::move(nl));
+            build_level_operators(l, nullptr, r);
+            LevelT<T>& cc = *lv[l];
+            LevelT<T>& nn = *lv[l + 1];
+            nn.X.alloc((size_t)nn.n * ld);
+            BAMG_CK(cudaMemsetAsync(nn.X.get(), 0, sizeof(T) * nn.n * ld, s));
+            inject_cols<T>(nn.n, cc.c2f.get(), cc.X.get(), nn.X.get(), ld, 0, r, s);
+        }
+        const int L = (int)lv.size() - 1;
+        LevelT<T>& Lc = *lv[L];
+        nL = Lc.n;
+        BAMG_REQUIRE(nL <= 64, BAMG_EINVAL,
+                     "coarsest level has more than 64 states: raise `levels` or lower coarse_max");
+        // ---- coarsest eigenpairs
+        {
+            TmpBuf<double> Bd((size_t)nL * nL, s), Td((size_t)nL * nL, s), Vd((size_t)nL * (o.k_ev + 1), s);
+            TmpBuf<int32_t> kinds(o.k_ev + 1, s);
+            csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.bv.get(), Bd.get(), s);
+            csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.tv.get(), Td.get(), s);
+            Lc.lam.alloc(ldV);
+            BAMG_CK(cudaMemsetAsync(Lc.lam.get(), 0, sizeof(double) * ldV, s));
+            const int nv = coarse_eig(nL, Bd.get(), Td.get(), o.k_ev, Lc.lam.get(), Vd.get(), kinds.get(), s);
+            BAMG_REQUIRE(nv > 0, BAMG_ENUMERIC, "coarsest eigensolve did not converge");
+            nvec = nv;
+            for (int q = 0; q < nvec; ++q)
+                launch_vec_to_strided<double, T>(nL, Vd.get() + (size_t)q * nL, Lc.X.get(), ld, ldU + q, s);
+        }
+        // ---- up (Algorithm 3: V_l = P_l V_{l+1}, relax (B_l - lambda_i T_l) x = 0, Rayleigh update)
+        for (int l = L - 1; l >= 0; --l) {
+            LevelT<T>& c = *lv[l];
+            LevelT<T>& ch = *lv[l + 1];
+            prolong_cols<T>(c.P(o.caliber), ch.X.get(), c.X.get(), ld, ldU, nvec, s);
+            c.lam.alloc(ldV);
+            BAMG_CK(cudaMemcpyAsync(c.lam.get(), ch.lam.get(), sizeof(double) * ldV, cudaMemcpyDeviceToDevice, s));
+            {
+                TmpBuf<T> work((size_t)c.n * ld, s);
+                relax<T>(c.B(), c.tv.get(), c.dB.get(), c.dinv.get(), c.dT.get(), c.lam.get(), nvec, ld, ldU, omega,
+                         o.nu_ev, c.X.get(), work.get(), s);
+            }
+            c.sel.alloc(ldV);
+            rayleigh_update<T>(c.B(), c.tv.get(), c.X.get(), nvec, ld, ldU, o.ev_change_tol, c.lam.get(), c.sel.get(),
+                               s);
+        }
+        // ---- rebuild all P_l, B_{l+1}, T_{l+1} from U_l and the selected V_l, top-down
+        {
+            TmpBuf<uint8_t> active(32, s);
+            for (int l = 0; l < L; ++l) {
+                BAMG_LAUNCH(k_active_mask, 1, 32, 0, s, r, ldU, nvec, ld, lv[l]->sel.get(), active.get());
+                build_level_operators(l, active.get(), ld);
+            }
+        }
+        // ---- coarsest minimal-norm inverse of the rebuilt B_L
+        {
+            TmpBuf<double> Bd((size_t)nL * nL, s);
+            csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.bv.get(), Bd.get(), s);
+            pinv64.alloc((size_t)nL * nL);
+            BAMG_REQUIRE(coarse_pinv(nL, Bd.get(), pinv64.get(), s) == 0, BAMG_ENUMERIC, "singular coarsest factor");
+            pinvT.alloc((size_t)nL * nL);
+            if constexpr (std::is_same<T, double>::value)
+                BAMG_CK(cudaMemcpyAsync(pinvT.get(), pinv64.get(), sizeof(double) * nL * nL, cudaMemcpyDeviceToDevice, s));
+            else
+                launch_convert<double, float>((int64_t)nL * nL, pinv64.get(), pinvT.get(), s);
+        }
+        // ---- initial guess: the state-vector approximation, 1^T x = 1
+        x_init.alloc(n);
+        launch_strided_to_vec<T, double>(n, lv[0]->X.get(), ld, ldU, x_init.get(), s);
+        {
+            TmpBuf<double> sums(4, s), part((size_t)blocks_for(n, 256) * 4, s);
+            residual_norms(B64(), x_init.get(), sums.get(), part.get(), s);
+            scale_vec(n, x_init.get(), sums.get(), 3, true, x_init.get(), s);
+        }
+        alloc_vcycle_work();
+        BAMG_CK(cudaStreamSynchronize(s));
+        setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+
+    // --------------------------------------------------------------- import
+    void import(int nlev, const bamg_level_in* in, const double* h_pinv, const double* h_x_init) {
+        lv.clear();
+        for (int l = 0; l < nlev; ++l) {
+            auto L = std::make_unique<LevelT<T>>();
+            L->n = in[l].n;
+            L->nnz = in[l].nnz;
+            L->rp.alloc(L->n + 1);
+            L->ci.alloc(std::max(L->nnz, 1));
+            L->bv.alloc(std::max(L->nnz, 1));
+            BAMG_CK(cudaMemcpyAsync(L->rp.get(), in[l].h_row_ptr, sizeof(int32_t) * (L->n + 1), cudaMemcpyHostToDevice, s));
+            BAMG_CK(cudaMemcpyAsync(L->ci.get(), in[l].h_col, sizeof(int32_t) * L->nnz, cudaMemcpyHostToDevice, s));
+            DevBuf<double> v64(std::max(L->nnz, 1));
+            BAMG_CK(cudaMemcpyAsync(v64.get(), in[l].h_val, sizeof(double) * L->nnz, cudaMemcpyHostToDevice, s));
+            if constexpr (std::is_same<T, double>::value) {
+                L->bv = std::move(v64);
+            } else {
+                launch_convert<double, float>(L->nnz, v64.get(), L->bv.get(), s);
+                if (l == 0) b64_own = std::move(v64);
+                BAMG_CK(cudaStreamSynchronize(s));
+            }
+            L->diagonals(s);
+            if (l + 1 < nlev) {
+                const int c = o.caliber;
+                std::vector<int32_t> pcol((size_t)L->n * c, -1), pcnt(L->n, 0);
+                std::vector<T> pval((size_t)L->n * c, T(0));
+                for (int i = 0; i < L->n; ++i) {
+                    const int a = in[l].h_p_row_ptr[i], b = in[l].h_p_row_ptr[i + 1];
+                    BAMG_REQUIRE(b - a <= c, BAMG_EINVAL, "import: a row of P has more than `caliber` entries");
+                    pcnt[i] = b - a;
+                    for (int q = a; q < b; ++q) {
+                        pcol[(size_t)i * c + (q - a)] = in[l].h_p_col[q];
+                        pval[(size_t)i * c + (q - a)] = (T)in[l].h_p_val[q];
+                    }
+                }
+                L->pcol.alloc(pcol.size());
+                L->pval.alloc(pval.size());
+                L->pcnt.alloc(pcnt.size());
+                BAMG_CK(cudaMemcpyAsync(L->pcol.get(), pcol.data(), sizeof(int32_t) * pcol.size(), cudaMemcpyHostToDevice, s));
+                BAMG_CK(cudaMemcpyAsync(L->pval.get(), pval.data(), sizeof(T) * pval.size(), cudaMemcpyHostToDevice, s));
+                BAMG_CK(cudaMemcpyAsync(L->pcnt.get(), pcnt.data(), sizeof(int32_t) * pcnt.size(), cudaMemcpyHostToDevice, s));
+                L->nc = in[l + 1].n;
+                build_restriction<T>(L->P(c), L->nc, L->qrp, L->qci, L->qv, s);
+                BAMG_CK(cudaStreamSynchronize(s));
+            }
+            lv.push_back(std::move(L));
+        }
+        b64 = std::is_same<T, double>::value ? reinterpret_cast<const double*>(lv[0]->bv.get()) : b64_own.get();
+        nL = lv.back()->n;
+        pinv64.alloc((size_t)nL * nL);
+        BAMG_CK(cudaMemcpyAsync(pinv64.get(), h_pinv, sizeof(double) * nL * nL, cudaMemcpyHostToDevice, s));
+        pinvT.alloc((size_t)nL * nL);
+        launch_convert<double, T>((int64_t)nL * nL, pinv64.get(), pinvT.get(), s);
+        x_init.alloc(lv[0]->n);
+        BAMG_CK(cudaMemcpyAsync(x_init.get(), h_x_init, sizeof(double) * lv[0]->n, cudaMemcpyHostToDevice, s));
+        alloc_vcycle_work();
+        BAMG_CK(cudaStreamSynchronize(s));
+    }
+
+    // --------------------------------------------------------------- V-cycle
+    void vcycle_apply(const double* v, double* z) override {
+        const int n = lv[0]->n;
+        if constexpr (std::is_same<T, double>::value) {
+            auto vl = vlevels(v, z);
+            vcycle<T>(vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, s);
+        } else {
+            vin.ensure(n);
+            TmpBuf<float> zo(n, s);
+            launch_convert<double, float>(n, v, vin.get(), s);
+            auto vl = vlevels(vin.get(), zo.get());
+            vcycle<T>(vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, s);
+            launch_convert<float, double>(n, zo.get(), z, s);
+        }
+    }
+
+    // --------------------------------------------------------------- FGMRES
+    double read_d(const double* d) {
+        BAMG_CK(cudaMemcpyAsync(h_pin, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+        BAMG_CK(cudaStreamSynchronize(s));
+        return h_pin[0];
+    }
+    void read_n(const double* d, int k) {
+        BAMG_CK(cudaMemcpyAsync(h_pin, d, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        BAMG_CK(cudaStreamSynchronize(s));
+    }
+
+    void solve(double* x_user, int flags, double tol, bamg_stats* st) override {
+        auto t0 = std::chrono::steady_clock::now();
+        const int n = lv[0]->n;
+        m = std::min(std::max(o.gmres_m, 1), GMRES_MMAX);
+        GmresLayout GL(m);
+        V.ensure((size_t)n * (m + 1));
+        Z.ensure((size_t)n * m);
+        state.ensure(GL.total);
+        const int pb = std::max(dots_partial_blocks(n) * (m + 1), (int)blocks_for(n, 256) * 4);
+        partial.ensure(pb);
+        x0.ensure(n);
+        xw.ensure(n);
+        rn.ensure(8);
+        vin.ensure(n);
+        if (!h_pin) BAMG_CK(cudaMallocHost(&h_pin, 16 * sizeof(double)));
+        const MatView<double> B = B64();
+        if (flags & BAMG_X_GUESS) {
+            BAMG_CK(cudaMemcpyAsync(x0.get(), x_user, sizeof(double) * n,
+                                    (flags & BAMG_X_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+        } else {
+            BAMG_CK(cudaMemcpyAsync(x0.get(), x_init.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        }
+        int it = 0, restarts = 0, checks = 0, status = BAMG_ENOCONV;
+        residual_norms(B, x0.get(), rn.get(), partial.get(), s);
+        read_n(rn.get(), 4);
+        double ratio = h_pin[0] / h_pin[2];
+        double x1 = h_pin[2], xsum = h_pin[3], last_x1 = x1;
+        double kappa = 1.0;
+        bool have_xw = false;
+        if (ratio <= tol) status = BAMG_OK;
+        while (status != BAMG_OK && it < o.max_it) {
+            double* V0 = V.get();
+            spmv_f64(B, x0.get(), V0, -1.0, s);
+            dots(n, V0, n, 1, V0, state.get() + GL.nrm2, partial.get(), s);
+            gmres_init(state.get(), m, s);
+            scale_vec(n, V0, state.get(), GL.hn, true, V0, s);
+            int jlast = -1;
+            for (int j = 0; j < m && it < o.max_it; ++j) {
+                double* vj = V.get() + (size_t)j * n;
+                double* w = V.get() + (size_t)(j + 1) * n;
+                T* zj = Z.get() + (size_t)j * n;
+                if constexpr (std::is_same<T, double>::value) {
+                    auto vl = vlevels(vj, zj);
+                    vcycle<T>(vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, s);
+                    spmv_f64(B, zj, w, 1.0, s);
+                } else {
+                    launch_convert<double, float>(n, vj, vin.get(), s);
+                    auto vl = vlevels(vin.get(), zj);
+                    vcycle<T>(vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, s);
+                    spmv_f64_from_f32(B, zj, w, s);
+                }
+                dots(n, V.get(), n, j + 1, w, state.get() + GL.h1, partial.get(), s);
+                update_minus(n, V.get(), n, j + 1, state.get() + GL.h1, w, s);
+                dots(n, V.get(), n, j + 1, w, state.get() + GL.h2, partial.get(), s);
+                update_minus(n, V.get(), n, j + 1, state.get() + GL.h2, w, s);
+                dots(n, w, n, 1, w, state.get() + GL.nrm2, partial.get(), s);
+                gmres_arnoldi_step(state.get(), j, m, s);
+                scale_vec(n, w, state.get(), GL.hn, true, w, s);
+                ++it;
+                jlast = j;
+                read_n(state.get() + GL.est, 2);
+                const double est = h_pin[0], hn = h_pin[1];
+                const bool last = (j == m - 1) || it >= o.max_it || hn == 0.0;
+                if (est * kappa <= tol * x1 || last) {
+                    gmres_solve_y(state.get(), j, m, s);
+                    form_x<T>(n, x0.get(), Z.get(), n, j + 1, state.get() + GL.y, xw.get(), s);
+                    residual_norms(B, xw.get(), rn.get(), partial.get(), s);
+                    read_n(rn.get(), 4);
+                    ++checks;
+                    have_xw = true;
+                    const double r1 = h_pin[0], r2 = std::sqrt(h_pin[1]);
+                    ratio = r1 / h_pin[2];
+                    last_x1 = h_pin[2];
+                    xsum = h_pin[3];
+                    if (r2 > 0.0) kappa = std::max(1.0, r1 / r2);
+                    if (!(ratio == ratio)) throw Error(BAMG_ENUMERIC, "NaN in the Krylov iteration");
+                    if (ratio <= tol) {
+                        status = BAMG_OK;
+                        break;
+                    }
+                    if (last) break;
+                }
+            }
+            (void)jlast;
+            if (status == BAMG_OK) break;
+            // restart from the last iterate
+            if (have_xw) {
+                BAMG_CK(cudaMemcpyAsync(x0.get(), xw.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                x1 = last_x1;
+            }
+            ++restarts;
+        }
+        double* xfinal = have_xw ? xw.get() : x0.get();
+        // normalise 1^T x = 1
+        TmpBuf<double> out(n, s);
+        h_pin[8] = xsum;
+        BAMG_CK(cudaMemcpyAsync(rn.get() + 5, h_pin + 8, sizeof(double), cudaMemcpyHostToDevice, s));
+        scale_vec(n, xfinal, rn.get(), 5, true, out.get(), s);
+        if (flags & BAMG_X_HOST)
+            BAMG_CK(cudaMemcpyAsync(x_user, out.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        else
+            BAMG_CK(cudaMemcpyAsync(x_user, out.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        BAMG_CK(cudaStreamSynchronize(s));
+        if (st) {
+            st->status = status;
+            st->iterations = it;
+            st->restarts = restarts;
+            st->true_checks = checks;
+            st->residual_l1 = ratio;
+            st->setup_ms = setup_ms;
+            st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        if (status != BAMG_OK) throw Error(status, "FGMRES did not reach the tolerance within max_it iterations");
+    }
+
+    // --------------------------------------------------------------- export
+    template <typename S>
+    static void to_host_double(const S* d, size_t cnt, double* h, cudaStream_t s) {
+        std::vector<S> tmp(cnt);
+        if (cnt) BAMG_CK(cudaMemcpyAsync(tmp.data(), d, sizeof(S) * cnt, cudaMemcpyDeviceToHost, s));
+        BAMG_CK(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < cnt; ++i) h[i] = (double)tmp[i];
+    }
+    void export_obj(int l, int what, void* h_dst, int64_t cap, int64_t* bytes) override {
+        BAMG_REQUIRE(l >= 0 && l < (int)lv.size(), BAMG_EINVAL, "export: level out of range");
+        LevelT<T>& L = *lv[l];
+        int64_t need = 0;
+        switch (what) {
+            case BAMG_EXPORT_B: need = 4LL * (L.n + 1) + 4LL * L.nnz + 8LL * L.nnz; break;
+            case BAMG_EXPORT_T: need = 8LL * L.nnz; break;
+            case BAMG_EXPORT_P:
+                BAMG_REQUIRE(l + 1 < (int)lv.size(), BAMG_EINVAL, "export: the coarsest level has no P");
+                need = 4LL * L.n * o.caliber + 4LL * L.n + 8LL * L.n * o.caliber;
+                break;
+            case BAMG_EXPORT_CF:
+                BAMG_REQUIRE(l + 1 < (int)lv.size(), BAMG_EINVAL, "export: the coarsest level has no splitting");
+                need = L.n;
+                break;
+            case BAMG_EXPORT_X: need = 8LL * L.n * ld; break;
+            case BAMG_EXPORT_PINV: need = 8LL * nL * nL; break;
+            case BAMG_EXPORT_XINIT: need = 8LL * lv[0]->n; break;
+            case BAMG_EXPORT_LAMBDA: need = 8LL * nvec; break;
+            default: throw Error(BAMG_EINVAL, "export: unknown object");
+        }
+        if (bytes) *bytes = need;
+        if (cap < need) throw Error(BAMG_ESIZE, "export: capacity too small");
+        char* h = (char*)h_dst;
+        switch (what) {
+            case BAMG_EXPORT_B:
+                BAMG_CK(cudaMemcpyAsync(h, L.rp.get(), 4LL * (L.n + 1), cudaMemcpyDeviceToHost, s));
+                BAMG_CK(cudaMemcpyAsync(h + 4LL * (L.n + 1), L.ci.get(), 4LL * L.nnz, cudaMemcpyDeviceToHost, s));
+                if (l == 0 && b64) {
+                    BAMG_CK(cudaMemcpyAsync(h + 4LL * (L.n + 1) + 4LL * L.nnz, b64, 8LL * L.nnz, cudaMemcpyDeviceToHost, s));
+                    BAMG_CK(cudaStreamSynchronize(s));
+                } else {
+                    to_host_double(L.bv.get(), L.nnz, (double*)(h + 4LL * (L.n + 1) + 4LL * L.nnz), s);
+                }
+                break;
+            case BAMG_EXPORT_T: to_host_double(L.tv.get(), L.nnz, (double*)h, s); break;
+            case BAMG_EXPORT_P:
+                BAMG_CK(cudaMemcpyAsync(h, L.pcol.get(), 4LL * L.n * o.caliber, cudaMemcpyDeviceToHost, s));
+                BAMG_CK(cudaMemcpyAsync(h + 4LL * L.n * o.caliber, L.pcnt.get(), 4LL * L.n, cudaMemcpyDeviceToHost, s));
+                to_host_double(L.pval.get(), (size_t)L.n * o.caliber, (double*)(h + 4LL * L.n * o.caliber + 4LL * L.n), s);
+                break;
+            case BAMG_EXPORT_CF: BAMG_CK(cudaMemcpyAsync(h, L.cf.get(), L.n, cudaMemcpyDeviceToHost, s)); break;
+            case BAMG_EXPORT_X: to_host_double(L.X.get(), (size_t)L.n * ld, (double*)h, s); break;
+            case BAMG_EXPORT_PINV: to_host_double(pinv64.get(), (size_t)nL * nL, (double*)h, s); break;
+            case BAMG_EXPORT_XINIT: to_host_double(x_init.get(), (size_t)lv[0]->n, (double*)h, s); break;
+            case BAMG_EXPORT_LAMBDA: to_host_double(L.lam.get(), (size_t)nvec, (double*)h, s); break;
+        }
+        BAMG_CK(cudaStreamSynchronize(s));
+    }
+};
+
+}  // namespace bamg
+
+// =================================================================== C ABI
+using namespace bamg;
+
+struct bamg_handle {
+    std::unique_ptr<SolverBase> impl;
+};
+
+template <typename F>
+static int guarded(F&& f) {
+    try {
+        f();
+        g_err.clear();
+        return BAMG_OK;
+    } catch (const Error& e) {
+        g_err = e.what();
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_err = "host allocation failed";
+        return BAMG_ENOMEM;
+    } catch (const std::exception& e) {
+        g_err = e.what();
+        return BAMG_EINVAL;
+    }
+}
+
+extern "C" {
+
+int bamg_default_opts(bamg_opts* o) {
+    if (!o) return BAMG_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->omega = 0.7;
+    o->nu_tv = 4;
+    o->nu_ev = 2;
+    o->nu_pre = 2;
+    o->nu_post = 2;
+    o->caliber = 2;
+    o->z = 2;
+    o->mmax = 16;
+    o->k_ev = 6;
+    o->coarse_max = 64;
+    o->gmres_m = 50;
+    o->max_it = 500;
+    o->precision = BAMG_PREC_FP64;
+    o->coarsen = BAMG_COARSEN_GRID;
+    o->seed = 0;
+    o->tv_lo = 1.0;
+    o->tv_hi = 2.0;
+    o->ev_change_tol = 1e-3;
+    o->ridge = 1e-12;
+    o->ridge32 = 1e-6;
+    o->weight_floor = 1e-28;
+    o->cr_theta = 0.85;
+    o->cr_nu = 8;
+    o->cr_max_rounds = 20;
+    o->cr_omega = 0.7;
+    o->stream = nullptr;
+    return BAMG_OK;
+}
+
+static void check_opts(const bamg_opts& o) {
+    BAMG_REQUIRE(o.caliber >= 1 && o.caliber <= 4, BAMG_EINVAL, "caliber must be 1..4");
+    BAMG_REQUIRE(o.z >= 1 && o.z <= 3, BAMG_EINVAL, "z must be 1..3");
+    BAMG_REQUIRE(o.mmax >= 1 && o.mmax <= 16, BAMG_EINVAL, "mmax must be 1..16");
+    BAMG_REQUIRE(o.k_ev >= 1 && o.k_ev <= 15, BAMG_EINVAL, "k_ev must be 1..15");
+    BAMG_REQUIRE(o.coarse_max >= 1 && o.coarse_max <= 64, BAMG_EINVAL, "coarse_max must be 1..64");
+    BAMG_REQUIRE(o.nu_pre >= 0 && o.nu_post >= 0 && o.nu_tv >= 0 && o.nu_ev >= 0, BAMG_EINVAL, "negative sweep count");
+    BAMG_REQUIRE(o.gmres_m >= 1 && o.gmres_m <= GMRES_MMAX, BAMG_EINVAL, "gmres_m must be 1..64");
+    BAMG_REQUIRE(o.max_it >= 1, BAMG_EINVAL, "max_it must be >= 1");
+    BAMG_REQUIRE(o.precision == BAMG_PREC_FP64 || o.precision == BAMG_PREC_MIXED, BAMG_EINVAL, "bad precision");
+    BAMG_REQUIRE(o.coarsen == BAMG_COARSEN_GRID || o.coarsen == BAMG_COARSEN_CR, BAMG_EINVAL, "bad coarsening");
+    BAMG_REQUIRE(o.omega > 0.0 && o.omega < 2.0, BAMG_EINVAL, "omega must be in (0, 2)");
+}
+
+int bamg_setup(const bamg_csr* A, int r, int levels, const bamg_opts* opts, bamg_handle** h) {
+    return guarded([&] {
+        BAMG_REQUIRE(A && h, BAMG_EINVAL, "null argument");
+        *h = nullptr;
+        bamg_opts o;
+        if (opts) o = *opts;
+        else bamg_default_opts(&o);
+        check_opts(o);
+        BAMG_REQUIRE(A->n >= 2 && A->nnz >= 1, BAMG_EINVAL, "A must have n >= 2 and nnz >= 1");
+        BAMG_REQUIRE(A->row_ptr && A->col && A->val, BAMG_EINVAL, "null CSR array");
+        BAMG_REQUIRE(r >= 1 && r <= 24, BAMG_EINVAL, "r must be 1..24");
+        BAMG_REQUIRE(levels >= 0 && levels <= 30, BAMG_EINVAL, "levels must be 0..30");
+        if (o.coarsen == BAMG_COARSEN_GRID)
+            BAMG_REQUIRE(o.grid_nx >= 1 && o.grid_ny >= 1 && (int64_t)o.grid_nx * o.grid_ny == A->n, BAMG_EINVAL,
+                         "full coarsening needs grid_nx * grid_ny == n");
+        auto hh = std::make_unique<bamg_handle>();
+        if (o.precision == BAMG_PREC_FP64) {
+            auto sv = std::make_unique<Solver<double>>();
+            sv->o = o;
+            sv->s = (cudaStream_t)o.stream;
+            sv->setup(A, r, levels);
+            hh->impl = std::move(sv);
+        } else {
+            auto sv = std::make_unique<Solver<float>>();
+            sv->o = o;
+            sv->s = (cudaStream_t)o.stream;
+            sv->setup(A, r, levels);
+            hh->impl = std::move(sv);
+        }
+        *h = hh.release();
+    });
+}
+
+int bamg_solve(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st) {
+    return guarded([&] {
+        BAMG_REQUIRE(h && h->impl && x, BAMG_EINVAL, "null argument");
+        BAMG_REQUIRE(tol > 0.0, BAMG_EINVAL, "tol must be positive");
+        if (st) std::memset(st, 0, sizeof(*st));
+        h->impl->solve(x, flags, tol, st);
+    });
+}
+
+void bamg_free(bamg_handle* h) { delete h; }
+
+const char* bamg_last_error(void) { return g_err.c_str(); }
+
+uint64_t bamg_launch_count(void) { return g_launches.load(); }
+
+int bamg_hierarchy_info(const bamg_handle* h, int* nlevels, int64_t* h_n, int64_t* h_nnz, double* opc) {
+    return guarded([&] {
+        BAMG_REQUIRE(h && h->impl, BAMG_EINVAL, "null handle");
+        const int L = h->impl->nlevels();
+        if (nlevels) *nlevels = L;
+        double tot = 0, n0 = 0;
+        for (int l = 0; l < L && l < 32; ++l) {
+            int64_t n, nnz;
+            h->impl->level_size(l, &n, &nnz);
+            if (h_n) h_n[l] = n;
+            if (h_nnz) h_nnz[l] = nnz;
+            tot += (double)nnz;
+            if (l == 0) n0 = (double)nnz;
+        }
+        if (opc) *opc = tot / n0;
+    });
+}
+
+int bamg_level_export(const bamg_handle* h, int level, int what, void* h_dst, int64_t cap, int64_t* h_bytes) {
+    return guarded([&] {
+        BAMG_REQUIRE(h && h->impl, BAMG_EINVAL, "null handle");
+        h->impl->export_obj(level, what, h_dst, cap, h_bytes);
+    });
+}
+
+int bamg_hierarchy_layout(const bamg_handle* h, int level, int* ld, int* r, int* v_col0, int* nvec) {
+    return guarded([&] {
+        BAMG_REQUIRE(h && h->impl, BAMG_EINVAL, "null handle");
+        h->impl->layout(level, ld, r, v_col0, nvec);
+    });
+}
+
+int bamg_import(int nlevels, const bamg_level_in* levels, const double* h_pinv, const double* h_x_init,
+                const bamg_opts* opts, bamg_handle** h) {
+    return guarded([&] {
+        BAMG_REQUIRE(levels && h && h_pinv && h_x_init && nlevels >= 1 && nlevels <= 30, BAMG_EINVAL, "bad import args");
+        *h = nullptr;
+        bamg_opts o;
+        if (opts) o = *opts;
+        else bamg_default_opts(&o);
+        check_opts(o);
+        BAMG_REQUIRE(levels[nlevels - 1].n <= 64, BAMG_EINVAL, "import: coarsest level must have <= 64 states");
+        auto hh = std::make_unique<bamg_handle>();
+        if (o.precision == BAMG_PREC_FP64) {
+            auto sv = std::make_unique<Solver<double>>();
+            sv->o = o;
+            sv->s = (cudaStream_t)o.stream;
+            sv->import(nlevels, levels, h_pinv, h_x_init);
+            hh->impl = std::move(sv);
+        } else {
+            auto sv = std::make_unique<Solver<float>>();
+            sv->o = o;
+            sv->s = (cudaStream_t)o.stream;
+            sv->import(nlevels, levels, h_pinv, h_x_init);
+            hh->impl = std::move(sv);
+        }
+        *h = hh.release();
+    });
+}
+
+int bamg_vcycle_apply(bamg_handle* h, const double* v, double* z) {
+    return guarded([&] {
+        BAMG_REQUIRE(h && h->impl && v && z, BAMG_EINVAL, "null argument");
+        h->impl->vcycle_apply(v, z);
+        BAMG_CK(cudaStreamSynchronize(h->impl->s));
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+"""The C ABI library builds, loads without a GPU, and exports exactly the entry points
+include/bamg.h declares (and the binding declares them all)."""
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bamg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bamg_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import paper_1004_1451_gb300.build as b
+
+    return b.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("bamg_setup", "bamg_solve", "bamg_free"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (bamg_[a-z0-9_]+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_loads_and_covers_header(libpath):
+    from paper_1004_1451_gb300 import _capi
+
+    lib = _capi.load()
+    assert set(_capi.SIGNATURES) == set(_declared())
+    for n in _declared():
+        assert hasattr(lib, n)
+
+
+def test_default_opts_are_the_papers():
+    import ctypes
+
+    from paper_1004_1451_gb300 import _capi
+
+    o = _capi.Opts()
+    assert _capi.load().bamg_default_opts(ctypes.byref(o)) == 0
+    assert o.omega == 0.7 and o.nu_pre == 2 and o.nu_post == 2 and o.caliber == 2 and o.k_ev == 6
+    assert o.cr_theta == 0.85 and o.cr_nu == 8
+    from oracle import bamg as ob
+
+    d = ob.Opts()
+    for k in ("omega", "nu_tv", "nu_ev", "nu_pre", "nu_post", "caliber", "z", "mmax", "k_ev", "coarse_max", "gmres_m",
+              "tv_lo", "tv_hi", "ev_change_tol", "ridge", "weight_floor", "cr_theta", "cr_nu", "cr_omega"):
+        assert getattr(o, k) == getattr(d, k), k
+
+
+def test_struct_layouts_match_header():
+    # offsets of the ctypes mirrors against a C compile of the header
+    import ctypes
+    import tempfile
+
+    from paper_1004_1451_gb300 import _capi
+
+    prog = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "bamg.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(bamg_opts), sizeof(bamg_csr), sizeof(bamg_mat), sizeof(bamg_stats),
+         sizeof(bamg_level_in));
+  printf("%zu %zu %zu\n", offsetof(bamg_opts, seed), offsetof(bamg_opts, stream), offsetof(bamg_opts, cr_omega));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    sizes = list(map(int, out[:5]))
+    offs = list(map(int, out[5:]))
+    assert sizes == [ctypes.sizeof(_capi.Opts), ctypes.sizeof(_capi.Csr), ctypes.sizeof(_capi.Mat),
+                     ctypes.sizeof(_capi.Stats), ctypes.sizeof(_capi.LevelIn)]
+    assert offs == [_capi.Opts.seed.offset, _capi.Opts.stream.offset, _capi.Opts.cr_omega.offset]

@@ -1,0 +1,223 @@
+"""Parity of the solve phase and of the whole path with the CPU oracle and the exact
+stationary vectors.  FP64 runs must agree to relative L1 1e-8, mixed runs to 1e-6."""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from gpu_util import need_gpu, rel
+from oracle import bamg as ob
+from oracle import exact
+from workloads import delaunay_walk, grid_walk, random_birth_death, tandem_queue
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _bamg():
+    import paper_1004_1451_gb300 as bamg
+
+    return bamg
+
+
+def _levels_of(H):
+    out = []
+    for l, lv in enumerate(H.levels):
+        B = sp.csr_matrix(lv.B)
+        B.sort_indices()
+        d = {"B": (B.indptr, B.indices, B.data)}
+        if l < H.L:
+            P = sp.csr_matrix(lv.P)
+            P.sort_indices()
+            d["P"] = (P.indptr, P.indices, P.data)
+        out.append(d)
+    return out
+
+
+@pytest.fixture(scope="module")
+def oracle_H():
+    ch = tandem_queue(40)
+    H = ob.setup(ch.to_scipy(), 8, 10, ob.Opts(), grid=ch.grid)
+    return ch, H
+
+
+def test_vcycle_matches_oracle(oracle_H):
+    torch = _torch()
+    ch, H = oracle_H
+    s = _bamg().import_hierarchy(_levels_of(H), H.pinv, H.x_init)
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        v = rng.standard_normal(ch.n)
+        v -= v.mean()
+        z = s.vcycle(torch.tensor(v, device="cuda")).cpu().numpy()
+        assert rel(z, ob.vcycle(H, v)) < 1e-12
+
+
+def test_vcycle_mixed_close_to_oracle(oracle_H):
+    torch = _torch()
+    ch, H = oracle_H
+    s = _bamg().import_hierarchy(_levels_of(H), H.pinv, H.x_init, precision="mixed")
+    v = np.random.default_rng(5).standard_normal(ch.n)
+    z = s.vcycle(torch.tensor(v, device="cuda")).cpu().numpy()
+    assert rel(z, ob.vcycle(H, v)) < 1e-5
+
+
+def test_fgmres_matches_oracle(oracle_H):
+    ch, H = oracle_H
+    s = _bamg().import_hierarchy(_levels_of(H), H.pinv, H.x_init)
+    x, st = s.solve(1e-13)
+    xo, sto = ob.solve(H, 1e-13)
+    assert st["residual_l1"] <= 1e-13
+    assert abs(st["iterations"] - sto["iterations"]) <= 1
+    assert rel(x.cpu().numpy(), xo) < 1e-10
+    assert rel(x.cpu().numpy(), exact.exact_stationary(ch)) < 1e-9
+
+
+def _run(ch, r, levels, tol, precision, **kw):
+    torch = _torch()
+    rp = torch.tensor(ch.row_ptr, device="cuda")
+    ci = torch.tensor(ch.col, device="cuda")
+    v = torch.tensor(ch.val, device="cuda")
+    s = _bamg().Solver(rp, ci, v, r=r, levels=levels, grid=ch.grid, precision=precision, **kw)
+    x, st = s.solve(tol)
+    return s, x.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-9), ("mixed", 1e-6)])
+@pytest.mark.parametrize("kind", ["grid33", "tandem32", "bd700", "grid_rect"])
+def test_full_path_reaches_exact(kind, precision, bound):
+    if kind == "grid33":
+        ch, r = grid_walk(33), 8
+    elif kind == "tandem32":
+        ch, r = tandem_queue(32), 10
+    elif kind == "grid_rect":
+        ch, r = grid_walk(45, 19), 6
+    else:
+        ch, r = random_birth_death(700, 2), 6
+    s, x, st = _run(ch, r, 12, 1e-13 if precision == "fp64" else 1e-12, precision, tv_lo=0.0, tv_hi=1.0)
+    xe = exact.exact_stationary(ch)
+    assert rel(x, xe) < bound, (rel(x, xe), st)
+    assert abs(x.sum() - 1.0) < 1e-13
+    assert np.all(x >= -1e-14 * x.max())
+    B = ob.system_matrix(ch.to_scipy())
+    assert ob.l1_ratio(B, x) <= 2e-12
+
+
+def test_full_path_agrees_with_oracle_run():
+    ch = grid_walk(40, 24)
+    s, x, st = _run(ch, 8, 10, 1e-13, "fp64", tv_lo=0.0, tv_hi=1.0)
+    xo, H, sto = ob.stationary(ch.to_scipy(), 8, 10, 1e-13, ob.Opts(tv_lo=0.0, tv_hi=1.0), grid=ch.grid)
+    assert rel(x, xo) < 1e-9
+    info = s.info()
+    assert info["n"] == [lv.B.shape[0] for lv in H.levels]
+    # same hierarchy sizes and nearly the same iteration count
+    assert abs(st["iterations"] - sto["iterations"]) <= 2
+
+
+def test_hierarchy_invariants():
+    ch = tandem_queue(48)
+    s, x, st = _run(ch, 10, 12, 1e-12, "fp64")
+    bamg = _bamg()
+    info = s.info()
+    for l in range(info["levels"]):
+        rp, ci, v = s.export(l, bamg._capi.EXPORT_B)
+        n = len(rp) - 1
+        B = sp.csr_matrix((v, ci, rp), shape=(n, n))
+        cs = np.abs(np.asarray(B.sum(axis=0)).ravel()).max()
+        assert cs <= 1e-12 * np.abs(v).max(), (l, cs)  # 1^T B_l = 0 (Section 4)
+        if l + 1 < info["levels"]:
+            pcol, pval, pcnt = s.export(l, bamg._capi.EXPORT_P)
+            cf = s.export(l, bamg._capi.EXPORT_CF)
+            assert np.all(pcnt[cf] == 1) and np.all(pval[cf, 0] == 1.0)
+            assert np.all(pcnt <= 2)
+    pinv = s.export(info["levels"] - 1, bamg._capi.EXPORT_PINV)
+    rp, ci, v = s.export(info["levels"] - 1, bamg._capi.EXPORT_B)
+    BL = sp.csr_matrix((v, ci, rp)).toarray()
+    assert np.allclose(BL @ pinv @ BL, BL, atol=1e-10 * np.abs(BL).max())
+    assert np.allclose(pinv @ BL @ pinv, pinv, atol=1e-8 * np.abs(pinv).max())
+
+
+def test_config1_grid64_fp64():
+    # 64 x 64 grid walk, r = 8 test vectors U(0,1), 3 coarsenings to 64 states, FP64
+    ch = grid_walk(64)
+    s, x, st = _run(ch, 8, 3, 1e-13, "fp64", tv_lo=0.0, tv_hi=1.0)
+    assert s.info()["n"] == [4096, 1024, 256, 64]
+    assert rel(x, exact.exact_stationary(ch)) < 1e-8
+
+
+def test_config2_tandem256_mixed():
+    # tandem queue, capacities 255 (65,536 states), r = 10, FP32 V-cycle inside FP64 GMRES
+    ch = tandem_queue(255)
+    s, x, st = _run(ch, 10, 20, 1e-13, "mixed")
+    xe = exact.sparse_nullspace(ch.to_scipy())
+    assert st["residual_l1"] <= 1e-13
+    assert rel(x, xe) < 1e-6, rel(x, xe)
+
+
+def test_host_buffers_round_trip():
+    torch = _torch()
+    ch = grid_walk(30)
+    rp = torch.tensor(ch.row_ptr)
+    ci = torch.tensor(ch.col)
+    v = torch.tensor(ch.val)
+    s = _bamg().Solver(rp, ci, v, r=6, levels=6, grid=ch.grid, on_host=True)
+    x, st = s.solve(1e-12, host=True)
+    assert x.device.type == "cpu"
+    assert rel(x.numpy(), exact.exact_stationary(ch)) < 1e-9
+
+
+def test_initial_guess_flag():
+    torch = _torch()
+    ch = grid_walk(21)
+    xe = exact.exact_stationary(ch)
+    s, x, st = _run(ch, 6, 6, 1e-12, "fp64")
+    x2, st2 = s.solve(1e-12, x0=torch.tensor(xe, device="cuda"))
+    assert st2["iterations"] == 0 and rel(x2.cpu().numpy(), xe) < 1e-14
+
+
+def test_rejects_bad_input():
+    torch = _torch()
+    bamg = _bamg()
+    ch = grid_walk(10)
+    val = ch.val.copy()
+    val[3] *= 1.5
+    args = (torch.tensor(ch.row_ptr, device="cuda"), torch.tensor(ch.col, device="cuda"))
+    with pytest.raises(bamg.BamgError) as e:
+        bamg.Solver(*args, torch.tensor(val, device="cuda"), r=6, levels=3, grid=ch.grid)
+    assert e.value.code == bamg._capi.BAMG_ENOTSTOCH
+    with pytest.raises(bamg.BamgError) as e:
+        bamg.Solver(*args, torch.tensor(ch.val, device="cuda"), r=6, levels=3, grid=(9, 10))
+    assert e.value.code == bamg._capi.BAMG_EINVAL
+    with pytest.raises(bamg.BamgError) as e:
+        bamg.Solver(*args, torch.tensor(ch.val, device="cuda"), r=40, levels=3, grid=ch.grid)
+    assert e.value.code == bamg._capi.BAMG_EINVAL
+    with pytest.raises(bamg.BamgError) as e:  # too few levels for a 64-state coarsest grid
+        bamg.Solver(*args, torch.tensor(ch.val, device="cuda"), r=6, levels=0, grid=ch.grid)
+    assert e.value.code == bamg._capi.BAMG_EINVAL
+
+
+def test_nonconvergence_reports_enoconv():
+    bamg = _bamg()
+    ch = grid_walk(40)
+    with pytest.raises(bamg.BamgError) as e:
+        _run(ch, 6, 8, 1e-15, "fp64", max_it=2)
+    assert e.value.code == bamg._capi.BAMG_ENOCONV
+    assert e.value.stats["iterations"] == 2
+
+
+def test_delaunay_cr_fp64():
+    ch = delaunay_walk(5000, 3)
+    s, x, st = _run(ch, 8, 12, 1e-13, "fp64", coarsen="cr")
+    assert rel(x, exact.exact_stationary(ch)) < 1e-8
+    xo, H, sto = ob.stationary(ch.to_scipy(), 8, 12, 1e-13, ob.Opts(coarsen="cr"))
+    assert rel(x, xo) < 1e-8
