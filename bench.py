@@ -150,6 +150,11 @@ def run_ours(args):
     launches = (bamg.launch_count() - l0) / args.steps
     torch.cuda.synchronize()
     ck = clocks.stop()
+    if args.only_step:
+        if rank == 0:
+            _line({"metric": METRIC, "value": round(float(np.mean(times)), 4), "unit": "ms",
+                   "gmres_iterations": int(np.median(iters)), "gpu_launches": int(round(launches)), "only_step": True})
+        return
     ms = float(np.sum(times)) / args.steps
     if ws > 1:
         t = torch.tensor([ms], device=dev)
@@ -343,6 +348,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only-step", action="store_true", help="time the workload steps only (for profiler launch lists)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -59,7 +59,8 @@ int bamg_tv_init(int dtype, int n, int ncols, int ld, int col0, uint64_t seed, d
                  void* stream) {
     return guard([&] {
         cudaStream_t s = (cudaStream_t)stream;
-        BAMG_REQUIRE(n >= 0 && ncols >= 0 && X && col0 >= 0 && col0 + ncols <= ld, BAMG_EINVAL, "bad tv_init args");
+        BAMG_REQUIRE(n >= 0 && ncols >= 0 && (X || n == 0) && col0 >= 0 && col0 + ncols <= ld, BAMG_EINVAL,
+                     "bad tv_init args");
         if (dtype == BAMG_F64) launch_tv_init<double>(n, ncols, ld, col0, seed, lo, hi, (double*)X, s);
         else if (dtype == BAMG_F32) launch_tv_init<float>(n, ncols, ld, col0, seed, lo, hi, (float*)X, s);
         else throw Error(BAMG_EINVAL, "bad dtype");

@@ -334,10 +334,13 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
 #pragma unroll
                 for (int b = 0; b < CMAX; ++b) A[a][b] = (a < t && b < t) ? GJJ[a][b] : T(0);
                 rhs[a] = a < t ? bJ[a] : T(0);
+                if (a < t) tr += GJJ[a][a];
+            }
+#pragma unroll
+            for (int a = 0; a < CMAX; ++a) {
                 if (a < t) {
                     A[a][t] = gsj[a];
                     A[t][a] = gsj[a];
-                    tr += GJJ[a][a];
                 }
             }
             A[t][t] = gss;
