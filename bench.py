@@ -134,7 +134,7 @@ def run_ours(args):
         dist.barrier()
     clocks = Clocks()
     clocks.start()
-    times, iters = [], []
+    times, iters, split = [], [], []
     l0 = bamg.launch_count()
     for _ in range(args.steps):
         flush.fill_(1)
@@ -146,6 +146,7 @@ def run_ours(args):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
         iters.append(st["iterations"])
+        split.append((st["setup_ms"], st["solve_ms"]))
         s.close()
     launches = (bamg.launch_count() - l0) / args.steps
     torch.cuda.synchronize()
@@ -210,6 +211,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "n": ch.n, "nnz_A": nnz_a, "r": R, "tol": TOL,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
         "gmres_iterations": int(np.median(iters)), "rel_l1_vs_exact": err,
+        "host_setup_ms": round(float(np.median([a for a, b in split])), 3),
+        "host_solve_ms": round(float(np.median([b for a, b in split])), 3),
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 4 * (ch.n + 1) + 12 * nnz_a,
                 "d2h_bytes_per_step": 8 * ch.n},
         "fp64_ms": round(float(np.median(fp64)), 4), "fp64_iterations": st64["iterations"],
@@ -237,21 +240,23 @@ def _grid_B(N, dev, dtype):
     return rp.int(), cols[ok].int(), vals[ok].to(dtype)
 
 
-def _time_relax(bamg, B, X, ncols, col0, reps, stream):
+def _time_relax(bamg, B, X, ncols, col0, reps, stream, sweeps=20):
+    """Average duration of one omega-Jacobi sweep launch: `sweeps` launches per call
+    (the call's two diagonal kernels and its synchronisation amortised over them)."""
     import torch
 
     work = torch.empty_like(X)
-    bamg.relax(B, X, ncols, col0, 0.7, 1, work=work)  # warm-up
+    bamg.relax(B, X, ncols, col0, 0.7, 2, work=work)  # warm-up
     evs = []
     for _ in range(reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        bamg.relax(B, X, ncols, col0, 0.7, 1, work=work)
+        bamg.relax(B, X, ncols, col0, 0.7, sweeps, work=work)
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
-    return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    return float(np.mean([a.elapsed_time(b) for a, b in evs])) / sweeps
 
 
 def dominant_kernel(ch, peaks):
@@ -269,7 +274,7 @@ def dominant_kernel(ch, peaks):
     Bd = (torch.tensor(B.indptr.astype(np.int32), device=dev), torch.tensor(B.indices.astype(np.int32), device=dev),
           torch.tensor(B.data, dtype=torch.float32, device=dev))
     X = torch.rand(ch.n, 20, dtype=torch.float32, device=dev)
-    ms = _time_relax(bamg, Bd, X, 10, 0, 50, torch.cuda.current_stream())
+    ms = _time_relax(bamg, Bd, X, 10, 0, 10, torch.cuda.current_stream())
     nbytes = B.nnz * 8 + 4 * (ch.n + 1) + 4 * ch.n + 2 * 4 * ch.n * 12
     gbs = nbytes / (ms * 1e-3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -290,13 +295,13 @@ def spmm_probe(peaks, N=4096):
     B = _grid_B(N, dev, torch.float32)
     n, nnz = N * N, int(B[1].numel())
     X = torch.rand(n, 16, dtype=torch.float32, device=dev)
-    ms = _time_relax(bamg, B, X, 16, 0, 10, torch.cuda.current_stream())
+    ms = _time_relax(bamg, B, X, 16, 0, 3, torch.cuda.current_stream())
     nbytes = nnz * 8 + 4 * (n + 1) + 4 * n + 2 * 4 * n * 16
     gbs = nbytes / (ms * 1e-3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
     del X, B
     torch.cuda.empty_cache()
-    return {"workload": "grid walk 4096^2, r=16, FP32", "kernel": "k_jacobi<float>", "ms": round(ms, 4),
+    return {"workload": f"grid walk {N}^2, r=16, FP32", "kernel": "k_jacobi<float>", "ms": round(ms, 4),
             "bytes": int(nbytes), "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
 
 
@@ -349,9 +354,20 @@ def main():
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only-step", action="store_true", help="time the workload steps only (for profiler launch lists)")
+    ap.add_argument("--probe-only", type=int, default=0, help="run only the SpMM probe on an N x N grid walk")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.probe_only:
+        import torch
+
+        import paper_1004_1451_gb300.build as pb
+
+        pb.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+        _line(spmm_probe(peaks, N=args.probe_only))
     else:
         run_ours(args)
 

@@ -145,6 +145,12 @@ static void galerkin_step(const bamg_mat* Bm, const void* T_val, int nc, const i
                           int64_t cap, int64_t* h_nnz, cudaStream_t s) {
     MatView<T> B = view<T>(Bm);
     EllView<T> P{B.n, c, pcol, (const T*)pval, pcnt};
+    cudaStream_t prev = alloc_stream();
+    alloc_stream() = s;
+    struct Restore {
+        cudaStream_t p;
+        ~Restore() { alloc_stream() = p; }
+    } restore_{prev};
     DevBuf<int32_t> qrp, qci;
     DevBuf<T> qv;
     build_restriction<T>(P, nc, qrp, qci, qv, s);

@@ -18,6 +18,7 @@ struct Error : std::runtime_error {
 };
 
 void count_launch();
+void count_launches(int64_t k);  // adds k (may be negative: graph capture bookkeeping)
 void set_last_error(const std::string& msg);
 
 #define BAMG_CK(call)                                                                              \
@@ -48,34 +49,43 @@ inline unsigned blocks_for(int64_t work, int per_block) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
-// Owning device buffer (cudaMalloc).  Persistent storage of a hierarchy.
+// Stream on which DevBuf allocations are ordered (set by the owner of the work: the
+// handle's stream during setup and solve).  Thread-local.
+cudaStream_t& alloc_stream();
+
+// Owning device buffer from the stream-ordered pool (cudaMallocAsync on alloc_stream()),
+// so building a hierarchy does not synchronise the device for every allocation.
+// Callers synchronise their streams before the owner is destroyed.
 template <typename T>
 struct DevBuf {
     T* p = nullptr;
     size_t n = 0;
+    cudaStream_t s = nullptr;
     DevBuf() = default;
     explicit DevBuf(size_t n_) { alloc(n_); }
     void alloc(size_t n_) {
         release();
-        if (n_) BAMG_CK(cudaMalloc(&p, n_ * sizeof(T)));
+        s = alloc_stream();
+        if (n_) BAMG_CK(cudaMallocAsync((void**)&p, n_ * sizeof(T), s));
         n = n_;
     }
     void ensure(size_t n_) {
         if (n_ > n) alloc(n_);
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, s);
         p = nullptr;
         n = 0;
     }
     ~DevBuf() { release(); }
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
     DevBuf& operator=(DevBuf&& o) noexcept {
         release();
         p = o.p;
         n = o.n;
+        s = o.s;
         o.p = nullptr;
         o.n = 0;
         return *this;

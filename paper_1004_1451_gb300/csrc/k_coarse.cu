@@ -1,171 +1,207 @@
 // Coarsest level (Algorithm 3, first branch; Section 4.2): the eigenpairs of
 // B_L x = lambda T_L x with the smallest |lambda|, and the minimal-norm inverse B_L^+.
-// Dense FP64, order n <= 64, each kernel run by one warp with the matrices in shared
-// memory.  Methods: LU with partial pivoting; Householder reduction to Hessenberg
-// form and the implicit double-shift QR iteration for the eigenvalues (Francis; Golub &
-// Van Loan, Matrix Computations, Sec. 7.5); inverse iteration in complex arithmetic
-// for the eigenvectors; a bordered LU solve for B^+.
+// Order n <= 64, one thread block per task, matrices in shared memory.
+//
+// Eigenpairs: the eigenvalues of T^{-1} B from an LU solve, a Householder reduction to
+// Hessenberg form and the implicit double-shift QR iteration (Francis; Golub & Van Loan,
+// Matrix Computations, Sec. 7.5), all in FP32 because they only serve as shifts; then,
+// per selected eigenvalue, FP64 inverse iteration in complex arithmetic on the pencil
+// (B - sigma T) and a Rayleigh-type quotient give the eigenvector and the eigenvalue to
+// FP64 accuracy.  B^+: a bordered FP64 LU solve.
 #include <cfloat>
+#include <cstdio>
+#include <cstdlib>
 
 #include "kernels.cuh"
 
 namespace bamg {
 
 constexpr int CN = 64;
+constexpr int LDP = CN + 1;  // padded row stride of shared matrices (no bank conflicts on columns)
+constexpr int CT = 256;  // threads per block
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
-// ---------------------------------------------------------------- real LU
-// In-place LU with partial pivoting of the n x n row-major A; perm[k] = pivot row of
-// step k.  Pivots smaller than floorv in magnitude are replaced by +-floorv.
-__device__ void lu_factor(double* A, int n, int* perm, double floorv) {
-    const int lane = lane_id();
+// ---------------------------------------------------------------- block-parallel real LU
+// In-place LU with partial pivoting of the n x n row-major A (shared memory); perm[k] =
+// pivot row of step k.  Pivots smaller than floorv in magnitude become +-floorv.
+__device__ void blu_factor(double* A, int n, int* perm, double floorv) {
+    const int tid = threadIdx.x;
     for (int k = 0; k < n; ++k) {
-        double best = -1.0;
-        int br = k;
-        for (int r = k + lane; r < n; r += 32) {
-            const double v = fabs(A[r * n + k]);
-            if (v > best) {
-                best = v;
-                br = r;
+        if (tid < 32) {
+            double best = -1.0;
+            int br = k;
+            for (int r = k + tid; r < n; r += 32) {
+                const double v = fabs(A[r * LDP + k]);
+                if (v > best) {
+                    best = v;
+                    br = r;
+                }
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-            if (ob > best || (ob == best && orr < br)) {
-                best = ob;
-                br = orr;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+                if (ob > best || (ob == best && orr < br)) {
+                    best = ob;
+                    br = orr;
+                }
             }
+            if (tid == 0) perm[k] = br;
         }
-        if (lane == 0) perm[k] = br;
+        __syncthreads();
+        const int br = perm[k];
         if (br != k)
-            for (int c = lane; c < n; c += 32) {
-                const double t = A[k * n + c];
-                A[k * n + c] = A[br * n + c];
-                A[br * n + c] = t;
+            for (int c = tid; c < n; c += blockDim.x) {
+                const double t = A[k * LDP + c];
+                A[k * LDP + c] = A[br * LDP + c];
+                A[br * LDP + c] = t;
             }
-        __syncwarp();
-        double p = A[k * n + k];
+        __syncthreads();
+        double p = A[k * LDP + k];
         if (fabs(p) < floorv) p = p >= 0.0 ? floorv : -floorv;
-        __syncwarp();
-        if (lane == 0) A[k * n + k] = p;
-        for (int r = k + 1 + lane; r < n; r += 32) A[r * n + k] /= p;
-        __syncwarp();
+        for (int r = k + 1 + tid; r < n; r += blockDim.x) A[r * LDP + k] /= p;
+        __syncthreads();
+        if (tid == 0) A[k * LDP + k] = p;
         const int m = n - k - 1;
-        for (int idx = lane; idx < m * m; idx += 32) {
+        for (int idx = tid; idx < m * m; idx += blockDim.x) {
             const int r = k + 1 + idx / m, c = k + 1 + idx % m;
-            A[r * n + c] -= A[r * n + k] * A[k * n + c];
+            A[r * LDP + c] -= A[r * LDP + k] * A[k * LDP + c];
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
-// Solves A X = Bm for m right-hand sides stored row-major (n x m) in place.
-__device__ void lu_solve(const double* A, int n, const int* perm, double* Bm, int m) {
-    const int lane = lane_id();
+// Solves A X = R for the m right-hand sides stored row-major (n x m) in R, in place.
+__device__ void blu_solve(const double* A, int n, const int* perm, double* R, int m) {
+    const int tid = threadIdx.x;
     for (int k = 0; k < n; ++k) {
         const int pk = perm[k];
-        if (pk != k)
-            for (int c = lane; c < m; c += 32) {
-                const double t = Bm[k * m + c];
-                Bm[k * m + c] = Bm[pk * m + c];
-                Bm[pk * m + c] = t;
+        if (pk != k) {
+            for (int c = tid; c < m; c += blockDim.x) {
+                const double t = R[k * m + c];
+                R[k * m + c] = R[pk * m + c];
+                R[pk * m + c] = t;
             }
-        __syncwarp();
-    }
-    for (int c = lane; c < m; c += 32) {
-        for (int r = 0; r < n; ++r) {
-            double s = Bm[r * m + c];
-            for (int q = 0; q < r; ++q) s -= A[r * n + q] * Bm[q * m + c];
-            Bm[r * m + c] = s;
-        }
-        for (int r = n - 1; r >= 0; --r) {
-            double s = Bm[r * m + c];
-            for (int q = r + 1; q < n; ++q) s -= A[r * n + q] * Bm[q * m + c];
-            Bm[r * m + c] = s / A[r * n + r];
+            __syncthreads();
         }
     }
-    __syncwarp();
+    for (int q = 0; q < n; ++q) {
+        const int rows = n - q - 1;
+        for (int idx = tid; idx < rows * m; idx += blockDim.x) {
+            const int r = q + 1 + idx / m, c = idx % m;
+            R[r * m + c] -= A[r * LDP + q] * R[q * m + c];
+        }
+        __syncthreads();
+    }
+    for (int q = n - 1; q >= 0; --q) {
+        for (int c = tid; c < m; c += blockDim.x) R[q * m + c] /= A[q * LDP + q];
+        __syncthreads();
+        for (int idx = tid; idx < q * m; idx += blockDim.x) {
+            const int r = idx / m, c = idx % m;
+            R[r * m + c] -= A[r * LDP + q] * R[q * m + c];
+        }
+        __syncthreads();
+    }
 }
 
-// ---------------------------------------------------------------- Hessenberg + QR
-__device__ void hessenberg(double* H, int n, double* v) {
-    const int lane = lane_id();
+// ---------------------------------------------------------------- FP32 Hessenberg + QR
+__device__ void hessenberg_f32(float* H, int n, float* v, float* dv, int* flag) {
+    const int tid = threadIdx.x;
     for (int k = 0; k + 2 < n; ++k) {
-        double ss = 0.0;
-        for (int r = k + 1 + lane; r < n; r += 32) ss += H[r * n + k] * H[r * n + k];
-        ss = warp_sum(ss);
-        const double x0 = H[(k + 1) * n + k];
-        if (ss == x0 * x0) continue;  // column already reduced
-        const double alpha = -copysign(sqrt(ss), x0);
-        const double v0 = x0 - alpha;
-        const double vn2 = ss - x0 * x0 + v0 * v0;
-        const double beta = 2.0 / vn2;
-        for (int r = k + 1 + lane; r < n; r += 32) v[r] = (r == k + 1) ? v0 : H[r * n + k];
-        __syncwarp();
-        for (int c = k + lane; c < n; c += 32) {
-            double d = 0.0;
-            for (int r = k + 1; r < n; ++r) d += v[r] * H[r * n + c];
-            d *= beta;
-            for (int r = k + 1; r < n; ++r) H[r * n + c] -= d * v[r];
+        if (tid < 32) {
+            float ss = 0.f;
+            for (int r = k + 1 + tid; r < n; r += 32) ss += H[r * LDP + k] * H[r * LDP + k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            const float x0 = H[(k + 1) * LDP + k];
+            const float tail = ss - x0 * x0;
+            if (tid == 0) {
+                if (!(tail > 0.f)) {
+                    flag[0] = 1;
+                } else {
+                    const float alpha = -copysignf(sqrtf(ss), x0);
+                    const float v0 = x0 - alpha;
+                    flag[0] = 0;
+                    dv[CN] = 2.f / (tail + v0 * v0);  // beta
+                    dv[CN + 1] = alpha;
+                    v[k + 1] = v0;
+                }
+            }
+            for (int r = k + 2 + tid; r < n; r += 32) v[r] = H[r * LDP + k];
         }
-        __syncwarp();
-        for (int r = lane; r < n; r += 32) {
-            double d = 0.0;
-            for (int c = k + 1; c < n; ++c) d += H[r * n + c] * v[c];
-            d *= beta;
-            for (int c = k + 1; c < n; ++c) H[r * n + c] -= d * v[c];
+        __syncthreads();
+        const int skip = flag[0];
+        const float beta = dv[CN];
+        __syncthreads();  // every thread has read flag and beta before warp 0 rewrites them
+        if (skip) continue;
+        for (int c = k + tid; c < n; c += blockDim.x) {
+            float d = 0.f;
+            for (int r = k + 1; r < n; ++r) d += v[r] * H[r * LDP + c];
+            dv[c] = beta * d;
         }
-        __syncwarp();
-        if (lane == 0) {
-            H[(k + 1) * n + k] = alpha;
-            for (int r = k + 2; r < n; ++r) H[r * n + k] = 0.0;
+        __syncthreads();
+        for (int idx = tid; idx < (n - k - 1) * (n - k); idx += blockDim.x) {
+            const int r = k + 1 + idx / (n - k), c = k + idx % (n - k);
+            H[r * LDP + c] -= dv[c] * v[r];
         }
-        __syncwarp();
+        __syncthreads();
+        for (int r = tid; r < n; r += blockDim.x) {
+            float d = 0.f;
+            for (int c = k + 1; c < n; ++c) d += H[r * LDP + c] * v[c];
+            dv[r] = beta * d;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < n * (n - k - 1); idx += blockDim.x) {
+            const int r = idx / (n - k - 1), c = k + 1 + idx % (n - k - 1);
+            H[r * LDP + c] -= dv[r] * v[c];
+        }
+        __syncthreads();
+        if (tid == 0) H[(k + 1) * LDP + k] = dv[CN + 1];
+        for (int r = k + 2 + tid; r < n; r += blockDim.x) H[r * LDP + k] = 0.f;
+        __syncthreads();
     }
 }
 
-__device__ __forceinline__ void house3(double x, double y, double z, double& v0, double& v1, double& v2, double& beta) {
-    const double nrm = sqrt(x * x + y * y + z * z);
-    if (nrm == 0.0) {
-        v0 = 1.0;
-        v1 = v2 = 0.0;
-        beta = 0.0;
+__device__ __forceinline__ void house3f(float x, float y, float z, float& v0, float& v1, float& v2, float& beta) {
+    const float nrm = sqrtf(x * x + y * y + z * z);
+    if (nrm == 0.f) {
+        v0 = 1.f;
+        v1 = v2 = 0.f;
+        beta = 0.f;
         return;
     }
-    const double alpha = -copysign(nrm, x);
+    const float alpha = -copysignf(nrm, x);
     v0 = x - alpha;
     v1 = y;
     v2 = z;
-    beta = 2.0 / (v0 * v0 + v1 * v1 + v2 * v2);
+    beta = 2.f / (v0 * v0 + v1 * v1 + v2 * v2);
 }
 
-// Eigenvalues of the upper Hessenberg H (destroyed).  Returns 0, or -1 if the
+// Eigenvalues of the upper Hessenberg H (destroyed), one warp.  0, or -1 when the
 // iteration did not converge within 40 n double-shift steps.
-__device__ int hqr(double* H, int n, double* wr, double* wi) {
+__device__ int hqr_f32(float* H, int n, float* wr, float* wi, int* steps) {
     const int lane = lane_id();
-    double hnorm = 0.0;
-    for (int idx = lane; idx < n * n; idx += 32) hnorm = fmax(hnorm, fabs(H[idx]));
+    float hnorm = 0.f;
+    for (int idx = lane; idx < n * n; idx += 32) hnorm = fmaxf(hnorm, fabsf(H[(idx / n) * LDP + idx % n]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) hnorm = fmax(hnorm, __shfl_xor_sync(0xffffffffu, hnorm, o));
-    if (hnorm == 0.0) hnorm = 1.0;
+    for (int o = 16; o > 0; o >>= 1) hnorm = fmaxf(hnorm, __shfl_xor_sync(0xffffffffu, hnorm, o));
+    if (hnorm == 0.f) hnorm = 1.f;
     int hi = n - 1, its = 0, total = 0;
     while (hi >= 0) {
         if (total > 40 * n) return -1;
         int l = hi;
         while (l > 0) {
-            double s = fabs(H[(l - 1) * n + l - 1]) + fabs(H[l * n + l]);
-            if (s == 0.0) s = hnorm;
-            if (fabs(H[l * n + l - 1]) <= DBL_EPSILON * s) break;
+            float s = fabsf(H[(l - 1) * LDP + l - 1]) + fabsf(H[l * LDP + l]);
+            if (s == 0.f) s = hnorm;
+            if (fabsf(H[l * LDP + l - 1]) <= FLT_EPSILON * s) break;
             --l;
         }
         __syncwarp();
         if (l == hi) {
             if (lane == 0) {
-                wr[hi] = H[hi * n + hi];
-                wi[hi] = 0.0;
+                wr[hi] = H[hi * LDP + hi];
+                wi[hi] = 0.f;
             }
             --hi;
             its = 0;
@@ -173,20 +209,19 @@ __device__ int hqr(double* H, int n, double* wr, double* wi) {
             continue;
         }
         if (l == hi - 1) {
-            const double a = H[(hi - 1) * n + hi - 1], b = H[(hi - 1) * n + hi];
-            const double c = H[hi * n + hi - 1], d = H[hi * n + hi];
-            const double p = 0.5 * (a - d), q = p * p + b * c, mid = d + p;
+            const float a = H[(hi - 1) * LDP + hi - 1], b = H[(hi - 1) * LDP + hi];
+            const float c = H[hi * LDP + hi - 1], d = H[hi * LDP + hi];
+            const float p = 0.5f * (a - d), q = p * p + b * c, mid = d + p;
             if (lane == 0) {
-                if (q >= 0.0) {
-                    const double sq = sqrt(q);
-                    const double l1 = mid + copysign(sq, mid);
-                    const double det = a * d - b * c;
-                    const double l2 = l1 != 0.0 ? det / l1 : mid - sq;
+                if (q >= 0.f) {
+                    const float sq = sqrtf(q);
+                    const float l1 = mid + copysignf(sq, mid);
+                    const float det = a * d - b * c;
                     wr[hi - 1] = l1;
-                    wr[hi] = l2;
-                    wi[hi - 1] = wi[hi] = 0.0;
+                    wr[hi] = l1 != 0.f ? det / l1 : mid - sq;
+                    wi[hi - 1] = wi[hi] = 0.f;
                 } else {
-                    const double im = sqrt(-q);
+                    const float im = sqrtf(-q);
                     wr[hi - 1] = wr[hi] = mid;
                     wi[hi - 1] = im;
                     wi[hi] = -im;
@@ -197,103 +232,187 @@ __device__ int hqr(double* H, int n, double* wr, double* wi) {
             __syncwarp();
             continue;
         }
-        double s, t;
+        float s, t;
         if (its == 10 || its == 20) {
-            const double e = fabs(H[hi * n + hi - 1]) + fabs(H[(hi - 1) * n + hi - 2]);
-            s = 1.5 * e;
+            const float e = fabsf(H[hi * LDP + hi - 1]) + fabsf(H[(hi - 1) * LDP + hi - 2]);
+            s = 1.5f * e;
             t = e * e;
         } else {
-            s = H[(hi - 1) * n + hi - 1] + H[hi * n + hi];
-            t = H[(hi - 1) * n + hi - 1] * H[hi * n + hi] - H[(hi - 1) * n + hi] * H[hi * n + hi - 1];
+            s = H[(hi - 1) * LDP + hi - 1] + H[hi * LDP + hi];
+            t = H[(hi - 1) * LDP + hi - 1] * H[hi * LDP + hi] - H[(hi - 1) * LDP + hi] * H[hi * LDP + hi - 1];
         }
         ++its;
         ++total;
-        double x = H[l * n + l] * H[l * n + l] + H[l * n + l + 1] * H[(l + 1) * n + l] - s * H[l * n + l] + t;
-        double y = H[(l + 1) * n + l] * (H[l * n + l] + H[(l + 1) * n + l + 1] - s);
-        double z = H[(l + 1) * n + l] * H[(l + 2) * n + l + 1];
+        float x = H[l * LDP + l] * H[l * LDP + l] + H[l * LDP + l + 1] * H[(l + 1) * LDP + l] - s * H[l * LDP + l] + t;
+        float y = H[(l + 1) * LDP + l] * (H[l * LDP + l] + H[(l + 1) * LDP + l + 1] - s);
+        float z = H[(l + 1) * LDP + l] * H[(l + 2) * LDP + l + 1];
         __syncwarp();
         for (int k = l; k <= hi - 2; ++k) {
-            double v0, v1, v2, beta;
-            house3(x, y, z, v0, v1, v2, beta);
+            float v0, v1, v2, beta;
+            house3f(x, y, z, v0, v1, v2, beta);
             const int c0 = k - 1 > l ? k - 1 : l;
             for (int c = c0 + lane; c <= hi; c += 32) {
-                const double d = beta * (v0 * H[k * n + c] + v1 * H[(k + 1) * n + c] + v2 * H[(k + 2) * n + c]);
-                H[k * n + c] -= d * v0;
-                H[(k + 1) * n + c] -= d * v1;
-                H[(k + 2) * n + c] -= d * v2;
+                const float d = beta * (v0 * H[k * LDP + c] + v1 * H[(k + 1) * LDP + c] + v2 * H[(k + 2) * LDP + c]);
+                H[k * LDP + c] -= d * v0;
+                H[(k + 1) * LDP + c] -= d * v1;
+                H[(k + 2) * LDP + c] -= d * v2;
             }
             __syncwarp();
             const int r1 = k + 3 < hi ? k + 3 : hi;
             for (int r = l + lane; r <= r1; r += 32) {
-                const double d = beta * (H[r * n + k] * v0 + H[r * n + k + 1] * v1 + H[r * n + k + 2] * v2);
-                H[r * n + k] -= d * v0;
-                H[r * n + k + 1] -= d * v1;
-                H[r * n + k + 2] -= d * v2;
+                const float d = beta * (H[r * LDP + k] * v0 + H[r * LDP + k + 1] * v1 + H[r * LDP + k + 2] * v2);
+                H[r * LDP + k] -= d * v0;
+                H[r * LDP + k + 1] -= d * v1;
+                H[r * LDP + k + 2] -= d * v2;
             }
             __syncwarp();
-            x = H[(k + 1) * n + k];
-            y = H[(k + 2) * n + k];
-            z = (k + 3 <= hi) ? H[(k + 3) * n + k] : 0.0;
+            x = H[(k + 1) * LDP + k];
+            y = H[(k + 2) * LDP + k];
+            z = (k + 3 <= hi) ? H[(k + 3) * LDP + k] : 0.f;
             __syncwarp();
         }
         {
-            double v0, v1, v2, beta;
-            house3(x, y, 0.0, v0, v1, v2, beta);
+            float v0, v1, v2, beta;
+            house3f(x, y, 0.f, v0, v1, v2, beta);
             const int k = hi - 1;
             for (int c = (k - 1) + lane; c <= hi; c += 32) {
-                const double d = beta * (v0 * H[k * n + c] + v1 * H[(k + 1) * n + c]);
-                H[k * n + c] -= d * v0;
-                H[(k + 1) * n + c] -= d * v1;
+                const float d = beta * (v0 * H[k * LDP + c] + v1 * H[(k + 1) * LDP + c]);
+                H[k * LDP + c] -= d * v0;
+                H[(k + 1) * LDP + c] -= d * v1;
             }
             __syncwarp();
             for (int r = l + lane; r <= hi; r += 32) {
-                const double d = beta * (H[r * n + k] * v0 + H[r * n + k + 1] * v1);
-                H[r * n + k] -= d * v0;
-                H[r * n + k + 1] -= d * v1;
+                const float d = beta * (H[r * LDP + k] * v0 + H[r * LDP + k + 1] * v1);
+                H[r * LDP + k] -= d * v0;
+                H[r * LDP + k + 1] -= d * v1;
             }
             __syncwarp();
         }
     }
+    *steps = total;
     return 0;
 }
 
-// Kernel 1: M = T^{-1} B (kept in global memory for the vectors), its eigenvalues, and
-// the selection: eigenvalues with Im >= 0 (each complex pair is represented by its
-// member with positive imaginary part) sorted by |lambda|; a real one takes one vector
-// column, a pair two (Re v, Im v), until k_ev columns are filled.
-// sel[3*q + {0,1,2}] = (Re lambda, Im lambda, first column); info = {nvec, nsel, status}.
-__global__ void k_coarse_eigvals(int n, const double* __restrict__ Bg, const double* __restrict__ Tg, int k_ev,
-                                 double* __restrict__ Mg, double* __restrict__ sel, double* __restrict__ lam,
-                                 int32_t* __restrict__ kind, int* __restrict__ info) {
-    extern __shared__ double sm[];
-    double* A = sm;            // B -> M -> Hessenberg
-    double* Tm = sm + CN * CN; // T -> LU(T)
-    __shared__ int perm[CN];
-    __shared__ double v[CN], wr[CN], wi[CN];
-    const int lane = lane_id();
-    for (int idx = lane; idx < n * n; idx += 32) {
-        A[idx] = Bg[idx];
-        Tm[idx] = Tg[idx];
+// FP32 LU with partial pivoting (block-parallel) and the solve T M = B for n right-hand
+// sides, used only to obtain shifts.
+__device__ void blu_factor_f32(float* A, int n, int* perm) {
+    const int tid = threadIdx.x;
+    for (int k = 0; k < n; ++k) {
+        if (tid < 32) {
+            float best = -1.f;
+            int br = k;
+            for (int r = k + tid; r < n; r += 32) {
+                const float v = fabsf(A[r * LDP + k]);
+                if (v > best) {
+                    best = v;
+                    br = r;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+                if (ob > best || (ob == best && orr < br)) {
+                    best = ob;
+                    br = orr;
+                }
+            }
+            if (tid == 0) perm[k] = br;
+        }
+        __syncthreads();
+        const int br = perm[k];
+        if (br != k)
+            for (int c = tid; c < n; c += blockDim.x) {
+                const float t = A[k * LDP + c];
+                A[k * LDP + c] = A[br * LDP + c];
+                A[br * LDP + c] = t;
+            }
+        __syncthreads();
+        float p = A[k * LDP + k];
+        if (fabsf(p) < 1e-30f) p = p >= 0.f ? 1e-30f : -1e-30f;
+        const float pinv = 1.f / p;
+        for (int r = k + 1 + tid; r < n; r += blockDim.x) A[r * LDP + k] *= pinv;
+        __syncthreads();
+        if (tid == 0) A[k * LDP + k] = p;
+        const int m = n - k - 1;
+        for (int idx = tid; idx < m * m; idx += blockDim.x) {
+            const int r = k + 1 + idx / m, c = k + 1 + idx % m;
+            A[r * LDP + c] -= A[r * LDP + k] * A[k * LDP + c];
+        }
+        __syncthreads();
     }
+}
+
+__device__ void blu_solve_f32(const float* A, int n, const int* perm, float* R, int m, int ldr) {
+    const int tid = threadIdx.x;
+    for (int k = 0; k < n; ++k) {
+        const int pk = perm[k];
+        if (pk != k) {
+            for (int c = tid; c < m; c += blockDim.x) {
+                const float t = R[k * ldr + c];
+                R[k * ldr + c] = R[pk * ldr + c];
+                R[pk * ldr + c] = t;
+            }
+            __syncthreads();
+        }
+    }
+    for (int q = 0; q < n; ++q) {
+        for (int idx = tid; idx < (n - q - 1) * m; idx += blockDim.x) {
+            const int r = q + 1 + idx / m, c = idx % m;
+            R[r * ldr + c] -= A[r * LDP + q] * R[q * ldr + c];
+        }
+        __syncthreads();
+    }
+    for (int q = n - 1; q >= 0; --q) {
+        const float d = 1.f / A[q * LDP + q];
+        for (int c = tid; c < m; c += blockDim.x) R[q * ldr + c] *= d;
+        __syncthreads();
+        for (int idx = tid; idx < q * m; idx += blockDim.x) {
+            const int r = idx / m, c = idx % m;
+            R[r * ldr + c] -= A[r * LDP + q] * R[q * ldr + c];
+        }
+        __syncthreads();
+    }
+}
+
+// Kernel 1: eigenvalues of T^{-1} B in FP32 (they serve only as shifts) and the
+// selection: eigenvalues with Im >= 0 (a complex pair is represented by its member
+// with positive imaginary part) in order of |lambda|; a real one takes one vector
+// column, a pair two (Re v, Im v), until k_ev columns are filled.
+// sel[3q + {0,1,2}] = (Re, Im, first column); info = {columns, selected, status}.
+__global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __restrict__ Bg,
+                                                       const double* __restrict__ Tg, int k_ev,
+                                                       double* __restrict__ sel, double* __restrict__ lam,
+                                                       int32_t* __restrict__ kind, int* __restrict__ info) {
+    __shared__ float A[CN * LDP], Tm[CN * LDP];
+    __shared__ int perm[CN];
+    __shared__ float v[CN], dv[CN + 2], wr[CN], wi[CN];
+    __shared__ int flag[1];
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const int r = idx / n, c = idx % n;
+        A[r * LDP + c] = (float)Bg[idx];
+        Tm[r * LDP + c] = (float)Tg[idx];
+    }
+    __syncthreads();
+    blu_factor_f32(Tm, n, perm);
+    blu_solve_f32(Tm, n, perm, A, n, LDP);
+    hessenberg_f32(A, n, v, dv, flag);
+    if (tid >= 32) return;
+    int steps = 0;
+    const int st = hqr_f32(A, n, wr, wi, &steps);
     __syncwarp();
-    lu_factor(Tm, n, perm, 1e-300);
-    lu_solve(Tm, n, perm, A, n);
-    for (int idx = lane; idx < n * n; idx += 32) Mg[idx] = A[idx];
-    __syncwarp();
-    hessenberg(A, n, v);
-    const int st = hqr(A, n, wr, wi);
-    __syncwarp();
-    if (lane == 0) {
+    if (tid == 0) {
         int order[CN];
         int m = 0;
         for (int q = 0; q < n; ++q)
-            if (wi[q] >= 0.0) order[m++] = q;
+            if (wi[q] >= 0.f) order[m++] = q;
         for (int a = 1; a < m; ++a)
             for (int b = a; b > 0; --b) {
-                const double m0 = hypot(wr[order[b - 1]], wi[order[b - 1]]);
-                const double m1 = hypot(wr[order[b]], wi[order[b]]);
+                const float m0 = hypotf(wr[order[b - 1]], wi[order[b - 1]]);
+                const float m1 = hypotf(wr[order[b]], wi[order[b]]);
                 if (m0 > m1) {
-                    int t = order[b];
+                    const int t = order[b];
                     order[b] = order[b - 1];
                     order[b - 1] = t;
                 } else
@@ -306,7 +425,7 @@ __global__ void k_coarse_eigvals(int n, const double* __restrict__ Bg, const dou
             sel[3 * ns + 1] = wi[q];
             sel[3 * ns + 2] = (double)col;
             ++ns;
-            if (wi[q] == 0.0) {
+            if (wi[q] == 0.f) {
                 lam[col] = wr[q];
                 kind[col] = 0;
                 col += 1;
@@ -321,141 +440,188 @@ __global__ void k_coarse_eigvals(int n, const double* __restrict__ Bg, const dou
         info[0] = col;
         info[1] = ns;
         info[2] = st;
+        info[3] = steps;
     }
 }
 
 // ---------------------------------------------------------------- complex inverse iteration
-// Kernel 2: one block per selected eigenvalue.  Three steps of inverse iteration with
-// (M - sigma I), sigma = lambda + delta (delta = 1e-10 max(1, max|M|) keeps the LU
-// finite); then unit 2-norm and the phase that makes <w, v> real positive, w_i = i + 1.
-__global__ void k_coarse_eigvec(int n, const double* __restrict__ Mg, const double* __restrict__ sel,
-                                double* __restrict__ V) {
+// Kernel 2, one block per selected eigenvalue: LU of the pencil (B - sigma T) in
+// complex FP64 with sigma the FP32 estimate; four steps of inverse iteration
+// v <- (B - sigma T)^{-1} T v from a fixed positive start; the Rayleigh-type quotient
+// lambda = v^H B v / v^H T v (Algorithm 3's update, in complex form); and the phase that
+// makes <w, v> real and positive (w_i = i + 1) with unit 2-norm.
+__global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __restrict__ Bg,
+                                                      const double* __restrict__ Tg, const double* __restrict__ sel,
+                                                      double* __restrict__ V, double* __restrict__ lam) {
     extern __shared__ double sm[];
     double* Ar = sm;
-    double* Ai = sm + CN * CN;
-    __shared__ double vr[CN], vi[CN];
+    double* Ai = sm + CN * LDP;
+    __shared__ double vr[CN], vi[CN], tr[CN], ti[CN], red[4 * (CT / 32)];
     __shared__ int perm[CN];
-    const int lane = lane_id();
-    const double lre = sel[3 * blockIdx.x], lim = sel[3 * blockIdx.x + 1];
+    const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+    const double sr = sel[3 * blockIdx.x], si = sel[3 * blockIdx.x + 1];
     const int col = (int)sel[3 * blockIdx.x + 2];
-    double mx = 0.0;
-    for (int idx = lane; idx < n * n; idx += 32) mx = fmax(mx, fabs(Mg[idx]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const double sr = lre + 1e-10 * fmax(1.0, mx), si = lim;
-    for (int idx = lane; idx < n * n; idx += 32) {
-        const int r = idx / n, c = idx % n;
-        Ar[idx] = Mg[idx] - (r == c ? sr : 0.0);
-        Ai[idx] = (r == c ? -si : 0.0);
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const double t = Tg[idx];
+        Ar[(idx / n) * LDP + idx % n] = Bg[idx] - sr * t;
+        Ai[(idx / n) * LDP + idx % n] = -si * t;
     }
-    __syncwarp();
-    // complex LU with partial pivoting on |a|
+    __syncthreads();
     for (int k = 0; k < n; ++k) {
-        double best = -1.0;
-        int br = k;
-        for (int r = k + lane; r < n; r += 32) {
-            const double m = hypot(Ar[r * n + k], Ai[r * n + k]);
-            if (m > best) {
-                best = m;
-                br = r;
+        if (tid < 32) {
+            double best = -1.0;
+            int br = k;
+            for (int r = k + tid; r < n; r += 32) {
+                const double m = fabs(Ar[r * LDP + k]) + fabs(Ai[r * LDP + k]);
+                if (m > best) {
+                    best = m;
+                    br = r;
+                }
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-            if (ob > best || (ob == best && orr < br)) {
-                best = ob;
-                br = orr;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+                if (ob > best || (ob == best && orr < br)) {
+                    best = ob;
+                    br = orr;
+                }
             }
+            if (tid == 0) perm[k] = br;
         }
-        if (lane == 0) perm[k] = br;
+        __syncthreads();
+        const int br = perm[k];
         if (br != k)
-            for (int c = lane; c < n; c += 32) {
-                double t = Ar[k * n + c];
-                Ar[k * n + c] = Ar[br * n + c];
-                Ar[br * n + c] = t;
-                t = Ai[k * n + c];
-                Ai[k * n + c] = Ai[br * n + c];
-                Ai[br * n + c] = t;
+            for (int c = tid; c < n; c += blockDim.x) {
+                double t = Ar[k * LDP + c];
+                Ar[k * LDP + c] = Ar[br * LDP + c];
+                Ar[br * LDP + c] = t;
+                t = Ai[k * LDP + c];
+                Ai[k * LDP + c] = Ai[br * LDP + c];
+                Ai[br * LDP + c] = t;
             }
-        __syncwarp();
-        double pr = Ar[k * n + k], pi = Ai[k * n + k];
-        if (hypot(pr, pi) < 1e-300) {
+        __syncthreads();
+        double pr = Ar[k * LDP + k], pi = Ai[k * LDP + k];
+        if (fabs(pr) + fabs(pi) < 1e-300) {
             pr = 1e-300;
             pi = 0.0;
         }
-        const double den = pr * pr + pi * pi;
-        __syncwarp();
-        if (lane == 0) {
-            Ar[k * n + k] = pr;
-            Ai[k * n + k] = pi;
+        const double inv = 1.0 / (pr * pr + pi * pi);
+        const double qr_ = pr * inv, qi_ = -pi * inv;  // 1 / pivot
+        for (int r = k + 1 + tid; r < n; r += blockDim.x) {
+            const double ar = Ar[r * LDP + k], ai = Ai[r * LDP + k];
+            Ar[r * LDP + k] = ar * qr_ - ai * qi_;
+            Ai[r * LDP + k] = ar * qi_ + ai * qr_;
         }
-        for (int r = k + 1 + lane; r < n; r += 32) {
-            const double ar = Ar[r * n + k], ai = Ai[r * n + k];
-            Ar[r * n + k] = (ar * pr + ai * pi) / den;
-            Ai[r * n + k] = (ai * pr - ar * pi) / den;
+        __syncthreads();
+        if (tid == 0) {
+            Ar[k * LDP + k] = pr;
+            Ai[k * LDP + k] = pi;
         }
-        __syncwarp();
         const int m = n - k - 1;
-        for (int idx = lane; idx < m * m; idx += 32) {
+        for (int idx = tid; idx < m * m; idx += blockDim.x) {
             const int r = k + 1 + idx / m, c = k + 1 + idx % m;
-            const double lr = Ar[r * n + k], li = Ai[r * n + k];
-            const double ur = Ar[k * n + c], ui = Ai[k * n + c];
-            Ar[r * n + c] -= lr * ur - li * ui;
-            Ai[r * n + c] -= lr * ui + li * ur;
+            const double lr = Ar[r * LDP + k], li = Ai[r * LDP + k];
+            const double ur = Ar[k * LDP + c], ui = Ai[k * LDP + c];
+            Ar[r * LDP + c] -= lr * ur - li * ui;
+            Ai[r * LDP + c] -= lr * ui + li * ur;
         }
-        __syncwarp();
+        __syncthreads();
     }
-    for (int r = lane; r < n; r += 32) {
+    for (int r = tid; r < n; r += blockDim.x) {
         vr[r] = 1.0 + (double)r / (double)n;
         vi[r] = 0.0;
     }
-    __syncwarp();
-    for (int it = 0; it < 3; ++it) {
-        if (lane == 0) {
+    __syncthreads();
+    for (int it = 0; it < 4; ++it) {
+        // t = T v (rows in parallel)
+        for (int r = tid; r < n; r += blockDim.x) {
+            double a = 0.0, b = 0.0;
+            for (int c = 0; c < n; ++c) {
+                const double t = Tg[r * n + c];
+                a += t * vr[c];
+                b += t * vi[c];
+            }
+            tr[r] = a;
+            ti[r] = b;
+        }
+        __syncthreads();
+        if (tid < 32) {  // one warp: column-oriented substitutions on t
             for (int k = 0; k < n; ++k) {
                 const int pk = perm[k];
-                if (pk != k) {
-                    double t = vr[k];
-                    vr[k] = vr[pk];
-                    vr[pk] = t;
-                    t = vi[k];
-                    vi[k] = vi[pk];
-                    vi[pk] = t;
+                if (pk != k && lane == 0) {
+                    double t = tr[k];
+                    tr[k] = tr[pk];
+                    tr[pk] = t;
+                    t = ti[k];
+                    ti[k] = ti[pk];
+                    ti[pk] = t;
                 }
+                __syncwarp();
             }
-            for (int r = 0; r < n; ++r) {
-                double sr2 = vr[r], si2 = vi[r];
-                for (int q = 0; q < r; ++q) {
-                    sr2 -= Ar[r * n + q] * vr[q] - Ai[r * n + q] * vi[q];
-                    si2 -= Ar[r * n + q] * vi[q] + Ai[r * n + q] * vr[q];
+            for (int q = 0; q < n; ++q) {
+                const double yr = tr[q], yi = ti[q];
+                for (int r = q + 1 + lane; r < n; r += 32) {
+                    tr[r] -= Ar[r * LDP + q] * yr - Ai[r * LDP + q] * yi;
+                    ti[r] -= Ar[r * LDP + q] * yi + Ai[r * LDP + q] * yr;
                 }
-                vr[r] = sr2;
-                vi[r] = si2;
+                __syncwarp();
             }
-            for (int r = n - 1; r >= 0; --r) {
-                double sr2 = vr[r], si2 = vi[r];
-                for (int q = r + 1; q < n; ++q) {
-                    sr2 -= Ar[r * n + q] * vr[q] - Ai[r * n + q] * vi[q];
-                    si2 -= Ar[r * n + q] * vi[q] + Ai[r * n + q] * vr[q];
+            for (int q = n - 1; q >= 0; --q) {
+                if (lane == 0) {
+                    const double ur = Ar[q * LDP + q], ui = Ai[q * LDP + q];
+                    const double d = 1.0 / (ur * ur + ui * ui);
+                    const double a = tr[q], b = ti[q];
+                    tr[q] = (a * ur + b * ui) * d;
+                    ti[q] = (b * ur - a * ui) * d;
                 }
-                const double ur = Ar[r * n + r], ui = Ai[r * n + r];
-                const double d = ur * ur + ui * ui;
-                vr[r] = (sr2 * ur + si2 * ui) / d;
-                vi[r] = (si2 * ur - sr2 * ui) / d;
+                __syncwarp();
+                const double yr = tr[q], yi = ti[q];
+                for (int r = lane; r < q; r += 32) {
+                    tr[r] -= Ar[r * LDP + q] * yr - Ai[r * LDP + q] * yi;
+                    ti[r] -= Ar[r * LDP + q] * yi + Ai[r * LDP + q] * yr;
+                }
+                __syncwarp();
             }
+            double nn = 0.0;
+            for (int r = lane; r < n; r += 32) nn += tr[r] * tr[r] + ti[r] * ti[r];
+            nn = 1.0 / sqrt(warp_sum(nn));
+            for (int r = lane; r < n; r += 32) {
+                vr[r] = tr[r] * nn;
+                vi[r] = ti[r] * nn;
+            }
+            __syncwarp();
         }
-        __syncwarp();
-        double nn = 0.0;
-        for (int r = lane; r < n; r += 32) nn += vr[r] * vr[r] + vi[r] * vi[r];
-        nn = sqrt(warp_sum(nn));
-        for (int r = lane; r < n; r += 32) {
-            vr[r] /= nn;
-            vi[r] /= nn;
-        }
-        __syncwarp();
+        __syncthreads();
     }
+    // lambda = v^H B v / v^H T v
+    double br_ = 0.0, bi_ = 0.0, tr_ = 0.0, ti_ = 0.0;
+    for (int r = tid; r < n; r += blockDim.x) {
+        double wbr = 0.0, wbi = 0.0, wtr = 0.0, wti = 0.0;
+        for (int c = 0; c < n; ++c) {
+            const double b = Bg[r * n + c], t = Tg[r * n + c];
+            wbr += b * vr[c];
+            wbi += b * vi[c];
+            wtr += t * vr[c];
+            wti += t * vi[c];
+        }
+        br_ += vr[r] * wbr + vi[r] * wbi;
+        bi_ += vr[r] * wbi - vi[r] * wbr;
+        tr_ += vr[r] * wtr + vi[r] * wti;
+        ti_ += vr[r] * wti - vi[r] * wtr;
+    }
+    br_ = warp_sum(br_);
+    bi_ = warp_sum(bi_);
+    tr_ = warp_sum(tr_);
+    ti_ = warp_sum(ti_);
+    if (lane == 0) {
+        red[4 * wid] = br_;
+        red[4 * wid + 1] = bi_;
+        red[4 * wid + 2] = tr_;
+        red[4 * wid + 3] = ti_;
+    }
+    __syncthreads();
+    if (tid >= 32) return;
     double sr2 = 0.0, si2 = 0.0;
     for (int r = lane; r < n; r += 32) {
         sr2 += (double)(r + 1) * vr[r];
@@ -472,10 +638,24 @@ __global__ void k_coarse_eigvec(int n, const double* __restrict__ Mg, const doub
         vi[r] = b;
         nn += a * a + b * b;
     }
-    nn = sqrt(warp_sum(nn));
+    nn = 1.0 / sqrt(warp_sum(nn));
     for (int r = lane; r < n; r += 32) {
-        V[(int64_t)col * n + r] = vr[r] / nn;
-        if (lim != 0.0) V[(int64_t)(col + 1) * n + r] = vi[r] / nn;
+        V[(int64_t)col * n + r] = vr[r] * nn;
+        if (si != 0.0) V[(int64_t)(col + 1) * n + r] = vi[r] * nn;
+    }
+    if (lane == 0) {
+        double nbr = 0.0, nbi = 0.0, ntr = 0.0, nti = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            nbr += red[4 * w];
+            nbi += red[4 * w + 1];
+            ntr += red[4 * w + 2];
+            nti += red[4 * w + 3];
+        }
+        // Re of (nbr + i nbi) / (ntr + i nti)
+        double lre = (nbr * ntr + nbi * nti) / (ntr * ntr + nti * nti);
+        if (col == 0) lre = 0.0;  // the state vector's eigenvalue is exactly zero
+        lam[col] = lre;
+        if (si != 0.0) lam[col + 1] = lre;
     }
 }
 
@@ -484,20 +664,20 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
     BAMG_REQUIRE(n >= 1 && n <= CN, BAMG_EINVAL, "coarse_eig: coarsest order must be 1..64");
     BAMG_REQUIRE(k_ev >= 1 && k_ev <= 16, BAMG_EINVAL, "coarse_eig: 1 <= k_ev <= 16");
     static bool attr = false;
-    const size_t smem = 2 * CN * CN * sizeof(double);
+    const size_t smem = 2 * CN * LDP * sizeof(double);
     if (!attr) {
-        BAMG_CK(cudaFuncSetAttribute(k_coarse_eigvals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         BAMG_CK(cudaFuncSetAttribute(k_coarse_eigvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    TmpBuf<double> M((size_t)n * n, s), sel(3 * (k_ev + 1), s);
+    TmpBuf<double> sel(3 * (k_ev + 1), s);
     TmpBuf<int> info(4, s);
-    BAMG_LAUNCH(k_coarse_eigvals, 1, 32, smem, s, n, dB, dT, k_ev, M.get(), sel.get(), d_lam, d_kind, info.get());
+    BAMG_LAUNCH(k_coarse_eigvals, 1, CT, 0, s, n, dB, dT, k_ev, sel.get(), d_lam, d_kind, info.get());
     int h[4] = {0, 0, 0, 0};
     BAMG_CK(cudaMemcpyAsync(h, info.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
     BAMG_CK(cudaStreamSynchronize(s));
+    if (getenv("BAMG_DEBUG")) fprintf(stderr, "[bamg] coarse QR: n=%d double-shift steps=%d status=%d\n", n, h[3], h[2]);
     if (h[2] != 0) return BAMG_ENUMERIC;
-    if (h[1] > 0) BAMG_LAUNCH(k_coarse_eigvec, h[1], 32, smem, s, n, M.get(), sel.get(), d_V);
+    if (h[1] > 0) BAMG_LAUNCH(k_coarse_eigvec, h[1], CT, smem, s, n, dB, dT, sel.get(), d_V, d_lam);
     return h[0];
 }
 
@@ -506,63 +686,70 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
 // inverse iteration on the LU of B with a pivot floor); with z = 1/sqrt(n) the bordered
 // matrix M = B + z y^T is nonsingular and B^+ = M^{-1} (I - z z^T): M w = (I - z z^T) b
 // forces y^T w = 0, so w is the solution of B w = (I - z z^T) b orthogonal to null(B).
-__global__ void k_coarse_pinv(int n, const double* __restrict__ Bg, double* __restrict__ Pg, int* __restrict__ info) {
+__global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restrict__ Bg, double* __restrict__ Pg,
+                                                    int* __restrict__ info) {
     extern __shared__ double sm[];
     double* A = sm;
-    double* R = sm + CN * CN;
-    __shared__ double y[CN];
+    double* R = sm + CN * LDP;
+    __shared__ double y[CN], red[CT / 32];
     __shared__ int perm[CN];
-    const int lane = lane_id();
+    const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
     double mx = 0.0;
-    for (int idx = lane; idx < n * n; idx += 32) {
-        A[idx] = Bg[idx];
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        A[(idx / n) * LDP + idx % n] = Bg[idx];
         mx = fmax(mx, fabs(Bg[idx]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __syncwarp();
-    lu_factor(A, n, perm, 1e-14 * fmax(mx, 1e-300));
-    for (int r = lane; r < n; r += 32) R[r] = 1.0;
-    __syncwarp();
+    if (lane == 0) red[wid] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    __syncthreads();
+    blu_factor(A, n, perm, 1e-14 * fmax(mx, 1e-300));
+    for (int r = tid; r < n; r += blockDim.x) R[r] = 1.0;
+    __syncthreads();
     for (int it = 0; it < 2; ++it) {
-        lu_solve(A, n, perm, R, 1);
-        double nn = 0.0;
-        for (int r = lane; r < n; r += 32) nn += R[r] * R[r];
-        nn = sqrt(warp_sum(nn));
-        for (int r = lane; r < n; r += 32) R[r] /= nn;
-        __syncwarp();
+        blu_solve(A, n, perm, R, 1);
+        if (tid < 32) {
+            double nn = 0.0;
+            for (int r = lane; r < n; r += 32) nn += R[r] * R[r];
+            nn = sqrt(warp_sum(nn));
+            for (int r = lane; r < n; r += 32) R[r] /= nn;
+        }
+        __syncthreads();
     }
-    for (int r = lane; r < n; r += 32) y[r] = R[r];
-    __syncwarp();
+    for (int r = tid; r < n; r += blockDim.x) y[r] = R[r];
+    __syncthreads();
     const double zs = 1.0 / sqrt((double)n);
-    for (int idx = lane; idx < n * n; idx += 32) {
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
         const int r = idx / n, c = idx % n;
-        A[idx] = Bg[idx] + zs * y[c];
+        A[r * LDP + c] = Bg[idx] + zs * y[c];
         R[idx] = (r == c ? 1.0 : 0.0) - 1.0 / (double)n;
     }
-    __syncwarp();
-    lu_factor(A, n, perm, 1e-300);
-    lu_solve(A, n, perm, R, n);
+    __syncthreads();
+    blu_factor(A, n, perm, 1e-300);
+    blu_solve(A, n, perm, R, n);
     int bad = 0;
-    for (int idx = lane; idx < n * n; idx += 32) {
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
         const double v = R[idx];
         if (!(fabs(v) < INFINITY)) bad = 1;
         Pg[idx] = v;
     }
-    bad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) info[0] = bad;
+    bad = __syncthreads_or(bad);
+    if (tid == 0) info[0] = bad;
 }
 
 int coarse_pinv(int n, const double* dB, double* dP, cudaStream_t s) {
     BAMG_REQUIRE(n >= 1 && n <= CN, BAMG_EINVAL, "coarse_pinv: coarsest order must be 1..64");
     static bool attr = false;
-    const size_t smem = 2 * CN * CN * sizeof(double);
+    const size_t smem = 2 * CN * LDP * sizeof(double);
     if (!attr) {
         BAMG_CK(cudaFuncSetAttribute(k_coarse_pinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
     TmpBuf<int> info(1, s);
-    BAMG_LAUNCH(k_coarse_pinv, 1, 32, smem, s, n, dB, dP, info.get());
+    BAMG_LAUNCH(k_coarse_pinv, 1, CT, smem, s, n, dB, dP, info.get());
     int h = 0;
     BAMG_CK(cudaMemcpyAsync(&h, info.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     BAMG_CK(cudaStreamSynchronize(s));

@@ -76,7 +76,7 @@ void launch_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* 
 // gathering the matching chunk of each neighbour's test-vector row (contiguous in the
 // row-interleaved layout), so the W columns share every matrix load.
 template <typename T, bool SHIFT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     k_jacobi(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
              const T* __restrict__ tv, const T* __restrict__ dB, const T* __restrict__ dinvB, const T* __restrict__ dT,
              const double* __restrict__ lam, int ncols, const T* __restrict__ X, T* __restrict__ Y, int ld, int col0,
@@ -91,17 +91,34 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int e = 0; e < W; ++e) acc[e] = accT[e] = T(0);
     const int p0 = rp[row], p1 = rp[row + 1];
-    for (int p = p0; p < p1; ++p) {
-        const int j = __ldg(ci + p);
-        T xv[W];
-        V16<T>::load(X + (int64_t)j * ld + off, xv);
-        const T b = __ldg(bv + p);
+    // batches of up to JB entries: indices and values first, then the predicated
+    // gathers, so each thread has up to JB independent loads in flight
+    constexpr int JB = 6;
+    for (int base = p0; base < p1; base += JB) {
+        const int cnt = min(JB, p1 - base);
+        int jj[JB];
+        T bb[JB], tt[JB], xv[JB][W];
 #pragma unroll
-        for (int e = 0; e < W; ++e) acc[e] += b * xv[e];
-        if (SHIFT && tv != nullptr) {
-            const T tt = __ldg(tv + p);
+        for (int u = 0; u < JB; ++u) {
+            if (u < cnt) {
+                jj[u] = __ldg(ci + base + u);
+                bb[u] = __ldg(bv + base + u);
+                tt[u] = (SHIFT && tv != nullptr) ? __ldg(tv + base + u) : T(0);
+            }
+        }
 #pragma unroll
-            for (int e = 0; e < W; ++e) accT[e] += tt * xv[e];
+        for (int u = 0; u < JB; ++u)
+            if (u < cnt) V16<T>::load(X + (int64_t)jj[u] * ld + off, xv[u]);
+#pragma unroll
+        for (int u = 0; u < JB; ++u) {
+            if (u < cnt) {
+#pragma unroll
+                for (int e = 0; e < W; ++e) acc[e] += bb[u] * xv[u][e];
+                if (SHIFT && tv != nullptr) {
+#pragma unroll
+                    for (int e = 0; e < W; ++e) accT[e] += tt[u] * xv[u][e];
+                }
+            }
         }
     }
     T xs[W], y[W];

@@ -144,7 +144,7 @@ void spmv_f64_from_f32(const MatView<double>& B, const float* x, double* y, cuda
     BAMG_LAUNCH(k_spmv64<float>, blocks_for(B.n, 256), 256, 0, s, B.n, B.rp, B.ci, B.v, x, y, 1.0);
 }
 
-constexpr int DOT_ROWS = 2048;
+constexpr int DOT_ROWS = 512;
 int dots_partial_blocks(int n) { return (int)blocks_for(n, DOT_ROWS); }
 
 __global__ void __launch_bounds__(256) k_dots_partial(int n, const double* __restrict__ V, int64_t ldv, int nv,
@@ -158,25 +158,30 @@ __global__ void __launch_bounds__(256) k_dots_partial(int n, const double* __res
     for (int q = wid; q < nv; q += nw) {
         const double* vq = V + (int64_t)q * ldv + r0;
         double acc = 0.0;
+#pragma unroll 4
         for (int e = lane; e < cnt; e += 32) acc += vq[e] * sw[e];
         acc = warp_sum(acc);
         if (lane == 0) partial[(int64_t)blockIdx.x * nv + q] = acc;
     }
 }
 
+// One warp per column: lanes take the block partials in a fixed stride, then a fixed
+// butterfly; the order depends only on nb, so the result is deterministic.
 __global__ void k_reduce_cols(int nb, int nv, const double* __restrict__ partial, double* __restrict__ h) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (q >= nv) return;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * nv + q];
-    h[q] = s;
+    for (int b = lane; b < nb; b += 32) s += partial[(int64_t)b * nv + q];
+    s = warp_sum(s);
+    if (lane == 0) h[q] = s;
 }
 
 void dots(int n, const double* V, int64_t ldv, int nv, const double* w, double* d_h, double* d_partial,
           cudaStream_t s) {
     const int nb = dots_partial_blocks(n);
     BAMG_LAUNCH(k_dots_partial, nb, 256, 0, s, n, V, ldv, nv, w, d_partial);
-    BAMG_LAUNCH(k_reduce_cols, blocks_for(nv, 64), 64, 0, s, nb, nv, d_partial, d_h);
+    BAMG_LAUNCH(k_reduce_cols, blocks_for(nv, 4), 128, 0, s, nb, nv, d_partial, d_h);
 }
 
 __global__ void k_update_minus(int n, const double* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ h,
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(256) k_resnorm_partial(int n, const int32_t* _
 void residual_norms(const MatView<double>& B, const double* x, double* d_out, double* d_partial, cudaStream_t s) {
     const int nb = (int)blocks_for(B.n, 256);
     BAMG_LAUNCH(k_resnorm_partial, nb, 256, 0, s, B.n, B.rp, B.ci, B.v, x, d_partial);
-    BAMG_LAUNCH(k_reduce_cols, 1, 64, 0, s, nb, 4, d_partial, d_out);
+    BAMG_LAUNCH(k_reduce_cols, 1, 128, 0, s, nb, 4, d_partial, d_out);
 }
 
 // y = x * num or x / num with num = d_num[num_idx] (a device scalar).
@@ -319,6 +324,150 @@ __global__ void k_solve_y(double* __restrict__ st, int j, int m) {
     }
 }
 void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s) { BAMG_LAUNCH(k_solve_y, 1, 32, 0, s, d_state, j, m); }
+
+
+// ---------------------------------------------------------------- graph-replayable Arnoldi step
+// The kernels below read the Arnoldi index j from device memory (*dj), so one captured
+// graph serves every iteration of a cycle: v_j -> V-cycle input, z_j <- V-cycle output,
+// w = V[j+1] = B z_j, two classical Gram-Schmidt passes, ||w||, the Givens update,
+// v_{j+1} = w / ||w||, and j <- j + 1.
+template <typename T>
+__global__ void k_v_to_in(int n, const double* __restrict__ V, const int* __restrict__ dj, T* __restrict__ vin) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) vin[i] = (T)V[(int64_t)(*dj) * n + i];
+}
+template <typename T>
+__global__ void k_z_store(int n, const T* __restrict__ z, const int* __restrict__ dj, T* __restrict__ Z) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) Z[(int64_t)(*dj) * n + i] = z[i];
+}
+template <typename TX>
+__global__ void k_spmv64_j(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ bv, const TX* __restrict__ x, const int* __restrict__ dj,
+                           double* __restrict__ V) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) s += bv[p] * (double)x[ci[p]];
+    V[(int64_t)(*dj + 1) * n + i] = s;
+}
+// self = 0: dots of w = V[j+1] with V[0..j];  self = 1: w . w
+__global__ void __launch_bounds__(256) k_dots_partial_j(int n, const double* __restrict__ V,
+                                                        const int* __restrict__ dj, int self,
+                                                        double* __restrict__ partial, int stride) {
+    __shared__ double sw[DOT_ROWS];
+    const int j = *dj;
+    const double* w = V + (int64_t)(j + 1) * n;
+    const int nv = self ? 1 : j + 1;
+    const int r0 = blockIdx.x * DOT_ROWS;
+    const int cnt = min(DOT_ROWS, n - r0);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sw[e] = w[r0 + e];
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = wid; q < nv; q += nw) {
+        const double* vq = (self ? w : V + (int64_t)q * n) + r0;
+        double acc = 0.0;
+#pragma unroll 4
+        for (int e = lane; e < cnt; e += 32) acc += vq[e] * sw[e];
+        acc = warp_sum(acc);
+        if (lane == 0) partial[(int64_t)blockIdx.x * stride + q] = acc;
+    }
+}
+__global__ void k_reduce_cols_j(int nb, const int* __restrict__ dj, int self, int stride,
+                                const double* __restrict__ partial, double* __restrict__ h) {
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int nv = self ? 1 : *dj + 1;
+    if (q >= nv) return;
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += partial[(int64_t)b * stride + q];
+    s = warp_sum(s);
+    if (lane == 0) h[q] = s;
+}
+__global__ void k_update_minus_j(int n, double* __restrict__ V, const int* __restrict__ dj,
+                                 const double* __restrict__ h) {
+    __shared__ double sh[GMRES_MMAX + 1];
+    const int j = *dj;
+    for (int q = threadIdx.x; q <= j; q += blockDim.x) sh[q] = h[q];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double* w = V + (int64_t)(j + 1) * n;
+    double s = w[i];
+    for (int q = 0; q <= j; ++q) s -= V[(int64_t)q * n + i] * sh[q];
+    w[i] = s;
+}
+__global__ void k_givens_j(double* __restrict__ st, const int* __restrict__ dj, int m) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = *dj;
+    GmresLayout L(m);
+    double col[GMRES_MMAX + 1];
+    for (int i = 0; i <= j; ++i) col[i] = st[L.h1 + i] + st[L.h2 + i];
+    const double hn = sqrt(st[L.nrm2]);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double c = st[L.cs + i], s = st[L.sn + i];
+        const double a = col[i], b = col[i + 1];
+        col[i] = c * a + s * b;
+        col[i + 1] = -s * a + c * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double den = hypot(a, b);
+    const double c = den == 0.0 ? 1.0 : a / den, s = den == 0.0 ? 0.0 : b / den;
+    st[L.cs + j] = c;
+    st[L.sn + j] = s;
+    col[j] = c * a + s * b;
+    const double gj = st[L.g + j];
+    st[L.g + j + 1] = -s * gj;
+    st[L.g + j] = c * gj;
+    for (int i = 0; i <= j; ++i) st[L.R + i + (int64_t)j * m] = col[i];
+    st[L.est] = fabs(st[L.g + j + 1]);
+    st[L.hn] = hn;
+}
+__global__ void k_scale_j(int n, double* __restrict__ V, const int* __restrict__ dj, const double* __restrict__ st,
+                          int hn_idx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = st[hn_idx];
+    double* w = V + (int64_t)(*dj + 1) * n;
+    w[i] = a != 0.0 ? w[i] / a : 0.0;
+}
+__global__ void k_inc_j(int* dj) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dj += 1;
+}
+
+template <typename T>
+void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T* vin, T* zout, int* dj,
+                            double* st, int m, double* partial, const std::vector<VLevel<T>>& lv, const T* pinv,
+                            double omega, int nu_pre, int nu_post, double* h_est, cudaStream_t s) {
+    GmresLayout L(m);
+    const unsigned g = blocks_for(n, 256);
+    const int nb = dots_partial_blocks(n);
+    const int stride = m + 1;
+    BAMG_LAUNCH(k_v_to_in<T>, g, 256, 0, s, n, V, dj, vin);
+    vcycle<T>(lv, pinv, omega, nu_pre, nu_post, s);
+    BAMG_LAUNCH(k_z_store<T>, g, 256, 0, s, n, zout, dj, Z);
+    BAMG_LAUNCH(k_spmv64_j<T>, g, 256, 0, s, n, B.rp, B.ci, B.v, zout, dj, V);
+    for (int pass = 0; pass < 2; ++pass) {
+        double* h = st + (pass == 0 ? L.h1 : L.h2);
+        BAMG_LAUNCH(k_dots_partial_j, nb, 256, 0, s, n, V, dj, 0, partial, stride);
+        BAMG_LAUNCH(k_reduce_cols_j, blocks_for(m + 1, 4), 128, 0, s, nb, dj, 0, stride, partial, h);
+        BAMG_LAUNCH(k_update_minus_j, g, 256, 0, s, n, V, dj, h);
+    }
+    BAMG_LAUNCH(k_dots_partial_j, nb, 256, 0, s, n, V, dj, 1, partial, stride);
+    BAMG_LAUNCH(k_reduce_cols_j, 1, 128, 0, s, nb, dj, 1, stride, partial, st + L.nrm2);
+    BAMG_LAUNCH(k_givens_j, 1, 32, 0, s, st, dj, m);
+    BAMG_LAUNCH(k_scale_j, g, 256, 0, s, n, V, dj, st, L.hn);
+    BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BAMG_LAUNCH(k_inc_j, 1, 32, 0, s, dj);
+}
+
+template void arnoldi_step_graphable<float>(int, const MatView<double>&, double*, float*, float*, float*, int*,
+                                            double*, int, double*, const std::vector<VLevel<float>>&, const float*,
+                                            double, int, int, double*, cudaStream_t);
+template void arnoldi_step_graphable<double>(int, const MatView<double>&, double*, double*, double*, double*, int*,
+                                             double*, int, double*, const std::vector<VLevel<double>>&,
+                                             const double*, double, int, int, double*, cudaStream_t);
 
 template void vcycle<float>(const std::vector<VLevel<float>>&, const float*, double, int, int, cudaStream_t);
 template void vcycle<double>(const std::vector<VLevel<double>>&, const double*, double, int, int, cudaStream_t);

@@ -128,6 +128,13 @@ void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const dou
 void residual_norms(const MatView<double>& B, const double* x, double* d_out, double* d_partial, cudaStream_t s);
 void scale_vec(int n, double* x, const double* d_num, int num_idx, bool reciprocal, double* y, cudaStream_t s);
 void gmres_init(double* d_state, int m, cudaStream_t s);
+// One Arnoldi step of flexible GMRES whose index j lives in device memory (*dj), so the
+// whole sequence can be captured once in a CUDA graph and replayed.  h_est (pinned host
+// memory) receives {residual estimate, h_{j+1,j}}.
+template <typename T>
+void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T* vin, T* zout, int* dj, double* st,
+                            int m, double* partial, const std::vector<VLevel<T>>& lv, const T* pinv, double omega,
+                            int nu_pre, int nu_post, double* h_est, cudaStream_t s);
 void gmres_arnoldi_step(double* d_state, int j, int m, cudaStream_t s);
 void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s);
 

@@ -16,8 +16,19 @@ namespace bamg {
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
 static thread_local std::string g_err;
 void set_last_error(const std::string& m) { g_err = m; }
+cudaStream_t& alloc_stream() {
+    static thread_local cudaStream_t st = nullptr;
+    return st;
+}
+// Sets the allocation stream for the lifetime of the object.
+struct AllocStream {
+    cudaStream_t prev;
+    explicit AllocStream(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
+    ~AllocStream() { alloc_stream() = prev; }
+};
 
 static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
@@ -87,10 +98,24 @@ struct Solver : SolverBase {
     // Krylov workspace
     int m = 0;
     DevBuf<double> V, state, partial, x0, xw, rn;
-    DevBuf<T> Z, vin;
+    DevBuf<T> Z, vin, zout;
+    DevBuf<int> dj;
     double* h_pin = nullptr;
+    // one Arnoldi step captured as a CUDA graph, replayed on a private stream
+    cudaStream_t ps = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_kernels = 0;
 
     ~Solver() override {
+        cudaStreamSynchronize(s);
+        if (ps) cudaStreamSynchronize(ps);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (ps) cudaStreamDestroy(ps);
         if (h_pin) cudaFreeHost(h_pin);
     }
     int nlevels() const override { return (int)lv.size(); }
@@ -185,6 +210,7 @@ struct Solver : SolverBase {
     // --------------------------------------------------------------- setup
     void setup(const bamg_csr* A, int r_, int levels) {
         auto t0 = std::chrono::steady_clock::now();
+        AllocStream as_(s);
         const int n = A->n;
         r = r_;
         // inputs on the device
@@ -331,6 +357,7 @@ struct Solver : SolverBase {
 
     // --------------------------------------------------------------- import
     void import(int nlev, const bamg_level_in* in, const double* h_pinv, const double* h_x_init) {
+        AllocStream as_(s);
         lv.clear();
         for (int l = 0; l < nlev; ++l) {
             auto L = std::make_unique<LevelT<T>>();
@@ -390,6 +417,7 @@ struct Solver : SolverBase {
 
     // --------------------------------------------------------------- V-cycle
     void vcycle_apply(const double* v, double* z) override {
+        AllocStream as_(s);
         const int n = lv[0]->n;
         if constexpr (std::is_same<T, double>::value) {
             auto vl = vlevels(v, z);
@@ -415,8 +443,27 @@ struct Solver : SolverBase {
         BAMG_CK(cudaStreamSynchronize(s));
     }
 
+    void capture_step(int n) {
+        std::vector<VLevel<T>> vl = vlevels(vin.get(), zout.get());
+        const uint64_t c0 = bamg_launch_count();
+        BAMG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            arnoldi_step_graphable<T>(n, B64(), V.get(), Z.get(), vin.get(), zout.get(), dj.get(), state.get(), m,
+                                      partial.get(), vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, h_pin, s);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        BAMG_CK(cudaStreamEndCapture(s, &graph));
+        graph_kernels = (int64_t)(bamg_launch_count() - c0);
+        count_launches(-graph_kernels);  // counted again at every replay
+        BAMG_CK(cudaGraphInstantiate(&gexec, graph, 0));
+    }
+
     void solve(double* x_user, int flags, double tol, bamg_stats* st) override {
-        auto t0 = std::chrono::steady_clock::now();
+        AllocStream as_(s);
         const int n = lv[0]->n;
         m = std::min(std::max(o.gmres_m, 1), GMRES_MMAX);
         GmresLayout GL(m);
@@ -429,7 +476,36 @@ struct Solver : SolverBase {
         xw.ensure(n);
         rn.ensure(8);
         vin.ensure(n);
+        zout.ensure(n);
+        dj.ensure(1);
         if (!h_pin) BAMG_CK(cudaMallocHost(&h_pin, 16 * sizeof(double)));
+        if (!ps) {
+            BAMG_CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+            BAMG_CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+            BAMG_CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+        }
+        // all work of the solve runs on the private stream, fenced against the caller's
+        cudaStream_t su = s;
+        BAMG_CK(cudaEventRecord(ev_in, su));
+        BAMG_CK(cudaStreamWaitEvent(ps, ev_in, 0));
+        s = ps;
+        try {
+            solve_on_private_stream(x_user, flags, tol, st);
+        } catch (...) {
+            cudaEventRecord(ev_out, ps);
+            cudaStreamWaitEvent(su, ev_out, 0);
+            s = su;
+            throw;
+        }
+        BAMG_CK(cudaEventRecord(ev_out, ps));
+        BAMG_CK(cudaStreamWaitEvent(su, ev_out, 0));
+        s = su;
+    }
+
+    void solve_on_private_stream(double* x_user, int flags, double tol, bamg_stats* st) {
+        auto t0 = std::chrono::steady_clock::now();
+        const int n = lv[0]->n;
+        GmresLayout GL(m);
         const MatView<double> B = B64();
         if (flags & BAMG_X_GUESS) {
             BAMG_CK(cudaMemcpyAsync(x0.get(), x_user, sizeof(double) * n,
@@ -437,6 +513,7 @@ struct Solver : SolverBase {
         } else {
             BAMG_CK(cudaMemcpyAsync(x0.get(), x_init.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         }
+        if (!gexec) capture_step(n);
         int it = 0, restarts = 0, checks = 0, status = BAMG_ENOCONV;
         residual_norms(B, x0.get(), rn.get(), partial.get(), s);
         read_n(rn.get(), 4);
@@ -451,31 +528,12 @@ struct Solver : SolverBase {
             dots(n, V0, n, 1, V0, state.get() + GL.nrm2, partial.get(), s);
             gmres_init(state.get(), m, s);
             scale_vec(n, V0, state.get(), GL.hn, true, V0, s);
-            int jlast = -1;
+            BAMG_CK(cudaMemsetAsync(dj.get(), 0, sizeof(int), s));
             for (int j = 0; j < m && it < o.max_it; ++j) {
-                double* vj = V.get() + (size_t)j * n;
-                double* w = V.get() + (size_t)(j + 1) * n;
-                T* zj = Z.get() + (size_t)j * n;
-                if constexpr (std::is_same<T, double>::value) {
-                    auto vl = vlevels(vj, zj);
-                    vcycle<T>(vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, s);
-                    spmv_f64(B, zj, w, 1.0, s);
-                } else {
-                    launch_convert<double, float>(n, vj, vin.get(), s);
-                    auto vl = vlevels(vin.get(), zj);
-                    vcycle<T>(vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, s);
-                    spmv_f64_from_f32(B, zj, w, s);
-                }
-                dots(n, V.get(), n, j + 1, w, state.get() + GL.h1, partial.get(), s);
-                update_minus(n, V.get(), n, j + 1, state.get() + GL.h1, w, s);
-                dots(n, V.get(), n, j + 1, w, state.get() + GL.h2, partial.get(), s);
-                update_minus(n, V.get(), n, j + 1, state.get() + GL.h2, w, s);
-                dots(n, w, n, 1, w, state.get() + GL.nrm2, partial.get(), s);
-                gmres_arnoldi_step(state.get(), j, m, s);
-                scale_vec(n, w, state.get(), GL.hn, true, w, s);
+                BAMG_CK(cudaGraphLaunch(gexec, s));
+                count_launches(graph_kernels);
+                BAMG_CK(cudaStreamSynchronize(s));
                 ++it;
-                jlast = j;
-                read_n(state.get() + GL.est, 2);
                 const double est = h_pin[0], hn = h_pin[1];
                 const bool last = (j == m - 1) || it >= o.max_it || hn == 0.0;
                 if (est * kappa <= tol * x1 || last) {
@@ -498,10 +556,8 @@ struct Solver : SolverBase {
                     if (last) break;
                 }
             }
-            (void)jlast;
             if (status == BAMG_OK) break;
-            // restart from the last iterate
-            if (have_xw) {
+            if (have_xw) {  // restart from the last iterate
                 BAMG_CK(cudaMemcpyAsync(x0.get(), xw.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
                 x1 = last_x1;
             }
