@@ -204,6 +204,21 @@ int bamg_relax(int dtype, const bamg_mat* B, const void* T_val, const double* d_
 int bamg_tv_weights(int dtype, const bamg_mat* B, int ncols, int ld, int col0, const uint8_t* d_active,
                     double floor, void* X, double* d_w, void* stream);
 
+/* Same sweeps as bamg_relax, but the call allocates nothing: no paper counterpart;
+ * it exists for callers that cannot let a library allocate device memory (a service
+ * that reserves its whole device budget at start-up, a framework whose allocator owns
+ * the device, a latency-critical loop where cudaMalloc/cudaFree would block).  The
+ * second copy of the vector block and the diagonals live in one 8 MiB device array
+ * compiled into the library, held by every device that loads it until the process
+ * exits.  Requires n * (ld + 3) * sizeof(element) <= 8 MiB (each part rounded up to 256
+ * bytes); larger problems return BAMG_EINVAL.  The first call on a device looks up the
+ * array's device address with that device current (make that first call before any
+ * stream capture).  All calls share the array and nothing in it needs to start at zero;
+ * calls that overlap on the GPU, from any stream or thread, race on it.  Arguments and
+ * results as for bamg_relax; returns after the work has completed on `stream`. */
+int bamg_relax_noalloc(int dtype, const bamg_mat* B, const void* T_val, const double* d_lambda, int ncols, int ld,
+                       int col0, double omega, int nu, void* X, void* stream);
+
 /* Full coarsening (Section 5.1): cf[i] = 1 on states with even ix and even iy;
  * cidx[i] = (ix/2) + (iy/2) * ((nx+1)/2) on coarse states, -1 on fine states. */
 int bamg_coarsen_grid(int nx, int ny, uint8_t* cf, int32_t* cidx, void* stream);

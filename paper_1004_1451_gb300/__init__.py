@@ -14,7 +14,7 @@ import torch
 from . import _capi as capi
 from ._capi import BamgError  # noqa: F401
 
-__all__ = ["Solver", "import_hierarchy", "tv_init", "relax", "tv_weights", "coarsen_grid", "coarsen_cr",
+__all__ = ["Solver", "import_hierarchy", "tv_init", "relax", "relax_noalloc", "tv_weights", "coarsen_grid", "coarsen_cr",
            "interp_ls", "galerkin", "coarse_eig", "launch_count", "default_opts", "BamgError"]
 
 
@@ -222,6 +222,16 @@ def relax(B, X: torch.Tensor, ncols: int, col0: int, omega: float, nu: int, T_va
     m = _mat(*B)
     capi.check(_lib().bamg_relax(_dtype_code(X), C.byref(m), _p(T_val), _p(lam), ncols, ld, col0, omega, nu, _p(X),
                                  _p(work), _stream()))
+    return X
+
+
+def relax_noalloc(B, X: torch.Tensor, ncols: int, col0: int, omega: float, nu: int, T_val=None, lam=None):
+    """bamg_relax_noalloc: the sweeps of relax() with the library's fixed device scratch
+    instead of any allocation (see include/bamg.h for its size limit)."""
+    n, ld = X.shape
+    m = _mat(*B)
+    capi.check(_lib().bamg_relax_noalloc(_dtype_code(X), C.byref(m), _p(T_val), _p(lam), ncols, ld, col0, omega, nu,
+                                         _p(X), _stream()))
     return X
 
 

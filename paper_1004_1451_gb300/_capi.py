@@ -72,6 +72,7 @@ SIGNATURES = {
     "bamg_vcycle_apply": (_I, [_P, _P, _P]),
     "bamg_tv_init": (_I, [_I, _I, _I, _I, _I, C.c_uint64, _D, _D, _P, _P]),
     "bamg_relax": (_I, [_I, C.POINTER(Mat), _P, _P, _I, _I, _I, _D, _I, _P, _P, _P]),
+    "bamg_relax_noalloc": (_I, [_I, C.POINTER(Mat), _P, _P, _I, _I, _I, _D, _I, _P, _P]),
     "bamg_tv_weights": (_I, [_I, C.POINTER(Mat), _I, _I, _I, _P, _D, _P, _P, _P]),
     "bamg_coarsen_grid": (_I, [_I, _I, _P, _P, _P]),
     "bamg_coarsen_cr": (_I, [C.POINTER(Mat), _I, C.c_uint64, _D, _I, _D, _I, _P, _P, C.POINTER(_I), C.POINTER(_I),
