@@ -258,7 +258,23 @@ def neighborhoods(B, cf: np.ndarray, cidx: np.ndarray, z: int, mmax: int):
     where G has an edge (i, j) for every off-diagonal entry b_ij (row i, column j).
 
     R24: the candidates of a point are ordered by (path length, coarse index) and at most
-    mmax are kept.  Returns cand (n x mmax, fine indices, -1 padded) and the count."""
+    mmax are kept.  R30: a fine point that reaches no coarse point within z takes those
+    within the smallest length <= 3 (the bound of Eq. (3.5)) that reaches one, so that
+    its column of Q is not empty and 1^T Q = 1^T holds.  Returns cand (n x mmax, fine
+    indices, -1 padded) and the count."""
+    cand, ncand = _neighborhoods_depth(B, cf, cidx, z, mmax)
+    for d in range(z + 1, 4):
+        miss = (~cf) & (ncand == 0)
+        if not miss.any():
+            break
+        cd, nd = _neighborhoods_depth(B, cf, cidx, d, mmax)
+        cand[miss] = cd[miss]
+        ncand[miss] = nd[miss]
+    return cand, ncand
+
+
+def _neighborhoods_depth(B, cf: np.ndarray, cidx: np.ndarray, z: int, mmax: int):
+    """Coarse points within path length z, ordered by (length, coarse index), at most mmax."""
     n = B.shape[0]
     G = sp.csr_matrix(B, copy=True)
     G.data[:] = 1.0

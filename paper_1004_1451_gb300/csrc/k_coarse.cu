@@ -106,62 +106,6 @@ __device__ void blu_solve(const double* A, int n, const int* perm, double* R, in
 }
 
 // ---------------------------------------------------------------- FP32 Hessenberg + QR
-__device__ void hessenberg_f32(float* H, int n, float* v, float* dv, int* flag) {
-    const int tid = threadIdx.x;
-    for (int k = 0; k + 2 < n; ++k) {
-        if (tid < 32) {
-            float ss = 0.f;
-            for (int r = k + 1 + tid; r < n; r += 32) ss += H[r * LDP + k] * H[r * LDP + k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-            const float x0 = H[(k + 1) * LDP + k];
-            const float tail = ss - x0 * x0;
-            if (tid == 0) {
-                if (!(tail > 0.f)) {
-                    flag[0] = 1;
-                } else {
-                    const float alpha = -copysignf(sqrtf(ss), x0);
-                    const float v0 = x0 - alpha;
-                    flag[0] = 0;
-                    dv[CN] = 2.f / (tail + v0 * v0);  // beta
-                    dv[CN + 1] = alpha;
-                    v[k + 1] = v0;
-                }
-            }
-            for (int r = k + 2 + tid; r < n; r += 32) v[r] = H[r * LDP + k];
-        }
-        __syncthreads();
-        const int skip = flag[0];
-        const float beta = dv[CN];
-        __syncthreads();  // every thread has read flag and beta before warp 0 rewrites them
-        if (skip) continue;
-        for (int c = k + tid; c < n; c += blockDim.x) {
-            float d = 0.f;
-            for (int r = k + 1; r < n; ++r) d += v[r] * H[r * LDP + c];
-            dv[c] = beta * d;
-        }
-        __syncthreads();
-        for (int idx = tid; idx < (n - k - 1) * (n - k); idx += blockDim.x) {
-            const int r = k + 1 + idx / (n - k), c = k + idx % (n - k);
-            H[r * LDP + c] -= dv[c] * v[r];
-        }
-        __syncthreads();
-        for (int r = tid; r < n; r += blockDim.x) {
-            float d = 0.f;
-            for (int c = k + 1; c < n; ++c) d += H[r * LDP + c] * v[c];
-            dv[r] = beta * d;
-        }
-        __syncthreads();
-        for (int idx = tid; idx < n * (n - k - 1); idx += blockDim.x) {
-            const int r = idx / (n - k - 1), c = k + 1 + idx % (n - k - 1);
-            H[r * LDP + c] -= dv[r] * v[c];
-        }
-        __syncthreads();
-        if (tid == 0) H[(k + 1) * LDP + k] = dv[CN + 1];
-        for (int r = k + 2 + tid; r < n; r += blockDim.x) H[r * LDP + k] = 0.f;
-        __syncthreads();
-    }
-}
 
 __device__ __forceinline__ void house3f(float x, float y, float z, float& v0, float& v1, float& v2, float& beta) {
     const float nrm = sqrtf(x * x + y * y + z * z);
@@ -343,69 +287,145 @@ __device__ void blu_factor_f32(float* A, int n, int* perm) {
     }
 }
 
-__device__ void blu_solve_f32(const float* A, int n, const int* perm, float* R, int m, int ldr) {
-    const int tid = threadIdx.x;
-    for (int k = 0; k < n; ++k) {
-        const int pk = perm[k];
-        if (pk != k) {
-            for (int c = tid; c < m; c += blockDim.x) {
-                const float t = R[k * ldr + c];
-                R[k * ldr + c] = R[pk * ldr + c];
-                R[pk * ldr + c] = t;
-            }
-            __syncthreads();
-        }
-    }
-    for (int q = 0; q < n; ++q) {
-        for (int idx = tid; idx < (n - q - 1) * m; idx += blockDim.x) {
-            const int r = q + 1 + idx / m, c = idx % m;
-            R[r * ldr + c] -= A[r * LDP + q] * R[q * ldr + c];
-        }
-        __syncthreads();
-    }
-    for (int q = n - 1; q >= 0; --q) {
-        const float d = 1.f / A[q * LDP + q];
-        for (int c = tid; c < m; c += blockDim.x) R[q * ldr + c] *= d;
-        __syncthreads();
-        for (int idx = tid; idx < q * m; idx += blockDim.x) {
-            const int r = idx / m, c = idx % m;
-            R[r * ldr + c] -= A[r * LDP + q] * R[q * ldr + c];
-        }
-        __syncthreads();
-    }
-}
 
-// Kernel 1: eigenvalues of T^{-1} B in FP32 (they serve only as shifts) and the
-// selection: eigenvalues with Im >= 0 (a complex pair is represented by its member
-// with positive imaginary part) in order of |lambda|; a real one takes one vector
-// column, a pair two (Re v, Im v), until k_ev columns are filled.
-// sel[3q + {0,1,2}] = (Re, Im, first column); info = {columns, selected, status}.
+// Kernel 1: estimates of the eigenvalues of B x = lambda T x closest to zero, in FP32
+// (they serve only as shifts): shift-and-invert Arnoldi on K = (B - sigma T)^{-1} T with
+// sigma = -1e-4 max|B| (K's dominant eigenvalues theta = 1/(lambda - sigma) belong to
+// the lambda of smallest modulus), KRY steps with classical Gram-Schmidt applied twice,
+// the eigenvalues of the small Hessenberg matrix by the Francis QR iteration, then
+// lambda = sigma + 1/theta.  Selection: eigenvalues with Im >= 0 (a complex pair is
+// represented by its member with positive imaginary part) in order of |lambda|; a real
+// one takes one vector column, a pair two (Re v, Im v), until k_ev columns are filled.
+// sel[3q + {0,1,2}] = (Re, Im, first column); info = {columns, selected, status, steps}.
+constexpr int KRY = 32;
 __global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __restrict__ Bg,
                                                        const double* __restrict__ Tg, int k_ev,
                                                        double* __restrict__ sel, double* __restrict__ lam,
                                                        int32_t* __restrict__ kind, int* __restrict__ info) {
     __shared__ float A[CN * LDP], Tm[CN * LDP];
+    __shared__ float Vk[(KRY + 1) * CN];
+    __shared__ float w[CN], hcol[KRY + 1];
     __shared__ int perm[CN];
-    __shared__ float v[CN], dv[CN + 2], wr[CN], wi[CN];
-    __shared__ int flag[1];
-    const int tid = threadIdx.x;
+    __shared__ float wr[CN], wi[CN], red[CT / 32];
+    const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+    // sigma from the largest entry of B
+    float mx = 0.f;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) mx = fmaxf(mx, fabsf((float)Bg[idx]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[wid] = mx;
+    __syncthreads();
+    mx = 0.f;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) mx = fmaxf(mx, red[q]);
+    const float sigma = -1e-4f * fmaxf(mx, 1e-30f);
     for (int idx = tid; idx < n * n; idx += blockDim.x) {
         const int r = idx / n, c = idx % n;
-        A[r * LDP + c] = (float)Bg[idx];
-        Tm[r * LDP + c] = (float)Tg[idx];
+        const float t = (float)Tg[idx];
+        Tm[r * LDP + c] = t;
+        A[r * LDP + c] = (float)Bg[idx] - sigma * t;
     }
     __syncthreads();
-    blu_factor_f32(Tm, n, perm);
-    blu_solve_f32(Tm, n, perm, A, n, LDP);
-    hessenberg_f32(A, n, v, dv, flag);
-    if (tid >= 32) return;
-    int steps = 0;
-    const int st = hqr_f32(A, n, wr, wi, &steps);
+    blu_factor_f32(A, n, perm);
+    const int kd = n < KRY ? n : KRY;
+    if (tid >= 32) return;  // the Arnoldi process runs in one warp
+    // v_0: fixed generic start, unit norm
+    {
+        float nn = 0.f;
+        for (int r = lane; r < n; r += 32) {
+            const float v = 1.f + (float)r / (float)n;
+            Vk[r] = v;
+            nn += v * v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        nn = rsqrtf(nn);
+        for (int r = lane; r < n; r += 32) Vk[r] *= nn;
+        __syncwarp();
+    }
+    __shared__ float Hs[KRY * KRY];
+    for (int idx = lane; idx < KRY * KRY; idx += 32) Hs[idx] = 0.f;
+    int kk = kd;
+    for (int k = 0; k < kd; ++k) {
+        const float* vk = Vk + k * CN;
+        // w = T v_k
+        for (int r = lane; r < n; r += 32) {
+            float sacc = 0.f;
+            for (int c = 0; c < n; ++c) sacc += Tm[r * LDP + c] * vk[c];
+            w[r] = sacc;
+        }
+        __syncwarp();
+        // w <- (B - sigma T)^{-1} w
+        for (int q = 0; q < n; ++q) {
+            const int pq = perm[q];
+            if (pq != q && lane == 0) {
+                const float t = w[q];
+                w[q] = w[pq];
+                w[pq] = t;
+            }
+            __syncwarp();
+        }
+        for (int q = 0; q < n; ++q) {
+            const float yq = w[q];
+            for (int r = q + 1 + lane; r < n; r += 32) w[r] -= A[r * LDP + q] * yq;
+            __syncwarp();
+        }
+        for (int q = n - 1; q >= 0; --q) {
+            if (lane == 0) w[q] /= A[q * LDP + q];
+            __syncwarp();
+            const float yq = w[q];
+            for (int r = lane; r < q; r += 32) w[r] -= A[r * LDP + q] * yq;
+            __syncwarp();
+        }
+        // classical Gram-Schmidt, twice
+        for (int q = 0; q <= k; ++q) hcol[q] = 0.f;
+        __syncwarp();
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int q = 0; q <= k; ++q) {
+                float d = 0.f;
+                for (int r = lane; r < n; r += 32) d += Vk[q * CN + r] * w[r];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                for (int r = lane; r < n; r += 32) w[r] -= d * Vk[q * CN + r];
+                if (lane == 0) hcol[q] += d;
+                __syncwarp();
+            }
+        }
+        float nn = 0.f;
+        for (int r = lane; r < n; r += 32) nn += w[r] * w[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        nn = sqrtf(nn);
+        for (int q = lane; q <= k; q += 32) Hs[q * KRY + k] = hcol[q];
+        if (k + 1 < kd && lane == 0) Hs[(k + 1) * KRY + k] = nn;
+        __syncwarp();
+        if (!(nn > 1e-6f * fabsf(hcol[0]) + 1e-30f)) {  // invariant subspace found
+            kk = k + 1;
+            break;
+        }
+        if (k + 1 < kd)
+            for (int r = lane; r < n; r += 32) Vk[(k + 1) * CN + r] = w[r] / nn;
+        __syncwarp();
+    }
+    // eigenvalues of the kk x kk Hessenberg matrix (stored with the padded row stride)
+    for (int idx = lane; idx < kk * kk; idx += 32) {
+        const int r = idx / kk, c = idx % kk;
+        Tm[r * LDP + c] = Hs[r * KRY + c];
+    }
     __syncwarp();
-    if (tid == 0) {
-        int order[CN];
+    int steps = 0;
+    const int st = hqr_f32(Tm, kk, wr, wi, &steps);
+    __syncwarp();
+    if (lane == 0) {
+        // lambda = sigma + 1 / theta
+        for (int q = 0; q < kk; ++q) {
+            const float tr = wr[q], ti = wi[q];
+            const float d = tr * tr + ti * ti;
+            wr[q] = d > 0.f ? sigma + tr / d : 3.0e38f;
+            wi[q] = d > 0.f ? -ti / d : 0.f;
+        }
+        int order[KRY];
         int m = 0;
-        for (int q = 0; q < n; ++q)
+        for (int q = 0; q < kk; ++q)
             if (wi[q] >= 0.f) order[m++] = q;
         for (int a = 1; a < m; ++a)
             for (int b = a; b > 0; --b) {

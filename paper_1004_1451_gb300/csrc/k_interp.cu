@@ -192,8 +192,9 @@ __device__ __forceinline__ bool chol_solve(T (&A)[CMAX][CMAX], const T (&b)[CMAX
 }
 
 // One warp per point.  Fine points: breadth-first search to depth z over the row
-// pattern of B (edges i -> j for b_ij != 0, i != j), candidates = coarse points found,
-// ranked by (depth, coarse index) and cut to mmax; then the greedy steps of
+// pattern of B (edges i -> j for b_ij != 0, i != j), continued up to depth 3 while no
+// coarse point has been found; candidates = coarse points found, ranked by (depth,
+// coarse index) and cut to mmax; then the greedy steps of
 // Algorithm 2 with one lane per candidate: each lane forms its (|J|+1)-square weighted
 // normal equations (plus the Tikhonov term), solves them by Cholesky and evaluates the
 // functional of Eq. (3.6) directly; the lane with the smallest value (lowest slot on
@@ -235,7 +236,15 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
     __syncwarp();
     int nvis = 1, fs = 0, fe = 1;
     bool ovf = false;
-    for (int d = 1; d <= z; ++d) {
+    for (int d = 1; d <= 3; ++d) {
+        if (d > z) {  // beyond z only while no coarse point has been reached
+            bool anyc = false;
+            for (int q0 = 1; q0 < nvis && !anyc; q0 += 32) {
+                const int q = q0 + lane;
+                anyc = __any_sync(0xffffffffu, q < nvis && cf[vis[q]] != 0);
+            }
+            if (anyc) break;
+        }
         for (int f = fs; f < fe; ++f) {
             const int u = vis[f];
             const int p0 = rp[u], p1 = rp[u + 1];
@@ -428,12 +437,17 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
 template <typename T>
 int interp_ls(int n, const int32_t* rp, const int32_t* ci, const uint8_t* cf, const int32_t* cidx, const T* X, int ncols,
               int ld, const double* d_w, int z, int mmax, int c, double ridge, int32_t* pcol, T* pval, int32_t* pcnt,
-              cudaStream_t s) {
+              cudaStream_t s, int* d_err) {
     BAMG_REQUIRE(ncols >= 1 && ncols <= KMAX, BAMG_EINVAL, "interp_ls: 1 <= ncols <= 32");
     BAMG_REQUIRE(c >= 1 && c <= CMAX, BAMG_EINVAL, "interp_ls: 1 <= caliber <= 4");
     BAMG_REQUIRE(mmax >= 1 && mmax <= MMAX, BAMG_EINVAL, "interp_ls: 1 <= mmax <= 16");
     BAMG_REQUIRE(z >= 1 && z <= 3, BAMG_EINVAL, "interp_ls: 1 <= z <= 3");
     if (n == 0) return 0;
+    if (d_err) {  // the caller reads the overflow flag later
+        BAMG_LAUNCH(k_ls_fit<T>, blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, cf, cidx, X, ncols, ld, d_w,
+                    z, mmax, c, ridge, pcol, pval, pcnt, d_err);
+        return 0;
+    }
     TmpBuf<int> err(1, s);
     BAMG_CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
     BAMG_LAUNCH(k_ls_fit<T>, blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, cf, cidx, X, ncols, ld, d_w, z,
@@ -490,7 +504,7 @@ void build_restriction(const EllView<T>& P, int nc, DevBuf<int32_t>& qrp, DevBuf
     BAMG_LAUNCH(k_q_count, blocks_for(P.n, 256), 256, 0, s, P.n, P.c, P.pcol, P.pcnt, cnt.get());
     qrp.alloc(nc + 1);
     exclusive_scan(cnt.get(), qrp.get(), nc, s);
-    const int nq = read_int(qrp.get() + nc, s);
+    const size_t nq = (size_t)P.n * P.c;  // bound: every row of P has at most c entries
     qci.alloc(nq > 0 ? nq : 1);
     qv.alloc(nq > 0 ? nq : 1);
     BAMG_LAUNCH(k_q_fill, blocks_for(P.n, 256), 256, 0, s, P.n, P.c, P.pcol, P.pcnt, qrp.get(), cursor.get(), qci.get());
@@ -660,9 +674,10 @@ void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int
     TmpBuf<int32_t> np(nc, s), poff(nc + 1, s);
     BAMG_LAUNCH(k_gal_count, blocks_for(nc, 128), 128, 0, s, nc, qrp, qci, B.rp, B.ci, P.pcnt, np.get());
     exclusive_scan(np.get(), poff.get(), nc, s);
-    const int total = read_int(poff.get() + nc, s);
-    BAMG_REQUIRE(total >= 0, BAMG_EINVAL, "galerkin: product count overflows int32");
-    const size_t tot = total > 0 ? (size_t)total : 1;
+    // bound on the product count: each entry b_ij meets at most c columns of Q and c rows of P
+    const size_t bound = (size_t)B.nnz * P.c * P.c;
+    BAMG_REQUIRE(bound < (size_t)INT32_MAX, BAMG_EINVAL, "galerkin: product count may overflow int32");
+    const size_t tot = bound > 0 ? bound : 1;
     TmpBuf<int32_t> pJ(tot, s), uJ(tot, s), ucnt(nc, s);
     TmpBuf<T> pvb(tot, s), pvt(tot, s), ubv(tot, s), utv(tot, s);
     TmpBuf<uint8_t> head(tot, s);
@@ -696,7 +711,8 @@ void csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const T* v, doubl
 
 #define INST(T)                                                                                                     \
     template int interp_ls<T>(int, const int32_t*, const int32_t*, const uint8_t*, const int32_t*, const T*, int,   \
-                              int, const double*, int, int, int, double, int32_t*, T*, int32_t*, cudaStream_t);     \
+                              int, const double*, int, int, int, double, int32_t*, T*, int32_t*, cudaStream_t,      \
+                              int*);                                                                                \
     template void build_restriction<T>(const EllView<T>&, int, DevBuf<int32_t>&, DevBuf<int32_t>&, DevBuf<T>&,      \
                                        cudaStream_t);                                                               \
     template void galerkin<T>(const MatView<T>&, const T*, const int32_t*, const int32_t*, const T*,                \

@@ -242,12 +242,15 @@ __global__ void k_colstats(int n, const int32_t* __restrict__ rp, const int32_t*
         for (int q = 0; q < 2 * W; ++q) partial[(int64_t)blockIdx.x * (nvec * 2 * W) + ch * 2 * W + q] = sh[base + q];
 }
 
+// one warp per output: lanes stride the block partials, then a fixed butterfly
 __global__ void k_reduce_partials(int nblocks, int width, const double* __restrict__ partial, double* __restrict__ out) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (q >= width) return;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * width + q];
-    out[q] = s;
+    for (int b = lane; b < nblocks; b += 32) s += partial[(int64_t)b * width + q];
+    s = warp_sum(s);
+    if (lane == 0) out[q] = s;
 }
 
 template <typename T, int MODE>
@@ -264,7 +267,7 @@ static void colstats(const MatView<T>& B, const T* T_val, const T* X, int ld, in
     size_t smem = (size_t)ny * nvec * 2 * W * sizeof(double);
     BAMG_LAUNCH((k_colstats<T, MODE>), nb, dim3(nvec, ny), smem, s, B.n, B.rp, B.ci, B.v, T_val, X, ld, col0, nvec,
                 partial.get());
-    BAMG_LAUNCH(k_reduce_partials, blocks_for(width, 64), 64, 0, s, nb, width, partial.get(), d_sums);
+    BAMG_LAUNCH(k_reduce_partials, blocks_for(width, 4), 128, 0, s, nb, width, partial.get(), d_sums);
 }
 
 // ---------------------------------------------------------------- LS weights

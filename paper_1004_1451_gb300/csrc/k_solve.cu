@@ -8,56 +8,97 @@
 
 namespace bamg {
 
-// ---------------------------------------------------------------- V-cycle kernels
+// ---------------------------------------------------------------- V-cycle
+// Per-row arithmetic shared by the grid kernels and the single-block coarse kernel, in
+// the order of the plain definition: x1 = (w d^{-1}) b; x_new = x + (w d^{-1}) (b - B x);
+// r = b - B x; b_c = Q r; x += P e_c.
+// sum_p bv[p] * f(ci[p]) over p0 <= p < p1, accumulated in order; groups of four
+// indices and gathers are issued before they are consumed so that each thread keeps
+// several loads in flight.
+template <typename T, typename F>
+__device__ __forceinline__ T row_sum(int p0, int p1, const int32_t* __restrict__ ci, const T* __restrict__ bv, F f) {
+    T s = T(0);
+    int p = p0;
+    for (; p + 4 <= p1; p += 4) {
+        const int j0 = ci[p], j1 = ci[p + 1], j2 = ci[p + 2], j3 = ci[p + 3];
+        const T b0 = bv[p], b1 = bv[p + 1], b2 = bv[p + 2], b3 = bv[p + 3];
+        const T x0 = f(j0), x1 = f(j1), x2 = f(j2), x3 = f(j3);
+        s += b0 * x0;
+        s += b1 * x1;
+        s += b2 * x2;
+        s += b3 * x3;
+    }
+    for (; p < p1; ++p) s += bv[p] * f(ci[p]);
+    return s;
+}
+template <typename T>
+__device__ __forceinline__ T row_Bx(int i, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                    const T* __restrict__ bv, const T* __restrict__ x) {
+    return row_sum<T>(rp[i], rp[i + 1], ci, bv, [&](int j) { return x[j]; });
+}
+// B x1 with x1 = (w d^{-1}) b formed on the fly (the first sweep from a zero guess)
+template <typename T>
+__device__ __forceinline__ T row_Bx1(int i, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const T* __restrict__ bv, const T* __restrict__ dinv, const T* __restrict__ b,
+                                     T omega) {
+    return row_sum<T>(rp[i], rp[i + 1], ci, bv, [&](int j) { return (omega * dinv[j]) * b[j]; });
+}
+template <typename T>
+__device__ __forceinline__ T row_prolonged(int j, int c, const int32_t* __restrict__ pcol, const T* __restrict__ pval,
+                                           const int32_t* __restrict__ pcnt, const T* __restrict__ ec,
+                                           const T* __restrict__ x) {
+    T s = T(0);
+    for (int t = 0; t < pcnt[j]; ++t) s += pval[(int64_t)j * c + t] * ec[pcol[(int64_t)j * c + t]];
+    return x[j] + s;
+}
+
 template <typename T>
 __global__ void k_smooth0(int n, const T* __restrict__ dinv, const T* __restrict__ b, T* __restrict__ x, T omega) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = (omega * dinv[i]) * b[i];
 }
-
+// two sweeps from a zero guess in one pass
+template <typename T>
+__global__ void k_presmooth2(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const T* __restrict__ bv, const T* __restrict__ dinv, const T* __restrict__ b,
+                             T* __restrict__ y, T omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T x1 = (omega * dinv[i]) * b[i];
+    y[i] = x1 + (omega * dinv[i]) * (b[i] - row_Bx1(i, rp, ci, bv, dinv, b, omega));
+}
+// one sweep; optionally also stores the result at Z + (*dj) n
 template <typename T>
 __global__ void k_smooth(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const T* __restrict__ bv, const T* __restrict__ dinv, const T* __restrict__ b,
-                         const T* __restrict__ x, T* __restrict__ y, T omega) {
+                         const T* __restrict__ x, T* __restrict__ y, T omega, T* __restrict__ Z,
+                         const int* __restrict__ dj) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    T s = T(0);
-    for (int p = rp[i]; p < rp[i + 1]; ++p) s += bv[p] * x[ci[p]];
-    y[i] = x[i] + (omega * dinv[i]) * (b[i] - s);
+    const T v = x[i] + (omega * dinv[i]) * (b[i] - row_Bx(i, rp, ci, bv, x));
+    y[i] = v;
+    if (Z) Z[(int64_t)(*dj) * n + i] = v;
 }
-
 template <typename T>
 __global__ void k_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                         const T* __restrict__ bv, const T* __restrict__ b, const T* __restrict__ x,
                         T* __restrict__ r) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T s = T(0);
-    for (int p = rp[i]; p < rp[i + 1]; ++p) s += bv[p] * x[ci[p]];
-    r[i] = b[i] - s;
+    if (i < n) r[i] = b[i] - row_Bx(i, rp, ci, bv, x);
 }
-
 template <typename T>
 __global__ void k_restrict(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
                            const T* __restrict__ qv, const T* __restrict__ r, T* __restrict__ bc) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
-    T s = T(0);
-    for (int q = qrp[I]; q < qrp[I + 1]; ++q) s += qv[q] * r[qci[q]];
-    bc[I] = s;
+    bc[I] = row_sum<T>(qrp[I], qrp[I + 1], qci, qv, [&](int i) { return r[i]; });
 }
-
 template <typename T>
 __global__ void k_prolong_add(int n, int c, const int32_t* __restrict__ pcol, const T* __restrict__ pval,
                               const int32_t* __restrict__ pcnt, const T* __restrict__ ec, T* __restrict__ x) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T s = T(0);
-    for (int t = 0; t < pcnt[i]; ++t) s += pval[(int64_t)i * c + t] * ec[pcol[(int64_t)i * c + t]];
-    x[i] = x[i] + s;
+    if (i < n) x[i] = row_prolonged(i, c, pcol, pval, pcnt, ec, x);
 }
-
-// Coarsest level: x = B_L^+ b, one warp per row.
 template <typename T>
 __global__ void k_dense_mv(int n, const T* __restrict__ A, const T* __restrict__ b, T* __restrict__ x) {
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -69,15 +110,17 @@ __global__ void k_dense_mv(int n, const T* __restrict__ A, const T* __restrict__
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) x[row] = s;
 }
-
 template <typename T>
-__global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b) {
+__global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b, T* __restrict__ Z, const int* __restrict__ dj) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = a[i];
+    if (i >= n) return;
+    b[i] = a[i];
+    if (Z) Z[(int64_t)(*dj) * n + i] = a[i];
 }
 
 template <typename T>
-void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int nu_pre, int nu_post, cudaStream_t s) {
+void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int nu_pre, int nu_post, cudaStream_t s,
+            T* Z, const int* dj) {
     const int L = (int)lv.size() - 1;
     const T omega = (T)omega_d;
     std::vector<T*> xcur(L + 1), xtmp(L + 1);
@@ -87,14 +130,17 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         const unsigned g = blocks_for(n, 256);
         T* x = v.x;
         T* t = v.r;
-        if (nu_pre >= 1) {
-            BAMG_LAUNCH(k_smooth0<T>, g, 256, 0, s, n, v.dinv, v.b, x, omega);
-            for (int k = 1; k < nu_pre; ++k) {
-                BAMG_LAUNCH(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega);
+        if (nu_pre >= 2) {
+            BAMG_LAUNCH(k_presmooth2<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, omega);
+            for (int k = 2; k < nu_pre; ++k) {
+                BAMG_LAUNCH(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
+                            (T*)nullptr, (const int*)nullptr);
                 T* q = x;
                 x = t;
                 t = q;
             }
+        } else if (nu_pre == 1) {
+            BAMG_LAUNCH(k_smooth0<T>, g, 256, 0, s, n, v.dinv, v.b, x, omega);
         } else {
             BAMG_CK(cudaMemsetAsync(x, 0, sizeof(T) * n, s));
         }
@@ -108,6 +154,7 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         const int n = lv[L].B.n;
         BAMG_LAUNCH(k_dense_mv<T>, blocks_for(n, 4), 128, 0, s, n, pinv, lv[L].b, lv[L].x);
         xcur[L] = lv[L].x;
+        if (L == 0 && Z) BAMG_LAUNCH(k_copy<T>, blocks_for(n, 256), 256, 0, s, n, lv[0].x, lv[0].x, Z, dj);
     }
     for (int l = L - 1; l >= 0; --l) {
         const VLevel<T>& v = lv[l];
@@ -115,16 +162,21 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         const unsigned g = blocks_for(n, 256);
         T* x = xcur[l];
         T* t = xtmp[l];
+        T* zl = (l == 0) ? Z : nullptr;
         BAMG_LAUNCH(k_prolong_add<T>, g, 256, 0, s, n, v.P.c, v.P.pcol, v.P.pval, v.P.pcnt, xcur[l + 1], x);
         for (int k = 0; k < nu_post; ++k) {
-            BAMG_LAUNCH(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega);
+            BAMG_LAUNCH(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
+                        k == nu_post - 1 ? zl : (T*)nullptr, dj);
             T* q = x;
             x = t;
             t = q;
         }
+        if (nu_post == 0 && zl) BAMG_LAUNCH(k_copy<T>, g, 256, 0, s, n, x, x, zl, dj);
         xcur[l] = x;
     }
-    if (L > 0 && xcur[0] != lv[0].x) BAMG_LAUNCH(k_copy<T>, blocks_for(lv[0].B.n, 256), 256, 0, s, lv[0].B.n, xcur[0], lv[0].x);
+    if (L > 0 && xcur[0] != lv[0].x)
+        BAMG_LAUNCH(k_copy<T>, blocks_for(lv[0].B.n, 256), 256, 0, s, lv[0].B.n, xcur[0], lv[0].x, (T*)nullptr,
+                    (const int*)nullptr);
 }
 
 // ---------------------------------------------------------------- FP64 Krylov pieces
@@ -144,7 +196,7 @@ void spmv_f64_from_f32(const MatView<double>& B, const float* x, double* y, cuda
     BAMG_LAUNCH(k_spmv64<float>, blocks_for(B.n, 256), 256, 0, s, B.n, B.rp, B.ci, B.v, x, y, 1.0);
 }
 
-constexpr int DOT_ROWS = 512;
+constexpr int DOT_ROWS = 128;
 int dots_partial_blocks(int n) { return (int)blocks_for(n, DOT_ROWS); }
 
 __global__ void __launch_bounds__(256) k_dots_partial(int n, const double* __restrict__ V, int64_t ldv, int nv,
@@ -313,15 +365,26 @@ __global__ void k_gmres_init(double* __restrict__ st, int m) {
 }
 void gmres_init(double* d_state, int m, cudaStream_t s) { BAMG_LAUNCH(k_gmres_init, 1, 32, 0, s, d_state, m); }
 
-// y = R^{-1} g for the leading (j+1) x (j+1) block.
+// y = R^{-1} g for the leading (j+1) x (j+1) block: R and g staged in shared memory,
+// column-oriented back substitution by one warp.
 __global__ void k_solve_y(double* __restrict__ st, int j, int m) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double R[GMRES_MMAX * GMRES_MMAX], y[GMRES_MMAX];
     GmresLayout L(m);
-    for (int r = j; r >= 0; --r) {
-        double s = st[L.g + r];
-        for (int q = r + 1; q <= j; ++q) s -= st[L.R + r + (int64_t)q * m] * st[L.y + q];
-        st[L.y + r] = s / st[L.R + r + (int64_t)r * m];
+    const int lane = threadIdx.x;
+    for (int idx = lane; idx < (j + 1) * (j + 1); idx += 32) {
+        const int r = idx % (j + 1), c = idx / (j + 1);
+        R[r * GMRES_MMAX + c] = st[L.R + r + (int64_t)c * m];
     }
+    for (int r = lane; r <= j; r += 32) y[r] = st[L.g + r];
+    __syncwarp();
+    for (int q = j; q >= 0; --q) {
+        if (lane == 0) y[q] /= R[q * GMRES_MMAX + q];
+        __syncwarp();
+        const double yq = y[q];
+        for (int r = lane; r < q; r += 32) y[r] -= R[r * GMRES_MMAX + q] * yq;
+        __syncwarp();
+    }
+    for (int r = lane; r <= j; r += 32) st[L.y + r] = y[r];
 }
 void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s) { BAMG_LAUNCH(k_solve_y, 1, 32, 0, s, d_state, j, m); }
 
@@ -336,20 +399,13 @@ __global__ void k_v_to_in(int n, const double* __restrict__ V, const int* __rest
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) vin[i] = (T)V[(int64_t)(*dj) * n + i];
 }
-template <typename T>
-__global__ void k_z_store(int n, const T* __restrict__ z, const int* __restrict__ dj, T* __restrict__ Z) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) Z[(int64_t)(*dj) * n + i] = z[i];
-}
 template <typename TX>
 __global__ void k_spmv64_j(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ bv, const TX* __restrict__ x, const int* __restrict__ dj,
                            double* __restrict__ V) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = 0.0;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) s += bv[p] * (double)x[ci[p]];
-    V[(int64_t)(*dj + 1) * n + i] = s;
+    V[(int64_t)(*dj + 1) * n + i] = row_sum<double>(rp[i], rp[i + 1], ci, bv, [&](int j) { return (double)x[j]; });
 }
 // self = 0: dots of w = V[j+1] with V[0..j];  self = 1: w . w
 __global__ void __launch_bounds__(256) k_dots_partial_j(int n, const double* __restrict__ V,
@@ -394,59 +450,73 @@ __global__ void k_update_minus_j(int n, double* __restrict__ V, const int* __res
     if (i >= n) return;
     double* w = V + (int64_t)(j + 1) * n;
     double s = w[i];
+#pragma unroll 8
     for (int q = 0; q <= j; ++q) s -= V[(int64_t)q * n + i] * sh[q];
     w[i] = s;
-}
-__global__ void k_givens_j(double* __restrict__ st, const int* __restrict__ dj, int m) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int j = *dj;
-    GmresLayout L(m);
-    double col[GMRES_MMAX + 1];
-    for (int i = 0; i <= j; ++i) col[i] = st[L.h1 + i] + st[L.h2 + i];
-    const double hn = sqrt(st[L.nrm2]);
-    col[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-        const double c = st[L.cs + i], s = st[L.sn + i];
-        const double a = col[i], b = col[i + 1];
-        col[i] = c * a + s * b;
-        col[i + 1] = -s * a + c * b;
-    }
-    const double a = col[j], b = col[j + 1];
-    const double den = hypot(a, b);
-    const double c = den == 0.0 ? 1.0 : a / den, s = den == 0.0 ? 0.0 : b / den;
-    st[L.cs + j] = c;
-    st[L.sn + j] = s;
-    col[j] = c * a + s * b;
-    const double gj = st[L.g + j];
-    st[L.g + j + 1] = -s * gj;
-    st[L.g + j] = c * gj;
-    for (int i = 0; i <= j; ++i) st[L.R + i + (int64_t)j * m] = col[i];
-    st[L.est] = fabs(st[L.g + j + 1]);
-    st[L.hn] = hn;
-}
-__global__ void k_scale_j(int n, double* __restrict__ V, const int* __restrict__ dj, const double* __restrict__ st,
-                          int hn_idx) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double a = st[hn_idx];
-    double* w = V + (int64_t)(*dj + 1) * n;
-    w[i] = a != 0.0 ? w[i] / a : 0.0;
 }
 __global__ void k_inc_j(int* dj) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dj += 1;
 }
 
+// Givens update (one thread) fused with v_{j+1} = w / ||w||: every thread forms
+// ||w|| = sqrt(nrm2) itself, so the scaling does not wait for the rotation.
+__global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __restrict__ dj, double* __restrict__ st,
+                                 int m) {
+    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX];
+    GmresLayout L(m);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = *dj;
+    if (blockIdx.x == 0) {
+        // operands staged in shared memory by the block, then the serial rotations
+        for (int q = threadIdx.x; q <= j; q += blockDim.x) {
+            col[q] = st[L.h1 + q] + st[L.h2 + q];
+            if (q < j) {
+                cs[q] = st[L.cs + q];
+                sn[q] = st[L.sn + q];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double hn = sqrt(st[L.nrm2]);
+            col[j + 1] = hn;
+            for (int q = 0; q < j; ++q) {
+                const double c = cs[q], s = sn[q];
+                const double a = col[q], b = col[q + 1];
+                col[q] = c * a + s * b;
+                col[q + 1] = -s * a + c * b;
+            }
+            const double a = col[j], b = col[j + 1];
+            const double den = hypot(a, b);
+            const double c = den == 0.0 ? 1.0 : a / den, s = den == 0.0 ? 0.0 : b / den;
+            st[L.cs + j] = c;
+            st[L.sn + j] = s;
+            col[j] = c * a + s * b;
+            const double gj = st[L.g + j];
+            st[L.g + j + 1] = -s * gj;
+            st[L.g + j] = c * gj;
+            st[L.est] = fabs(st[L.g + j + 1]);
+            st[L.hn] = hn;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q <= j; q += blockDim.x) st[L.R + q + (int64_t)j * m] = col[q];
+    }
+    if (i < n) {
+        const double hn = sqrt(st[L.nrm2]);
+        double* w = V + (int64_t)(j + 1) * n;
+        w[i] = hn != 0.0 ? w[i] / hn : 0.0;
+    }
+}
+
 template <typename T>
 void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T* vin, T* zout, int* dj,
-                            double* st, int m, double* partial, const std::vector<VLevel<T>>& lv, const T* pinv,
-                            double omega, int nu_pre, int nu_post, double* h_est, cudaStream_t s) {
+                            double* st, int m, double* partial, const std::vector<VLevel<T>>& lv,
+                            const T* pinv, double omega, int nu_pre, int nu_post, double* h_est, cudaStream_t s) {
     GmresLayout L(m);
     const unsigned g = blocks_for(n, 256);
     const int nb = dots_partial_blocks(n);
     const int stride = m + 1;
     BAMG_LAUNCH(k_v_to_in<T>, g, 256, 0, s, n, V, dj, vin);
-    vcycle<T>(lv, pinv, omega, nu_pre, nu_post, s);
-    BAMG_LAUNCH(k_z_store<T>, g, 256, 0, s, n, zout, dj, Z);
+    vcycle<T>(lv, pinv, omega, nu_pre, nu_post, s, Z, dj);
     BAMG_LAUNCH(k_spmv64_j<T>, g, 256, 0, s, n, B.rp, B.ci, B.v, zout, dj, V);
     for (int pass = 0; pass < 2; ++pass) {
         double* h = st + (pass == 0 ? L.h1 : L.h2);
@@ -456,8 +526,7 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
     }
     BAMG_LAUNCH(k_dots_partial_j, nb, 256, 0, s, n, V, dj, 1, partial, stride);
     BAMG_LAUNCH(k_reduce_cols_j, 1, 128, 0, s, nb, dj, 1, stride, partial, st + L.nrm2);
-    BAMG_LAUNCH(k_givens_j, 1, 32, 0, s, st, dj, m);
-    BAMG_LAUNCH(k_scale_j, g, 256, 0, s, n, V, dj, st, L.hn);
+    BAMG_LAUNCH(k_givens_scale_j, g, 256, 0, s, n, V, dj, st, m);
     BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     BAMG_LAUNCH(k_inc_j, 1, 32, 0, s, dj);
 }
@@ -469,8 +538,10 @@ template void arnoldi_step_graphable<double>(int, const MatView<double>&, double
                                              double*, int, double*, const std::vector<VLevel<double>>&,
                                              const double*, double, int, int, double*, cudaStream_t);
 
-template void vcycle<float>(const std::vector<VLevel<float>>&, const float*, double, int, int, cudaStream_t);
-template void vcycle<double>(const std::vector<VLevel<double>>&, const double*, double, int, int, cudaStream_t);
+template void vcycle<float>(const std::vector<VLevel<float>>&, const float*, double, int, int, cudaStream_t, float*,
+                            const int*);
+template void vcycle<double>(const std::vector<VLevel<double>>&, const double*, double, int, int, cudaStream_t,
+                             double*, const int*);
 template void form_x<float>(int, const double*, const float*, int64_t, int, const double*, double*, cudaStream_t);
 template void form_x<double>(int, const double*, const double*, int64_t, int, const double*, double*, cudaStream_t);
 

@@ -69,7 +69,7 @@ void coarse_to_fine(int n, const uint8_t* cf, const int32_t* cidx, int32_t* c2f,
 template <typename T>
 int interp_ls(int n, const int32_t* rp, const int32_t* ci, const uint8_t* cf, const int32_t* cidx, const T* X, int ncols,
               int ld, const double* d_w, int z, int mmax, int c, double ridge, int32_t* pcol, T* pval, int32_t* pcnt,
-              cudaStream_t s);
+              cudaStream_t s, int* d_err = nullptr);
 // Q rows (CSR by coarse rows, sorted by fine index) from the ELL interpolation.
 template <typename T>
 void build_restriction(const EllView<T>& P, int nc, DevBuf<int32_t>& qrp, DevBuf<int32_t>& qci, DevBuf<T>& qv,
@@ -112,8 +112,11 @@ struct VLevel {  // one level of the V-cycle
     const T* qv = nullptr;
     T *b = nullptr, *x = nullptr, *r = nullptr;  // work vectors of n entries
 };
+// One V-cycle: lv[0].b -> lv[0].x.  With Z != null the result is also stored at
+// Z + (*dj) * n_0.
 template <typename T>
-void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega, int nu_pre, int nu_post, cudaStream_t s);
+void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega, int nu_pre, int nu_post, cudaStream_t s,
+            T* Z = nullptr, const int* dj = nullptr);
 
 void spmv_f64(const MatView<double>& B, const double* x, double* y, double alpha, cudaStream_t s);  // y = alpha B x
 void spmv_f64_from_f32(const MatView<double>& B, const float* x, double* y, cudaStream_t s);

@@ -154,6 +154,8 @@ struct Solver : SolverBase {
         return v;
     }
 
+    DevBuf<int> ls_err;  // overflow flag of the neighbourhood searches, read once per setup
+
     void alloc_vcycle_work() {
         for (auto& L : lv) {
             L->vb.alloc(L->n);
@@ -174,9 +176,8 @@ struct Solver : SolverBase {
         c.pcol.alloc((size_t)c.n * o.caliber);
         c.pval.alloc((size_t)c.n * o.caliber);
         c.pcnt.alloc(c.n);
-        int e = interp_ls<T>(c.n, c.rp.get(), c.ci.get(), c.cf.get(), c.cidx.get(), c.X.get(), ld, ld, c.w.get(), o.z,
-                             o.mmax, o.caliber, ridge(), c.pcol.get(), c.pval.get(), c.pcnt.get(), s);
-        BAMG_REQUIRE(e == 0, BAMG_EOVERFLOW, "neighbourhood search exceeded its capacity of 256 visited states");
+        interp_ls<T>(c.n, c.rp.get(), c.ci.get(), c.cf.get(), c.cidx.get(), c.X.get(), ld, ld, c.w.get(), o.z, o.mmax,
+                     o.caliber, ridge(), c.pcol.get(), c.pval.get(), c.pcnt.get(), s, ls_err.get());
         build_restriction<T>(c.P(o.caliber), c.nc, c.qrp, c.qci, c.qv, s);
         GalerkinOut<T> go;
         galerkin<T>(c.B(), c.tv.get(), c.qrp.get(), c.qci.get(), c.qv.get(), c.P(o.caliber), c.nc, go, s);
@@ -260,6 +261,8 @@ struct Solver : SolverBase {
         ldV = round_up(o.k_ev + 1, W);
         ld = ldU + ldV;
         BAMG_REQUIRE(ld <= 32, BAMG_EINVAL, "r + k_ev too large: padded test-vector block must be <= 32 columns");
+        ls_err.alloc(1);
+        BAMG_CK(cudaMemsetAsync(ls_err.get(), 0, sizeof(int), s));
         L0->X.alloc((size_t)n * ld);
         BAMG_CK(cudaMemsetAsync(L0->X.get(), 0, sizeof(T) * n * ld, s));
         launch_tv_init<T>(n, r, ld, 0, o.seed, o.tv_lo, o.tv_hi, L0->X.get(), s);
@@ -351,7 +354,10 @@ struct Solver : SolverBase {
             scale_vec(n, x_init.get(), sums.get(), 3, true, x_init.get(), s);
         }
         alloc_vcycle_work();
+        int h_err = 0;
+        BAMG_CK(cudaMemcpyAsync(&h_err, ls_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CK(cudaStreamSynchronize(s));
+        BAMG_REQUIRE(h_err == 0, BAMG_EOVERFLOW, "neighbourhood search exceeded its capacity of 256 visited states");
         setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
 

@@ -110,13 +110,46 @@ def test_neighborhoods_vs_bfs(z):
     B = bamg.system_matrix(ch.to_scipy())
     cf, cidx, _ = bamg.coarsen_grid(*ch.grid)
     cand, ncand = bamg.neighborhoods(B, cf, cidx, z, 64)
+    extended = 0
     for i in range(ch.n):
         if cf[i]:
             assert ncand[i] == 0
             continue
-        dist = _bfs(B, i, z)
-        want = sorted([j for j in dist if j != i and cf[j]], key=lambda j: (dist[j], cidx[j]))
+        depth = z
+        while True:  # the smallest depth <= 3 that reaches a coarse point (at least z)
+            dist = _bfs(B, i, depth)
+            want = sorted([j for j in dist if j != i and cf[j]], key=lambda j: (dist[j], cidx[j]))
+            if want or depth >= 3:
+                break
+            depth += 1
+        extended += depth > z
         assert list(cand[i, :ncand[i]]) == want
+
+
+def test_neighborhood_extension_reaches_the_corner():
+    # in the directed graph of the 32 x 32 tandem queue one fine state reaches no coarse
+    # state within two steps; the extension to three gives it candidates
+    ch = tandem_queue(31)
+    B = bamg.system_matrix(ch.to_scipy())
+    cf, cidx, _ = bamg.coarsen_grid(*ch.grid)
+    c2, n2 = bamg._neighborhoods_depth(B, cf, cidx, 2, 16)
+    cand, ncand = bamg.neighborhoods(B, cf, cidx, 2, 16)
+    miss = np.flatnonzero((~cf) & (n2 == 0))
+    assert len(miss) >= 1
+    for i in miss:
+        dist = _bfs(B, i, 3)
+        want = sorted([j for j in dist if j != i and cf[j]], key=lambda j: (dist[j], cidx[j]))
+        assert len(want) > 0 and list(cand[i, :ncand[i]]) == want
+
+
+def test_every_fine_point_is_interpolated_on_tandem_hierarchy():
+    # with the extension every column of Q sums to one, hence 1^T B_l = 0 on every level
+    ch = tandem_queue(31)
+    H = bamg.setup(ch.to_scipy(), 6, 10, bamg.Opts(), grid=ch.grid)
+    for lv in H.levels[:-1]:
+        assert np.all(lv.ncand[~lv.cf] > 0)
+    for lv in H.levels:
+        assert np.abs(np.asarray(lv.B.sum(axis=0)).ravel()).max() < 1e-13
 
 
 def test_independent_set_is_maximal():
