@@ -90,7 +90,7 @@ class Opts:
     tv_lo: float = 1.0  # Section 5.1: U[1, 2]
     tv_hi: float = 2.0
     ev_change_tol: float = 1e-3  # R9: "relative change significant"
-    ridge: float = 1e-12  # R25: Tikhonov term of the local LS problems
+    ridge: float = 1e-4  # R25: Tikhonov term of the local LS problems
     weight_floor: float = 1e-28  # R7
     cr_theta: float = 0.85  # Section 3.1
     cr_nu: int = 8

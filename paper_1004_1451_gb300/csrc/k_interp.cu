@@ -135,8 +135,8 @@ void coarse_to_fine(int n, const uint8_t* cf, const int32_t* cidx, int32_t* c2f,
 }
 
 // ================================================================ least-squares interpolation
-constexpr int LS_WARPS = 4;
-constexpr int VIS_CAP = 256;  // nodes visited by one neighbourhood search
+constexpr int LS_WARPS = 2;
+constexpr int VIS_CAP = 1024;  // nodes visited by one neighbourhood search
 constexpr int MMAX = 16;
 constexpr int CMAX = 4;
 constexpr int KMAX = 32;
@@ -193,7 +193,8 @@ __device__ __forceinline__ bool chol_solve(T (&A)[CMAX][CMAX], const T (&b)[CMAX
 
 // One warp per point.  Fine points: breadth-first search to depth z over the row
 // pattern of B (edges i -> j for b_ij != 0, i != j), continued up to depth 3 while no
-// coarse point has been found; candidates = coarse points found, ranked by (depth,
+// coarse point has been found, and stopped early once mmax coarse points are known at
+// the depths already completed; candidates = coarse points found, ranked by (depth,
 // coarse index) and cut to mmax; then the greedy steps of
 // Algorithm 2 with one lane per candidate: each lane forms its (|J|+1)-square weighted
 // normal equations (plus the Tikhonov term), solves them by Cholesky and evaluates the
@@ -234,17 +235,13 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
         dist[0] = 0;
     }
     __syncwarp();
-    int nvis = 1, fs = 0, fe = 1;
+    int nvis = 1, fs = 0, fe = 1, ncvis = 0;
     bool ovf = false;
     for (int d = 1; d <= 3; ++d) {
-        if (d > z) {  // beyond z only while no coarse point has been reached
-            bool anyc = false;
-            for (int q0 = 1; q0 < nvis && !anyc; q0 += 32) {
-                const int q = q0 + lane;
-                anyc = __any_sync(0xffffffffu, q < nvis && cf[vis[q]] != 0);
-            }
-            if (anyc) break;
-        }
+        // beyond z only while no coarse point has been reached (the extension of R30);
+        // and no deeper once mmax coarse points are known: deeper ones would rank after them
+        if ((d > z && ncvis > 0) || ncvis >= mmax) break;
+        bool fonly = false;  // visited list full: record only coarse nodes for the rest of this depth
         for (int f = fs; f < fe; ++f) {
             const int u = vis[f];
             const int p0 = rp[u], p1 = rp[u + 1];
@@ -258,13 +255,19 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
                             isnew = false;
                             break;
                         }
+                const bool isc = isnew && cf[v] != 0;
                 const int key = isnew ? v : -1 - lane;
                 const unsigned grp = __match_any_sync(0xffffffffu, key);
                 const unsigned lt = (1u << lane) - 1u;
                 const bool leader = isnew && (grp & lt) == 0u;
-                const unsigned bal = __ballot_sync(0xffffffffu, leader);
+                unsigned bal = __ballot_sync(0xffffffffu, leader && (!fonly || isc));
+                if (!fonly && nvis + __popc(bal) > VIS_CAP) {
+                    fonly = true;
+                    bal = __ballot_sync(0xffffffffu, leader && isc);
+                }
+                const bool rec = (bal >> lane) & 1u;
                 const int pos = nvis + __popc(bal & lt);
-                if (leader && pos < VIS_CAP) {
+                if (rec && pos < VIS_CAP) {
                     vis[pos] = v;
                     dist[pos] = (uint8_t)d;
                 }
@@ -273,9 +276,15 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
                     ovf = true;
                     added = VIS_CAP - nvis;
                 }
+                ncvis += __popc(__ballot_sync(0xffffffffu, rec && isc && pos < VIS_CAP));
                 nvis += added;
                 __syncwarp();
             }
+        }
+        // a truncated depth (fine nodes not recorded) is exact only if the search ends here
+        if (fonly) {
+            if (d < 3 && ncvis < mmax && !(d >= z && ncvis > 0)) ovf = true;
+            break;
         }
         fs = fe;
         fe = nvis;

@@ -701,8 +701,8 @@ int bamg_default_opts(bamg_opts* o) {
     o->tv_lo = 1.0;
     o->tv_hi = 2.0;
     o->ev_change_tol = 1e-3;
-    o->ridge = 1e-12;
-    o->ridge32 = 1e-6;
+    o->ridge = 1e-4;
+    o->ridge32 = 1e-4;
     o->weight_floor = 1e-28;
     o->cr_theta = 0.85;
     o->cr_nu = 8;

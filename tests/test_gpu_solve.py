@@ -221,3 +221,14 @@ def test_delaunay_cr_fp64():
     assert rel(x, exact.exact_stationary(ch)) < 1e-8
     xo, H, sto = ob.stationary(ch.to_scipy(), 8, 12, 1e-13, ob.Opts(coarsen="cr"))
     assert rel(x, xo) < 1e-8
+
+
+def test_config3_delaunay_2e20_mixed():
+    # Delaunay triangulation of 2^20 points U[0,1]^2, walk with probability 1/deg, r = 16,
+    # FP32 setup and V-cycle inside FP64 GMRES, compatible-relaxation coarsening
+    ch = delaunay_walk(1 << 20, 0)
+    s, x, st = _run(ch, 16, 20, 1e-12, "mixed", coarsen="cr")
+    info = s.info()
+    assert info["n"][-1] <= 64
+    assert rel(x, exact.exact_stationary(ch)) < 1e-6
+    print("delaunay 2^20:", info["n"], st)
