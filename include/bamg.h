@@ -128,6 +128,18 @@ enum { BAMG_X_GUESS = 1, BAMG_X_HOST = 2 };
  * ENUMERIC, ECUDA. */
 int bamg_solve(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st);
 
+/* Batched form: sets up and solves nchains independent chains to ||B x||_1/||x||_1 <= tol
+ * and frees them, with nworkers host threads (0: one per 4 chains, at most 16), each
+ * driving its own non-blocking stream; chains are taken largest first from a shared
+ * queue, so the small latency-bound kernels of several chains overlap on the GPU.
+ * As[k], r[k], levels[k], opts[k] as for bamg_setup (opts[k].stream is ignored);
+ * xs[k]: n_k doubles for the result, device memory unless flags has BAMG_X_HOST
+ * (BAMG_X_GUESS is not accepted).  st (may be NULL) receives one entry per chain.
+ * Returns BAMG_OK if every chain succeeded, else the first failing chain's code (its
+ * message in bamg_last_error); the other chains are still solved. */
+int bamg_solve_batch(int nchains, const bamg_csr* As, const int* r, const int* levels, const bamg_opts* opts,
+                     double* const* xs, int flags, double tol, int nworkers, bamg_stats* st);
+
 /* Frees the handle and its device memory.  NULL is allowed. */
 void bamg_free(bamg_handle* h);
 
@@ -254,9 +266,12 @@ int bamg_galerkin(int dtype, const bamg_mat* B, const void* T_val, int nc, const
  * as two real columns (Re v, Im v) sharing Re lambda; at most k_ev + 1 columns.
  * d_lam[col], d_V (n x ncols, column-major, unit norm, <w, v> > 0 for w_i = i+1),
  * d_kind[col] (0 real, 1 real part, 2 imaginary part); *h_nvec = columns written.
+ * dtype: arithmetic of the eigenvector refinement and of B_L^+ (BAMG_F64, or BAMG_F32 as
+ * in the mixed-precision setup, whose V-cycle applies B_L^+ in FP32); the outputs are
+ * FP64 either way.  The eigenvalue estimates that serve as shifts are FP32 in both.
  * The smallest eigenvalue is set to exactly 0.  With d_pinv != NULL also writes
  * B_L^+ (row-major), the minimal-norm inverse of Section 4.2. */
-int bamg_coarse_eig(int n, const double* d_B, const double* d_T, int k_ev, double* d_lam, double* d_V,
+int bamg_coarse_eig(int dtype, int n, const double* d_B, const double* d_T, int k_ev, double* d_lam, double* d_V,
                     int32_t* d_kind, int* h_nvec, double* d_pinv, void* stream);
 
 #ifdef __cplusplus

@@ -14,7 +14,7 @@ import torch
 from . import _capi as capi
 from ._capi import BamgError  # noqa: F401
 
-__all__ = ["Solver", "import_hierarchy", "tv_init", "relax", "relax_noalloc", "tv_weights", "coarsen_grid", "coarsen_cr",
+__all__ = ["Solver", "solve_batch", "import_hierarchy", "tv_init", "relax", "relax_noalloc", "tv_weights", "coarsen_grid", "coarsen_cr",
            "interp_ls", "galerkin", "coarse_eig", "launch_count", "default_opts", "BamgError"]
 
 
@@ -182,6 +182,42 @@ class Solver:
             pass
 
 
+def solve_batch(chains, r, levels, tol: float, opts=None, workers: int = 0, host: bool = False):
+    """bamg_solve_batch over a list of chains.  chains[k] = (row_ptr, col, val) torch
+    tensors (on the GPU, or on the CPU with host=True); r, levels: ints or per-chain
+    lists; opts: a dict of options or a list of dicts (e.g. grid=(nx, ny) per chain).
+    Returns (list of x tensors, list of stats dicts); raises on the first failing chain."""
+    n = len(chains)
+    rs = [r] * n if isinstance(r, int) else list(r)
+    lv = [levels] * n if isinstance(levels, int) else list(levels)
+    ol = [dict(opts or {}) for _ in range(n)] if not isinstance(opts, (list, tuple)) else [dict(o) for o in opts]
+    As = (capi.Csr * n)()
+    Os = (capi.Opts * n)()
+    xs = (C.c_void_p * n)()
+    keep, outs = [], []
+    for k, (rp, ci, v) in enumerate(chains):
+        if host:
+            rp, ci, v = rp.contiguous(), ci.contiguous(), v.contiguous()
+        keep += [rp, ci, v]
+        m = int(rp.numel() - 1)
+        As[k] = capi.Csr(m, int(ci.numel()), _p(_i32(rp)).value, _p(_i32(ci)).value, _p(v).value, 1 if host else 0)
+        Os[k] = default_opts(**ol[k])
+        x = torch.empty(m, dtype=torch.float64, pin_memory=True) if host else \
+            torch.empty(m, dtype=torch.float64, device="cuda")
+        outs.append(x)
+        xs[k] = x.data_ptr()
+    st = (capi.Stats * n)()
+    torch.cuda.synchronize()
+    code = _lib().bamg_solve_batch(n, As, (C.c_int * n)(*rs), (C.c_int * n)(*lv), Os, xs,
+                                   capi.X_HOST if host else 0, float(tol), workers, st)
+    stats = [{f[0]: getattr(st[k], f[0]) for f in capi.Stats._fields_} for k in range(n)]
+    if code != capi.BAMG_OK:
+        err = BamgError(code, _lib().bamg_last_error().decode())
+        err.stats = stats
+        raise err
+    return outs, stats
+
+
 def import_hierarchy(levels, pinv: np.ndarray, x_init: np.ndarray, **opts) -> Solver:
     """Solver over a given hierarchy.  levels: list of dicts with numpy 'B' = (row_ptr,
     col, val) and, except on the coarsest level, 'P' = (row_ptr, col, val) in CSR."""
@@ -292,14 +328,15 @@ def galerkin(B, T_val, nc: int, pcol, pval, pcnt, c: int):
     return rp, ci[:nnz], bv[:nnz], tv[:nnz]
 
 
-def coarse_eig(Bd: torch.Tensor, Td: torch.Tensor, k_ev: int, with_pinv: bool = True):
+def coarse_eig(Bd: torch.Tensor, Td: torch.Tensor, k_ev: int, with_pinv: bool = True, fp32_vectors: bool = False):
     n = Bd.shape[0]
     lam = torch.zeros(k_ev + 1, dtype=torch.float64, device=Bd.device)
     V = torch.zeros(k_ev + 1, n, dtype=torch.float64, device=Bd.device)
     kinds = torch.zeros(k_ev + 1, dtype=torch.int32, device=Bd.device)
     pinv = torch.zeros(n, n, dtype=torch.float64, device=Bd.device) if with_pinv else None
     nv = C.c_int()
-    capi.check(_lib().bamg_coarse_eig(n, _p(Bd.contiguous()), _p(Td.contiguous()), k_ev, _p(lam), _p(V), _p(kinds),
+    capi.check(_lib().bamg_coarse_eig(capi.F32 if fp32_vectors else capi.F64, n, _p(Bd.contiguous()),
+                                      _p(Td.contiguous()), k_ev, _p(lam), _p(V), _p(kinds),
                                       C.byref(nv), _p(pinv), _stream()))
     k = nv.value
     return lam[:k], V[:k].T, kinds[:k], pinv

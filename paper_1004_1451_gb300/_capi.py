@@ -63,6 +63,8 @@ SIGNATURES = {
     "bamg_setup": (_I, [C.POINTER(Csr), _I, _I, C.POINTER(Opts), C.POINTER(_P)]),
     "bamg_solve": (_I, [_P, _P, _I, _D, C.POINTER(Stats)]),
     "bamg_free": (None, [_P]),
+    "bamg_solve_batch": (_I, [_I, C.POINTER(Csr), C.POINTER(_I), C.POINTER(_I), C.POINTER(Opts), C.POINTER(_P), _I,
+                              _D, _I, C.POINTER(Stats)]),
     "bamg_last_error": (C.c_char_p, []),
     "bamg_launch_count": (C.c_uint64, []),
     "bamg_hierarchy_info": (_I, [_P, C.POINTER(_I), _P, _P, C.POINTER(_D)]),
@@ -80,7 +82,7 @@ SIGNATURES = {
     "bamg_interp_ls": (_I, [_I, C.POINTER(Mat), _P, _P, _P, _I, _I, _P, _I, _I, _I, _D, _P, _P, _P, _P]),
     "bamg_galerkin": (_I, [_I, C.POINTER(Mat), _P, _I, _P, _P, _P, _I, _P, _P, _P, _P, C.c_int64,
                            C.POINTER(C.c_int64), _P]),
-    "bamg_coarse_eig": (_I, [_I, _P, _P, _I, _P, _P, _P, C.POINTER(_I), _P, _P]),
+    "bamg_coarse_eig": (_I, [_I, _I, _P, _P, _I, _P, _P, _P, C.POINTER(_I), _P, _P]),
 }
 
 _lib = None

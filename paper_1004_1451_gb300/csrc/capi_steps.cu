@@ -132,7 +132,7 @@ int bamg_interp_ls(int dtype, const bamg_mat* B, const uint8_t* cf, const int32_
                                  ridge, pcol, (float*)pval, pcnt, s);
         else
             throw Error(BAMG_EINVAL, "bad dtype");
-        BAMG_REQUIRE(e == 0, BAMG_EOVERFLOW, "neighbourhood search exceeded its capacity of 256 visited states");
+        BAMG_REQUIRE(e == 0, BAMG_EOVERFLOW, "neighbourhood search exceeded its capacity of 1024 visited states");
     });
 }
 
@@ -185,15 +185,18 @@ int bamg_galerkin(int dtype, const bamg_mat* B, const void* T_val, int nc, const
     });
 }
 
-int bamg_coarse_eig(int n, const double* d_B, const double* d_T, int k_ev, double* d_lam, double* d_V,
+int bamg_coarse_eig(int dtype, int n, const double* d_B, const double* d_T, int k_ev, double* d_lam, double* d_V,
                     int32_t* d_kind, int* h_nvec, double* d_pinv, void* stream) {
     return guard([&] {
         cudaStream_t s = (cudaStream_t)stream;
         BAMG_REQUIRE(d_B && d_T && d_lam && d_V && d_kind, BAMG_EINVAL, "bad coarse_eig args");
-        const int nv = coarse_eig(n, d_B, d_T, k_ev, d_lam, d_V, d_kind, s);
+        BAMG_REQUIRE(dtype == BAMG_F64 || dtype == BAMG_F32, BAMG_EINVAL, "bad dtype");
+        const int nv = coarse_eig(n, d_B, d_T, k_ev, d_lam, d_V, d_kind, dtype == BAMG_F32, s);
         BAMG_REQUIRE(nv > 0, BAMG_ENUMERIC, "coarsest eigensolve did not converge");
         if (h_nvec) *h_nvec = nv;
-        if (d_pinv) BAMG_REQUIRE(coarse_pinv(n, d_B, d_pinv, s) == 0, BAMG_ENUMERIC, "singular coarsest factor");
+        if (d_pinv)
+            BAMG_REQUIRE(coarse_pinv(n, d_B, d_pinv, dtype == BAMG_F32, s) == 0, BAMG_ENUMERIC,
+                         "singular coarsest factor");
         BAMG_CK(cudaStreamSynchronize(s));
     });
 }

@@ -1,16 +1,19 @@
 // Coarsest level (Algorithm 3, first branch; Section 4.2): the eigenpairs of
 // B_L x = lambda T_L x with the smallest |lambda|, and the minimal-norm inverse B_L^+.
-// Order n <= 64, one thread block per task, matrices in shared memory.
+// Order n <= 64, matrices in shared memory, 256 threads per block.
 //
-// Eigenpairs: the eigenvalues of T^{-1} B from an LU solve, a Householder reduction to
-// Hessenberg form and the implicit double-shift QR iteration (Francis; Golub & Van Loan,
-// Matrix Computations, Sec. 7.5), all in FP32 because they only serve as shifts; then,
-// per selected eigenvalue, FP64 inverse iteration in complex arithmetic on the pencil
-// (B - sigma T) and a Rayleigh-type quotient give the eigenvector and the eigenvalue to
-// FP64 accuracy.  B^+: a bordered FP64 LU solve.
+// Eigenvalues (FP32; they only serve as shifts): shift-and-invert Arnoldi on the explicit
+// operator K = (B - sigma T)^{-1} T, then the Francis double-shift QR iteration on the
+// small Hessenberg matrix (Golub & Van Loan, Matrix Computations, Sec. 7.5).
+// Eigenvectors, one block per selected eigenvalue: inverse iteration in complex
+// arithmetic on the pencil (B - sigma T) and a Rayleigh-type quotient, in FP64 (or in
+// FP32 for the mixed-precision setup).  B^+: a bordered FP64 LU solve, the right-hand
+// sides split over several blocks.
 #include <cfloat>
 #include <cstdio>
 #include <cstdlib>
+
+#include <atomic>
 
 #include "kernels.cuh"
 
@@ -18,21 +21,29 @@ namespace bamg {
 
 constexpr int CN = 64;
 constexpr int LDP = CN + 1;  // padded row stride of shared matrices (no bank conflicts on columns)
-constexpr int CT = 256;  // threads per block
+constexpr int CT = 256;      // threads per block
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+template <typename F>
+__device__ __forceinline__ F absv(F x) {
+    return x < F(0) ? -x : x;
+}
 
 // ---------------------------------------------------------------- block-parallel real LU
-// In-place LU with partial pivoting of the n x n row-major A (shared memory); perm[k] =
-// pivot row of step k.  Pivots smaller than floorv in magnitude become +-floorv.
-__device__ void blu_factor(double* A, int n, int* perm, double floorv) {
-    const int tid = threadIdx.x;
+// In-place LU with partial pivoting of the n x n row-major A (shared, stride LDP);
+// perm[k] = pivot row of step k; pivots smaller than floorv in magnitude become
+// +-floorv.  On return the strict lower part holds L (unit diagonal), dinv[k] = 1 / u_kk,
+// and the strict upper part holds the rows of U scaled by dinv (a unit upper factor),
+// so that a solve needs no division.  Rank-one updates use a 16 x 16 thread grid.
+template <typename F>
+__device__ void blu_factor(F* A, int n, int* perm, F* dinv, F floorv) {
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     for (int k = 0; k < n; ++k) {
-        if (tid < 32) {
-            double best = -1.0;
+        if (tid < 32) {  // pivot search; one thread forms the (floored) pivot's reciprocal
+            F best = F(-1);
             int br = k;
             for (int r = k + tid; r < n; r += 32) {
-                const double v = fabs(A[r * LDP + k]);
+                const F v = absv(A[r * LDP + k]);
                 if (v > best) {
                     best = v;
                     br = r;
@@ -40,66 +51,138 @@ __device__ void blu_factor(double* A, int n, int* perm, double floorv) {
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const F ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int orr = __shfl_xor_sync(0xffffffffu, br, o);
                 if (ob > best || (ob == best && orr < br)) {
                     best = ob;
                     br = orr;
                 }
             }
-            if (tid == 0) perm[k] = br;
+            if (tid == 0) {
+                perm[k] = br;
+                F p = A[br * LDP + k];
+                if (absv(p) < floorv) p = p >= F(0) ? floorv : -floorv;
+                dinv[k] = F(1) / p;
+                A[br * LDP + k] = p;  // lands on the diagonal with the row swap
+            }
         }
         __syncthreads();
         const int br = perm[k];
-        if (br != k)
-            for (int c = tid; c < n; c += blockDim.x) {
-                const double t = A[k * LDP + c];
+        if (br != k) {
+            for (int c = tid; c < n; c += CT) {
+                const F t = A[k * LDP + c];
                 A[k * LDP + c] = A[br * LDP + c];
                 A[br * LDP + c] = t;
             }
-        __syncthreads();
-        double p = A[k * LDP + k];
-        if (fabs(p) < floorv) p = p >= 0.0 ? floorv : -floorv;
-        for (int r = k + 1 + tid; r < n; r += blockDim.x) A[r * LDP + k] /= p;
-        __syncthreads();
-        if (tid == 0) A[k * LDP + k] = p;
-        const int m = n - k - 1;
-        for (int idx = tid; idx < m * m; idx += blockDim.x) {
-            const int r = k + 1 + idx / m, c = k + 1 + idx % m;
-            A[r * LDP + c] -= A[r * LDP + k] * A[k * LDP + c];
-        }
-        __syncthreads();
-    }
-}
-
-// Solves A X = R for the m right-hand sides stored row-major (n x m) in R, in place.
-__device__ void blu_solve(const double* A, int n, const int* perm, double* R, int m) {
-    const int tid = threadIdx.x;
-    for (int k = 0; k < n; ++k) {
-        const int pk = perm[k];
-        if (pk != k) {
-            for (int c = tid; c < m; c += blockDim.x) {
-                const double t = R[k * m + c];
-                R[k * m + c] = R[pk * m + c];
-                R[pk * m + c] = t;
-            }
             __syncthreads();
         }
+        const F inv = dinv[k];
+        // rank-one update, a 4 x 4 register tile per thread (n <= 64)
+        F u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = k + 1 + tx + 16 * j;
+            u[j] = c < n ? A[k * LDP + c] : F(0);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = k + 1 + ty + 16 * i;
+            if (r < n) {
+                const F l = A[r * LDP + k] * inv;
+                F a[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = k + 1 + tx + 16 * j;
+                    a[j] = c < n ? A[r * LDP + c] : F(0);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = k + 1 + tx + 16 * j;
+                    if (c < n) A[r * LDP + c] = a[j] - l * u[j];
+                }
+            }
+        }
+        __syncthreads();
+        for (int r = k + 1 + tid; r < n; r += CT) A[r * LDP + k] *= inv;
     }
-    for (int q = 0; q < n; ++q) {
-        const int rows = n - q - 1;
-        for (int idx = tid; idx < rows * m; idx += blockDim.x) {
-            const int r = q + 1 + idx / m, c = idx % m;
-            R[r * m + c] -= A[r * LDP + q] * R[q * m + c];
+    __syncthreads();
+    for (int r = ty; r < n; r += 16)
+        for (int c = r + 1 + tx; c < n; c += 16) A[r * LDP + c] *= dinv[r];
+    __syncthreads();
+}
+
+// Solves A X = R in place for the m right-hand sides of the n x m row-major R (row
+// stride ldr), with the factor of blu_factor.
+template <typename F>
+__device__ void blu_solve(const F* A, int n, const int* perm, const F* dinv, F* R, int m, int ldr) {
+    const int tid = threadIdx.x;
+    const int gx = m >= 16 ? 16 : (m >= 4 ? 4 : 1);  // thread grid gy x gx over (rows, columns)
+    const int gy = CT / gx, ty = tid / gx, tx = tid % gx;
+    for (int c = tid; c < m; c += CT)  // row interchanges: columns are independent
+        for (int k = 0; k < n; ++k) {
+            const int pk = perm[k];
+            if (pk != k) {
+                const F t = R[k * ldr + c];
+                R[k * ldr + c] = R[pk * ldr + c];
+                R[pk * ldr + c] = t;
+            }
+        }
+    __syncthreads();
+    // each thread updates at most 4 rows x 4 columns per step (n, m <= 64), from registers
+    for (int q = 0; q + 1 < n; ++q) {  // unit lower L
+        F y[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = tx + gx * j;
+            y[j] = c < m ? R[q * ldr + c] : F(0);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = q + 1 + ty + gy * i;
+            if (r < n) {
+                const F l = A[r * LDP + q];
+                F a[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = tx + gx * j;
+                    a[j] = c < m ? R[r * ldr + c] : F(0);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = tx + gx * j;
+                    if (c < m) R[r * ldr + c] = a[j] - l * y[j];
+                }
+            }
         }
         __syncthreads();
     }
-    for (int q = n - 1; q >= 0; --q) {
-        for (int c = tid; c < m; c += blockDim.x) R[q * m + c] /= A[q * LDP + q];
-        __syncthreads();
-        for (int idx = tid; idx < q * m; idx += blockDim.x) {
-            const int r = idx / m, c = idx % m;
-            R[r * m + c] -= A[r * LDP + q] * R[q * m + c];
+    for (int r = ty; r < n; r += gy)
+        for (int c = tx; c < m; c += gx) R[r * ldr + c] *= dinv[r];
+    __syncthreads();
+    for (int q = n - 1; q > 0; --q) {  // unit upper
+        F y[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = tx + gx * j;
+            y[j] = c < m ? R[q * ldr + c] : F(0);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = ty + gy * i;
+            if (r < q) {
+                const F u = A[r * LDP + q];
+                F a[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = tx + gx * j;
+                    a[j] = c < m ? R[r * ldr + c] : F(0);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = tx + gx * j;
+                    if (c < m) R[r * ldr + c] = a[j] - u * y[j];
+                }
+            }
         }
         __syncthreads();
     }
@@ -237,184 +320,129 @@ __device__ int hqr_f32(float* H, int n, float* wr, float* wi, int* steps) {
     return 0;
 }
 
-// FP32 LU with partial pivoting (block-parallel) and the solve T M = B for n right-hand
-// sides, used only to obtain shifts.
-__device__ void blu_factor_f32(float* A, int n, int* perm) {
-    const int tid = threadIdx.x;
-    for (int k = 0; k < n; ++k) {
-        if (tid < 32) {
-            float best = -1.f;
-            int br = k;
-            for (int r = k + tid; r < n; r += 32) {
-                const float v = fabsf(A[r * LDP + k]);
-                if (v > best) {
-                    best = v;
-                    br = r;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-                if (ob > best || (ob == best && orr < br)) {
-                    best = ob;
-                    br = orr;
-                }
-            }
-            if (tid == 0) perm[k] = br;
-        }
-        __syncthreads();
-        const int br = perm[k];
-        if (br != k)
-            for (int c = tid; c < n; c += blockDim.x) {
-                const float t = A[k * LDP + c];
-                A[k * LDP + c] = A[br * LDP + c];
-                A[br * LDP + c] = t;
-            }
-        __syncthreads();
-        float p = A[k * LDP + k];
-        if (fabsf(p) < 1e-30f) p = p >= 0.f ? 1e-30f : -1e-30f;
-        const float pinv = 1.f / p;
-        for (int r = k + 1 + tid; r < n; r += blockDim.x) A[r * LDP + k] *= pinv;
-        __syncthreads();
-        if (tid == 0) A[k * LDP + k] = p;
-        const int m = n - k - 1;
-        for (int idx = tid; idx < m * m; idx += blockDim.x) {
-            const int r = k + 1 + idx / m, c = k + 1 + idx % m;
-            A[r * LDP + c] -= A[r * LDP + k] * A[k * LDP + c];
-        }
-        __syncthreads();
-    }
-}
-
-
 // Kernel 1: estimates of the eigenvalues of B x = lambda T x closest to zero, in FP32
-// (they serve only as shifts): shift-and-invert Arnoldi on K = (B - sigma T)^{-1} T with
-// sigma = -1e-4 max|B| (K's dominant eigenvalues theta = 1/(lambda - sigma) belong to
-// the lambda of smallest modulus), KRY steps with classical Gram-Schmidt applied twice,
-// the eigenvalues of the small Hessenberg matrix by the Francis QR iteration, then
-// lambda = sigma + 1/theta.  Selection: eigenvalues with Im >= 0 (a complex pair is
-// represented by its member with positive imaginary part) in order of |lambda|; a real
+// (they serve only as shifts).  sigma = -1e-4 max|B|; K = (B - sigma T)^{-1} T is formed
+// explicitly (its dominant eigenvalues theta = 1 / (lambda - sigma) belong to the lambda
+// of smallest modulus); KRY Arnoldi steps on K with classical Gram-Schmidt applied twice
+// (whole block: 4 threads per row for K v, one warp per basis vector for the inner
+// products); the eigenvalues of the Hessenberg matrix by the Francis QR iteration (one
+// warp); lambda = sigma + 1 / theta.  Selection: eigenvalues with Im >= 0 (a complex pair
+// is represented by its member with positive imaginary part) in order of |lambda|; a real
 // one takes one vector column, a pair two (Re v, Im v), until k_ev columns are filled.
-// sel[3q + {0,1,2}] = (Re, Im, first column); info = {columns, selected, status, steps}.
+// sel[3q + {0,1,2}] = (Re, Im, first column); info = {columns, selected, status, steps,
+// cycles of the phases}.
 constexpr int KRY = 32;
 __global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __restrict__ Bg,
                                                        const double* __restrict__ Tg, int k_ev,
                                                        double* __restrict__ sel, double* __restrict__ lam,
                                                        int32_t* __restrict__ kind, int* __restrict__ info) {
-    __shared__ float A[CN * LDP], Tm[CN * LDP];
+    __shared__ float A[CN * LDP], Km[CN * LDP];
     __shared__ float Vk[(KRY + 1) * CN];
-    __shared__ float w[CN], hcol[KRY + 1];
+    __shared__ float Hs[KRY * KRY];
+    __shared__ float part[4 * CN];
+    __shared__ float w[CN], hq[KRY + 1], hcol[KRY + 1], dinv[CN];
+    __shared__ float wr[CN], wi[CN], red[CT / 32], s_nn;
     __shared__ int perm[CN];
-    __shared__ float wr[CN], wi[CN], red[CT / 32];
     const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+    const long long c_start = clock64();
     // sigma from the largest entry of B
     float mx = 0.f;
-    for (int idx = tid; idx < n * n; idx += blockDim.x) mx = fmaxf(mx, fabsf((float)Bg[idx]));
+    for (int idx = tid; idx < n * n; idx += CT) mx = fmaxf(mx, fabsf((float)Bg[idx]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) red[wid] = mx;
     __syncthreads();
     mx = 0.f;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) mx = fmaxf(mx, red[q]);
+    for (int q = 0; q < CT / 32; ++q) mx = fmaxf(mx, red[q]);
     const float sigma = -1e-4f * fmaxf(mx, 1e-30f);
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-        const int r = idx / n, c = idx % n;
+    for (int idx = tid; idx < n * n; idx += CT) {
+        const int r = idx / n, c = idx - r * n;
         const float t = (float)Tg[idx];
-        Tm[r * LDP + c] = t;
+        Km[r * LDP + c] = t;
         A[r * LDP + c] = (float)Bg[idx] - sigma * t;
     }
     __syncthreads();
-    blu_factor_f32(A, n, perm);
+    blu_factor<float>(A, n, perm, dinv, 1e-30f);
+    blu_solve<float>(A, n, perm, dinv, Km, n, LDP);  // Km = (B - sigma T)^{-1} T
+    const long long c_lu = clock64();
     const int kd = n < KRY ? n : KRY;
-    if (tid >= 32) return;  // the Arnoldi process runs in one warp
-    // v_0: fixed generic start, unit norm
-    {
+    if (tid < n) {  // v_0: fixed generic start
+        Vk[tid] = 1.f + (float)tid / (float)n;
+    }
+    for (int idx = tid; idx < KRY * KRY; idx += CT) Hs[idx] = 0.f;
+    __syncthreads();
+    if (wid == 0) {
         float nn = 0.f;
-        for (int r = lane; r < n; r += 32) {
-            const float v = 1.f + (float)r / (float)n;
-            Vk[r] = v;
-            nn += v * v;
-        }
+        for (int r = lane; r < n; r += 32) nn += Vk[r] * Vk[r];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-        nn = rsqrtf(nn);
-        for (int r = lane; r < n; r += 32) Vk[r] *= nn;
-        __syncwarp();
+        if (lane == 0) s_nn = rsqrtf(nn);
     }
-    __shared__ float Hs[KRY * KRY];
-    for (int idx = lane; idx < KRY * KRY; idx += 32) Hs[idx] = 0.f;
+    __syncthreads();
+    if (tid < n) Vk[tid] *= s_nn;
+    __syncthreads();
+    const int row = tid & (CN - 1), quarter = tid >> 6;  // K v: 4 threads per row
     int kk = kd;
     for (int k = 0; k < kd; ++k) {
         const float* vk = Vk + k * CN;
-        // w = T v_k
-        for (int r = lane; r < n; r += 32) {
-            float sacc = 0.f;
-            for (int c = 0; c < n; ++c) sacc += Tm[r * LDP + c] * vk[c];
-            w[r] = sacc;
+        if (row < n) {
+            float acc = 0.f;
+            const int c1 = min(n, 16 * quarter + 16);
+            for (int c = 16 * quarter; c < c1; ++c) acc += Km[row * LDP + c] * vk[c];
+            part[quarter * CN + row] = acc;
         }
-        __syncwarp();
-        // w <- (B - sigma T)^{-1} w
-        for (int q = 0; q < n; ++q) {
-            const int pq = perm[q];
-            if (pq != q && lane == 0) {
-                const float t = w[q];
-                w[q] = w[pq];
-                w[pq] = t;
-            }
-            __syncwarp();
-        }
-        for (int q = 0; q < n; ++q) {
-            const float yq = w[q];
-            for (int r = q + 1 + lane; r < n; r += 32) w[r] -= A[r * LDP + q] * yq;
-            __syncwarp();
-        }
-        for (int q = n - 1; q >= 0; --q) {
-            if (lane == 0) w[q] /= A[q * LDP + q];
-            __syncwarp();
-            const float yq = w[q];
-            for (int r = lane; r < q; r += 32) w[r] -= A[r * LDP + q] * yq;
-            __syncwarp();
-        }
-        // classical Gram-Schmidt, twice
-        for (int q = 0; q <= k; ++q) hcol[q] = 0.f;
-        __syncwarp();
+        __syncthreads();
+        if (tid < n) w[tid] = (part[tid] + part[CN + tid]) + (part[2 * CN + tid] + part[3 * CN + tid]);
+        if (tid <= k) hcol[tid] = 0.f;
+        __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {
-            for (int q = 0; q <= k; ++q) {
+            for (int q = wid; q <= k; q += CT / 32) {
                 float d = 0.f;
                 for (int r = lane; r < n; r += 32) d += Vk[q * CN + r] * w[r];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                for (int r = lane; r < n; r += 32) w[r] -= d * Vk[q * CN + r];
-                if (lane == 0) hcol[q] += d;
-                __syncwarp();
+                if (lane == 0) hq[q] = d;
             }
+            __syncthreads();
+            if (tid < n) {
+                float acc = 0.f;
+                for (int q = 0; q <= k; ++q) acc += Vk[q * CN + tid] * hq[q];
+                w[tid] -= acc;
+            }
+            if (tid <= k) hcol[tid] += hq[tid];
+            __syncthreads();
         }
-        float nn = 0.f;
-        for (int r = lane; r < n; r += 32) nn += w[r] * w[r];
+        if (wid == 0) {
+            float nn = 0.f;
+            for (int r = lane; r < n; r += 32) nn += w[r] * w[r];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-        nn = sqrtf(nn);
-        for (int q = lane; q <= k; q += 32) Hs[q * KRY + k] = hcol[q];
-        if (k + 1 < kd && lane == 0) Hs[(k + 1) * KRY + k] = nn;
-        __syncwarp();
-        if (!(nn > 1e-6f * fabsf(hcol[0]) + 1e-30f)) {  // invariant subspace found
+            for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+            if (lane == 0) s_nn = sqrtf(nn);
+        }
+        __syncthreads();
+        const float nn = s_nn;
+        if (tid <= k) Hs[tid * KRY + k] = hcol[tid];
+        if (k + 1 < kd && tid == 0) Hs[(k + 1) * KRY + k] = nn;
+        if (!(nn > 1e-6f * fabsf(hcol[0]) + 1e-30f)) {  // invariant subspace found (uniform)
             kk = k + 1;
             break;
         }
-        if (k + 1 < kd)
-            for (int r = lane; r < n; r += 32) Vk[(k + 1) * CN + r] = w[r] / nn;
-        __syncwarp();
+        if (k + 1 < kd && tid < n) Vk[(k + 1) * CN + tid] = w[tid] / nn;
+        __syncthreads();
     }
-    // eigenvalues of the kk x kk Hessenberg matrix (stored with the padded row stride)
+    __syncthreads();
+    const long long c_arn = clock64();
+    if (tid >= 32) return;
+    // eigenvalues of the kk x kk Hessenberg matrix (copied to the padded stride)
     for (int idx = lane; idx < kk * kk; idx += 32) {
         const int r = idx / kk, c = idx % kk;
-        Tm[r * LDP + c] = Hs[r * KRY + c];
+        A[r * LDP + c] = Hs[r * KRY + c];
     }
     __syncwarp();
     int steps = 0;
-    const int st = hqr_f32(Tm, kk, wr, wi, &steps);
+    const int st = hqr_f32(A, kk, wr, wi, &steps);
     __syncwarp();
+    const long long c_qr = clock64();
     if (lane == 0) {
         // lambda = sigma + 1 / theta
         for (int q = 0; q < kk; ++q) {
@@ -461,38 +489,61 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __re
         info[1] = ns;
         info[2] = st;
         info[3] = steps;
+        info[4] = (int)(c_lu - c_start);  // phase durations in SM cycles (diagnostics)
+        info[5] = (int)(c_arn - c_lu);
+        info[6] = (int)(c_qr - c_arn);
+        info[7] = (int)(clock64() - c_qr);
     }
 }
 
 // ---------------------------------------------------------------- complex inverse iteration
-// Kernel 2, one block per selected eigenvalue: LU of the pencil (B - sigma T) in
-// complex FP64 with sigma the FP32 estimate; four steps of inverse iteration
-// v <- (B - sigma T)^{-1} T v from a fixed positive start; the Rayleigh-type quotient
-// lambda = v^H B v / v^H T v (Algorithm 3's update, in complex form); and the phase that
-// makes <w, v> real and positive (w_i = i + 1) with unit 2-norm.
+// Kernel 2, one block per selected eigenvalue, in arithmetic F (double, or float for the
+// mixed-precision setup): LU of the pencil (B - sigma T) in complex arithmetic with sigma
+// the FP32 estimate; four steps of inverse iteration v <- (B - sigma T)^{-1} T v from a
+// fixed positive start; the Rayleigh-type quotient lambda = v^H B v / v^H T v (Algorithm
+// 3's update, in complex form, accumulated in FP64); and the phase that makes <w, v> real
+// and positive (w_i = i + 1) with unit 2-norm.
+template <typename F>
+__device__ __forceinline__ F pivot_tiny() {
+    if constexpr (sizeof(F) == 8)
+        return F(1e-300);
+    else
+        return F(1e-36f);
+}
+
+template <typename F>
 __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __restrict__ Bg,
                                                       const double* __restrict__ Tg, const double* __restrict__ sel,
-                                                      double* __restrict__ V, double* __restrict__ lam) {
-    extern __shared__ double sm[];
-    double* Ar = sm;
-    double* Ai = sm + CN * LDP;
-    __shared__ double vr[CN], vi[CN], tr[CN], ti[CN], red[4 * (CT / 32)];
+                                                      double* __restrict__ V, double* __restrict__ lam,
+                                                      int* __restrict__ cycles) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    F* Ar = reinterpret_cast<F*>(smraw);
+    F* Ai = Ar + CN * LDP;
+    F* Bm = Ai + CN * LDP;
+    F* Tm = Bm + CN * LDP;
+    __shared__ F vr[CN], vi[CN], tr[CN], ti[CN], dr[CN], di[CN], pre[4 * CN], pim[4 * CN];
+    __shared__ double red[4 * (CT / 32)], s_nrm;
     __shared__ int perm[CN];
-    const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
-    const double sr = sel[3 * blockIdx.x], si = sel[3 * blockIdx.x + 1];
+    const long long c_start = clock64();
+    const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5, ty = tid >> 4, tx = tid & 15;
+    const F sr = (F)sel[3 * blockIdx.x], si = (F)sel[3 * blockIdx.x + 1];
     const int col = (int)sel[3 * blockIdx.x + 2];
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-        const double t = Tg[idx];
-        Ar[(idx / n) * LDP + idx % n] = Bg[idx] - sr * t;
-        Ai[(idx / n) * LDP + idx % n] = -si * t;
+    for (int idx = tid; idx < n * n; idx += CT) {
+        const int r = idx / n, c = idx - r * n;
+        const F b = (F)Bg[idx], t = (F)Tg[idx];
+        Bm[r * LDP + c] = b;
+        Tm[r * LDP + c] = t;
+        Ar[r * LDP + c] = b - sr * t;
+        Ai[r * LDP + c] = -si * t;
     }
     __syncthreads();
+    // complex LU with partial pivoting on |Re| + |Im|; dr + i di = 1 / u_kk
     for (int k = 0; k < n; ++k) {
         if (tid < 32) {
-            double best = -1.0;
+            F best = F(-1);
             int br = k;
             for (int r = k + tid; r < n; r += 32) {
-                const double m = fabs(Ar[r * LDP + k]) + fabs(Ai[r * LDP + k]);
+                const F m = absv(Ar[r * LDP + k]) + absv(Ai[r * LDP + k]);
                 if (m > best) {
                     best = m;
                     br = r;
@@ -500,145 +551,197 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const F ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int orr = __shfl_xor_sync(0xffffffffu, br, o);
                 if (ob > best || (ob == best && orr < br)) {
                     best = ob;
                     br = orr;
                 }
             }
-            if (tid == 0) perm[k] = br;
+            if (tid == 0) {  // the pivot's reciprocal, formed once
+                perm[k] = br;
+                F pr = Ar[br * LDP + k], pi = Ai[br * LDP + k];
+                const F tiny = pivot_tiny<F>();
+                if (absv(pr) + absv(pi) < tiny) {
+                    pr = tiny;
+                    pi = F(0);
+                    Ar[br * LDP + k] = pr;
+                    Ai[br * LDP + k] = pi;
+                }
+                // 1 / (pr + i pi) without squaring (Smith's method: no underflow in FP32)
+                if (absv(pr) >= absv(pi)) {
+                    const F t = pi / pr, d = F(1) / (pr + pi * t);
+                    dr[k] = d;
+                    di[k] = -t * d;
+                } else {
+                    const F t = pr / pi, d = F(1) / (pr * t + pi);
+                    dr[k] = t * d;
+                    di[k] = -d;
+                }
+            }
         }
         __syncthreads();
         const int br = perm[k];
-        if (br != k)
-            for (int c = tid; c < n; c += blockDim.x) {
-                double t = Ar[k * LDP + c];
+        if (br != k) {
+            for (int c = tid; c < n; c += CT) {
+                F t = Ar[k * LDP + c];
                 Ar[k * LDP + c] = Ar[br * LDP + c];
                 Ar[br * LDP + c] = t;
                 t = Ai[k * LDP + c];
                 Ai[k * LDP + c] = Ai[br * LDP + c];
                 Ai[br * LDP + c] = t;
             }
-        __syncthreads();
-        double pr = Ar[k * LDP + k], pi = Ai[k * LDP + k];
-        if (fabs(pr) + fabs(pi) < 1e-300) {
-            pr = 1e-300;
-            pi = 0.0;
+            __syncthreads();
         }
-        const double inv = 1.0 / (pr * pr + pi * pi);
-        const double qr_ = pr * inv, qi_ = -pi * inv;  // 1 / pivot
-        for (int r = k + 1 + tid; r < n; r += blockDim.x) {
-            const double ar = Ar[r * LDP + k], ai = Ai[r * LDP + k];
+        const F qr_ = dr[k], qi_ = di[k];  // 1 / pivot
+        F ur[4], ui[4];  // rank-one update, a 4 x 4 register tile per thread
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = k + 1 + tx + 16 * j;
+            ur[j] = c < n ? Ar[k * LDP + c] : F(0);
+            ui[j] = c < n ? Ai[k * LDP + c] : F(0);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = k + 1 + ty + 16 * i;
+            if (r < n) {
+                const F ar = Ar[r * LDP + k], ai = Ai[r * LDP + k];
+                const F lr = ar * qr_ - ai * qi_, li = ar * qi_ + ai * qr_;
+                F xr[4], xi[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = k + 1 + tx + 16 * j;
+                    xr[j] = c < n ? Ar[r * LDP + c] : F(0);
+                    xi[j] = c < n ? Ai[r * LDP + c] : F(0);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = k + 1 + tx + 16 * j;
+                    if (c < n) {
+                        Ar[r * LDP + c] = xr[j] - (lr * ur[j] - li * ui[j]);
+                        Ai[r * LDP + c] = xi[j] - (lr * ui[j] + li * ur[j]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int r = k + 1 + tid; r < n; r += CT) {
+            const F ar = Ar[r * LDP + k], ai = Ai[r * LDP + k];
             Ar[r * LDP + k] = ar * qr_ - ai * qi_;
             Ai[r * LDP + k] = ar * qi_ + ai * qr_;
         }
-        __syncthreads();
-        if (tid == 0) {
-            Ar[k * LDP + k] = pr;
-            Ai[k * LDP + k] = pi;
-        }
-        const int m = n - k - 1;
-        for (int idx = tid; idx < m * m; idx += blockDim.x) {
-            const int r = k + 1 + idx / m, c = k + 1 + idx % m;
-            const double lr = Ar[r * LDP + k], li = Ai[r * LDP + k];
-            const double ur = Ar[k * LDP + c], ui = Ai[k * LDP + c];
-            Ar[r * LDP + c] -= lr * ur - li * ui;
-            Ai[r * LDP + c] -= lr * ui + li * ur;
-        }
-        __syncthreads();
-    }
-    for (int r = tid; r < n; r += blockDim.x) {
-        vr[r] = 1.0 + (double)r / (double)n;
-        vi[r] = 0.0;
     }
     __syncthreads();
+    for (int r = ty; r < n; r += 16)  // rows of U times 1 / u_rr: a unit upper factor
+        for (int c = r + 1 + tx; c < n; c += 16) {
+            const F ur = Ar[r * LDP + c], ui = Ai[r * LDP + c];
+            Ar[r * LDP + c] = ur * dr[r] - ui * di[r];
+            Ai[r * LDP + c] = ur * di[r] + ui * dr[r];
+        }
+    if (tid < n) {
+        vr[tid] = F(1) + (F)tid / (F)n;
+        vi[tid] = F(0);
+    }
+    __syncthreads();
+    const long long c_lu = clock64();
+    const int row = tid & (CN - 1), quarter = tid >> 6;
     for (int it = 0; it < 4; ++it) {
-        // t = T v (rows in parallel)
-        for (int r = tid; r < n; r += blockDim.x) {
-            double a = 0.0, b = 0.0;
-            for (int c = 0; c < n; ++c) {
-                const double t = Tg[r * n + c];
+        // t = T v, 4 threads per row
+        if (row < n) {
+            F a = F(0), b = F(0);
+            const int c1 = min(n, 16 * quarter + 16);
+            for (int c = 16 * quarter; c < c1; ++c) {
+                const F t = Tm[row * LDP + c];
                 a += t * vr[c];
                 b += t * vi[c];
             }
-            tr[r] = a;
-            ti[r] = b;
+            pre[quarter * CN + row] = a;
+            pim[quarter * CN + row] = b;
         }
         __syncthreads();
-        if (tid < 32) {  // one warp: column-oriented substitutions on t
+        if (tid < n) {
+            tr[tid] = (pre[tid] + pre[CN + tid]) + (pre[2 * CN + tid] + pre[3 * CN + tid]);
+            ti[tid] = (pim[tid] + pim[CN + tid]) + (pim[2 * CN + tid] + pim[3 * CN + tid]);
+        }
+        __syncthreads();
+        if (tid == 0)
             for (int k = 0; k < n; ++k) {
                 const int pk = perm[k];
-                if (pk != k && lane == 0) {
-                    double t = tr[k];
+                if (pk != k) {
+                    F t = tr[k];
                     tr[k] = tr[pk];
                     tr[pk] = t;
                     t = ti[k];
                     ti[k] = ti[pk];
                     ti[pk] = t;
                 }
-                __syncwarp();
             }
-            for (int q = 0; q < n; ++q) {
-                const double yr = tr[q], yi = ti[q];
-                for (int r = q + 1 + lane; r < n; r += 32) {
-                    tr[r] -= Ar[r * LDP + q] * yr - Ai[r * LDP + q] * yi;
-                    ti[r] -= Ar[r * LDP + q] * yi + Ai[r * LDP + q] * yr;
-                }
-                __syncwarp();
+        __syncthreads();
+        for (int q = 0; q + 1 < n; ++q) {  // unit lower
+            const int r = q + 1 + tid;
+            if (r < n) {
+                const F yr = tr[q], yi = ti[q], lr = Ar[r * LDP + q], li = Ai[r * LDP + q];
+                tr[r] -= lr * yr - li * yi;
+                ti[r] -= lr * yi + li * yr;
             }
-            for (int q = n - 1; q >= 0; --q) {
-                if (lane == 0) {
-                    const double ur = Ar[q * LDP + q], ui = Ai[q * LDP + q];
-                    const double d = 1.0 / (ur * ur + ui * ui);
-                    const double a = tr[q], b = ti[q];
-                    tr[q] = (a * ur + b * ui) * d;
-                    ti[q] = (b * ur - a * ui) * d;
-                }
-                __syncwarp();
-                const double yr = tr[q], yi = ti[q];
-                for (int r = lane; r < q; r += 32) {
-                    tr[r] -= Ar[r * LDP + q] * yr - Ai[r * LDP + q] * yi;
-                    ti[r] -= Ar[r * LDP + q] * yi + Ai[r * LDP + q] * yr;
-                }
-                __syncwarp();
+            __syncthreads();
+        }
+        if (tid < n) {
+            const F a = tr[tid], b = ti[tid];
+            tr[tid] = a * dr[tid] - b * di[tid];
+            ti[tid] = a * di[tid] + b * dr[tid];
+        }
+        __syncthreads();
+        for (int q = n - 1; q > 0; --q) {  // unit upper
+            if (tid < q) {
+                const F yr = tr[q], yi = ti[q], ur = Ar[tid * LDP + q], ui = Ai[tid * LDP + q];
+                tr[tid] -= ur * yr - ui * yi;
+                ti[tid] -= ur * yi + ui * yr;
             }
+            __syncthreads();
+        }
+        if (wid == 0) {
             double nn = 0.0;
-            for (int r = lane; r < n; r += 32) nn += tr[r] * tr[r] + ti[r] * ti[r];
-            nn = 1.0 / sqrt(warp_sum(nn));
-            for (int r = lane; r < n; r += 32) {
-                vr[r] = tr[r] * nn;
-                vi[r] = ti[r] * nn;
-            }
-            __syncwarp();
+            for (int r = lane; r < n; r += 32) nn += (double)tr[r] * tr[r] + (double)ti[r] * ti[r];
+            nn = warp_sum(nn);
+            if (lane == 0) s_nrm = 1.0 / sqrt(nn);
+        }
+        __syncthreads();
+        if (tid < n) {
+            vr[tid] = (F)(tr[tid] * s_nrm);
+            vi[tid] = (F)(ti[tid] * s_nrm);
         }
         __syncthreads();
     }
-    // lambda = v^H B v / v^H T v
-    double br_ = 0.0, bi_ = 0.0, tr_ = 0.0, ti_ = 0.0;
-    for (int r = tid; r < n; r += blockDim.x) {
-        double wbr = 0.0, wbi = 0.0, wtr = 0.0, wti = 0.0;
-        for (int c = 0; c < n; ++c) {
-            const double b = Bg[r * n + c], t = Tg[r * n + c];
-            wbr += b * vr[c];
-            wbi += b * vi[c];
-            wtr += t * vr[c];
-            wti += t * vi[c];
+    // lambda = v^H B v / v^H T v: (B v)_r and (T v)_r with 4 threads per row
+    {
+        double br_ = 0.0, bi_ = 0.0, tr_ = 0.0, ti_ = 0.0;
+        if (row < n) {
+            F wbr = F(0), wbi = F(0), wtr = F(0), wti = F(0);
+            const int c1 = min(n, 16 * quarter + 16);
+            for (int c = 16 * quarter; c < c1; ++c) {
+                const F b = Bm[row * LDP + c], t = Tm[row * LDP + c];
+                wbr += b * vr[c];
+                wbi += b * vi[c];
+                wtr += t * vr[c];
+                wti += t * vi[c];
+            }
+            const double xr = vr[row], xi = vi[row];
+            br_ = xr * wbr + xi * wbi;
+            bi_ = xr * wbi - xi * wbr;
+            tr_ = xr * wtr + xi * wti;
+            ti_ = xr * wti - xi * wtr;
         }
-        br_ += vr[r] * wbr + vi[r] * wbi;
-        bi_ += vr[r] * wbi - vi[r] * wbr;
-        tr_ += vr[r] * wtr + vi[r] * wti;
-        ti_ += vr[r] * wti - vi[r] * wtr;
-    }
-    br_ = warp_sum(br_);
-    bi_ = warp_sum(bi_);
-    tr_ = warp_sum(tr_);
-    ti_ = warp_sum(ti_);
-    if (lane == 0) {
-        red[4 * wid] = br_;
-        red[4 * wid + 1] = bi_;
-        red[4 * wid + 2] = tr_;
-        red[4 * wid + 3] = ti_;
+        br_ = warp_sum(br_);
+        bi_ = warp_sum(bi_);
+        tr_ = warp_sum(tr_);
+        ti_ = warp_sum(ti_);
+        if (lane == 0) {
+            red[4 * wid] = br_;
+            red[4 * wid + 1] = bi_;
+            red[4 * wid + 2] = tr_;
+            red[4 * wid + 3] = ti_;
+        }
     }
     __syncthreads();
     if (tid >= 32) return;
@@ -652,52 +755,79 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
     const double sa = hypot(sr2, si2);
     const double cr = sa > 0.0 ? sr2 / sa : 1.0, ci = sa > 0.0 ? -si2 / sa : 0.0;  // conj(s)/|s|
     double nn = 0.0;
-    for (int r = lane; r < n; r += 32) {
-        const double a = vr[r] * cr - vi[r] * ci, b = vr[r] * ci + vi[r] * cr;
-        vr[r] = a;
-        vi[r] = b;
-        nn += a * a + b * b;
+    double ar[2], ai[2];
+    for (int q = 0, r = lane; q < 2; ++q, r += 32) {
+        ar[q] = ai[q] = 0.0;
+        if (r < n) {
+            ar[q] = (double)vr[r] * cr - (double)vi[r] * ci;
+            ai[q] = (double)vr[r] * ci + (double)vi[r] * cr;
+            nn += ar[q] * ar[q] + ai[q] * ai[q];
+        }
     }
     nn = 1.0 / sqrt(warp_sum(nn));
-    for (int r = lane; r < n; r += 32) {
-        V[(int64_t)col * n + r] = vr[r] * nn;
-        if (si != 0.0) V[(int64_t)(col + 1) * n + r] = vi[r] * nn;
-    }
+    for (int q = 0, r = lane; q < 2; ++q, r += 32)
+        if (r < n) {
+            V[(int64_t)col * n + r] = ar[q] * nn;
+            if (si != F(0)) V[(int64_t)(col + 1) * n + r] = ai[q] * nn;
+        }
     if (lane == 0) {
         double nbr = 0.0, nbi = 0.0, ntr = 0.0, nti = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            nbr += red[4 * w];
-            nbi += red[4 * w + 1];
-            ntr += red[4 * w + 2];
-            nti += red[4 * w + 3];
+        for (int q = 0; q < CT / 32; ++q) {
+            nbr += red[4 * q];
+            nbi += red[4 * q + 1];
+            ntr += red[4 * q + 2];
+            nti += red[4 * q + 3];
         }
         // Re of (nbr + i nbi) / (ntr + i nti)
         double lre = (nbr * ntr + nbi * nti) / (ntr * ntr + nti * nti);
         if (col == 0) lre = 0.0;  // the state vector's eigenvalue is exactly zero
         lam[col] = lre;
-        if (si != 0.0) lam[col + 1] = lre;
+        if (si != F(0)) lam[col + 1] = lre;
+        cycles[2 * blockIdx.x] = (int)(c_lu - c_start);  // diagnostics
+        cycles[2 * blockIdx.x + 1] = (int)(clock64() - c_lu);
     }
 }
 
 int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_lam, double* d_V, int32_t* d_kind,
-               cudaStream_t s) {
+               bool fp32_vectors, cudaStream_t s) {
     BAMG_REQUIRE(n >= 1 && n <= CN, BAMG_EINVAL, "coarse_eig: coarsest order must be 1..64");
     BAMG_REQUIRE(k_ev >= 1 && k_ev <= 16, BAMG_EINVAL, "coarse_eig: 1 <= k_ev <= 16");
-    static bool attr = false;
-    const size_t smem = 2 * CN * LDP * sizeof(double);
+    static std::atomic<bool> attr{false};  // idempotent; several host threads may get here
+    const size_t smem64 = 4 * CN * LDP * sizeof(double), smem32 = 4 * CN * LDP * sizeof(float);
     if (!attr) {
-        BAMG_CK(cudaFuncSetAttribute(k_coarse_eigvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BAMG_CK(cudaFuncSetAttribute(k_coarse_eigvec<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem64));
+        BAMG_CK(cudaFuncSetAttribute(k_coarse_eigvec<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem32));
         attr = true;
     }
     TmpBuf<double> sel(3 * (k_ev + 1), s);
-    TmpBuf<int> info(4, s);
+    TmpBuf<int> info(8, s);
     BAMG_LAUNCH(k_coarse_eigvals, 1, CT, 0, s, n, dB, dT, k_ev, sel.get(), d_lam, d_kind, info.get());
-    int h[4] = {0, 0, 0, 0};
+    int h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     BAMG_CK(cudaMemcpyAsync(h, info.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
     BAMG_CK(cudaStreamSynchronize(s));
-    if (getenv("BAMG_DEBUG")) fprintf(stderr, "[bamg] coarse QR: n=%d double-shift steps=%d status=%d\n", n, h[3], h[2]);
+    const bool dbg = getenv("BAMG_DEBUG") != nullptr;
+    if (dbg)
+        fprintf(stderr,
+                "[bamg] coarse eigenvalues: n=%d QR double-shift steps=%d status=%d cycles lu+K=%d arnoldi=%d qr=%d "
+                "tail=%d\n",
+                n, h[3], h[2], h[4], h[5], h[6], h[7]);
     if (h[2] != 0) return BAMG_ENUMERIC;
-    if (h[1] > 0) BAMG_LAUNCH(k_coarse_eigvec, h[1], CT, smem, s, n, dB, dT, sel.get(), d_V, d_lam);
+    if (h[1] > 0) {
+        TmpBuf<int> cyc(2 * h[1], s);
+        if (fp32_vectors)
+            BAMG_LAUNCH(k_coarse_eigvec<float>, h[1], CT, smem32, s, n, dB, dT, sel.get(), d_V, d_lam, cyc.get());
+        else
+            BAMG_LAUNCH(k_coarse_eigvec<double>, h[1], CT, smem64, s, n, dB, dT, sel.get(), d_V, d_lam, cyc.get());
+        if (dbg) {
+            int hc[64] = {0};
+            BAMG_CK(cudaMemcpyAsync(hc, cyc.get(), sizeof(int) * 2 * h[1], cudaMemcpyDeviceToHost, s));
+            BAMG_CK(cudaStreamSynchronize(s));
+            fprintf(stderr, "[bamg] coarse eigenvectors (%s): %d blocks, cycles lu=%d iterate=%d\n",
+                    fp32_vectors ? "fp32" : "fp64", h[1], hc[0], hc[1]);
+        }
+    }
     return h[0];
 }
 
@@ -706,74 +836,100 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
 // inverse iteration on the LU of B with a pivot floor); with z = 1/sqrt(n) the bordered
 // matrix M = B + z y^T is nonsingular and B^+ = M^{-1} (I - z z^T): M w = (I - z z^T) b
 // forces y^T w = 0, so w is the solution of B w = (I - z z^T) b orthogonal to null(B).
+// Every block factors B and M (the factorisations are identical) and solves its own
+// PINV_COLS columns of (I - z z^T).  Arithmetic F: FP64, or FP32 for the mixed-precision
+// V-cycle, which applies B^+ in FP32.
+constexpr int PINV_COLS = 8;
+template <typename F>
 __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restrict__ Bg, double* __restrict__ Pg,
                                                     int* __restrict__ info) {
-    extern __shared__ double sm[];
-    double* A = sm;
-    double* R = sm + CN * LDP;
-    __shared__ double y[CN], red[CT / 32];
+    __shared__ F A[CN * LDP];
+    __shared__ F R[CN * PINV_COLS];
+    __shared__ F y[CN], dinv[CN], red[CT / 32], s_nrm;
     __shared__ int perm[CN];
     const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
-    double mx = 0.0;
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-        A[(idx / n) * LDP + idx % n] = Bg[idx];
-        mx = fmax(mx, fabs(Bg[idx]));
+    const long long c_start = clock64();
+    const int c0 = blockIdx.x * PINV_COLS, mc = min(PINV_COLS, n - c0);
+    F mx = F(0);
+    for (int idx = tid; idx < n * n; idx += CT) {
+        const int r = idx / n, c = idx - r * n;
+        const F b = (F)Bg[idx];
+        A[r * LDP + c] = b;
+        mx = mx > absv(b) ? mx : absv(b);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const F t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = mx > t ? mx : t;
+    }
     if (lane == 0) red[wid] = mx;
     __syncthreads();
-    mx = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
-    __syncthreads();
-    blu_factor(A, n, perm, 1e-14 * fmax(mx, 1e-300));
-    for (int r = tid; r < n; r += blockDim.x) R[r] = 1.0;
+    mx = F(0);
+    for (int q = 0; q < CT / 32; ++q) mx = mx > red[q] ? mx : red[q];
+    const F rel_floor = sizeof(F) == 8 ? F(1e-14) : F(1e-6f);
+    blu_factor<F>(A, n, perm, dinv, rel_floor * (mx > F(0) ? mx : F(1)));
+    if (tid < n) y[tid] = F(1);
     __syncthreads();
     for (int it = 0; it < 2; ++it) {
-        blu_solve(A, n, perm, R, 1);
-        if (tid < 32) {
+        blu_solve<F>(A, n, perm, dinv, y, 1, 1);
+        if (wid == 0) {
             double nn = 0.0;
-            for (int r = lane; r < n; r += 32) nn += R[r] * R[r];
-            nn = sqrt(warp_sum(nn));
-            for (int r = lane; r < n; r += 32) R[r] /= nn;
+            for (int r = lane; r < n; r += 32) nn += (double)y[r] * y[r];
+            nn = warp_sum(nn);
+            if (lane == 0) s_nrm = (F)(1.0 / sqrt(nn));
         }
         __syncthreads();
+        if (tid < n) y[tid] *= s_nrm;
+        __syncthreads();
     }
-    for (int r = tid; r < n; r += blockDim.x) y[r] = R[r];
-    __syncthreads();
-    const double zs = 1.0 / sqrt((double)n);
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-        const int r = idx / n, c = idx % n;
-        A[r * LDP + c] = Bg[idx] + zs * y[c];
-        R[idx] = (r == c ? 1.0 : 0.0) - 1.0 / (double)n;
+    const F zs = (F)(1.0 / sqrt((double)n)), ninv = (F)(1.0 / (double)n);
+    for (int idx = tid; idx < n * n; idx += CT) {
+        const int r = idx / n, c = idx - r * n;
+        A[r * LDP + c] = (F)Bg[idx] + zs * y[c];
+    }
+    for (int idx = tid; idx < n * mc; idx += CT) {
+        const int r = idx / mc, c = idx - r * mc;
+        R[r * mc + c] = (r == c0 + c ? F(1) : F(0)) - ninv;
     }
     __syncthreads();
-    blu_factor(A, n, perm, 1e-300);
-    blu_solve(A, n, perm, R, n);
+    const long long c_null = clock64();
+    blu_factor<F>(A, n, perm, dinv, pivot_tiny<F>());
+    const long long c_lu = clock64();
+    blu_solve<F>(A, n, perm, dinv, R, mc, mc);
+    const long long c_solve = clock64();
     int bad = 0;
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-        const double v = R[idx];
+    for (int idx = tid; idx < n * mc; idx += CT) {
+        const int r = idx / mc, c = idx - r * mc;
+        const double v = (double)R[idx];
         if (!(fabs(v) < INFINITY)) bad = 1;
-        Pg[idx] = v;
+        Pg[r * n + c0 + c] = v;
     }
     bad = __syncthreads_or(bad);
-    if (tid == 0) info[0] = bad;
+    if (tid == 0) {
+        info[4 * blockIdx.x] = bad;
+        info[4 * blockIdx.x + 1] = (int)(c_null - c_start);  // diagnostics: cycles per phase
+        info[4 * blockIdx.x + 2] = (int)(c_lu - c_null);
+        info[4 * blockIdx.x + 3] = (int)(c_solve - c_lu);
+    }
 }
 
-int coarse_pinv(int n, const double* dB, double* dP, cudaStream_t s) {
+int coarse_pinv(int n, const double* dB, double* dP, bool fp32, cudaStream_t s) {
     BAMG_REQUIRE(n >= 1 && n <= CN, BAMG_EINVAL, "coarse_pinv: coarsest order must be 1..64");
-    static bool attr = false;
-    const size_t smem = 2 * CN * LDP * sizeof(double);
-    if (!attr) {
-        BAMG_CK(cudaFuncSetAttribute(k_coarse_pinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
-    TmpBuf<int> info(1, s);
-    BAMG_LAUNCH(k_coarse_pinv, 1, CT, smem, s, n, dB, dP, info.get());
-    int h = 0;
-    BAMG_CK(cudaMemcpyAsync(&h, info.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    const int nb = (n + PINV_COLS - 1) / PINV_COLS;
+    TmpBuf<int> info(4 * nb, s);
+    if (fp32)
+        BAMG_LAUNCH(k_coarse_pinv<float>, nb, CT, 0, s, n, dB, dP, info.get());
+    else
+        BAMG_LAUNCH(k_coarse_pinv<double>, nb, CT, 0, s, n, dB, dP, info.get());
+    int h[4 * (CN / PINV_COLS)] = {0};
+    BAMG_CK(cudaMemcpyAsync(h, info.get(), sizeof(int) * 4 * nb, cudaMemcpyDeviceToHost, s));
     BAMG_CK(cudaStreamSynchronize(s));
-    return h ? BAMG_ENUMERIC : 0;
+    if (getenv("BAMG_DEBUG"))
+        fprintf(stderr, "[bamg] coarse pinv (%s): n=%d blocks=%d cycles null=%d lu=%d solve=%d\n", fp32 ? "fp32" : "fp64",
+                n, nb, h[1], h[2], h[3]);
+    for (int b = 0; b < nb; ++b)
+        if (h[4 * b]) return BAMG_ENUMERIC;
+    return 0;
 }
 
 }  // namespace bamg

@@ -94,12 +94,14 @@ int coarsen_cr(const MatView<T>& B, int level, uint64_t seed, double theta, int 
                uint8_t* cf, int32_t* cidx, int* nc_out, cudaStream_t s);
 
 // ------------------------------------------------------------------ k_coarse.cu
-// Eigenpairs of B x = lambda T x (dense FP64, n <= 64).  Returns the number of vector
+// Eigenpairs of B x = lambda T x (dense FP64 input, n <= 64); the eigenvectors are
+// refined in FP32 when fp32_vectors is set, else in FP64.  Returns the number of vector
 // columns written (<= k_ev + 1) or a negative status.
 int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_lam, double* d_V, int32_t* d_kind,
-               cudaStream_t s);
-// Minimal-norm inverse of the rank n-1 matrix B (dense FP64, row-major).
-int coarse_pinv(int n, const double* dB, double* dP, cudaStream_t s);
+               bool fp32_vectors, cudaStream_t s);
+// Minimal-norm inverse of the rank n-1 matrix B (dense FP64 in and out, row-major),
+// computed in FP32 arithmetic when fp32 is set, else in FP64.
+int coarse_pinv(int n, const double* dB, double* dP, bool fp32, cudaStream_t s);
 
 // ------------------------------------------------------------------ k_solve.cu
 template <typename T>

@@ -7,6 +7,9 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <numeric>
+#include <thread>
 #include <type_traits>
 
 #include "gmres_state.cuh"
@@ -15,8 +18,15 @@
 namespace bamg {
 
 static std::atomic<uint64_t> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-void count_launches(int64_t k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+static thread_local uint64_t t_launches = 0;  // this thread's share, for graph-capture bookkeeping
+void count_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
+void count_launches(int64_t k) {
+    g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed);
+    t_launches += (uint64_t)k;
+}
 static thread_local std::string g_err;
 void set_last_error(const std::string& m) { g_err = m; }
 cudaStream_t& alloc_stream() {
@@ -303,7 +313,8 @@ struct Solver : SolverBase {
             csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.tv.get(), Td.get(), s);
             Lc.lam.alloc(ldV);
             BAMG_CK(cudaMemsetAsync(Lc.lam.get(), 0, sizeof(double) * ldV, s));
-            const int nv = coarse_eig(nL, Bd.get(), Td.get(), o.k_ev, Lc.lam.get(), Vd.get(), kinds.get(), s);
+            const int nv = coarse_eig(nL, Bd.get(), Td.get(), o.k_ev, Lc.lam.get(), Vd.get(), kinds.get(),
+                                      std::is_same<T, float>::value, s);
             BAMG_REQUIRE(nv > 0, BAMG_ENUMERIC, "coarsest eigensolve did not converge");
             nvec = nv;
             for (int q = 0; q < nvec; ++q)
@@ -338,7 +349,8 @@ struct Solver : SolverBase {
             TmpBuf<double> Bd((size_t)nL * nL, s);
             csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.bv.get(), Bd.get(), s);
             pinv64.alloc((size_t)nL * nL);
-            BAMG_REQUIRE(coarse_pinv(nL, Bd.get(), pinv64.get(), s) == 0, BAMG_ENUMERIC, "singular coarsest factor");
+            BAMG_REQUIRE(coarse_pinv(nL, Bd.get(), pinv64.get(), std::is_same<T, float>::value, s) == 0, BAMG_ENUMERIC,
+                         "singular coarsest factor");
             pinvT.alloc((size_t)nL * nL);
             if constexpr (std::is_same<T, double>::value)
                 BAMG_CK(cudaMemcpyAsync(pinvT.get(), pinv64.get(), sizeof(double) * nL * nL, cudaMemcpyDeviceToDevice, s));
@@ -357,7 +369,7 @@ struct Solver : SolverBase {
         int h_err = 0;
         BAMG_CK(cudaMemcpyAsync(&h_err, ls_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CK(cudaStreamSynchronize(s));
-        BAMG_REQUIRE(h_err == 0, BAMG_EOVERFLOW, "neighbourhood search exceeded its capacity of 256 visited states");
+        BAMG_REQUIRE(h_err == 0, BAMG_EOVERFLOW, "neighbourhood search exceeded its capacity of 1024 visited states");
         setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
 
@@ -451,7 +463,7 @@ struct Solver : SolverBase {
 
     void capture_step(int n) {
         std::vector<VLevel<T>> vl = vlevels(vin.get(), zout.get());
-        const uint64_t c0 = bamg_launch_count();
+        const uint64_t c0 = t_launches;  // other threads may launch meanwhile
         BAMG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         try {
             arnoldi_step_graphable<T>(n, B64(), V.get(), Z.get(), vin.get(), zout.get(), dj.get(), state.get(), m,
@@ -463,7 +475,7 @@ struct Solver : SolverBase {
             throw;
         }
         BAMG_CK(cudaStreamEndCapture(s, &graph));
-        graph_kernels = (int64_t)(bamg_launch_count() - c0);
+        graph_kernels = (int64_t)(t_launches - c0);
         count_launches(-graph_kernels);  // counted again at every replay
         BAMG_CK(cudaGraphInstantiate(&gexec, graph, 0));
     }
@@ -769,6 +781,70 @@ int bamg_solve(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st)
 }
 
 void bamg_free(bamg_handle* h) { delete h; }
+
+int bamg_solve_batch(int nchains, const bamg_csr* As, const int* r, const int* levels, const bamg_opts* opts,
+                     double* const* xs, int flags, double tol, int nworkers, bamg_stats* st) {
+    if (nchains < 0 || (nchains > 0 && (!As || !r || !levels || !opts || !xs))) {
+        g_err = "bamg_solve_batch: bad arguments";
+        return BAMG_EINVAL;
+    }
+    if (flags & BAMG_X_GUESS) {
+        g_err = "bamg_solve_batch: BAMG_X_GUESS is not supported";
+        return BAMG_EINVAL;
+    }
+    if (nchains == 0) return BAMG_OK;
+    if (nworkers <= 0) nworkers = std::min(16, std::max(1, (nchains + 3) / 4));
+    nworkers = std::min(nworkers, nchains);
+    // largest chains first: the queue ends with the short jobs
+    std::vector<int> order(nchains);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return As[a].n > As[b].n; });
+    std::atomic<int> next{0};
+    std::mutex mu;
+    int first_code = BAMG_OK;
+    int first_chain = nchains;
+    std::string first_msg;
+    auto worker = [&]() {
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+            std::lock_guard<std::mutex> lock(mu);
+            if (first_code == BAMG_OK) {
+                first_code = BAMG_ECUDA;
+                first_msg = "bamg_solve_batch: stream creation failed";
+            }
+            return;
+        }
+        for (;;) {
+            const int q = next.fetch_add(1);
+            if (q >= nchains) break;
+            const int k = order[q];
+            bamg_opts o = opts[k];
+            o.stream = ws;
+            bamg_handle* h = nullptr;
+            bamg_stats local{};
+            int code = bamg_setup(&As[k], r[k], levels[k], &o, &h);
+            if (code == BAMG_OK) code = bamg_solve(h, xs[k], flags & BAMG_X_HOST, tol, &local);
+            local.status = code;
+            if (st) st[k] = local;
+            if (code != BAMG_OK) {
+                std::lock_guard<std::mutex> lock(mu);
+                if (k < first_chain) {
+                    first_chain = k;
+                    first_code = code;
+                    first_msg = "chain " + std::to_string(k) + ": " + g_err;
+                }
+            }
+            bamg_free(h);
+        }
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nworkers; ++t) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+    g_err = first_msg;
+    return first_code;
+}
 
 const char* bamg_last_error(void) { return g_err.c_str(); }
 

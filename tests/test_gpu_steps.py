@@ -230,3 +230,28 @@ def test_coarse_eig_matches_oracle():
             if gap > 1e-4:
                 assert np.allclose(v, V_o[:, c], atol=1e-8)
     assert np.allclose(pinv, ob.pinv_truncated(Bd), rtol=1e-9, atol=1e-11)
+
+
+def test_coarse_eig_fp32_vectors_close_to_oracle():
+    # the mixed-precision setup refines the coarsest eigenvectors in FP32: same selection,
+    # eigenvalues and vectors to FP32 accuracy
+    torch = _torch()
+    Bd, Td, H = _coarse_pair()
+    lam_o, V_o, kinds_o = ob.coarse_eigs(Bd, Td, 6)
+    lam, V, kinds, pinv = _bamg().coarse_eig(torch.tensor(Bd, device="cuda"), torch.tensor(Td, device="cuda"), 6,
+                                             fp32_vectors=True)
+    lam, V, kinds, pinv = lam.cpu().numpy(), V.cpu().numpy(), kinds.cpu().numpy(), pinv.cpu().numpy()
+    P = ob.pinv_truncated(Bd)
+    assert np.abs(pinv - P).max() <= 1e-4 * np.abs(P).max()
+    assert lam[0] == 0.0
+    assert np.array_equal(kinds, kinds_o)
+    scale = np.abs(Bd).max()
+    assert np.allclose(lam, lam_o, rtol=1e-4, atol=1e-6 * scale)
+    ev = np.linalg.eigvals(np.linalg.solve(Td, Bd))
+    for c in range(V.shape[1]):
+        if kinds[c] == 0:
+            v = V[:, c]
+            assert np.linalg.norm(Bd @ v - lam[c] * (Td @ v)) < 1e-4 * scale
+            gap = np.sort(np.abs(ev - (lam_o[c] if c else 0.0)))[1]
+            if gap > 1e-3:
+                assert np.allclose(v, V_o[:, c], atol=1e-4)
