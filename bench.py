@@ -5,8 +5,9 @@ queueing network with two queues of capacity 255 (65,536 states), arrival 11/31,
 service 10/31 and 10/31, r = 10 test vectors, FP32 setup and V-cycle inside FP64
 flexible GMRES.  Inputs are resident in HBM when a step's timing starts; L2 is
 flushed between steps.  Also reported: the same metric end to end from host buffers,
-the plain FP64 method on the same chain, the roofline of the dominant kernel, an SpMM
-HBM probe, and the CPU oracle on the host cores.
+the plain FP64 method on the same chain, the roofline of the dominant kernel (the V-cycle
+smoother on the finest level), an SpMM HBM probe, the batched form on 512 chains, and
+the CPU oracle on the host cores.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -162,10 +163,8 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
-    # ---- parity of the timed result against the exact stationary vector
-    from oracle import exact
-
-    xe = exact.sparse_nullspace(ch.to_scipy()) if rank == 0 else None
+    # ---- accuracy of the timed result against a sparse direct solution
+    xe = _direct_stationary(ch) if rank == 0 else None
     xr = x.cpu().numpy()
     err = float(np.abs(xr - xe).sum() / np.abs(xe).sum()) if xe is not None else None
     # ---- end to end from host buffers through the C ABI
@@ -200,8 +199,11 @@ def run_ours(args):
         return
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-    roof = dominant_kernel(ch, peaks)
+    s_dom = bamg.Solver(rp, ci, v, r=R, levels=20, grid=ch.grid, precision="mixed")
+    roof = dominant_kernel(s_dom, peaks)
+    s_dom.close()
     probe = spmm_probe(peaks) if not args.no_probe else None
+    batch = batch_line(args) if not args.no_batch else None
     cpu = cpu_baseline() if not args.no_cpu else None
     nnz_a = int(ch.nnz)
     out = {
@@ -218,9 +220,23 @@ def run_ours(args):
         "fp64_ms": round(float(np.median(fp64)), 4), "fp64_iterations": st64["iterations"],
         "speedup_mixed_vs_fp64": round(float(np.median(fp64)) / ms, 3),
         "gpu_launches": int(round(launches)),
-        "roofline": roof, "spmm_hbm": probe, "cpu_baseline": cpu, "clocks": ck,
+        "roofline": roof, "spmm_hbm": probe, "batch": batch, "cpu_baseline": cpu, "clocks": ck,
     }
     _line(out)
+
+
+def _direct_stationary(ch):
+    """x with (I - A) x = 0, 1^T x = 1 by a sparse LU (SuperLU): fix the last entry to one,
+    solve the remaining rows and columns of I - A (nonsingular for an irreducible chain)
+    and normalise.  The accuracy yardstick of the timed result."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    n = ch.n
+    M = (sp.identity(n, format="csr") - ch.to_scipy().tocsr()).tocsc()
+    x = np.ones(n)
+    x[:-1] = spla.spsolve(M[:-1, :-1], -M[:-1, n - 1].toarray().ravel())
+    return x / x.sum()
 
 
 def _grid_B(N, dev, dtype):
@@ -259,29 +275,54 @@ def _time_relax(bamg, B, X, ncols, col0, reps, stream, sweeps=20):
     return float(np.mean([a.elapsed_time(b) for a, b in evs])) / sweeps
 
 
-def dominant_kernel(ch, peaks):
-    """omega-Jacobi SpMM sweep on the workload's finest level (FP32, r = 10 columns of a
-    20-wide block, as in the setup).  Algorithmic bytes per launch: the matrix once
-    (nnz * (4 + 4) + 4 (n + 1)), the inverse diagonal (4 n), the relaxed columns read and
-    written once (2 * 4 * n * 12)."""
+# DRAM traffic of one finest-level k_smooth launch from the ncu capture summarised in
+# profiles/k_smooth_tandem256_level0.md, valid while the kernel's source is unchanged.
+SMOOTH_TRAFFIC = {"bytes": 3145216, "source_sha1": "e7fd823059eeabb793162c2b26fd53f579630f1b"}
+
+
+def _kernel_source_sha1():
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_1004_1451_gb300", "csrc", "k_solve.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def dominant_kernel(solver, peaks, sweeps=20, reps=10):
+    """k_smooth, the V-cycle smoother (Eq. (4.4)), on the finest level of the workload's
+    own hierarchy: the kernel with the largest share of the step (ncu launch list).
+    Timed live with CUDA events on the stream it is launched on, `sweeps` launches per
+    event pair.  Algorithmic bytes per launch (FP32 values, int32 indices): the CSR of
+    B_0 once (8 nnz + 4 (n + 1)), D^{-1}, b and x read once, y written once (16 n)."""
     import torch
 
-    import paper_1004_1451_gb300 as bamg
-    from oracle import bamg as ob  # noqa: F401  (input matrix only)
-
-    dev = torch.device("cuda")
-    B = ob.system_matrix(ch.to_scipy())
-    Bd = (torch.tensor(B.indptr.astype(np.int32), device=dev), torch.tensor(B.indices.astype(np.int32), device=dev),
-          torch.tensor(B.data, dtype=torch.float32, device=dev))
-    X = torch.rand(ch.n, 20, dtype=torch.float32, device=dev)
-    ms = _time_relax(bamg, Bd, X, 10, 0, 10, torch.cuda.current_stream())
-    nbytes = B.nnz * 8 + 4 * (ch.n + 1) + 4 * ch.n + 2 * 4 * ch.n * 12
-    gbs = nbytes / (ms * 1e-3) / 1e9
+    info = solver.info()
+    n, nnz = int(info["n"][0]), int(info["nnz"][0])
+    dt = solver.dtype
+    esz = 4 if dt == torch.float32 else 8
+    b = torch.rand(n, dtype=dt, device="cuda")
+    x = torch.rand(n, dtype=dt, device="cuda")
+    work = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    solver.smooth(0, b, x, sweeps=2, work=work)  # warm-up
+    evs = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.smooth(0, b, x, sweeps=sweeps, work=work)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    us = float(np.median([a.elapsed_time(c) for a, c in evs])) * 1e3 / sweeps
+    nbytes = (esz + 4) * nnz + 4 * (n + 1) + 4 * esz * n
+    gbs = nbytes / (us * 1e-6) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    return {"kernel": "k_jacobi<float> (SpMM sweep, finest level)", "bound": "hbm", "achieved": round(gbs, 1),
-            "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "traffic": None,
-            "bytes_per_launch": int(nbytes), "us_per_launch": round(ms * 1e3, 3),
-            "note": "working set fits in L2 (8.9 MB); bytes are algorithmic"}
+    traffic = SMOOTH_TRAFFIC["bytes"] if SMOOTH_TRAFFIC["source_sha1"] == _kernel_source_sha1() else None
+    return {"kernel": "k_smooth<float> (V-cycle smoother, finest level, 65,536 rows)", "bound": "hbm",
+            "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+            "traffic": traffic, "bytes_per_launch": int(nbytes), "us_per_launch": round(us, 3),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
+            "note": "level-0 working set (%.1f MB) stays in the 129 MB L2 between launches" % (nbytes / 1e6)}
 
 
 def spmm_probe(peaks, N=4096):
@@ -303,6 +344,60 @@ def spmm_probe(peaks, N=4096):
     torch.cuda.empty_cache()
     return {"workload": f"grid walk {N}^2, r=16, FP32", "kernel": "k_jacobi<float>", "ms": round(ms, 4),
             "bytes": int(nbytes), "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
+
+
+BATCH_WORKLOAD = ("512 chains, seed 0: 256 birth-death chains (n log-uniform in [1024, 65536], per-state "
+                  "rates U(0.2, 0.5)) and 256 grid walks (side uniform in [32, 256]); r=8; mixed")
+# Birth-death chains with i.i.d. per-state rates have stationary vectors spanning many
+# orders of magnitude; their LS fits use a small ridge (the default suits 2-D chains).
+BD_OPTS = dict(ridge=1e-10, ridge32=1e-6)
+
+
+def batch_line(args, workers=8):
+    """Chains solved per second by bamg_solve_batch on the 512-chain mixture (inputs
+    resident on the device), with the count of chains that reached the tolerance."""
+    import torch
+
+    import paper_1004_1451_gb300 as bamg
+    from workloads import batched_mixture
+
+    chains = batched_mixture(0)
+    mats = [(torch.tensor(c.row_ptr, device="cuda"), torch.tensor(c.col, device="cuda"),
+             torch.tensor(c.val, device="cuda")) for c in chains]
+    opts = [dict(grid=c.grid, precision="mixed", **(BD_OPTS if c.kind == "birth_death" else {})) for c in chains]
+
+    def once():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            _, st = bamg.solve_batch(mats, 8, 20, TOL, opts=opts, workers=workers)
+        except bamg.BamgError as e:
+            st = e.stats
+        return time.perf_counter() - t0, st
+
+    once()  # warm-up
+    dt, st = once()
+    ok = [s_["status"] == 0 for s_ in st]
+    bd = [c.kind == "birth_death" for c in chains]
+    return {"workload": BATCH_WORKLOAD, "chains": len(chains), "states": int(sum(c.n for c in chains)),
+            "nnz_A": int(sum(c.nnz for c in chains)), "value": round(len(chains) / dt, 2), "unit": "chains/s",
+            "ms": round(dt * 1e3, 1), "workers": workers, "converged": int(sum(ok)),
+            "converged_grid": int(sum(o and not b for o, b in zip(ok, bd))),
+            "converged_birth_death": int(sum(o and b for o, b in zip(ok, bd))),
+            "gmres_iterations_total": int(sum(s_["iterations"] for s_ in st)),
+            "note": "birth-death chains that stop at max_it count in the time; host-timed (threads and streams)"}
+
+
+def kernel_probe():
+    """Only the dominant-kernel timing (for an ncu capture of k_smooth on the finest level)."""
+    import torch
+
+    import paper_1004_1451_gb300 as bamg
+
+    ch = _workload()
+    rp, ci, v = (torch.tensor(a, device="cuda") for a in (ch.row_ptr, ch.col, ch.val))
+    s = bamg.Solver(rp, ci, v, r=R, levels=20, grid=ch.grid, precision="mixed")
+    _line(dominant_kernel(s, {"hbm_gbs": 6800.0}, sweeps=3, reps=1))
 
 
 def cpu_baseline():
@@ -348,16 +443,26 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only-step", action="store_true", help="time the workload steps only (for profiler launch lists)")
     ap.add_argument("--probe-only", type=int, default=0, help="run only the SpMM probe on an N x N grid walk")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-chain batched line")
+    ap.add_argument("--kernel-probe", action="store_true", help="run only the dominant-kernel timing")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernel_probe:
+        import torch
+
+        import paper_1004_1451_gb300.build as pb
+
+        pb.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        kernel_probe()
     elif args.probe_only:
         import torch
 

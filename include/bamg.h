@@ -191,6 +191,17 @@ int bamg_import(int nlevels, const bamg_level_in* levels, const double* h_pinv, 
  * zero initial guess, B_L^+ on the coarsest level).  v, z: n_0 device doubles. */
 int bamg_vcycle_apply(bamg_handle* h, const double* v, double* z);
 
+/* Arithmetic of the handle's hierarchy and V-cycle: BAMG_F32 (mixed precision) or
+ * BAMG_F64; BAMG_EINVAL for a NULL handle. */
+int bamg_hierarchy_precision(const bamg_handle* h);
+
+/* `sweeps` sweeps of the V-cycle smoother of Eq. (4.4), x <- x + omega D^{-1} (b - B_l x),
+ * on level l of the handle's hierarchy: one kernel launch per sweep on the handle's
+ * stream, asynchronous (no synchronisation; time it with events on that stream).
+ * b, x, work: n_l device elements in the hierarchy's arithmetic (bamg_hierarchy_precision);
+ * x is updated in place, work is scratch.  The V-cycle's own smoothing steps. */
+int bamg_smooth_apply(bamg_handle* h, int level, int sweeps, const void* b, void* x, void* work);
+
 /* ---------------------------------------------------------------------------------
  * Step entry points: one step of the setup on caller buffers (device memory).
  * --------------------------------------------------------------------------------- */

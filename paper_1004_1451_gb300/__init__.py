@@ -127,6 +127,21 @@ class Solver:
         capi.check(_lib().bamg_vcycle_apply(self._h, _p(v.contiguous()), _p(z)))
         return z
 
+    @property
+    def dtype(self):
+        """Arithmetic of the hierarchy and V-cycle (torch.float32 for mixed precision)."""
+        code = _lib().bamg_hierarchy_precision(self._h)
+        return torch.float32 if code == capi.F32 else torch.float64
+
+    def smooth(self, level: int, b: torch.Tensor, x: torch.Tensor, sweeps: int = 1, work=None):
+        """sweeps V-cycle smoother sweeps on `level`, x updated in place, launched
+        asynchronously on the stream the hierarchy was set up on."""
+        assert b.dtype == self.dtype and x.dtype == self.dtype and x.is_contiguous() and b.is_contiguous()
+        if work is None:
+            work = torch.empty_like(x)
+        capi.check(_lib().bamg_smooth_apply(self._h, level, sweeps, _p(b), _p(x), _p(work)))
+        return x
+
     def info(self) -> dict:
         L = C.c_int(0)
         ns = (C.c_int64 * 32)()

@@ -72,6 +72,8 @@ SIGNATURES = {
     "bamg_hierarchy_layout": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "bamg_import": (_I, [_I, C.POINTER(LevelIn), _P, _P, C.POINTER(Opts), C.POINTER(_P)]),
     "bamg_vcycle_apply": (_I, [_P, _P, _P]),
+    "bamg_hierarchy_precision": (_I, [_P]),
+    "bamg_smooth_apply": (_I, [_P, _I, _I, _P, _P, _P]),
     "bamg_tv_init": (_I, [_I, _I, _I, _I, _I, C.c_uint64, _D, _D, _P, _P]),
     "bamg_relax": (_I, [_I, C.POINTER(Mat), _P, _P, _I, _I, _I, _D, _I, _P, _P, _P]),
     "bamg_relax_noalloc": (_I, [_I, C.POINTER(Mat), _P, _P, _I, _I, _I, _D, _I, _P, _P]),

@@ -132,7 +132,7 @@ int bamg_interp_ls(int dtype, const bamg_mat* B, const uint8_t* cf, const int32_
                                  ridge, pcol, (float*)pval, pcnt, s);
         else
             throw Error(BAMG_EINVAL, "bad dtype");
-        BAMG_REQUIRE(e == 0, BAMG_EOVERFLOW, "neighbourhood search exceeded its capacity of 1024 visited states");
+        BAMG_REQUIRE(e == 0, BAMG_EOVERFLOW, "neighbourhood search: a fine point needs more than 2048 recorded states");
     });
 }
 

@@ -135,8 +135,10 @@ void coarse_to_fine(int n, const uint8_t* cf, const int32_t* cidx, int32_t* c2f,
 }
 
 // ================================================================ least-squares interpolation
-constexpr int LS_WARPS = 2;
-constexpr int VIS_CAP = 1024;  // nodes visited by one neighbourhood search
+constexpr int LS_WARPS = 4;
+constexpr int VIS_CAP = 256;    // nodes recorded by one neighbourhood search (first pass)
+constexpr int VIS_CAP2 = 2048;  // second pass, for the points whose search overflowed
+constexpr int LS2_BLOCKS = 608;
 constexpr int MMAX = 16;
 constexpr int CMAX = 4;
 constexpr int KMAX = 32;
@@ -200,24 +202,13 @@ __device__ __forceinline__ bool chol_solve(T (&A)[CMAX][CMAX], const T (&b)[CMAX
 // normal equations (plus the Tikhonov term), solves them by Cholesky and evaluates the
 // functional of Eq. (3.6) directly; the lane with the smallest value (lowest slot on
 // ties) joins J.
-template <typename T>
-__global__ void __launch_bounds__(LS_WARPS * 32)
-    k_ls_fit(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const uint8_t* __restrict__ cf,
-             const int32_t* __restrict__ cidx, const T* __restrict__ X, int ncols, int ld, const double* __restrict__ w,
-             int z, int mmax, int c, double ridge, int32_t* __restrict__ pcol, T* __restrict__ pval,
-             int32_t* __restrict__ pcnt, int* __restrict__ err) {
-    __shared__ int s_vis[LS_WARPS][VIS_CAP];
-    __shared__ unsigned long long s_key[LS_WARPS][VIS_CAP];
-    __shared__ uint8_t s_dist[LS_WARPS][VIS_CAP];
-    __shared__ int s_cand[LS_WARPS][MMAX];
-    __shared__ T s_xi[LS_WARPS][KMAX];
-    __shared__ T s_xj[LS_WARPS][CMAX][KMAX];
-    __shared__ T s_w[KMAX];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < KMAX) s_w[threadIdx.x] = threadIdx.x < ncols ? (T)w[threadIdx.x] : T(0);
-    __syncthreads();
-    const int i = blockIdx.x * LS_WARPS + wid;
-    if (i >= n) return;
+template <typename T, int CAP>
+__device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx, const T* __restrict__ X,
+                         int ncols, int ld, const T* s_w, int z, int mmax, int c, double ridge,
+                         int32_t* __restrict__ pcol, T* __restrict__ pval, int32_t* __restrict__ pcnt, int* vis,
+                         unsigned long long* key, uint8_t* dist, int* cand, T* xi, T (*xj)[KMAX], bool defer) {
+    const int lane = threadIdx.x & 31;
     const int64_t prow = (int64_t)i * c;
     if (cf[i]) {
         if (lane < c) {
@@ -225,11 +216,10 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
             pval[prow + lane] = lane == 0 ? T(1) : T(0);
         }
         if (lane == 0) pcnt[i] = 1;
-        return;
+        return false;
     }
     // ---- neighbourhood search (Eq. (3.5))
-    int* vis = s_vis[wid];
-    uint8_t* dist = s_dist[wid];
+    __syncwarp();
     if (lane == 0) {
         vis[0] = i;
         dist[0] = 0;
@@ -261,22 +251,22 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
                 const unsigned lt = (1u << lane) - 1u;
                 const bool leader = isnew && (grp & lt) == 0u;
                 unsigned bal = __ballot_sync(0xffffffffu, leader && (!fonly || isc));
-                if (!fonly && nvis + __popc(bal) > VIS_CAP) {
+                if (!fonly && nvis + __popc(bal) > CAP) {
                     fonly = true;
                     bal = __ballot_sync(0xffffffffu, leader && isc);
                 }
                 const bool rec = (bal >> lane) & 1u;
                 const int pos = nvis + __popc(bal & lt);
-                if (rec && pos < VIS_CAP) {
+                if (rec && pos < CAP) {
                     vis[pos] = v;
                     dist[pos] = (uint8_t)d;
                 }
                 int added = __popc(bal);
-                if (nvis + added > VIS_CAP) {
+                if (nvis + added > CAP) {
                     ovf = true;
-                    added = VIS_CAP - nvis;
+                    added = CAP - nvis;
                 }
-                ncvis += __popc(__ballot_sync(0xffffffffu, rec && isc && pos < VIS_CAP));
+                ncvis += __popc(__ballot_sync(0xffffffffu, rec && isc && pos < CAP));
                 nvis += added;
                 __syncwarp();
             }
@@ -289,8 +279,8 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
         fs = fe;
         fe = nvis;
     }
+    if (ovf && defer) return true;  // the second pass redoes this point with a larger list
     // ---- candidates: coarse points ranked by (depth, coarse index)
-    unsigned long long* key = s_key[wid];
     int ntot = 0;
     for (int q0 = 1; q0 < nvis; q0 += 32) {
         const int q = q0 + lane;
@@ -309,21 +299,21 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
             const unsigned long long kq = key[q];
             int rank = 0;
             for (int q2 = 1; q2 < nvis; ++q2) rank += key[q2] < kq;
-            if (rank < mmax) s_cand[wid][rank] = vis[q];
+            if (rank < mmax) cand[rank] = vis[q];
         }
     }
     const int ncand = ntot < mmax ? ntot : mmax;
-    for (int k = lane; k < KMAX; k += 32) s_xi[wid][k] = k < ncols ? X[(int64_t)i * ld + k] : T(0);
+    for (int k = lane; k < KMAX; k += 32) xi[k] = k < ncols ? X[(int64_t)i * ld + k] : T(0);
     __syncwarp();
     // ---- greedy least squares (Algorithm 2)
-    const int node = lane < ncand ? s_cand[wid][lane] : -1;
+    const int node = lane < ncand ? cand[lane] : -1;
     const T* xs = node >= 0 ? X + (int64_t)node * ld : nullptr;
     T gss = T(0), bs = T(0);
     if (node >= 0)
         for (int k = 0; k < ncols; ++k) {
             const T wk = s_w[k], v = xs[k];
             gss += wk * v * v;
-            bs += wk * v * s_xi[wid][k];
+            bs += wk * v * xi[k];
         }
     T gsj[CMAX], GJJ[CMAX][CMAX], bJ[CMAX], pbest[CMAX];
     int J[CMAX];
@@ -370,10 +360,10 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
             if (chol_solve<T>(A, rhs, t + 1, pl)) {
                 T acc = T(0);
                 for (int k = 0; k < ncols; ++k) {
-                    T r = s_xi[wid][k] - pl[t] * xs[k];
+                    T r = xi[k] - pl[t] * xs[k];
 #pragma unroll
                     for (int a = 0; a < CMAX; ++a)
-                        if (a < t) r -= pl[a] * s_xj[wid][a][k];
+                        if (a < t) r -= pl[a] * xj[a][k];
                     acc += s_w[k] * r * r;
                 }
                 L = (acc == acc) ? acc : INF;
@@ -409,11 +399,11 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
         J[t] = w_node;
         nJ = t + 1;
         if (lane == bestLane) used = true;
-        for (int k = lane; k < KMAX; k += 32) s_xj[wid][t][k] = k < ncols ? X[(int64_t)w_node * ld + k] : T(0);
+        for (int k = lane; k < KMAX; k += 32) xj[t][k] = k < ncols ? X[(int64_t)w_node * ld + k] : T(0);
         __syncwarp();
         if (node >= 0) {
             T g = T(0);
-            for (int k = 0; k < ncols; ++k) g += s_w[k] * xs[k] * s_xj[wid][t][k];
+            for (int k = 0; k < ncols; ++k) g += s_w[k] * xs[k] * xj[t][k];
             gsj[t] = g;
         }
     }
@@ -439,7 +429,50 @@ __global__ void __launch_bounds__(LS_WARPS * 32)
             pval[prow + a] = a < nJ ? vals[a] : T(0);
         }
         pcnt[i] = nJ;
-        if (ovf) atomicOr(err, 1);
+    }
+    return ovf;
+}
+
+// First pass (list == nullptr): warp per point i; a point whose search overflows the
+// CAP-entry list is appended to ovf_list (or flags err when ovf_list is null).  Second
+// pass (list != nullptr): persistent warps over the *list_count points of list.
+template <typename T, int CAP, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_ls_fit(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const uint8_t* __restrict__ cf,
+             const int32_t* __restrict__ cidx, const T* __restrict__ X, int ncols, int ld, const double* __restrict__ w,
+             int z, int mmax, int c, double ridge, int32_t* __restrict__ pcol, T* __restrict__ pval,
+             int32_t* __restrict__ pcnt, const int* __restrict__ list, const int* __restrict__ list_count,
+             int* __restrict__ ovf_list, int* __restrict__ ovf_count, int* __restrict__ err) {
+    __shared__ int s_vis[WARPS][CAP];
+    __shared__ unsigned long long s_key[WARPS][CAP];
+    __shared__ uint8_t s_dist[WARPS][CAP];
+    __shared__ int s_cand[WARPS][MMAX];
+    __shared__ T s_xi[WARPS][KMAX];
+    __shared__ T s_xj[WARPS][CMAX][KMAX];
+    __shared__ T s_w[KMAX];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < KMAX) s_w[threadIdx.x] = threadIdx.x < ncols ? (T)w[threadIdx.x] : T(0);
+    __syncthreads();
+    if (list == nullptr) {
+        const int i = blockIdx.x * WARPS + wid;
+        if (i >= n) return;
+        const bool ovf = ls_point<T, CAP>(i, rp, ci, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol, pval, pcnt,
+                                          s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_xi[wid], s_xj[wid],
+                                          ovf_list != nullptr);
+        if (ovf && lane == 0) {
+            if (ovf_list)
+                ovf_list[atomicAdd(ovf_count, 1)] = i;
+            else
+                atomicOr(err, 1);
+        }
+        return;
+    }
+    const int cnt = *list_count;
+    for (int k = blockIdx.x * WARPS + wid; k < cnt; k += gridDim.x * WARPS) {
+        const bool ovf = ls_point<T, CAP>(list[k], rp, ci, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol, pval,
+                                          pcnt, s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_xi[wid],
+                                          s_xj[wid], false);
+        if (ovf && lane == 0) atomicOr(err, 1);
     }
 }
 
@@ -452,15 +485,19 @@ int interp_ls(int n, const int32_t* rp, const int32_t* ci, const uint8_t* cf, co
     BAMG_REQUIRE(mmax >= 1 && mmax <= MMAX, BAMG_EINVAL, "interp_ls: 1 <= mmax <= 16");
     BAMG_REQUIRE(z >= 1 && z <= 3, BAMG_EINVAL, "interp_ls: 1 <= z <= 3");
     if (n == 0) return 0;
-    if (d_err) {  // the caller reads the overflow flag later
-        BAMG_LAUNCH(k_ls_fit<T>, blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, cf, cidx, X, ncols, ld, d_w,
-                    z, mmax, c, ridge, pcol, pval, pcnt, d_err);
-        return 0;
-    }
-    TmpBuf<int> err(1, s);
-    BAMG_CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
-    BAMG_LAUNCH(k_ls_fit<T>, blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, cf, cidx, X, ncols, ld, d_w, z,
-                mmax, c, ridge, pcol, pval, pcnt, err.get());
+    // two passes: the common case with a small visited list and 4 warps per block, then the
+    // (rare) points whose search overflowed it, with a large list and one warp per block
+    TmpBuf<int> olist(n, s), ocount(1, s), err(1, s);
+    BAMG_CK(cudaMemsetAsync(ocount.get(), 0, sizeof(int), s));
+    int* e = d_err ? d_err : err.get();  // with d_err the caller reads the overflow flag later
+    if (!d_err) BAMG_CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    BAMG_LAUNCH((k_ls_fit<T, VIS_CAP, LS_WARPS>), blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, cf, cidx, X,
+                ncols, ld, d_w, z, mmax, c, ridge, pcol, pval, pcnt, (const int*)nullptr, (const int*)nullptr,
+                olist.get(), ocount.get(), e);
+    BAMG_LAUNCH((k_ls_fit<T, VIS_CAP2, 1>), LS2_BLOCKS, 32, 0, s, n, rp, ci, cf, cidx, X, ncols, ld, d_w, z, mmax, c,
+                ridge, pcol, pval, pcnt, (const int*)olist.get(), (const int*)ocount.get(), (int*)nullptr,
+                (int*)nullptr, e);
+    if (d_err) return 0;
     int h = 0;
     BAMG_CK(cudaMemcpyAsync(&h, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     BAMG_CK(cudaStreamSynchronize(s));

@@ -538,6 +538,27 @@ template void arnoldi_step_graphable<double>(int, const MatView<double>&, double
                                              double*, int, double*, const std::vector<VLevel<double>>&,
                                              const double*, double, int, int, double*, cudaStream_t);
 
+// `sweeps` sweeps of the smoother S of Eq. (4.4) on one level, ping-ponging between x and
+// y; the result ends in x (one copy when sweeps is odd).
+template <typename T>
+void smooth_sweeps(const VLevel<T>& v, const T* b, T* x, T* y, double omega_d, int sweeps, cudaStream_t s) {
+    const int n = v.B.n;
+    const unsigned g = blocks_for(n, 256);
+    const T omega = (T)omega_d;
+    T* cur = x;
+    T* nxt = y;
+    for (int k = 0; k < sweeps; ++k) {
+        BAMG_LAUNCH(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, b, cur, nxt, omega, (T*)nullptr,
+                    (const int*)nullptr);
+        T* q = cur;
+        cur = nxt;
+        nxt = q;
+    }
+    if (cur != x) BAMG_CK(cudaMemcpyAsync(x, cur, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+}
+template void smooth_sweeps<float>(const VLevel<float>&, const float*, float*, float*, double, int, cudaStream_t);
+template void smooth_sweeps<double>(const VLevel<double>&, const double*, double*, double*, double, int, cudaStream_t);
+
 template void vcycle<float>(const std::vector<VLevel<float>>&, const float*, double, int, int, cudaStream_t, float*,
                             const int*);
 template void vcycle<double>(const std::vector<VLevel<double>>&, const double*, double, int, int, cudaStream_t,

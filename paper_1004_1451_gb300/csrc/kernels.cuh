@@ -116,6 +116,9 @@ struct VLevel {  // one level of the V-cycle
 };
 // One V-cycle: lv[0].b -> lv[0].x.  With Z != null the result is also stored at
 // Z + (*dj) * n_0.
+// sweeps x <- x + omega D^{-1} (b - B x) on one level (y: work array of n); result in x.
+template <typename T>
+void smooth_sweeps(const VLevel<T>& v, const T* b, T* x, T* y, double omega, int sweeps, cudaStream_t s);
 template <typename T>
 void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega, int nu_pre, int nu_post, cudaStream_t s,
             T* Z = nullptr, const int* dj = nullptr);

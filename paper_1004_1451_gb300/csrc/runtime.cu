@@ -92,6 +92,8 @@ struct SolverBase {
     virtual void level_size(int l, int64_t* n, int64_t* nnz) const = 0;
     virtual void solve(double* x, int flags, double tol, bamg_stats* st) = 0;
     virtual void vcycle_apply(const double* v, double* z) = 0;
+    virtual void smooth_apply(int level, int sweeps, const void* b, void* x, void* work) = 0;
+    virtual int precision() const = 0;
     virtual void export_obj(int level, int what, void* h_dst, int64_t cap, int64_t* bytes) = 0;
     virtual void layout(int level, int* ld, int* r, int* v0, int* nvec) const = 0;
 };
@@ -369,7 +371,7 @@ struct Solver : SolverBase {
         int h_err = 0;
         BAMG_CK(cudaMemcpyAsync(&h_err, ls_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CK(cudaStreamSynchronize(s));
-        BAMG_REQUIRE(h_err == 0, BAMG_EOVERFLOW, "neighbourhood search exceeded its capacity of 1024 visited states");
+        BAMG_REQUIRE(h_err == 0, BAMG_EOVERFLOW, "neighbourhood search: a fine point needs more than 2048 recorded states");
         setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
 
@@ -434,6 +436,17 @@ struct Solver : SolverBase {
     }
 
     // --------------------------------------------------------------- V-cycle
+    int precision() const override { return std::is_same<T, float>::value ? BAMG_F32 : BAMG_F64; }
+
+    void smooth_apply(int level, int sweeps, const void* b, void* x, void* work) override {
+        BAMG_REQUIRE(level >= 0 && level < (int)lv.size(), BAMG_EINVAL, "smooth_apply: no such level");
+        BAMG_REQUIRE(sweeps >= 0, BAMG_EINVAL, "smooth_apply: sweeps < 0");
+        VLevel<T> v;
+        v.B = lv[level]->B();
+        v.dinv = lv[level]->dinv.get();
+        smooth_sweeps<T>(v, (const T*)b, (T*)x, (T*)work, o.omega, sweeps, s);
+    }
+
     void vcycle_apply(const double* v, double* z) override {
         AllocStream as_(s);
         const int n = lv[0]->n;
@@ -909,6 +922,15 @@ int bamg_import(int nlevels, const bamg_level_in* levels, const double* h_pinv, 
         *h = hh.release();
     });
 }
+
+int bamg_smooth_apply(bamg_handle* h, int level, int sweeps, const void* b, void* x, void* work) {
+    return guarded([&] {
+        BAMG_REQUIRE(h && h->impl && b && x && work, BAMG_EINVAL, "null argument");
+        h->impl->smooth_apply(level, sweeps, b, x, work);
+    });
+}
+
+int bamg_hierarchy_precision(const bamg_handle* h) { return h && h->impl ? h->impl->precision() : BAMG_EINVAL; }
 
 int bamg_vcycle_apply(bamg_handle* h, const double* v, double* z) {
     return guarded([&] {

@@ -232,3 +232,30 @@ def test_config3_delaunay_2e20_mixed():
     assert info["n"][-1] <= 64
     assert rel(x, exact.exact_stationary(ch)) < 1e-6
     print("delaunay 2^20:", info["n"], st)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_smooth_apply_matches_eq44_smoother(precision):
+    # three sweeps x <- x + omega D^{-1} (b - B x) of the V-cycle smoother (Eq. (4.4)) on
+    # levels 0 and 1, against the same sweeps on the exported level matrix
+    torch = _torch()
+    bamg = _bamg()
+    ch = tandem_queue(40)
+    s, _, _ = _run(ch, 8, 10, 1e-10, precision)
+    dt = s.dtype
+    assert dt == (torch.float32 if precision == "mixed" else torch.float64)
+    rng = np.random.default_rng(11)
+    for level in (0, 1):
+        rp, ci, v = s.export(level, bamg._capi.EXPORT_B)
+        n = len(rp) - 1
+        B = sp.csr_matrix((v, ci, rp), shape=(n, n))
+        b = rng.standard_normal(n)
+        x0 = rng.standard_normal(n)
+        xg = torch.tensor(x0, dtype=dt, device="cuda")
+        s.smooth(level, torch.tensor(b, dtype=dt, device="cuda"), xg, sweeps=3)
+        torch.cuda.synchronize()
+        dinv = 1.0 / B.diagonal()
+        x = x0.copy()
+        for _ in range(3):
+            x = x + 0.7 * dinv * (b - B @ x)
+        assert rel(xg.cpu().double().numpy(), x) < (1e-12 if precision == "fp64" else 1e-5)
