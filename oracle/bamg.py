@@ -96,6 +96,11 @@ class Opts:
     cr_nu: int = 8
     cr_omega: float = 0.7
     cr_max_rounds: int = 20
+    # learned interpolation (oracle/learned.py); the paper uses least squares only
+    interp: str = "ls"  # "ls" (Algorithm 2) or "learned"
+    model: dict | None = None  # MLP parameters for interp == "learned"
+    learned_refit: bool = True  # learned rows: Eq. (3.6) weights over the MLP's choice
+    record: list | None = None  # if a list: (features, LS targets, fine mask) of every fit
 
 
 # ---------------------------------------------------------------------------------
@@ -556,7 +561,19 @@ def _split(B, grid, level: int, opts: Opts):
 def _build_interp(lv: Level, X: np.ndarray, active: np.ndarray, opts: Opts):
     Xh, w = normalize_weights(lv.B, X, active, opts.weight_floor)
     lv.cand, lv.ncand = neighborhoods(lv.B, lv.cf, lv.cidx, opts.z, opts.mmax)
-    P = ls_interpolation(Xh[:, active], w[active], lv.cf, lv.cidx, lv.cand, lv.ncand, opts.caliber, opts.ridge)
+    if opts.interp == "learned" or opts.record is not None:
+        from . import learned
+
+        feats = learned.features(lv.B, lv.cf, Xh[:, active], w[active], lv.cand, lv.ncand)
+    if opts.interp == "learned":
+        y, _ = learned.forward(opts.model, feats)
+        P = learned.learned_rows(y, Xh[:, active], w[active], lv.cf, lv.cidx, lv.cand, lv.ncand, opts.caliber,
+                                 opts.learned_refit, opts.ridge)
+    else:
+        P = ls_interpolation(Xh[:, active], w[active], lv.cf, lv.cidx, lv.cand, lv.ncand, opts.caliber, opts.ridge)
+        if opts.record is not None:
+            tg = learned.ls_targets(Xh[:, active], w[active], lv.cf, lv.cand, lv.ncand, opts.caliber, opts.ridge)
+            opts.record.append((feats, tg, ~lv.cf))
     Q = averaging_restriction(P)
     return Xh, w, P, Q
 
