@@ -69,6 +69,9 @@ typedef struct {
     const void* val;
 } bamg_mat;
 
+/* The MLP of the learned interpolation (opaque; bamg_model_create). */
+typedef struct bamg_model bamg_model;
+
 typedef struct {
     double omega;       /* omega-Jacobi damping (Section 3: 0.7) */
     int32_t nu_tv;      /* setup sweeps on the random test vectors */
@@ -95,7 +98,15 @@ typedef struct {
     int32_t cr_max_rounds;
     double cr_omega;
     void* stream;       /* cudaStream_t for all work of the handle */
+    /* learned interpolation (no counterpart in the paper; see bamg_model_create) */
+    int32_t interp;     /* BAMG_INTERP_LS (Algorithm 2) or BAMG_INTERP_LEARNED */
+    int32_t learned_refit; /* learned rows: 1 = Eq. (3.6) weights over the MLP's choice, 0 = MLP weights */
+    const bamg_model* model; /* the MLP for BAMG_INTERP_LEARNED (caller keeps ownership) */
+    double learned_rho_max; /* > 0: fall back to least squares when the learned hierarchy's
+                               V-cycle factor (bamg_vcycle_factor, 20 steps) exceeds this */
 } bamg_opts;
+
+enum { BAMG_INTERP_LS = 0, BAMG_INTERP_LEARNED = 1 };
 
 typedef struct {
     int32_t status;
@@ -203,6 +214,52 @@ int bamg_hierarchy_precision(const bamg_handle* h);
 int bamg_smooth_apply(bamg_handle* h, int level, int sweeps, const void* b, void* x, void* work);
 
 /* ---------------------------------------------------------------------------------
+ * Learned interpolation.  No counterpart in the paper: a 112-128-128-16 ReLU MLP maps the
+ * features of a fine point (its candidates of Eq. (3.5): per slot [valid, path length / 3,
+ * g_ij / g_jj, g_ij / sqrt(g_ii g_jj), -b_ij / b_ii, -b_ji / b_jj] with g_ab the LS-weighted
+ * test-vector inner products of Section 3.2, then [m / 16, sum_{j!=i} |b_ij| / b_ii],
+ * zero-padded) to 16 slot weights; the c slots of largest |y| form the row of P, with the
+ * MLP's weights or the Eq. (3.6) minimiser over them (learned_refit).  It is trained on
+ * the least-squares rows of Algorithm 2 (bamg_interp_dataset).  Products take bfloat16
+ * inputs with FP32 sums; loss = (1/rows) sum over valid slots of (y - t)^2; Adam with
+ * beta1 = 0.9, beta2 = 0.999, eps = 1e-8.  Parameters: one flat FP32 array
+ * [W1 (128 x 112) | b1 | W2 (128 x 128) | b2 | W3 (16 x 128) | b3], W row-major (out x in).
+ * All calls are synchronous with respect to the host except bamg_model_forward.
+ * --------------------------------------------------------------------------------- */
+enum { BAMG_MLP_F = 112, BAMG_MLP_H = 128, BAMG_MLP_S = 16 };
+/* He-uniform weights W = (2u - 1) sqrt(6 / fan_in), u from SplitMix64 (seed, layer, index). */
+int bamg_model_create(uint64_t seed, bamg_model** m);
+void bamg_model_free(bamg_model* m);
+int64_t bamg_model_param_count(void);
+/* host FP32 parameters in (set; resets Adam) or out (get); count = bamg_model_param_count() */
+int bamg_model_set(bamg_model* m, const float* h_params, int64_t count);
+int bamg_model_get(const bamg_model* m, float* h_params, int64_t count);
+/* d_out (rows x 16, FP32) = MLP(d_feat (rows x 112, FP32)); asynchronous on stream */
+int bamg_model_forward(const bamg_model* m, const float* d_feat, int64_t rows, float* d_out, void* stream);
+/* gradient of the loss over all rows (one batch) into h_grad (param_count floats, may be
+ * NULL) and the loss into *h_loss; parameters unchanged */
+int bamg_model_gradients(bamg_model* m, const float* d_feat, const float* d_target, int64_t rows, float* h_grad,
+                         double* h_loss, void* stream);
+/* epochs x (rows / batch) Adam steps over contiguous batches in row order; h_epoch_loss
+ * (epochs doubles, may be NULL) = mean batch loss of each epoch */
+int bamg_model_train(bamg_model* m, const float* d_feat, const float* d_target, int64_t rows, int epochs, int batch,
+                     double lr, double* h_epoch_loss, void* stream);
+/* Training data: runs the least-squares setup of A and writes, for every point of every
+ * level of both passes, its features (d_feat, rows x 112) and its Algorithm 2 row on the
+ * slots (d_target, rows x 16; coarse points and empty slots 0).  *h_rows = rows needed;
+ * BAMG_ESIZE (nothing written beyond cap_rows) when cap_rows is smaller. */
+int bamg_interp_dataset(const bamg_csr* A, int r, int levels, const bamg_opts* o, float* d_feat, float* d_target,
+                        int64_t cap_rows, int64_t* h_rows);
+/* rho of the stationary iteration x <- x - C B x: power iteration on the residual
+ * propagator I - B C (mean removed, unit norm each step) from B x0, x0 in U[1, 2)
+ * (SplitMix64 seed 7); geometric mean of the growth over the second half of iters. */
+int bamg_vcycle_factor(bamg_handle* h, int iters, double* rho);
+/* BAMG_INTERP_LS or BAMG_INTERP_LEARNED: the interpolation the hierarchy was built with
+ * (LS after a fallback); *h_rho (may be NULL) = the factor measured for the fallback
+ * decision, or 0 when none was measured. */
+int bamg_hierarchy_interp(const bamg_handle* h, double* h_rho);
+
+/* ---------------------------------------------------------------------------------
  * Step entry points: one step of the setup on caller buffers (device memory).
  * --------------------------------------------------------------------------------- */
 
@@ -262,6 +319,18 @@ int bamg_coarsen_cr(const bamg_mat* B, int level, uint64_t seed, double theta, i
 int bamg_interp_ls(int dtype, const bamg_mat* B, const uint8_t* cf, const int32_t* cidx, const void* X,
                    int ncols, int ld, const double* d_w, int z, int mmax, int c, double ridge,
                    int32_t* pcol, void* pval, int32_t* pcnt, void* stream);
+
+/* The LS kernel's candidates and features without Algorithm 2 (d_target == NULL), or with
+ * it (d_target: the LS rows on the slots, and P written to pcol/pval/pcnt when these are
+ * not NULL): d_feat rows x 112 and d_cand (rows x 16, -1 padded) may each be NULL. */
+int bamg_interp_features(int dtype, const bamg_mat* B, const uint8_t* cf, const int32_t* cidx, const void* X, int ncols,
+                         int ld, const double* d_w, int z, int mmax, int c, double ridge, float* d_feat,
+                         float* d_target, int32_t* d_cand, void* stream);
+/* Learned interpolation of one level (arguments as bamg_interp_ls, plus the model and
+ * refit): P in ELL form (pcol/pval/pcnt). */
+int bamg_interp_learned(int dtype, const bamg_mat* B, const uint8_t* cf, const int32_t* cidx, const void* X, int ncols,
+                        int ld, const double* d_w, int z, int mmax, int c, double ridge, const bamg_model* m, int refit,
+                        int32_t* pcol, void* pval, int32_t* pcnt, void* stream);
 
 /* Petrov-Galerkin products B_c = Q B P and T_c = Q T P (Section 1 step 3; Algorithm 3)
  * with the averaging Q of Section 4 (Q[I,i] = 1/pcnt[i] for I in row i of P).

@@ -14,7 +14,7 @@ import torch
 from . import _capi as capi
 from ._capi import BamgError  # noqa: F401
 
-__all__ = ["Solver", "solve_batch", "import_hierarchy", "tv_init", "relax", "relax_noalloc", "tv_weights", "coarsen_grid", "coarsen_cr",
+__all__ = ["Solver", "Model", "solve_batch", "interp_dataset", "interp_features", "interp_learned", "import_hierarchy", "tv_init", "relax", "relax_noalloc", "tv_weights", "coarsen_grid", "coarsen_cr",
            "interp_ls", "galerkin", "coarse_eig", "launch_count", "default_opts", "BamgError"]
 
 
@@ -62,6 +62,13 @@ def default_opts(**kw) -> capi.Opts:
         kw["precision"] = {"fp64": capi.PREC_FP64, "mixed": capi.PREC_MIXED}[kw["precision"]]
     if "coarsen" in kw and isinstance(kw["coarsen"], str):
         kw["coarsen"] = {"grid": capi.COARSEN_GRID, "cr": capi.COARSEN_CR}[kw["coarsen"]]
+    if "interp" in kw and isinstance(kw["interp"], str):
+        kw["interp"] = {"ls": capi.INTERP_LS, "learned": capi.INTERP_LEARNED}[kw["interp"]]
+    if "model" in kw:
+        m = kw.pop("model")
+        kw["model"] = m._h.value if m is not None else None
+    if "learned_refit" in kw:
+        kw["learned_refit"] = int(bool(kw["learned_refit"]))
     if "grid" in kw:
         g = kw.pop("grid")
         if g is not None:
@@ -141,6 +148,20 @@ class Solver:
             work = torch.empty_like(x)
         capi.check(_lib().bamg_smooth_apply(self._h, level, sweeps, _p(b), _p(x), _p(work)))
         return x
+
+    def vcycle_factor(self, iters: int = 20) -> float:
+        """V-cycle factor of x <- x - C B x (power iteration on I - B C, bamg_vcycle_factor)."""
+        rho = C.c_double()
+        capi.check(_lib().bamg_vcycle_factor(self._h, iters, C.byref(rho)))
+        return rho.value
+
+    def interp_used(self):
+        """("ls" | "learned", the V-cycle factor measured for the fallback decision or 0)."""
+        rho = C.c_double()
+        code = _lib().bamg_hierarchy_interp(self._h, C.byref(rho))
+        if code < 0:
+            raise BamgError(code, "bad handle")
+        return ("learned" if code == capi.INTERP_LEARNED else "ls"), rho.value
 
     def info(self) -> dict:
         L = C.c_int(0)
@@ -231,6 +252,107 @@ def solve_batch(chains, r, levels, tol: float, opts=None, workers: int = 0, host
         err.stats = stats
         raise err
     return outs, stats
+
+
+class Model:
+    """The MLP of the learned interpolation (bamg_model_*): 112 features -> 128 -> 128 -> 16
+    slot weights, bfloat16 products with FP32 sums, trained with Adam on LS rows."""
+
+    F, H, S = capi.MLP_F, capi.MLP_H, capi.MLP_S
+
+    def __init__(self, seed: int = 0):
+        self._h = C.c_void_p(0)
+        capi.check(_lib().bamg_model_create(seed, C.byref(self._h)))
+        self.n_params = int(_lib().bamg_model_param_count())
+
+    def close(self):
+        if self._h.value:
+            _lib().bamg_model_free(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        capi.check(_lib().bamg_model_get(self._h, out.ctypes.data, self.n_params))
+        return out
+
+    def set(self, params) -> None:
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.n_params
+        capi.check(_lib().bamg_model_set(self._h, a.ctypes.data, self.n_params))
+
+    def forward(self, feat: torch.Tensor) -> torch.Tensor:
+        assert feat.dtype == torch.float32 and feat.is_contiguous() and feat.shape[1] == self.F
+        y = torch.empty(feat.shape[0], self.S, dtype=torch.float32, device=feat.device)
+        capi.check(_lib().bamg_model_forward(self._h, _p(feat), feat.shape[0], _p(y), _stream()))
+        return y
+
+    def gradients(self, feat: torch.Tensor, target: torch.Tensor):
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = C.c_double()
+        capi.check(_lib().bamg_model_gradients(self._h, _p(feat), _p(target), feat.shape[0], g.ctypes.data,
+                                               C.byref(loss), _stream()))
+        return g, loss.value
+
+    def train(self, feat: torch.Tensor, target: torch.Tensor, epochs: int, batch: int, lr: float):
+        """Adam over contiguous batches in row order; returns the mean batch loss per epoch."""
+        assert feat.is_contiguous() and target.is_contiguous()
+        hist = np.zeros(max(epochs, 1))
+        capi.check(_lib().bamg_model_train(self._h, _p(feat), _p(target), feat.shape[0], epochs, batch, float(lr),
+                                           hist.ctypes.data, _stream()))
+        return hist[:epochs]
+
+
+def interp_dataset(row_ptr, col, val, r: int, levels: int, **opts):
+    """(features, LS targets) of every point of every level of a least-squares setup
+    (bamg_interp_dataset), as float32 CUDA tensors (rows x 112, rows x 16)."""
+    n = int(row_ptr.numel() - 1)
+    A = capi.Csr(n, int(col.numel()), _p(_i32(row_ptr)).value, _p(_i32(col)).value, _p(val).value, 0)
+    o = default_opts(**opts)
+    o.stream = _stream().value
+    need = C.c_int64(0)
+    code = _lib().bamg_interp_dataset(C.byref(A), r, levels, C.byref(o), None, None, 0, C.byref(need))
+    if code not in (capi.BAMG_OK, capi.BAMG_ESIZE):
+        capi.check(code)
+    rows = need.value
+    feat = torch.empty(rows, capi.MLP_F, dtype=torch.float32, device=row_ptr.device)
+    tgt = torch.empty(rows, capi.MLP_S, dtype=torch.float32, device=row_ptr.device)
+    capi.check(_lib().bamg_interp_dataset(C.byref(A), r, levels, C.byref(o), _p(feat), _p(tgt), rows,
+                                          C.byref(need)))
+    return feat, tgt
+
+
+def interp_features(B, cf, cidx, X, ncols, w, z=2, mmax=16, c=2, ridge=1e-4, targets=False):
+    """The LS kernel's per-point features (and, with targets, its LS rows on the slots and
+    candidates) for one level (bamg_interp_features)."""
+    rp, ci, v = B
+    n = int(rp.numel() - 1)
+    m = _mat(rp, ci, v)
+    feat = torch.empty(n, capi.MLP_F, dtype=torch.float32, device=v.device)
+    tgt = torch.empty(n, capi.MLP_S, dtype=torch.float32, device=v.device) if targets else None
+    cand = torch.empty(n, capi.MLP_S, dtype=torch.int32, device=v.device)
+    capi.check(_lib().bamg_interp_features(_dtype_code(v), C.byref(m), _p(cf), _p(cidx), _p(X), ncols, X.shape[1],
+                                           _p(w), z, mmax, c, float(ridge), _p(feat), _p(tgt), _p(cand), _stream()))
+    return feat, tgt, cand
+
+
+def interp_learned(B, cf, cidx, X, ncols, w, model: Model, refit=True, z=2, mmax=16, c=2, ridge=1e-4):
+    """Learned interpolation of one level (bamg_interp_learned): P in ELL form."""
+    rp, ci, v = B
+    n = int(rp.numel() - 1)
+    m = _mat(rp, ci, v)
+    pcol = torch.empty(n * c, dtype=torch.int32, device=v.device)
+    pval = torch.empty(n * c, dtype=v.dtype, device=v.device)
+    pcnt = torch.empty(n, dtype=torch.int32, device=v.device)
+    capi.check(_lib().bamg_interp_learned(_dtype_code(v), C.byref(m), _p(cf), _p(cidx), _p(X), ncols, X.shape[1],
+                                          _p(w), z, mmax, c, float(ridge), model._h, int(bool(refit)), _p(pcol),
+                                          _p(pval), _p(pcnt), _stream()))
+    return pcol.view(n, c), pval.view(n, c), pcnt
 
 
 def import_hierarchy(levels, pinv: np.ndarray, x_init: np.ndarray, **opts) -> Solver:

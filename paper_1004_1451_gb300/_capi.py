@@ -15,6 +15,8 @@ F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 COARSEN_GRID, COARSEN_CR = 0, 1
 X_GUESS, X_HOST = 1, 2
+INTERP_LS, INTERP_LEARNED = 0, 1
+MLP_F, MLP_H, MLP_S = 112, 128, 16
 EXPORT_B, EXPORT_T, EXPORT_P, EXPORT_CF, EXPORT_X, EXPORT_PINV, EXPORT_XINIT, EXPORT_LAMBDA = range(8)
 
 ERROR_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOTSTOCH", -3: "ECUDA", -4: "ENOMEM", -5: "ENOCONV", -6: "ETIMEOUT",
@@ -39,7 +41,8 @@ class Opts(C.Structure):
                 ("seed", C.c_uint64), ("tv_lo", C.c_double), ("tv_hi", C.c_double), ("ev_change_tol", C.c_double),
                 ("ridge", C.c_double), ("ridge32", C.c_double), ("weight_floor", C.c_double),
                 ("cr_theta", C.c_double), ("cr_nu", C.c_int32), ("cr_max_rounds", C.c_int32),
-                ("cr_omega", C.c_double), ("stream", C.c_void_p)]
+                ("cr_omega", C.c_double), ("stream", C.c_void_p), ("interp", C.c_int32), ("learned_refit", C.c_int32),
+                ("model", C.c_void_p), ("learned_rho_max", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -85,6 +88,20 @@ SIGNATURES = {
     "bamg_galerkin": (_I, [_I, C.POINTER(Mat), _P, _I, _P, _P, _P, _I, _P, _P, _P, _P, C.c_int64,
                            C.POINTER(C.c_int64), _P]),
     "bamg_coarse_eig": (_I, [_I, _I, _P, _P, _I, _P, _P, _P, C.POINTER(_I), _P, _P]),
+    "bamg_interp_features": (_I, [_I, C.POINTER(Mat), _P, _P, _P, _I, _I, _P, _I, _I, _I, _D, _P, _P, _P, _P]),
+    "bamg_interp_learned": (_I, [_I, C.POINTER(Mat), _P, _P, _P, _I, _I, _P, _I, _I, _I, _D, _P, _I, _P, _P, _P,
+                                 _P]),
+    "bamg_model_create": (_I, [C.c_uint64, C.POINTER(_P)]),
+    "bamg_model_free": (None, [_P]),
+    "bamg_model_param_count": (C.c_int64, []),
+    "bamg_model_set": (_I, [_P, _P, C.c_int64]),
+    "bamg_model_get": (_I, [_P, _P, C.c_int64]),
+    "bamg_model_forward": (_I, [_P, _P, C.c_int64, _P, _P]),
+    "bamg_model_gradients": (_I, [_P, _P, _P, C.c_int64, _P, C.POINTER(_D), _P]),
+    "bamg_model_train": (_I, [_P, _P, _P, C.c_int64, _I, _I, _D, _P, _P]),
+    "bamg_interp_dataset": (_I, [C.POINTER(Csr), _I, _I, C.POINTER(Opts), _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
+    "bamg_vcycle_factor": (_I, [_P, _I, C.POINTER(_D)]),
+    "bamg_hierarchy_interp": (_I, [_P, C.POINTER(_D)]),
 }
 
 _lib = None

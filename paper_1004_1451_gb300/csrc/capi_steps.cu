@@ -1,6 +1,7 @@
 // C ABI of the single setup steps (bamg.h, "Step entry points"): thin wrappers that
 // validate the arguments and run the same launchers the hierarchy uses.
 #include <cstring>
+#include <memory>
 
 #include "kernels.cuh"
 
@@ -125,10 +126,12 @@ int bamg_interp_ls(int dtype, const bamg_mat* B, const uint8_t* cf, const int32_
                      "bad interp_ls args");
         int e;
         if (dtype == BAMG_F64)
-            e = interp_ls<double>(B->n, B->row_ptr, B->col, cf, cidx, (const double*)X, ncols, ld, d_w, z, mmax, c,
+            e = interp_ls<double>(B->n, B->row_ptr, B->col, (const double*)B->val, cf, cidx, (const double*)X, ncols,
+                                  ld, d_w, z, mmax, c,
                                   ridge, pcol, (double*)pval, pcnt, s);
         else if (dtype == BAMG_F32)
-            e = interp_ls<float>(B->n, B->row_ptr, B->col, cf, cidx, (const float*)X, ncols, ld, d_w, z, mmax, c,
+            e = interp_ls<float>(B->n, B->row_ptr, B->col, (const float*)B->val, cf, cidx, (const float*)X, ncols, ld,
+                                 d_w, z, mmax, c,
                                  ridge, pcol, (float*)pval, pcnt, s);
         else
             throw Error(BAMG_EINVAL, "bad dtype");
@@ -167,6 +170,44 @@ static void galerkin_step(const bamg_mat* Bm, const void* T_val, int nc, const i
 }
 }  // namespace bamg
 
+namespace bamg {
+template <typename T>
+static void features_step(const bamg_mat* B, const uint8_t* cf, const int32_t* cidx, const void* X, int ncols, int ld,
+                          const double* d_w, int z, int mmax, int c, double ridge, float* d_feat, float* d_target,
+                          int32_t* d_cand, cudaStream_t s) {
+    AllocStream as_(s);
+    const MatView<T> Bv = view<T>(B);
+    TmpBuf<int32_t> pcol((size_t)Bv.n * c, s), pcnt(Bv.n, s);
+    TmpBuf<T> pval((size_t)Bv.n * c, s);
+    LsOut ex;
+    ex.feat = d_feat;
+    ex.target = d_target;
+    ex.cand = d_cand;
+    ex.greedy = d_target != nullptr;
+    const int e = interp_ls<T>(Bv.n, Bv.rp, Bv.ci, Bv.v, cf, cidx, (const T*)X, ncols, ld, d_w, z, mmax, c, ridge,
+                               pcol.get(), pval.get(), pcnt.get(), s, nullptr, ex);
+    BAMG_REQUIRE(e == 0, BAMG_EOVERFLOW, "neighbourhood search: a fine point needs more than 2048 recorded states");
+    BAMG_CK(cudaStreamSynchronize(s));
+}
+
+template <typename T>
+static void learned_step(const bamg_mat* B, const uint8_t* cf, const int32_t* cidx, const void* X, int ncols, int ld,
+                         const double* d_w, int z, int mmax, int c, double ridge, const bamg_model* m, int refit,
+                         int32_t* pcol, void* pval, int32_t* pcnt, cudaStream_t s) {
+    AllocStream as_(s);
+    const MatView<T> Bv = view<T>(B);
+    TmpBuf<int> err(1, s);
+    BAMG_CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    interp_learned<T>(Bv.n, Bv.rp, Bv.ci, Bv.v, cf, cidx, (const T*)X, ncols, ld, d_w, z, mmax, c, ridge, m->impl,
+                      refit != 0, pcol, (T*)pval, pcnt, s, err.get());
+    int h = 0;
+    BAMG_CK(cudaMemcpyAsync(&h, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    BAMG_CK(cudaStreamSynchronize(s));
+    BAMG_REQUIRE(h == 0, BAMG_EOVERFLOW, "neighbourhood search: a fine point needs more than 2048 recorded states");
+}
+
+}  // namespace bamg
+
 extern "C" {
 
 int bamg_galerkin(int dtype, const bamg_mat* B, const void* T_val, int nc, const int32_t* pcol, const void* pval,
@@ -198,6 +239,101 @@ int bamg_coarse_eig(int dtype, int n, const double* d_B, const double* d_T, int 
             BAMG_REQUIRE(coarse_pinv(n, d_B, d_pinv, dtype == BAMG_F32, s) == 0, BAMG_ENUMERIC,
                          "singular coarsest factor");
         BAMG_CK(cudaStreamSynchronize(s));
+    });
+}
+
+
+int bamg_interp_features(int dtype, const bamg_mat* B, const uint8_t* cf, const int32_t* cidx, const void* X, int ncols,
+                         int ld, const double* d_w, int z, int mmax, int c, double ridge, float* d_feat,
+                         float* d_target, int32_t* d_cand, void* stream) {
+    return guard([&] {
+        BAMG_REQUIRE(B && cf && cidx && X && d_w && ncols <= ld && mmax <= 16, BAMG_EINVAL, "bad interp_features args");
+        if (dtype == BAMG_F64)
+            features_step<double>(B, cf, cidx, X, ncols, ld, d_w, z, mmax, c, ridge, d_feat, d_target, d_cand,
+                                  (cudaStream_t)stream);
+        else if (dtype == BAMG_F32)
+            features_step<float>(B, cf, cidx, X, ncols, ld, d_w, z, mmax, c, ridge, d_feat, d_target, d_cand,
+                                 (cudaStream_t)stream);
+        else
+            throw Error(BAMG_EINVAL, "bad dtype");
+    });
+}
+
+int bamg_interp_learned(int dtype, const bamg_mat* B, const uint8_t* cf, const int32_t* cidx, const void* X, int ncols,
+                        int ld, const double* d_w, int z, int mmax, int c, double ridge, const bamg_model* m, int refit,
+                        int32_t* pcol, void* pval, int32_t* pcnt, void* stream) {
+    return guard([&] {
+        BAMG_REQUIRE(B && cf && cidx && X && d_w && m && m->impl && pcol && pval && pcnt && ncols <= ld,
+                     BAMG_EINVAL, "bad interp_learned args");
+        if (dtype == BAMG_F64)
+            learned_step<double>(B, cf, cidx, X, ncols, ld, d_w, z, mmax, c, ridge, m, refit, pcol, pval, pcnt,
+                                 (cudaStream_t)stream);
+        else if (dtype == BAMG_F32)
+            learned_step<float>(B, cf, cidx, X, ncols, ld, d_w, z, mmax, c, ridge, m, refit, pcol, pval, pcnt,
+                                (cudaStream_t)stream);
+        else
+            throw Error(BAMG_EINVAL, "bad dtype");
+    });
+}
+
+// ------------------------------------------------------------------ the model
+int bamg_model_create(uint64_t seed, bamg_model** m) {
+    return guard([&] {
+        BAMG_REQUIRE(m, BAMG_EINVAL, "null model pointer");
+        *m = nullptr;
+        auto h = std::make_unique<bamg_model>();
+        h->impl = mlp_create(seed, nullptr);
+        BAMG_CK(cudaStreamSynchronize(nullptr));
+        *m = h.release();
+    });
+}
+
+void bamg_model_free(bamg_model* m) {
+    if (!m) return;
+    mlp_destroy(m->impl);
+    delete m;
+}
+
+int64_t bamg_model_param_count(void) { return mlp_param_count(); }
+
+int bamg_model_set(bamg_model* m, const float* h_params, int64_t count) {
+    return guard([&] {
+        BAMG_REQUIRE(m && m->impl && h_params && count == mlp_param_count(), BAMG_EINVAL, "bad model_set args");
+        mlp_set(m->impl, h_params, nullptr);
+        BAMG_CK(cudaStreamSynchronize(nullptr));
+    });
+}
+
+int bamg_model_get(const bamg_model* m, float* h_params, int64_t count) {
+    return guard([&] {
+        BAMG_REQUIRE(m && m->impl && h_params && count == mlp_param_count(), BAMG_EINVAL, "bad model_get args");
+        mlp_get(m->impl, h_params, nullptr);
+    });
+}
+
+int bamg_model_forward(const bamg_model* m, const float* d_feat, int64_t rows, float* d_out, void* stream) {
+    return guard([&] {
+        BAMG_REQUIRE(m && m->impl && rows >= 0 && (rows == 0 || (d_feat && d_out)), BAMG_EINVAL,
+                     "bad model_forward args");
+        mlp_forward(m->impl, rows, d_feat, d_out, (cudaStream_t)stream);
+    });
+}
+
+int bamg_model_gradients(bamg_model* m, const float* d_feat, const float* d_target, int64_t rows, float* h_grad,
+                         double* h_loss, void* stream) {
+    return guard([&] {
+        BAMG_REQUIRE(m && m->impl && rows > 0 && d_feat && d_target, BAMG_EINVAL, "bad model_gradients args");
+        const double l = mlp_gradients(m->impl, rows, d_feat, d_target, h_grad, (cudaStream_t)stream);
+        if (h_loss) *h_loss = l;
+    });
+}
+
+int bamg_model_train(bamg_model* m, const float* d_feat, const float* d_target, int64_t rows, int epochs, int batch,
+                     double lr, double* h_epoch_loss, void* stream) {
+    return guard([&] {
+        BAMG_REQUIRE(m && m->impl && rows > 0 && d_feat && d_target && epochs >= 0 && batch > 0 && lr > 0.0,
+                     BAMG_EINVAL, "bad model_train args");
+        mlp_train(m->impl, rows, d_feat, d_target, epochs, batch, lr, h_epoch_loss, (cudaStream_t)stream);
     });
 }
 

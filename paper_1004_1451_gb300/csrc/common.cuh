@@ -52,6 +52,12 @@ inline unsigned blocks_for(int64_t work, int per_block) {
 // Stream on which DevBuf allocations are ordered (set by the owner of the work: the
 // handle's stream during setup and solve).  Thread-local.
 cudaStream_t& alloc_stream();
+// Sets alloc_stream() for a scope.
+struct AllocStream {
+    cudaStream_t prev;
+    explicit AllocStream(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
+    ~AllocStream() { alloc_stream() = prev; }
+};
 
 // Owning device buffer from the stream-ordered pool (cudaMallocAsync on alloc_stream()),
 // so building a hierarchy does not synchronise the device for every allocation.

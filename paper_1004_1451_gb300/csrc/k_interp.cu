@@ -193,6 +193,66 @@ __device__ __forceinline__ bool chol_solve(T (&A)[CMAX][CMAX], const T (&b)[CMAX
     return true;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// b_rc, or 0 when column c is not in row r
+template <typename T>
+__device__ __forceinline__ T entry_of(int r, int c, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                      const T* __restrict__ bv) {
+    for (int p = rp[r]; p < rp[r + 1]; ++p)
+        if (ci[p] == c) return bv[p];
+    return T(0);
+}
+
+// Features of fine point i for the learned interpolation (one warp; lane s < ncand holds
+// candidate `node` with path length `depth`, g_jj = gss and g_ij = bs): per slot
+// [1, d / 3, g_ij / g_jj, g_ij / sqrt(g_ii g_jj), -b_ij / b_ii, -b_ji / b_jj] (ratios with a
+// zero denominator are 0), zeros for empty slots, then [m / 16, sum_{j != i} |b_ij| / b_ii],
+// zero-padded to MLP_F.
+template <typename T>
+__device__ void learned_features(int i, int lane, int node, int ncand, int depth, T gss, T bs, const T* xi,
+                                 const T* s_w, int ncols, const int32_t* __restrict__ rp,
+                                 const int32_t* __restrict__ ci, const T* __restrict__ bv, float* f) {
+    T gii = T(0);
+    for (int k = 0; k < ncols; ++k) gii += s_w[k] * xi[k] * xi[k];
+    T bii_l = T(0), off_l = T(0);
+    for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+        const T v = bv[p];
+        if (ci[p] == i)
+            bii_l += v;
+        else
+            off_l += v < T(0) ? -v : v;
+    }
+    const T bii = warp_sum_t(bii_l), off = warp_sum_t(off_l);
+    if (lane < MLP_S) {
+        float o[MLP_NF_SLOT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (lane < ncand && node >= 0) {
+            const T bij = entry_of<T>(i, node, rp, ci, bv);
+            const T bji = entry_of<T>(node, i, rp, ci, bv);
+            const T bjj = entry_of<T>(node, node, rp, ci, bv);
+            o[0] = 1.f;
+            o[1] = (float)((double)depth / 3.0);
+            o[2] = gss != T(0) ? (float)(bs / gss) : 0.f;
+            o[3] = gii * gss != T(0) ? (float)(bs / sqrt(gii * gss)) : 0.f;
+            o[4] = (float)(-bij / bii);
+            o[5] = (float)(-bji / bjj);
+        }
+#pragma unroll
+        for (int e = 0; e < MLP_NF_SLOT; ++e) f[MLP_NF_SLOT * lane + e] = o[e];
+    }
+    for (int k = MLP_NF_SLOT * MLP_S + lane; k < MLP_F; k += 32) {
+        float v = 0.f;
+        if (k == MLP_NF_SLOT * MLP_S) v = (float)((double)ncand / (double)MLP_S);
+        if (k == MLP_NF_SLOT * MLP_S + 1) v = (float)(off / bii);
+        f[k] = v;
+    }
+}
+
 // One warp per point.  Fine points: breadth-first search to depth z over the row
 // pattern of B (edges i -> j for b_ij != 0, i != j), continued up to depth 3 while no
 // coarse point has been found, and stopped early once mmax coarse points are known at
@@ -204,10 +264,11 @@ __device__ __forceinline__ bool chol_solve(T (&A)[CMAX][CMAX], const T (&b)[CMAX
 // ties) joins J.
 template <typename T, int CAP>
 __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                         const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx, const T* __restrict__ X,
+                         const T* __restrict__ bv, const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx, const T* __restrict__ X,
                          int ncols, int ld, const T* s_w, int z, int mmax, int c, double ridge,
                          int32_t* __restrict__ pcol, T* __restrict__ pval, int32_t* __restrict__ pcnt, int* vis,
-                         unsigned long long* key, uint8_t* dist, int* cand, T* xi, T (*xj)[KMAX], bool defer) {
+                         unsigned long long* key, uint8_t* dist, int* cand, uint8_t* cdep, T* xi, T (*xj)[KMAX],
+                         bool defer, const LsOut& ex) {
     const int lane = threadIdx.x & 31;
     const int64_t prow = (int64_t)i * c;
     if (cf[i]) {
@@ -216,6 +277,10 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
             pval[prow + lane] = lane == 0 ? T(1) : T(0);
         }
         if (lane == 0) pcnt[i] = 1;
+        if (ex.feat)
+            for (int k = lane; k < MLP_F; k += 32) ex.feat[(int64_t)i * MLP_F + k] = 0.f;
+        if (ex.target && lane < MLP_S) ex.target[(int64_t)i * MLP_S + lane] = 0.f;
+        if (ex.cand && lane < MLP_S) ex.cand[(int64_t)i * MLP_S + lane] = -1;
         return false;
     }
     // ---- neighbourhood search (Eq. (3.5))
@@ -299,7 +364,10 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
             const unsigned long long kq = key[q];
             int rank = 0;
             for (int q2 = 1; q2 < nvis; ++q2) rank += key[q2] < kq;
-            if (rank < mmax) cand[rank] = vis[q];
+            if (rank < mmax) {
+                cand[rank] = vis[q];
+                cdep[rank] = dist[q];
+            }
         }
     }
     const int ncand = ntot < mmax ? ntot : mmax;
@@ -315,6 +383,10 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
             gss += wk * v * v;
             bs += wk * v * xi[k];
         }
+    if (ex.cand && lane < MLP_S) ex.cand[(int64_t)i * MLP_S + lane] = node;
+    if (ex.feat) learned_features<T>(i, lane, node, ncand, lane < ncand ? cdep[lane] : 0, gss, bs, xi, s_w, ncols, rp,
+                                     ci, bv, ex.feat + (int64_t)i * MLP_F);
+    if (!ex.greedy) return false;
     T gsj[CMAX], GJJ[CMAX][CMAX], bJ[CMAX], pbest[CMAX];
     int J[CMAX];
 #pragma unroll
@@ -430,6 +502,13 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
         }
         pcnt[i] = nJ;
     }
+    if (ex.target && lane < MLP_S) {  // the LS row on the slots (Algorithm 2's choice)
+        float tv = 0.f;
+#pragma unroll
+        for (int a = 0; a < CMAX; ++a)
+            if (a < nJ && node >= 0 && J[a] == node) tv = (float)pbest[a];
+        ex.target[(int64_t)i * MLP_S + lane] = tv;
+    }
     return ovf;
 }
 
@@ -438,15 +517,17 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
 // pass (list != nullptr): persistent warps over the *list_count points of list.
 template <typename T, int CAP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
-    k_ls_fit(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const uint8_t* __restrict__ cf,
-             const int32_t* __restrict__ cidx, const T* __restrict__ X, int ncols, int ld, const double* __restrict__ w,
-             int z, int mmax, int c, double ridge, int32_t* __restrict__ pcol, T* __restrict__ pval,
-             int32_t* __restrict__ pcnt, const int* __restrict__ list, const int* __restrict__ list_count,
-             int* __restrict__ ovf_list, int* __restrict__ ovf_count, int* __restrict__ err) {
+    k_ls_fit(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
+             const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx, const T* __restrict__ X, int ncols,
+             int ld, const double* __restrict__ w, int z, int mmax, int c, double ridge, int32_t* __restrict__ pcol,
+             T* __restrict__ pval, int32_t* __restrict__ pcnt, const int* __restrict__ list,
+             const int* __restrict__ list_count, int* __restrict__ ovf_list, int* __restrict__ ovf_count,
+             int* __restrict__ err, LsOut ex) {
     __shared__ int s_vis[WARPS][CAP];
     __shared__ unsigned long long s_key[WARPS][CAP];
     __shared__ uint8_t s_dist[WARPS][CAP];
     __shared__ int s_cand[WARPS][MMAX];
+    __shared__ uint8_t s_cdep[WARPS][MMAX];
     __shared__ T s_xi[WARPS][KMAX];
     __shared__ T s_xj[WARPS][CMAX][KMAX];
     __shared__ T s_w[KMAX];
@@ -456,9 +537,9 @@ __global__ void __launch_bounds__(WARPS * 32)
     if (list == nullptr) {
         const int i = blockIdx.x * WARPS + wid;
         if (i >= n) return;
-        const bool ovf = ls_point<T, CAP>(i, rp, ci, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol, pval, pcnt,
-                                          s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_xi[wid], s_xj[wid],
-                                          ovf_list != nullptr);
+        const bool ovf = ls_point<T, CAP>(i, rp, ci, bv, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol, pval,
+                                          pcnt, s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_cdep[wid],
+                                          s_xi[wid], s_xj[wid], ovf_list != nullptr, ex);
         if (ovf && lane == 0) {
             if (ovf_list)
                 ovf_list[atomicAdd(ovf_count, 1)] = i;
@@ -469,17 +550,17 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
     const int cnt = *list_count;
     for (int k = blockIdx.x * WARPS + wid; k < cnt; k += gridDim.x * WARPS) {
-        const bool ovf = ls_point<T, CAP>(list[k], rp, ci, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol, pval,
-                                          pcnt, s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_xi[wid],
-                                          s_xj[wid], false);
+        const bool ovf = ls_point<T, CAP>(list[k], rp, ci, bv, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol,
+                                          pval, pcnt, s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_cdep[wid],
+                                          s_xi[wid], s_xj[wid], false, ex);
         if (ovf && lane == 0) atomicOr(err, 1);
     }
 }
 
 template <typename T>
-int interp_ls(int n, const int32_t* rp, const int32_t* ci, const uint8_t* cf, const int32_t* cidx, const T* X, int ncols,
-              int ld, const double* d_w, int z, int mmax, int c, double ridge, int32_t* pcol, T* pval, int32_t* pcnt,
-              cudaStream_t s, int* d_err) {
+int interp_ls(int n, const int32_t* rp, const int32_t* ci, const T* bv, const uint8_t* cf, const int32_t* cidx,
+              const T* X, int ncols, int ld, const double* d_w, int z, int mmax, int c, double ridge, int32_t* pcol,
+              T* pval, int32_t* pcnt, cudaStream_t s, int* d_err, const LsOut& ex) {
     BAMG_REQUIRE(ncols >= 1 && ncols <= KMAX, BAMG_EINVAL, "interp_ls: 1 <= ncols <= 32");
     BAMG_REQUIRE(c >= 1 && c <= CMAX, BAMG_EINVAL, "interp_ls: 1 <= caliber <= 4");
     BAMG_REQUIRE(mmax >= 1 && mmax <= MMAX, BAMG_EINVAL, "interp_ls: 1 <= mmax <= 16");
@@ -491,17 +572,124 @@ int interp_ls(int n, const int32_t* rp, const int32_t* ci, const uint8_t* cf, co
     BAMG_CK(cudaMemsetAsync(ocount.get(), 0, sizeof(int), s));
     int* e = d_err ? d_err : err.get();  // with d_err the caller reads the overflow flag later
     if (!d_err) BAMG_CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
-    BAMG_LAUNCH((k_ls_fit<T, VIS_CAP, LS_WARPS>), blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, cf, cidx, X,
-                ncols, ld, d_w, z, mmax, c, ridge, pcol, pval, pcnt, (const int*)nullptr, (const int*)nullptr,
-                olist.get(), ocount.get(), e);
-    BAMG_LAUNCH((k_ls_fit<T, VIS_CAP2, 1>), LS2_BLOCKS, 32, 0, s, n, rp, ci, cf, cidx, X, ncols, ld, d_w, z, mmax, c,
-                ridge, pcol, pval, pcnt, (const int*)olist.get(), (const int*)ocount.get(), (int*)nullptr,
-                (int*)nullptr, e);
+    BAMG_LAUNCH((k_ls_fit<T, VIS_CAP, LS_WARPS>), blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, bv, cf,
+                cidx, X, ncols, ld, d_w, z, mmax, c, ridge, pcol, pval, pcnt, (const int*)nullptr, (const int*)nullptr,
+                olist.get(), ocount.get(), e, ex);
+    BAMG_LAUNCH((k_ls_fit<T, VIS_CAP2, 1>), LS2_BLOCKS, 32, 0, s, n, rp, ci, bv, cf, cidx, X, ncols, ld, d_w, z, mmax,
+                c, ridge, pcol, pval, pcnt, (const int*)olist.get(), (const int*)ocount.get(), (int*)nullptr,
+                (int*)nullptr, e, ex);
     if (d_err) return 0;
     int h = 0;
     BAMG_CK(cudaMemcpyAsync(&h, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     BAMG_CK(cudaStreamSynchronize(s));
     return h ? BAMG_EOVERFLOW : 0;
+}
+
+// ================================================================ learned interpolation
+// One thread per fine point: the c valid slots of largest |y| (lower slot on ties) form J;
+// weights y, or with refit the minimiser of Eq. (3.6) over J with the Tikhonov term
+// delta = ridge tr(G_JJ) / |J| (R25); the row is stored sorted by coarse index.
+template <typename T>
+__global__ void k_learned_select(int n, const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx,
+                                 const int32_t* __restrict__ cand, const float* __restrict__ Y, const T* __restrict__ X,
+                                 int ncols, int ld, const double* __restrict__ w, int c, int refit, double ridge,
+                                 int32_t* __restrict__ pcol, T* __restrict__ pval, int32_t* __restrict__ pcnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || cf[i]) return;
+    const int32_t* cd = cand + (int64_t)i * MLP_S;
+    const float* y = Y + (int64_t)i * MLP_S;
+    int m = 0;
+    while (m < MLP_S && cd[m] >= 0) ++m;
+    int slot[CMAX];
+    int nJ = 0;
+    unsigned used = 0u;
+    for (int t = 0; t < c && t < m; ++t) {
+        int best = -1;
+        float bv = -1.f;
+        for (int q = 0; q < m; ++q) {
+            const float a = fabsf(y[q]);
+            if (!((used >> q) & 1u) && a > bv) {
+                bv = a;
+                best = q;
+            }
+        }
+        if (best < 0) break;
+        used |= 1u << best;
+        slot[nJ++] = best;
+    }
+    T p[CMAX];
+#pragma unroll
+    for (int a = 0; a < CMAX; ++a) p[a] = (a < nJ) ? (T)y[slot[a < nJ ? a : 0]] : T(0);
+    if (refit && nJ > 0) {
+        T A[CMAX][CMAX], rhs[CMAX], sol[CMAX];
+        T tr = T(0);
+#pragma unroll
+        for (int a = 0; a < CMAX; ++a) {
+            rhs[a] = T(0);
+#pragma unroll
+            for (int b = 0; b < CMAX; ++b) A[a][b] = T(0);
+        }
+        const T* xi = X + (int64_t)i * ld;
+        for (int a = 0; a < nJ; ++a) {
+            const T* xa = X + (int64_t)cd[slot[a]] * ld;
+            for (int b = 0; b <= a; ++b) {
+                const T* xb = X + (int64_t)cd[slot[b]] * ld;
+                T g = T(0);
+                for (int k = 0; k < ncols; ++k) g += (T)w[k] * xa[k] * xb[k];
+                A[a][b] = g;
+                A[b][a] = g;
+            }
+            T r = T(0);
+            for (int k = 0; k < ncols; ++k) r += (T)w[k] * xa[k] * xi[k];
+            rhs[a] = r;
+            tr += A[a][a];
+        }
+        const T delta = (T)ridge * tr / (T)nJ;
+        for (int a = 0; a < nJ; ++a) A[a][a] += delta;
+        if (chol_solve<T>(A, rhs, nJ, sol))
+#pragma unroll
+            for (int a = 0; a < CMAX; ++a) p[a] = a < nJ ? sol[a] : T(0);
+    }
+    int cols[CMAX];
+#pragma unroll
+    for (int a = 0; a < CMAX; ++a) cols[a] = a < nJ ? cidx[cd[slot[a < nJ ? a : 0]]] : 0x7fffffff;
+    for (int a = 1; a < nJ; ++a)
+        for (int b = a; b > 0 && cols[b - 1] > cols[b]; --b) {
+            const int tc = cols[b];
+            cols[b] = cols[b - 1];
+            cols[b - 1] = tc;
+            const T tv = p[b];
+            p[b] = p[b - 1];
+            p[b - 1] = tv;
+        }
+    const int64_t prow = (int64_t)i * c;
+    for (int a = 0; a < c; ++a) {
+        pcol[prow + a] = a < nJ ? cols[a] : -1;
+        pval[prow + a] = a < nJ ? p[a] : T(0);
+    }
+    pcnt[i] = nJ;
+}
+
+template <typename T>
+int interp_learned(int n, const int32_t* rp, const int32_t* ci, const T* bv, const uint8_t* cf, const int32_t* cidx,
+                   const T* X, int ncols, int ld, const double* d_w, int z, int mmax, int c, double ridge,
+                   const Model* model, bool refit, int32_t* pcol, T* pval, int32_t* pcnt, cudaStream_t s, int* d_err) {
+    BAMG_REQUIRE(model != nullptr, BAMG_EINVAL, "learned interpolation without a model");
+    BAMG_REQUIRE(mmax <= MLP_S, BAMG_EINVAL, "learned interpolation: mmax must be <= 16");
+    if (n == 0) return 0;
+    TmpBuf<float> feat((size_t)n * MLP_F, s), Y((size_t)n * MLP_S, s);
+    TmpBuf<int32_t> cand((size_t)n * MLP_S, s);
+    LsOut ex;
+    ex.feat = feat.get();
+    ex.cand = cand.get();
+    ex.greedy = false;
+    const int e = interp_ls<T>(n, rp, ci, bv, cf, cidx, X, ncols, ld, d_w, z, mmax, c, ridge, pcol, pval, pcnt, s,
+                               d_err, ex);
+    if (e) return e;
+    mlp_forward(model, n, feat.get(), Y.get(), s);
+    BAMG_LAUNCH(k_learned_select<T>, blocks_for(n, 128), 128, 0, s, n, cf, cidx, (const int32_t*)cand.get(),
+                (const float*)Y.get(), X, ncols, ld, d_w, c, refit ? 1 : 0, ridge, pcol, pval, pcnt);
+    return 0;
 }
 
 // ================================================================ restriction Q
@@ -756,9 +944,12 @@ void csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const T* v, doubl
 }
 
 #define INST(T)                                                                                                     \
-    template int interp_ls<T>(int, const int32_t*, const int32_t*, const uint8_t*, const int32_t*, const T*, int,   \
-                              int, const double*, int, int, int, double, int32_t*, T*, int32_t*, cudaStream_t,      \
-                              int*);                                                                                \
+    template int interp_ls<T>(int, const int32_t*, const int32_t*, const T*, const uint8_t*, const int32_t*,       \
+                              const T*, int, int, const double*, int, int, int, double, int32_t*, T*, int32_t*,     \
+                              cudaStream_t, int*, const LsOut&);                                                    \
+    template int interp_learned<T>(int, const int32_t*, const int32_t*, const T*, const uint8_t*, const int32_t*,  \
+                                   const T*, int, int, const double*, int, int, int, double, const Model*, bool,    \
+                                   int32_t*, T*, int32_t*, cudaStream_t, int*);                                     \
     template void build_restriction<T>(const EllView<T>&, int, DevBuf<int32_t>&, DevBuf<int32_t>&, DevBuf<T>&,      \
                                        cudaStream_t);                                                               \
     template void galerkin<T>(const MatView<T>&, const T*, const int32_t*, const int32_t*, const T*,                \

@@ -62,14 +62,46 @@ void launch_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col, cudaSt
 int build_system_matrix(int n, int nnzA, const int32_t* rpA, const int32_t* ciA, const double* vA,
                         DevBuf<int32_t>& rpB, DevBuf<int32_t>& ciB, DevBuf<double>& vB, cudaStream_t s);
 
+// ------------------------------------------------------------------ learned interpolation
+constexpr int MLP_S = 16;       // candidate slots (m_max)
+constexpr int MLP_NF_SLOT = 6;  // features per slot
+constexpr int MLP_F = 112;      // features per point: 16 x 6 + 2, zero-padded
+constexpr int MLP_H = 128;      // hidden width
+struct Model;                   // the MLP (k_mlp.cu)
+Model* mlp_create(uint64_t seed, cudaStream_t s);
+void mlp_destroy(Model* m);
+int64_t mlp_param_count();
+void mlp_set(Model* m, const float* h_params, cudaStream_t s);
+void mlp_get(const Model* m, float* h_params, cudaStream_t s);
+void mlp_forward(const Model* m, int64_t rows, const float* feat, float* Y, cudaStream_t s);
+double mlp_gradients(Model* m, int64_t rows, const float* feat, const float* target, float* h_grad, cudaStream_t s);
+void mlp_train(Model* m, int64_t rows, const float* feat, const float* target, int epochs, int batch, double lr,
+               double* h_loss, cudaStream_t s);
+// Optional outputs of the LS kernel: per point MLP_F features, the LS row on the MLP_S
+// slots, the candidate of each slot (-1 padded); greedy = false skips Algorithm 2.
+struct LsOut {
+    float* feat = nullptr;
+    float* target = nullptr;
+    int32_t* cand = nullptr;
+    bool greedy = true;
+};
+
 // ------------------------------------------------------------------ k_interp.cu
 void coarsen_grid(int nx, int ny, uint8_t* cf, int32_t* cidx, cudaStream_t s);
 void coarse_to_fine(int n, const uint8_t* cf, const int32_t* cidx, int32_t* c2f, cudaStream_t s);
 // Returns an error flag (BAMG_EOVERFLOW if a neighbourhood search overflowed).
 template <typename T>
-int interp_ls(int n, const int32_t* rp, const int32_t* ci, const uint8_t* cf, const int32_t* cidx, const T* X, int ncols,
-              int ld, const double* d_w, int z, int mmax, int c, double ridge, int32_t* pcol, T* pval, int32_t* pcnt,
-              cudaStream_t s, int* d_err = nullptr);
+int interp_ls(int n, const int32_t* rp, const int32_t* ci, const T* bv, const uint8_t* cf, const int32_t* cidx,
+              const T* X, int ncols, int ld, const double* d_w, int z, int mmax, int c, double ridge, int32_t* pcol,
+              T* pval, int32_t* pcnt, cudaStream_t s, int* d_err = nullptr, const LsOut& ex = LsOut());
+// Learned interpolation of one level: candidates and features (the LS kernel's search),
+// the MLP, then per fine point the c slots of largest |y| with weights y or, with refit,
+// the Eq. (3.6) minimiser over them.  Coarse rows are unit rows.
+template <typename T>
+int interp_learned(int n, const int32_t* rp, const int32_t* ci, const T* bv, const uint8_t* cf, const int32_t* cidx,
+                   const T* X, int ncols, int ld, const double* d_w, int z, int mmax, int c, double ridge,
+                   const Model* model, bool refit, int32_t* pcol, T* pval, int32_t* pcnt, cudaStream_t s,
+                   int* d_err = nullptr);
 // Q rows (CSR by coarse rows, sorted by fine index) from the ELL interpolation.
 template <typename T>
 void build_restriction(const EllView<T>& P, int nc, DevBuf<int32_t>& qrp, DevBuf<int32_t>& qci, DevBuf<T>& qv,
@@ -147,3 +179,8 @@ void gmres_arnoldi_step(double* d_state, int j, int m, cudaStream_t s);
 void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s);
 
 }  // namespace bamg
+
+// The opaque model handle of the C ABI.
+struct bamg_model {
+    bamg::Model* impl = nullptr;
+};

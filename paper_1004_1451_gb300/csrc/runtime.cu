@@ -34,13 +34,36 @@ cudaStream_t& alloc_stream() {
     return st;
 }
 // Sets the allocation stream for the lifetime of the object.
-struct AllocStream {
-    cudaStream_t prev;
-    explicit AllocStream(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
-    ~AllocStream() { alloc_stream() = prev; }
-};
-
 static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// V-cycle factor helpers: x0 = 1 + u (SplitMix64 seed 7, stream 0), sums of r and r^2,
+// r <- (r - mean) * scale, r <- r - t.
+__global__ void k_vf_start(int n, double* __restrict__ x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 1.0 + counter_uniform(7, 0, (uint64_t)i);
+}
+__global__ void k_vf_moments(int n, const double* __restrict__ r, double* __restrict__ mom) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double a = 0.0, b = 0.0;
+    if (i < n) {
+        a = r[i];
+        b = a * a;
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(mom, a);
+        atomicAdd(mom + 1, b);
+    }
+}
+__global__ void k_vf_affine(int n, double* __restrict__ r, double mean, double scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = (r[i] - mean) * scale;
+}
+__global__ void k_vf_axpy(int n, double* __restrict__ r, const double* __restrict__ t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] -= t[i];
+}
 
 // active[k] = 1 for the random vectors, sel[q] for eigenvector column ldU + q, else 0.
 __global__ void k_active_mask(int r, int ldU, int nvec, int ld, const uint8_t* __restrict__ sel,
@@ -94,7 +117,15 @@ struct SolverBase {
     virtual void vcycle_apply(const double* v, double* z) = 0;
     virtual void smooth_apply(int level, int sweeps, const void* b, void* x, void* work) = 0;
     virtual int precision() const = 0;
+    virtual double vcycle_factor(int iters) = 0;
     virtual void export_obj(int level, int what, void* h_dst, int64_t cap, int64_t* bytes) = 0;
+    // training-data recording (bamg_interp_dataset): features and LS rows of every fit
+    bool record = false;
+    float* rec_feat = nullptr;
+    float* rec_target = nullptr;
+    int64_t rec_cap = 0, rec_rows = 0;
+    int interp_used = BAMG_INTERP_LS;
+    double rho_measured = 0.0;
     virtual void layout(int level, int* ld, int* r, int* v0, int* nvec) const = 0;
 };
 
@@ -188,8 +219,23 @@ struct Solver : SolverBase {
         c.pcol.alloc((size_t)c.n * o.caliber);
         c.pval.alloc((size_t)c.n * o.caliber);
         c.pcnt.alloc(c.n);
-        interp_ls<T>(c.n, c.rp.get(), c.ci.get(), c.cf.get(), c.cidx.get(), c.X.get(), ld, ld, c.w.get(), o.z, o.mmax,
-                     o.caliber, ridge(), c.pcol.get(), c.pval.get(), c.pcnt.get(), s, ls_err.get());
+        if (o.interp == BAMG_INTERP_LEARNED) {
+            interp_learned<T>(c.n, c.rp.get(), c.ci.get(), c.bv.get(), c.cf.get(), c.cidx.get(), c.X.get(), ld, ld,
+                              c.w.get(), o.z, o.mmax, o.caliber, ridge(), o.model->impl, o.learned_refit != 0,
+                              c.pcol.get(), c.pval.get(), c.pcnt.get(), s, ls_err.get());
+        } else {
+            LsOut ex;
+            if (record) {
+                if (rec_feat && rec_target && rec_rows + c.n <= rec_cap) {
+                    ex.feat = rec_feat + rec_rows * MLP_F;
+                    ex.target = rec_target + rec_rows * MLP_S;
+                }
+                rec_rows += c.n;
+            }
+            interp_ls<T>(c.n, c.rp.get(), c.ci.get(), c.bv.get(), c.cf.get(), c.cidx.get(), c.X.get(), ld, ld,
+                         c.w.get(), o.z, o.mmax, o.caliber, ridge(), c.pcol.get(), c.pval.get(), c.pcnt.get(), s,
+                         ls_err.get(), ex);
+        }
         build_restriction<T>(c.P(o.caliber), c.nc, c.qrp, c.qci, c.qv, s);
         GalerkinOut<T> go;
         galerkin<T>(c.B(), c.tv.get(), c.qrp.get(), c.qci.get(), c.qv.get(), c.P(o.caliber), c.nc, go, s);
@@ -445,6 +491,42 @@ struct Solver : SolverBase {
         v.B = lv[level]->B();
         v.dinv = lv[level]->dinv.get();
         smooth_sweeps<T>(v, (const T*)b, (T*)x, (T*)work, o.omega, sweeps, s);
+    }
+
+    // power iteration on the residual propagator I - B C (see bamg_vcycle_factor)
+    double vcycle_factor(int iters) override {
+        AllocStream as_(s);
+        const int n = lv[0]->n;
+        const MatView<double> B = B64();
+        TmpBuf<double> x(n, s), r(n, s), z(n, s), t(n, s), mom(2, s);
+        if (!h_pin) BAMG_CK(cudaMallocHost(&h_pin, 16 * sizeof(double)));
+        BAMG_LAUNCH(k_vf_start, blocks_for(n, 256), 256, 0, s, n, x.get());
+        spmv_f64(B, x.get(), r.get(), 1.0, s);
+        auto normalise = [&]() {  // r <- (r - mean) / ||r - mean||; returns the norm
+            BAMG_CK(cudaMemsetAsync(mom.get(), 0, 2 * sizeof(double), s));
+            BAMG_LAUNCH(k_vf_moments, blocks_for(n, 256), 256, 0, s, n, (const double*)r.get(), mom.get());
+            BAMG_CK(cudaMemcpyAsync(h_pin, mom.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            BAMG_CK(cudaStreamSynchronize(s));
+            const double mean = h_pin[0] / n;
+            const double nrm = std::sqrt(std::max(h_pin[1] - n * mean * mean, 0.0));
+            BAMG_LAUNCH(k_vf_affine, blocks_for(n, 256), 256, 0, s, n, r.get(), mean, nrm > 0.0 ? 1.0 / nrm : 0.0);
+            return nrm;
+        };
+        normalise();
+        std::vector<double> logs;
+        for (int k = 0; k < iters; ++k) {
+            vcycle_apply(r.get(), z.get());
+            spmv_f64(B, z.get(), t.get(), 1.0, s);
+            BAMG_LAUNCH(k_vf_axpy, blocks_for(n, 256), 256, 0, s, n, r.get(), (const double*)t.get());
+            const double nr = normalise();
+            if (!(nr > 0.0)) break;
+            logs.push_back(std::log(nr));
+        }
+        if (logs.empty()) return 0.0;
+        double acc = 0.0;
+        const size_t h = logs.size() / 2;
+        for (size_t k = h; k < logs.size(); ++k) acc += logs[k];
+        return std::exp(acc / (double)(logs.size() - h));
     }
 
     void vcycle_apply(const double* v, double* z) override {
@@ -734,6 +816,10 @@ int bamg_default_opts(bamg_opts* o) {
     o->cr_max_rounds = 20;
     o->cr_omega = 0.7;
     o->stream = nullptr;
+    o->interp = BAMG_INTERP_LS;
+    o->learned_refit = 1;
+    o->model = nullptr;
+    o->learned_rho_max = 0.0;
     return BAMG_OK;
 }
 
@@ -749,6 +835,57 @@ static void check_opts(const bamg_opts& o) {
     BAMG_REQUIRE(o.precision == BAMG_PREC_FP64 || o.precision == BAMG_PREC_MIXED, BAMG_EINVAL, "bad precision");
     BAMG_REQUIRE(o.coarsen == BAMG_COARSEN_GRID || o.coarsen == BAMG_COARSEN_CR, BAMG_EINVAL, "bad coarsening");
     BAMG_REQUIRE(o.omega > 0.0 && o.omega < 2.0, BAMG_EINVAL, "omega must be in (0, 2)");
+    BAMG_REQUIRE(o.interp == BAMG_INTERP_LS || o.interp == BAMG_INTERP_LEARNED, BAMG_EINVAL, "bad interp");
+    BAMG_REQUIRE(o.interp == BAMG_INTERP_LS || (o.model && o.model->impl), BAMG_EINVAL,
+                 "BAMG_INTERP_LEARNED needs a model");
+}
+
+static void check_setup_args(const bamg_csr* A, int r, int levels, const bamg_opts& o) {
+    check_opts(o);
+    BAMG_REQUIRE(A->n >= 2 && A->nnz >= 1, BAMG_EINVAL, "A must have n >= 2 and nnz >= 1");
+    BAMG_REQUIRE(A->row_ptr && A->col && A->val, BAMG_EINVAL, "null CSR array");
+    BAMG_REQUIRE(r >= 1 && r <= 24, BAMG_EINVAL, "r must be 1..24");
+    BAMG_REQUIRE(levels >= 0 && levels <= 30, BAMG_EINVAL, "levels must be 0..30");
+    if (o.coarsen == BAMG_COARSEN_GRID)
+        BAMG_REQUIRE(o.grid_nx >= 1 && o.grid_ny >= 1 && (int64_t)o.grid_nx * o.grid_ny == A->n, BAMG_EINVAL,
+                     "full coarsening needs grid_nx * grid_ny == n");
+}
+
+// Builds the hierarchy; with the learned interpolation and learned_rho_max > 0, measures
+// the V-cycle factor and falls back to least squares when it exceeds the limit.
+static std::unique_ptr<SolverBase> make_solver(const bamg_csr* A, int r, int levels, const bamg_opts& o,
+                                               bool record = false, float* rec_feat = nullptr,
+                                               float* rec_target = nullptr, int64_t rec_cap = 0) {
+    std::unique_ptr<SolverBase> sv;
+    if (o.precision == BAMG_PREC_FP64) {
+        auto p = std::make_unique<Solver<double>>();
+        p->o = o;
+        p->s = (cudaStream_t)o.stream;
+        p->record = record, p->rec_feat = rec_feat, p->rec_target = rec_target, p->rec_cap = rec_cap;
+        p->setup(A, r, levels);
+        sv = std::move(p);
+    } else {
+        auto p = std::make_unique<Solver<float>>();
+        p->o = o;
+        p->s = (cudaStream_t)o.stream;
+        p->record = record, p->rec_feat = rec_feat, p->rec_target = rec_target, p->rec_cap = rec_cap;
+        p->setup(A, r, levels);
+        sv = std::move(p);
+    }
+    sv->interp_used = o.interp;
+    if (o.interp == BAMG_INTERP_LEARNED && o.learned_rho_max > 0.0) {
+        const double rho = sv->vcycle_factor(20);
+        if (!(rho <= o.learned_rho_max)) {
+            bamg_opts ls = o;
+            ls.interp = BAMG_INTERP_LS;
+            const double ms = sv->setup_ms;
+            sv.reset();
+            sv = make_solver(A, r, levels, ls);
+            sv->setup_ms += ms;
+        }
+        sv->rho_measured = rho;
+    }
+    return sv;
 }
 
 int bamg_setup(const bamg_csr* A, int r, int levels, const bamg_opts* opts, bamg_handle** h) {
@@ -758,28 +895,9 @@ int bamg_setup(const bamg_csr* A, int r, int levels, const bamg_opts* opts, bamg
         bamg_opts o;
         if (opts) o = *opts;
         else bamg_default_opts(&o);
-        check_opts(o);
-        BAMG_REQUIRE(A->n >= 2 && A->nnz >= 1, BAMG_EINVAL, "A must have n >= 2 and nnz >= 1");
-        BAMG_REQUIRE(A->row_ptr && A->col && A->val, BAMG_EINVAL, "null CSR array");
-        BAMG_REQUIRE(r >= 1 && r <= 24, BAMG_EINVAL, "r must be 1..24");
-        BAMG_REQUIRE(levels >= 0 && levels <= 30, BAMG_EINVAL, "levels must be 0..30");
-        if (o.coarsen == BAMG_COARSEN_GRID)
-            BAMG_REQUIRE(o.grid_nx >= 1 && o.grid_ny >= 1 && (int64_t)o.grid_nx * o.grid_ny == A->n, BAMG_EINVAL,
-                         "full coarsening needs grid_nx * grid_ny == n");
+        check_setup_args(A, r, levels, o);
         auto hh = std::make_unique<bamg_handle>();
-        if (o.precision == BAMG_PREC_FP64) {
-            auto sv = std::make_unique<Solver<double>>();
-            sv->o = o;
-            sv->s = (cudaStream_t)o.stream;
-            sv->setup(A, r, levels);
-            hh->impl = std::move(sv);
-        } else {
-            auto sv = std::make_unique<Solver<float>>();
-            sv->o = o;
-            sv->s = (cudaStream_t)o.stream;
-            sv->setup(A, r, levels);
-            hh->impl = std::move(sv);
-        }
+        hh->impl = make_solver(A, r, levels, o);
         *h = hh.release();
     });
 }
@@ -931,6 +1049,37 @@ int bamg_smooth_apply(bamg_handle* h, int level, int sweeps, const void* b, void
 }
 
 int bamg_hierarchy_precision(const bamg_handle* h) { return h && h->impl ? h->impl->precision() : BAMG_EINVAL; }
+
+int bamg_vcycle_factor(bamg_handle* h, int iters, double* rho) {
+    return guarded([&] {
+        BAMG_REQUIRE(h && h->impl && rho && iters >= 2, BAMG_EINVAL, "bad vcycle_factor arguments");
+        *rho = h->impl->vcycle_factor(iters);
+        BAMG_CK(cudaStreamSynchronize(h->impl->s));
+    });
+}
+
+int bamg_hierarchy_interp(const bamg_handle* h, double* h_rho) {
+    if (!h || !h->impl) return BAMG_EINVAL;
+    if (h_rho) *h_rho = h->impl->rho_measured;
+    return h->impl->interp_used;
+}
+
+int bamg_interp_dataset(const bamg_csr* A, int r, int levels, const bamg_opts* opts, float* d_feat, float* d_target,
+                        int64_t cap_rows, int64_t* h_rows) {
+    return guarded([&] {
+        BAMG_REQUIRE(A && h_rows && cap_rows >= 0 && (cap_rows == 0 || (d_feat && d_target)), BAMG_EINVAL,
+                     "bad interp_dataset arguments");
+        bamg_opts o;
+        if (opts) o = *opts;
+        else bamg_default_opts(&o);
+        o.interp = BAMG_INTERP_LS;
+        check_setup_args(A, r, levels, o);
+        auto sv = make_solver(A, r, levels, o, true, d_feat, d_target, cap_rows);
+        *h_rows = sv->rec_rows;
+        BAMG_CK(cudaStreamSynchronize((cudaStream_t)o.stream));
+        BAMG_REQUIRE(*h_rows <= cap_rows, BAMG_ESIZE, "interp_dataset: cap_rows too small");
+    });
+}
 
 int bamg_vcycle_apply(bamg_handle* h, const double* v, double* z) {
     return guarded([&] {
