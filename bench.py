@@ -6,8 +6,9 @@ service 10/31 and 10/31, r = 10 test vectors, FP32 setup and V-cycle inside FP64
 flexible GMRES.  Inputs are resident in HBM when a step's timing starts; L2 is
 flushed between steps.  Also reported: the same metric end to end from host buffers,
 the plain FP64 method on the same chain, the roofline of the dominant kernel (the V-cycle
-smoother on the finest level), an SpMM HBM probe, the batched form on 512 chains, and
-the CPU oracle on the host cores.
+smoother on the finest level), an SpMM HBM probe, the batched form on 512 chains, LS vs
+learned interpolation on a held-out tandem queue of 262,144 states, and the CPU oracle on
+the host cores.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -204,6 +205,7 @@ def run_ours(args):
     s_dom.close()
     probe = spmm_probe(peaks) if not args.no_probe else None
     batch = batch_line(args) if not args.no_batch else None
+    learned = learned_line(args) if not args.no_learned else None
     cpu = cpu_baseline() if not args.no_cpu else None
     nnz_a = int(ch.nnz)
     out = {
@@ -220,7 +222,7 @@ def run_ours(args):
         "fp64_ms": round(float(np.median(fp64)), 4), "fp64_iterations": st64["iterations"],
         "speedup_mixed_vs_fp64": round(float(np.median(fp64)) / ms, 3),
         "gpu_launches": int(round(launches)),
-        "roofline": roof, "spmm_hbm": probe, "batch": batch, "cpu_baseline": cpu, "clocks": ck,
+        "roofline": roof, "spmm_hbm": probe, "batch": batch, "learned": learned, "cpu_baseline": cpu, "clocks": ck,
     }
     _line(out)
 
@@ -388,6 +390,78 @@ def batch_line(args, workers=8):
             "note": "birth-death chains that stop at max_it count in the time; host-timed (threads and streams)"}
 
 
+LEARNED_WORKLOAD = ("learned P: MLP trained on the LS rows of 16 tandem queues (capacities uniform in [63, 255], "
+                    "rates U(0.2, 0.45) normalised, seed 1; rows with an LS weight above 4 left out); tested on a "
+                    "held-out tandem queue of capacity 511 (262,144 states, seed 99); r=10; mixed")
+
+
+def _timed(fn, reps):
+    import torch
+
+    out, ts = None, []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return out, float(np.median(ts))
+
+
+def learned_line(args, train_rows=1 << 20, epochs=10, batch=4096):
+    """LS vs learned interpolation on the held-out tandem queue: V-cycle factor, setup and
+    solve times (CUDA events on the current stream), iterations, accuracy."""
+    import torch
+
+    import paper_1004_1451_gb300 as bamg
+    from workloads import tandem_training_set
+
+    def dev(ch):
+        return (torch.tensor(ch.row_ptr, device="cuda"), torch.tensor(ch.col, device="cuda"),
+                torch.tensor(ch.val, device="cuda"))
+
+    t0 = time.perf_counter()
+    Fs, Ts = [], []
+    for ch in tandem_training_set(1, 16, n_lo=63, n_hi=255):
+        f, t = bamg.interp_dataset(*dev(ch), R, 20, grid=ch.grid, precision="mixed")
+        # fine points with candidates; rows whose LS weights exceed 4 in magnitude (a few
+        # in 10^4, from nearly collinear candidates) are left out of the MSE training set
+        keep = (f[:, 0:96:6].sum(dim=1) > 0) & (t.abs().amax(dim=1) <= 4.0)
+        Fs.append(f[keep])
+        Ts.append(t[keep])
+    F, T = torch.cat(Fs), torch.cat(Ts)
+    del Fs, Ts
+    perm = torch.randperm(F.shape[0], generator=torch.Generator().manual_seed(0))[:train_rows].to(F.device)
+    F, T = F[perm].contiguous(), T[perm].contiguous()
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    model = bamg.Model(0)
+    t0 = time.perf_counter()
+    hist = model.train(F, T, epochs=epochs, batch=batch, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    rows = int(F.shape[0])
+    del F, T
+    test = tandem_training_set(99, 1, n_lo=511, n_hi=511)[0]
+    A = dev(test)
+    xe = _direct_stationary(test)
+    out = {"workload": LEARNED_WORKLOAD, "n": test.n, "train_rows": rows, "epochs": epochs, "batch": batch,
+           "data_s": round(data_s, 2), "train_s": round(train_s, 2), "train_loss_first_last": [round(hist[0], 5),
+                                                                                               round(hist[-1], 5)]}
+    for name, kw in (("ls", {}), ("learned", {"interp": "learned", "model": model})):
+        s, setup_ms = _timed(lambda: bamg.Solver(*A, r=R, levels=20, grid=test.grid, precision="mixed", **kw), 5)
+        rho = s.vcycle_factor(20)
+        (x, st), solve_ms = _timed(lambda: s.solve(TOL), 3)
+        err = float(np.abs(x.cpu().numpy() - xe).sum() / np.abs(xe).sum())
+        out[name] = {"setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3), "gmres_iterations": st["iterations"],
+                     "vcycle_factor": round(rho, 4), "rel_l1_vs_exact": err, "levels": s.info()["n"]}
+        s.close()
+    model.close()
+    return out
+
+
 def kernel_probe():
     """Only the dominant-kernel timing (for an ncu capture of k_smooth on the finest level)."""
     import torch
@@ -451,6 +525,7 @@ def main():
     ap.add_argument("--only-step", action="store_true", help="time the workload steps only (for profiler launch lists)")
     ap.add_argument("--probe-only", type=int, default=0, help="run only the SpMM probe on an N x N grid walk")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-chain batched line")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-interpolation line")
     ap.add_argument("--kernel-probe", action="store_true", help="run only the dominant-kernel timing")
     args = ap.parse_args()
     if args.impl == "reference":
