@@ -536,6 +536,27 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
         Ar[r * LDP + c] = b - sr * t;
         Ai[r * LDP + c] = -si * t;
     }
+    // pivot floor relative to the pencil's largest entry: near an eigenvalue the LU is
+    // (nearly) singular by design, and an absolute floor would let the inverse iteration
+    // overflow in FP32
+    {
+        F m = F(0);
+        for (int idx = tid; idx < n * n; idx += CT) {
+            const int r = idx / n, c = idx - r * n;
+            const F a = absv(Ar[r * LDP + c]) + absv(Ai[r * LDP + c]);
+            m = m > a ? m : a;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const F q = __shfl_xor_sync(0xffffffffu, m, o);
+            m = m > q ? m : q;
+        }
+        if (lane == 0) pre[wid] = m;
+    }
+    __syncthreads();
+    F amax = F(0);
+    for (int q = 0; q < CT / 32; ++q) amax = amax > pre[q] ? amax : pre[q];
+    const F pfloor = (sizeof(F) == 8 ? F(1e-15) : F(1e-7)) * (amax > F(0) ? amax : F(1));
     __syncthreads();
     // complex LU with partial pivoting on |Re| + |Im|; dr + i di = 1 / u_kk
     for (int k = 0; k < n; ++k) {
@@ -561,9 +582,8 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
             if (tid == 0) {  // the pivot's reciprocal, formed once
                 perm[k] = br;
                 F pr = Ar[br * LDP + k], pi = Ai[br * LDP + k];
-                const F tiny = pivot_tiny<F>();
-                if (absv(pr) + absv(pi) < tiny) {
-                    pr = tiny;
+                if (absv(pr) + absv(pi) < pfloor) {
+                    pr = pfloor;
                     pi = F(0);
                     Ar[br * LDP + k] = pr;
                     Ai[br * LDP + k] = pi;

@@ -4,6 +4,8 @@
 // vector blocks, and the construction of B = I - A.
 #include <cfloat>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace bamg {
@@ -72,75 +74,156 @@ void launch_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* 
 }
 
 // ---------------------------------------------------------------- omega-Jacobi SpMM
-// One thread owns one 16-byte chunk (W columns) of one row: it walks the row of B once,
+// One thread owns one 16-byte chunk (W columns) of a row: it walks the row of B once,
 // gathering the matching chunk of each neighbour's test-vector row (contiguous in the
-// row-interleaved layout), so the W columns share every matrix load.
+// row-interleaved layout), so the W columns share every matrix load.  The grid is a
+// fixed number of blocks per SM that strides over the rows; while a row's gathers are in
+// flight the thread loads the next row's first JB column indices and values and the row
+// pointers of the row after it, so the three dependent loads of a row (row pointers,
+// entries, gathers) overlap with earlier rows' work.  Entries beyond the first JB of a
+// row are read in predicated batches of JB.
+constexpr int JAC_BLOCKS_PER_SM = 2;
+constexpr int JB = 6;
+
 template <typename T, bool SHIFT>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, JAC_BLOCKS_PER_SM)
     k_jacobi(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
              const T* __restrict__ tv, const T* __restrict__ dB, const T* __restrict__ dinvB, const T* __restrict__ dT,
              const double* __restrict__ lam, int ncols, const T* __restrict__ X, T* __restrict__ Y, int ld, int col0,
              int nvec, T omega) {
     constexpr int W = V16<T>::W;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int row = (int)(t / nvec);
+    constexpr int NT = SHIFT ? JB : 1;  // T values are carried only by the shifted sweep
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x / nvec;  // rows per pass of the grid
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= stride * nvec) return;
+    int64_t row = t / nvec;
     if (row >= n) return;
-    int ch = (int)(t - (int64_t)row * nvec);
-    int off = col0 + ch * W;
-    T acc[W], accT[W];
+    const int ch = (int)(t - row * nvec);
+    const int off = col0 + ch * W;
+    const bool has_t = SHIFT && tv != nullptr;
+    int p0 = __ldg(rp + row), p1 = __ldg(rp + row + 1);
+    int cnt = min(JB, p1 - p0);
+    int jj[JB];
+    T bb[JB], tt[NT];
 #pragma unroll
-    for (int e = 0; e < W; ++e) acc[e] = accT[e] = T(0);
-    const int p0 = rp[row], p1 = rp[row + 1];
-    // batches of up to JB entries: indices and values first, then the predicated
-    // gathers, so each thread has up to JB independent loads in flight
-    constexpr int JB = 6;
-    for (int base = p0; base < p1; base += JB) {
-        const int cnt = min(JB, p1 - base);
-        int jj[JB];
-        T bb[JB], tt[JB], xv[JB][W];
-#pragma unroll
-        for (int u = 0; u < JB; ++u) {
-            if (u < cnt) {
-                jj[u] = __ldg(ci + base + u);
-                bb[u] = __ldg(bv + base + u);
-                tt[u] = (SHIFT && tv != nullptr) ? __ldg(tv + base + u) : T(0);
-            }
+    for (int u = 0; u < JB; ++u)
+        if (u < cnt) {
+            jj[u] = __ldg(ci + p0 + u);
+            bb[u] = __ldg(bv + p0 + u);
+            if (has_t) tt[u < NT ? u : 0] = __ldg(tv + p0 + u);
         }
+    int64_t nrow = row + stride;
+    int np0 = 0, np1 = 0;
+    if (nrow < n) {
+        np0 = __ldg(rp + nrow);
+        np1 = __ldg(rp + nrow + 1);
+    }
+    for (;;) {
+        // this row's gathers, its own values and diagonal terms ...
+        T xv[JB][W];
 #pragma unroll
         for (int u = 0; u < JB; ++u)
             if (u < cnt) V16<T>::load(X + (int64_t)jj[u] * ld + off, xv[u]);
+        T xs[W];
+        V16<T>::load(X + row * ld + off, xs);
+        const T d0 = SHIFT ? __ldg(dB + row) : __ldg(dinvB + row);
+        const T d1 = has_t ? __ldg(dT + row) : T(1);
+        // ... while the next row's first entries and the row pointers after it arrive
+        const int ncnt = nrow < n ? min(JB, np1 - np0) : 0;
+        int njj[JB];
+        T nbb[JB], ntt[NT];
 #pragma unroll
-        for (int u = 0; u < JB; ++u) {
+        for (int u = 0; u < JB; ++u)
+            if (u < ncnt) {
+                njj[u] = __ldg(ci + np0 + u);
+                nbb[u] = __ldg(bv + np0 + u);
+                if (has_t) ntt[u < NT ? u : 0] = __ldg(tv + np0 + u);
+            }
+        const int64_t nnrow = nrow + stride;
+        int nnp0 = 0, nnp1 = 0;
+        if (nnrow < n) {
+            nnp0 = __ldg(rp + nnrow);
+            nnp1 = __ldg(rp + nnrow + 1);
+        }
+        T acc[W], accT[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) acc[e] = accT[e] = T(0);
+        for (int base = p0 + JB; base < p1; base += JB) {  // the rest of a long row, JB at a time
+            const int c2 = min(JB, p1 - base);
+            int kj[JB];
+            T kb[JB], kt[NT], kx[JB][W];
+#pragma unroll
+            for (int u = 0; u < JB; ++u)
+                if (u < c2) {
+                    kj[u] = __ldg(ci + base + u);
+                    kb[u] = __ldg(bv + base + u);
+                    if (has_t) kt[u < NT ? u : 0] = __ldg(tv + base + u);
+                }
+#pragma unroll
+            for (int u = 0; u < JB; ++u)
+                if (u < c2) V16<T>::load(X + (int64_t)kj[u] * ld + off, kx[u]);
+#pragma unroll
+            for (int u = 0; u < JB; ++u)
+                if (u < c2) {
+#pragma unroll
+                    for (int e = 0; e < W; ++e) acc[e] += kb[u] * kx[u][e];
+                    if (has_t)
+#pragma unroll
+                        for (int e = 0; e < W; ++e) accT[e] += kt[u < NT ? u : 0] * kx[u][e];
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < JB; ++u)
             if (u < cnt) {
 #pragma unroll
                 for (int e = 0; e < W; ++e) acc[e] += bb[u] * xv[u][e];
-                if (SHIFT && tv != nullptr) {
+                if (has_t)
 #pragma unroll
-                    for (int e = 0; e < W; ++e) accT[e] += tt[u] * xv[u][e];
-                }
+                    for (int e = 0; e < W; ++e) accT[e] += tt[u < NT ? u : 0] * xv[u][e];
             }
-        }
-    }
-    T xs[W], y[W];
-    V16<T>::load(X + (int64_t)row * ld + off, xs);
-    if (SHIFT) {
-        const T db = dB[row];
-        const T dt = tv ? dT[row] : T(1);
+        T y[W];
+        if (SHIFT) {
 #pragma unroll
-        for (int e = 0; e < W; ++e) {
-            const int c = ch * W + e;
-            const T l = c < ncols ? (T)lam[c] : T(0);
-            const T tx = tv ? accT[e] : xs[e];
-            const T r = acc[e] - l * tx;
-            const T d = db - l * dt;
-            y[e] = xs[e] - omega * r / d;
-        }
-    } else {
-        const T di = dinvB[row];
+            for (int e = 0; e < W; ++e) {
+                const int c = ch * W + e;
+                const T l = c < ncols ? (T)lam[c] : T(0);
+                const T tx = has_t ? accT[e] : xs[e];
+                const T r = acc[e] - l * tx;
+                const T d = d0 - l * d1;
+                y[e] = xs[e] - omega * r / d;
+            }
+        } else {
 #pragma unroll
-        for (int e = 0; e < W; ++e) y[e] = xs[e] - omega * (di * acc[e]);
+            for (int e = 0; e < W; ++e) y[e] = xs[e] - omega * (d0 * acc[e]);
+        }
+        V16<T>::store(Y + row * ld + off, y);
+        if (nrow >= n) break;
+        row = nrow;
+        p0 = np0;
+        p1 = np1;
+        cnt = ncnt;
+#pragma unroll
+        for (int u = 0; u < JB; ++u) {
+            jj[u] = njj[u];
+            bb[u] = nbb[u];
+        }
+#pragma unroll
+        for (int u = 0; u < NT; ++u) tt[u] = ntt[u];
+        nrow = nnrow;
+        np0 = nnp0;
+        np1 = nnp1;
     }
-    V16<T>::store(Y + (int64_t)row * ld + off, y);
+}
+
+static int sm_count() {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0, v = 0;
+        BAMG_CK(cudaGetDevice(&dev));
+        BAMG_CK(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        nsm = v > 0 ? v : 1;
+    }
+    return nsm;
 }
 
 template <typename T>
@@ -162,7 +245,8 @@ void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, con
     const int nvec = (ncols + W - 1) / W;
     if (B.n == 0 || nvec == 0 || nu <= 0) return;
     const int64_t work_items = (int64_t)B.n * nvec;
-    const unsigned grid = blocks_for(work_items, 256);
+    const unsigned grid = (unsigned)std::min<int64_t>(blocks_for(work_items, 256),
+                                                      (int64_t)sm_count() * JAC_BLOCKS_PER_SM);
     T* src = X;
     T* dst = work;
     for (int k = 0; k < nu; ++k) {

@@ -92,6 +92,38 @@ def test_shifted_relax_matches_oracle(with_T):
     assert rel(X.cpu().numpy()[:, 2:2 + K], want) < 1e-13
 
 
+@pytest.mark.parametrize("dtype_name,shift", [("float32", False), ("float32", True), ("float64", False),
+                                               ("float64", True)])
+def test_relax_long_rows_match_oracle(dtype_name, shift):
+    # a coarse-level operator (rows of 20-40 entries) exercises the batches beyond the
+    # first entries of a row; with shifts and a non-identity T as in the upward pass
+    torch = _torch()
+    dt = getattr(torch, dtype_name)
+    ch = tandem_queue(31)
+    H = ob.setup(ch.to_scipy(), 8, 3, ob.Opts(), grid=ch.grid)
+    lv = H.levels[2]
+    B, Tm = sp.csr_matrix(lv.B), sp.csr_matrix(lv.T)
+    B.sort_indices()
+    assert np.diff(B.indptr).max() > 6  # rows longer than the first batch of entries
+    n = B.shape[0]
+    rng = np.random.default_rng(5)
+    K, ld = 6, 8
+    V0 = rng.uniform(-1, 1, (n, K))
+    X = torch.zeros(n, ld, dtype=dt, device="cuda")
+    X[:, :K] = torch.tensor(V0, dtype=dt)
+    if shift:
+        lam = np.array([0.0, 0.01, 0.02, -0.03, 0.05, 0.1])
+        want = ob.jacobi_shifted(B, Tm, V0, lam, 0.7, 2)
+        _bamg().relax(dev_csr(B, dt), X, K, 0, 0.7, 2, T_val=torch.tensor(on_pattern(B, Tm), dtype=dt, device="cuda"),
+                      lam=torch.tensor(lam, device="cuda"))
+    else:
+        want = ob.jacobi(B, V0, 0.7, 2)
+        _bamg().relax(dev_csr(B, dt), X, K, 0, 0.7, 2)
+    got = X.cpu().numpy().astype(np.float64)
+    assert np.isfinite(got).all()
+    assert rel(got[:, :K], want) < (1e-12 if dt == torch.float64 else 1e-4)
+
+
 def test_weights_match_oracle():
     torch = _torch()
     ch, B = _tandem_B(40)
