@@ -527,9 +527,18 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-chain batched line")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-interpolation line")
     ap.add_argument("--kernel-probe", action="store_true", help="run only the dominant-kernel timing")
+    ap.add_argument("--learned-only", action="store_true", help="run only the learned-interpolation line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.learned_only:
+        import torch
+
+        import paper_1004_1451_gb300.build as pb
+
+        pb.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        _line(learned_line(args))
     elif args.kernel_probe:
         import torch
 

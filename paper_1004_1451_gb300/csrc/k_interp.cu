@@ -262,7 +262,7 @@ __device__ void learned_features(int i, int lane, int node, int ncand, int depth
 // normal equations (plus the Tikhonov term), solves them by Cholesky and evaluates the
 // functional of Eq. (3.6) directly; the lane with the smallest value (lowest slot on
 // ties) joins J.
-template <typename T, int CAP>
+template <typename T, int CAP, bool EXTRA>
 __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const T* __restrict__ bv, const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx, const T* __restrict__ X,
                          int ncols, int ld, const T* s_w, int z, int mmax, int c, double ridge,
@@ -277,10 +277,12 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
             pval[prow + lane] = lane == 0 ? T(1) : T(0);
         }
         if (lane == 0) pcnt[i] = 1;
-        if (ex.feat)
-            for (int k = lane; k < MLP_F; k += 32) ex.feat[(int64_t)i * MLP_F + k] = 0.f;
-        if (ex.target && lane < MLP_S) ex.target[(int64_t)i * MLP_S + lane] = 0.f;
-        if (ex.cand && lane < MLP_S) ex.cand[(int64_t)i * MLP_S + lane] = -1;
+        if (EXTRA) {
+            if (ex.feat)
+                for (int k = lane; k < MLP_F; k += 32) ex.feat[(int64_t)i * MLP_F + k] = 0.f;
+            if (ex.target && lane < MLP_S) ex.target[(int64_t)i * MLP_S + lane] = 0.f;
+            if (ex.cand && lane < MLP_S) ex.cand[(int64_t)i * MLP_S + lane] = -1;
+        }
         return false;
     }
     // ---- neighbourhood search (Eq. (3.5))
@@ -383,10 +385,10 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
             gss += wk * v * v;
             bs += wk * v * xi[k];
         }
-    if (ex.cand && lane < MLP_S) ex.cand[(int64_t)i * MLP_S + lane] = node;
-    if (ex.feat) learned_features<T>(i, lane, node, ncand, lane < ncand ? cdep[lane] : 0, gss, bs, xi, s_w, ncols, rp,
+    if (EXTRA && ex.cand && lane < MLP_S) ex.cand[(int64_t)i * MLP_S + lane] = node;
+    if (EXTRA && ex.feat) learned_features<T>(i, lane, node, ncand, lane < ncand ? cdep[lane] : 0, gss, bs, xi, s_w, ncols, rp,
                                      ci, bv, ex.feat + (int64_t)i * MLP_F);
-    if (!ex.greedy) return false;
+    if (EXTRA && !ex.greedy) return false;
     T gsj[CMAX], GJJ[CMAX][CMAX], bJ[CMAX], pbest[CMAX];
     int J[CMAX];
 #pragma unroll
@@ -502,7 +504,7 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
         }
         pcnt[i] = nJ;
     }
-    if (ex.target && lane < MLP_S) {  // the LS row on the slots (Algorithm 2's choice)
+    if (EXTRA && ex.target && lane < MLP_S) {  // the LS row on the slots (Algorithm 2's choice)
         float tv = 0.f;
 #pragma unroll
         for (int a = 0; a < CMAX; ++a)
@@ -515,7 +517,7 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
 // First pass (list == nullptr): warp per point i; a point whose search overflows the
 // CAP-entry list is appended to ovf_list (or flags err when ovf_list is null).  Second
 // pass (list != nullptr): persistent warps over the *list_count points of list.
-template <typename T, int CAP, int WARPS>
+template <typename T, int CAP, int WARPS, bool EXTRA>
 __global__ void __launch_bounds__(WARPS * 32)
     k_ls_fit(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
              const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx, const T* __restrict__ X, int ncols,
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     if (list == nullptr) {
         const int i = blockIdx.x * WARPS + wid;
         if (i >= n) return;
-        const bool ovf = ls_point<T, CAP>(i, rp, ci, bv, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol, pval,
+        const bool ovf = ls_point<T, CAP, EXTRA>(i, rp, ci, bv, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol, pval,
                                           pcnt, s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_cdep[wid],
                                           s_xi[wid], s_xj[wid], ovf_list != nullptr, ex);
         if (ovf && lane == 0) {
@@ -550,7 +552,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
     const int cnt = *list_count;
     for (int k = blockIdx.x * WARPS + wid; k < cnt; k += gridDim.x * WARPS) {
-        const bool ovf = ls_point<T, CAP>(list[k], rp, ci, bv, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol,
+        const bool ovf = ls_point<T, CAP, EXTRA>(list[k], rp, ci, bv, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol,
                                           pval, pcnt, s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_cdep[wid],
                                           s_xi[wid], s_xj[wid], false, ex);
         if (ovf && lane == 0) atomicOr(err, 1);
@@ -572,12 +574,23 @@ int interp_ls(int n, const int32_t* rp, const int32_t* ci, const T* bv, const ui
     BAMG_CK(cudaMemsetAsync(ocount.get(), 0, sizeof(int), s));
     int* e = d_err ? d_err : err.get();  // with d_err the caller reads the overflow flag later
     if (!d_err) BAMG_CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
-    BAMG_LAUNCH((k_ls_fit<T, VIS_CAP, LS_WARPS>), blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, bv, cf,
-                cidx, X, ncols, ld, d_w, z, mmax, c, ridge, pcol, pval, pcnt, (const int*)nullptr, (const int*)nullptr,
-                olist.get(), ocount.get(), e, ex);
-    BAMG_LAUNCH((k_ls_fit<T, VIS_CAP2, 1>), LS2_BLOCKS, 32, 0, s, n, rp, ci, bv, cf, cidx, X, ncols, ld, d_w, z, mmax,
-                c, ridge, pcol, pval, pcnt, (const int*)olist.get(), (const int*)ocount.get(), (int*)nullptr,
-                (int*)nullptr, e, ex);
+    // the optional outputs are compiled into a separate instance (they cost registers)
+    const bool extra = ex.feat || ex.target || ex.cand || !ex.greedy;
+    if (extra) {
+        BAMG_LAUNCH((k_ls_fit<T, VIS_CAP, LS_WARPS, true>), blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci, bv,
+                    cf, cidx, X, ncols, ld, d_w, z, mmax, c, ridge, pcol, pval, pcnt, (const int*)nullptr,
+                    (const int*)nullptr, olist.get(), ocount.get(), e, ex);
+        BAMG_LAUNCH((k_ls_fit<T, VIS_CAP2, 1, true>), LS2_BLOCKS, 32, 0, s, n, rp, ci, bv, cf, cidx, X, ncols, ld, d_w,
+                    z, mmax, c, ridge, pcol, pval, pcnt, (const int*)olist.get(), (const int*)ocount.get(),
+                    (int*)nullptr, (int*)nullptr, e, ex);
+    } else {
+        BAMG_LAUNCH((k_ls_fit<T, VIS_CAP, LS_WARPS, false>), blocks_for(n, LS_WARPS), LS_WARPS * 32, 0, s, n, rp, ci,
+                    bv, cf, cidx, X, ncols, ld, d_w, z, mmax, c, ridge, pcol, pval, pcnt, (const int*)nullptr,
+                    (const int*)nullptr, olist.get(), ocount.get(), e, ex);
+        BAMG_LAUNCH((k_ls_fit<T, VIS_CAP2, 1, false>), LS2_BLOCKS, 32, 0, s, n, rp, ci, bv, cf, cidx, X, ncols, ld,
+                    d_w, z, mmax, c, ridge, pcol, pval, pcnt, (const int*)olist.get(), (const int*)ocount.get(),
+                    (int*)nullptr, (int*)nullptr, e, ex);
+    }
     if (d_err) return 0;
     int h = 0;
     BAMG_CK(cudaMemcpyAsync(&h, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
