@@ -49,6 +49,19 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(v: float, device) -> float:
+    """The maximum of v over the ranks of the initialised process group (v itself when
+    there is none): the job's step time is its slowest replica's."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _line(d):
     print(json.dumps(d), flush=True)
 
@@ -158,11 +171,8 @@ def run_ours(args):
             _line({"metric": METRIC, "value": round(float(np.mean(times)), 4), "unit": "ms",
                    "gmres_iterations": int(np.median(iters)), "gpu_launches": int(round(launches)), "only_step": True})
         return
-    ms = float(np.sum(times)) / args.steps
+    ms = max_over_ranks(float(np.sum(times)) / args.steps, dev)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     # ---- accuracy of the timed result against a sparse direct solution
     xe = _direct_stationary(ch) if rank == 0 else None
