@@ -777,54 +777,102 @@ __global__ void k_gal_count(int nc, const int32_t* __restrict__ qrp, const int32
 }
 
 template <typename T>
-__global__ void k_gal_expand(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
-                             const T* __restrict__ qv, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                             const T* __restrict__ bv, const T* __restrict__ tv, const int32_t* __restrict__ pcol,
-                             const T* __restrict__ pval, const int32_t* __restrict__ pcnt, int c,
-                             const int32_t* __restrict__ poff, int32_t* __restrict__ pJ, T* __restrict__ pvb,
-                             T* __restrict__ pvt) {
+__global__ void k_gal_compact(int nc, const int32_t* __restrict__ poff, const int32_t* __restrict__ ucnt,
+                              const int32_t* __restrict__ rpc, const int32_t* __restrict__ uJ, const T* __restrict__ ubv,
+                              const T* __restrict__ utv, int32_t* __restrict__ ci, T* __restrict__ bv,
+                              T* __restrict__ tv) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
-    int o = poff[I];
-    for (int q = qrp[I]; q < qrp[I + 1]; ++q) {
-        const int i = qci[q];
-        const T qq = qv[q];
-        for (int p = rp[i]; p < rp[i + 1]; ++p) {
-            const int j = ci[p];
-            const T qb = mul_rn(qq, bv[p]);
-            const T qt = tv ? mul_rn(qq, tv[p]) : (j == i ? qq : T(0));
-            const int cnt = pcnt[j];
-            for (int s = 0; s < cnt; ++s) {
-                const T pv = pval[(int64_t)j * c + s];
-                pJ[o] = pcol[(int64_t)j * c + s];
-                pvb[o] = mul_rn(qb, pv);
-                pvt[o] = mul_rn(qt, pv);
-                ++o;
-            }
-        }
+    const int o = poff[I], d = rpc[I];
+    for (int u = 0; u < ucnt[I]; ++u) {
+        ci[d + u] = uJ[o + u];
+        bv[d + u] = ubv[o + u];
+        tv[d + u] = utv[o + u];
     }
 }
 
-constexpr int GAL_WARPS = 2;
-constexpr int GAL_CAP = 2048;
+// Expansion, ordering and summation of one coarse row in one warp, in shared memory: the
+// lanes enumerate the row's (Q entry, B entry) pairs in order, each writing the products of
+// its pair at their position in the definition order (a warp prefix sum over the pairs'
+// product counts); the (J, position) keys are sorted by a bitonic network and every run of
+// equal J is summed in position order.  Rows with more than GALF_CAP products take the
+// expansion to global memory and a quadratic scan over it.
+constexpr int GALF_WARPS = 2;
+constexpr int GALF_CAP = 1024;
 
 template <typename T>
-__global__ void __launch_bounds__(GAL_WARPS * 32)
-    k_gal_reduce(int nc, const int32_t* __restrict__ poff, const int32_t* __restrict__ pJ, const T* __restrict__ pvb,
-                 const T* __restrict__ pvt, int32_t* __restrict__ ucnt, int32_t* __restrict__ uJ, T* __restrict__ ubv,
-                 T* __restrict__ utv, uint8_t* __restrict__ head) {
-    __shared__ unsigned long long s_keys[GAL_WARPS][GAL_CAP];
+__global__ void __launch_bounds__(GALF_WARPS * 32)
+    k_gal_fused(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci, const T* __restrict__ qv,
+                const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
+                const T* __restrict__ tv, const int32_t* __restrict__ pcol, const T* __restrict__ pval,
+                const int32_t* __restrict__ pcnt, int c, const int32_t* __restrict__ poff, int32_t* __restrict__ pJ,
+                T* __restrict__ pvb, T* __restrict__ pvt, int32_t* __restrict__ ucnt, int32_t* __restrict__ uJ,
+                T* __restrict__ ubv, T* __restrict__ utv, uint8_t* __restrict__ head) {
+    extern __shared__ __align__(16) unsigned char galf_smem[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int I = blockIdx.x * GAL_WARPS + wid;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(galf_smem) + (size_t)wid * GALF_CAP;
+    T* svb = reinterpret_cast<T*>(reinterpret_cast<unsigned long long*>(galf_smem) + (size_t)GALF_WARPS * GALF_CAP) +
+             (size_t)wid * 2 * GALF_CAP;
+    T* svt = svb + GALF_CAP;
+    const int I = blockIdx.x * GALF_WARPS + wid;
     if (I >= nc) return;
     const int o = poff[I], np = poff[I + 1] - o;
     const unsigned lt = (1u << lane) - 1u;
-    if (np <= GAL_CAP) {
-        unsigned long long* keys = s_keys[wid];
+    const bool local = np <= GALF_CAP;
+    // ---- enumerate (q, p) pairs; pair f of the row: the f-th B entry over the Q entries
+    const int q0 = qrp[I], q1 = qrp[I + 1];
+    int npairs = 0;
+    for (int q = q0; q < q1; ++q) npairs += rp[qci[q] + 1] - rp[qci[q]];
+    int base = 0;
+    for (int f0 = 0; f0 < npairs; f0 += 32) {
+        const int f = f0 + lane;
+        int q = q0, acc = 0, i = -1, p = -1;
+        if (f < npairs) {
+            for (; q < q1; ++q) {
+                const int ii = qci[q], len = rp[ii + 1] - rp[ii];
+                if (f < acc + len) {
+                    i = ii;
+                    p = rp[ii] + (f - acc);
+                    break;
+                }
+                acc += len;
+            }
+        }
+        const int j = f < npairs ? ci[p] : 0;
+        const int cnt = f < npairs ? pcnt[j] : 0;
+        int incl = cnt;  // inclusive warp prefix sum of the product counts
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int pos0 = base + incl - cnt;
+        if (f < npairs) {
+            const T qq = qv[q];
+            const T qb = mul_rn(qq, bv[p]);
+            const T qt = tv ? mul_rn(qq, tv[p]) : (j == i ? qq : T(0));
+            for (int sl = 0; sl < cnt; ++sl) {
+                const T pv = pval[(int64_t)j * c + sl];
+                const int J = pcol[(int64_t)j * c + sl];
+                const int e = pos0 + sl;
+                if (local) {
+                    keys[e] = ((unsigned long long)(unsigned)J << 32) | (unsigned)e;
+                    svb[e] = mul_rn(qb, pv);
+                    svt[e] = mul_rn(qt, pv);
+                } else {
+                    pJ[o + e] = J;
+                    pvb[o + e] = mul_rn(qb, pv);
+                    pvt[o + e] = mul_rn(qt, pv);
+                }
+            }
+        }
+        base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    if (local) {
         int N = 32;
         while (N < np) N <<= 1;
-        for (int e = lane; e < N; e += 32)
-            keys[e] = e < np ? (((unsigned long long)(unsigned)pJ[o + e] << 32) | (unsigned)e) : ~0ull;
+        for (int e = np + lane; e < N; e += 32) keys[e] = ~0ull;
         __syncwarp();
         for (int k = 2; k <= N; k <<= 1) {
             for (int jj = k >> 1; jj > 0; jj >>= 1) {
@@ -842,77 +890,63 @@ __global__ void __launch_bounds__(GAL_WARPS * 32)
                 __syncwarp();
             }
         }
-        int base = 0;
+        int ub = 0;
         for (int e0 = 0; e0 < np; e0 += 32) {
             const int e = e0 + lane;
             const unsigned Je = e < np ? (unsigned)(keys[e] >> 32) : 0u;
             const bool hd = e < np && (e == 0 || (unsigned)(keys[e - 1] >> 32) != Je);
             const unsigned bal = __ballot_sync(0xffffffffu, hd);
             if (hd) {
-                const int rank = base + __popc(bal & lt);
+                const int rank = ub + __popc(bal & lt);
                 const int pos0 = (int)(keys[e] & 0xffffffffu);
-                T sb = pvb[o + pos0], st = pvt[o + pos0];
+                T sb = svb[pos0], st = svt[pos0];
                 for (int e2 = e + 1; e2 < np && (unsigned)(keys[e2] >> 32) == Je; ++e2) {
                     const int pos = (int)(keys[e2] & 0xffffffffu);
-                    sb = add_rn(sb, pvb[o + pos]);
-                    st = add_rn(st, pvt[o + pos]);
+                    sb = add_rn(sb, svb[pos]);
+                    st = add_rn(st, svt[pos]);
                 }
                 uJ[o + rank] = (int32_t)Je;
                 ubv[o + rank] = sb;
                 utv[o + rank] = st;
             }
-            base += __popc(bal);
+            ub += __popc(bal);
         }
-        if (lane == 0) ucnt[I] = base;
-    } else {
-        // long rows: quadratic scan in global memory
-        for (int e = lane; e < np; e += 32) {
-            const int Je = pJ[o + e];
-            bool hd = true;
-            for (int e2 = 0; e2 < e; ++e2)
-                if (pJ[o + e2] == Je) {
-                    hd = false;
-                    break;
-                }
-            head[o + e] = hd ? 1 : 0;
-        }
-        __syncwarp();
-        int cnt = 0;
-        for (int e = lane; e < np; e += 32) {
-            if (!head[o + e]) continue;
-            ++cnt;
-            const int Je = pJ[o + e];
-            int rank = 0;
-            for (int e2 = 0; e2 < np; ++e2) rank += (head[o + e2] && pJ[o + e2] < Je);
-            T sb = pvb[o + e], st = pvt[o + e];
-            for (int e2 = e + 1; e2 < np; ++e2)
-                if (pJ[o + e2] == Je) {
-                    sb = add_rn(sb, pvb[o + e2]);
-                    st = add_rn(st, pvt[o + e2]);
-                }
-            uJ[o + rank] = Je;
-            ubv[o + rank] = sb;
-            utv[o + rank] = st;
-        }
+        if (lane == 0) ucnt[I] = ub;
+        return;
+    }
+    // ---- long rows: the products are in global memory; quadratic scan
+    __syncwarp();
+    for (int e = lane; e < np; e += 32) {
+        const int Je = pJ[o + e];
+        bool hd = true;
+        for (int e2 = 0; e2 < e; ++e2)
+            if (pJ[o + e2] == Je) {
+                hd = false;
+                break;
+            }
+        head[o + e] = hd ? 1 : 0;
+    }
+    __syncwarp();
+    int cntu = 0;
+    for (int e = lane; e < np; e += 32) {
+        if (!head[o + e]) continue;
+        ++cntu;
+        const int Je = pJ[o + e];
+        int rank = 0;
+        for (int e2 = 0; e2 < np; ++e2) rank += (head[o + e2] && pJ[o + e2] < Je);
+        T sb = pvb[o + e], st = pvt[o + e];
+        for (int e2 = e + 1; e2 < np; ++e2)
+            if (pJ[o + e2] == Je) {
+                sb = add_rn(sb, pvb[o + e2]);
+                st = add_rn(st, pvt[o + e2]);
+            }
+        uJ[o + rank] = Je;
+        ubv[o + rank] = sb;
+        utv[o + rank] = st;
+    }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
-        if (lane == 0) ucnt[I] = cnt;
-    }
-}
-
-template <typename T>
-__global__ void k_gal_compact(int nc, const int32_t* __restrict__ poff, const int32_t* __restrict__ ucnt,
-                              const int32_t* __restrict__ rpc, const int32_t* __restrict__ uJ, const T* __restrict__ ubv,
-                              const T* __restrict__ utv, int32_t* __restrict__ ci, T* __restrict__ bv,
-                              T* __restrict__ tv) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
-    const int o = poff[I], d = rpc[I];
-    for (int u = 0; u < ucnt[I]; ++u) {
-        ci[d + u] = uJ[o + u];
-        bv[d + u] = ubv[o + u];
-        tv[d + u] = utv[o + u];
-    }
+    for (int off = 16; off > 0; off >>= 1) cntu += __shfl_xor_sync(0xffffffffu, cntu, off);
+    if (lane == 0) ucnt[I] = cntu;
 }
 
 template <typename T>
@@ -928,10 +962,10 @@ void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int
     TmpBuf<int32_t> pJ(tot, s), uJ(tot, s), ucnt(nc, s);
     TmpBuf<T> pvb(tot, s), pvt(tot, s), ubv(tot, s), utv(tot, s);
     TmpBuf<uint8_t> head(tot, s);
-    BAMG_LAUNCH(k_gal_expand<T>, blocks_for(nc, 128), 128, 0, s, nc, qrp, qci, qv, B.rp, B.ci, B.v, T_val, P.pcol,
-                P.pval, P.pcnt, P.c, poff.get(), pJ.get(), pvb.get(), pvt.get());
-    BAMG_LAUNCH(k_gal_reduce<T>, blocks_for(nc, GAL_WARPS), GAL_WARPS * 32, 0, s, nc, poff.get(), pJ.get(), pvb.get(),
-                pvt.get(), ucnt.get(), uJ.get(), ubv.get(), utv.get(), head.get());
+    const size_t smem = (size_t)GALF_WARPS * GALF_CAP * (sizeof(unsigned long long) + 2 * sizeof(T));
+    BAMG_LAUNCH(k_gal_fused<T>, blocks_for(nc, GALF_WARPS), GALF_WARPS * 32, smem, s, nc, qrp, qci, qv, B.rp, B.ci, B.v,
+                T_val, P.pcol, P.pval, P.pcnt, P.c, poff.get(), pJ.get(), pvb.get(), pvt.get(), ucnt.get(), uJ.get(),
+                ubv.get(), utv.get(), head.get());
     out.rp.alloc(nc + 1);
     exclusive_scan(ucnt.get(), out.rp.get(), nc, s);
     out.nnz = read_int(out.rp.get() + nc, s);

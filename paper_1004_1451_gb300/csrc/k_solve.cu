@@ -3,6 +3,9 @@
 // FP64 pieces of flexible GMRES on B x = 0 (Section 4.2): sparse products with B,
 // classical Gram-Schmidt dots and updates, Givens rotations, the update x0 + Z y, and
 // the true residual ||B x||_1 / ||x||_1.
+#include <algorithm>
+#include <utility>
+
 #include "gmres_state.cuh"
 #include "kernels.cuh"
 
@@ -118,13 +121,124 @@ __global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b, T* __r
     if (Z) Z[(int64_t)(*dj) * n + i] = a[i];
 }
 
+// The coarse end of the cycle in one block: every level from the first one with at most
+// TAIL_MAX_N rows down to the coarsest solve and back up, with block barriers between
+// the phases instead of kernel boundaries (the levels are too small to fill the GPU, and
+// each launch would cost more than its work).  Same per-row arithmetic and buffer
+// sequence as the grid kernels, so the result is identical.
+constexpr int TAIL_MAX_N = 1024;
+constexpr int TAIL_THREADS = 512;
+constexpr int TAIL_MAX_LEVELS = 12;
+template <typename T>
+struct TailArgs {
+    VLevel<T> lv[TAIL_MAX_LEVELS];
+    int nl = 0;  // levels in the tail; the last one is the coarsest
+    const T* pinv = nullptr;
+    int nu_pre = 0, nu_post = 0;
+    T omega = T(0);
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<T> a) {
+    const int tid = threadIdx.x;
+    T* xcur[TAIL_MAX_LEVELS];
+    T* xtmp[TAIL_MAX_LEVELS];
+    for (int l = 0; l + 1 < a.nl; ++l) {
+        const VLevel<T>& v = a.lv[l];
+        const int n = v.B.n;
+        T* x = v.x;
+        T* t = v.r;
+        if (a.nu_pre >= 2) {
+            for (int i = tid; i < n; i += blockDim.x) {
+                const T x1 = (a.omega * v.dinv[i]) * v.b[i];
+                x[i] = x1 + (a.omega * v.dinv[i]) * (v.b[i] - row_Bx1(i, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, a.omega));
+            }
+            __syncthreads();
+            for (int k = 2; k < a.nu_pre; ++k) {
+                for (int i = tid; i < n; i += blockDim.x)
+                    t[i] = x[i] + (a.omega * v.dinv[i]) * (v.b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x));
+                __syncthreads();
+                T* q = x;
+                x = t;
+                t = q;
+            }
+        } else if (a.nu_pre == 1) {
+            for (int i = tid; i < n; i += blockDim.x) x[i] = (a.omega * v.dinv[i]) * v.b[i];
+            __syncthreads();
+        } else {
+            for (int i = tid; i < n; i += blockDim.x) x[i] = T(0);
+            __syncthreads();
+        }
+        for (int i = tid; i < n; i += blockDim.x) t[i] = v.b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x);
+        __syncthreads();
+        const int nc = a.lv[l + 1].B.n;
+        T* bc = a.lv[l + 1].b;
+        for (int I = tid; I < nc; I += blockDim.x)
+            bc[I] = row_sum<T>(v.qrp[I], v.qrp[I + 1], v.qci, v.qv, [&](int i) { return t[i]; });
+        __syncthreads();
+        xcur[l] = x;
+        xtmp[l] = t;
+    }
+    {  // coarsest: x = B_L^+ b, one warp per row as in the grid kernel
+        const VLevel<T>& v = a.lv[a.nl - 1];
+        const int n = v.B.n;
+        const int lane = tid & 31;
+        for (int row = tid >> 5; row < n; row += blockDim.x >> 5) {
+            T sum = T(0);
+            for (int c = lane; c < n; c += 32) sum += a.pinv[(int64_t)row * n + c] * v.b[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) v.x[row] = sum;
+        }
+        __syncthreads();
+        xcur[a.nl - 1] = v.x;
+    }
+    for (int l = a.nl - 2; l >= 0; --l) {
+        const VLevel<T>& v = a.lv[l];
+        const int n = v.B.n;
+        T* x = xcur[l];
+        T* t = xtmp[l];
+        const T* ec = xcur[l + 1];
+        for (int i = tid; i < n; i += blockDim.x) x[i] = row_prolonged(i, v.P.c, v.P.pcol, v.P.pval, v.P.pcnt, ec, x);
+        __syncthreads();
+        for (int k = 0; k < a.nu_post; ++k) {
+            for (int i = tid; i < n; i += blockDim.x)
+                t[i] = x[i] + (a.omega * v.dinv[i]) * (v.b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x));
+            __syncthreads();
+            T* q = x;
+            x = t;
+            t = q;
+        }
+        xcur[l] = x;
+    }
+}
+
+// The buffer that holds a level's final x after the down and up passes (the sequence of
+// swaps in vcycle and k_vcycle_tail).
+template <typename T>
+static T* final_x(const VLevel<T>& v, int nu_pre, int nu_post, bool coarsest) {
+    if (coarsest) return v.x;
+    T* x = v.x;
+    T* t = v.r;
+    for (int k = 2; k < nu_pre; ++k) std::swap(x, t);
+    for (int k = 0; k < nu_post; ++k) std::swap(x, t);
+    return x;
+}
+
 template <typename T>
 void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int nu_pre, int nu_post, cudaStream_t s,
             T* Z, const int* dj) {
     const int L = (int)lv.size() - 1;
     const T omega = (T)omega_d;
+    // the levels from l0 on (small enough for one block) run in k_vcycle_tail
+    int l0 = L + 1;
+    for (int l = 1; l <= L; ++l)
+        if (lv[l].B.n <= TAIL_MAX_N && L - l + 1 <= TAIL_MAX_LEVELS) {
+            l0 = l;
+            break;
+        }
     std::vector<T*> xcur(L + 1), xtmp(L + 1);
-    for (int l = 0; l < L; ++l) {
+    for (int l = 0; l < std::min(L, l0); ++l) {
         const VLevel<T>& v = lv[l];
         const int n = v.B.n;
         const unsigned g = blocks_for(n, 256);
@@ -150,13 +264,23 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         xcur[l] = x;
         xtmp[l] = t;
     }
-    {
+    if (l0 <= L) {
+        TailArgs<T> a;
+        a.nl = L - l0 + 1;
+        for (int q = 0; q < a.nl; ++q) a.lv[q] = lv[l0 + q];
+        a.pinv = pinv;
+        a.nu_pre = nu_pre;
+        a.nu_post = nu_post;
+        a.omega = omega;
+        BAMG_LAUNCH(k_vcycle_tail<T>, 1, TAIL_THREADS, 0, s, a);
+        xcur[l0] = final_x(lv[l0], nu_pre, nu_post, l0 == L);
+    } else {
         const int n = lv[L].B.n;
         BAMG_LAUNCH(k_dense_mv<T>, blocks_for(n, 4), 128, 0, s, n, pinv, lv[L].b, lv[L].x);
         xcur[L] = lv[L].x;
         if (L == 0 && Z) BAMG_LAUNCH(k_copy<T>, blocks_for(n, 256), 256, 0, s, n, lv[0].x, lv[0].x, Z, dj);
     }
-    for (int l = L - 1; l >= 0; --l) {
+    for (int l = std::min(L, l0) - 1; l >= 0; --l) {
         const VLevel<T>& v = lv[l];
         const int n = v.B.n;
         const unsigned g = blocks_for(n, 256);
