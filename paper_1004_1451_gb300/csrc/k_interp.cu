@@ -312,15 +312,14 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
                             isnew = false;
                             break;
                         }
-                const bool isc = isnew && cf[v] != 0;
                 const int key = isnew ? v : -1 - lane;
                 const unsigned grp = __match_any_sync(0xffffffffu, key);
                 const unsigned lt = (1u << lane) - 1u;
                 const bool leader = isnew && (grp & lt) == 0u;
-                unsigned bal = __ballot_sync(0xffffffffu, leader && (!fonly || isc));
-                if (!fonly && nvis + __popc(bal) > CAP) {
+                unsigned bal = __ballot_sync(0xffffffffu, leader);
+                if (fonly || nvis + __popc(bal) > CAP) {  // list full: keep the coarse nodes only
                     fonly = true;
-                    bal = __ballot_sync(0xffffffffu, leader && isc);
+                    bal = __ballot_sync(0xffffffffu, leader && cf[v] != 0);
                 }
                 const bool rec = (bal >> lane) & 1u;
                 const int pos = nvis + __popc(bal & lt);
@@ -333,10 +332,13 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
                     ovf = true;
                     added = CAP - nvis;
                 }
-                ncvis += __popc(__ballot_sync(0xffffffffu, rec && isc && pos < CAP));
                 nvis += added;
                 __syncwarp();
             }
+        }
+        for (int q0 = fe; q0 < nvis; q0 += 32) {  // coarse points recorded at this depth
+            const int q = q0 + lane;
+            ncvis += __popc(__ballot_sync(0xffffffffu, q < nvis && cf[vis[q]] != 0));
         }
         // a truncated depth (fine nodes not recorded) is exact only if the search ends here
         if (fonly) {
