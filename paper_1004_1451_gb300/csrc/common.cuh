@@ -44,6 +44,42 @@ void set_last_error(const std::string& msg);
         BAMG_CK(cudaGetLastError());                                                               \
     } while (0)
 
+// Programmatic dependent launch: while pdl_enabled() is set (the capture of the Arnoldi
+// step) BAMG_LAUNCH_PDL lets a kernel start launching before its predecessor finishes;
+// every such kernel calls pdl_begin() before its first memory access, which waits until
+// the predecessor grid has completed and its writes are visible, and signals that its own
+// dependents may launch.  Without the attribute both instructions return at once.
+bool& pdl_enabled();
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+struct PdlScope {
+    bool prev;
+    PdlScope() : prev(pdl_enabled()) { pdl_enabled() = true; }
+    ~PdlScope() { pdl_enabled() = prev; }
+};
+#define BAMG_LAUNCH_PDL(kernel, grid, block, smem, strm_, ...)                                      \
+    do {                                                                                           \
+        if (::bamg::pdl_enabled()) {                                                               \
+            cudaLaunchConfig_t cfg_ = {};                                                          \
+            cfg_.gridDim = dim3(grid);                                                             \
+            cfg_.blockDim = dim3(block);                                                           \
+            cfg_.dynamicSmemBytes = (smem);                                                        \
+            cfg_.stream = (strm_);                                                                  \
+            cudaLaunchAttribute at_[1];                                                            \
+            at_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                        \
+            at_[0].val.programmaticStreamSerializationAllowed = 1;                                 \
+            cfg_.attrs = at_;                                                                      \
+            cfg_.numAttrs = 1;                                                                     \
+            BAMG_CK(cudaLaunchKernelEx(&cfg_, kernel, __VA_ARGS__));                               \
+        } else {                                                                                   \
+            kernel<<<(grid), (block), (smem), (strm_)>>>(__VA_ARGS__);                              \
+        }                                                                                          \
+        ::bamg::count_launch();                                                                    \
+        BAMG_CK(cudaGetLastError());                                                               \
+    } while (0)
+
 inline unsigned blocks_for(int64_t work, int per_block) {
     int64_t b = (work + per_block - 1) / per_block;
     return (unsigned)(b < 1 ? 1 : b);

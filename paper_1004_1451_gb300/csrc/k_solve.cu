@@ -57,6 +57,7 @@ __device__ __forceinline__ T row_prolonged(int j, int c, const int32_t* __restri
 
 template <typename T>
 __global__ void k_smooth0(int n, const T* __restrict__ dinv, const T* __restrict__ b, T* __restrict__ x, T omega) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = (omega * dinv[i]) * b[i];
 }
@@ -65,6 +66,7 @@ template <typename T>
 __global__ void k_presmooth2(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                              const T* __restrict__ bv, const T* __restrict__ dinv, const T* __restrict__ b,
                              T* __restrict__ y, T omega) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const T x1 = (omega * dinv[i]) * b[i];
@@ -76,6 +78,7 @@ __global__ void k_smooth(int n, const int32_t* __restrict__ rp, const int32_t* _
                          const T* __restrict__ bv, const T* __restrict__ dinv, const T* __restrict__ b,
                          const T* __restrict__ x, T* __restrict__ y, T omega, T* __restrict__ Z,
                          const int* __restrict__ dj) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const T v = x[i] + (omega * dinv[i]) * (b[i] - row_Bx(i, rp, ci, bv, x));
@@ -86,12 +89,14 @@ template <typename T>
 __global__ void k_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                         const T* __restrict__ bv, const T* __restrict__ b, const T* __restrict__ x,
                         T* __restrict__ r) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) r[i] = b[i] - row_Bx(i, rp, ci, bv, x);
 }
 template <typename T>
 __global__ void k_restrict(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
                            const T* __restrict__ qv, const T* __restrict__ r, T* __restrict__ bc) {
+    pdl_begin();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
     bc[I] = row_sum<T>(qrp[I], qrp[I + 1], qci, qv, [&](int i) { return r[i]; });
@@ -99,11 +104,13 @@ __global__ void k_restrict(int nc, const int32_t* __restrict__ qrp, const int32_
 template <typename T>
 __global__ void k_prolong_add(int n, int c, const int32_t* __restrict__ pcol, const T* __restrict__ pval,
                               const int32_t* __restrict__ pcnt, const T* __restrict__ ec, T* __restrict__ x) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = row_prolonged(i, c, pcol, pval, pcnt, ec, x);
 }
 template <typename T>
 __global__ void k_dense_mv(int n, const T* __restrict__ A, const T* __restrict__ b, T* __restrict__ x) {
+    pdl_begin();
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
@@ -115,6 +122,7 @@ __global__ void k_dense_mv(int n, const T* __restrict__ A, const T* __restrict__
 }
 template <typename T>
 __global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b, T* __restrict__ Z, const int* __restrict__ dj) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     b[i] = a[i];
@@ -140,6 +148,7 @@ struct TailArgs {
 
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<T> a) {
+    pdl_begin();
     const int tid = threadIdx.x;
     T* xcur[TAIL_MAX_LEVELS];
     T* xtmp[TAIL_MAX_LEVELS];
@@ -245,22 +254,22 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         T* x = v.x;
         T* t = v.r;
         if (nu_pre >= 2) {
-            BAMG_LAUNCH(k_presmooth2<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, omega);
+            BAMG_LAUNCH_PDL(k_presmooth2<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, omega);
             for (int k = 2; k < nu_pre; ++k) {
-                BAMG_LAUNCH(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
+                BAMG_LAUNCH_PDL(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
                             (T*)nullptr, (const int*)nullptr);
                 T* q = x;
                 x = t;
                 t = q;
             }
         } else if (nu_pre == 1) {
-            BAMG_LAUNCH(k_smooth0<T>, g, 256, 0, s, n, v.dinv, v.b, x, omega);
+            BAMG_LAUNCH_PDL(k_smooth0<T>, g, 256, 0, s, n, v.dinv, v.b, x, omega);
         } else {
             BAMG_CK(cudaMemsetAsync(x, 0, sizeof(T) * n, s));
         }
-        BAMG_LAUNCH(k_resid<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.b, x, t);
+        BAMG_LAUNCH_PDL(k_resid<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.b, x, t);
         const int nc = lv[l + 1].B.n;
-        BAMG_LAUNCH(k_restrict<T>, blocks_for(nc, 256), 256, 0, s, nc, v.qrp, v.qci, v.qv, t, lv[l + 1].b);
+        BAMG_LAUNCH_PDL(k_restrict<T>, blocks_for(nc, 256), 256, 0, s, nc, v.qrp, v.qci, v.qv, t, lv[l + 1].b);
         xcur[l] = x;
         xtmp[l] = t;
     }
@@ -272,13 +281,13 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         a.nu_pre = nu_pre;
         a.nu_post = nu_post;
         a.omega = omega;
-        BAMG_LAUNCH(k_vcycle_tail<T>, 1, TAIL_THREADS, 0, s, a);
+        BAMG_LAUNCH_PDL(k_vcycle_tail<T>, 1, TAIL_THREADS, 0, s, a);
         xcur[l0] = final_x(lv[l0], nu_pre, nu_post, l0 == L);
     } else {
         const int n = lv[L].B.n;
-        BAMG_LAUNCH(k_dense_mv<T>, blocks_for(n, 4), 128, 0, s, n, pinv, lv[L].b, lv[L].x);
+        BAMG_LAUNCH_PDL(k_dense_mv<T>, blocks_for(n, 4), 128, 0, s, n, pinv, lv[L].b, lv[L].x);
         xcur[L] = lv[L].x;
-        if (L == 0 && Z) BAMG_LAUNCH(k_copy<T>, blocks_for(n, 256), 256, 0, s, n, lv[0].x, lv[0].x, Z, dj);
+        if (L == 0 && Z) BAMG_LAUNCH_PDL(k_copy<T>, blocks_for(n, 256), 256, 0, s, n, lv[0].x, lv[0].x, Z, dj);
     }
     for (int l = std::min(L, l0) - 1; l >= 0; --l) {
         const VLevel<T>& v = lv[l];
@@ -287,19 +296,19 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         T* x = xcur[l];
         T* t = xtmp[l];
         T* zl = (l == 0) ? Z : nullptr;
-        BAMG_LAUNCH(k_prolong_add<T>, g, 256, 0, s, n, v.P.c, v.P.pcol, v.P.pval, v.P.pcnt, xcur[l + 1], x);
+        BAMG_LAUNCH_PDL(k_prolong_add<T>, g, 256, 0, s, n, v.P.c, v.P.pcol, v.P.pval, v.P.pcnt, xcur[l + 1], x);
         for (int k = 0; k < nu_post; ++k) {
-            BAMG_LAUNCH(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
+            BAMG_LAUNCH_PDL(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
                         k == nu_post - 1 ? zl : (T*)nullptr, dj);
             T* q = x;
             x = t;
             t = q;
         }
-        if (nu_post == 0 && zl) BAMG_LAUNCH(k_copy<T>, g, 256, 0, s, n, x, x, zl, dj);
+        if (nu_post == 0 && zl) BAMG_LAUNCH_PDL(k_copy<T>, g, 256, 0, s, n, x, x, zl, dj);
         xcur[l] = x;
     }
     if (L > 0 && xcur[0] != lv[0].x)
-        BAMG_LAUNCH(k_copy<T>, blocks_for(lv[0].B.n, 256), 256, 0, s, lv[0].B.n, xcur[0], lv[0].x, (T*)nullptr,
+        BAMG_LAUNCH_PDL(k_copy<T>, blocks_for(lv[0].B.n, 256), 256, 0, s, lv[0].B.n, xcur[0], lv[0].x, (T*)nullptr,
                     (const int*)nullptr);
 }
 
@@ -520,6 +529,7 @@ void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s) { BAMG_LAUNCH(
 // v_{j+1} = w / ||w||, and j <- j + 1.
 template <typename T>
 __global__ void k_v_to_in(int n, const double* __restrict__ V, const int* __restrict__ dj, T* __restrict__ vin) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) vin[i] = (T)V[(int64_t)(*dj) * n + i];
 }
@@ -527,6 +537,7 @@ template <typename TX>
 __global__ void k_spmv64_j(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ bv, const TX* __restrict__ x, const int* __restrict__ dj,
                            double* __restrict__ V) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     V[(int64_t)(*dj + 1) * n + i] = row_sum<double>(rp[i], rp[i + 1], ci, bv, [&](int j) { return (double)x[j]; });
@@ -535,6 +546,7 @@ __global__ void k_spmv64_j(int n, const int32_t* __restrict__ rp, const int32_t*
 __global__ void __launch_bounds__(256) k_dots_partial_j(int n, const double* __restrict__ V,
                                                         const int* __restrict__ dj, int self,
                                                         double* __restrict__ partial, int stride) {
+    pdl_begin();
     __shared__ double sw[DOT_ROWS];
     const int j = *dj;
     const double* w = V + (int64_t)(j + 1) * n;
@@ -555,6 +567,7 @@ __global__ void __launch_bounds__(256) k_dots_partial_j(int n, const double* __r
 }
 __global__ void k_reduce_cols_j(int nb, const int* __restrict__ dj, int self, int stride,
                                 const double* __restrict__ partial, double* __restrict__ h) {
+    pdl_begin();
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int nv = self ? 1 : *dj + 1;
@@ -566,6 +579,7 @@ __global__ void k_reduce_cols_j(int nb, const int* __restrict__ dj, int self, in
 }
 __global__ void k_update_minus_j(int n, double* __restrict__ V, const int* __restrict__ dj,
                                  const double* __restrict__ h) {
+    pdl_begin();
     __shared__ double sh[GMRES_MMAX + 1];
     const int j = *dj;
     for (int q = threadIdx.x; q <= j; q += blockDim.x) sh[q] = h[q];
@@ -579,6 +593,7 @@ __global__ void k_update_minus_j(int n, double* __restrict__ V, const int* __res
     w[i] = s;
 }
 __global__ void k_inc_j(int* dj) {
+    pdl_begin();
     if (threadIdx.x == 0 && blockIdx.x == 0) *dj += 1;
 }
 
@@ -586,6 +601,7 @@ __global__ void k_inc_j(int* dj) {
 // ||w|| = sqrt(nrm2) itself, so the scaling does not wait for the rotation.
 __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __restrict__ dj, double* __restrict__ st,
                                  int m) {
+    pdl_begin();
     __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX];
     GmresLayout L(m);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -639,20 +655,20 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
     const unsigned g = blocks_for(n, 256);
     const int nb = dots_partial_blocks(n);
     const int stride = m + 1;
-    BAMG_LAUNCH(k_v_to_in<T>, g, 256, 0, s, n, V, dj, vin);
+    BAMG_LAUNCH_PDL(k_v_to_in<T>, g, 256, 0, s, n, V, dj, vin);
     vcycle<T>(lv, pinv, omega, nu_pre, nu_post, s, Z, dj);
-    BAMG_LAUNCH(k_spmv64_j<T>, g, 256, 0, s, n, B.rp, B.ci, B.v, zout, dj, V);
+    BAMG_LAUNCH_PDL(k_spmv64_j<T>, g, 256, 0, s, n, B.rp, B.ci, B.v, zout, dj, V);
     for (int pass = 0; pass < 2; ++pass) {
         double* h = st + (pass == 0 ? L.h1 : L.h2);
-        BAMG_LAUNCH(k_dots_partial_j, nb, 256, 0, s, n, V, dj, 0, partial, stride);
-        BAMG_LAUNCH(k_reduce_cols_j, blocks_for(m + 1, 4), 128, 0, s, nb, dj, 0, stride, partial, h);
-        BAMG_LAUNCH(k_update_minus_j, g, 256, 0, s, n, V, dj, h);
+        BAMG_LAUNCH_PDL(k_dots_partial_j, nb, 256, 0, s, n, V, dj, 0, partial, stride);
+        BAMG_LAUNCH_PDL(k_reduce_cols_j, blocks_for(m + 1, 4), 128, 0, s, nb, dj, 0, stride, partial, h);
+        BAMG_LAUNCH_PDL(k_update_minus_j, g, 256, 0, s, n, V, dj, h);
     }
-    BAMG_LAUNCH(k_dots_partial_j, nb, 256, 0, s, n, V, dj, 1, partial, stride);
-    BAMG_LAUNCH(k_reduce_cols_j, 1, 128, 0, s, nb, dj, 1, stride, partial, st + L.nrm2);
-    BAMG_LAUNCH(k_givens_scale_j, g, 256, 0, s, n, V, dj, st, m);
+    BAMG_LAUNCH_PDL(k_dots_partial_j, nb, 256, 0, s, n, V, dj, 1, partial, stride);
+    BAMG_LAUNCH_PDL(k_reduce_cols_j, 1, 128, 0, s, nb, dj, 1, stride, partial, st + L.nrm2);
+    BAMG_LAUNCH_PDL(k_givens_scale_j, g, 256, 0, s, n, V, dj, st, m);
     BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    BAMG_LAUNCH(k_inc_j, 1, 32, 0, s, dj);
+    BAMG_LAUNCH_PDL(k_inc_j, 1, 32, 0, s, dj);
 }
 
 template void arnoldi_step_graphable<float>(int, const MatView<double>&, double*, float*, float*, float*, int*,

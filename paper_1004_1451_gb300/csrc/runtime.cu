@@ -28,6 +28,10 @@ void count_launches(int64_t k) {
     t_launches += (uint64_t)k;
 }
 static thread_local std::string g_err;
+bool& pdl_enabled() {
+    static thread_local bool on = false;
+    return on;
+}
 void set_last_error(const std::string& m) { g_err = m; }
 cudaStream_t& alloc_stream() {
     static thread_local cudaStream_t st = nullptr;
@@ -560,6 +564,7 @@ struct Solver : SolverBase {
         std::vector<VLevel<T>> vl = vlevels(vin.get(), zout.get());
         const uint64_t c0 = t_launches;  // other threads may launch meanwhile
         BAMG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        PdlScope pdl_;  // programmatic edges between the step's kernels
         try {
             arnoldi_step_graphable<T>(n, B64(), V.get(), Z.get(), vin.get(), zout.get(), dj.get(), state.get(), m,
                                       partial.get(), vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, h_pin, s);
