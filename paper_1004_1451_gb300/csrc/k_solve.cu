@@ -533,79 +533,109 @@ __global__ void k_v_to_in(int n, const double* __restrict__ V, const int* __rest
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) vin[i] = (T)V[(int64_t)(*dj) * n + i];
 }
-template <typename TX>
-__global__ void k_spmv64_j(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const double* __restrict__ bv, const TX* __restrict__ x, const int* __restrict__ dj,
-                           double* __restrict__ V) {
-    pdl_begin();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    V[(int64_t)(*dj + 1) * n + i] = row_sum<double>(rp[i], rp[i + 1], ci, bv, [&](int j) { return (double)x[j]; });
-}
-// self = 0: dots of w = V[j+1] with V[0..j];  self = 1: w . w
-__global__ void __launch_bounds__(256) k_dots_partial_j(int n, const double* __restrict__ V,
-                                                        const int* __restrict__ dj, int self,
-                                                        double* __restrict__ partial, int stride) {
-    pdl_begin();
-    __shared__ double sw[DOT_ROWS];
-    const int j = *dj;
-    const double* w = V + (int64_t)(j + 1) * n;
-    const int nv = self ? 1 : j + 1;
-    const int r0 = blockIdx.x * DOT_ROWS;
-    const int cnt = min(DOT_ROWS, n - r0);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sw[e] = w[r0 + e];
-    __syncthreads();
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int q = wid; q < nv; q += nw) {
-        const double* vq = (self ? w : V + (int64_t)q * n) + r0;
-        double acc = 0.0;
-#pragma unroll 4
-        for (int e = lane; e < cnt; e += 32) acc += vq[e] * sw[e];
-        acc = warp_sum(acc);
-        if (lane == 0) partial[(int64_t)blockIdx.x * stride + q] = acc;
-    }
-}
-__global__ void k_reduce_cols_j(int nb, const int* __restrict__ dj, int self, int stride,
-                                const double* __restrict__ partial, double* __restrict__ h) {
-    pdl_begin();
-    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    const int nv = self ? 1 : *dj + 1;
-    if (q >= nv) return;
-    double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += partial[(int64_t)b * stride + q];
-    s = warp_sum(s);
-    if (lane == 0) h[q] = s;
-}
-__global__ void k_update_minus_j(int n, double* __restrict__ V, const int* __restrict__ dj,
-                                 const double* __restrict__ h) {
-    pdl_begin();
-    __shared__ double sh[GMRES_MMAX + 1];
-    const int j = *dj;
-    for (int q = threadIdx.x; q <= j; q += blockDim.x) sh[q] = h[q];
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double* w = V + (int64_t)(j + 1) * n;
-    double s = w[i];
-#pragma unroll 8
-    for (int q = 0; q <= j; ++q) s -= V[(int64_t)q * n + i] * sh[q];
-    w[i] = s;
-}
 __global__ void k_inc_j(int* dj) {
     pdl_begin();
     if (threadIdx.x == 0 && blockIdx.x == 0) *dj += 1;
 }
 
+// Fused Arnoldi kernels over tiles of ARN_TILE rows (one block each).  The column sums of
+// the per-tile dot products are formed again by every block that needs them (warp per
+// column, lanes strided over the tiles, the same order in every block), so the reductions
+// need no kernel of their own.
+constexpr int ARN_TILE = 256;
+int arn_tiles(int n) { return (int)blocks_for(n, ARN_TILE); }
+
+__device__ __forceinline__ double arn_colsum(const double* __restrict__ P, int nb, int stride, int q, int lane) {
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += P[(int64_t)b * stride + q];
+    return warp_sum(s);
+}
+// per-tile dots of the tile's w (in shared memory) with V[0..j] (self = 0) or with itself
+__device__ __forceinline__ void arn_tile_dots(const double* __restrict__ V, int n, int j, int r0, int cnt,
+                                              const double* sw, int self, double* __restrict__ Pout, int stride) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nv = self ? 1 : j + 1;
+    for (int q = wid; q < nv; q += nw) {
+        const double* vq = self ? sw : V + (int64_t)q * n + r0;
+        double acc = 0.0;
+#pragma unroll 4
+        for (int e = lane; e < cnt; e += 32) acc += vq[e] * sw[e];
+        acc = warp_sum(acc);
+        if (lane == 0) Pout[(int64_t)blockIdx.x * stride + q] = acc;
+    }
+}
+
+// w = V[j+1] = B z_j (FP64) and its per-tile dots with V[0..j]
+template <typename TX>
+__global__ void __launch_bounds__(256) k_arn_spmv_dots(int n, const int32_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ ci, const double* __restrict__ bv,
+                                                       const TX* __restrict__ z, const int* __restrict__ dj,
+                                                       double* __restrict__ V, double* __restrict__ Pout, int stride) {
+    pdl_begin();
+    __shared__ double sw[ARN_TILE];
+    const int j = *dj;
+    const int r0 = blockIdx.x * ARN_TILE, cnt = min(ARN_TILE, n - r0);
+    double* w = V + (int64_t)(j + 1) * n;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int i = r0 + e;
+        const double v = row_sum<double>(rp[i], rp[i + 1], ci, bv, [&](int c) { return (double)z[c]; });
+        w[i] = v;
+        sw[e] = v;
+    }
+    __syncthreads();
+    arn_tile_dots(V, n, j, r0, cnt, sw, 0, Pout, stride);
+}
+
+// h = column sums of Pin (block 0 stores them at hout); w -= V[0..j] h; then the per-tile
+// dots of the new w with V[0..j] (next_self = 0) or with itself (next_self = 1)
+__global__ void __launch_bounds__(256) k_arn_update_dots(int n, const int* __restrict__ dj, double* __restrict__ V,
+                                                         const double* __restrict__ Pin, int nb,
+                                                         double* __restrict__ hout, double* __restrict__ Pout,
+                                                         int stride, int next_self) {
+    pdl_begin();
+    __shared__ double sh[GMRES_MMAX + 1];
+    __shared__ double sw[ARN_TILE];
+    const int j = *dj;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = wid; q <= j; q += nw) {
+        const double hq = arn_colsum(Pin, nb, stride, q, lane);
+        if (lane == 0) {
+            sh[q] = hq;
+            if (blockIdx.x == 0) hout[q] = hq;
+        }
+    }
+    __syncthreads();
+    const int r0 = blockIdx.x * ARN_TILE, cnt = min(ARN_TILE, n - r0);
+    double* w = V + (int64_t)(j + 1) * n;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int i = r0 + e;
+        double sacc = w[i];
+#pragma unroll 8
+        for (int q = 0; q <= j; ++q) sacc -= V[(int64_t)q * n + i] * sh[q];
+        w[i] = sacc;
+        sw[e] = sacc;
+    }
+    __syncthreads();
+    arn_tile_dots(V, n, j, r0, cnt, sw, next_self, Pout, stride);
+}
+
 // Givens update (one thread) fused with v_{j+1} = w / ||w||: every thread forms
 // ||w|| = sqrt(nrm2) itself, so the scaling does not wait for the rotation.
 __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __restrict__ dj, double* __restrict__ st,
-                                 int m) {
+                                 int m, const double* __restrict__ Pn, int nb, int stride) {
     pdl_begin();
-    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX];
+    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX], s_nrm2;
     GmresLayout L(m);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = *dj;
+    if (threadIdx.x < 32) {  // ||w||^2 from the per-tile partial sums
+        const double nn = arn_colsum(Pn, nb, stride, 0, threadIdx.x);
+        if (threadIdx.x == 0) {
+            s_nrm2 = nn;
+            if (blockIdx.x == 0) st[L.nrm2] = nn;
+        }
+    }
+    __syncthreads();
     if (blockIdx.x == 0) {
         // operands staged in shared memory by the block, then the serial rotations
         for (int q = threadIdx.x; q <= j; q += blockDim.x) {
@@ -617,7 +647,7 @@ __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __res
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            const double hn = sqrt(st[L.nrm2]);
+            const double hn = sqrt(s_nrm2);
             col[j + 1] = hn;
             for (int q = 0; q < j; ++q) {
                 const double c = cs[q], s = sn[q];
@@ -641,7 +671,7 @@ __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __res
         for (int q = threadIdx.x; q <= j; q += blockDim.x) st[L.R + q + (int64_t)j * m] = col[q];
     }
     if (i < n) {
-        const double hn = sqrt(st[L.nrm2]);
+        const double hn = sqrt(s_nrm2);
         double* w = V + (int64_t)(j + 1) * n;
         w[i] = hn != 0.0 ? w[i] / hn : 0.0;
     }
@@ -653,20 +683,19 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
                             const T* pinv, double omega, int nu_pre, int nu_post, double* h_est, cudaStream_t s) {
     GmresLayout L(m);
     const unsigned g = blocks_for(n, 256);
-    const int nb = dots_partial_blocks(n);
     const int stride = m + 1;
     BAMG_LAUNCH_PDL(k_v_to_in<T>, g, 256, 0, s, n, V, dj, vin);
     vcycle<T>(lv, pinv, omega, nu_pre, nu_post, s, Z, dj);
-    BAMG_LAUNCH_PDL(k_spmv64_j<T>, g, 256, 0, s, n, B.rp, B.ci, B.v, zout, dj, V);
-    for (int pass = 0; pass < 2; ++pass) {
-        double* h = st + (pass == 0 ? L.h1 : L.h2);
-        BAMG_LAUNCH_PDL(k_dots_partial_j, nb, 256, 0, s, n, V, dj, 0, partial, stride);
-        BAMG_LAUNCH_PDL(k_reduce_cols_j, blocks_for(m + 1, 4), 128, 0, s, nb, dj, 0, stride, partial, h);
-        BAMG_LAUNCH_PDL(k_update_minus_j, g, 256, 0, s, n, V, dj, h);
-    }
-    BAMG_LAUNCH_PDL(k_dots_partial_j, nb, 256, 0, s, n, V, dj, 1, partial, stride);
-    BAMG_LAUNCH_PDL(k_reduce_cols_j, 1, 128, 0, s, nb, dj, 1, stride, partial, st + L.nrm2);
-    BAMG_LAUNCH_PDL(k_givens_scale_j, g, 256, 0, s, n, V, dj, st, m);
+    const int nt = arn_tiles(n);
+    double* Pa = partial;
+    double* Pb = partial + (size_t)nt * stride;
+    BAMG_LAUNCH_PDL(k_arn_spmv_dots<T>, nt, 256, 0, s, n, B.rp, B.ci, B.v, (const T*)zout, (const int*)dj, V, Pa,
+                    stride);
+    BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, (const int*)dj, V, (const double*)Pa, nt, st + L.h1, Pb,
+                    stride, 0);
+    BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, (const int*)dj, V, (const double*)Pb, nt, st + L.h2, Pa,
+                    stride, 1);
+    BAMG_LAUNCH_PDL(k_givens_scale_j, g, 256, 0, s, n, V, (const int*)dj, st, m, (const double*)Pa, nt, stride);
     BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     BAMG_LAUNCH_PDL(k_inc_j, 1, 32, 0, s, dj);
 }

@@ -161,6 +161,7 @@ void spmv_f64_from_f32(const MatView<double>& B, const float* x, double* y, cuda
 void dots(int n, const double* V, int64_t ldv, int nv, const double* w, double* d_h, double* d_partial,
           cudaStream_t s);
 int dots_partial_blocks(int n);
+int arn_tiles(int n);  // row tiles of the fused Arnoldi kernels
 void update_minus(int n, const double* V, int64_t ldv, int nv, const double* d_h, double* w, cudaStream_t s);
 template <typename TZ>
 void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const double* d_y, double* x, cudaStream_t s);

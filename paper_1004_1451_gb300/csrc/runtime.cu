@@ -588,7 +588,8 @@ struct Solver : SolverBase {
         V.ensure((size_t)n * (m + 1));
         Z.ensure((size_t)n * m);
         state.ensure(GL.total);
-        const int pb = std::max(dots_partial_blocks(n) * (m + 1), (int)blocks_for(n, 256) * 4);
+        const int pb = std::max({dots_partial_blocks(n) * (m + 1), (int)blocks_for(n, 256) * 4,
+                                 2 * arn_tiles(n) * (m + 1)});
         partial.ensure(pb);
         x0.ensure(n);
         xw.ensure(n);
