@@ -4,6 +4,7 @@
 // classical Gram-Schmidt dots and updates, Givens rotations, the update x0 + Z y, and
 // the true residual ||B x||_1 / ||x||_1.
 #include <algorithm>
+#include <atomic>
 #include <utility>
 
 #include "gmres_state.cuh"
@@ -149,39 +150,65 @@ struct TailArgs {
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<T> a) {
     pdl_begin();
+    // the vectors of all tail levels live in shared memory: b, x and the work vector per level
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    T* sbuf = reinterpret_cast<T*>(tail_smem);
     const int tid = threadIdx.x;
+    T* sb[TAIL_MAX_LEVELS];
+    T* sx[TAIL_MAX_LEVELS];
+    T* sr[TAIL_MAX_LEVELS];
+    {
+        size_t off = 0;
+        for (int l = 0; l < a.nl; ++l) {
+            const int n = a.lv[l].B.n;
+            sb[l] = sbuf + off;
+            sx[l] = sbuf + off + n;
+            sr[l] = sbuf + off + 2 * (size_t)n;
+            off += 3 * (size_t)n;
+        }
+    }
+    for (int i = tid; i < a.lv[0].B.n; i += blockDim.x) sb[0][i] = a.lv[0].b[i];
+    __syncthreads();
     T* xcur[TAIL_MAX_LEVELS];
     T* xtmp[TAIL_MAX_LEVELS];
+    T* gx = a.lv[0].x;  // global buffer that receives the first tail level's result
+    T* gt = a.lv[0].r;
     for (int l = 0; l + 1 < a.nl; ++l) {
         const VLevel<T>& v = a.lv[l];
         const int n = v.B.n;
-        T* x = v.x;
-        T* t = v.r;
+        T* b = sb[l];
+        T* x = sx[l];
+        T* t = sr[l];
         if (a.nu_pre >= 2) {
             for (int i = tid; i < n; i += blockDim.x) {
-                const T x1 = (a.omega * v.dinv[i]) * v.b[i];
-                x[i] = x1 + (a.omega * v.dinv[i]) * (v.b[i] - row_Bx1(i, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, a.omega));
+                const T x1 = (a.omega * v.dinv[i]) * b[i];
+                x[i] = x1 + (a.omega * v.dinv[i]) * (b[i] - row_Bx1(i, v.B.rp, v.B.ci, v.B.v, v.dinv, b, a.omega));
             }
             __syncthreads();
             for (int k = 2; k < a.nu_pre; ++k) {
                 for (int i = tid; i < n; i += blockDim.x)
-                    t[i] = x[i] + (a.omega * v.dinv[i]) * (v.b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x));
+                    t[i] = x[i] + (a.omega * v.dinv[i]) * (b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x));
                 __syncthreads();
                 T* q = x;
                 x = t;
                 t = q;
+                if (l == 0) {
+                    T* g = gx;
+                    gx = gt;
+                    gt = g;
+                }
             }
         } else if (a.nu_pre == 1) {
-            for (int i = tid; i < n; i += blockDim.x) x[i] = (a.omega * v.dinv[i]) * v.b[i];
+            for (int i = tid; i < n; i += blockDim.x) x[i] = (a.omega * v.dinv[i]) * b[i];
             __syncthreads();
         } else {
             for (int i = tid; i < n; i += blockDim.x) x[i] = T(0);
             __syncthreads();
         }
-        for (int i = tid; i < n; i += blockDim.x) t[i] = v.b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x);
+        for (int i = tid; i < n; i += blockDim.x) t[i] = b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x);
         __syncthreads();
         const int nc = a.lv[l + 1].B.n;
-        T* bc = a.lv[l + 1].b;
+        T* bc = sb[l + 1];
         for (int I = tid; I < nc; I += blockDim.x)
             bc[I] = row_sum<T>(v.qrp[I], v.qrp[I + 1], v.qci, v.qv, [&](int i) { return t[i]; });
         __syncthreads();
@@ -189,22 +216,23 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
         xtmp[l] = t;
     }
     {  // coarsest: x = B_L^+ b, one warp per row as in the grid kernel
-        const VLevel<T>& v = a.lv[a.nl - 1];
-        const int n = v.B.n;
+        const int L = a.nl - 1;
+        const int n = a.lv[L].B.n;
         const int lane = tid & 31;
         for (int row = tid >> 5; row < n; row += blockDim.x >> 5) {
             T sum = T(0);
-            for (int c = lane; c < n; c += 32) sum += a.pinv[(int64_t)row * n + c] * v.b[c];
+            for (int c = lane; c < n; c += 32) sum += a.pinv[(int64_t)row * n + c] * sb[L][c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if (lane == 0) v.x[row] = sum;
+            if (lane == 0) sx[L][row] = sum;
         }
         __syncthreads();
-        xcur[a.nl - 1] = v.x;
+        xcur[L] = sx[L];
     }
     for (int l = a.nl - 2; l >= 0; --l) {
         const VLevel<T>& v = a.lv[l];
         const int n = v.B.n;
+        T* b = sb[l];
         T* x = xcur[l];
         T* t = xtmp[l];
         const T* ec = xcur[l + 1];
@@ -212,14 +240,22 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
         __syncthreads();
         for (int k = 0; k < a.nu_post; ++k) {
             for (int i = tid; i < n; i += blockDim.x)
-                t[i] = x[i] + (a.omega * v.dinv[i]) * (v.b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x));
+                t[i] = x[i] + (a.omega * v.dinv[i]) * (b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x));
             __syncthreads();
             T* q = x;
             x = t;
             t = q;
+            if (l == 0) {
+                T* g = gx;
+                gx = gt;
+                gt = g;
+            }
         }
         xcur[l] = x;
     }
+    // the first tail level's x to the global buffer the grid kernels read it from
+    const T* xf = xcur[0];
+    for (int i = tid; i < a.lv[0].B.n; i += blockDim.x) gx[i] = xf[i];
 }
 
 // The buffer that holds a level's final x after the down and up passes (the sequence of
@@ -281,7 +317,15 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         a.nu_pre = nu_pre;
         a.nu_post = nu_post;
         a.omega = omega;
-        BAMG_LAUNCH_PDL(k_vcycle_tail<T>, 1, TAIL_THREADS, 0, s, a);
+        size_t smem = 0;
+        for (int q = 0; q < a.nl; ++q) smem += 3 * sizeof(T) * (size_t)a.lv[q].B.n;
+        BAMG_REQUIRE(smem <= 96 * 1024, BAMG_EINVAL, "vcycle tail: levels too large for shared memory");
+        static std::atomic<bool> attr{false};  // idempotent; several host threads may get here
+        if (!attr) {
+            BAMG_CK(cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            attr = true;
+        }
+        BAMG_LAUNCH_PDL(k_vcycle_tail<T>, 1, TAIL_THREADS, smem, s, a);
         xcur[l0] = final_x(lv[l0], nu_pre, nu_post, l0 == L);
     } else {
         const int n = lv[L].B.n;
