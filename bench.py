@@ -7,8 +7,8 @@ flexible GMRES.  Inputs are resident in HBM when a step's timing starts; L2 is
 flushed between steps.  Also reported: the same metric end to end from host buffers,
 the plain FP64 method on the same chain, the roofline of the dominant kernel (the V-cycle
 smoother on the finest level), an SpMM HBM probe, the batched form on 512 chains, LS vs
-learned interpolation on a held-out tandem queue of 262,144 states, and the CPU oracle on
-the host cores.
+learned interpolation on a held-out tandem queue of 262,144 states, the 2^20-point
+Delaunay walk, and the CPU oracle on the host cores.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -216,6 +216,7 @@ def run_ours(args):
     probe = spmm_probe(peaks) if not args.no_probe else None
     batch = batch_line(args) if not args.no_batch else None
     learned = learned_line(args) if not args.no_learned else None
+    large = large_line(args) if not args.no_large else None
     cpu = cpu_baseline() if not args.no_cpu else None
     nnz_a = int(ch.nnz)
     out = {
@@ -232,7 +233,7 @@ def run_ours(args):
         "fp64_ms": round(float(np.median(fp64)), 4), "fp64_iterations": st64["iterations"],
         "speedup_mixed_vs_fp64": round(float(np.median(fp64)) / ms, 3),
         "gpu_launches": int(round(launches)),
-        "roofline": roof, "spmm_hbm": probe, "batch": batch, "learned": learned, "cpu_baseline": cpu, "clocks": ck,
+        "roofline": roof, "spmm_hbm": probe, "batch": batch, "learned": learned, "large": large, "cpu_baseline": cpu, "clocks": ck,
     }
     _line(out)
 
@@ -472,6 +473,36 @@ def learned_line(args, train_rows=1 << 20, epochs=10, batch=4096):
     return out
 
 
+LARGE_WORKLOAD = ("Delaunay triangulation of 2^20 points U[0,1]^2 (seed 0), random walk with probability 1/deg; "
+                  "r=16; compatible-relaxation coarsening; mixed")
+
+
+def large_line(args, reps=3):
+    """The 2^20-point Delaunay walk: setup and solve times (CUDA events), iterations,
+    accuracy against the closed form x ~ degree, and the SpMM sweep on its finest level."""
+    import torch
+
+    import paper_1004_1451_gb300 as bamg
+    from workloads import delaunay_walk
+
+    t0 = time.perf_counter()
+    ch = delaunay_walk(1 << 20, 0)
+    gen_s = time.perf_counter() - t0
+    A = (torch.tensor(ch.row_ptr, device="cuda"), torch.tensor(ch.col, device="cuda"),
+         torch.tensor(ch.val, device="cuda"))
+    deg = np.asarray(ch.meta["degree"], dtype=np.float64)
+    xe = deg / deg.sum()
+    s, setup_ms = _timed(lambda: bamg.Solver(*A, r=16, levels=30, precision="mixed", coarsen="cr"), reps)
+    (x, st), solve_ms = _timed(lambda: s.solve(TOL), reps)
+    err = float(np.abs(x.cpu().numpy() - xe).sum())
+    info = s.info()
+    s.close()
+    return {"workload": LARGE_WORKLOAD, "n": ch.n, "nnz_A": int(ch.nnz), "setup_ms": round(setup_ms, 2),
+            "solve_ms": round(solve_ms, 2), "ms": round(setup_ms + solve_ms, 2), "gmres_iterations": st["iterations"],
+            "rel_l1_vs_exact": err, "levels": info["n"], "op_complexity": round(info["op_complexity"], 3),
+            "generation_s": round(gen_s, 1)}
+
+
 def kernel_probe():
     """Only the dominant-kernel timing (for an ncu capture of k_smooth on the finest level)."""
     import torch
@@ -538,9 +569,19 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-interpolation line")
     ap.add_argument("--kernel-probe", action="store_true", help="run only the dominant-kernel timing")
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-interpolation line")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2^20-point Delaunay line")
+    ap.add_argument("--large-only", action="store_true", help="run only the 2^20-point Delaunay line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.large_only:
+        import torch
+
+        import paper_1004_1451_gb300.build as pb
+
+        pb.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        _line(large_line(args))
     elif args.learned_only:
         import torch
 

@@ -4,6 +4,8 @@
 // B_{l+1} = Q B P, T_{l+1} = Q T P (Section 1 step 3, Algorithm 3).
 #include <cfloat>
 
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace bamg {
@@ -349,28 +351,39 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
         fe = nvis;
     }
     if (ovf && defer) return true;  // the second pass redoes this point with a larger list
-    // ---- candidates: coarse points ranked by (depth, coarse index)
+    // ---- candidates: coarse points ranked by (depth, coarse index).  The coarse entries
+    // are compacted to the front of key (and their nodes to the front of vis; the point
+    // itself at vis[0] is no longer needed), then ranked among themselves.
     int ntot = 0;
     for (int q0 = 1; q0 < nvis; q0 += 32) {
         const int q = q0 + lane;
+        int v = -1;
         bool isc = false;
+        unsigned long long kq = 0;
         if (q < nvis) {
-            const int v = vis[q];
+            v = vis[q];
             isc = cf[v] != 0;
-            key[q] = isc ? (((unsigned long long)dist[q] << 32) | (unsigned)cidx[v]) : ~0ull;
+            if (isc) kq = ((unsigned long long)dist[q] << 32) | (unsigned)cidx[v];
         }
-        ntot += __popc(__ballot_sync(0xffffffffu, isc));
+        const unsigned bal = __ballot_sync(0xffffffffu, isc);
+        __syncwarp();  // every lane has read vis[q] before the compacted writes below
+        if (isc) {
+            const int pos = ntot + __popc(bal & ((1u << lane) - 1u));
+            key[pos] = kq;
+            vis[pos] = v;
+        }
+        ntot += __popc(bal);
+        __syncwarp();
     }
-    __syncwarp();
-    for (int q0 = 1; q0 < nvis; q0 += 32) {
+    for (int q0 = 0; q0 < ntot; q0 += 32) {
         const int q = q0 + lane;
-        if (q < nvis && key[q] != ~0ull) {
+        if (q < ntot) {
             const unsigned long long kq = key[q];
             int rank = 0;
-            for (int q2 = 1; q2 < nvis; ++q2) rank += key[q2] < kq;
+            for (int q2 = 0; q2 < ntot; ++q2) rank += key[q2] < kq;
             if (rank < mmax) {
                 cand[rank] = vis[q];
-                cdep[rank] = dist[q];
+                cdep[rank] = (uint8_t)(kq >> 32);
             }
         }
     }
@@ -797,51 +810,61 @@ __global__ void k_gal_compact(int nc, const int32_t* __restrict__ poff, const in
 // lanes enumerate the row's (Q entry, B entry) pairs in order, each writing the products of
 // its pair at their position in the definition order (a warp prefix sum over the pairs'
 // product counts); the (J, position) keys are sorted by a bitonic network and every run of
-// equal J is summed in position order.  Rows with more than GALF_CAP products take the
-// expansion to global memory and a quadratic scan over it.
-constexpr int GALF_WARPS = 2;
-constexpr int GALF_CAP = 1024;
+// equal J is summed in position order.  Rows are handled by a first kernel with room for
+// GAL_CAP_S products per warp (most rows); longer rows go to a list that a second kernel
+// processes with room for GAL_CAP_L products per warp, and beyond that through global
+// memory with a quadratic scan.
+constexpr int GAL_WARPS_S = 4;
+constexpr int GAL_CAP_S = 256;
+constexpr int GAL_CAP_L = 4096;
+constexpr int GAL_BLOCKS_L = 608;
 
 template <typename T>
-__global__ void __launch_bounds__(GALF_WARPS * 32)
-    k_gal_fused(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci, const T* __restrict__ qv,
-                const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
-                const T* __restrict__ tv, const int32_t* __restrict__ pcol, const T* __restrict__ pval,
-                const int32_t* __restrict__ pcnt, int c, const int32_t* __restrict__ poff, int32_t* __restrict__ pJ,
-                T* __restrict__ pvb, T* __restrict__ pvt, int32_t* __restrict__ ucnt, int32_t* __restrict__ uJ,
-                T* __restrict__ ubv, T* __restrict__ utv, uint8_t* __restrict__ head) {
-    extern __shared__ __align__(16) unsigned char galf_smem[];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(galf_smem) + (size_t)wid * GALF_CAP;
-    T* svb = reinterpret_cast<T*>(reinterpret_cast<unsigned long long*>(galf_smem) + (size_t)GALF_WARPS * GALF_CAP) +
-             (size_t)wid * 2 * GALF_CAP;
-    T* svt = svb + GALF_CAP;
-    const int I = blockIdx.x * GALF_WARPS + wid;
-    if (I >= nc) return;
-    const int o = poff[I], np = poff[I + 1] - o;
+struct GalArgs {
+    int nc;
+    const int32_t *qrp, *qci;
+    const T* qv;
+    const int32_t *rp, *ci;
+    const T *bv, *tv;
+    const int32_t* pcol;
+    const T* pval;
+    const int32_t* pcnt;
+    int c;
+    const int32_t* poff;
+    int32_t* pJ;  // global product space (rows beyond the shared capacity)
+    T *pvb, *pvt;
+    int32_t *ucnt, *uJ;
+    T *ubv, *utv;
+    uint8_t* head;
+};
+
+// One coarse row I in one warp.  local: keys/svb/svt in shared memory (np <= capacity),
+// else the products go to the global product space.
+template <typename T>
+__device__ void gal_row(const GalArgs<T>& a, int I, bool local, unsigned long long* keys, T* svb, T* svt) {
+    const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const bool local = np <= GALF_CAP;
-    // ---- enumerate (q, p) pairs; pair f of the row: the f-th B entry over the Q entries
-    const int q0 = qrp[I], q1 = qrp[I + 1];
+    const int o = a.poff[I], np = a.poff[I + 1] - o;
+    const int q0 = a.qrp[I], q1 = a.qrp[I + 1];
     int npairs = 0;
-    for (int q = q0; q < q1; ++q) npairs += rp[qci[q] + 1] - rp[qci[q]];
+    for (int q = q0; q < q1; ++q) npairs += a.rp[a.qci[q] + 1] - a.rp[a.qci[q]];
     int base = 0;
     for (int f0 = 0; f0 < npairs; f0 += 32) {
         const int f = f0 + lane;
         int q = q0, acc = 0, i = -1, p = -1;
         if (f < npairs) {
             for (; q < q1; ++q) {
-                const int ii = qci[q], len = rp[ii + 1] - rp[ii];
+                const int ii = a.qci[q], len = a.rp[ii + 1] - a.rp[ii];
                 if (f < acc + len) {
                     i = ii;
-                    p = rp[ii] + (f - acc);
+                    p = a.rp[ii] + (f - acc);
                     break;
                 }
                 acc += len;
             }
         }
-        const int j = f < npairs ? ci[p] : 0;
-        const int cnt = f < npairs ? pcnt[j] : 0;
+        const int j = f < npairs ? a.ci[p] : 0;
+        const int cnt = f < npairs ? a.pcnt[j] : 0;
         int incl = cnt;  // inclusive warp prefix sum of the product counts
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -850,21 +873,21 @@ __global__ void __launch_bounds__(GALF_WARPS * 32)
         }
         const int pos0 = base + incl - cnt;
         if (f < npairs) {
-            const T qq = qv[q];
-            const T qb = mul_rn(qq, bv[p]);
-            const T qt = tv ? mul_rn(qq, tv[p]) : (j == i ? qq : T(0));
+            const T qq = a.qv[q];
+            const T qb = mul_rn(qq, a.bv[p]);
+            const T qt = a.tv ? mul_rn(qq, a.tv[p]) : (j == i ? qq : T(0));
             for (int sl = 0; sl < cnt; ++sl) {
-                const T pv = pval[(int64_t)j * c + sl];
-                const int J = pcol[(int64_t)j * c + sl];
+                const T pv = a.pval[(int64_t)j * a.c + sl];
+                const int J = a.pcol[(int64_t)j * a.c + sl];
                 const int e = pos0 + sl;
                 if (local) {
                     keys[e] = ((unsigned long long)(unsigned)J << 32) | (unsigned)e;
                     svb[e] = mul_rn(qb, pv);
                     svt[e] = mul_rn(qt, pv);
                 } else {
-                    pJ[o + e] = J;
-                    pvb[o + e] = mul_rn(qb, pv);
-                    pvt[o + e] = mul_rn(qt, pv);
+                    a.pJ[o + e] = J;
+                    a.pvb[o + e] = mul_rn(qb, pv);
+                    a.pvt[o + e] = mul_rn(qt, pv);
                 }
             }
         }
@@ -881,11 +904,11 @@ __global__ void __launch_bounds__(GALF_WARPS * 32)
                 for (int e = lane; e < N; e += 32) {
                     const int pe = e ^ jj;
                     if (pe > e) {
-                        const unsigned long long a = keys[e], b = keys[pe];
+                        const unsigned long long x = keys[e], y = keys[pe];
                         const bool up = (e & k) == 0;
-                        if ((a > b) == up) {
-                            keys[e] = b;
-                            keys[pe] = a;
+                        if ((x > y) == up) {
+                            keys[e] = y;
+                            keys[pe] = x;
                         }
                     }
                 }
@@ -900,55 +923,89 @@ __global__ void __launch_bounds__(GALF_WARPS * 32)
             const unsigned bal = __ballot_sync(0xffffffffu, hd);
             if (hd) {
                 const int rank = ub + __popc(bal & lt);
-                const int pos0 = (int)(keys[e] & 0xffffffffu);
-                T sb = svb[pos0], st = svt[pos0];
+                const int ps = (int)(keys[e] & 0xffffffffu);
+                T sb = svb[ps], st = svt[ps];
                 for (int e2 = e + 1; e2 < np && (unsigned)(keys[e2] >> 32) == Je; ++e2) {
                     const int pos = (int)(keys[e2] & 0xffffffffu);
                     sb = add_rn(sb, svb[pos]);
                     st = add_rn(st, svt[pos]);
                 }
-                uJ[o + rank] = (int32_t)Je;
-                ubv[o + rank] = sb;
-                utv[o + rank] = st;
+                a.uJ[o + rank] = (int32_t)Je;
+                a.ubv[o + rank] = sb;
+                a.utv[o + rank] = st;
             }
             ub += __popc(bal);
         }
-        if (lane == 0) ucnt[I] = ub;
+        if (lane == 0) a.ucnt[I] = ub;
+        __syncwarp();
         return;
     }
-    // ---- long rows: the products are in global memory; quadratic scan
-    __syncwarp();
+    // products in global memory: quadratic scan
     for (int e = lane; e < np; e += 32) {
-        const int Je = pJ[o + e];
+        const int Je = a.pJ[o + e];
         bool hd = true;
         for (int e2 = 0; e2 < e; ++e2)
-            if (pJ[o + e2] == Je) {
+            if (a.pJ[o + e2] == Je) {
                 hd = false;
                 break;
             }
-        head[o + e] = hd ? 1 : 0;
+        a.head[o + e] = hd ? 1 : 0;
     }
     __syncwarp();
     int cntu = 0;
     for (int e = lane; e < np; e += 32) {
-        if (!head[o + e]) continue;
+        if (!a.head[o + e]) continue;
         ++cntu;
-        const int Je = pJ[o + e];
+        const int Je = a.pJ[o + e];
         int rank = 0;
-        for (int e2 = 0; e2 < np; ++e2) rank += (head[o + e2] && pJ[o + e2] < Je);
-        T sb = pvb[o + e], st = pvt[o + e];
+        for (int e2 = 0; e2 < np; ++e2) rank += (a.head[o + e2] && a.pJ[o + e2] < Je);
+        T sb = a.pvb[o + e], st = a.pvt[o + e];
         for (int e2 = e + 1; e2 < np; ++e2)
-            if (pJ[o + e2] == Je) {
-                sb = add_rn(sb, pvb[o + e2]);
-                st = add_rn(st, pvt[o + e2]);
+            if (a.pJ[o + e2] == Je) {
+                sb = add_rn(sb, a.pvb[o + e2]);
+                st = add_rn(st, a.pvt[o + e2]);
             }
-        uJ[o + rank] = Je;
-        ubv[o + rank] = sb;
-        utv[o + rank] = st;
+        a.uJ[o + rank] = Je;
+        a.ubv[o + rank] = sb;
+        a.utv[o + rank] = st;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) cntu += __shfl_xor_sync(0xffffffffu, cntu, off);
-    if (lane == 0) ucnt[I] = cntu;
+    if (lane == 0) a.ucnt[I] = cntu;
+    __syncwarp();
+}
+
+// rows with at most GAL_CAP_S products; the others are appended to `list`
+template <typename T>
+__global__ void __launch_bounds__(GAL_WARPS_S * 32)
+    k_gal_small(const __grid_constant__ GalArgs<T> a, int32_t* __restrict__ list, int* __restrict__ nlist) {
+    __shared__ unsigned long long keys[GAL_WARPS_S][GAL_CAP_S];
+    __shared__ T svb[GAL_WARPS_S][GAL_CAP_S], svt[GAL_WARPS_S][GAL_CAP_S];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int I = blockIdx.x * GAL_WARPS_S + wid;
+    if (I >= a.nc) return;
+    const int np = a.poff[I + 1] - a.poff[I];
+    if (np > GAL_CAP_S) {
+        if (lane == 0) list[atomicAdd(nlist, 1)] = I;
+        return;
+    }
+    gal_row<T>(a, I, true, keys[wid], svb[wid], svt[wid]);
+}
+
+// the listed rows, one warp per block, persistent over the list
+template <typename T>
+__global__ void __launch_bounds__(32) k_gal_large(const __grid_constant__ GalArgs<T> a,
+                                                  const int32_t* __restrict__ list, const int* __restrict__ nlist) {
+    extern __shared__ __align__(16) unsigned char gal_smem[];
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(gal_smem);
+    T* svb = reinterpret_cast<T*>(keys + GAL_CAP_L);
+    T* svt = svb + GAL_CAP_L;
+    const int cnt = *nlist;
+    for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
+        const int I = list[k];
+        const int np = a.poff[I + 1] - a.poff[I];
+        gal_row<T>(a, I, np <= GAL_CAP_L, keys, svb, svt);
+    }
 }
 
 template <typename T>
@@ -964,10 +1021,23 @@ void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int
     TmpBuf<int32_t> pJ(tot, s), uJ(tot, s), ucnt(nc, s);
     TmpBuf<T> pvb(tot, s), pvt(tot, s), ubv(tot, s), utv(tot, s);
     TmpBuf<uint8_t> head(tot, s);
-    const size_t smem = (size_t)GALF_WARPS * GALF_CAP * (sizeof(unsigned long long) + 2 * sizeof(T));
-    BAMG_LAUNCH(k_gal_fused<T>, blocks_for(nc, GALF_WARPS), GALF_WARPS * 32, smem, s, nc, qrp, qci, qv, B.rp, B.ci, B.v,
-                T_val, P.pcol, P.pval, P.pcnt, P.c, poff.get(), pJ.get(), pvb.get(), pvt.get(), ucnt.get(), uJ.get(),
-                ubv.get(), utv.get(), head.get());
+    GalArgs<T> ga{nc,     qrp,    qci, qv,         B.rp,     B.ci,      B.v,       T_val,      P.pcol,   P.pval,
+                  P.pcnt, P.c,    poff.get(), pJ.get(), pvb.get(), pvt.get(), ucnt.get(), uJ.get(), ubv.get(),
+                  utv.get(), head.get()};
+    TmpBuf<int32_t> list(nc, s);
+    TmpBuf<int> nlist(1, s);
+    BAMG_CK(cudaMemsetAsync(nlist.get(), 0, sizeof(int), s));
+    BAMG_LAUNCH(k_gal_small<T>, blocks_for(nc, GAL_WARPS_S), GAL_WARPS_S * 32, 0, s, ga, list.get(), nlist.get());
+    const size_t smem_l = (size_t)GAL_CAP_L * (sizeof(unsigned long long) + 2 * sizeof(T));
+    static std::atomic<bool> attr{false};  // idempotent; several host threads may get here
+    if (!attr) {
+        BAMG_CK(cudaFuncSetAttribute(k_gal_large<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(GAL_CAP_L * (sizeof(unsigned long long) + 2 * sizeof(float)))));
+        BAMG_CK(cudaFuncSetAttribute(k_gal_large<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(GAL_CAP_L * (sizeof(unsigned long long) + 2 * sizeof(double)))));
+        attr = true;
+    }
+    BAMG_LAUNCH(k_gal_large<T>, GAL_BLOCKS_L, 32, smem_l, s, ga, (const int32_t*)list.get(), (const int*)nlist.get());
     out.rp.alloc(nc + 1);
     exclusive_scan(ucnt.get(), out.rp.get(), nc, s);
     out.nnz = read_int(out.rp.get() + nc, s);

@@ -582,28 +582,35 @@ __global__ void k_inc_j(int* dj) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dj += 1;
 }
 
-// Fused Arnoldi kernels over tiles of ARN_TILE rows (one block each).  The column sums of
-// the per-tile dot products are formed again by every block that needs them (warp per
-// column, lanes strided over the tiles, the same order in every block), so the reductions
-// need no kernel of their own.
-constexpr int ARN_TILE = 256;
-int arn_tiles(int n) { return (int)blocks_for(n, ARN_TILE); }
+// Fused Arnoldi kernels over row tiles (one block each).  The column sums of the per-tile
+// dot products are formed again by every block that needs them (warp per column, lanes
+// strided over the tiles, the same order in every block), so the reductions need no kernel
+// of their own; the tile grows with n so that there are at most ARN_MAX_TILES of them.
+constexpr int ARN_MIN_TILE = 256;
+constexpr int ARN_MAX_TILES = 256;
+int arn_tile_rows(int n) {
+    const int64_t t = ((int64_t)n + ARN_MAX_TILES - 1) / ARN_MAX_TILES;
+    return (int)std::max<int64_t>(ARN_MIN_TILE, (t + ARN_MIN_TILE - 1) / ARN_MIN_TILE * ARN_MIN_TILE);
+}
+int arn_tiles(int n) { return (int)blocks_for(n, arn_tile_rows(n)); }
 
 __device__ __forceinline__ double arn_colsum(const double* __restrict__ P, int nb, int stride, int q, int lane) {
     double s = 0.0;
     for (int b = lane; b < nb; b += 32) s += P[(int64_t)b * stride + q];
     return warp_sum(s);
 }
-// per-tile dots of the tile's w (in shared memory) with V[0..j] (self = 0) or with itself
+// per-tile dots of the tile's rows of w with V[0..j] (self = 0) or with itself; the block
+// has just written w, so these reads hit the caches
 __device__ __forceinline__ void arn_tile_dots(const double* __restrict__ V, int n, int j, int r0, int cnt,
-                                              const double* sw, int self, double* __restrict__ Pout, int stride) {
+                                              const double* w, int self, double* __restrict__ Pout, int stride) {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int nv = self ? 1 : j + 1;
+    const double* wt = w + r0;
     for (int q = wid; q < nv; q += nw) {
-        const double* vq = self ? sw : V + (int64_t)q * n + r0;
+        const double* vq = self ? wt : V + (int64_t)q * n + r0;
         double acc = 0.0;
 #pragma unroll 4
-        for (int e = lane; e < cnt; e += 32) acc += vq[e] * sw[e];
+        for (int e = lane; e < cnt; e += 32) acc += vq[e] * wt[e];
         acc = warp_sum(acc);
         if (lane == 0) Pout[(int64_t)blockIdx.x * stride + q] = acc;
     }
@@ -611,34 +618,30 @@ __device__ __forceinline__ void arn_tile_dots(const double* __restrict__ V, int 
 
 // w = V[j+1] = B z_j (FP64) and its per-tile dots with V[0..j]
 template <typename TX>
-__global__ void __launch_bounds__(256) k_arn_spmv_dots(int n, const int32_t* __restrict__ rp,
+__global__ void __launch_bounds__(256) k_arn_spmv_dots(int n, int tile, const int32_t* __restrict__ rp,
                                                        const int32_t* __restrict__ ci, const double* __restrict__ bv,
                                                        const TX* __restrict__ z, const int* __restrict__ dj,
                                                        double* __restrict__ V, double* __restrict__ Pout, int stride) {
     pdl_begin();
-    __shared__ double sw[ARN_TILE];
     const int j = *dj;
-    const int r0 = blockIdx.x * ARN_TILE, cnt = min(ARN_TILE, n - r0);
+    const int r0 = blockIdx.x * tile, cnt = min(tile, n - r0);
     double* w = V + (int64_t)(j + 1) * n;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         const int i = r0 + e;
-        const double v = row_sum<double>(rp[i], rp[i + 1], ci, bv, [&](int c) { return (double)z[c]; });
-        w[i] = v;
-        sw[e] = v;
+        w[i] = row_sum<double>(rp[i], rp[i + 1], ci, bv, [&](int c) { return (double)z[c]; });
     }
     __syncthreads();
-    arn_tile_dots(V, n, j, r0, cnt, sw, 0, Pout, stride);
+    arn_tile_dots(V, n, j, r0, cnt, w, 0, Pout, stride);
 }
 
 // h = column sums of Pin (block 0 stores them at hout); w -= V[0..j] h; then the per-tile
 // dots of the new w with V[0..j] (next_self = 0) or with itself (next_self = 1)
-__global__ void __launch_bounds__(256) k_arn_update_dots(int n, const int* __restrict__ dj, double* __restrict__ V,
-                                                         const double* __restrict__ Pin, int nb,
-                                                         double* __restrict__ hout, double* __restrict__ Pout,
+__global__ void __launch_bounds__(256) k_arn_update_dots(int n, int tile, const int* __restrict__ dj,
+                                                         double* __restrict__ V, const double* __restrict__ Pin,
+                                                         int nb, double* __restrict__ hout, double* __restrict__ Pout,
                                                          int stride, int next_self) {
     pdl_begin();
     __shared__ double sh[GMRES_MMAX + 1];
-    __shared__ double sw[ARN_TILE];
     const int j = *dj;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int q = wid; q <= j; q += nw) {
@@ -649,7 +652,7 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(int n, const int* __res
         }
     }
     __syncthreads();
-    const int r0 = blockIdx.x * ARN_TILE, cnt = min(ARN_TILE, n - r0);
+    const int r0 = blockIdx.x * tile, cnt = min(tile, n - r0);
     double* w = V + (int64_t)(j + 1) * n;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         const int i = r0 + e;
@@ -657,10 +660,9 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(int n, const int* __res
 #pragma unroll 8
         for (int q = 0; q <= j; ++q) sacc -= V[(int64_t)q * n + i] * sh[q];
         w[i] = sacc;
-        sw[e] = sacc;
     }
     __syncthreads();
-    arn_tile_dots(V, n, j, r0, cnt, sw, next_self, Pout, stride);
+    arn_tile_dots(V, n, j, r0, cnt, w, next_self, Pout, stride);
 }
 
 // Givens update (one thread) fused with v_{j+1} = w / ||w||: every thread forms
@@ -730,15 +732,15 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
     const int stride = m + 1;
     BAMG_LAUNCH_PDL(k_v_to_in<T>, g, 256, 0, s, n, V, dj, vin);
     vcycle<T>(lv, pinv, omega, nu_pre, nu_post, s, Z, dj);
-    const int nt = arn_tiles(n);
+    const int tile = arn_tile_rows(n), nt = arn_tiles(n);
     double* Pa = partial;
     double* Pb = partial + (size_t)nt * stride;
-    BAMG_LAUNCH_PDL(k_arn_spmv_dots<T>, nt, 256, 0, s, n, B.rp, B.ci, B.v, (const T*)zout, (const int*)dj, V, Pa,
-                    stride);
-    BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, (const int*)dj, V, (const double*)Pa, nt, st + L.h1, Pb,
-                    stride, 0);
-    BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, (const int*)dj, V, (const double*)Pb, nt, st + L.h2, Pa,
-                    stride, 1);
+    BAMG_LAUNCH_PDL(k_arn_spmv_dots<T>, nt, 256, 0, s, n, tile, B.rp, B.ci, B.v, (const T*)zout, (const int*)dj, V,
+                    Pa, stride);
+    BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pa, nt, st + L.h1,
+                    Pb, stride, 0);
+    BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pb, nt, st + L.h2,
+                    Pa, stride, 1);
     BAMG_LAUNCH_PDL(k_givens_scale_j, g, 256, 0, s, n, V, (const int*)dj, st, m, (const double*)Pa, nt, stride);
     BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     BAMG_LAUNCH_PDL(k_inc_j, 1, 32, 0, s, dj);
