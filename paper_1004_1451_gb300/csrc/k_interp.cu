@@ -812,11 +812,10 @@ __global__ void k_gal_compact(int nc, const int32_t* __restrict__ poff, const in
 // product counts); the (J, position) keys are sorted by a bitonic network and every run of
 // equal J is summed in position order.  Rows are handled by a first kernel with room for
 // GAL_CAP_S products per warp (most rows); longer rows go to a list that a second kernel
-// processes with room for GAL_CAP_L products per warp, and beyond that through global
-// memory with a quadratic scan.
+// accumulates in a hash table (below), and beyond its capacity through global memory
+// with a quadratic scan.
 constexpr int GAL_WARPS_S = 4;
 constexpr int GAL_CAP_S = 256;
-constexpr int GAL_CAP_L = 4096;
 constexpr int GAL_BLOCKS_L = 608;
 
 template <typename T>
@@ -992,19 +991,168 @@ __global__ void __launch_bounds__(GAL_WARPS_S * 32)
     gal_row<T>(a, I, true, keys[wid], svb[wid], svt[wid]);
 }
 
+// Long rows by accumulation instead of sorting: the products of each batch of 32 (Q, B)
+// pairs are staged in definition order in shared memory; chunks of 32 staged products
+// then find or claim their J in an open-addressing table (GAL_HSLOTS slots), the lanes
+// that share a J in a chunk are summed by the lowest one in lane order, so every J
+// accumulates its products in definition order.  The table's entries are finally sorted
+// by J.  A row with more distinct J than half the table goes to the quadratic scan.
+constexpr int GAL_HSLOTS = 2048;
+constexpr int GAL_STAGE = 32 * 4;  // products of one batch of pairs (caliber <= 4)
+
+template <typename T>
+__device__ bool gal_row_hash(const GalArgs<T>& a, int I, int* hkey, T* hvb, T* hvt, int* sJ, T* sb_, T* st_,
+                             unsigned long long* skeys) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int o = a.poff[I];
+    for (int e = lane; e < GAL_HSLOTS; e += 32) {
+        hkey[e] = -1;
+        hvb[e] = T(0);
+        hvt[e] = T(0);
+    }
+    __syncwarp();
+    const int q0 = a.qrp[I], q1 = a.qrp[I + 1];
+    int npairs = 0;
+    for (int q = q0; q < q1; ++q) npairs += a.rp[a.qci[q] + 1] - a.rp[a.qci[q]];
+    int used = 0;  // claimed slots
+    for (int f0 = 0; f0 < npairs; f0 += 32) {
+        const int f = f0 + lane;
+        int q = q0, acc = 0, i = -1, p = -1;
+        if (f < npairs) {
+            for (; q < q1; ++q) {
+                const int ii = a.qci[q], len = a.rp[ii + 1] - a.rp[ii];
+                if (f < acc + len) {
+                    i = ii;
+                    p = a.rp[ii] + (f - acc);
+                    break;
+                }
+                acc += len;
+            }
+        }
+        const int j = f < npairs ? a.ci[p] : 0;
+        const int cnt = f < npairs ? a.pcnt[j] : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int pos0 = incl - cnt, nb = __shfl_sync(0xffffffffu, incl, 31);
+        if (f < npairs) {  // stage this batch's products in definition order
+            const T qq = a.qv[q];
+            const T qb = mul_rn(qq, a.bv[p]);
+            const T qt = a.tv ? mul_rn(qq, a.tv[p]) : (j == i ? qq : T(0));
+            for (int sl = 0; sl < cnt; ++sl) {
+                const T pv = a.pval[(int64_t)j * a.c + sl];
+                sJ[pos0 + sl] = a.pcol[(int64_t)j * a.c + sl];
+                sb_[pos0 + sl] = mul_rn(qb, pv);
+                st_[pos0 + sl] = mul_rn(qt, pv);
+            }
+        }
+        __syncwarp();
+        for (int e0 = 0; e0 < nb; e0 += 32) {
+            const int e = e0 + lane;
+            const int J = e < nb ? sJ[e] : -1 - lane;
+            const unsigned grp = __match_any_sync(0xffffffffu, J);
+            const bool leader = e < nb && (grp & lt) == 0u;
+            bool claimed = false;
+            if (leader) {
+                // find or claim the slot of J (linear probing)
+                unsigned h = ((unsigned)J * 2654435761u) & (GAL_HSLOTS - 1);
+                int slot = -1;
+                for (int probe = 0; probe < GAL_HSLOTS; ++probe) {
+                    const int k = hkey[h];
+                    if (k == J) {
+                        slot = (int)h;
+                        break;
+                    }
+                    if (k == -1) {
+                        const int prev = atomicCAS(&hkey[h], -1, J);
+                        if (prev == -1 || prev == J) {
+                            slot = (int)h;
+                            claimed = prev == -1;
+                            break;
+                        }
+                    }
+                    h = (h + 1) & (GAL_HSLOTS - 1);
+                }
+                if (slot >= 0) {
+                    T vb = hvb[slot], vt = hvt[slot];
+                    unsigned m = grp;
+                    while (m) {  // the group's products in lane (= definition) order
+                        const int l2 = __ffs(m) - 1;
+                        m &= m - 1;
+                        vb = add_rn(vb, sb_[e0 + l2]);
+                        vt = add_rn(vt, st_[e0 + l2]);
+                    }
+                    hvb[slot] = vb;
+                    hvt[slot] = vt;
+                }
+            }
+            used += __popc(__ballot_sync(0xffffffffu, claimed));
+            __syncwarp();
+        }
+        if (used > GAL_HSLOTS / 2) return false;  // too many distinct J: quadratic fallback
+    }
+    // compact the occupied slots, sort by J, write the row
+    int u = 0;
+    for (int e0 = 0; e0 < GAL_HSLOTS; e0 += 32) {
+        const int e = e0 + lane;
+        const bool occ = hkey[e] >= 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, occ);
+        if (occ) skeys[u + __popc(bal & lt)] = ((unsigned long long)(unsigned)hkey[e] << 32) | (unsigned)e;
+        u += __popc(bal);
+    }
+    __syncwarp();
+    int N = 32;
+    while (N < u) N <<= 1;
+    for (int e = u + lane; e < N; e += 32) skeys[e] = ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int e = lane; e < N; e += 32) {
+                const int pe = e ^ jj;
+                if (pe > e) {
+                    const unsigned long long x = skeys[e], y = skeys[pe];
+                    const bool up = (e & k) == 0;
+                    if ((x > y) == up) {
+                        skeys[e] = y;
+                        skeys[pe] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    for (int e = lane; e < u; e += 32) {
+        const unsigned long long kk = skeys[e];
+        const int slot = (int)(kk & 0xffffffffu);
+        a.uJ[o + e] = (int32_t)(kk >> 32);
+        a.ubv[o + e] = hvb[slot];
+        a.utv[o + e] = hvt[slot];
+    }
+    if (lane == 0) a.ucnt[I] = u;
+    __syncwarp();
+    return true;
+}
+
 // the listed rows, one warp per block, persistent over the list
 template <typename T>
 __global__ void __launch_bounds__(32) k_gal_large(const __grid_constant__ GalArgs<T> a,
                                                   const int32_t* __restrict__ list, const int* __restrict__ nlist) {
     extern __shared__ __align__(16) unsigned char gal_smem[];
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(gal_smem);
-    T* svb = reinterpret_cast<T*>(keys + GAL_CAP_L);
-    T* svt = svb + GAL_CAP_L;
+    unsigned long long* skeys = reinterpret_cast<unsigned long long*>(gal_smem);  // GAL_HSLOTS
+    T* hvb = reinterpret_cast<T*>(skeys + GAL_HSLOTS);
+    T* hvt = hvb + GAL_HSLOTS;
+    T* sb_ = hvt + GAL_HSLOTS;
+    T* st_ = sb_ + GAL_STAGE;
+    int* hkey = reinterpret_cast<int*>(st_ + GAL_STAGE);
+    int* sJ = hkey + GAL_HSLOTS;
     const int cnt = *nlist;
     for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
         const int I = list[k];
-        const int np = a.poff[I + 1] - a.poff[I];
-        gal_row<T>(a, I, np <= GAL_CAP_L, keys, svb, svt);
+        if (!gal_row_hash<T>(a, I, hkey, hvb, hvt, sJ, sb_, st_, skeys)) gal_row<T>(a, I, false, nullptr, nullptr, nullptr);
     }
 }
 
@@ -1028,13 +1176,16 @@ void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int
     TmpBuf<int> nlist(1, s);
     BAMG_CK(cudaMemsetAsync(nlist.get(), 0, sizeof(int), s));
     BAMG_LAUNCH(k_gal_small<T>, blocks_for(nc, GAL_WARPS_S), GAL_WARPS_S * 32, 0, s, ga, list.get(), nlist.get());
-    const size_t smem_l = (size_t)GAL_CAP_L * (sizeof(unsigned long long) + 2 * sizeof(T));
+    auto large_smem = [](size_t tb) {
+        return (size_t)GAL_HSLOTS * (sizeof(unsigned long long) + 2 * tb + sizeof(int)) + GAL_STAGE * (2 * tb + sizeof(int));
+    };
+    const size_t smem_l = large_smem(sizeof(T));
     static std::atomic<bool> attr{false};  // idempotent; several host threads may get here
     if (!attr) {
         BAMG_CK(cudaFuncSetAttribute(k_gal_large<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(GAL_CAP_L * (sizeof(unsigned long long) + 2 * sizeof(float)))));
+                                     (int)large_smem(sizeof(float))));
         BAMG_CK(cudaFuncSetAttribute(k_gal_large<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(GAL_CAP_L * (sizeof(unsigned long long) + 2 * sizeof(double)))));
+                                     (int)large_smem(sizeof(double))));
         attr = true;
     }
     BAMG_LAUNCH(k_gal_large<T>, GAL_BLOCKS_L, 32, smem_l, s, ga, (const int32_t*)list.get(), (const int*)nlist.get());

@@ -235,6 +235,48 @@ def test_galerkin_bit_exact(with_T):
     assert np.array_equal(Tg, Tc.toarray())
 
 
+@pytest.mark.parametrize("nq,dense", [(40, 12), (400, 60), (1200, 120)])
+def test_galerkin_long_rows_bit_exact(nq, dense):
+    # coarse rows of a few hundred to several thousand products (the shared-memory table
+    # path), and with more distinct columns than the table takes (the global fallback);
+    # caliber 4, random signs
+    torch = _torch()
+    rng = np.random.default_rng(nq + dense)
+    n = 4 * nq
+    rows = np.repeat(np.arange(n), dense)
+    cols = rng.integers(0, n, n * dense)
+    B = sp.csr_matrix((rng.uniform(-1, 1, n * dense), (rows, cols)), shape=(n, n))
+    B = B + sp.identity(n) * 3.0
+    B = sp.csr_matrix(B)
+    B.sort_indices()
+    cf = np.zeros(n, dtype=bool)
+    cf[rng.choice(n, nq, replace=False)] = True
+    cidx = np.full(n, -1)
+    cidx[cf] = np.arange(nq)
+    pr, pc, pv = [], [], []
+    for i in range(n):
+        if cf[i]:
+            pr.append(i), pc.append(cidx[i]), pv.append(1.0)
+        else:
+            for J in np.sort(rng.choice(nq, 4, replace=False)):
+                pr.append(i), pc.append(J), pv.append(rng.uniform(-0.5, 1.0))
+    P = sp.csr_matrix((pv, (pr, pc)), shape=(n, nq))
+    P.sort_indices()
+    Q = ob.averaging_restriction(P)
+    Tm = sp.csr_matrix(B, copy=True)
+    Tm.data = rng.uniform(0.0, 1.0, Tm.nnz)
+    Bc = ob.galerkin(Q, B, P)
+    Tc = ob.galerkin(Q, Tm, P)
+    pcol, pval, pcnt = ell_from_csr(P, 4)
+    rp, ci, bv, tv = _bamg().galerkin(dev_csr(B), torch.tensor(Tm.data.copy(), device="cuda"), nq,
+                                      torch.tensor(pcol, device="cuda"), torch.tensor(pval, device="cuda"),
+                                      torch.tensor(pcnt, device="cuda"), 4)
+    rp, ci, bv, tv = rp.cpu().numpy(), ci.cpu().numpy(), bv.cpu().numpy(), tv.cpu().numpy()
+    assert np.array_equal(rp, Bc.indptr) and np.array_equal(ci, Bc.indices)
+    assert np.array_equal(bv, Bc.data)
+    assert np.array_equal(sp.csr_matrix((tv, ci, rp), shape=(nq, nq)).toarray(), Tc.toarray())
+
+
 # ------------------------------------------------------------------ coarsest level
 def _coarse_pair():
     ch = grid_walk(33)
