@@ -264,13 +264,31 @@ __device__ void learned_features(int i, int lane, int node, int ncand, int depth
 // normal equations (plus the Tikhonov term), solves them by Cholesky and evaluates the
 // functional of Eq. (3.6) directly; the lane with the smallest value (lowest slot on
 // ties) joins J.
+// Visited set of a neighbourhood search: open addressing over 2 CAP slots (load <= 1/2),
+// keys are node indices, -1 = empty.
+__device__ __forceinline__ unsigned vis_hash(int v, int nslots) { return ((unsigned)v * 2654435761u) & (nslots - 1); }
+__device__ __forceinline__ bool vis_contains(const int* hs, int nslots, int v) {
+    for (unsigned h = vis_hash(v, nslots);; h = (h + 1) & (nslots - 1)) {
+        const int k = hs[h];
+        if (k == v) return true;
+        if (k == -1) return false;
+    }
+}
+__device__ __forceinline__ void vis_insert(int* hs, int nslots, int v) {
+    for (unsigned h = vis_hash(v, nslots);; h = (h + 1) & (nslots - 1)) {
+        const int prev = atomicCAS(&hs[h], -1, v);
+        if (prev == -1 || prev == v) return;
+    }
+}
+
 template <typename T, int CAP, bool EXTRA>
 __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const T* __restrict__ bv, const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx, const T* __restrict__ X,
                          int ncols, int ld, const T* s_w, int z, int mmax, int c, double ridge,
                          int32_t* __restrict__ pcol, T* __restrict__ pval, int32_t* __restrict__ pcnt, int* vis,
                          unsigned long long* key, uint8_t* dist, int* cand, uint8_t* cdep, T* xi, T (*xj)[KMAX],
-                         bool defer, const LsOut& ex) {
+                         int* hs, bool defer, const LsOut& ex) {
+    constexpr int HS = 2 * CAP;  // visited-set slots
     const int lane = threadIdx.x & 31;
     const int64_t prow = (int64_t)i * c;
     if (cf[i]) {
@@ -289,9 +307,12 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
     }
     // ---- neighbourhood search (Eq. (3.5))
     __syncwarp();
+    for (int e = lane; e < HS; e += 32) hs[e] = -1;
+    __syncwarp();
     if (lane == 0) {
         vis[0] = i;
         dist[0] = 0;
+        vis_insert(hs, HS, i);
     }
     __syncwarp();
     int nvis = 1, fs = 0, fe = 1, ncvis = 0;
@@ -307,13 +328,7 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
             for (int base = p0; base < p1; base += 32) {
                 const int p = base + lane;
                 const int v = p < p1 ? ci[p] : -1;
-                bool isnew = v >= 0;
-                if (isnew)
-                    for (int q = 0; q < nvis; ++q)
-                        if (vis[q] == v) {
-                            isnew = false;
-                            break;
-                        }
+                const bool isnew = v >= 0 && !vis_contains(hs, HS, v);
                 const int key = isnew ? v : -1 - lane;
                 const unsigned grp = __match_any_sync(0xffffffffu, key);
                 const unsigned lt = (1u << lane) - 1u;
@@ -328,6 +343,7 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
                 if (rec && pos < CAP) {
                     vis[pos] = v;
                     dist[pos] = (uint8_t)d;
+                    vis_insert(hs, HS, v);
                 }
                 int added = __popc(bal);
                 if (nvis + added > CAP) {
@@ -545,6 +561,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     __shared__ uint8_t s_dist[WARPS][CAP];
     __shared__ int s_cand[WARPS][MMAX];
     __shared__ uint8_t s_cdep[WARPS][MMAX];
+    __shared__ int s_hash[WARPS][2 * CAP];
     __shared__ T s_xi[WARPS][KMAX];
     __shared__ T s_xj[WARPS][CMAX][KMAX];
     __shared__ T s_w[KMAX];
@@ -556,7 +573,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         if (i >= n) return;
         const bool ovf = ls_point<T, CAP, EXTRA>(i, rp, ci, bv, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol, pval,
                                           pcnt, s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_cdep[wid],
-                                          s_xi[wid], s_xj[wid], ovf_list != nullptr, ex);
+                                          s_xi[wid], s_xj[wid], s_hash[wid], ovf_list != nullptr, ex);
         if (ovf && lane == 0) {
             if (ovf_list)
                 ovf_list[atomicAdd(ovf_count, 1)] = i;
@@ -569,7 +586,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     for (int k = blockIdx.x * WARPS + wid; k < cnt; k += gridDim.x * WARPS) {
         const bool ovf = ls_point<T, CAP, EXTRA>(list[k], rp, ci, bv, cf, cidx, X, ncols, ld, s_w, z, mmax, c, ridge, pcol,
                                           pval, pcnt, s_vis[wid], s_key[wid], s_dist[wid], s_cand[wid], s_cdep[wid],
-                                          s_xi[wid], s_xj[wid], false, ex);
+                                          s_xi[wid], s_xj[wid], s_hash[wid], false, ex);
         if (ovf && lane == 0) atomicOr(err, 1);
     }
 }
