@@ -132,11 +132,11 @@ __global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b, T* __r
 
 // The coarse end of the cycle in one block: every level from the first one with at most
 // TAIL_MAX_N rows and TAIL_MAX_NNZ entries down to the coarsest solve and back up, with
-// block barriers between the phases instead of kernel boundaries (the levels are too small to fill the GPU, and
-// each launch would cost more than its work).  Same per-row arithmetic and buffer
-// sequence as the grid kernels, so the result is identical.
+// block barriers between the phases instead of kernel boundaries (the levels are too
+// small to fill the GPU, and each launch would cost more than its work).  Same per-row
+// arithmetic and buffer sequence as the grid kernels, so the result is identical.
 constexpr int TAIL_MAX_N = 1024;
-constexpr int TAIL_MAX_NNZ = 16384;  // the tail's rows are walked serially per thread: dense levels stay on the grid
+constexpr int TAIL_MAX_NNZ = 16384;  // rows are walked serially per thread: dense levels stay on the grid
 constexpr int TAIL_THREADS = 512;
 constexpr int TAIL_MAX_LEVELS = 12;
 template <typename T>
