@@ -149,7 +149,7 @@ def run_ours(args):
         dist.barrier()
     clocks = Clocks()
     clocks.start()
-    times, iters, split = [], [], []
+    times, iters, split, waits = [], [], [], []
     l0 = bamg.launch_count()
     for _ in range(args.steps):
         flush.fill_(1)
@@ -162,6 +162,7 @@ def run_ours(args):
         times.append(e0.elapsed_time(e1))
         iters.append(st["iterations"])
         split.append((st["setup_ms"], st["solve_ms"]))
+        waits.append(st["host_waits"])
         s.close()
     launches = (bamg.launch_count() - l0) / args.steps
     torch.cuda.synchronize()
@@ -169,7 +170,8 @@ def run_ours(args):
     if args.only_step:
         if rank == 0:
             _line({"metric": METRIC, "value": round(float(np.mean(times)), 4), "unit": "ms",
-                   "gmres_iterations": int(np.median(iters)), "gpu_launches": int(round(launches)), "only_step": True})
+                   "gmres_iterations": int(np.median(iters)), "host_waits_in_solve": int(np.median(waits)),
+                   "gpu_launches": int(round(launches)), "only_step": True})
         return
     ms = max_over_ranks(float(np.sum(times)) / args.steps, dev)
     if ws > 1:
@@ -225,7 +227,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": ch.n, "nnz_A": nnz_a, "r": R, "tol": TOL,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
-        "gmres_iterations": int(np.median(iters)), "rel_l1_vs_exact": err,
+        "gmres_iterations": int(np.median(iters)), "host_waits_in_solve": int(np.median(waits)),
+        "rel_l1_vs_exact": err,
         "host_setup_ms": round(float(np.median([a for a, b in split])), 3),
         "host_solve_ms": round(float(np.median([b for a, b in split])), 3),
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 4 * (ch.n + 1) + 12 * nnz_a,

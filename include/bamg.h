@@ -104,6 +104,9 @@ typedef struct {
     const bamg_model* model; /* the MLP for BAMG_INTERP_LEARNED (caller keeps ownership) */
     double learned_rho_max; /* > 0: fall back to least squares when the learned hierarchy's
                                V-cycle factor (bamg_vcycle_factor, 20 steps) exceeds this */
+    int32_t device_loop;    /* 1 (default): between true-residual checks the Arnoldi steps run in a
+                               device-side loop (a CUDA graph WHILE node, one host wait per check);
+                               0: one graph launch and one host wait per step.  Same iterates. */
 } bamg_opts;
 
 enum { BAMG_INTERP_LS = 0, BAMG_INTERP_LEARNED = 1 };
@@ -116,6 +119,8 @@ typedef struct {
     double residual_l1;   /* ||B x||_1 / ||x||_1 of the returned x */
     double setup_ms;      /* wall time of bamg_setup */
     double solve_ms;      /* wall time of this bamg_solve */
+    int32_t host_waits;   /* host synchronisations on Arnoldi steps: one per step, or one per
+                             estimate-triggered check where the steps loop on the device */
 } bamg_stats;
 
 typedef struct bamg_handle bamg_handle;

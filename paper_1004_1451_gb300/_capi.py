@@ -42,13 +42,14 @@ class Opts(C.Structure):
                 ("ridge", C.c_double), ("ridge32", C.c_double), ("weight_floor", C.c_double),
                 ("cr_theta", C.c_double), ("cr_nu", C.c_int32), ("cr_max_rounds", C.c_int32),
                 ("cr_omega", C.c_double), ("stream", C.c_void_p), ("interp", C.c_int32), ("learned_refit", C.c_int32),
-                ("model", C.c_void_p), ("learned_rho_max", C.c_double)]
+                ("model", C.c_void_p), ("learned_rho_max", C.c_double),
+                ("device_loop", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("restarts", C.c_int32),
                 ("true_checks", C.c_int32), ("residual_l1", C.c_double), ("setup_ms", C.c_double),
-                ("solve_ms", C.c_double)]
+                ("solve_ms", C.c_double), ("host_waits", C.c_int32)]
 
 
 class LevelIn(C.Structure):

@@ -135,24 +135,115 @@ __global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b, T* __r
 // block barriers between the phases instead of kernel boundaries (the levels are too
 // small to fill the GPU, and each launch would cost more than its work).  Same per-row
 // arithmetic and buffer sequence as the grid kernels, so the result is identical.
+// The vectors of the tail levels live in shared memory, and so do the levels' matrices
+// (B, D^{-1}, P, Q) and B_L^+ as far as they fit: they are copied in with cp.async at
+// the start, before the wait on the preceding kernel (they do not change during a
+// solve), so every later row walk reads shared memory instead of L2.
 constexpr int TAIL_MAX_N = 1024;
 constexpr int TAIL_MAX_NNZ = 16384;  // rows are walked serially per thread: dense levels stay on the grid
 constexpr int TAIL_THREADS = 512;
 constexpr int TAIL_MAX_LEVELS = 12;
+constexpr int TAIL_SMEM = 227 * 1024;  // the opt-in maximum per block
 template <typename T>
 struct TailArgs {
     VLevel<T> lv[TAIL_MAX_LEVELS];
+    int32_t soff[TAIL_MAX_LEVELS];  // byte offset of the level's staged matrices, -1: read from global
+    int32_t pinv_off = -1;          // byte offset of the staged B_L^+, -1: read from global
     int nl = 0;  // levels in the tail; the last one is the coarsest
     const T* pinv = nullptr;
     int nu_pre = 0, nu_post = 0;
     T omega = T(0);
 };
 
+__host__ __device__ constexpr size_t al16(size_t b) { return (b + 15) & ~size_t(15); }
+// Byte offsets of one non-coarsest level's arrays within its staged block; every array
+// starts on a 16-byte boundary.
+template <typename T>
+struct TailLayout {
+    size_t rp, ci, v, dinv, pcol, pval, pcnt, qrp, qci, qv, end;
+    __host__ __device__ TailLayout(const VLevel<T>& L, int nc) {
+        const size_t n = (size_t)L.B.n, nnz = (size_t)L.B.nnz, nP = n * (size_t)L.P.c, nq = (size_t)L.qnnz;
+        rp = 0;
+        ci = rp + al16(4 * (n + 1));
+        v = ci + al16(4 * nnz);
+        dinv = v + al16(sizeof(T) * nnz);
+        pcol = dinv + al16(sizeof(T) * n);
+        pval = pcol + al16(4 * nP);
+        pcnt = pval + al16(sizeof(T) * nP);
+        qrp = pcnt + al16(4 * n);
+        qci = qrp + al16(4 * ((size_t)nc + 1));
+        qv = qci + al16(4 * nq);
+        end = qv + al16(sizeof(T) * nq);
+    }
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+// Issue the copy of `bytes` (a multiple of 4) from global memory to 16-byte aligned
+// shared memory: 16-byte pieces while the source is 16-byte aligned, 4-byte ones for the rest.
+__device__ __forceinline__ void stage_async(unsigned char* dst, const void* src, size_t bytes) {
+    const unsigned char* g = static_cast<const unsigned char*>(src);
+    size_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+        const size_t n16 = bytes >> 4;
+        for (size_t k = threadIdx.x; k < n16; k += blockDim.x) cp_async16(dst + 16 * k, g + 16 * k);
+        done = n16 << 4;
+    }
+    for (size_t k = (done >> 2) + threadIdx.x; k < (bytes >> 2); k += blockDim.x) cp_async4(dst + 4 * k, g + 4 * k);
+}
+// Level l of the tail with its matrix pointers moved to the staged copies.
+template <typename T>
+__device__ __forceinline__ VLevel<T> tail_level(const TailArgs<T>& a, int l, unsigned char* smem) {
+    VLevel<T> v = a.lv[l];
+    if (a.soff[l] < 0) return v;
+    const TailLayout<T> o(v, a.lv[l + 1].B.n);
+    unsigned char* base = smem + a.soff[l];
+    v.B.rp = reinterpret_cast<const int32_t*>(base + o.rp);
+    v.B.ci = reinterpret_cast<const int32_t*>(base + o.ci);
+    v.B.v = reinterpret_cast<const T*>(base + o.v);
+    v.dinv = reinterpret_cast<const T*>(base + o.dinv);
+    v.P.pcol = reinterpret_cast<const int32_t*>(base + o.pcol);
+    v.P.pval = reinterpret_cast<const T*>(base + o.pval);
+    v.P.pcnt = reinterpret_cast<const int32_t*>(base + o.pcnt);
+    v.qrp = reinterpret_cast<const int32_t*>(base + o.qrp);
+    v.qci = reinterpret_cast<const int32_t*>(base + o.qci);
+    v.qv = reinterpret_cast<const T*>(base + o.qv);
+    return v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<T> a) {
-    pdl_begin();
-    // the vectors of all tail levels live in shared memory: b, x and the work vector per level
     extern __shared__ __align__(16) unsigned char tail_smem[];
+    // the matrices first: they were written during the setup, long before this launch
+    for (int l = 0; l + 1 < a.nl; ++l) {
+        if (a.soff[l] < 0) continue;
+        const VLevel<T>& g = a.lv[l];
+        const TailLayout<T> o(g, a.lv[l + 1].B.n);
+        unsigned char* base = tail_smem + a.soff[l];
+        const size_t n = (size_t)g.B.n, nP = n * (size_t)g.P.c;
+        stage_async(base + o.rp, g.B.rp, 4 * (n + 1));
+        stage_async(base + o.ci, g.B.ci, 4 * (size_t)g.B.nnz);
+        stage_async(base + o.v, g.B.v, sizeof(T) * (size_t)g.B.nnz);
+        stage_async(base + o.dinv, g.dinv, sizeof(T) * n);
+        stage_async(base + o.pcol, g.P.pcol, 4 * nP);
+        stage_async(base + o.pval, g.P.pval, sizeof(T) * nP);
+        stage_async(base + o.pcnt, g.P.pcnt, 4 * n);
+        stage_async(base + o.qrp, g.qrp, 4 * ((size_t)a.lv[l + 1].B.n + 1));
+        stage_async(base + o.qci, g.qci, 4 * (size_t)g.qnnz);
+        stage_async(base + o.qv, g.qv, sizeof(T) * (size_t)g.qnnz);
+    }
+    const int nL = a.lv[a.nl - 1].B.n;
+    if (a.pinv_off >= 0) stage_async(tail_smem + a.pinv_off, a.pinv, sizeof(T) * (size_t)nL * nL);
+    pdl_begin();
+    // the vectors of all tail levels: b, x and the work vector per level
     T* sbuf = reinterpret_cast<T*>(tail_smem);
     const int tid = threadIdx.x;
     T* sb[TAIL_MAX_LEVELS];
@@ -169,13 +260,14 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
         }
     }
     for (int i = tid; i < a.lv[0].B.n; i += blockDim.x) sb[0][i] = a.lv[0].b[i];
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     T* xcur[TAIL_MAX_LEVELS];
     T* xtmp[TAIL_MAX_LEVELS];
     T* gx = a.lv[0].x;  // global buffer that receives the first tail level's result
     T* gt = a.lv[0].r;
     for (int l = 0; l + 1 < a.nl; ++l) {
-        const VLevel<T>& v = a.lv[l];
+        const VLevel<T> v = tail_level(a, l, tail_smem);
         const int n = v.B.n;
         T* b = sb[l];
         T* x = sx[l];
@@ -220,9 +312,10 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
         const int L = a.nl - 1;
         const int n = a.lv[L].B.n;
         const int lane = tid & 31;
+        const T* pinv = a.pinv_off >= 0 ? reinterpret_cast<const T*>(tail_smem + a.pinv_off) : a.pinv;
         for (int row = tid >> 5; row < n; row += blockDim.x >> 5) {
             T sum = T(0);
-            for (int c = lane; c < n; c += 32) sum += a.pinv[(int64_t)row * n + c] * sb[L][c];
+            for (int c = lane; c < n; c += 32) sum += pinv[(int64_t)row * n + c] * sb[L][c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
             if (lane == 0) sx[L][row] = sum;
@@ -231,7 +324,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
         xcur[L] = sx[L];
     }
     for (int l = a.nl - 2; l >= 0; --l) {
-        const VLevel<T>& v = a.lv[l];
+        const VLevel<T> v = tail_level(a, l, tail_smem);
         const int n = v.B.n;
         T* b = sb[l];
         T* x = xcur[l];
@@ -321,9 +414,26 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         size_t smem = 0;
         for (int q = 0; q < a.nl; ++q) smem += 3 * sizeof(T) * (size_t)a.lv[q].B.n;
         BAMG_REQUIRE(smem <= 96 * 1024, BAMG_EINVAL, "vcycle tail: levels too large for shared memory");
+        // stage the matrices of the finer tail levels first (their rows are walked most),
+        // then B_L^+, while they fit
+        smem = al16(smem);
+        for (int q = 0; q < a.nl; ++q) {
+            a.soff[q] = -1;
+            if (q + 1 == a.nl) continue;
+            const size_t need = TailLayout<T>(a.lv[q], a.lv[q + 1].B.n).end;
+            if (smem + need <= (size_t)TAIL_SMEM) {
+                a.soff[q] = (int32_t)smem;
+                smem += need;
+            }
+        }
+        const size_t npinv = al16(sizeof(T) * (size_t)a.lv[a.nl - 1].B.n * a.lv[a.nl - 1].B.n);
+        if (smem + npinv <= (size_t)TAIL_SMEM) {
+            a.pinv_off = (int32_t)smem;
+            smem += npinv;
+        }
         static std::atomic<bool> attr{false};  // idempotent; several host threads may get here
         if (!attr) {
-            BAMG_CK(cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            BAMG_CK(cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM));
             attr = true;
         }
         BAMG_LAUNCH_PDL(k_vcycle_tail<T>, 1, TAIL_THREADS, smem, s, a);
@@ -582,6 +692,21 @@ __global__ void k_inc_j(int* dj) {
     pdl_begin();
     if (threadIdx.x == 0 && blockIdx.x == 0) *dj += 1;
 }
+// j += 1 at the end of a step of the device-side loop, and the loop's condition: go on
+// while j < ctl[2], h_{j+1,j} != 0 and estimate * kappa > tol ||x||_1 (the host's test
+// for a true residual check, with the same operands).
+__global__ void k_step_end(int* dj, const double* __restrict__ st, int m, const double* __restrict__ ctl,
+                           cudaGraphConditionalHandle cond) {
+    pdl_begin();
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const GmresLayout L(m);
+        const int jn = *dj + 1;
+        *dj = jn;
+        const double est = st[L.est], hn = st[L.hn];
+        const bool stop = jn >= (int)ctl[2] || hn == 0.0 || est * ctl[0] <= ctl[1];
+        cudaGraphSetConditional(cond, stop ? 0u : 1u);
+    }
+}
 
 // Fused Arnoldi kernels over row tiles (one block each).  The column sums of the per-tile
 // dot products are formed again by every block that needs them (warp per column, lanes
@@ -727,7 +852,8 @@ __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __res
 template <typename T>
 void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T* vin, T* zout, int* dj,
                             double* st, int m, double* partial, const std::vector<VLevel<T>>& lv,
-                            const T* pinv, double omega, int nu_pre, int nu_post, double* h_est, cudaStream_t s) {
+                            const T* pinv, double omega, int nu_pre, int nu_post, double* h_est, const double* ctl,
+                            cudaGraphConditionalHandle cond, cudaStream_t s) {
     GmresLayout L(m);
     const unsigned g = blocks_for(n, 256);
     const int stride = m + 1;
@@ -743,16 +869,22 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
     BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pb, nt, st + L.h2,
                     Pa, stride, 1);
     BAMG_LAUNCH_PDL(k_givens_scale_j, g, 256, 0, s, n, V, (const int*)dj, st, m, (const double*)Pa, nt, stride);
-    BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    BAMG_LAUNCH_PDL(k_inc_j, 1, 32, 0, s, dj);
+    if (cond) {
+        BAMG_LAUNCH_PDL(k_step_end, 1, 32, 0, s, dj, (const double*)st, m, ctl, cond);
+    } else {
+        BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        BAMG_LAUNCH_PDL(k_inc_j, 1, 32, 0, s, dj);
+    }
 }
 
 template void arnoldi_step_graphable<float>(int, const MatView<double>&, double*, float*, float*, float*, int*,
                                             double*, int, double*, const std::vector<VLevel<float>>&, const float*,
-                                            double, int, int, double*, cudaStream_t);
+                                            double, int, int, double*, const double*, cudaGraphConditionalHandle,
+                                            cudaStream_t);
 template void arnoldi_step_graphable<double>(int, const MatView<double>&, double*, double*, double*, double*, int*,
                                              double*, int, double*, const std::vector<VLevel<double>>&,
-                                             const double*, double, int, int, double*, cudaStream_t);
+                                             const double*, double, int, int, double*, const double*,
+                                             cudaGraphConditionalHandle, cudaStream_t);
 
 // `sweeps` sweeps of the smoother S of Eq. (4.4) on one level, ping-ponging between x and
 // y; the result ends in x (one copy when sweeps is odd).

@@ -144,6 +144,7 @@ struct VLevel {  // one level of the V-cycle
     const int32_t* qrp = nullptr;  // Q by coarse rows
     const int32_t* qci = nullptr;
     const T* qv = nullptr;
+    int qnnz = 0;                  // entries of Q
     T *b = nullptr, *x = nullptr, *r = nullptr;  // work vectors of n entries
 };
 // One V-cycle: lv[0].b -> lv[0].x.  With Z != null the result is also stored at
@@ -170,12 +171,16 @@ void residual_norms(const MatView<double>& B, const double* x, double* d_out, do
 void scale_vec(int n, double* x, const double* d_num, int num_idx, bool reciprocal, double* y, cudaStream_t s);
 void gmres_init(double* d_state, int m, cudaStream_t s);
 // One Arnoldi step of flexible GMRES whose index j lives in device memory (*dj), so the
-// whole sequence can be captured once in a CUDA graph and replayed.  h_est (pinned host
-// memory) receives {residual estimate, h_{j+1,j}}.
+// whole sequence can be captured once in a CUDA graph and replayed.  With cond == 0,
+// h_est (pinned host memory) receives {residual estimate, h_{j+1,j}} after the step.
+// With a WHILE conditional handle the step is the body of a device-side loop: its last
+// kernel sets the handle to 0 once j + 1 >= ctl[2], h_{j+1,j} = 0, or
+// estimate * ctl[0] <= ctl[1] (ctl in device memory: kappa, tol ||x||_1, last j + 1).
 template <typename T>
 void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T* vin, T* zout, int* dj, double* st,
                             int m, double* partial, const std::vector<VLevel<T>>& lv, const T* pinv, double omega,
-                            int nu_pre, int nu_post, double* h_est, cudaStream_t s);
+                            int nu_pre, int nu_post, double* h_est, const double* ctl,
+                            cudaGraphConditionalHandle cond, cudaStream_t s);
 void gmres_arnoldi_step(double* d_state, int j, int m, cudaStream_t s);
 void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s);
 

@@ -153,7 +153,9 @@ struct Solver : SolverBase {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    int64_t graph_kernels = 0;
+    int64_t graph_kernels = 0;  // kernels of one step
+    bool graph_loop = false;    // one launch runs steps until the device-side test stops it
+    DevBuf<double> ctl;         // the loop's kappa, tol ||x||_1 and last j + 1
 
     ~Solver() override {
         cudaStreamSynchronize(s);
@@ -191,6 +193,7 @@ struct Solver : SolverBase {
                 v[l].qrp = L.qrp.get();
                 v[l].qci = L.qci.get();
                 v[l].qv = L.qv.get();
+                v[l].qnnz = (int)L.qci.n;
             }
             v[l].b = L.vb.get();
             v[l].x = L.vx.get();
@@ -560,24 +563,75 @@ struct Solver : SolverBase {
         BAMG_CK(cudaStreamSynchronize(s));
     }
 
+    // One Arnoldi step captured as a CUDA graph.  Preferred form: the step is the body of
+    // a WHILE conditional node, so one launch runs steps until the step's last kernel
+    // stops the loop (the host's own test for a true residual check) and the host waits
+    // once per check instead of once per step.  Where the driver refuses the conditional
+    // node the graph is one step per launch.
     void capture_step(int n) {
+        if (!ctl.get()) ctl.alloc(3);
+        if (!(o.device_loop && capture_step_graph(n, true))) capture_step_graph(n, false);
+    }
+    bool capture_step_graph(int n, bool loop) {
         std::vector<VLevel<T>> vl = vlevels(vin.get(), zout.get());
         const uint64_t c0 = t_launches;  // other threads may launch meanwhile
-        BAMG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        PdlScope pdl_;  // programmatic edges between the step's kernels
+        cudaGraph_t g = nullptr;
+        cudaGraphConditionalHandle cond = 0;
+        if (loop) {
+            BAMG_CK(cudaGraphCreate(&g, 0));
+            bool ok = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+            cudaGraphNodeParams p = {};
+            if (ok) {
+                p.type = cudaGraphNodeTypeConditional;
+                p.conditional.handle = cond;
+                p.conditional.type = cudaGraphCondTypeWhile;
+                p.conditional.size = 1;
+                cudaGraphNode_t node = nullptr;
+                ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p) == cudaSuccess;
+            }
+            if (ok)
+                ok = cudaStreamBeginCaptureToGraph(s, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                cudaGraphDestroy(g);
+                return false;
+            }
+        } else {
+            BAMG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        }
         try {
+            PdlScope pdl_;  // programmatic edges between the step's kernels
             arnoldi_step_graphable<T>(n, B64(), V.get(), Z.get(), vin.get(), zout.get(), dj.get(), state.get(), m,
-                                      partial.get(), vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, h_pin, s);
+                                      partial.get(), vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, h_pin, ctl.get(),
+                                      cond, s);
         } catch (...) {
-            cudaGraph_t g = nullptr;
-            cudaStreamEndCapture(s, &g);
-            if (g) cudaGraphDestroy(g);
+            cudaGraph_t c = nullptr;
+            cudaStreamEndCapture(s, &c);
+            if (loop) {
+                if (g) cudaGraphDestroy(g);
+            } else if (c) {
+                cudaGraphDestroy(c);
+            }
             throw;
         }
-        BAMG_CK(cudaStreamEndCapture(s, &graph));
-        graph_kernels = (int64_t)(t_launches - c0);
-        count_launches(-graph_kernels);  // counted again at every replay
-        BAMG_CK(cudaGraphInstantiate(&gexec, graph, 0));
+        cudaGraph_t c = nullptr;
+        BAMG_CK(cudaStreamEndCapture(s, &c));
+        if (!loop) g = c;
+        const int64_t kernels = (int64_t)(t_launches - c0);
+        count_launches(-kernels);  // counted again at every executed step
+        cudaGraphExec_t ex = nullptr;
+        if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(g);
+            if (loop) return false;
+            throw Error(BAMG_ECUDA, "cudaGraphInstantiate of the Arnoldi step failed");
+        }
+        graph = g;
+        gexec = ex;
+        graph_kernels = kernels;
+        graph_loop = loop;
+        return true;
     }
 
     void solve(double* x_user, int flags, double tol, bamg_stats* st) override {
@@ -633,7 +687,7 @@ struct Solver : SolverBase {
             BAMG_CK(cudaMemcpyAsync(x0.get(), x_init.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         }
         if (!gexec) capture_step(n);
-        int it = 0, restarts = 0, checks = 0, status = BAMG_ENOCONV;
+        int it = 0, restarts = 0, checks = 0, waits = 0, status = BAMG_ENOCONV;
         residual_norms(B, x0.get(), rn.get(), partial.get(), s);
         read_n(rn.get(), 4);
         double ratio = h_pin[0] / h_pin[2];
@@ -649,10 +703,29 @@ struct Solver : SolverBase {
             scale_vec(n, V0, state.get(), GL.hn, true, V0, s);
             BAMG_CK(cudaMemsetAsync(dj.get(), 0, sizeof(int), s));
             for (int j = 0; j < m && it < o.max_it; ++j) {
-                BAMG_CK(cudaGraphLaunch(gexec, s));
-                count_launches(graph_kernels);
-                BAMG_CK(cudaStreamSynchronize(s));
-                ++it;
+                if (graph_loop) {  // steps j .. jn - 1 in one launch
+                    h_pin[12] = kappa;
+                    h_pin[13] = tol * x1;
+                    h_pin[14] = (double)std::min(m, j + (o.max_it - it));
+                    BAMG_CK(cudaMemcpyAsync(ctl.get(), h_pin + 12, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+                    BAMG_CK(cudaGraphLaunch(gexec, s));
+                    BAMG_CK(cudaMemcpyAsync(h_pin, state.get() + GL.est, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                            s));
+                    BAMG_CK(cudaMemcpyAsync(h_pin + 4, dj.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+                    BAMG_CK(cudaStreamSynchronize(s));
+                    ++waits;
+                    const int jn = *reinterpret_cast<const int*>(h_pin + 4);
+                    BAMG_REQUIRE(jn > j && jn <= (int)h_pin[14], BAMG_ECUDA, "device-side Arnoldi loop: bad step count");
+                    count_launches(graph_kernels * (jn - j));
+                    it += jn - j;
+                    j = jn - 1;
+                } else {
+                    BAMG_CK(cudaGraphLaunch(gexec, s));
+                    count_launches(graph_kernels);
+                    BAMG_CK(cudaStreamSynchronize(s));
+                    ++waits;
+                    ++it;
+                }
                 const double est = h_pin[0], hn = h_pin[1];
                 const bool last = (j == m - 1) || it >= o.max_it || hn == 0.0;
                 if (est * kappa <= tol * x1 || last) {
@@ -698,6 +771,7 @@ struct Solver : SolverBase {
             st->iterations = it;
             st->restarts = restarts;
             st->true_checks = checks;
+            st->host_waits = waits;
             st->residual_l1 = ratio;
             st->setup_ms = setup_ms;
             st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -826,6 +900,7 @@ int bamg_default_opts(bamg_opts* o) {
     o->learned_refit = 1;
     o->model = nullptr;
     o->learned_rho_max = 0.0;
+    o->device_loop = 1;
     return BAMG_OK;
 }
 

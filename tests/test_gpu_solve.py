@@ -215,6 +215,31 @@ def test_nonconvergence_reports_enoconv():
     assert e.value.stats["iterations"] == 2
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_device_loop_gives_the_same_iterates(precision):
+    # the Arnoldi steps looping on the device (graph WHILE node) and one launch per step
+    # run the same arithmetic and take the same decisions: bit-identical results; a short
+    # restart length exercises restarts and the end-of-cycle exit
+    ch = tandem_queue(63)
+    runs = [_run(ch, 10, 10, 1e-12, precision, gmres_m=6, device_loop=d) for d in (0, 1)]
+    (_, x0, st0), (_, x1, st1) = runs
+    assert np.array_equal(x0, x1)
+    for k in ("iterations", "restarts", "true_checks", "residual_l1"):
+        assert st0[k] == st1[k], k
+    assert st0["restarts"] >= 1
+    assert st0["host_waits"] == st0["iterations"]
+    assert st1["host_waits"] == st1["true_checks"] < st1["iterations"]
+
+
+def test_device_loop_stops_at_max_it():
+    bamg = _bamg()
+    ch = grid_walk(40)
+    with pytest.raises(bamg.BamgError) as e:
+        _run(ch, 6, 8, 1e-15, "fp64", max_it=3, device_loop=1)
+    assert e.value.code == bamg._capi.BAMG_ENOCONV
+    assert e.value.stats["iterations"] == 3 and e.value.stats["host_waits"] == 1
+
+
 def test_delaunay_cr_fp64():
     ch = delaunay_walk(5000, 3)
     s, x, st = _run(ch, 8, 12, 1e-13, "fp64", coarsen="cr")
