@@ -135,16 +135,100 @@ struct DevBuf {
     T* get() const { return p; }
 };
 
-// Stream-ordered temporary (cudaMallocAsync / cudaFreeAsync).
+// Stack allocator for the temporaries of one stream: chunks from the stream-ordered pool,
+// handed out in 256-byte aligned slices and taken back when the slices are released (any
+// order; space is reclaimed from the top).  A slice released here can be handed out again
+// at once: its next user is ordered after its last one on the same stream.  Spares the
+// pool calls of the many short-lived buffers of a setup.
+struct StackArena {
+    struct Chunk {
+        char* base;
+        size_t cap, top;
+    };
+    struct Slice {
+        int chunk;
+        size_t prev;
+        char* p;
+        bool live;
+    };
+    cudaStream_t s;
+    std::vector<Chunk> chunks;
+    std::vector<Slice> stack;
+    static constexpr size_t MIN_CHUNK = size_t(64) << 20;
+    explicit StackArena(cudaStream_t st) : s(st) {}
+    void* push(size_t bytes) {
+        bytes = (bytes + 255) & ~size_t(255);
+        size_t c = stack.empty() ? 0 : (size_t)stack.back().chunk;
+        while (c < chunks.size() && chunks[c].top + bytes > chunks[c].cap) ++c;
+        if (c == chunks.size()) {
+            Chunk k{nullptr, bytes > MIN_CHUNK ? bytes : MIN_CHUNK, 0};
+            BAMG_CK(cudaMallocAsync((void**)&k.base, k.cap, s));
+            chunks.push_back(k);
+        }
+        Chunk& k = chunks[c];
+        stack.push_back(Slice{(int)c, k.top, k.base + k.top, true});
+        k.top += bytes;
+        return stack.back().p;
+    }
+    void pop(void* p) {
+        for (size_t q = stack.size(); q-- > 0;)
+            if (stack[q].p == p && stack[q].live) {
+                stack[q].live = false;
+                break;
+            }
+        while (!stack.empty() && !stack.back().live) {
+            chunks[stack.back().chunk].top = stack.back().prev;
+            stack.pop_back();
+        }
+    }
+    // returns the chunks to the pool once no slice is live
+    void release() {
+        if (!stack.empty()) return;
+        for (Chunk& k : chunks) cudaFreeAsync(k.base, s);
+        chunks.clear();
+    }
+    ~StackArena() {
+        stack.clear();
+        release();
+    }
+    StackArena(const StackArena&) = delete;
+    StackArena& operator=(const StackArena&) = delete;
+};
+// The arena that TmpBufs on its stream draw from (thread-local; null: the pool directly).
+StackArena*& tmp_arena();
+struct ArenaScope {  // sets tmp_arena() for a scope and releases the arena's chunks after
+    StackArena* prev;
+    StackArena& a;
+    explicit ArenaScope(StackArena& a_) : prev(tmp_arena()), a(a_) { tmp_arena() = &a; }
+    ~ArenaScope() {
+        tmp_arena() = prev;
+        a.release();
+    }
+};
+
+// Stream-ordered temporary: a slice of the current StackArena when it serves this stream,
+// else cudaMallocAsync / cudaFreeAsync.
 template <typename T>
 struct TmpBuf {
     T* p = nullptr;
     cudaStream_t s = nullptr;
+    StackArena* a = nullptr;
     TmpBuf(size_t n, cudaStream_t st) : s(st) {
-        if (n) BAMG_CK(cudaMallocAsync((void**)&p, n * sizeof(T), s));
+        if (!n) return;
+        StackArena* cur = tmp_arena();
+        if (cur && cur->s == st) {
+            a = cur;
+            p = static_cast<T*>(a->push(n * sizeof(T)));
+        } else {
+            BAMG_CK(cudaMallocAsync((void**)&p, n * sizeof(T), s));
+        }
     }
     ~TmpBuf() {
-        if (p) cudaFreeAsync(p, s);
+        if (!p) return;
+        if (a)
+            a->pop(p);
+        else
+            cudaFreeAsync(p, s);
     }
     TmpBuf(const TmpBuf&) = delete;
     TmpBuf& operator=(const TmpBuf&) = delete;

@@ -95,9 +95,62 @@ __global__ void k_scan_add(int32_t* __restrict__ out, int n, const int32_t* __re
     if (i < n) out[i] += bsum[i / SCAN_B];
 }
 
+// Arrays of up to SCAN_ONE_MAX entries: one block walks the tiles in order with a running
+// carry (one launch instead of three).  out[n] = total; out may alias in.
+constexpr int SCAN_ONE_T = 1024, SCAN_ONE_MAX = 32768;
+__global__ void __launch_bounds__(SCAN_ONE_T) k_scan_one(const int32_t* in, int32_t* out, int n) {
+    __shared__ int32_t wsum[SCAN_ONE_T / 32];
+    __shared__ int32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    for (int64_t t0 = 0; t0 < n; t0 += (int64_t)SCAN_ONE_T * SCAN_I) {
+        const int64_t base = t0 + (int64_t)threadIdx.x * SCAN_I;
+        int32_t v[SCAN_I];
+        int32_t tsum = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_I; ++k) {
+            v[k] = (base + k < n) ? in[base + k] : 0;
+            tsum += v[k];
+        }
+        int32_t x = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const int32_t w = wsum[lane];
+            int32_t incl = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            wsum[lane] = incl - w;
+        }
+        __syncthreads();
+        int32_t run = carry + wsum[warp] + x - tsum;
+#pragma unroll
+        for (int k = 0; k < SCAN_I; ++k) {
+            if (base + k < n) out[base + k] = run;
+            run += v[k];
+        }
+        __syncthreads();  // every thread has read carry and wsum
+        if (threadIdx.x == SCAN_ONE_T - 1) carry = run;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
 void exclusive_scan(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s) {
     if (n <= 0) {
         BAMG_CK(cudaMemsetAsync(d_out, 0, sizeof(int32_t), s));
+        return;
+    }
+    if (n <= SCAN_ONE_MAX) {
+        BAMG_LAUNCH(k_scan_one, 1, SCAN_ONE_T, 0, s, d_in, d_out, n);
         return;
     }
     const int nb = (int)blocks_for(n, SCAN_B);

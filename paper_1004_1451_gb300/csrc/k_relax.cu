@@ -52,6 +52,30 @@ void launch_diag(const MatView<T>& M, T* d, cudaStream_t s) {
     launch_diag_vals<T>(M.n, M.rp, M.ci, M.v, d, s);
 }
 
+// diag(B), diag(T) (when tv != null) and 1 / diag(B) in one pass
+template <typename T>
+__global__ void k_diagonals(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const T* __restrict__ bv, const T* __restrict__ tv, T* __restrict__ dB, T* __restrict__ dT,
+                            T* __restrict__ dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T b = T(0), t = T(0);
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+        if (ci[p] == i) {
+            b = bv[p];
+            if (tv) t = tv[p];
+            break;
+        }
+    dB[i] = b;
+    if (tv) dT[i] = t;
+    dinv[i] = T(1) / b;
+}
+template <typename T>
+void launch_diagonals(int n, const int32_t* rp, const int32_t* ci, const T* bv, const T* tv, T* dB, T* dT, T* dinv,
+                      cudaStream_t s) {
+    if (n) BAMG_LAUNCH(k_diagonals<T>, blocks_for(n, 256), 256, 0, s, n, rp, ci, bv, tv, dB, dT, dinv);
+}
+
 template <typename T>
 __global__ void k_reciprocal(int n, const T* d, T* dinv) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -337,26 +361,54 @@ __global__ void k_reduce_partials(int nblocks, int width, const double* __restri
     if (lane == 0) out[q] = s;
 }
 
+// Column statistics of Eq. (3.4) / the Rayleigh quotients as per-block partial sums
+// (nb rows of `width` values in `partial`); the consumer forms the sums with
+// colsum_partials.  Returns nb.
+template <typename T>
+static int colstats_blocks(int n, int ncols, int* width) {
+    constexpr int W = V16<T>::W;
+    const int nvec = (ncols + W - 1) / W;
+    int ny = 1;
+    while (ny * 2 * nvec <= 256) ny *= 2;
+    int nb = (int)blocks_for(n, ny);
+    if (nb > 512) nb = 512;
+    *width = nvec * 2 * W;
+    return nb;
+}
 template <typename T, int MODE>
-static void colstats(const MatView<T>& B, const T* T_val, const T* X, int ld, int col0, int ncols, double* d_sums,
+static void colstats(const MatView<T>& B, const T* T_val, const T* X, int ld, int col0, int ncols, double* partial,
                      cudaStream_t s) {
     constexpr int W = V16<T>::W;
     const int nvec = (ncols + W - 1) / W;
     int ny = 1;
     while (ny * 2 * nvec <= 256) ny *= 2;
-    int nb = (int)blocks_for(B.n, ny);
-    if (nb > 512) nb = 512;
-    const int width = nvec * 2 * W;
-    TmpBuf<double> partial((size_t)nb * width, s);
+    int width = 0;
+    const int nb = colstats_blocks<T>(B.n, ncols, &width);
     size_t smem = (size_t)ny * nvec * 2 * W * sizeof(double);
     BAMG_LAUNCH((k_colstats<T, MODE>), nb, dim3(nvec, ny), smem, s, B.n, B.rp, B.ci, B.v, T_val, X, ld, col0, nvec,
-                partial.get());
-    BAMG_LAUNCH(k_reduce_partials, blocks_for(width, 4), 128, 0, s, nb, width, partial.get(), d_sums);
+                partial);
+}
+// sums[q] for q < width from the partials, one warp per output as in k_reduce_partials
+// (lanes stride the blocks, then the butterfly); a block of COLSUM_T threads.
+constexpr int COLSUM_T = 256;
+__device__ void colsum_partials(int nblocks, int width, const double* __restrict__ partial, double* sums) {
+    const int lane = threadIdx.x & 31;
+    for (int q = threadIdx.x >> 5; q < width; q += COLSUM_T / 32) {
+        double s = 0.0;
+        for (int b = lane; b < nblocks; b += 32) s += partial[(int64_t)b * width + q];
+        s = warp_sum(s);
+        if (lane == 0) sums[q] = s;
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- LS weights
-__global__ void k_weights(int ncols, int W, const double* __restrict__ sums, const uint8_t* __restrict__ active,
-                          double floor, double* __restrict__ w, double* __restrict__ nrm) {
+__global__ void __launch_bounds__(COLSUM_T) k_weights(int ncols, int W, int nblocks, const double* __restrict__ partial,
+                                                        const uint8_t* __restrict__ active, double floor,
+                                                        double* __restrict__ w, double* __restrict__ nrm) {
+    __shared__ double sums[64];
+    colsum_partials(nblocks, 2 * ((ncols + W - 1) / W) * W, partial, sums);
+    if (threadIdx.x >= 32) return;
     const int k = threadIdx.x;  // one warp, ncols <= 32
     double m = 0.0, nk = 1.0;
     if (k < ncols) {
@@ -395,17 +447,21 @@ void tv_weights(const MatView<T>& B, int ncols, int ld, int col0, const uint8_t*
                 double* d_w, cudaStream_t s) {
     constexpr int W = V16<T>::W;
     BAMG_REQUIRE(ncols >= 1 && ncols <= 32, BAMG_EINVAL, "tv_weights: 1 <= ncols <= 32");
-    const int nvec = (ncols + W - 1) / W;
-    TmpBuf<double> sums((size_t)nvec * 2 * W, s);
+    int width = 0;
+    const int nb = colstats_blocks<T>(B.n, ncols, &width);
+    TmpBuf<double> partial((size_t)nb * width, s);
     TmpBuf<double> nrm(32, s);
-    colstats<T, 0>(B, nullptr, X, ld, col0, ncols, sums.get(), s);
-    BAMG_LAUNCH(k_weights, 1, 32, 0, s, ncols, W, sums.get(), d_active, floor, d_w, nrm.get());
+    colstats<T, 0>(B, nullptr, X, ld, col0, ncols, partial.get(), s);
+    BAMG_LAUNCH(k_weights, 1, COLSUM_T, 0, s, ncols, W, nb, (const double*)partial.get(), d_active, floor, d_w,
+                nrm.get());
     BAMG_LAUNCH(k_scale_cols<T>, blocks_for((int64_t)B.n * ncols, 256), 256, 0, s, B.n, X, ld, col0, ncols, nrm.get());
 }
 
 // ---------------------------------------------------------------- Rayleigh update
-__global__ void k_rayleigh(int ncols, int W, const double* __restrict__ sums, double tol, double* __restrict__ lam,
-                           uint8_t* __restrict__ sel) {
+__global__ void __launch_bounds__(COLSUM_T) k_rayleigh(int ncols, int W, int nblocks, const double* __restrict__ partial,
+                                                         double tol, double* __restrict__ lam, uint8_t* __restrict__ sel) {
+    __shared__ double sums[64];
+    colsum_partials(nblocks, 2 * ((ncols + W - 1) / W) * W, partial, sums);
     const int k = threadIdx.x;
     if (k >= ncols) return;
     const int ch = k / W, e = k - ch * W;
@@ -421,10 +477,11 @@ template <typename T>
 void rayleigh_update(const MatView<T>& B, const T* T_val, const T* X, int ncols, int ld, int col0, double tol,
                      double* d_lam, uint8_t* d_sel, cudaStream_t s) {
     constexpr int W = V16<T>::W;
-    const int nvec = (ncols + W - 1) / W;
-    TmpBuf<double> sums((size_t)nvec * 2 * W, s);
-    colstats<T, 1>(B, T_val, X, ld, col0, ncols, sums.get(), s);
-    BAMG_LAUNCH(k_rayleigh, 1, 32, 0, s, ncols, W, sums.get(), tol, d_lam, d_sel);
+    int width = 0;
+    const int nb = colstats_blocks<T>(B.n, ncols, &width);
+    TmpBuf<double> partial((size_t)nb * width, s);
+    colstats<T, 1>(B, T_val, X, ld, col0, ncols, partial.get(), s);
+    BAMG_LAUNCH(k_rayleigh, 1, COLSUM_T, 0, s, ncols, W, nb, (const double*)partial.get(), tol, d_lam, d_sel);
 }
 
 // ---------------------------------------------------------------- injection / prolongation
@@ -506,6 +563,19 @@ __global__ void k_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col) 
 template <typename Tin, typename Tout>
 void launch_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col, cudaStream_t s) {
     if (n) BAMG_LAUNCH((k_vec_to_strided<Tin, Tout>), blocks_for(n, 256), 256, 0, s, n, y, X, ld, col);
+}
+// nv vectors y[q * n + i] to the columns col0 + q
+template <typename Tin, typename Tout>
+__global__ void k_vecs_to_strided(int n, int nv, const Tin* y, Tout* X, int ld, int col0) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * nv) return;
+    const int q = (int)(t / n), i = (int)(t - (int64_t)q * n);
+    X[(int64_t)i * ld + col0 + q] = (Tout)y[t];
+}
+template <typename Tin, typename Tout>
+void launch_vecs_to_strided(int n, int nv, const Tin* y, Tout* X, int ld, int col0, cudaStream_t s) {
+    if (n && nv)
+        BAMG_LAUNCH((k_vecs_to_strided<Tin, Tout>), blocks_for((int64_t)n * nv, 256), 256, 0, s, n, nv, y, X, ld, col0);
 }
 
 // ---------------------------------------------------------------- B = I - A
@@ -601,6 +671,8 @@ int build_system_matrix(int n, int nnzA, const int32_t* rpA, const int32_t* ciA,
     template void launch_diag<T>(const MatView<T>&, T*, cudaStream_t);                                             \
     template void launch_diag_vals<T>(int, const int32_t*, const int32_t*, const T*, T*, cudaStream_t);            \
     template void launch_reciprocal<T>(int, const T*, T*, cudaStream_t);                                           \
+    template void launch_diagonals<T>(int, const int32_t*, const int32_t*, const T*, const T*, T*, T*, T*,         \
+                                      cudaStream_t);                                                                \
     template void launch_identity_on_pattern<T>(int, const int32_t*, const int32_t*, T*, cudaStream_t);            \
     template void relax<T>(const MatView<T>&, const T*, const T*, const T*, const T*, const double*, int, int, int, \
                            T, int, T*, T*, cudaStream_t);                                                          \
@@ -619,5 +691,7 @@ template void launch_strided_to_vec<float, double>(int, const float*, int, int, 
 template void launch_strided_to_vec<double, double>(int, const double*, int, int, double*, cudaStream_t);
 template void launch_vec_to_strided<double, float>(int, const double*, float*, int, int, cudaStream_t);
 template void launch_vec_to_strided<double, double>(int, const double*, double*, int, int, cudaStream_t);
+template void launch_vecs_to_strided<double, float>(int, int, const double*, float*, int, int, cudaStream_t);
+template void launch_vecs_to_strided<double, double>(int, int, const double*, double*, int, int, cudaStream_t);
 
 }  // namespace bamg

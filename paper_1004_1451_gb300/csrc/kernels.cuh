@@ -31,6 +31,10 @@ template <typename T>
 void launch_diag_vals(int n, const int32_t* rp, const int32_t* ci, const T* vals, T* d, cudaStream_t s);
 template <typename T>
 void launch_reciprocal(int n, const T* d, T* dinv, cudaStream_t s);
+// dB = diag(B), dT = diag(T) (skipped when tv is null), dinv = 1 / dB, one launch
+template <typename T>
+void launch_diagonals(int n, const int32_t* rp, const int32_t* ci, const T* bv, const T* tv, T* dB, T* dT, T* dinv,
+                      cudaStream_t s);
 template <typename T>
 void launch_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* tv, cudaStream_t s);
 // nu sweeps; T_val/dT/d_lambda may be null (no shift).  work: n*ld scratch.
@@ -55,6 +59,8 @@ template <typename Tin, typename Tout>
 void launch_strided_to_vec(int n, const Tin* X, int ld, int col, Tout* y, cudaStream_t s);
 template <typename Tin, typename Tout>
 void launch_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col, cudaStream_t s);
+template <typename Tin, typename Tout>
+void launch_vecs_to_strided(int n, int nv, const Tin* y, Tout* X, int ld, int col0, cudaStream_t s);
 
 // Build B = I - A (diagonal always stored) from A (sorted CSR); checks column sums,
 // signs and a_ii < 1.  Returns the status flags (bit 0: negative entry, bit 1: colsum,

@@ -5,10 +5,13 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
 #include <numeric>
+#include <string>
 #include <thread>
 #include <type_traits>
 
@@ -36,6 +39,10 @@ void set_last_error(const std::string& m) { g_err = m; }
 cudaStream_t& alloc_stream() {
     static thread_local cudaStream_t st = nullptr;
     return st;
+}
+StackArena*& tmp_arena() {
+    static thread_local StackArena* a = nullptr;
+    return a;
 }
 // Sets the allocation stream for the lifetime of the object.
 static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
@@ -104,9 +111,42 @@ struct LevelT {
         dB.alloc(n);
         dT.alloc(n);
         dinv.alloc(n);
-        launch_diag_vals<T>(n, rp.get(), ci.get(), bv.get(), dB.get(), s);
-        if (tv.get()) launch_diag_vals<T>(n, rp.get(), ci.get(), tv.get(), dT.get(), s);
-        launch_reciprocal<T>(n, dB.get(), dinv.get(), s);
+        launch_diagonals<T>(n, rp.get(), ci.get(), bv.get(), tv.get(), dB.get(), dT.get(), dinv.get(), s);
+    }
+};
+
+// BAMG_TRACE set (and not "0"): the setup synchronises at each phase boundary and prints
+// the wall time of every phase to stderr.  Diagnostic only; off by default.
+struct PhaseTrace {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    std::chrono::steady_clock::time_point t;
+    std::string out;
+    explicit PhaseTrace(cudaStream_t s_) : s(s_) {
+        const char* e = std::getenv("BAMG_TRACE");
+        on = e && std::strcmp(e, "0") != 0;
+        if (on) {
+            cudaStreamSynchronize(s);
+            t = std::chrono::steady_clock::now();
+        }
+    }
+    void mark(const char* what, int l = -1) {
+        if (!on) return;
+        const auto issued = std::chrono::steady_clock::now();
+        cudaStreamSynchronize(s);
+        const auto now = std::chrono::steady_clock::now();
+        const double ms = std::chrono::duration<double, std::milli>(now - t).count();
+        const double ims = std::chrono::duration<double, std::milli>(issued - t).count();
+        char buf[96];  // phase: host time to issue its work / wall time to its completion
+        if (l >= 0)
+            std::snprintf(buf, sizeof buf, " %s@%d %.3f/%.3f", what, l, ims, ms);
+        else
+            std::snprintf(buf, sizeof buf, " %s %.3f/%.3f", what, ims, ms);
+        out += buf;
+        t = now;
+    }
+    ~PhaseTrace() {
+        if (on) std::fprintf(stderr, "bamg setup phases (ms):%s\n", out.c_str());
     }
 };
 
@@ -205,6 +245,8 @@ struct Solver : SolverBase {
     }
 
     DevBuf<int> ls_err;  // overflow flag of the neighbourhood searches, read once per setup
+    std::unique_ptr<StackArena> arena;  // the setup's temporaries
+    PhaseTrace* trace = nullptr;  // set during a traced setup
 
     void alloc_vcycle_work() {
         for (auto& L : lv) {
@@ -223,6 +265,7 @@ struct Solver : SolverBase {
         c.w.alloc(ld);
         BAMG_CK(cudaMemsetAsync(c.w.get(), 0, sizeof(double) * ld, s));
         tv_weights<T>(c.B(), ncols_w, ld, 0, d_active, o.weight_floor, c.X.get(), c.w.get(), s);
+        if (trace) trace->mark(" w", l);
         c.pcol.alloc((size_t)c.n * o.caliber);
         c.pval.alloc((size_t)c.n * o.caliber);
         c.pcnt.alloc(c.n);
@@ -243,9 +286,12 @@ struct Solver : SolverBase {
                          c.w.get(), o.z, o.mmax, o.caliber, ridge(), c.pcol.get(), c.pval.get(), c.pcnt.get(), s,
                          ls_err.get(), ex);
         }
+        if (trace) trace->mark(" interp", l);
         build_restriction<T>(c.P(o.caliber), c.nc, c.qrp, c.qci, c.qv, s);
+        if (trace) trace->mark(" q", l);
         GalerkinOut<T> go;
         galerkin<T>(c.B(), c.tv.get(), c.qrp.get(), c.qci.get(), c.qv.get(), c.P(o.caliber), c.nc, go, s);
+        if (trace) trace->mark(" gal", l);
         nx.n = c.nc;
         nx.nnz = go.nnz;
         nx.rp = std::move(go.rp);
@@ -277,6 +323,14 @@ struct Solver : SolverBase {
     void setup(const bamg_csr* A, int r_, int levels) {
         auto t0 = std::chrono::steady_clock::now();
         AllocStream as_(s);
+        if (!arena || arena->s != s) arena = std::make_unique<StackArena>(s);
+        ArenaScope ar_(*arena);
+        PhaseTrace tr(s);
+        trace = tr.on ? &tr : nullptr;
+        struct Untrace {
+            PhaseTrace*& p;
+            ~Untrace() { p = nullptr; }
+        } untrace_{trace};
         const int n = A->n;
         r = r_;
         // inputs on the device
@@ -334,6 +388,7 @@ struct Solver : SolverBase {
         lv.clear();
         lv.push_back(std::move(L0));
         const T omega = (T)o.omega;
+        tr.mark("input");
         // ---- first pass, down (Algorithm 3: relax U_l, P_l, Q_l, B_{l+1}, T_{l+1}, U_{l+1} = R U_l)
         for (int l = 0; l < levels; ++l) {
             LevelT<T>& c = *lv.back();
@@ -343,7 +398,9 @@ struct Solver : SolverBase {
                 relax<T>(c.B(), nullptr, c.dB.get(), c.dinv.get(), nullptr, nullptr, r, ld, 0, omega, o.nu_tv,
                          c.X.get(), work.get(), s);
             }
+            tr.mark("relax", l);
             split(l);
+            tr.mark("split", l);
             auto nl = std::make_unique<LevelT<T>>();
             nl->nx = (c.nx + 1) / 2;
             nl->ny = (c.ny + 1) / 2;
@@ -354,6 +411,7 @@ struct Solver : SolverBase {
             nn.X.alloc((size_t)nn.n * ld);
             BAMG_CK(cudaMemsetAsync(nn.X.get(), 0, sizeof(T) * nn.n * ld, s));
             inject_cols<T>(nn.n, cc.c2f.get(), cc.X.get(), nn.X.get(), ld, 0, r, s);
+            tr.mark("operators", l);
         }
         const int L = (int)lv.size() - 1;
         LevelT<T>& Lc = *lv[L];
@@ -372,9 +430,9 @@ struct Solver : SolverBase {
                                       std::is_same<T, float>::value, s);
             BAMG_REQUIRE(nv > 0, BAMG_ENUMERIC, "coarsest eigensolve did not converge");
             nvec = nv;
-            for (int q = 0; q < nvec; ++q)
-                launch_vec_to_strided<double, T>(nL, Vd.get() + (size_t)q * nL, Lc.X.get(), ld, ldU + q, s);
+            launch_vecs_to_strided<double, T>(nL, nvec, Vd.get(), Lc.X.get(), ld, ldU, s);
         }
+        tr.mark("coarse_eig");
         // ---- up (Algorithm 3: V_l = P_l V_{l+1}, relax (B_l - lambda_i T_l) x = 0, Rayleigh update)
         for (int l = L - 1; l >= 0; --l) {
             LevelT<T>& c = *lv[l];
@@ -390,6 +448,7 @@ struct Solver : SolverBase {
             c.sel.alloc(ldV);
             rayleigh_update<T>(c.B(), c.tv.get(), c.X.get(), nvec, ld, ldU, o.ev_change_tol, c.lam.get(), c.sel.get(),
                                s);
+            tr.mark("up", l);
         }
         // ---- rebuild all P_l, B_{l+1}, T_{l+1} from U_l and the selected V_l, top-down
         {
@@ -397,6 +456,7 @@ struct Solver : SolverBase {
             for (int l = 0; l < L; ++l) {
                 BAMG_LAUNCH(k_active_mask, 1, 32, 0, s, r, ldU, nvec, ld, lv[l]->sel.get(), active.get());
                 build_level_operators(l, active.get(), ld);
+                tr.mark("rebuild", l);
             }
         }
         // ---- coarsest minimal-norm inverse of the rebuilt B_L
@@ -412,6 +472,7 @@ struct Solver : SolverBase {
             else
                 launch_convert<double, float>((int64_t)nL * nL, pinv64.get(), pinvT.get(), s);
         }
+        tr.mark("pinv");
         // ---- initial guess: the state-vector approximation, 1^T x = 1
         x_init.alloc(n);
         launch_strided_to_vec<T, double>(n, lv[0]->X.get(), ld, ldU, x_init.get(), s);
@@ -425,6 +486,7 @@ struct Solver : SolverBase {
         BAMG_CK(cudaMemcpyAsync(&h_err, ls_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CK(cudaStreamSynchronize(s));
         BAMG_REQUIRE(h_err == 0, BAMG_EOVERFLOW, "neighbourhood search: a fine point needs more than 2048 recorded states");
+        tr.mark("guess");
         setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
 
