@@ -35,20 +35,12 @@ void set_last_error(const std::string& msg);
         if (!(cond)) throw ::bamg::Error((code), (msg));                                           \
     } while (0)
 
-// Every kernel of the library goes through this macro so the process-wide launch
-// counter is exact.
-#define BAMG_LAUNCH(kernel, grid, block, smem, stream, ...)                                        \
-    do {                                                                                           \
-        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                                \
-        ::bamg::count_launch();                                                                    \
-        BAMG_CK(cudaGetLastError());                                                               \
-    } while (0)
-
-// Programmatic dependent launch: while pdl_enabled() is set (the capture of the Arnoldi
-// step) BAMG_LAUNCH_PDL lets a kernel start launching before its predecessor finishes;
-// every such kernel calls pdl_begin() before its first memory access, which waits until
-// the predecessor grid has completed and its writes are visible, and signals that its own
-// dependents may launch.  Without the attribute both instructions return at once.
+// Programmatic dependent launch: while pdl_enabled() is set (the default; BAMG_PDL=0 in
+// the environment clears it) every launch lets the kernel start before its predecessor in
+// the stream finishes.  Every kernel of the library calls pdl_begin() before its first
+// access to memory written by earlier work: it waits until the predecessor grid has
+// completed and its writes are visible, and signals that its own dependents may launch.
+// Without the attribute both instructions return at once.
 bool& pdl_enabled();
 __device__ __forceinline__ void pdl_begin() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -79,6 +71,10 @@ struct PdlScope {
         ::bamg::count_launch();                                                                    \
         BAMG_CK(cudaGetLastError());                                                               \
     } while (0)
+// Every kernel of the library goes through this macro so the process-wide launch
+// counter is exact.
+#define BAMG_LAUNCH(kernel, grid, block, smem, stream, ...) \
+    BAMG_LAUNCH_PDL(kernel, grid, block, smem, stream, __VA_ARGS__)
 
 inline unsigned blocks_for(int64_t work, int per_block) {
     int64_t b = (work + per_block - 1) / per_block;

@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __re
                                                        const double* __restrict__ Tg, int k_ev,
                                                        double* __restrict__ sel, double* __restrict__ lam,
                                                        int32_t* __restrict__ kind, int* __restrict__ info) {
+    pdl_begin();
     __shared__ float A[CN * LDP], Km[CN * LDP];
     __shared__ float Vk[(KRY + 1) * CN];
     __shared__ float Hs[KRY * KRY];
@@ -516,6 +517,7 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
                                                       const double* __restrict__ Tg, const double* __restrict__ sel,
                                                       double* __restrict__ V, double* __restrict__ lam,
                                                       int* __restrict__ cycles) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smraw[];
     F* Ar = reinterpret_cast<F*>(smraw);
     F* Ai = Ar + CN * LDP;
@@ -863,6 +865,7 @@ constexpr int PINV_COLS = 8;
 template <typename F>
 __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restrict__ Bg, double* __restrict__ Pg,
                                                     int* __restrict__ info) {
+    pdl_begin();
     __shared__ F A[CN * LDP];
     __shared__ F R[CN * PINV_COLS];
     __shared__ F y[CN], dinv[CN], red[CT / 32], s_nrm;

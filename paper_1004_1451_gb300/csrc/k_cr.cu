@@ -10,6 +10,7 @@ namespace bamg {
 
 __global__ void k_tcount(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          int32_t* __restrict__ cnt) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int p = rp[i]; p < rp[i + 1]; ++p)
@@ -17,6 +18,7 @@ __global__ void k_tcount(int n, const int32_t* __restrict__ rp, const int32_t* _
 }
 __global__ void k_tfill(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                         const int32_t* __restrict__ rpT, int32_t* __restrict__ cursor, int32_t* __restrict__ ciT) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int p = rp[i]; p < rp[i + 1]; ++p) {
@@ -30,6 +32,7 @@ __device__ __forceinline__ bool beats(uint64_t pi, int i, uint64_t pj, int j) { 
 __global__ void k_mis_step(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const int32_t* __restrict__ rpT, const int32_t* __restrict__ ciT,
                            const uint8_t* __restrict__ und, uint8_t* __restrict__ win, uint64_t seed, uint64_t stream) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (!und[i]) {
@@ -53,6 +56,7 @@ __global__ void k_mis_remove(int n, const int32_t* __restrict__ rp, const int32_
                              const int32_t* __restrict__ rpT, const int32_t* __restrict__ ciT,
                              uint8_t* __restrict__ und, const uint8_t* __restrict__ win, uint8_t* __restrict__ chosen,
                              int* __restrict__ left) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !und[i]) return;
     if (win[i]) {
@@ -93,6 +97,7 @@ static void independent_set(int n, const int32_t* rp, const int32_t* ci, const i
 
 __global__ void k_cr_start(int n, const uint8_t* __restrict__ cf, double* __restrict__ u, uint64_t seed,
                            uint64_t stream) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) u[i] = cf[i] ? 0.0 : 1.0 + counter_uniform(seed, stream, (uint64_t)i);
 }
@@ -101,6 +106,7 @@ template <typename T>
 __global__ void k_frelax(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const T* __restrict__ bv, const uint8_t* __restrict__ cf, const double* __restrict__ u,
                          double* __restrict__ un, double omega) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (cf[i]) {
@@ -118,6 +124,7 @@ __global__ void k_frelax(int n, const int32_t* __restrict__ rp, const int32_t* _
 
 __global__ void k_cr_norms(int n, const double* __restrict__ u0, const double* __restrict__ u,
                            double* __restrict__ partial) {
+    pdl_begin();
     __shared__ double sh[2][8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double a = 0.0, b = 0.0;
@@ -140,6 +147,7 @@ __global__ void k_cr_norms(int n, const double* __restrict__ u0, const double* _
     }
 }
 __global__ void k_sum2(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+    pdl_begin();
     const int q = threadIdx.x;
     if (q >= 2) return;
     double s = 0.0;
@@ -149,17 +157,20 @@ __global__ void k_sum2(int nb, const double* __restrict__ partial, double* __res
 
 __global__ void k_cr_slow(int n, const uint8_t* __restrict__ cf, const double* __restrict__ up,
                           const double* __restrict__ u, double theta, uint8_t* __restrict__ cand) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     cand[i] = (!cf[i] && fabs(u[i]) / fabs(up[i]) > theta) ? 1 : 0;
 }
 
 __global__ void k_u8_to_i32(int n, const uint8_t* __restrict__ a, int32_t* __restrict__ b) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = a[i];
 }
 __global__ void k_cidx_from_scan(int n, const uint8_t* __restrict__ cf, const int32_t* __restrict__ sc,
                                  int32_t* __restrict__ cidx) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) cidx[i] = cf[i] ? sc[i] : -1;
 }

@@ -15,6 +15,7 @@ constexpr int SCAN_T = 256, SCAN_I = 8, SCAN_B = SCAN_T * SCAN_I;
 
 __global__ void k_scan_local(const int32_t* __restrict__ in, int32_t* __restrict__ out, int n,
                              int32_t* __restrict__ bsum) {
+    pdl_begin();
     __shared__ int32_t wsum[SCAN_T / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_I;
@@ -54,6 +55,7 @@ __global__ void k_scan_local(const int32_t* __restrict__ in, int32_t* __restrict
 }
 
 __global__ void k_scan_sums(int32_t* __restrict__ bsum, int nb, int32_t* __restrict__ total) {
+    pdl_begin();
     __shared__ int32_t wsum[32];
     __shared__ int32_t carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -91,6 +93,7 @@ __global__ void k_scan_sums(int32_t* __restrict__ bsum, int nb, int32_t* __restr
 }
 
 __global__ void k_scan_add(int32_t* __restrict__ out, int n, const int32_t* __restrict__ bsum) {
+    pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] += bsum[i / SCAN_B];
 }
@@ -99,6 +102,7 @@ __global__ void k_scan_add(int32_t* __restrict__ out, int n, const int32_t* __re
 // carry (one launch instead of three).  out[n] = total; out may alias in.
 constexpr int SCAN_ONE_T = 1024, SCAN_ONE_MAX = 32768;
 __global__ void __launch_bounds__(SCAN_ONE_T) k_scan_one(const int32_t* in, int32_t* out, int n) {
+    pdl_begin();
     __shared__ int32_t wsum[SCAN_ONE_T / 32];
     __shared__ int32_t carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -169,6 +173,7 @@ int32_t read_int(const int32_t* d_p, cudaStream_t s) {
 
 // ================================================================ coarsening
 __global__ void k_coarsen_grid(int nx, int ny, uint8_t* __restrict__ cf, int32_t* __restrict__ cidx) {
+    pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)nx * ny) return;
     const int ix = (int)(i % nx), iy = (int)(i / nx);
@@ -182,6 +187,7 @@ void coarsen_grid(int nx, int ny, uint8_t* cf, int32_t* cidx, cudaStream_t s) {
 
 __global__ void k_coarse_to_fine(int n, const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx,
                                  int32_t* __restrict__ c2f) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && cf[i]) c2f[cidx[i]] = i;
 }
@@ -609,6 +615,7 @@ __global__ void __launch_bounds__(WARPS * 32)
              T* __restrict__ pval, int32_t* __restrict__ pcnt, const int* __restrict__ list,
              const int* __restrict__ list_count, int* __restrict__ ovf_list, int* __restrict__ ovf_count,
              int* __restrict__ err, LsOut ex) {
+    pdl_begin();
     __shared__ int s_vis[WARPS][CAP];
     __shared__ unsigned long long s_key[WARPS][CAP];
     __shared__ uint8_t s_dist[WARPS][CAP];
@@ -692,6 +699,7 @@ __global__ void k_learned_select(int n, const uint8_t* __restrict__ cf, const in
                                  const int32_t* __restrict__ cand, const float* __restrict__ Y, const T* __restrict__ X,
                                  int ncols, int ld, const double* __restrict__ w, int c, int refit, double ridge,
                                  int32_t* __restrict__ pcol, T* __restrict__ pval, int32_t* __restrict__ pcnt) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || cf[i]) return;
     const int32_t* cd = cand + (int64_t)i * MLP_S;
@@ -793,12 +801,14 @@ int interp_learned(int n, const int32_t* rp, const int32_t* ci, const T* bv, con
 // ================================================================ restriction Q
 __global__ void k_q_count(int n, int c, const int32_t* __restrict__ pcol, const int32_t* __restrict__ pcnt,
                           int32_t* __restrict__ qcnt) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int t = 0; t < pcnt[i]; ++t) atomicAdd(qcnt + pcol[(int64_t)i * c + t], 1);
 }
 __global__ void k_q_fill(int n, int c, const int32_t* __restrict__ pcol, const int32_t* __restrict__ pcnt,
                          const int32_t* __restrict__ qrp, int32_t* __restrict__ cursor, int32_t* __restrict__ qci) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int t = 0; t < pcnt[i]; ++t) {
@@ -812,6 +822,7 @@ __global__ void k_q_fill(int n, int c, const int32_t* __restrict__ pcol, const i
 template <typename T>
 __global__ void k_q_sort(int nc, const int32_t* __restrict__ qrp, int32_t* __restrict__ qci, T* __restrict__ qv,
                          const int32_t* __restrict__ pcnt) {
+    pdl_begin();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
     const int a = qrp[I], b = qrp[I + 1];
@@ -851,6 +862,7 @@ void build_restriction(const EllView<T>& P, int nc, DevBuf<int32_t>& qrp, DevBuf
 __global__ void k_gal_count(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
                             const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                             const int32_t* __restrict__ pcnt, int32_t* __restrict__ np) {
+    pdl_begin();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
     int s = 0;
@@ -866,6 +878,7 @@ __global__ void k_gal_compact(int nc, const int32_t* __restrict__ poff, const in
                               const int32_t* __restrict__ rpc, const int32_t* __restrict__ uJ, const T* __restrict__ ubv,
                               const T* __restrict__ utv, int32_t* __restrict__ ci, T* __restrict__ bv,
                               T* __restrict__ tv) {
+    pdl_begin();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
     const int o = poff[I], d = rpc[I];
@@ -1048,6 +1061,7 @@ __device__ void gal_row(const GalArgs<T>& a, int I, bool local, unsigned long lo
 template <typename T>
 __global__ void __launch_bounds__(GAL_WARPS_S * 32)
     k_gal_small(const __grid_constant__ GalArgs<T> a, int32_t* __restrict__ list, int* __restrict__ nlist) {
+    pdl_begin();
     __shared__ unsigned long long keys[GAL_WARPS_S][GAL_CAP_S];
     __shared__ T svb[GAL_WARPS_S][GAL_CAP_S], svt[GAL_WARPS_S][GAL_CAP_S];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1211,6 +1225,7 @@ __device__ bool gal_row_hash(const GalArgs<T>& a, int I, int* hkey, T* hvb, T* h
 template <typename T>
 __global__ void __launch_bounds__(32) k_gal_large(const __grid_constant__ GalArgs<T> a,
                                                   const int32_t* __restrict__ list, const int* __restrict__ nlist) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char gal_smem[];
     unsigned long long* skeys = reinterpret_cast<unsigned long long*>(gal_smem);  // GAL_HSLOTS
     T* hvb = reinterpret_cast<T*>(skeys + GAL_HSLOTS);
@@ -1273,6 +1288,7 @@ void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int
 template <typename T>
 __global__ void k_csr_to_dense(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                const T* __restrict__ v, double* __restrict__ D) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int p = rp[i]; p < rp[i + 1]; ++p) D[(int64_t)i * n + ci[p]] = (double)v[p];

@@ -47,6 +47,7 @@ __device__ __forceinline__ int64_t bf_index(int64_t q) {
 // He-uniform weights W = (2u - 1) sqrt(6 / fan_in), u = SplitMix64 uniform of
 // (seed, stream = layer, index); biases zero.
 __global__ void k_mlp_init(uint64_t seed, float* __restrict__ P) {
+    pdl_begin();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= NPARAM) return;
     int layer = -1;
@@ -68,6 +69,7 @@ __global__ void k_mlp_init(uint64_t seed, float* __restrict__ P) {
 }
 
 __global__ void k_mlp_to_bf16(const float* __restrict__ P, __nv_bfloat16* __restrict__ Wb) {
+    pdl_begin();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= NPARAM) return;
     const int64_t b = bf_index(q);
@@ -108,6 +110,7 @@ template <typename TA, int N, int K>
 __global__ void __launch_bounds__(FWD_WARPS * 32)
     k_mlp_layer(int64_t M, const TA* __restrict__ A, const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias,
                 bool relu, __nv_bfloat16* __restrict__ Yb, float* __restrict__ Yf) {
+    pdl_begin();
     constexpr int LDW = K + 8;  // padded stride (bf16 elements): conflict-free fragment loads
     __shared__ __align__(16) __nv_bfloat16 sW[N * LDW];
     __shared__ float sb[N];
@@ -162,6 +165,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32)
 // loss sum mask (Y - T)^2 / rows_in_batch is added to *loss.
 __global__ void k_mlp_loss(int64_t M, int64_t Mtot, const float* __restrict__ Y, const float* __restrict__ Tg,
                            const float* __restrict__ Fe, float* __restrict__ dY, double* __restrict__ loss) {
+    pdl_begin();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
     if (q < M * MLP_S) {
@@ -181,6 +185,7 @@ __global__ void k_mlp_loss(int64_t M, int64_t Mtot, const float* __restrict__ Y,
 template <typename TX>
 __global__ void __launch_bounds__(256) k_gemm_tn(int64_t M, int N, int K, const float* __restrict__ D,
                                                  const TX* __restrict__ X, float* __restrict__ G) {
+    pdl_begin();
     __shared__ float sD[32][33], sX[32][33];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int n0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
@@ -222,6 +227,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int64_t M, int N, int K, const 
 __global__ void __launch_bounds__(256) k_gemm_nn_relu(int64_t M, int N, int K, const float* __restrict__ D,
                                                       const __nv_bfloat16* __restrict__ W,
                                                       const __nv_bfloat16* __restrict__ Hm, float* __restrict__ O) {
+    pdl_begin();
     __shared__ float sD[32][33], sW[32][33];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int64_t m0 = (int64_t)blockIdx.y * 32;
@@ -258,6 +264,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn_relu(int64_t M, int N, int K, c
 
 // g[n] += sum_m D[m][n]
 __global__ void k_colsum(int64_t M, int N, const float* __restrict__ D, float* __restrict__ g) {
+    pdl_begin();
     const int n = blockIdx.x;
     float s = 0.f;
     for (int64_t m = threadIdx.x; m < M; m += blockDim.x) s += D[m * N + n];
@@ -276,6 +283,7 @@ __global__ void k_colsum(int64_t M, int N, const float* __restrict__ D, float* _
 // Adam (bias-corrected), then the bf16 copy of the weights.
 __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ Mo,
                        float* __restrict__ Vo, __nv_bfloat16* __restrict__ Wb, float lr, float c1, float c2) {
+    pdl_begin();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= NPARAM) return;
     const float g = G[q];

@@ -13,6 +13,7 @@ namespace bamg {
 // ---------------------------------------------------------------- initial vectors
 template <typename T>
 __global__ void k_tv_init(int n, int ncols, int ld, int col0, uint64_t seed, double lo, double hi, T* X) {
+    pdl_begin();
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * ncols) return;
     int i = (int)(t / ncols);
@@ -33,6 +34,7 @@ void launch_tv_init(int n, int ncols, int ld, int col0, uint64_t seed, double lo
 template <typename T>
 __global__ void k_diag(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
                        T* __restrict__ d) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T x = T(0);
@@ -57,6 +59,7 @@ template <typename T>
 __global__ void k_diagonals(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                             const T* __restrict__ bv, const T* __restrict__ tv, T* __restrict__ dB, T* __restrict__ dT,
                             T* __restrict__ dinv) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T b = T(0), t = T(0);
@@ -78,6 +81,7 @@ void launch_diagonals(int n, const int32_t* rp, const int32_t* ci, const T* bv, 
 
 template <typename T>
 __global__ void k_reciprocal(int n, const T* d, T* dinv) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dinv[i] = T(1) / d[i];
 }
@@ -88,6 +92,7 @@ void launch_reciprocal(int n, const T* d, T* dinv, cudaStream_t s) {
 
 template <typename T>
 __global__ void k_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* tv) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int p = rp[i]; p < rp[i + 1]; ++p) tv[p] = (ci[p] == i) ? T(1) : T(0);
@@ -115,6 +120,7 @@ __global__ void __launch_bounds__(256, JAC_BLOCKS_PER_SM)
              const T* __restrict__ tv, const T* __restrict__ dB, const T* __restrict__ dinvB, const T* __restrict__ dT,
              const double* __restrict__ lam, int ncols, const T* __restrict__ X, T* __restrict__ Y, int ld, int col0,
              int nvec, T omega) {
+    pdl_begin();
     constexpr int W = V16<T>::W;
     constexpr int NT = SHIFT ? JB : 1;  // T values are carried only by the shifted sweep
     const int64_t stride = (int64_t)gridDim.x * blockDim.x / nvec;  // rows per pass of the grid
@@ -252,6 +258,7 @@ static int sm_count() {
 
 template <typename T>
 __global__ void k_copy_cols(int n, const T* __restrict__ src, T* __restrict__ dst, int ld, int col0, int nvec) {
+    pdl_begin();
     constexpr int W = V16<T>::W;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int row = (int)(t / nvec);
@@ -295,6 +302,7 @@ template <typename T, int MODE>
 __global__ void k_colstats(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const T* __restrict__ bv, const T* __restrict__ tv, const T* __restrict__ X, int ld,
                            int col0, int nvec, double* __restrict__ partial) {
+    pdl_begin();
     constexpr int W = V16<T>::W;
     extern __shared__ double sh[];
     const int ch = threadIdx.x, ry = threadIdx.y, ny = blockDim.y;
@@ -352,6 +360,7 @@ __global__ void k_colstats(int n, const int32_t* __restrict__ rp, const int32_t*
 
 // one warp per output: lanes stride the block partials, then a fixed butterfly
 __global__ void k_reduce_partials(int nblocks, int width, const double* __restrict__ partial, double* __restrict__ out) {
+    pdl_begin();
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (q >= width) return;
@@ -406,6 +415,7 @@ __device__ void colsum_partials(int nblocks, int width, const double* __restrict
 __global__ void __launch_bounds__(COLSUM_T) k_weights(int ncols, int W, int nblocks, const double* __restrict__ partial,
                                                         const uint8_t* __restrict__ active, double floor,
                                                         double* __restrict__ w, double* __restrict__ nrm) {
+    pdl_begin();
     __shared__ double sums[64];
     colsum_partials(nblocks, 2 * ((ncols + W - 1) / W) * W, partial, sums);
     if (threadIdx.x >= 32) return;
@@ -431,6 +441,7 @@ __global__ void __launch_bounds__(COLSUM_T) k_weights(int ncols, int W, int nblo
 
 template <typename T>
 __global__ void k_scale_cols(int n, T* __restrict__ X, int ld, int col0, int ncols, const double* __restrict__ nrm) {
+    pdl_begin();
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int row = (int)(t / ncols);
     if (row >= n) return;
@@ -460,6 +471,7 @@ void tv_weights(const MatView<T>& B, int ncols, int ld, int col0, const uint8_t*
 // ---------------------------------------------------------------- Rayleigh update
 __global__ void __launch_bounds__(COLSUM_T) k_rayleigh(int ncols, int W, int nblocks, const double* __restrict__ partial,
                                                          double tol, double* __restrict__ lam, uint8_t* __restrict__ sel) {
+    pdl_begin();
     __shared__ double sums[64];
     colsum_partials(nblocks, 2 * ((ncols + W - 1) / W) * W, partial, sums);
     const int k = threadIdx.x;
@@ -488,6 +500,7 @@ void rayleigh_update(const MatView<T>& B, const T* T_val, const T* X, int ncols,
 template <typename T>
 __global__ void k_inject(int nc, const int32_t* __restrict__ c2f, const T* __restrict__ X, T* __restrict__ Xc, int ld,
                          int col0, int nvec) {
+    pdl_begin();
     constexpr int W = V16<T>::W;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int I = (int)(t / nvec);
@@ -508,6 +521,7 @@ template <typename T>
 __global__ void k_prolong_cols(int n, int c, const int32_t* __restrict__ pcol, const T* __restrict__ pval,
                                const int32_t* __restrict__ pcnt, const T* __restrict__ Xc, T* __restrict__ X, int ld,
                                int col0, int nvec) {
+    pdl_begin();
     constexpr int W = V16<T>::W;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int i = (int)(t / nvec);
@@ -539,6 +553,7 @@ void prolong_cols(const EllView<T>& P, const T* Xc, T* X, int ld, int col0, int 
 // ---------------------------------------------------------------- conversions
 template <typename Tin, typename Tout>
 __global__ void k_convert(int64_t n, const Tin* a, Tout* b) {
+    pdl_begin();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (Tout)a[i];
 }
@@ -548,6 +563,7 @@ void launch_convert(int64_t n, const Tin* a, Tout* b, cudaStream_t s) {
 }
 template <typename Tin, typename Tout>
 __global__ void k_strided_to_vec(int n, const Tin* X, int ld, int col, Tout* y) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = (Tout)X[(int64_t)i * ld + col];
 }
@@ -557,6 +573,7 @@ void launch_strided_to_vec(int n, const Tin* X, int ld, int col, Tout* y, cudaSt
 }
 template <typename Tin, typename Tout>
 __global__ void k_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) X[(int64_t)i * ld + col] = (Tout)y[i];
 }
@@ -567,6 +584,7 @@ void launch_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col, cudaSt
 // nv vectors y[q * n + i] to the columns col0 + q
 template <typename Tin, typename Tout>
 __global__ void k_vecs_to_strided(int n, int nv, const Tin* y, Tout* X, int ld, int col0) {
+    pdl_begin();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * nv) return;
     const int q = (int)(t / n), i = (int)(t - (int64_t)q * n);
@@ -582,6 +600,7 @@ void launch_vecs_to_strided(int n, int nv, const Tin* y, Tout* X, int ld, int co
 __global__ void k_count_B(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                           const double* __restrict__ v, int32_t* __restrict__ cnt, int* __restrict__ flags,
                           double* __restrict__ colsum) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int f = 0;
@@ -609,6 +628,7 @@ __global__ void k_count_B(int n, const int32_t* __restrict__ rp, const int32_t* 
 __global__ void k_fill_B(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const double* __restrict__ v, const int32_t* __restrict__ rpB, int32_t* __restrict__ ciB,
                          double* __restrict__ vB) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int q = rpB[i];
@@ -638,6 +658,7 @@ __global__ void k_fill_B(int n, const int32_t* __restrict__ rp, const int32_t* _
 }
 
 __global__ void k_check_colsum(int n, const double* __restrict__ colsum, int* __restrict__ flags) {
+    pdl_begin();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n && !(fabs(colsum[j] - 1.0) <= 1e-12)) atomicOr(flags, 2);
 }

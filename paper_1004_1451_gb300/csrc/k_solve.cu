@@ -471,6 +471,7 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
 template <typename TX>
 __global__ void k_spmv64(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const double* __restrict__ bv, const TX* __restrict__ x, double* __restrict__ y, double alpha) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
@@ -489,6 +490,7 @@ int dots_partial_blocks(int n) { return (int)blocks_for(n, DOT_ROWS); }
 
 __global__ void __launch_bounds__(256) k_dots_partial(int n, const double* __restrict__ V, int64_t ldv, int nv,
                                                       const double* __restrict__ w, double* __restrict__ partial) {
+    pdl_begin();
     __shared__ double sw[DOT_ROWS];
     const int r0 = blockIdx.x * DOT_ROWS;
     const int cnt = min(DOT_ROWS, n - r0);
@@ -508,6 +510,7 @@ __global__ void __launch_bounds__(256) k_dots_partial(int n, const double* __res
 // One warp per column: lanes take the block partials in a fixed stride, then a fixed
 // butterfly; the order depends only on nb, so the result is deterministic.
 __global__ void k_reduce_cols(int nb, int nv, const double* __restrict__ partial, double* __restrict__ h) {
+    pdl_begin();
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (q >= nv) return;
@@ -526,6 +529,7 @@ void dots(int n, const double* V, int64_t ldv, int nv, const double* w, double* 
 
 __global__ void k_update_minus(int n, const double* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ h,
                                double* __restrict__ w) {
+    pdl_begin();
     __shared__ double sh[GMRES_MMAX + 1];
     for (int q = threadIdx.x; q < nv; q += blockDim.x) sh[q] = h[q];
     __syncthreads();
@@ -542,6 +546,7 @@ void update_minus(int n, const double* V, int64_t ldv, int nv, const double* d_h
 template <typename TZ>
 __global__ void k_form_x(int n, const double* __restrict__ x0, const TZ* __restrict__ Z, int64_t ldz, int nz,
                          const double* __restrict__ y, double* __restrict__ x) {
+    pdl_begin();
     __shared__ double sy[GMRES_MMAX];
     for (int q = threadIdx.x; q < nz; q += blockDim.x) sy[q] = y[q];
     __syncthreads();
@@ -560,6 +565,7 @@ void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const dou
 __global__ void __launch_bounds__(256) k_resnorm_partial(int n, const int32_t* __restrict__ rp,
                                                          const int32_t* __restrict__ ci, const double* __restrict__ bv,
                                                          const double* __restrict__ x, double* __restrict__ partial) {
+    pdl_begin();
     __shared__ double sh[4][8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double a = 0.0, b2 = 0.0, c = 0.0, d = 0.0;
@@ -598,6 +604,7 @@ void residual_norms(const MatView<double>& B, const double* x, double* d_out, do
 // y = x * num or x / num with num = d_num[num_idx] (a device scalar).
 __global__ void k_scale_vec(int n, const double* __restrict__ x, const double* __restrict__ d_num, int num_idx,
                             int reciprocal, double* __restrict__ y) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double a = d_num[num_idx];
@@ -612,6 +619,7 @@ void scale_vec(int n, double* x, const double* d_num, int num_idx, bool reciproc
 // sqrt(nrm2); previous rotations are applied, a new one annihilates h_{j+1,j}, and
 // |g_{j+1}| is the residual norm of the least-squares problem.
 __global__ void k_givens(double* __restrict__ st, int j, int m) {
+    pdl_begin();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     GmresLayout L(m);
     double col[GMRES_MMAX + 1];
@@ -643,6 +651,7 @@ void gmres_arnoldi_step(double* d_state, int j, int m, cudaStream_t s) {
 
 // Start of a cycle: beta = ||r0||_2 from nrm2, g = beta e_1; hn = beta scales v_1.
 __global__ void k_gmres_init(double* __restrict__ st, int m) {
+    pdl_begin();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     GmresLayout L(m);
     const double beta = sqrt(st[L.nrm2]);
@@ -656,6 +665,7 @@ void gmres_init(double* d_state, int m, cudaStream_t s) { BAMG_LAUNCH(k_gmres_in
 // y = R^{-1} g for the leading (j+1) x (j+1) block: R and g staged in shared memory,
 // column-oriented back substitution by one warp.
 __global__ void k_solve_y(double* __restrict__ st, int j, int m) {
+    pdl_begin();
     __shared__ double R[GMRES_MMAX * GMRES_MMAX], y[GMRES_MMAX];
     GmresLayout L(m);
     const int lane = threadIdx.x;

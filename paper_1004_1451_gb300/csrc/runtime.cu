@@ -32,7 +32,11 @@ void count_launches(int64_t k) {
 }
 static thread_local std::string g_err;
 bool& pdl_enabled() {
-    static thread_local bool on = false;
+    static const bool env_on = [] {
+        const char* e = std::getenv("BAMG_PDL");
+        return !(e && std::strcmp(e, "0") == 0);
+    }();
+    static thread_local bool on = env_on;
     return on;
 }
 void set_last_error(const std::string& m) { g_err = m; }
@@ -50,10 +54,12 @@ static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 // V-cycle factor helpers: x0 = 1 + u (SplitMix64 seed 7, stream 0), sums of r and r^2,
 // r <- (r - mean) * scale, r <- r - t.
 __global__ void k_vf_start(int n, double* __restrict__ x) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = 1.0 + counter_uniform(7, 0, (uint64_t)i);
 }
 __global__ void k_vf_moments(int n, const double* __restrict__ r, double* __restrict__ mom) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double a = 0.0, b = 0.0;
     if (i < n) {
@@ -68,10 +74,12 @@ __global__ void k_vf_moments(int n, const double* __restrict__ r, double* __rest
     }
 }
 __global__ void k_vf_affine(int n, double* __restrict__ r, double mean, double scale) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) r[i] = (r[i] - mean) * scale;
 }
 __global__ void k_vf_axpy(int n, double* __restrict__ r, const double* __restrict__ t) {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) r[i] -= t[i];
 }
@@ -79,6 +87,7 @@ __global__ void k_vf_axpy(int n, double* __restrict__ r, const double* __restric
 // active[k] = 1 for the random vectors, sel[q] for eigenvector column ldU + q, else 0.
 __global__ void k_active_mask(int r, int ldU, int nvec, int ld, const uint8_t* __restrict__ sel,
                               uint8_t* __restrict__ active) {
+    pdl_begin();
     const int k = threadIdx.x;
     if (k >= ld) return;
     uint8_t a = 0;
