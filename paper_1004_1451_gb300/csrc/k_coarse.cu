@@ -8,7 +8,8 @@
 // Eigenvectors, one block per selected eigenvalue: inverse iteration in complex
 // arithmetic on the pencil (B - sigma T) and a Rayleigh-type quotient, in FP64 (or in
 // FP32 for the mixed-precision setup).  B^+: a bordered FP64 LU solve, the right-hand
-// sides split over several blocks.
+// sides split over several blocks.  Factorisations use the whole block; triangular
+// solves run in single warps (registers and shuffles, no block barriers).
 #include <cfloat>
 #include <cstdio>
 #include <cstdlib>
@@ -111,81 +112,90 @@ __device__ void blu_factor(F* A, int n, int* perm, F* dinv, F floorv) {
     __syncthreads();
 }
 
-// Solves A X = R in place for the m right-hand sides of the n x m row-major R (row
-// stride ldr), with the factor of blu_factor.
-template <typename F>
-__device__ void blu_solve(const F* A, int n, const int* perm, const F* dinv, F* R, int m, int ldr) {
-    const int tid = threadIdx.x;
-    const int gx = m >= 16 ? 16 : (m >= 4 ? 4 : 1);  // thread grid gy x gx over (rows, columns)
-    const int gy = CT / gx, ty = tid / gx, tx = tid % gx;
-    for (int c = tid; c < m; c += CT)  // row interchanges: columns are independent
-        for (int k = 0; k < n; ++k) {
-            const int pk = perm[k];
-            if (pk != k) {
-                const F t = R[k * ldr + c];
-                R[k * ldr + c] = R[pk * ldr + c];
-                R[pk * ldr + c] = t;
-            }
-        }
-    __syncthreads();
-    // each thread updates at most 4 rows x 4 columns per step (n, m <= 64), from registers
-    for (int q = 0; q + 1 < n; ++q) {  // unit lower L
-        F y[4];
+// One warp solves A X = R for the NC columns c0 .. c0 + NC - 1 (those < m) of the
+// row-major R (row stride ldr) at once: the independent columns hide the latency of the
+// shuffles.  Row interchanges, then forward and back substitution eliminating one column
+// of L (of U) at a time, as in the plain algorithm.
+template <typename F, int NC>
+__device__ void warp_lu_solve_cols(const F* A, int n, const int* src, const F* dinv, F* R, int ldr, int c0, int m) {
+    const int lane = lane_id();
+    F x0[NC], x1[NC];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = tx + gx * j;
-            y[j] = c < m ? R[q * ldr + c] : F(0);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = q + 1 + ty + gy * i;
-            if (r < n) {
-                const F l = A[r * LDP + q];
-                F a[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = tx + gx * j;
-                    a[j] = c < m ? R[r * ldr + c] : F(0);
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = tx + gx * j;
-                    if (c < m) R[r * ldr + c] = a[j] - l * y[j];
-                }
-            }
-        }
-        __syncthreads();
+    for (int j = 0; j < NC; ++j) {
+        const bool cj = c0 + j < m;
+        x0[j] = lane < n && cj ? R[src[lane] * ldr + c0 + j] : F(0);
+        x1[j] = lane + 32 < n && cj ? R[src[lane + 32] * ldr + c0 + j] : F(0);
     }
-    for (int r = ty; r < n; r += gy)
-        for (int c = tx; c < m; c += gx) R[r * ldr + c] *= dinv[r];
-    __syncthreads();
+    __syncwarp();
+    for (int q = 0; q + 1 < n; ++q) {  // unit lower
+        const bool a0 = lane > q && lane < n, a1 = lane + 32 > q && lane + 32 < n;
+        const F l0 = a0 ? A[lane * LDP + q] : F(0), l1 = a1 ? A[(lane + 32) * LDP + q] : F(0);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const F y = __shfl_sync(0xffffffffu, q < 32 ? x0[j] : x1[j], q & 31);
+            if (a0) x0[j] = x0[j] - l0 * y;
+            if (a1) x1[j] = x1[j] - l1 * y;
+        }
+    }
+    const F d0 = lane < n ? dinv[lane] : F(0), d1 = lane + 32 < n ? dinv[lane + 32] : F(0);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        if (lane < n) x0[j] *= d0;
+        if (lane + 32 < n) x1[j] *= d1;
+    }
     for (int q = n - 1; q > 0; --q) {  // unit upper
-        F y[4];
+        const bool a0 = lane < q, a1 = lane + 32 < q;
+        const F u0 = a0 ? A[lane * LDP + q] : F(0), u1 = a1 ? A[(lane + 32) * LDP + q] : F(0);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = tx + gx * j;
-            y[j] = c < m ? R[q * ldr + c] : F(0);
+        for (int j = 0; j < NC; ++j) {
+            const F y = __shfl_sync(0xffffffffu, q < 32 ? x0[j] : x1[j], q & 31);
+            if (a0) x0[j] = x0[j] - u0 * y;
+            if (a1) x1[j] = x1[j] - u1 * y;
         }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = ty + gy * i;
-            if (r < q) {
-                const F u = A[r * LDP + q];
-                F a[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = tx + gx * j;
-                    a[j] = c < m ? R[r * ldr + c] : F(0);
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = tx + gx * j;
-                    if (c < m) R[r * ldr + c] = a[j] - u * y[j];
-                }
-            }
-        }
-        __syncthreads();
     }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        if (c0 + j >= m) continue;
+        if (lane < n) R[lane * ldr + c0 + j] = x0[j];
+        if (lane + 32 < n) R[(lane + 32) * ldr + c0 + j] = x1[j];
+    }
+    __syncwarp();
+}
+
+// One warp solves A x = b for one right-hand side b (stride ldb) with the factor of
+// blu_factor; src[i] is the row of b that the interchanges bring to row i
+// (lu_row_sources).  Lane l holds x_l and x_{l+32}; the eliminations run one column of
+// L (of U) at a time, as in the plain algorithm.  The warp's lanes must all call it.
+__device__ void lu_row_sources(int n, const int* perm, int* src) {  // one thread
+    for (int i = 0; i < n; ++i) src[i] = i;
+    for (int k = 0; k < n; ++k) {
+        const int pk = perm[k], t = src[k];
+        src[k] = src[pk];
+        src[pk] = t;
+    }
+}
+template <typename F>
+__device__ void warp_lu_solve(const F* A, int n, const int* src, const F* dinv, F* b, int ldb) {
+    const int lane = lane_id();
+    F x0 = lane < n ? b[src[lane] * ldb] : F(0);
+    F x1 = lane + 32 < n ? b[src[lane + 32] * ldb] : F(0);
+    __syncwarp();
+    for (int q = 0; q + 1 < n; ++q) {  // unit lower
+        const F y = __shfl_sync(0xffffffffu, q < 32 ? x0 : x1, q & 31);
+        if (lane > q && lane < n) x0 = x0 - A[lane * LDP + q] * y;
+        if (lane + 32 > q && lane + 32 < n) x1 = x1 - A[(lane + 32) * LDP + q] * y;
+    }
+    if (lane < n) x0 *= dinv[lane];
+    if (lane + 32 < n) x1 *= dinv[lane + 32];
+    for (int q = n - 1; q > 0; --q) {  // unit upper
+        const F y = __shfl_sync(0xffffffffu, q < 32 ? x0 : x1, q & 31);
+        if (lane < q) x0 = x0 - A[lane * LDP + q] * y;
+        if (lane + 32 < q) x1 = x1 - A[(lane + 32) * LDP + q] * y;
+    }
+    if (lane < n) b[lane * ldb] = x0;
+    if (lane + 32 < n) b[(lane + 32) * ldb] = x1;
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------- FP32 Hessenberg + QR
@@ -364,7 +374,13 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __re
     }
     __syncthreads();
     blu_factor<float>(A, n, perm, dinv, 1e-30f);
-    blu_solve<float>(A, n, perm, dinv, Km, n, LDP);  // Km = (B - sigma T)^{-1} T
+    {  // Km = (B - sigma T)^{-1} T, one column at a time per warp
+        __shared__ int src[CN];
+        if (tid == 0) lu_row_sources(n, perm, src);
+        __syncthreads();
+        warp_lu_solve_cols<float, CN / (CT / 32)>(A, n, src, dinv, Km, LDP, wid * (CN / (CT / 32)), n);
+        __syncthreads();
+    }
     const long long c_lu = clock64();
     const int kd = n < KRY ? n : KRY;
     if (tid < n) {  // v_0: fixed generic start
@@ -524,7 +540,7 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
     F* Bm = Ai + CN * LDP;
     F* Tm = Bm + CN * LDP;
     __shared__ F vr[CN], vi[CN], tr[CN], ti[CN], dr[CN], di[CN], pre[4 * CN], pim[4 * CN];
-    __shared__ double red[4 * (CT / 32)], s_nrm;
+    __shared__ double red[4 * (CT / 32)];
     __shared__ int perm[CN];
     const long long c_start = clock64();
     const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5, ty = tid >> 4, tx = tid & 15;
@@ -660,15 +676,19 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
             Ar[r * LDP + c] = ur * dr[r] - ui * di[r];
             Ai[r * LDP + c] = ur * di[r] + ui * dr[r];
         }
+    __shared__ int srcp[CN];
+    if (tid == 0) lu_row_sources(n, perm, srcp);
     if (tid < n) {
         vr[tid] = F(1) + (F)tid / (F)n;
         vi[tid] = F(0);
     }
     __syncthreads();
     const long long c_lu = clock64();
+    // four steps of inverse iteration: t = T v by the block (4 threads per row), the
+    // interchanges and the two triangular solves in warp 0 (registers and shuffles; lane l
+    // holds rows l and l + 32), in the order of operations of the plain solve
     const int row = tid & (CN - 1), quarter = tid >> 6;
     for (int it = 0; it < 4; ++it) {
-        // t = T v, 4 threads per row
         if (row < n) {
             F a = F(0), b = F(0);
             const int c1 = min(n, 16 * quarter + 16);
@@ -681,57 +701,71 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
             pim[quarter * CN + row] = b;
         }
         __syncthreads();
-        if (tid < n) {
-            tr[tid] = (pre[tid] + pre[CN + tid]) + (pre[2 * CN + tid] + pre[3 * CN + tid]);
-            ti[tid] = (pim[tid] + pim[CN + tid]) + (pim[2 * CN + tid] + pim[3 * CN + tid]);
-        }
-        __syncthreads();
-        if (tid == 0)
-            for (int k = 0; k < n; ++k) {
-                const int pk = perm[k];
-                if (pk != k) {
-                    F t = tr[k];
-                    tr[k] = tr[pk];
-                    tr[pk] = t;
-                    t = ti[k];
-                    ti[k] = ti[pk];
-                    ti[pk] = t;
+        if (wid == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = lane + 32 * h;
+                if (r < n) {
+                    tr[r] = (pre[r] + pre[CN + r]) + (pre[2 * CN + r] + pre[3 * CN + r]);
+                    ti[r] = (pim[r] + pim[CN + r]) + (pim[2 * CN + r] + pim[3 * CN + r]);
                 }
             }
-        __syncthreads();
-        for (int q = 0; q + 1 < n; ++q) {  // unit lower
-            const int r = q + 1 + tid;
-            if (r < n) {
-                const F yr = tr[q], yi = ti[q], lr = Ar[r * LDP + q], li = Ai[r * LDP + q];
-                tr[r] -= lr * yr - li * yi;
-                ti[r] -= lr * yi + li * yr;
+            __syncwarp();
+            F xr[2], xi[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // row interchanges
+                const int r = lane + 32 * h;
+                xr[h] = r < n ? tr[srcp[r]] : F(0);
+                xi[h] = r < n ? ti[srcp[r]] : F(0);
             }
-            __syncthreads();
-        }
-        if (tid < n) {
-            const F a = tr[tid], b = ti[tid];
-            tr[tid] = a * dr[tid] - b * di[tid];
-            ti[tid] = a * di[tid] + b * dr[tid];
-        }
-        __syncthreads();
-        for (int q = n - 1; q > 0; --q) {  // unit upper
-            if (tid < q) {
-                const F yr = tr[q], yi = ti[q], ur = Ar[tid * LDP + q], ui = Ai[tid * LDP + q];
-                tr[tid] -= ur * yr - ui * yi;
-                ti[tid] -= ur * yi + ui * yr;
+            for (int q = 0; q + 1 < n; ++q) {  // unit lower
+                const F yr = __shfl_sync(0xffffffffu, q < 32 ? xr[0] : xr[1], q & 31);
+                const F yi = __shfl_sync(0xffffffffu, q < 32 ? xi[0] : xi[1], q & 31);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = lane + 32 * h;
+                    if (r > q && r < n) {
+                        const F lr = Ar[r * LDP + q], li = Ai[r * LDP + q];
+                        xr[h] -= lr * yr - li * yi;
+                        xi[h] -= lr * yi + li * yr;
+                    }
+                }
             }
-            __syncthreads();
-        }
-        if (wid == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = lane + 32 * h;
+                if (r < n) {
+                    const F a = xr[h], b = xi[h];
+                    xr[h] = a * dr[r] - b * di[r];
+                    xi[h] = a * di[r] + b * dr[r];
+                }
+            }
+            for (int q = n - 1; q > 0; --q) {  // unit upper
+                const F yr = __shfl_sync(0xffffffffu, q < 32 ? xr[0] : xr[1], q & 31);
+                const F yi = __shfl_sync(0xffffffffu, q < 32 ? xi[0] : xi[1], q & 31);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = lane + 32 * h;
+                    if (r < q) {
+                        const F ur = Ar[r * LDP + q], ui = Ai[r * LDP + q];
+                        xr[h] -= ur * yr - ui * yi;
+                        xi[h] -= ur * yi + ui * yr;
+                    }
+                }
+            }
             double nn = 0.0;
-            for (int r = lane; r < n; r += 32) nn += (double)tr[r] * tr[r] + (double)ti[r] * ti[r];
-            nn = warp_sum(nn);
-            if (lane == 0) s_nrm = 1.0 / sqrt(nn);
-        }
-        __syncthreads();
-        if (tid < n) {
-            vr[tid] = (F)(tr[tid] * s_nrm);
-            vi[tid] = (F)(ti[tid] * s_nrm);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (lane + 32 * h < n) nn += (double)xr[h] * xr[h] + (double)xi[h] * xi[h];
+            nn = 1.0 / sqrt(warp_sum(nn));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = lane + 32 * h;
+                if (r < n) {
+                    vr[r] = (F)(xr[h] * nn);
+                    vi[r] = (F)(xi[h] * nn);
+                }
+            }
         }
         __syncthreads();
     }
@@ -868,7 +902,7 @@ __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restr
     pdl_begin();
     __shared__ F A[CN * LDP];
     __shared__ F R[CN * PINV_COLS];
-    __shared__ F y[CN], dinv[CN], red[CT / 32], s_nrm;
+    __shared__ F y[CN], dinv[CN], red[CT / 32];
     __shared__ int perm[CN];
     const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
     const long long c_start = clock64();
@@ -890,21 +924,22 @@ __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restr
     mx = F(0);
     for (int q = 0; q < CT / 32; ++q) mx = mx > red[q] ? mx : red[q];
     const F rel_floor = sizeof(F) == 8 ? F(1e-14) : F(1e-6f);
+    __shared__ int src[CN];
     blu_factor<F>(A, n, perm, dinv, rel_floor * (mx > F(0) ? mx : F(1)));
+    if (tid == 0) lu_row_sources(n, perm, src);
     if (tid < n) y[tid] = F(1);
     __syncthreads();
-    for (int it = 0; it < 2; ++it) {
-        blu_solve<F>(A, n, perm, dinv, y, 1, 1);
-        if (wid == 0) {
+    if (wid == 0) {  // two steps of inverse iteration, in one warp
+        for (int it = 0; it < 2; ++it) {
+            warp_lu_solve<F>(A, n, src, dinv, y, 1);
             double nn = 0.0;
             for (int r = lane; r < n; r += 32) nn += (double)y[r] * y[r];
-            nn = warp_sum(nn);
-            if (lane == 0) s_nrm = (F)(1.0 / sqrt(nn));
+            const F sc = (F)(1.0 / sqrt(warp_sum(nn)));
+            for (int r = lane; r < n; r += 32) y[r] *= sc;
+            __syncwarp();
         }
-        __syncthreads();
-        if (tid < n) y[tid] *= s_nrm;
-        __syncthreads();
     }
+    __syncthreads();
     const F zs = (F)(1.0 / sqrt((double)n)), ninv = (F)(1.0 / (double)n);
     for (int idx = tid; idx < n * n; idx += CT) {
         const int r = idx / n, c = idx - r * n;
@@ -917,8 +952,11 @@ __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restr
     __syncthreads();
     const long long c_null = clock64();
     blu_factor<F>(A, n, perm, dinv, pivot_tiny<F>());
+    if (tid == 0) lu_row_sources(n, perm, src);
+    __syncthreads();
     const long long c_lu = clock64();
-    blu_solve<F>(A, n, perm, dinv, R, mc, mc);
+    if (wid < mc) warp_lu_solve<F>(A, n, src, dinv, R + wid, mc);  // one right-hand side per warp
+    __syncthreads();
     const long long c_solve = clock64();
     int bad = 0;
     for (int idx = tid; idx < n * mc; idx += CT) {
