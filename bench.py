@@ -137,7 +137,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(precision="mixed"):
-        s = bamg.Solver(rp, ci, v, r=R, levels=20, grid=ch.grid, precision=precision)
+        s = bamg.Solver(rp, ci, v, r=R, levels=20, grid=ch.grid, precision=precision,
+                        device_loop=args.device_loop)
         _, st = s.solve(TOL, out=x)
         return s, st
 
@@ -293,7 +294,7 @@ def _time_relax(bamg, B, X, ncols, col0, reps, stream, sweeps=20):
 
 # DRAM traffic of one finest-level k_smooth launch from the ncu capture summarised in
 # profiles/k_smooth_tandem256_level0.md, valid while the kernel's source is unchanged.
-SMOOTH_TRAFFIC = {"bytes": 3145216, "source_sha1": "41b05b09bd141cf1ec89fd512941eb98d4a0e1a7"}
+SMOOTH_TRAFFIC = {"bytes": 3144960, "source_sha1": "b637629b77941a011075580bf1780564467ef695"}
 
 
 def _kernel_source_sha1():
@@ -574,6 +575,9 @@ def main():
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-interpolation line")
     ap.add_argument("--no-large", action="store_true", help="skip the 2^20-point Delaunay line")
     ap.add_argument("--large-only", action="store_true", help="run only the 2^20-point Delaunay line")
+    ap.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
+                    help="0: one graph launch per Arnoldi step (same kernels; ncu lists kernels of a "
+                         "graph's conditional body only this way)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -151,6 +151,9 @@ int bamg_solve(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st)
  * As[k], r[k], levels[k], opts[k] as for bamg_setup (opts[k].stream is ignored);
  * xs[k]: n_k doubles for the result, device memory unless flags has BAMG_X_HOST
  * (BAMG_X_GUESS is not accepted).  st (may be NULL) receives one entry per chain.
+ * With more than one worker, opts[k].device_loop is taken as 0 (one graph launch per
+ * Arnoldi step): conditional-node graphs in concurrent threads slowed the other threads'
+ * setups more than the device-side loop saves.
  * Returns BAMG_OK if every chain succeeded, else the first failing chain's code (its
  * message in bamg_last_error); the other chains are still solved. */
 int bamg_solve_batch(int nchains, const bamg_csr* As, const int* r, const int* levels, const bamg_opts* opts,

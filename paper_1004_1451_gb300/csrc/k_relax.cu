@@ -110,11 +110,11 @@ void launch_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* 
 // flight the thread loads the next row's first JB column indices and values and the row
 // pointers of the row after it, so the three dependent loads of a row (row pointers,
 // entries, gathers) overlap with earlier rows' work.  Entries beyond the first JB of a
-// row are read in predicated batches of JB.
+// row are read in predicated batches of JB; JB is 5 for matrices with at most five
+// entries per row on average (grid walks, tandem queues), else 6.
 constexpr int JAC_BLOCKS_PER_SM = 2;
-constexpr int JB = 6;
 
-template <typename T, bool SHIFT>
+template <typename T, bool SHIFT, int JB>
 __global__ void __launch_bounds__(256, JAC_BLOCKS_PER_SM)
     k_jacobi(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
              const T* __restrict__ tv, const T* __restrict__ dB, const T* __restrict__ dinvB, const T* __restrict__ dT,
@@ -280,13 +280,20 @@ void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, con
                                                       (int64_t)sm_count() * JAC_BLOCKS_PER_SM);
     T* src = X;
     T* dst = work;
+    const bool short_rows = (int64_t)B.nnz <= 5 * (int64_t)B.n;
     for (int k = 0; k < nu; ++k) {
-        if (d_lambda)
-            BAMG_LAUNCH((k_jacobi<T, true>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda,
+        if (d_lambda && short_rows)
+            BAMG_LAUNCH((k_jacobi<T, true, 5>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda,
                         ncols, src, dst, ld, col0, nvec, omega);
+        else if (d_lambda)
+            BAMG_LAUNCH((k_jacobi<T, true, 6>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda,
+                        ncols, src, dst, ld, col0, nvec, omega);
+        else if (short_rows)
+            BAMG_LAUNCH((k_jacobi<T, false, 5>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT,
+                        d_lambda, ncols, src, dst, ld, col0, nvec, omega);
         else
-            BAMG_LAUNCH((k_jacobi<T, false>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda,
-                        ncols, src, dst, ld, col0, nvec, omega);
+            BAMG_LAUNCH((k_jacobi<T, false, 6>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT,
+                        d_lambda, ncols, src, dst, ld, col0, nvec, omega);
         T* t = src;
         src = dst;
         dst = t;

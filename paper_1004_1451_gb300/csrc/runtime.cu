@@ -1103,6 +1103,10 @@ int bamg_solve_batch(int nchains, const bamg_csr* As, const int* r, const int* l
             const int k = order[q];
             bamg_opts o = opts[k];
             o.stream = ws;
+            // with several host threads, graphs holding a WHILE conditional node slowed the
+            // other threads' setups about fourfold (512-chain mixture, 8 workers), more than
+            // the device-side loop saves: one graph launch per Arnoldi step here
+            if (nworkers > 1) o.device_loop = 0;
             bamg_handle* h = nullptr;
             bamg_stats local{};
             int code = bamg_setup(&As[k], r[k], levels[k], &o, &h);
