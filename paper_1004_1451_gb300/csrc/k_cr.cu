@@ -31,9 +31,11 @@ __device__ __forceinline__ bool beats(uint64_t pi, int i, uint64_t pj, int j) { 
 
 __global__ void k_mis_step(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const int32_t* __restrict__ rpT, const int32_t* __restrict__ ciT,
-                           const uint8_t* __restrict__ und, uint8_t* __restrict__ win, uint64_t seed, uint64_t stream) {
+                           const uint8_t* __restrict__ und, uint8_t* __restrict__ win, uint64_t seed, uint64_t stream,
+                           int* __restrict__ left) {
     pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *left = 0;  // counted by this round's k_mis_remove
     if (i >= n) return;
     if (!und[i]) {
         win[i] = 0;
@@ -77,16 +79,21 @@ __global__ void k_mis_remove(int n, const int32_t* __restrict__ rp, const int32_
     atomicAdd(left, 1);
 }
 
-// chosen |= independent set of the candidates (und on entry; consumed).
+// chosen |= independent set of the candidates (und on entry; consumed).  The host reads
+// the count of undecided candidates every MIS_CHECK rounds: rounds after the last
+// decision change nothing (no candidate is left), so the result is that of a check
+// after every round.
+constexpr int MIS_CHECK = 4;
 static void independent_set(int n, const int32_t* rp, const int32_t* ci, const int32_t* rpT, const int32_t* ciT,
                             uint8_t* und, uint8_t* chosen, uint64_t seed, uint64_t stream, cudaStream_t s) {
     TmpBuf<uint8_t> win(n, s);
     TmpBuf<int> left(1, s);
     const unsigned g = blocks_for(n, 256);
-    for (int round = 0; round <= n; ++round) {
-        BAMG_CK(cudaMemsetAsync(left.get(), 0, sizeof(int), s));
-        BAMG_LAUNCH(k_mis_step, g, 256, 0, s, n, rp, ci, rpT, ciT, und, win.get(), seed, stream);
-        BAMG_LAUNCH(k_mis_remove, g, 256, 0, s, n, rp, ci, rpT, ciT, und, win.get(), chosen, left.get());
+    for (int round = 0; round <= n; round += MIS_CHECK) {
+        for (int k = 0; k < MIS_CHECK; ++k) {
+            BAMG_LAUNCH(k_mis_step, g, 256, 0, s, n, rp, ci, rpT, ciT, und, win.get(), seed, stream, left.get());
+            BAMG_LAUNCH(k_mis_remove, g, 256, 0, s, n, rp, ci, rpT, ciT, und, win.get(), chosen, left.get());
+        }
         int h = 0;
         BAMG_CK(cudaMemcpyAsync(&h, left.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CK(cudaStreamSynchronize(s));
@@ -186,8 +193,7 @@ int coarsen_cr(const MatView<T>& B, int level, uint64_t seed, double theta, int 
     BAMG_CK(cudaMemsetAsync(cursor.get(), 0, sizeof(int32_t) * n, s));
     BAMG_LAUNCH(k_tcount, g, 256, 0, s, n, B.rp, B.ci, cnt.get());
     exclusive_scan(cnt.get(), rpT.get(), n, s);
-    const int nT = read_int(rpT.get() + n, s);
-    TmpBuf<int32_t> ciT(nT > 0 ? nT : 1, s);
+    TmpBuf<int32_t> ciT(B.nnz > 0 ? B.nnz : 1, s);  // bound: the off-diagonal entries of B
     BAMG_LAUNCH(k_tfill, g, 256, 0, s, n, B.rp, B.ci, rpT.get(), cursor.get(), ciT.get());
     TmpBuf<uint8_t> und(n, s), cand(n, s);
     BAMG_CK(cudaMemsetAsync(cf, 0, n, s));
