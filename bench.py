@@ -220,6 +220,7 @@ def run_ours(args):
     batch = batch_line(args) if not args.no_batch else None
     learned = learned_line(args) if not args.no_learned else None
     large = large_line(args) if not args.no_large else None
+    small = small_line(args)
     cpu = cpu_baseline() if not args.no_cpu else None
     nnz_a = int(ch.nnz)
     out = {
@@ -237,7 +238,7 @@ def run_ours(args):
         "fp64_ms": round(float(np.median(fp64)), 4), "fp64_iterations": st64["iterations"],
         "speedup_mixed_vs_fp64": round(float(np.median(fp64)) / ms, 3),
         "gpu_launches": int(round(launches)),
-        "roofline": roof, "spmm_hbm": probe, "batch": batch, "learned": learned, "large": large, "cpu_baseline": cpu, "clocks": ck,
+        "roofline": roof, "spmm_hbm": probe, "batch": batch, "learned": learned, "large": large, "small": small, "cpu_baseline": cpu, "clocks": ck,
     }
     _line(out)
 
@@ -381,19 +382,21 @@ def batch_line(args, workers=8):
     chains = batched_mixture(0)
     mats = [(torch.tensor(c.row_ptr, device="cuda"), torch.tensor(c.col, device="cuda"),
              torch.tensor(c.val, device="cuda")) for c in chains]
-    opts = [dict(grid=c.grid, precision="mixed", **(BD_OPTS if c.kind == "birth_death" else {})) for c in chains]
+    def opts_for(prec):
+        return [dict(grid=c.grid, precision=prec, **(BD_OPTS if c.kind == "birth_death" else {})) for c in chains]
 
-    def once():
+    def once(prec="mixed"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         try:
-            _, st = bamg.solve_batch(mats, 8, 20, TOL, opts=opts, workers=workers)
+            _, st = bamg.solve_batch(mats, 8, 20, TOL, opts=opts_for(prec), workers=workers)
         except bamg.BamgError as e:
             st = e.stats
         return time.perf_counter() - t0, st
 
     once()  # warm-up
     dt, st = once()
+    dt64, st64 = once("fp64")
     ok = [s_["status"] == 0 for s_ in st]
     bd = [c.kind == "birth_death" for c in chains]
     return {"workload": BATCH_WORKLOAD, "chains": len(chains), "states": int(sum(c.n for c in chains)),
@@ -402,6 +405,8 @@ def batch_line(args, workers=8):
             "converged_grid": int(sum(o and not b for o, b in zip(ok, bd))),
             "converged_birth_death": int(sum(o and b for o, b in zip(ok, bd))),
             "gmres_iterations_total": int(sum(s_["iterations"] for s_ in st)),
+            "fp64": {"value": round(len(chains) / dt64, 2), "unit": "chains/s", "ms": round(dt64 * 1e3, 1),
+                     "converged": int(sum(s_["status"] == 0 for s_ in st64))},
             "note": "birth-death chains that stop at max_it count in the time; host-timed (threads and streams)"}
 
 
@@ -465,8 +470,9 @@ def learned_line(args, train_rows=1 << 20, epochs=10, batch=4096):
     out = {"workload": LEARNED_WORKLOAD, "n": test.n, "train_rows": rows, "epochs": epochs, "batch": batch,
            "data_s": round(data_s, 2), "train_s": round(train_s, 2), "train_loss_first_last": [round(hist[0], 5),
                                                                                                round(hist[-1], 5)]}
-    for name, kw in (("ls", {}), ("learned", {"interp": "learned", "model": model})):
-        s, setup_ms = _timed(lambda: bamg.Solver(*A, r=R, levels=20, grid=test.grid, precision="mixed", **kw), 5)
+    for name, prec, kw in (("ls", "mixed", {}), ("learned", "mixed", {"interp": "learned", "model": model}),
+                           ("ls_fp64", "fp64", {})):
+        s, setup_ms = _timed(lambda: bamg.Solver(*A, r=R, levels=20, grid=test.grid, precision=prec, **kw), 5)
         rho = s.vcycle_factor(20)
         (x, st), solve_ms = _timed(lambda: s.solve(TOL), 3)
         err = float(np.abs(x.cpu().numpy() - xe).sum() / np.abs(xe).sum())
@@ -474,6 +480,33 @@ def learned_line(args, train_rows=1 << 20, epochs=10, batch=4096):
                      "vcycle_factor": round(rho, 4), "rel_l1_vs_exact": err, "levels": s.info()["n"]}
         s.close()
     model.close()
+    return out
+
+
+SMALL_WORKLOAD = "random walk on a 64x64 grid (4,096 states, 4-neighbour, probability 1/deg); r=8"
+
+
+def small_line(args, reps=5):
+    """The 64x64 grid walk in plain FP64 and in mixed precision: setup and solve times (CUDA
+    events), iterations, accuracy against the closed form x ~ degree."""
+    import torch
+
+    import paper_1004_1451_gb300 as bamg
+    from workloads import grid_walk
+
+    ch = grid_walk(64)
+    A = (torch.tensor(ch.row_ptr, device="cuda"), torch.tensor(ch.col, device="cuda"),
+         torch.tensor(ch.val, device="cuda"))
+    deg = np.asarray(ch.meta["degree"], dtype=np.float64)
+    xe = deg / deg.sum()
+    out = {"workload": SMALL_WORKLOAD, "n": ch.n, "nnz_A": int(ch.nnz)}
+    for prec in ("fp64", "mixed"):
+        s, setup_ms = _timed(lambda: bamg.Solver(*A, r=8, levels=20, grid=ch.grid, precision=prec), reps)
+        (x, st), solve_ms = _timed(lambda: s.solve(TOL), reps)
+        out[prec] = {"setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
+                     "ms": round(setup_ms + solve_ms, 3), "gmres_iterations": st["iterations"],
+                     "rel_l1_vs_exact": float(np.abs(x.cpu().numpy() - xe).sum()), "levels": s.info()["n"]}
+        s.close()
     return out
 
 
@@ -501,9 +534,16 @@ def large_line(args, reps=3):
     err = float(np.abs(x.cpu().numpy() - xe).sum())
     info = s.info()
     s.close()
+    # the plain FP64 method on the same chain
+    s, setup64 = _timed(lambda: bamg.Solver(*A, r=16, levels=30, precision="fp64", coarsen="cr"), reps)
+    (x, st64), solve64 = _timed(lambda: s.solve(TOL), reps)
+    err64 = float(np.abs(x.cpu().numpy() - xe).sum())
+    s.close()
     return {"workload": LARGE_WORKLOAD, "n": ch.n, "nnz_A": int(ch.nnz), "setup_ms": round(setup_ms, 2),
             "solve_ms": round(solve_ms, 2), "ms": round(setup_ms + solve_ms, 2), "gmres_iterations": st["iterations"],
             "rel_l1_vs_exact": err, "levels": info["n"], "op_complexity": round(info["op_complexity"], 3),
+            "fp64": {"setup_ms": round(setup64, 2), "solve_ms": round(solve64, 2), "ms": round(setup64 + solve64, 2),
+                     "gmres_iterations": st64["iterations"], "rel_l1_vs_exact": err64},
             "generation_s": round(gen_s, 1)}
 
 
@@ -528,9 +568,15 @@ def cpu_baseline():
     t0 = time.perf_counter()
     x, H, st = ob.stationary(A, R, 20, TOL, ob.Opts(), grid=ch.grid)
     dt = time.perf_counter() - t0
+    from workloads import grid_walk
+
+    g = grid_walk(64)
+    t0 = time.perf_counter()
+    ob.stationary(g.to_scipy(), 8, 20, TOL, ob.Opts(), grid=g.grid)
+    dt_small = time.perf_counter() - t0
     return {"value": round(dt * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
             "sample": "one full setup + FGMRES solve of the same chain to 1e-10 (FP64 numpy/scipy)",
-            "iterations": st["iterations"]}
+            "iterations": st["iterations"], "grid64_r8_ms": round(dt_small * 1e3, 1)}
 
 
 # ------------------------------------------------------------------ reference arm
