@@ -514,7 +514,7 @@ LARGE_WORKLOAD = ("Delaunay triangulation of 2^20 points U[0,1]^2 (seed 0), rand
                   "r=16; compatible-relaxation coarsening; mixed")
 
 
-def large_line(args, reps=3):
+def large_line(args):
     """The 2^20-point Delaunay walk: setup and solve times (CUDA events), iterations,
     accuracy against the closed form x ~ degree, and the SpMM sweep on its finest level."""
     import torch
@@ -529,7 +529,9 @@ def large_line(args, reps=3):
          torch.tensor(ch.val, device="cuda"))
     deg = np.asarray(ch.meta["degree"], dtype=np.float64)
     xe = deg / deg.sum()
-    s, setup_ms = _timed(lambda: bamg.Solver(*A, r=16, levels=30, precision="mixed", coarsen="cr"), reps)
+    reps = args.large_reps
+    s, setup_ms = _timed(lambda: bamg.Solver(*A, r=16, levels=30, precision="mixed", coarsen="cr",
+                                             device_loop=args.device_loop), reps)
     (x, st), solve_ms = _timed(lambda: s.solve(TOL), reps)
     err = float(np.abs(x.cpu().numpy() - xe).sum())
     info = s.info()
@@ -621,6 +623,7 @@ def main():
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-interpolation line")
     ap.add_argument("--no-large", action="store_true", help="skip the 2^20-point Delaunay line")
     ap.add_argument("--large-only", action="store_true", help="run only the 2^20-point Delaunay line")
+    ap.add_argument("--large-reps", type=int, default=3, help="timed repetitions of the 2^20-point Delaunay line")
     ap.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
                     help="0: one graph launch per Arnoldi step (same kernels; ncu lists kernels of a "
                          "graph's conditional body only this way)")

@@ -129,6 +129,31 @@ __global__ void k_frelax(int n, const int32_t* __restrict__ rp, const int32_t* _
     un[i] = u[i] - (omega * (1.0 / d)) * s;
 }
 
+// k_frelax with G lanes per row (long rows of coarse levels): strided partial sums added
+// by a butterfly; the lane holding the diagonal contributes d, the others 0.
+template <typename T, int G>
+__global__ void k_frelax_grp(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const T* __restrict__ bv, const uint8_t* __restrict__ cf, const double* __restrict__ u,
+                             double* __restrict__ un, double omega) {
+    pdl_begin();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / G), sub = (int)(t % G);
+    double s = 0.0, d = 0.0;
+    const bool live = i < n && !cf[i];
+    if (live)
+        for (int p = rp[i] + sub; p < rp[i + 1]; p += G) {
+            const int j = ci[p];
+            if (j == i) d = (double)bv[p];
+            if (!cf[j]) s += (double)bv[p] * u[j];
+        }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        d += __shfl_xor_sync(0xffffffffu, d, o);
+    }
+    if (i < n && sub == 0) un[i] = live ? u[i] - (omega * (1.0 / d)) * s : 0.0;
+}
+
 __global__ void k_cr_norms(int n, const double* __restrict__ u0, const double* __restrict__ u,
                            double* __restrict__ partial) {
     pdl_begin();
@@ -187,6 +212,7 @@ int coarsen_cr(const MatView<T>& B, int level, uint64_t seed, double theta, int 
                uint8_t* cf, int32_t* cidx, int* nc_out, cudaStream_t s) {
     const int n = B.n;
     const unsigned g = blocks_for(n, 256);
+    const int G = lanes_per_row(n, B.nnz);
     // transpose pattern for the undirected neighbourhoods
     TmpBuf<int32_t> cnt(n, s), rpT(n + 1, s), cursor(n, s);
     BAMG_CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * n, s));
@@ -209,7 +235,17 @@ int coarsen_cr(const MatView<T>& B, int level, uint64_t seed, double theta, int 
         double* bufs[2] = {ua.get(), ub.get()};
         for (int k = 0; k < nu; ++k) {
             double* nxt = bufs[k & 1];
-            BAMG_LAUNCH(k_frelax<T>, g, 256, 0, s, n, B.rp, B.ci, B.v, cf, cur, nxt, omega);
+            const unsigned gg = blocks_for((int64_t)n * G, 256);
+            switch (G) {
+                case 1: BAMG_LAUNCH(k_frelax<T>, g, 256, 0, s, n, B.rp, B.ci, B.v, cf, cur, nxt, omega); break;
+                case 4: BAMG_LAUNCH((k_frelax_grp<T, 4>), gg, 256, 0, s, n, B.rp, B.ci, B.v, cf, cur, nxt, omega); break;
+                case 8: BAMG_LAUNCH((k_frelax_grp<T, 8>), gg, 256, 0, s, n, B.rp, B.ci, B.v, cf, cur, nxt, omega); break;
+                case 16:
+                    BAMG_LAUNCH((k_frelax_grp<T, 16>), gg, 256, 0, s, n, B.rp, B.ci, B.v, cf, cur, nxt, omega);
+                    break;
+                default:
+                    BAMG_LAUNCH((k_frelax_grp<T, 32>), gg, 256, 0, s, n, B.rp, B.ci, B.v, cf, cur, nxt, omega);
+            }
             prev = const_cast<double*>(cur);
             cur = nxt;
         }

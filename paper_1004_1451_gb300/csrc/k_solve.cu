@@ -94,6 +94,69 @@ __global__ void k_resid(int n, const int32_t* __restrict__ rp, const int32_t* __
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) r[i] = b[i] - row_Bx(i, rp, ci, bv, x);
 }
+// The same three kernels with G lanes per row (G = 4 .. 32), for levels whose rows are
+// long (the coarse levels of compatible-relaxation hierarchies): the lanes of a group take
+// the entries p0 + lane, p0 + lane + G, ... and add their partial sums by a butterfly.
+// Every lane of a warp takes part in the shuffles, also for rows past n.
+template <int G, typename T, typename F>
+__device__ __forceinline__ T row_sum_grp(int i, int n, int sub, const int32_t* __restrict__ rp,
+                                         const int32_t* __restrict__ ci, const T* __restrict__ bv, F f) {
+    T s = T(0);
+    if (i < n)
+        for (int p = rp[i] + sub; p < rp[i + 1]; p += G) s += bv[p] * f(ci[p]);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+template <typename T, int G>
+__global__ void k_presmooth2_grp(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const T* __restrict__ bv, const T* __restrict__ dinv, const T* __restrict__ b,
+                                 T* __restrict__ y, T omega) {
+    pdl_begin();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / G), sub = (int)(t % G);
+    const T bx = row_sum_grp<G, T>(i, n, sub, rp, ci, bv, [&](int j) { return (omega * dinv[j]) * b[j]; });
+    if (i < n && sub == 0) {
+        const T x1 = (omega * dinv[i]) * b[i];
+        y[i] = x1 + (omega * dinv[i]) * (b[i] - bx);
+    }
+}
+template <typename T, int G>
+__global__ void k_smooth_grp(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const T* __restrict__ bv, const T* __restrict__ dinv, const T* __restrict__ b,
+                             const T* __restrict__ x, T* __restrict__ y, T omega, T* __restrict__ Z,
+                             const int* __restrict__ dj) {
+    pdl_begin();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / G), sub = (int)(t % G);
+    const T bx = row_sum_grp<G, T>(i, n, sub, rp, ci, bv, [&](int j) { return x[j]; });
+    if (i < n && sub == 0) {
+        const T v = x[i] + (omega * dinv[i]) * (b[i] - bx);
+        y[i] = v;
+        if (Z) Z[(int64_t)(*dj) * n + i] = v;
+    }
+}
+template <typename T, int G>
+__global__ void k_resid_grp(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const T* __restrict__ bv, const T* __restrict__ b, const T* __restrict__ x,
+                            T* __restrict__ r) {
+    pdl_begin();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / G), sub = (int)(t % G);
+    const T bx = row_sum_grp<G, T>(i, n, sub, rp, ci, bv, [&](int j) { return x[j]; });
+    if (i < n && sub == 0) r[i] = b[i] - bx;
+}
+#define BAMG_LAUNCH_GRP(G_, kern, n_, s_, ...)                                                          \
+    do {                                                                                               \
+        const unsigned gg_ = blocks_for((int64_t)(n_) * (G_), 256);                                    \
+        switch (G_) {                                                                                  \
+            case 4: BAMG_LAUNCH_PDL((kern<T, 4>), gg_, 256, 0, s_, __VA_ARGS__); break;                \
+            case 8: BAMG_LAUNCH_PDL((kern<T, 8>), gg_, 256, 0, s_, __VA_ARGS__); break;                \
+            case 16: BAMG_LAUNCH_PDL((kern<T, 16>), gg_, 256, 0, s_, __VA_ARGS__); break;              \
+            default: BAMG_LAUNCH_PDL((kern<T, 32>), gg_, 256, 0, s_, __VA_ARGS__); break;             \
+        }                                                                                              \
+    } while (0)
+
 template <typename T>
 __global__ void k_restrict(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
                            const T* __restrict__ qv, const T* __restrict__ r, T* __restrict__ bc) {
@@ -381,13 +444,21 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         const VLevel<T>& v = lv[l];
         const int n = v.B.n;
         const unsigned g = blocks_for(n, 256);
+        const int G = lanes_per_row(n, v.B.nnz);
         T* x = v.x;
         T* t = v.r;
         if (nu_pre >= 2) {
-            BAMG_LAUNCH_PDL(k_presmooth2<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, omega);
+            if (G == 1)
+                BAMG_LAUNCH_PDL(k_presmooth2<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, omega);
+            else
+                BAMG_LAUNCH_GRP(G, k_presmooth2_grp, n, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, omega);
             for (int k = 2; k < nu_pre; ++k) {
-                BAMG_LAUNCH_PDL(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
-                            (T*)nullptr, (const int*)nullptr);
+                if (G == 1)
+                    BAMG_LAUNCH_PDL(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
+                                    (T*)nullptr, (const int*)nullptr);
+                else
+                    BAMG_LAUNCH_GRP(G, k_smooth_grp, n, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, (const T*)x, t,
+                                    omega, (T*)nullptr, (const int*)nullptr);
                 T* q = x;
                 x = t;
                 t = q;
@@ -397,7 +468,10 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         } else {
             BAMG_CK(cudaMemsetAsync(x, 0, sizeof(T) * n, s));
         }
-        BAMG_LAUNCH_PDL(k_resid<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.b, x, t);
+        if (G == 1)
+            BAMG_LAUNCH_PDL(k_resid<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.b, x, t);
+        else
+            BAMG_LAUNCH_GRP(G, k_resid_grp, n, s, n, v.B.rp, v.B.ci, v.B.v, v.b, (const T*)x, t);
         const int nc = lv[l + 1].B.n;
         BAMG_LAUNCH_PDL(k_restrict<T>, blocks_for(nc, 256), 256, 0, s, nc, v.qrp, v.qci, v.qv, t, lv[l + 1].b);
         xcur[l] = x;
@@ -451,10 +525,15 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         T* x = xcur[l];
         T* t = xtmp[l];
         T* zl = (l == 0) ? Z : nullptr;
+        const int G = lanes_per_row(n, v.B.nnz);
         BAMG_LAUNCH_PDL(k_prolong_add<T>, g, 256, 0, s, n, v.P.c, v.P.pcol, v.P.pval, v.P.pcnt, xcur[l + 1], x);
         for (int k = 0; k < nu_post; ++k) {
-            BAMG_LAUNCH_PDL(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
-                        k == nu_post - 1 ? zl : (T*)nullptr, dj);
+            if (G == 1)
+                BAMG_LAUNCH_PDL(k_smooth<T>, g, 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, x, t, omega,
+                                k == nu_post - 1 ? zl : (T*)nullptr, dj);
+            else
+                BAMG_LAUNCH_GRP(G, k_smooth_grp, n, s, n, v.B.rp, v.B.ci, v.B.v, v.dinv, v.b, (const T*)x, t, omega,
+                                k == nu_post - 1 ? zl : (T*)nullptr, dj);
             T* q = x;
             x = t;
             t = q;

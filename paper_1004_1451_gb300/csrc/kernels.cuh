@@ -22,6 +22,13 @@ struct EllView {
     const int32_t* pcnt = nullptr;
 };
 
+// Lanes per row for sparse row walks on a matrix with nnz entries in n rows: 1 (one thread
+// per row) below 12 entries per row on average, then 4, 8, 16 or 32.
+inline int lanes_per_row(int n, int64_t nnz) {
+    const double avg = n > 0 ? (double)nnz / n : 0.0;
+    return avg < 12.0 ? 1 : avg < 24.0 ? 4 : avg < 48.0 ? 8 : avg < 96.0 ? 16 : 32;
+}
+
 // ------------------------------------------------------------------ k_relax.cu
 template <typename T>
 void launch_tv_init(int n, int ncols, int ld, int col0, uint64_t seed, double lo, double hi, T* X, cudaStream_t s);
