@@ -381,12 +381,33 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
         // and no deeper once mmax coarse points are known: deeper ones would rank after them
         if ((d > z && ncvis > 0) || ncvis >= mmax) break;
         bool fonly = false;  // visited list full: record only coarse nodes for the rest of this depth
-        for (int f = fs; f < fe; ++f) {
-            const int u = vis[f];
-            const int p0 = rp[u], p1 = rp[u + 1];
-            for (int base = p0; base < p1; base += 32) {
-                const int p = base + lane;
-                const int v = p < p1 ? ci[p] : -1;
+        // the frontier's rows, 32 frontier nodes at a time: the lanes load the row pointers
+        // together, lay the rows end to end (warp prefix sum), and take 32 entries of the
+        // concatenation per batch (the same entries in the same order as row by row)
+        for (int f0 = fs; f0 < fe; f0 += 32) {
+            const int fu = f0 + lane;
+            const int u = fu < fe ? vis[fu] : -1;
+            const int ra = u >= 0 ? rp[u] : 0;
+            const int rlen = u >= 0 ? rp[u + 1] - ra : 0;
+            int incl = rlen;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            for (int e0 = 0; e0 < total; e0 += 32) {
+                const int e = e0 + lane;
+                int k = 0;  // the lane whose row holds entry e: the first with incl > e
+#pragma unroll
+                for (int st = 16; st >= 1; st >>= 1) {
+                    const int ic = __shfl_sync(0xffffffffu, incl, k + st - 1);
+                    if (ic <= e) k += st;
+                }
+                const int ka = __shfl_sync(0xffffffffu, ra, k);
+                const int kx = __shfl_sync(0xffffffffu, incl - rlen, k);
+                const int v = e < total ? ci[ka + e - kx] : -1;
                 const bool isnew = v >= 0 && !vis_contains(hs, HS, v);
                 const int key = isnew ? v : -1 - lane;
                 const unsigned grp = __match_any_sync(0xffffffffu, key);
@@ -608,7 +629,7 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
 // CAP-entry list is appended to ovf_list (or flags err when ovf_list is null).  Second
 // pass (list != nullptr): persistent warps over the *list_count points of list.
 template <typename T, int CAP, int WARPS, bool EXTRA>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, (WARPS > 1 && sizeof(T) == 4) ? 6 : 1)  // FP32: 6 blocks/SM
     k_ls_fit(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
              const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx, const T* __restrict__ X, int ncols,
              int ld, const double* __restrict__ w, int z, int mmax, int c, double ridge, int32_t* __restrict__ pcol,

@@ -72,6 +72,32 @@ def test_vcycle_mixed_close_to_oracle(oracle_H):
     assert rel(z, ob.vcycle(H, v)) < 1e-5
 
 
+@pytest.fixture(scope="module")
+def oracle_H_cr():
+    # compatible-relaxation hierarchy whose coarse levels have long rows (16-26 entries on
+    # average) and are too large for the single-block tail: the V-cycle runs them with the
+    # group-per-row kernels
+    ch = delaunay_walk(40000, 3)
+    H = ob.setup(ch.to_scipy(), 8, 12, ob.Opts(coarsen="cr"))
+    return ch, H
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_vcycle_long_rows_matches_oracle(oracle_H_cr, precision, bound):
+    torch = _torch()
+    ch, H = oracle_H_cr
+    grouped = [l for l, lv in enumerate(H.levels[:-1])
+               if lv.B.nnz >= 12 * lv.B.shape[0] and (lv.B.shape[0] > 1024 or lv.B.nnz > 16384)]
+    assert grouped, "no level takes the group-per-row kernels"
+    s = _bamg().import_hierarchy(_levels_of(H), H.pinv, H.x_init, precision=precision)
+    rng = np.random.default_rng(6)
+    for _ in range(2):
+        v = rng.standard_normal(ch.n)
+        v -= v.mean()
+        z = s.vcycle(torch.tensor(v, device="cuda")).cpu().numpy()
+        assert rel(z, ob.vcycle(H, v)) < bound
+
+
 def test_fgmres_matches_oracle(oracle_H):
     ch, H = oracle_H
     s = _bamg().import_hierarchy(_levels_of(H), H.pinv, H.x_init)
