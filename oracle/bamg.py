@@ -578,6 +578,23 @@ def _build_interp(lv: Level, X: np.ndarray, active: np.ndarray, opts: Opts):
     return Xh, w, P, Q
 
 
+def up_level(lv, Vc: np.ndarray, lam: np.ndarray, opts: Opts):
+    """One level of the upward pass of Algorithm 3: V = P Vc; nu_ev omega-Jacobi sweeps on
+    (B - lam_i T) x^(i) = 0; the Rayleigh-type update lambda_i = <B x, x> / <T x, x> for
+    i >= 1 (lambda_0, the state vector's, stays 0); reading R9: x^(i) is selected for the
+    rebuilt test set when |delta lambda_i| / |lambda_i| > ev_change_tol, the state vector
+    always.  lv supplies P, B, T.  Returns (V, new lambda, selection)."""
+    V = lv.P @ Vc
+    V = jacobi_shifted(lv.B, lv.T, V, lam, opts.omega, opts.nu_ev)
+    BV, TV = lv.B @ V, lv.T @ V
+    new = np.einsum("nk,nk->k", BV, V) / np.einsum("nk,nk->k", TV, V)
+    new[0] = 0.0
+    change = np.abs(new - lam) / np.maximum(np.abs(lam), 1e-300)
+    sel = change > opts.ev_change_tol
+    sel[0] = True
+    return V, new, sel
+
+
 def setup(A, r: int, levels: int, opts: Opts | None = None, grid: tuple | None = None) -> Hierarchy:
     """Bootstrap setup: one MLE pass (Algorithm 3, mu = 1) followed by the rebuild of all
     P_l, B_l, T_l from the enriched test sets (Section 1).
@@ -626,15 +643,7 @@ def setup(A, r: int, levels: int, opts: Opts | None = None, grid: tuple | None =
     # ---- up
     for l in range(len(lvs) - 2, -1, -1):
         lv = lvs[l]
-        V = lv.P @ V
-        V = jacobi_shifted(lv.B, lv.T, V, lam, opts.omega, opts.nu_ev)
-        BV, TV = lv.B @ V, lv.T @ V
-        new = np.einsum("nk,nk->k", BV, V) / np.einsum("nk,nk->k", TV, V)
-        new[0] = 0.0
-        change = np.abs(new - lam) / np.maximum(np.abs(lam), 1e-300)
-        sel = change > opts.ev_change_tol
-        sel[0] = True
-        lam = new
+        V, lam, sel = up_level(lv, V, lam, opts)
         lv.V, lv.lam, lv.sel = V, lam.copy(), sel
     # ---- rebuild, top-down
     for l in range(len(lvs) - 1):

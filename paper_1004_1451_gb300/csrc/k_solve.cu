@@ -204,7 +204,7 @@ __global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b, T* __r
 // solve), so every later row walk reads shared memory instead of L2.
 constexpr int TAIL_MAX_N = 1024;
 constexpr int TAIL_MAX_NNZ = 16384;  // rows are walked serially per thread: dense levels stay on the grid
-constexpr int TAIL_THREADS = 512;
+constexpr int TAIL_THREADS = 1024;
 constexpr int TAIL_MAX_LEVELS = 12;
 constexpr int TAIL_SMEM = 227 * 1024;  // the opt-in maximum per block
 template <typename T>

@@ -62,6 +62,72 @@ def test_jacobi_shifted_modes():
     assert np.allclose(Y, X * fac ** 2, atol=1e-14)
 
 
+class _UpLevel:
+    """The P, B, T of one level, for up_level."""
+
+    def __init__(self, P, B, T):
+        self.P, self.B, self.T = P, B, T
+
+
+def _pencil_with_fourier_modes(n=16, seed=0):
+    # B = diag(t) (I - A_ring), T = diag(t): B u = lambda T u for every Fourier mode u of
+    # the ring walk, lambda_k = 1 - cos(2 pi k / n), with a non-identity T
+    t = 1.0 + np.random.default_rng(seed).random(n)
+    C = sp.identity(n, format="csr") - ring_walk(n)
+    B = sp.csr_matrix(sp.diags(t) @ C)
+    T = sp.diags(t, format="csr")
+    i = np.arange(n)
+    ks = (0, 1, 2)
+    U = np.stack([np.cos(2 * np.pi * k * i / n) for k in ks], axis=1)
+    lam = np.array([1.0 - np.cos(2 * np.pi * k / n) for k in ks])
+    return B, T, U, lam
+
+
+def test_up_level_keeps_exact_eigenvectors():
+    # V = P Vc: exact eigenvectors of the pencil with their exact eigenvalues come back from
+    # the shifted sweeps unchanged, the Rayleigh-type update returns the same eigenvalues,
+    # and only the state vector is selected for the rebuild (Algorithm 3, reading R9)
+    B, T, U, lam = _pencil_with_fourier_modes()
+    lv = _UpLevel(sp.csr_matrix(U), B, T)
+    V, new, sel = bamg.up_level(lv, np.eye(3), lam.copy(), bamg.Opts())
+    assert np.allclose(V, U, rtol=0, atol=1e-14)
+    assert new[0] == 0.0 and np.allclose(new[1:], lam[1:], rtol=1e-13, atol=0)
+    assert sel.tolist() == [True, False, False]
+
+
+def test_up_level_wrong_shift_closed_form():
+    # a shift mu != lambda_2 for the third column: every sweep multiplies the eigenvector by
+    # 1 - omega (lambda - mu) / (1 - mu) (Jacobi diagonal t (1 - mu) of B - mu T), the
+    # quotient still returns lambda_2, and the relative change |lambda - mu| / mu = 1/3
+    # selects the column; a state-vector eigenvalue passed in is reset to 0
+    B, T, U, lam = _pencil_with_fourier_modes(seed=1)
+    o = bamg.Opts()
+    mu = 1.5 * lam[2]
+    V, new, sel = bamg.up_level(_UpLevel(sp.csr_matrix(U), B, T), np.eye(3), np.array([0.3, lam[1], mu]), o)
+    f = (1.0 - o.omega * (lam[2] - mu) / (1.0 - mu)) ** o.nu_ev
+    assert np.allclose(V[:, 2], f * U[:, 2], rtol=0, atol=1e-14)
+    assert np.allclose(V[:, 1], U[:, 1], rtol=0, atol=1e-14)
+    assert new[0] == 0.0 and new[2] == pytest.approx(lam[2], rel=1e-13)
+    assert sel.tolist() == [True, False, True]
+
+
+def test_up_level_prolongs_through_P():
+    # Vc = e_1 + e_2 is prolonged by P = [u0, u1, u2] to u1 + u2; with the shift lambda_1 each
+    # sweep leaves the u1 part and multiplies the u2 part by 1 - omega (lambda_2 - lambda_1)
+    # / (1 - lambda_1), so the result is u1 + f u2 in closed form, and its eigenvalue
+    # estimate has moved (selected)
+    B, T, U, lam = _pencil_with_fourier_modes(seed=2)
+    o = bamg.Opts()
+    Vc = np.zeros((3, 2))
+    Vc[0, 0] = 1.0
+    Vc[1, 1] = Vc[2, 1] = 1.0
+    V, new, sel = bamg.up_level(_UpLevel(sp.csr_matrix(U), B, T), Vc, np.array([0.0, lam[1]]), o)
+    f = (1.0 - o.omega * (lam[2] - lam[1]) / (1.0 - lam[1])) ** o.nu_ev
+    assert np.allclose(V[:, 1], U[:, 1] + f * U[:, 2], rtol=0, atol=1e-14)
+    assert np.allclose(V[:, 0], U[:, 0], rtol=0, atol=1e-14)
+    assert sel.tolist() == [True, True]
+
+
 def test_weights_closed_form():
     n = 32
     B = bamg.system_matrix(ring_walk(n))
