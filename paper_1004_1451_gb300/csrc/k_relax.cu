@@ -114,7 +114,7 @@ void launch_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* 
 // entries per row on average (grid walks, tandem queues), else 6.
 constexpr int JAC_BLOCKS_PER_SM = 2;
 
-template <typename T, bool SHIFT, int JB>
+template <typename T, bool SHIFT, int JB, int CPT>
 __global__ void __launch_bounds__(256, JAC_BLOCKS_PER_SM)
     k_jacobi(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
              const T* __restrict__ tv, const T* __restrict__ dB, const T* __restrict__ dinvB, const T* __restrict__ dT,
@@ -122,14 +122,16 @@ __global__ void __launch_bounds__(256, JAC_BLOCKS_PER_SM)
              int nvec, T omega) {
     pdl_begin();
     constexpr int W = V16<T>::W;
+    constexpr int CW = CPT * W;         // columns per thread
     constexpr int NT = SHIFT ? JB : 1;  // T values are carried only by the shifted sweep
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x / nvec;  // rows per pass of the grid
+    const int tpr = nvec / CPT;         // threads per row
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x / tpr;  // rows per pass of the grid
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= stride * nvec) return;
-    int64_t row = t / nvec;
+    if (t >= stride * tpr) return;
+    int64_t row = t / tpr;
     if (row >= n) return;
-    const int ch = (int)(t - row * nvec);
-    const int off = col0 + ch * W;
+    const int ch = (int)(t - row * tpr);
+    const int off = col0 + ch * CW;
     const bool has_t = SHIFT && tv != nullptr;
     int p0 = __ldg(rp + row), p1 = __ldg(rp + row + 1);
     int cnt = min(JB, p1 - p0);
@@ -150,12 +152,15 @@ __global__ void __launch_bounds__(256, JAC_BLOCKS_PER_SM)
     }
     for (;;) {
         // this row's gathers, its own values and diagonal terms ...
-        T xv[JB][W];
+        T xv[JB][CW];
 #pragma unroll
         for (int u = 0; u < JB; ++u)
-            if (u < cnt) V16<T>::load(X + (int64_t)jj[u] * ld + off, xv[u]);
-        T xs[W];
-        V16<T>::load(X + row * ld + off, xs);
+            if (u < cnt)
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) V16<T>::load(X + (int64_t)jj[u] * ld + off + q * W, xv[u] + q * W);
+        T xs[CW];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) V16<T>::load(X + row * ld + off + q * W, xs + q * W);
         const T d0 = SHIFT ? __ldg(dB + row) : __ldg(dinvB + row);
         const T d1 = has_t ? __ldg(dT + row) : T(1);
         // ... while the next row's first entries and the row pointers after it arrive
@@ -175,13 +180,30 @@ __global__ void __launch_bounds__(256, JAC_BLOCKS_PER_SM)
             nnp0 = __ldg(rp + nnrow);
             nnp1 = __ldg(rp + nnrow + 1);
         }
-        T acc[W], accT[W];
+        T acc[CW], accT[CW];
 #pragma unroll
-        for (int e = 0; e < W; ++e) acc[e] = accT[e] = T(0);
-        for (int base = p0 + JB; base < p1; base += JB) {  // the rest of a long row, JB at a time
+        for (int e = 0; e < CW; ++e) acc[e] = accT[e] = T(0);
+        if constexpr (CPT > 1) {  // the rest of a long row, one entry at a time (registers)
+            for (int p = p0 + JB; p < p1; ++p) {
+                const int j = __ldg(ci + p);
+                const T b = __ldg(bv + p);
+                const T tq = has_t ? __ldg(tv + p) : T(0);
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) {
+                    T xq[W];
+                    V16<T>::load(X + (int64_t)j * ld + off + q * W, xq);
+#pragma unroll
+                    for (int e = 0; e < W; ++e) {
+                        acc[q * W + e] += b * xq[e];
+                        if (has_t) accT[q * W + e] += tq * xq[e];
+                    }
+                }
+            }
+        }
+        for (int base = p0 + JB; CPT == 1 && base < p1; base += JB) {  // the rest of a long row, JB at a time
             const int c2 = min(JB, p1 - base);
             int kj[JB];
-            T kb[JB], kt[NT], kx[JB][W];
+            T kb[JB], kt[NT], kx[JB][CW];
 #pragma unroll
             for (int u = 0; u < JB; ++u)
                 if (u < c2) {
@@ -191,31 +213,33 @@ __global__ void __launch_bounds__(256, JAC_BLOCKS_PER_SM)
                 }
 #pragma unroll
             for (int u = 0; u < JB; ++u)
-                if (u < c2) V16<T>::load(X + (int64_t)kj[u] * ld + off, kx[u]);
+                if (u < c2)
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) V16<T>::load(X + (int64_t)kj[u] * ld + off + q * W, kx[u] + q * W);
 #pragma unroll
             for (int u = 0; u < JB; ++u)
                 if (u < c2) {
 #pragma unroll
-                    for (int e = 0; e < W; ++e) acc[e] += kb[u] * kx[u][e];
+                    for (int e = 0; e < CW; ++e) acc[e] += kb[u] * kx[u][e];
                     if (has_t)
 #pragma unroll
-                        for (int e = 0; e < W; ++e) accT[e] += kt[u < NT ? u : 0] * kx[u][e];
+                        for (int e = 0; e < CW; ++e) accT[e] += kt[u < NT ? u : 0] * kx[u][e];
                 }
         }
 #pragma unroll
         for (int u = 0; u < JB; ++u)
             if (u < cnt) {
 #pragma unroll
-                for (int e = 0; e < W; ++e) acc[e] += bb[u] * xv[u][e];
+                for (int e = 0; e < CW; ++e) acc[e] += bb[u] * xv[u][e];
                 if (has_t)
 #pragma unroll
-                    for (int e = 0; e < W; ++e) accT[e] += tt[u < NT ? u : 0] * xv[u][e];
+                    for (int e = 0; e < CW; ++e) accT[e] += tt[u < NT ? u : 0] * xv[u][e];
             }
-        T y[W];
+        T y[CW];
         if (SHIFT) {
 #pragma unroll
-            for (int e = 0; e < W; ++e) {
-                const int c = ch * W + e;
+            for (int e = 0; e < CW; ++e) {
+                const int c = ch * CW + e;
                 const T l = c < ncols ? (T)lam[c] : T(0);
                 const T tx = has_t ? accT[e] : xs[e];
                 const T r = acc[e] - l * tx;
@@ -224,9 +248,10 @@ __global__ void __launch_bounds__(256, JAC_BLOCKS_PER_SM)
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < W; ++e) y[e] = xs[e] - omega * (d0 * acc[e]);
+            for (int e = 0; e < CW; ++e) y[e] = xs[e] - omega * (d0 * acc[e]);
         }
-        V16<T>::store(Y + row * ld + off, y);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) V16<T>::store(Y + row * ld + off + q * W, y + q * W);
         if (nrow >= n) break;
         row = nrow;
         p0 = np0;
@@ -281,24 +306,38 @@ void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, con
     T* src = X;
     T* dst = work;
     const bool short_rows = (int64_t)B.nnz <= 5 * (int64_t)B.n;
+    // two 16-byte chunks per thread (half the threads per row, twice the rows in flight for
+    // the same registers) for the FP32 sweep without shift when the chunks pair up
+    const int cpt = (sizeof(T) == 4 && !d_lambda && nvec % 2 == 0) ? 2 : 1;
+    const unsigned grid2 = (unsigned)std::min<int64_t>(blocks_for((int64_t)B.n * (nvec / cpt), 256),
+                                                       (int64_t)sm_count() * JAC_BLOCKS_PER_SM);
+#define BAMG_JAC(SH, JBV, CP)                                                                                      \
+    BAMG_LAUNCH((k_jacobi<T, SH, JBV, CP>), grid2, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda, \
+                ncols, src, dst, ld, col0, nvec, omega)
     for (int k = 0; k < nu; ++k) {
-        if (d_lambda && short_rows)
-            BAMG_LAUNCH((k_jacobi<T, true, 5>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda,
-                        ncols, src, dst, ld, col0, nvec, omega);
-        else if (d_lambda)
-            BAMG_LAUNCH((k_jacobi<T, true, 6>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda,
-                        ncols, src, dst, ld, col0, nvec, omega);
-        else if (short_rows)
-            BAMG_LAUNCH((k_jacobi<T, false, 5>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT,
-                        d_lambda, ncols, src, dst, ld, col0, nvec, omega);
-        else
-            BAMG_LAUNCH((k_jacobi<T, false, 6>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT,
-                        d_lambda, ncols, src, dst, ld, col0, nvec, omega);
+        if (d_lambda) {
+            if (short_rows)
+                BAMG_JAC(true, 5, 1);
+            else
+                BAMG_JAC(true, 6, 1);
+        } else if (cpt == 2) {
+            if constexpr (sizeof(T) == 4) {
+                if (short_rows)
+                    BAMG_JAC(false, 5, 2);
+                else
+                    BAMG_JAC(false, 6, 2);
+            }
+        } else if (short_rows) {
+            BAMG_JAC(false, 5, 1);
+        } else {
+            BAMG_JAC(false, 6, 1);
+        }
         T* t = src;
         src = dst;
         dst = t;
     }
     if (src != X) BAMG_LAUNCH(k_copy_cols<T>, grid, 256, 0, s, B.n, src, X, ld, col0, nvec);
+#undef BAMG_JAC
 }
 
 // ---------------------------------------------------------------- column statistics
