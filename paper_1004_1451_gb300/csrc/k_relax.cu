@@ -307,8 +307,8 @@ void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, con
     T* dst = work;
     const bool short_rows = (int64_t)B.nnz <= 5 * (int64_t)B.n;
     // two 16-byte chunks per thread (half the threads per row, twice the rows in flight for
-    // the same registers) for the FP32 sweep without shift when the chunks pair up
-    const int cpt = (sizeof(T) == 4 && !d_lambda && nvec % 2 == 0) ? 2 : 1;
+    // the same registers) for the sweep without shift when the chunks pair up
+    const int cpt = (!d_lambda && nvec % 2 == 0) ? 2 : 1;
     const unsigned grid2 = (unsigned)std::min<int64_t>(blocks_for((int64_t)B.n * (nvec / cpt), 256),
                                                        (int64_t)sm_count() * JAC_BLOCKS_PER_SM);
 #define BAMG_JAC(SH, JBV, CP)                                                                                      \
@@ -321,12 +321,10 @@ void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, con
             else
                 BAMG_JAC(true, 6, 1);
         } else if (cpt == 2) {
-            if constexpr (sizeof(T) == 4) {
-                if (short_rows)
-                    BAMG_JAC(false, 5, 2);
-                else
-                    BAMG_JAC(false, 6, 2);
-            }
+            if (short_rows)
+                BAMG_JAC(false, 5, 2);
+            else
+                BAMG_JAC(false, 6, 2);
         } else if (short_rows) {
             BAMG_JAC(false, 5, 1);
         } else {
