@@ -307,15 +307,23 @@ void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, con
     T* dst = work;
     const bool short_rows = (int64_t)B.nnz <= 5 * (int64_t)B.n;
     // two 16-byte chunks per thread (half the threads per row, twice the rows in flight for
-    // the same registers) for the sweep without shift when the chunks pair up
-    const int cpt = (!d_lambda && nvec % 2 == 0) ? 2 : 1;
+    // the same registers) when the chunks pair up and the rows outnumber the grid's threads
+    // more than fourfold (large levels, where rows in flight set the rate; on small levels
+    // the shorter per-thread work of one chunk is faster)
+    const int64_t grid_threads = (int64_t)sm_count() * JAC_BLOCKS_PER_SM * 256;
+    const int cpt = (nvec % 2 == 0 && (int64_t)B.n * nvec > 4 * grid_threads) ? 2 : 1;
     const unsigned grid2 = (unsigned)std::min<int64_t>(blocks_for((int64_t)B.n * (nvec / cpt), 256),
                                                        (int64_t)sm_count() * JAC_BLOCKS_PER_SM);
 #define BAMG_JAC(SH, JBV, CP)                                                                                      \
     BAMG_LAUNCH((k_jacobi<T, SH, JBV, CP>), grid2, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda, \
                 ncols, src, dst, ld, col0, nvec, omega)
     for (int k = 0; k < nu; ++k) {
-        if (d_lambda) {
+        if (d_lambda && cpt == 2) {
+            if (short_rows)
+                BAMG_JAC(true, 5, 2);
+            else
+                BAMG_JAC(true, 6, 2);
+        } else if (d_lambda) {
             if (short_rows)
                 BAMG_JAC(true, 5, 1);
             else

@@ -68,6 +68,32 @@ def test_relax_matches_oracle(dtype_name, r, ld, nu):
     assert np.all(got[:, r:] == 0)
 
 
+@pytest.mark.parametrize("dtype_name,shift", [("float32", False), ("float32", True), ("float64", False)])
+def test_relax_large_level_matches_oracle(dtype_name, shift):
+    # 360,000 rows: more rows than four per thread of the sweep's grid, so the sweep runs
+    # with two 16-byte chunks per thread
+    torch = _torch()
+    dt = getattr(torch, dtype_name)
+    ch = grid_walk(600)
+    B = ob.system_matrix(ch.to_scipy())
+    B.sort_indices()
+    n, K, ld = ch.n, 8, 8
+    assert n * (K * torch.finfo(dt).bits // 8 // 16) > 4 * 160 * 2 * 256
+    rng = np.random.default_rng(8)
+    V0 = rng.uniform(-1, 1, (n, K))
+    X = torch.zeros(n, ld, dtype=dt, device="cuda")
+    X[:, :K] = torch.tensor(V0, dtype=dt)
+    if shift:
+        lam = np.linspace(0.0, 0.07, K)
+        want = ob.jacobi_shifted(B, sp.identity(n, format="csr"), V0, lam, 0.7, 2)
+        _bamg().relax(dev_csr(B, dt), X, K, 0, 0.7, 2, lam=torch.tensor(lam, device="cuda"))
+    else:
+        want = ob.jacobi(B, V0, 0.7, 2)
+        _bamg().relax(dev_csr(B, dt), X, K, 0, 0.7, 2)
+    got = X.cpu().numpy().astype(np.float64)
+    assert rel(got, want) < (1e-13 if dt == torch.float64 else 2e-6)
+
+
 @pytest.mark.parametrize("with_T", [False, True])
 def test_shifted_relax_matches_oracle(with_T):
     torch = _torch()
