@@ -8,9 +8,13 @@ flushed between steps.  Also reported: the same metric end to end from host buff
 the plain FP64 method on the same chain, the roofline of the dominant kernel (the V-cycle
 smoother on the finest level), an SpMM HBM probe, the batched form on 512 chains, LS vs
 learned interpolation on a held-out tandem queue of 262,144 states, the 2^20-point
-Delaunay walk, and the CPU oracle on the host cores.
+Delaunay walk, the 64x64 grid walk, plain-FP64 runs beside the mixed ones, and the CPU
+oracle on the host cores.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Profiling helpers: --only-step, --kernel-probe, --probe-only N, --large-only,
+--large-reps R, --device-loop 0 (one graph launch per Arnoldi step, so that ncu lists the
+solve kernels), --no-batch, --no-learned, --no-large.
 """
 
 import os
