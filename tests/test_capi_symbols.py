@@ -91,3 +91,32 @@ int main(void) {
     assert sizes == [ctypes.sizeof(_capi.Opts), ctypes.sizeof(_capi.Csr), ctypes.sizeof(_capi.Mat),
                      ctypes.sizeof(_capi.Stats), ctypes.sizeof(_capi.LevelIn)]
     assert offs == [_capi.Opts.seed.offset, _capi.Opts.stream.offset, _capi.Opts.cr_omega.offset]
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # the ctypes mirrors of the boundary's structs have the C compiler's size and field
+    # offsets (a field added on one side only would shift every later field)
+    import ctypes
+
+    from paper_1004_1451_gb300 import _capi
+
+    pairs = {"bamg_csr": _capi.Csr, "bamg_mat": _capi.Mat, "bamg_opts": _capi.Opts, "bamg_stats": _capi.Stats,
+             "bamg_level_in": _capi.LevelIn}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bamg.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        parts = line.split()
+        got[tuple(parts[:-1])] = int(parts[-1])
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
