@@ -364,8 +364,13 @@ def spmm_probe(peaks, N=4096):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     del X, B
     torch.cuda.empty_cache()
+    lg = n.bit_length() - 1
+    shape = [{"chunks_per_thread": r["chunks_per_thread"], "blocks_per_sm": r["blocks_per_sm"]}
+             for r in bamg.autotune_report()
+             if r["elem_bytes"] == 4 and r["shift"] == 0 and r["chunks_per_row"] == 4 and r["log2_n"] == lg]
     return {"workload": f"grid walk {N}^2, r=16, FP32", "kernel": "k_jacobi<float>", "ms": round(ms, 4),
-            "bytes": int(nbytes), "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
+            "bytes": int(nbytes), "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+            "launch_shape": shape[0] if shape else "fixed rule (two chunks per thread, 2 blocks/SM)"}
 
 
 BATCH_WORKLOAD = ("512 chains, seed 0: 256 birth-death chains (n log-uniform in [1024, 65536], per-state "

@@ -285,6 +285,15 @@ int bamg_tv_init(int dtype, int n, int ncols, int ld, int col0, uint64_t seed, d
 int bamg_relax(int dtype, const bamg_mat* B, const void* T_val, const double* d_lambda, int ncols, int ld,
                int col0, double omega, int nu, void* X, void* work, void* stream);
 
+/* Launch shapes chosen by the sweep's autotuner.  On levels with more than four rows per
+ * thread of the one-chunk grid, the first sweep of each key times the launch shapes (one
+ * or two 16-byte chunks per thread; 1, 2 or 4 blocks per SM), which all write the same
+ * bits, and keeps the fastest for the process (BAMG_AUTOTUNE=0 in the environment: the
+ * fixed rule instead).  Writes up to max_rows rows of 7 int32 to h_rows (host memory):
+ * element bytes, shift (0/1), entry batch, 16-byte chunks per row, floor(log2 n), chunks
+ * per thread, blocks per SM.  Returns the number of rows written (>= 0). */
+int bamg_autotune_report(int32_t* h_rows, int max_rows);
+
 /* LS weights of Section 3.2: scales each active column k of [col0, col0+ncols) to unit
  * 2-norm and sets w_k = 1 / max(||B x_k||_2^2, floor), then divides the active weights by
  * their maximum; inactive columns (d_active[k] = 0, or d_active NULL = all active) get 0.

@@ -398,6 +398,16 @@ def relax(B, X: torch.Tensor, ncols: int, col0: int, omega: float, nu: int, T_va
     return X
 
 
+def autotune_report():
+    """The SpMM sweep shapes the autotuner chose in this process (bamg_autotune_report):
+    one dict per key."""
+    rows = (C.c_int32 * (7 * 64))()
+    k = _lib().bamg_autotune_report(rows, 64)
+    capi.check(min(k, 0))
+    names = ("elem_bytes", "shift", "entry_batch", "chunks_per_row", "log2_n", "chunks_per_thread", "blocks_per_sm")
+    return [dict(zip(names, rows[7 * r:7 * r + 7])) for r in range(k)]
+
+
 def relax_noalloc(B, X: torch.Tensor, ncols: int, col0: int, omega: float, nu: int, T_val=None, lam=None):
     """bamg_relax_noalloc: the sweeps of relax() with the library's fixed device scratch
     instead of any allocation (see include/bamg.h for its size limit)."""

@@ -88,6 +88,7 @@ SIGNATURES = {
     "bamg_interp_ls": (_I, [_I, C.POINTER(Mat), _P, _P, _P, _I, _I, _P, _I, _I, _I, _D, _P, _P, _P, _P]),
     "bamg_galerkin": (_I, [_I, C.POINTER(Mat), _P, _I, _P, _P, _P, _I, _P, _P, _P, _P, C.c_int64,
                            C.POINTER(C.c_int64), _P]),
+    "bamg_autotune_report": (_I, [_P, _I]),
     "bamg_coarse_eig": (_I, [_I, _I, _P, _P, _I, _P, _P, _P, C.POINTER(_I), _P, _P]),
     "bamg_interp_features": (_I, [_I, C.POINTER(Mat), _P, _P, _P, _I, _I, _P, _I, _I, _I, _D, _P, _P, _P, _P]),
     "bamg_interp_learned": (_I, [_I, C.POINTER(Mat), _P, _P, _P, _I, _I, _P, _I, _I, _I, _D, _P, _I, _P, _P, _P,

@@ -79,6 +79,11 @@ int bamg_relax(int dtype, const bamg_mat* B, const void* T_val, const double* d_
     });
 }
 
+int bamg_autotune_report(int32_t* h_rows, int max_rows) {
+    if (!h_rows || max_rows < 0) return BAMG_EINVAL;
+    return jacobi_tuned_shapes(h_rows, max_rows);
+}
+
 int bamg_tv_weights(int dtype, const bamg_mat* B, int ncols, int ld, int col0, const uint8_t* d_active, double floor,
                     void* X, double* d_w, void* stream) {
     return guard([&] {

@@ -5,6 +5,12 @@
 #include <cfloat>
 
 #include <algorithm>
+#include <array>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -294,56 +300,132 @@ __global__ void k_copy_cols(int n, const T* __restrict__ src, T* __restrict__ ds
     V16<T>::store(dst + (int64_t)row * ld + col0 + ch * W, v);
 }
 
+// One sweep of the launch shape (chunks per thread, blocks per SM of the grid): Y from X.
+template <typename T>
+static void jacobi_sweep(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, const T* dT,
+                         const double* d_lambda, int ncols, int ld, int col0, T omega, int nvec, bool short_rows,
+                         int cpt, int bps, const T* X, T* Y, cudaStream_t s) {
+    const unsigned grid = (unsigned)std::min<int64_t>(blocks_for((int64_t)B.n * (nvec / cpt), 256),
+                                                      (int64_t)sm_count() * bps);
+#define BAMG_JAC(SH, JBV, CP)                                                                                     \
+    BAMG_LAUNCH((k_jacobi<T, SH, JBV, CP>), grid, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda, \
+                ncols, X, Y, ld, col0, nvec, omega)
+    const int variant = (d_lambda ? 4 : 0) + (cpt == 2 ? 2 : 0) + (short_rows ? 0 : 1);
+    switch (variant) {
+        case 0: BAMG_JAC(false, 5, 1); break;
+        case 1: BAMG_JAC(false, 6, 1); break;
+        case 2: BAMG_JAC(false, 5, 2); break;
+        case 3: BAMG_JAC(false, 6, 2); break;
+        case 4: BAMG_JAC(true, 5, 1); break;
+        case 5: BAMG_JAC(true, 6, 1); break;
+        case 6: BAMG_JAC(true, 5, 2); break;
+        default: BAMG_JAC(true, 6, 2); break;
+    }
+#undef BAMG_JAC
+}
+
+// ---------------------------------------------------------------- launch-shape autotuner
+// The sweep's launch shape (one or two 16-byte chunks per thread; one, two or four blocks
+// per SM in the grid) changes how the rows are spread over the GPU, never the arithmetic:
+// every shape writes the same bits.  On levels large enough for the shape to matter (more
+// than four rows per thread of the one-chunk grid), the first sweep of each (precision,
+// shift, entry batch, chunks per row, size class log2 n) times the shapes on the caller's
+// own data with CUDA events (X -> work, X untouched) and keeps the fastest for the
+// process.  BAMG_AUTOTUNE=0 keeps the fixed rule (two chunks when they pair up, two blocks
+// per SM).
+struct JacShape {
+    int cpt, bps;
+};
+static bool autotune_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("BAMG_AUTOTUNE");
+        return !(e && std::strcmp(e, "0") == 0);
+    }();
+    return on;
+}
+static std::mutex& tune_mutex() {
+    static std::mutex m;
+    return m;
+}
+static std::map<std::array<int, 5>, JacShape>& tune_cache() {
+    static std::map<std::array<int, 5>, JacShape> c;
+    return c;
+}
+// the cached choices as (key..., cpt, bps) rows, for reports and tests
+int jacobi_tuned_shapes(int* out, int max_rows) {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    int k = 0;
+    for (const auto& kv : tune_cache()) {
+        if (k >= max_rows) break;
+        for (int q = 0; q < 5; ++q) out[7 * k + q] = kv.first[q];
+        out[7 * k + 5] = kv.second.cpt;
+        out[7 * k + 6] = kv.second.bps;
+        ++k;
+    }
+    return k;
+}
+
 template <typename T>
 void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, const T* dT, const double* d_lambda,
-           int ncols, int ld, int col0, T omega, int nu, T* X, T* work, cudaStream_t s) {
+           int ncols, int ld, int col0, T omega, int nu, T* X, T* work, cudaStream_t s, bool tune) {
     constexpr int W = V16<T>::W;
     const int nvec = (ncols + W - 1) / W;
     if (B.n == 0 || nvec == 0 || nu <= 0) return;
     const int64_t work_items = (int64_t)B.n * nvec;
     const unsigned grid = (unsigned)std::min<int64_t>(blocks_for(work_items, 256),
                                                       (int64_t)sm_count() * JAC_BLOCKS_PER_SM);
+    const bool short_rows = (int64_t)B.nnz <= 5 * (int64_t)B.n;
+    // small levels: one chunk per thread, two blocks per SM (the shorter per-thread work is
+    // faster there); large levels: the fixed rule or the tuned shape
+    const int64_t grid_threads = (int64_t)sm_count() * JAC_BLOCKS_PER_SM * 256;
+    const bool large = work_items > 4 * grid_threads;
+    JacShape shape{(large && nvec % 2 == 0) ? 2 : 1, JAC_BLOCKS_PER_SM};
+    if (large && tune && autotune_enabled()) {
+        int lg = 0;
+        while ((int64_t(1) << (lg + 1)) <= B.n) ++lg;
+        const std::array<int, 5> key{(int)sizeof(T), d_lambda ? 1 : 0, short_rows ? 5 : 6, nvec, lg};
+        std::lock_guard<std::mutex> lock(tune_mutex());
+        auto it = tune_cache().find(key);
+        if (it != tune_cache().end()) {
+            shape = it->second;
+        } else {
+            std::vector<JacShape> cand{{1, 2}, {1, 4}};
+            if (nvec % 2 == 0) cand.insert(cand.end(), {{2, 1}, {2, 2}, {2, 4}});
+            cudaEvent_t e0, e1;
+            BAMG_CK(cudaEventCreate(&e0));
+            BAMG_CK(cudaEventCreate(&e1));
+            float best = 0.f;
+            for (const JacShape& c : cand) {
+                jacobi_sweep<T>(B, T_val, dB, dinvB, dT, d_lambda, ncols, ld, col0, omega, nvec, short_rows, c.cpt,
+                                c.bps, X, work, s);  // warm-up
+                BAMG_CK(cudaEventRecord(e0, s));
+                for (int r = 0; r < 3; ++r)
+                    jacobi_sweep<T>(B, T_val, dB, dinvB, dT, d_lambda, ncols, ld, col0, omega, nvec, short_rows, c.cpt,
+                                    c.bps, X, work, s);
+                BAMG_CK(cudaEventRecord(e1, s));
+                BAMG_CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BAMG_CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (&c == &cand[0] || ms < best) {
+                    best = ms;
+                    shape = c;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            tune_cache()[key] = shape;
+        }
+    }
     T* src = X;
     T* dst = work;
-    const bool short_rows = (int64_t)B.nnz <= 5 * (int64_t)B.n;
-    // two 16-byte chunks per thread (half the threads per row, twice the rows in flight for
-    // the same registers) when the chunks pair up and the rows outnumber the grid's threads
-    // more than fourfold (large levels, where rows in flight set the rate; on small levels
-    // the shorter per-thread work of one chunk is faster)
-    const int64_t grid_threads = (int64_t)sm_count() * JAC_BLOCKS_PER_SM * 256;
-    const int cpt = (nvec % 2 == 0 && (int64_t)B.n * nvec > 4 * grid_threads) ? 2 : 1;
-    const unsigned grid2 = (unsigned)std::min<int64_t>(blocks_for((int64_t)B.n * (nvec / cpt), 256),
-                                                       (int64_t)sm_count() * JAC_BLOCKS_PER_SM);
-#define BAMG_JAC(SH, JBV, CP)                                                                                      \
-    BAMG_LAUNCH((k_jacobi<T, SH, JBV, CP>), grid2, 256, 0, s, B.n, B.rp, B.ci, B.v, T_val, dB, dinvB, dT, d_lambda, \
-                ncols, src, dst, ld, col0, nvec, omega)
     for (int k = 0; k < nu; ++k) {
-        if (d_lambda && cpt == 2) {
-            if (short_rows)
-                BAMG_JAC(true, 5, 2);
-            else
-                BAMG_JAC(true, 6, 2);
-        } else if (d_lambda) {
-            if (short_rows)
-                BAMG_JAC(true, 5, 1);
-            else
-                BAMG_JAC(true, 6, 1);
-        } else if (cpt == 2) {
-            if (short_rows)
-                BAMG_JAC(false, 5, 2);
-            else
-                BAMG_JAC(false, 6, 2);
-        } else if (short_rows) {
-            BAMG_JAC(false, 5, 1);
-        } else {
-            BAMG_JAC(false, 6, 1);
-        }
+        jacobi_sweep<T>(B, T_val, dB, dinvB, dT, d_lambda, ncols, ld, col0, omega, nvec, short_rows, shape.cpt,
+                        shape.bps, src, dst, s);
         T* t = src;
         src = dst;
         dst = t;
     }
     if (src != X) BAMG_LAUNCH(k_copy_cols<T>, grid, 256, 0, s, B.n, src, X, ld, col0, nvec);
-#undef BAMG_JAC
 }
 
 // ---------------------------------------------------------------- column statistics
@@ -748,7 +830,7 @@ int build_system_matrix(int n, int nnzA, const int32_t* rpA, const int32_t* ciA,
                                       cudaStream_t);                                                                \
     template void launch_identity_on_pattern<T>(int, const int32_t*, const int32_t*, T*, cudaStream_t);            \
     template void relax<T>(const MatView<T>&, const T*, const T*, const T*, const T*, const double*, int, int, int, \
-                           T, int, T*, T*, cudaStream_t);                                                          \
+                           T, int, T*, T*, cudaStream_t, bool);                                                    \
     template void tv_weights<T>(const MatView<T>&, int, int, int, const uint8_t*, double, T*, double*, cudaStream_t); \
     template void rayleigh_update<T>(const MatView<T>&, const T*, const T*, int, int, int, double, double*,         \
                                      uint8_t*, cudaStream_t);                                                      \

@@ -44,10 +44,14 @@ void launch_diagonals(int n, const int32_t* rp, const int32_t* ci, const T* bv, 
                       cudaStream_t s);
 template <typename T>
 void launch_identity_on_pattern(int n, const int32_t* rp, const int32_t* ci, T* tv, cudaStream_t s);
-// nu sweeps; T_val/dT/d_lambda may be null (no shift).  work: n*ld scratch.
+// nu sweeps; T_val/dT/d_lambda may be null (no shift).  work: n*ld scratch.  tune: on large
+// levels, time the launch shapes once per shape key (jacobi_tuned_shapes lists the choices).
 template <typename T>
 void relax(const MatView<T>& B, const T* T_val, const T* dB, const T* dinvB, const T* dT, const double* d_lambda,
-           int ncols, int ld, int col0, T omega, int nu, T* X, T* work, cudaStream_t s);
+           int ncols, int ld, int col0, T omega, int nu, T* X, T* work, cudaStream_t s, bool tune = true);
+// Rows (precision bytes, shift, entry batch, 16-byte chunks per row, log2 n, chunks per
+// thread, blocks per SM) of the tuned sweep shapes, at most max_rows; returns the count.
+int jacobi_tuned_shapes(int* out, int max_rows);
 // Normalise active columns and write LS weights (ncols doubles).
 template <typename T>
 void tv_weights(const MatView<T>& B, int ncols, int ld, int col0, const uint8_t* d_active, double floor, T* X,

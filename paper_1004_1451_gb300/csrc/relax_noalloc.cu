@@ -63,7 +63,8 @@ static void relax_noalloc(const bamg_mat* Bm, const void* T_val, const double* l
     launch_diag<T>(B, dB, s);
     launch_reciprocal<T>(B.n, dB, dinv, s);
     if (T_val) launch_diag_vals<T>(B.n, B.rp, B.ci, (const T*)T_val, dT, s);
-    relax<T>(B, (const T*)T_val, dB, dinv, T_val ? dT : nullptr, lam, ncols, ld, col0, (T)omega, nu, (T*)X, work, s);
+    relax<T>(B, (const T*)T_val, dB, dinv, T_val ? dT : nullptr, lam, ncols, ld, col0, (T)omega, nu, (T*)X, work, s,
+             false);
     BAMG_CK(cudaStreamSynchronize(s));
 }
 

@@ -94,6 +94,49 @@ def test_relax_large_level_matches_oracle(dtype_name, shift):
     assert rel(got, want) < (1e-13 if dt == torch.float64 else 2e-6)
 
 
+_AUTOTUNE_CHILD = '''
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_1004_1451_gb300 as bamg
+from gpu_util import dev_csr
+from oracle import bamg as ob
+from workloads import grid_walk
+ch = grid_walk(600)
+B = ob.system_matrix(ch.to_scipy())
+B.sort_indices()
+V0 = np.random.default_rng(9).uniform(-1, 1, (ch.n, 8))
+X = torch.tensor(V0, dtype=torch.float32, device="cuda")
+bamg.relax(dev_csr(B, torch.float32), X, 8, 0, 0.7, 3)
+np.save(sys.argv[2], X.cpu().numpy())
+'''
+
+
+def test_relax_autotune_same_bits(tmp_path):
+    # the autotuner only changes the launch shape: the tuned sweeps write the bits of the
+    # fixed rule (BAMG_AUTOTUNE=0, in a separate process), and the choice is reported
+    import os
+    import subprocess
+    import sys
+
+    torch = _torch()
+    bamg = _bamg()
+    ch = grid_walk(600)
+    B = ob.system_matrix(ch.to_scipy())
+    B.sort_indices()
+    V0 = np.random.default_rng(9).uniform(-1, 1, (ch.n, 8))
+    X = torch.tensor(V0, dtype=torch.float32, device="cuda")
+    bamg.relax(dev_csr(B, torch.float32), X, 8, 0, 0.7, 3)
+    got = X.cpu().numpy()
+    rep = [r for r in bamg.autotune_report() if r["elem_bytes"] == 4 and r["shift"] == 0 and r["chunks_per_row"] == 2
+           and r["log2_n"] == 18]
+    assert len(rep) == 1 and rep[0]["chunks_per_thread"] in (1, 2) and rep[0]["blocks_per_sm"] in (1, 2, 4)
+    here = os.path.dirname(os.path.abspath(__file__))
+    out = tmp_path / "fixed.npy"
+    env = dict(os.environ, BAMG_AUTOTUNE="0", PYTHONPATH=os.pathsep.join([os.path.dirname(here), here]))
+    subprocess.run([sys.executable, "-c", _AUTOTUNE_CHILD, here, str(out)], env=env, check=True, timeout=600)
+    assert np.array_equal(got, np.load(out))
+
+
 @pytest.mark.parametrize("with_T", [False, True])
 def test_shifted_relax_matches_oracle(with_T):
     torch = _torch()
