@@ -230,6 +230,23 @@ def test_coarsen_cr_matches_oracle():
     assert nc == cf.sum()
 
 
+def test_coarsen_cr_long_rows_matches_oracle():
+    # a compatible-relaxation coarse level (3,278 rows, 17 entries per row on average): the
+    # F-relaxation sweeps run with four lanes per row
+    ch = delaunay_walk(40000, 3)
+    H = ob.setup(ch.to_scipy(), 8, 12, ob.Opts(coarsen="cr"))
+    B = sp.csr_matrix(H.levels[2].B)
+    B.sort_indices()
+    assert B.nnz >= 12 * B.shape[0]
+    o = ob.Opts(coarsen="cr", seed=5)
+    ocf, ocidx, orounds = ob.coarsen_cr(B, 2, o)
+    cf, cidx, nc, rounds = _bamg().coarsen_cr(dev_csr(B), 2, 5, o.cr_theta, o.cr_nu, o.cr_omega, o.cr_max_rounds)
+    cf = cf.cpu().numpy().astype(bool)
+    assert rounds == orounds
+    assert np.mean(cf != ocf) < 1e-3
+    assert nc == cf.sum()
+
+
 # ------------------------------------------------------------------ LS interpolation
 def _ls_inputs(N=40, K=8, z=2):
     ch, B = _tandem_B(N)
