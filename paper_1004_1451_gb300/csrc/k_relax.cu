@@ -492,17 +492,6 @@ __global__ void k_colstats(int n, const int32_t* __restrict__ rp, const int32_t*
         for (int q = 0; q < 2 * W; ++q) partial[(int64_t)blockIdx.x * (nvec * 2 * W) + ch * 2 * W + q] = sh[base + q];
 }
 
-// one warp per output: lanes stride the block partials, then a fixed butterfly
-__global__ void k_reduce_partials(int nblocks, int width, const double* __restrict__ partial, double* __restrict__ out) {
-    pdl_begin();
-    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (q >= width) return;
-    double s = 0.0;
-    for (int b = lane; b < nblocks; b += 32) s += partial[(int64_t)b * width + q];
-    s = warp_sum(s);
-    if (lane == 0) out[q] = s;
-}
 
 // Column statistics of Eq. (3.4) / the Rayleigh quotients as per-block partial sums
 // (nb rows of `width` values in `partial`); the consumer forms the sums with
@@ -531,8 +520,8 @@ static void colstats(const MatView<T>& B, const T* T_val, const T* X, int ld, in
     BAMG_LAUNCH((k_colstats<T, MODE>), nb, dim3(nvec, ny), smem, s, B.n, B.rp, B.ci, B.v, T_val, X, ld, col0, nvec,
                 partial);
 }
-// sums[q] for q < width from the partials, one warp per output as in k_reduce_partials
-// (lanes stride the blocks, then the butterfly); a block of COLSUM_T threads.
+// sums[q] for q < width from the partials, one warp per output (lanes stride the blocks,
+// then a fixed butterfly); a block of COLSUM_T threads.
 constexpr int COLSUM_T = 256;
 __device__ void colsum_partials(int nblocks, int width, const double* __restrict__ partial, double* sums) {
     const int lane = threadIdx.x & 31;
@@ -705,16 +694,6 @@ template <typename Tin, typename Tout>
 void launch_strided_to_vec(int n, const Tin* X, int ld, int col, Tout* y, cudaStream_t s) {
     if (n) BAMG_LAUNCH((k_strided_to_vec<Tin, Tout>), blocks_for(n, 256), 256, 0, s, n, X, ld, col, y);
 }
-template <typename Tin, typename Tout>
-__global__ void k_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col) {
-    pdl_begin();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) X[(int64_t)i * ld + col] = (Tout)y[i];
-}
-template <typename Tin, typename Tout>
-void launch_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col, cudaStream_t s) {
-    if (n) BAMG_LAUNCH((k_vec_to_strided<Tin, Tout>), blocks_for(n, 256), 256, 0, s, n, y, X, ld, col);
-}
 // nv vectors y[q * n + i] to the columns col0 + q
 template <typename Tin, typename Tout>
 __global__ void k_vecs_to_strided(int n, int nv, const Tin* y, Tout* X, int ld, int col0) {
@@ -844,8 +823,6 @@ template void launch_convert<float, double>(int64_t, const float*, double*, cuda
 template void launch_convert<double, double>(int64_t, const double*, double*, cudaStream_t);
 template void launch_strided_to_vec<float, double>(int, const float*, int, int, double*, cudaStream_t);
 template void launch_strided_to_vec<double, double>(int, const double*, int, int, double*, cudaStream_t);
-template void launch_vec_to_strided<double, float>(int, const double*, float*, int, int, cudaStream_t);
-template void launch_vec_to_strided<double, double>(int, const double*, double*, int, int, cudaStream_t);
 template void launch_vecs_to_strided<double, float>(int, int, const double*, float*, int, int, cudaStream_t);
 template void launch_vecs_to_strided<double, double>(int, int, const double*, double*, int, int, cudaStream_t);
 

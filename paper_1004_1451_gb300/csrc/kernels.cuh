@@ -69,8 +69,6 @@ void launch_convert(int64_t n, const Tin* a, Tout* b, cudaStream_t s);
 template <typename Tin, typename Tout>
 void launch_strided_to_vec(int n, const Tin* X, int ld, int col, Tout* y, cudaStream_t s);
 template <typename Tin, typename Tout>
-void launch_vec_to_strided(int n, const Tin* y, Tout* X, int ld, int col, cudaStream_t s);
-template <typename Tin, typename Tout>
 void launch_vecs_to_strided(int n, int nv, const Tin* y, Tout* X, int ld, int col0, cudaStream_t s);
 
 // Build B = I - A (diagonal always stored) from A (sorted CSR); checks column sums,
