@@ -74,7 +74,9 @@ def _line(d):
 class Clocks:
     def __init__(self):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+
+        self.path = os.path.join(tempfile.gettempdir(), f"bamg_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
