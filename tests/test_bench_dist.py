@@ -48,3 +48,23 @@ def test_single_process_is_identity():
     import bench
 
     assert bench.max_over_ranks(3.25, "cpu") == 3.25
+
+
+def test_reference_arm_json_line():
+    # the reference arm (the oracle on the host cores) prints one JSON line with the
+    # contract's keys: impl, the metric, a cpu_baseline object and a zero-copy e2e object
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, check=True, timeout=600).stdout
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["higher_is_better"] is False and d["unit"] == "ms" and d["value"] > 0
+    assert d["steps"] == 1 and d["n_gpus"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
