@@ -165,7 +165,8 @@ void bamg_free(bamg_handle* h);
 /* Message of the calling thread's last failed call ("" if none).  Static storage. */
 const char* bamg_last_error(void);
 
-/* Number of kernels this library has launched in the process (all threads). */
+/* Number of kernels this library has launched in the process (all threads; each
+ * replayed Arnoldi step counts its kernels).  Bookkeeping, no passage of the paper. */
 uint64_t bamg_launch_count(void);
 
 /* Levels of the hierarchy: *nlevels, and per level the size and non-zeros of B_l into
@@ -203,6 +204,8 @@ typedef struct {
     int32_t p_nnz;
     const int32_t* h_p_row_ptr; const int32_t* h_p_col; const double* h_p_val; /* P_l */
 } bamg_level_in;
+/* BAMG_EINVAL when nlevels is outside 1..30, the coarsest level has more than 64 states,
+ * or a row of P has more than o->caliber entries; *h is untouched on failure. */
 int bamg_import(int nlevels, const bamg_level_in* levels, const double* h_pinv, const double* h_x_init,
                 const bamg_opts* o, bamg_handle** h);
 
@@ -237,7 +240,9 @@ int bamg_smooth_apply(bamg_handle* h, int level, int sweeps, const void* b, void
 enum { BAMG_MLP_F = 112, BAMG_MLP_H = 128, BAMG_MLP_S = 16 };
 /* He-uniform weights W = (2u - 1) sqrt(6 / fan_in), u from SplitMix64 (seed, layer, index). */
 int bamg_model_create(uint64_t seed, bamg_model** m);
+/* frees the model (NULL allowed); a handle set up with it must not outlive it */
 void bamg_model_free(bamg_model* m);
+/* number of FP32 parameters of the MLP (112*128 + 128 + 128*128 + 128 + 128*16 + 16) */
 int64_t bamg_model_param_count(void);
 /* host FP32 parameters in (set; resets Adam) or out (get); count = bamg_model_param_count() */
 int bamg_model_set(bamg_model* m, const float* h_params, int64_t count);
