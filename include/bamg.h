@@ -283,7 +283,7 @@ int bamg_tv_init(int dtype, int n, int ncols, int ld, int col0, uint64_t seed, d
                  void* X, void* stream);
 
 /* nu omega-Jacobi sweeps (Section 3, Eq. (3.1), M = diag(B)/omega) on the columns
- * [col0, col0 + ncols) of X: X <- X - omega D^{-1} (B X).  With T_val and d_lambda
+ * [col0, col0 + ncols) of X (col0 >= 0): X <- X - omega D^{-1} (B X).  With T_val and d_lambda
  * the sweeps solve (B - lambda_k T) x_k = 0 (Algorithm 3): D_k = diag(B) - lambda_k diag(T).
  * T_val: values of T on B's pattern (NULL: T = I); d_lambda: ncols FP64 shifts (NULL: 0).
  * work: scratch of n * ld elements of dtype.  B must store its diagonal. */
@@ -317,7 +317,8 @@ int bamg_tv_weights(int dtype, const bamg_mat* B, int ncols, int ld, int col0, c
  * array's device address with that device current (make that first call before any
  * stream capture).  All calls share the array and nothing in it needs to start at zero;
  * calls that overlap on the GPU, from any stream or thread, race on it.  Arguments and
- * results as for bamg_relax; returns after the work has completed on `stream`. */
+ * results as for bamg_relax (col0 >= 0; ld at least one 16-byte chunk); the call
+ * synchronises `stream` and returns after the work has completed on it. */
 int bamg_relax_noalloc(int dtype, const bamg_mat* B, const void* T_val, const double* d_lambda, int ncols, int ld,
                        int col0, double omega, int nu, void* X, void* stream);
 

@@ -388,8 +388,21 @@ def tv_init(X: torch.Tensor, ncols: int, col0: int, seed: int, lo: float, hi: fl
     return X
 
 
+def _check_relax_args(B, X, ncols, T_val, lam):
+    """The C ABI takes raw device pointers with X row-major (n x ld): check the tensors
+    behind them before handing their addresses over."""
+    assert X.is_cuda and X.dim() == 2 and X.is_contiguous(), "X must be a contiguous 2-D CUDA tensor (n x ld)"
+    assert X.dtype in (torch.float64, torch.float32), "X must be float64 or float32"
+    assert B[2].is_cuda and B[2].dtype == X.dtype and B[2].is_contiguous(), "B's values must be CUDA tensors of X's dtype"
+    assert T_val is None or (T_val.is_cuda and T_val.dtype == X.dtype and T_val.is_contiguous()
+                             and T_val.numel() == B[1].numel()), "T_val must match B's pattern and X's dtype"
+    assert lam is None or (lam.is_cuda and lam.dtype == torch.float64 and lam.numel() >= ncols), \
+        "lam must be a CUDA float64 tensor with at least ncols entries"
+
+
 def relax(B, X: torch.Tensor, ncols: int, col0: int, omega: float, nu: int, T_val=None, lam=None, work=None):
     """B = (row_ptr, col, val) device tensors with val in X's dtype."""
+    _check_relax_args(B, X, ncols, T_val, lam)
     n, ld = X.shape
     work = torch.empty_like(X) if work is None else work
     m = _mat(*B)
@@ -411,6 +424,7 @@ def autotune_report():
 def relax_noalloc(B, X: torch.Tensor, ncols: int, col0: int, omega: float, nu: int, T_val=None, lam=None):
     """bamg_relax_noalloc: the sweeps of relax() with the library's fixed device scratch
     instead of any allocation (see include/bamg.h for its size limit)."""
+    _check_relax_args(B, X, ncols, T_val, lam)
     n, ld = X.shape
     m = _mat(*B)
     capi.check(_lib().bamg_relax_noalloc(_dtype_code(X), C.byref(m), _p(T_val), _p(lam), ncols, ld, col0, omega, nu,

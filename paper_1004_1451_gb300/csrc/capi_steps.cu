@@ -34,6 +34,7 @@ static void check_block(const void* X, int ncols, int ld, int col0) {
     constexpr int W = V16<T>::W;
     BAMG_REQUIRE(X != nullptr, BAMG_EINVAL, "null vector block");
     BAMG_REQUIRE(((uintptr_t)X & 15) == 0, BAMG_EINVAL, "vector block must be 16-byte aligned");
+    BAMG_REQUIRE(col0 >= 0 && ld >= W, BAMG_EINVAL, "col0 must be >= 0 and ld at least one 16-byte chunk");
     BAMG_REQUIRE(ld % W == 0 && col0 % W == 0, BAMG_EINVAL, "ld and col0 must be multiples of 2 (FP64) or 4 (FP32)");
     BAMG_REQUIRE(ncols >= 1 && col0 + (ncols + W - 1) / W * W <= ld, BAMG_EINVAL, "columns exceed the leading dimension");
 }

@@ -505,10 +505,15 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
             a.pinv_off = (int32_t)smem;
             smem += npinv;
         }
-        static std::atomic<bool> attr{false};  // idempotent; several host threads may get here
-        if (!attr) {
+        // the attribute is per device: set once on each device (idempotent; several host
+        // threads may get here)
+        static std::atomic<bool> attr[256] = {};
+        int dev = 0;
+        BAMG_CK(cudaGetDevice(&dev));
+        BAMG_REQUIRE(dev >= 0 && dev < 256, BAMG_EINVAL, "device ordinal out of range");
+        if (!attr[dev]) {
             BAMG_CK(cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM));
-            attr = true;
+            attr[dev] = true;
         }
         BAMG_LAUNCH_PDL(k_vcycle_tail<T>, 1, TAIL_THREADS, smem, s, a);
         xcur[l0] = final_x(lv[l0], nu_pre, nu_post, l0 == L);

@@ -42,6 +42,7 @@ static void relax_noalloc(const bamg_mat* Bm, const void* T_val, const double* l
     constexpr int W = V16<T>::W;
     BAMG_REQUIRE(Bm && Bm->n >= 1 && Bm->nnz >= 0 && Bm->row_ptr && Bm->col && Bm->val, BAMG_EINVAL, "bad matrix");
     BAMG_REQUIRE(X != nullptr && ((uintptr_t)X & 15) == 0, BAMG_EINVAL, "vector block must be 16-byte aligned");
+    BAMG_REQUIRE(col0 >= 0 && ld >= W, BAMG_EINVAL, "col0 must be >= 0 and ld at least one 16-byte chunk");
     BAMG_REQUIRE(ld % W == 0 && col0 % W == 0, BAMG_EINVAL, "ld and col0 must be multiples of 2 (FP64) or 4 (FP32)");
     BAMG_REQUIRE(ncols >= 1 && col0 + (ncols + W - 1) / W * W <= ld, BAMG_EINVAL, "columns exceed the leading dimension");
     BAMG_REQUIRE(nu >= 0, BAMG_EINVAL, "nu must be >= 0");

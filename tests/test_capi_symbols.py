@@ -62,37 +62,6 @@ def test_default_opts_are_the_papers():
         assert getattr(o, k) == getattr(d, k), k
 
 
-def test_struct_layouts_match_header():
-    # offsets of the ctypes mirrors against a C compile of the header
-    import ctypes
-    import tempfile
-
-    from paper_1004_1451_gb300 import _capi
-
-    prog = r"""
-#include <stddef.h>
-#include <stdio.h>
-#include "bamg.h"
-int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(bamg_opts), sizeof(bamg_csr), sizeof(bamg_mat), sizeof(bamg_stats),
-         sizeof(bamg_level_in));
-  printf("%zu %zu %zu\n", offsetof(bamg_opts, seed), offsetof(bamg_opts, stream), offsetof(bamg_opts, cr_omega));
-  return 0;
-}
-"""
-    with tempfile.TemporaryDirectory() as d:
-        c = os.path.join(d, "t.c")
-        open(c, "w").write(prog)
-        exe = os.path.join(d, "t")
-        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
-        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
-    sizes = list(map(int, out[:5]))
-    offs = list(map(int, out[5:]))
-    assert sizes == [ctypes.sizeof(_capi.Opts), ctypes.sizeof(_capi.Csr), ctypes.sizeof(_capi.Mat),
-                     ctypes.sizeof(_capi.Stats), ctypes.sizeof(_capi.LevelIn)]
-    assert offs == [_capi.Opts.seed.offset, _capi.Opts.stream.offset, _capi.Opts.cr_omega.offset]
-
-
 def test_struct_layouts_match_header(tmp_path):
     # the ctypes mirrors of the boundary's structs have the C compiler's size and field
     # offsets (a field added on one side only would shift every later field)
