@@ -101,6 +101,10 @@ class Opts:
     model: dict | None = None  # MLP parameters for interp == "learned"
     learned_refit: bool = True  # learned rows: Eq. (3.6) weights over the MLP's choice
     record: list | None = None  # if a list: (features, LS targets, fine mask) of every fit
+    # setup cycling and restarts (Section 4.1, Section 5.1)
+    mu: int = 1  # Algorithm 3's loop count: 1 = V-cycle setup, 2 = W-cycle setup
+    setup_cycles: int = 1  # MLE cycles before the final rebuild (R33; the tables' V^2 = 2)
+    mle_restart: bool = True  # R32: an MLE restart after every pGMRES cycle that fails
 
 
 # ---------------------------------------------------------------------------------
@@ -522,6 +526,9 @@ class Level:
     w: np.ndarray | None = None
     cand: np.ndarray | None = None
     ncand: np.ndarray | None = None
+    cgrid: tuple | None = None  # grid of level l+1 (full coarsening)
+    coarsest: bool = False
+    kinds: np.ndarray | None = None  # coarsest level: 0 real, 1 Re, 2 Im of a complex pair
 
 
 @dataclass
@@ -595,13 +602,116 @@ def up_level(lv, Vc: np.ndarray, lam: np.ndarray, opts: Opts):
     return V, new, sel
 
 
-def setup(A, r: int, levels: int, opts: Opts | None = None, grid: tuple | None = None) -> Hierarchy:
-    """Bootstrap setup: one MLE pass (Algorithm 3, mu = 1) followed by the rebuild of all
-    P_l, B_l, T_l from the enriched test sets (Section 1).
+def _first_visit(lvs: list, l: int, levels: int, opts: Opts) -> bool:
+    """First arrival at level l on the way down.  Returns True when l is the coarsest level
+    (R13: n_l <= coarse_max, or `levels` coarsenings done); otherwise Algorithm 3's "Relax
+    B_l x = 0, x in U_l" (nu_tv sweeps) and the C/F splitting of level l."""
+    lv = lvs[l]
+    lv.coarsest = l == levels or lv.B.shape[0] <= opts.coarse_max
+    if lv.coarsest:
+        return True
+    lv.U = jacobi(lv.B, lv.U, opts.omega, opts.nu_tv)
+    lv.cf, lv.cidx, lv.cgrid = _split(lv.B, lv.grid, l, opts)
+    return False
 
-    Down: relax the random test vectors U_l (nu_tv sweeps), fit P_l (Algorithm 2), form
-    Q_l, B_{l+1} = Q_l B_l P_l, T_{l+1} = Q_l T_l P_l and inject U_{l+1} = R_l U_l, until
-    n_{l+1} <= coarse_max or `levels` coarsenings (R13).
+
+def _interp_step(lvs: list, l: int, opts: Opts, with_v: bool):
+    """One pass of Algorithm 3's loop body down to level l+1: P_l = ls_interpolation of
+    U_l (and, with_v, the V_l columns selected by R9), the averaging Q_l, B_{l+1} = Q_l B_l P_l,
+    T_{l+1} = Q_l T_l P_l.  On the first descent (level l+1 not built yet) it creates
+    level l+1 with U_{l+1} = R_l U_l (injection of the normalised test vectors)."""
+    lv = lvs[l]
+    r = lv.U.shape[1]
+    if with_v:
+        X = np.concatenate([lv.U, lv.V], axis=1)
+        active = np.concatenate([np.ones(r, dtype=bool), lv.sel])
+    else:
+        X, active = lv.U, np.ones(r, dtype=bool)
+    Xh, w, P, Q = _build_interp(lv, X, active, opts)
+    lv.w, lv.P, lv.Q = w, P, Q
+    Bc = galerkin(Q, lv.B, P)
+    Tc = galerkin(Q, lv.T, P)
+    if len(lvs) == l + 1:
+        lv.U = Xh
+        c2f = np.flatnonzero(lv.cf)[np.argsort(lv.cidx[lv.cf], kind="stable")]
+        lvs.append(Level(B=Bc, T=Tc, grid=lv.cgrid, U=Xh[c2f]))
+    else:
+        lvs[l + 1].B, lvs[l + 1].T = Bc, Tc
+
+
+def _coarsest_eigs(lvs: list, l: int, opts: Opts):
+    """Algorithm 3, l = L: the k_ev eigenpairs of B_L x = lambda T_L x of smallest |lambda|."""
+    Lc = lvs[l]
+    lam, V, kinds = coarse_eigs(Lc.B.toarray(), Lc.T.toarray(), opts.k_ev)
+    Lc.V, Lc.lam, Lc.kinds = V, lam.copy(), kinds
+
+
+def _up_step(lvs: list, l: int, opts: Opts):
+    """Algorithm 3 after the recursive call: V_l = P_l V_{l+1}, relaxation of
+    (B_l - lambda_i T_l) x^(i) = 0, the lambda update and the R9 selection (up_level)."""
+    lv = lvs[l]
+    V, lam, sel = up_level(lv, lvs[l + 1].V, lvs[l + 1].lam, opts)
+    lv.V, lv.lam, lv.sel = V, lam.copy(), sel
+
+
+def mle(lvs: list, l: int, levels: int, opts: Opts, first: bool):
+    """bootamg_mle (Algorithm 3) on level l with cycle index mu = opts.mu (1: V-cycle,
+    2: W-cycle, Section 4.1).
+
+    R33: Algorithm 3 empties V_l at the start of every call, which would make a second
+    call from the finest level repeat the first; V_l = {} is read as holding on the first
+    visit of level l only, so every later visit (the second pass of a W-cycle's loop one
+    level up, and every later MLE cycle) fits P_l to U_l and the V_l its previous visit
+    left.  R10: U_l is relaxed on the first visit only, and U_{l+1} = R_l U_l is formed
+    on the first descent only.  Section 5.1 runs the MLE as a "V(2,2)" cycle: a visit
+    after the first relaxes V_l (nu_ev sweeps on (B_l - lambda_i T_l) x^(i) = 0) on the way
+    down before P_l is fitted, as the upward pass does after the recursion."""
+    if first:
+        if _first_visit(lvs, l, levels, opts):
+            _coarsest_eigs(lvs, l, opts)
+            return
+    elif lvs[l].coarsest:
+        _coarsest_eigs(lvs, l, opts)
+        return
+    else:
+        lv = lvs[l]
+        lv.V = jacobi_shifted(lv.B, lv.T, lv.V, lv.lam, opts.omega, opts.nu_ev)
+    for it in range(opts.mu):
+        fresh = first and it == 0
+        _interp_step(lvs, l, opts, with_v=not fresh)
+        mle(lvs, l + 1, levels, opts, fresh)
+        _up_step(lvs, l, opts)
+
+
+def rebuild(lvs: list, opts: Opts):
+    """Section 1: with the test sets of all levels updated, all P_l, B_l and T_l are
+    recalculated, top-down, from U_l and the selected V_l; the C/F splitting of the first
+    pass is kept (R26) and U_l is not relaxed again (R10)."""
+    for l in range(len(lvs) - 1):
+        _interp_step(lvs, l, opts, with_v=True)
+
+
+def _finish(H: "Hierarchy"):
+    """B_L^+ of the rebuilt coarsest matrix and the initial guess V_0[:, 0] / 1^T V_0[:, 0]."""
+    H.pinv = pinv_truncated(H.levels[-1].B.toarray())
+    x0 = H.levels[0].V[:, 0].copy()
+    H.x_init = x0 / x0.sum()
+
+
+def _start(A, r: int, opts: Opts, grid):
+    B0 = system_matrix(A)
+    n = B0.shape[0]
+    return [Level(B=B0, T=sp.identity(n, format="csr"), grid=grid, U=tv_init(n, r, opts.seed, opts.tv_lo, opts.tv_hi))]
+
+
+def setup(A, r: int, levels: int, opts: Opts | None = None, grid: tuple | None = None) -> Hierarchy:
+    """Bootstrap setup: opts.setup_cycles MLE cycles (Algorithm 3 with mu = opts.mu;
+    R33 for the cycles after the first) followed by the rebuild of all P_l, B_l, T_l from
+    the enriched test sets (Section 1).
+
+    First cycle, down: relax the random test vectors U_l (nu_tv sweeps), fit P_l
+    (Algorithm 2), form Q_l, B_{l+1} = Q_l B_l P_l, T_{l+1} = Q_l T_l P_l and inject
+    U_{l+1} = R_l U_l, until n_{l+1} <= coarse_max or `levels` coarsenings (R13).
     Coarsest: the k_ev eigenpairs of smallest |lambda|.
     Up: V_l = P_l V_{l+1}, nu_ev sweeps on (B_l - lambda_i T_l) x^(i) = 0, then
     lambda_i = <B x, x> / <T x, x> for i >= 1 (lambda_0 stays 0).  R9: x^(i) joins the
@@ -609,57 +719,70 @@ def setup(A, r: int, levels: int, opts: Opts | None = None, grid: tuple | None =
     always joins.
     Rebuild (R10): top-down, P_l from U_l (not relaxed again) plus the selected V_l, with
     weights and neighbourhoods recomputed on the current B_l; the C/F splitting of the
-    first pass is kept (R26).  The state vector approximation V_0[:, 0],
-    scaled to 1^T x = 1, is the initial guess of the solve."""
+    first pass is kept (R26).  The state vector approximation V_0[:, 0], scaled to
+    1^T x = 1, is the initial guess of the solve."""
     opts = opts or Opts()
     if opts.coarsen == "grid" and grid is None:
         raise ValueError("full coarsening needs the grid dimensions")
-    B0 = system_matrix(A)
-    n = B0.shape[0]
-    T0 = sp.identity(n, format="csr")
-    lvs = [Level(B=B0, T=T0, grid=grid)]
-    U = tv_init(n, r, opts.seed, opts.tv_lo, opts.tv_hi)
-    # ---- pass 1, down
-    for l in range(levels):
-        lv = lvs[-1]
-        if lv.B.shape[0] <= opts.coarse_max:
+    lvs = _start(A, r, opts, grid)
+    mle(lvs, 0, levels, opts, first=True)
+    for _ in range(1, opts.setup_cycles):
+        mle(lvs, 0, levels, opts, first=False)
+    rebuild(lvs, opts)
+    H = Hierarchy(levels=lvs, opts=opts)
+    _finish(H)
+    H.stats["kinds"] = lvs[-1].kinds
+    return H
+
+
+def _ratio(B, x, norm: str) -> float:
+    r = B @ x
+    if norm == "l1":
+        return float(np.abs(r).sum() / np.abs(x).sum())
+    return float(np.linalg.norm(r) / np.linalg.norm(x))
+
+
+def mle_solve(A, r: int, levels: int, tol: float, opts: Opts | None = None, grid: tuple | None = None,
+              max_cycles: int = 50, norm: str = "l2"):
+    """The MLE as a stand-alone solver (Section 4.1; the MLE rows of Tables 1, 2 and 4):
+    MLE cycles (Algorithm 3 with mu = opts.mu, R33) until the state vector approximation
+    x = V_0[:, 0] of the latest cycle meets ||B x|| / ||x|| <= tol (norm "l2": the
+    Section 5.1 criterion, R15; "l1": the l1 ratio).  Returns x (1^T x = 1) and the
+    cycle count and residual history."""
+    opts = opts or Opts()
+    lvs = _start(A, r, opts, grid)
+    B = lvs[0].B
+    hist = []
+    cycles = 0
+    while True:
+        mle(lvs, 0, levels, opts, first=(cycles == 0))
+        cycles += 1
+        x = lvs[0].V[:, 0].copy()
+        hist.append(_ratio(B, x, norm))
+        if hist[-1] <= tol or cycles >= max_cycles:
             break
-        U = jacobi(lv.B, U, opts.omega, opts.nu_tv)
-        lv.cf, lv.cidx, cgrid = _split(lv.B, lv.grid, l, opts)
-        Uh, w, P, Q = _build_interp(lv, U, np.ones(r, dtype=bool), opts)
-        lv.U, lv.w, lv.P, lv.Q = Uh, w, P, Q
-        Bc = galerkin(Q, lv.B, P)
-        Tc = galerkin(Q, lv.T, P)
-        c2f = np.flatnonzero(lv.cf)[np.argsort(lv.cidx[lv.cf], kind="stable")]
-        U = Uh[c2f]
-        lvs.append(Level(B=Bc, T=Tc, grid=cgrid))
-        if Bc.shape[0] <= opts.coarse_max:
-            break
-    Lc = lvs[-1]
-    Lc.U = U
-    # ---- coarsest eigenpairs
-    lam, V, kinds = coarse_eigs(Lc.B.toarray(), Lc.T.toarray(), opts.k_ev)
-    Lc.V, Lc.lam = V, lam.copy()
-    # ---- up
-    for l in range(len(lvs) - 2, -1, -1):
-        lv = lvs[l]
-        V, lam, sel = up_level(lv, V, lam, opts)
-        lv.V, lv.lam, lv.sel = V, lam.copy(), sel
-    # ---- rebuild, top-down
+    return x / x.sum(), {"cycles": cycles, "history": hist, "converged": hist[-1] <= tol}
+
+
+def mle_restart(H: Hierarchy, x: np.ndarray):
+    """R32, the MLE restart of Section 5.1 ("restarting the MLE iterations when the solution
+    is not found in a reasonable number of pGMRES iterations"; Section 4.1: alternate MLE
+    and AMG-GMRES when several eigenvalues are near zero): the pGMRES iterate x becomes the
+    state-vector test vector of every level (x / ||x||_2 on level 0, its injection R_l on
+    the coarser ones), all P_l, B_l, T_l are rebuilt top-down as in the setup's rebuild, and
+    B_L^+ is recomputed.  The other test vectors are unchanged."""
+    lvs = H.levels
+    lvs[0].V[:, 0] = x / np.linalg.norm(x)
+    lvs[0].sel[0] = True
     for l in range(len(lvs) - 1):
         lv = lvs[l]
-        X = np.concatenate([lv.U, lv.V], axis=1)
-        active = np.concatenate([np.ones(lv.U.shape[1], dtype=bool), lv.sel])
-        Xh, w, P, Q = _build_interp(lv, X, active, opts)
-        lv.w, lv.P, lv.Q = w, P, Q
-        lvs[l + 1].B = galerkin(Q, lv.B, P)
-        lvs[l + 1].T = galerkin(Q, lv.T, P)
-    H = Hierarchy(levels=lvs, opts=opts)
+        _interp_step(lvs, l, H.opts, with_v=True)
+        c2f = np.flatnonzero(lv.cf)[np.argsort(lv.cidx[lv.cf], kind="stable")]
+        lvs[l + 1].V[:, 0] = lv.V[c2f, 0]
+        if lvs[l + 1].sel is not None:
+            lvs[l + 1].sel[0] = True
     H.pinv = pinv_truncated(lvs[-1].B.toarray())
-    x0 = lvs[0].V[:, 0].copy()
-    H.x_init = x0 / x0.sum()
-    H.stats["kinds"] = kinds
-    return H
+    H.stats["mle_restarts"] = H.stats.get("mle_restarts", 0) + 1
 
 
 # ---------------------------------------------------------------------------------
@@ -760,14 +883,91 @@ def fgmres(B, x0: np.ndarray, precond, tol: float, m: int, max_it: int, norm: st
 
 def solve(H: Hierarchy, tol: float, x0: np.ndarray | None = None, norm: str = "l1"):
     """V(2,2)-preconditioned FGMRES from the setup's state-vector approximation, then the
-    normalisation 1^T x = 1."""
+    normalisation 1^T x = 1.  With opts.mle_restart (R32) every restart cycle of gmres_m
+    steps that ends above tol is followed by an MLE restart (mle_restart) before the next
+    cycle; without it the cycles simply restart from the last iterate."""
     o = H.opts
     B = H.levels[0].B
-    x0 = H.x_init if x0 is None else x0
-    x, st = fgmres(B, x0, lambda v: vcycle(H, v), tol, o.gmres_m, o.max_it, norm=norm)
+    x = H.x_init if x0 is None else x0
+    prec = lambda v: vcycle(H, v)  # noqa: E731
+    if not o.mle_restart:
+        x, st = fgmres(B, x, prec, tol, o.gmres_m, o.max_it, norm=norm)
+    else:
+        st = {"iterations": 0, "history": [], "restarts": 0, "mle_restarts": 0}
+        while True:
+            x, c = fgmres(B, x, prec, tol, o.gmres_m, min(o.gmres_m, o.max_it - st["iterations"]), norm=norm)
+            st["history"] += c["history"] if not st["history"] else c["history"][1:]
+            st["iterations"] += c["iterations"]
+            st["converged"] = c["converged"] if "converged" in c else c["history"][-1] <= tol
+            if st["converged"] or c["iterations"] == 0 or st["iterations"] >= o.max_it:
+                break
+            st["restarts"] += 1
+            mle_restart(H, x)
+            st["mle_restarts"] += 1
     x = x / x.sum()
     st["residual_l1"] = l1_ratio(B, x)
     return x, st
+
+
+def ritz_closest_to_zero(Hk: np.ndarray):
+    """Section 4.3: the eigenvalue of H_k closest to 0 and its eigenvector eta (unit 2-norm,
+    largest-modulus entry positive).  For a complex closest eigenvalue the real part of
+    its eigenvector is taken (the preconditioned matrix's eigenvalue 0 is real)."""
+    lam, E = np.linalg.eig(Hk)
+    q = int(np.argmin(np.abs(lam)))
+    eta = np.real(E[:, q])
+    eta = eta / np.linalg.norm(eta)
+    if eta[np.argmax(np.abs(eta))] < 0:
+        eta = -eta
+    return float(np.real(lam[q])), eta
+
+
+def parnoldi(H: Hierarchy, tol: float, x0: np.ndarray | None = None, m: int | None = None,
+             max_it: int | None = None, norm: str = "l1"):
+    """Multigrid-preconditioned Arnoldi (Section 4.3): orthonormal v_1, v_2, ... spanning
+    the Krylov space of C B from y (the setup's state-vector approximation, or x0),
+    H_k = V_k^T (C B) V_k, the eigenvalue of H_k closest to 0 with eigenvector eta, and
+    the Ritz vector x = V_k eta as the steady-state approximation.  C is the V(2,2) cycle.
+    The Gram-Schmidt process is the classical one with one reorthogonalisation (as in
+    fgmres).  After every step the true residual of the Ritz vector is tested; after m
+    steps the process restarts from the Ritz vector (explicit restart; the paper does not
+    restart).  Returns x with 1^T x = 1 and the history."""
+    o = H.opts
+    B = H.levels[0].B
+    m = o.gmres_m if m is None else m
+    max_it = o.max_it if max_it is None else max_it
+    y = np.array(H.x_init if x0 is None else x0, dtype=np.float64, copy=True)
+    n = len(y)
+    hist = [_ratio(B, y, norm)]
+    it = 0
+    x = y
+    restarts = 0
+    while hist[-1] > tol and it < max_it:
+        V = np.zeros((n, m + 1))
+        Hh = np.zeros((m + 1, m))
+        V[:, 0] = y / np.linalg.norm(y)
+        for j in range(m):
+            w = vcycle(H, B @ V[:, j])
+            h = V[:, :j + 1].T @ w
+            w = w - V[:, :j + 1] @ h
+            h2 = V[:, :j + 1].T @ w
+            w = w - V[:, :j + 1] @ h2
+            hn = np.linalg.norm(w)
+            Hh[:j + 1, j] = h + h2
+            Hh[j + 1, j] = hn
+            if hn > 0:
+                V[:, j + 1] = w / hn
+            it += 1
+            theta, eta = ritz_closest_to_zero(Hh[:j + 1, :j + 1])
+            x = V[:, :j + 1] @ eta
+            hist.append(_ratio(B, x, norm))
+            if hist[-1] <= tol or hn == 0 or it >= max_it:
+                break
+        y = x
+        restarts += 1
+    x = x / x.sum()
+    return x, {"iterations": it, "history": hist, "restarts": max(restarts - 1, 0), "converged": hist[-1] <= tol,
+               "residual_l1": l1_ratio(B, x)}
 
 
 def stationary(A, r: int, levels: int, tol: float, opts: Opts | None = None, grid=None):

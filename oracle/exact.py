@@ -33,6 +33,36 @@ def birth_death(birth: np.ndarray, death: np.ndarray) -> np.ndarray:
     return x / x.sum()
 
 
+def birth_death_ambiguity(birth: np.ndarray, death: np.ndarray, tol: float):
+    """How far the residual test ||B x||_1 / ||x||_1 <= tol pins a birth-death chain's x.
+
+    For x* (1^T x* = 1) and an edge m -> m+1 let M_L = sum_{k<=m} x*_k, M_R = 1 - M_L and
+    dx = x* * (M_R [k <= m] - M_L [k > m]), the move of mass across the edge.  Then
+    1^T dx = 0, ||dx||_1 = 2 M_L M_R, and by detailed balance (b_m x*_m = d_{m+1} x*_{m+1})
+    B dx is nonzero only at m and m+1, with ||B dx||_1 = 2 b_m x*_m.  Hence
+      kappa_lb = max_m M_L M_R / (b_m x*_m)  <=  ||B^#||_1  (B^# B dx = dx), and
+      eps(tol) = max_m 2 M_L M_R min(1, tol / (2 b_m x*_m)):
+    x* + s dx (s <= 1) is non-negative, has 1^T x = 1, meets the tolerance and lies eps
+    away from x* in relative l1.  Evaluated in log space.  Returns (log10 kappa_lb, eps)."""
+    birth = np.asarray(birth, dtype=np.float64)
+    death = np.asarray(death, dtype=np.float64)
+    n = len(birth)
+    if n < 2:
+        return 0.0, 0.0
+    logx = np.zeros(n)
+    logx[1:] = np.cumsum(np.log(birth[:-1]) - np.log(death[1:]))
+    logx -= logx.max()
+    logx -= np.log(np.exp(logx).sum())
+    ML = np.cumsum(np.exp(logx))[:-1]
+    MR = np.maximum(1.0 - ML, 0.0)
+    ok = (ML > 0) & (MR > 0)
+    mass = np.log(ML[ok]) + np.log(MR[ok])
+    flux = np.log(birth[:-1][ok]) + logx[:-1][ok]  # log(b_m x*_m)
+    log_kappa = float((mass - flux).max()) / np.log(10.0)
+    eps = float((2.0 * np.exp(mass + np.minimum(0.0, np.log(tol) - np.log(2.0) - flux))).max())
+    return log_kappa, eps
+
+
 def dense_nullspace(A_dense: np.ndarray) -> np.ndarray:
     """Bordered dense solve: replace the last equation of (I - A) x = 0 by 1^T x = 1.
     Nonsingular for irreducible A because the left null vector 1 of B has no zero entry."""

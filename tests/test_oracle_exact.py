@@ -4,7 +4,7 @@ SuperLU, power iteration on the lazy chain)."""
 import numpy as np
 
 from oracle import exact
-from workloads import delaunay_walk, grid_walk, random_birth_death, tandem_queue
+from workloads import birth_death, delaunay_walk, grid_walk, random_birth_death, tandem_queue
 
 
 def _rel(a, b):
@@ -36,3 +36,35 @@ def test_tandem_three_routes():
     assert _rel(xs, xd) < 1e-12
     assert _rel(x, xd) < 1e-9
     assert np.all(xd > 0)
+
+
+def test_birth_death_ambiguity_bounds_the_group_inverse():
+    """kappa_lb is a lower bound on ||B^#||_1 (dense group inverse (B + x* 1^T)^-1 - x* 1^T),
+    and the explicit mass move it is built on has exactly the stated residual and error."""
+    for n, seed in [(50, 1), (120, 5), (200, 7)]:
+        ch = random_birth_death(n, seed)
+        b, d = ch.meta["birth"], ch.meta["death"]
+        x = exact.birth_death(b, d)
+        B = np.eye(n) - ch.dense()
+        G = np.linalg.inv(B + np.outer(x, np.ones(n))) - np.outer(x, np.ones(n))
+        kappa = np.abs(G).sum(axis=0).max()
+        lk, _ = exact.birth_death_ambiguity(b, d, 1e-10)
+        assert 10 ** lk <= kappa * (1 + 1e-9)
+        assert 10 ** lk >= 0.01 * kappa  # not a vacuous bound on these chains
+        # the construction for the maximising edge
+        ML = np.cumsum(x)[:-1]
+        m = int(np.argmax(ML * (1 - ML) / (b[:-1] * x[:-1])))
+        dx = x * np.where(np.arange(n) <= m, 1 - ML[m], -ML[m])
+        assert abs(dx.sum()) < 1e-14
+        assert np.isclose(np.abs(dx).sum(), 2 * ML[m] * (1 - ML[m]), rtol=1e-12)
+        assert np.isclose(np.abs(B @ dx).sum(), 2 * b[m] * x[m], rtol=1e-8)
+
+
+def test_birth_death_ambiguity_of_a_uniform_chain_is_small():
+    """Equal birth and death rates: x* is uniform, the worst edge is the middle one,
+    kappa_lb = (1/4) / (b / n) = n / (4 b) in closed form."""
+    n, b = 100, 0.3
+    ch = birth_death(np.full(n, b), np.full(n, b))
+    lk, eps = exact.birth_death_ambiguity(ch.meta["birth"], ch.meta["death"], 1e-10)
+    assert np.isclose(10 ** lk, n / (4 * b), rtol=1e-9)
+    assert np.isclose(eps, 2 * 0.25 * 1e-10 / (2 * b / n), rtol=1e-9)

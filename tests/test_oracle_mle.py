@@ -1,0 +1,259 @@
+"""Pins of the oracle's setup composition and of the MLE variants: Algorithm 3 with mu = 1
+and 2, repeated MLE cycles, the MLE restart (R32), the stand-alone MLE solver, the
+multigrid-preconditioned Arnoldi method (Section 4.3), and the independent-set rule (R18).
+
+Each pin is chosen so that a named plausible mistake in the oracle fails it (said in the
+test's docstring)."""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import bamg as ob
+from oracle import exact
+from workloads import delaunay_walk, grid_walk, tandem_queue
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+# ------------------------------------------------------------------ independent sets
+def test_luby_rule_hand_worked_on_a_path():
+    """Path 0-1-2-3-4-5-6, seed 0: the SplitMix64 priorities (pinned by the golden file)
+    rank the nodes 4 < 0 < 5 < 3 < 2 < 6 < 1.  Round 1: 1 and 6 beat all their undecided
+    neighbours and join; 0, 2 and 5 leave.  Round 2: 3 beats 4 and joins.  Set {1, 3, 6}.
+    A reversed (lowest-wins) order gives {0, 2, 4, 6}; ignoring removed neighbours or
+    letting two neighbours join together also fails."""
+    n = 7
+    S = sp.csr_matrix((np.ones(2 * (n - 1)), (np.r_[np.arange(n - 1), np.arange(1, n)],
+                                               np.r_[np.arange(1, n), np.arange(n - 1)])), shape=(n, n))
+    pri = ob.counter_u64(0, ob.STREAM_MIS, np.arange(n, dtype=np.uint64))
+    assert list(np.argsort(pri)) == [4, 0, 5, 3, 2, 6, 1]
+    got = ob.independent_set(S, np.ones(n, dtype=bool), 0, ob.STREAM_MIS)
+    assert sorted(np.flatnonzero(got)) == [1, 3, 6]
+
+
+# ------------------------------------------------------------------ setup composition
+def _first_pass(A, r, levels, o, grid):
+    lvs = ob._start(A, r, o, grid)
+    ob.mle(lvs, 0, levels, o, first=True)
+    return lvs
+
+
+def test_stored_test_vectors_are_the_first_pass_relaxed_ones():
+    """R10: U_0 after the setup is tv_init relaxed nu_tv times and scaled to unit 2-norm,
+    computed here directly; relaxing U again in the rebuild changes it."""
+    ch = grid_walk(17)
+    o = ob.Opts(tv_lo=0.0, tv_hi=1.0)
+    H = ob.setup(ch.to_scipy(), 6, 5, o, grid=ch.grid)
+    B = ob.system_matrix(ch.to_scipy())
+    U = ob.tv_init(ch.n, 6, o.seed, 0.0, 1.0)
+    D = B.diagonal()
+    for _ in range(o.nu_tv):
+        U = U - o.omega * (B @ U) / D[:, None]
+    U = U / np.linalg.norm(U, axis=0)
+    assert np.allclose(H.levels[0].U, U, rtol=0, atol=1e-14)
+
+
+def test_rebuild_fits_the_stored_U_and_the_selected_V():
+    """The rebuilt P_l is Algorithm 2 on [U_l, V_l] with the R9 selection active: refitting
+    it here from the hierarchy's own stored sets gives the same matrix.  Dropping V from
+    the rebuild, or fitting it to U alone, gives a different P."""
+    ch = tandem_queue(16)
+    o = ob.Opts()
+    H = ob.setup(ch.to_scipy(), 6, 5, o, grid=ch.grid)
+    for lv in H.levels[:-1]:
+        X = np.concatenate([lv.U, lv.V], axis=1)
+        active = np.concatenate([np.ones(lv.U.shape[1], dtype=bool), lv.sel])
+        _, _, P, _ = ob._build_interp(lv, X, active, o)
+        assert (abs(P - lv.P)).max() == 0.0
+        _, _, Pu, _ = ob._build_interp(lv, lv.U, np.ones(lv.U.shape[1], dtype=bool), o)
+        assert (abs(Pu - lv.P)).max() > 1e-6
+
+
+def test_rebuild_reproduces_the_state_vector_better_than_the_first_pass():
+    """The state-vector approximation V_0[:, 0] carries the largest LS weight in the rebuild,
+    so the rebuilt P_0 reproduces it from its coarse values far better than the first-pass
+    P_0 (fitted to U alone).  A rebuild without V keeps the first-pass error."""
+    ch = grid_walk(33)
+    o = ob.Opts()
+    H = ob.setup(ch.to_scipy(), 6, 5, o, grid=ch.grid)
+    first = _first_pass(ch.to_scipy(), 6, 5, o, ch.grid)
+    lv = H.levels[0]
+    v = lv.V[:, 0]
+    c2f = np.flatnonzero(lv.cf)[np.argsort(lv.cidx[lv.cf], kind="stable")]
+    e_rebuilt = np.linalg.norm(lv.P @ v[c2f] - v)
+    e_first = np.linalg.norm(first[0].P @ v[c2f] - v)
+    assert e_rebuilt < 0.25 * e_first  # measured 0.11 with the R25 ridge; ~1 without V
+
+
+def test_rebuild_keeps_the_first_pass_splitting():
+    """R26: with compatible relaxation the C/F split of every level is the first pass's.
+    Recomputing it on the rebuilt B_l gives another split on this graph (checked), so a
+    rebuild that re-splits fails."""
+    ch = delaunay_walk(600, 3)
+    o = ob.Opts(coarsen="cr")
+    H = ob.setup(ch.to_scipy(), 6, 5, o, grid=None)
+    first = _first_pass(ch.to_scipy(), 6, 5, o, None)
+    assert len(first) == len(H.levels)
+    differs = False
+    for l in range(len(H.levels) - 1):
+        assert np.array_equal(H.levels[l].cf, first[l].cf)
+        if l > 0:
+            cf2, _, _ = ob.coarsen_cr(H.levels[l].B, l, o)
+            differs |= not np.array_equal(cf2, first[l].cf)
+    assert differs
+
+
+# ------------------------------------------------------------------ W-cycle and repeated cycles
+def _count_coarse_solves(monkeypatch):
+    calls = []
+    orig = ob.coarse_eigs
+
+    def counted(*a, **k):
+        calls.append(1)
+        return orig(*a, **k)
+
+    monkeypatch.setattr(ob, "coarse_eigs", counted)
+    return calls
+
+
+@pytest.mark.parametrize("mu,cycles", [(1, 1), (1, 3), (2, 1), (2, 2)])
+def test_coarsest_solves_per_setup(monkeypatch, mu, cycles):
+    """Algorithm 3 with loop count mu visits the coarsest level mu^L times per MLE cycle
+    (L coarsenings): 1 per V-cycle, 2^L per W-cycle.  A W-cycle that recurses once, or
+    a cycle count that is ignored, fails."""
+    calls = _count_coarse_solves(monkeypatch)
+    ch = grid_walk(33)
+    o = ob.Opts(mu=mu, setup_cycles=cycles)
+    H = ob.setup(ch.to_scipy(), 6, 3, o, grid=ch.grid)
+    L = len(H.levels) - 1
+    assert L == 3
+    assert len(calls) == cycles * mu ** L
+
+
+@pytest.mark.parametrize("mu,cycles", [(2, 1), (1, 2)])
+def test_cycled_setups_reach_the_closed_form(mu, cycles):
+    ch = grid_walk(17)
+    o = ob.Opts(mu=mu, setup_cycles=cycles, tv_lo=0.0, tv_hi=1.0)
+    x, H, st = ob.stationary(ch.to_scipy(), 6, 10, 1e-13, o, grid=ch.grid)
+    assert st["converged"] and _rel(x, exact.exact_stationary(ch)) < 1e-9
+
+
+def test_mle_cycles_reduce_the_state_vector_residual():
+    """R33: a later MLE cycle fits P_l to U_l and the previous V_l and relaxes V_l on the
+    way down, so the state vector approximation improves every cycle (monotone residual
+    history at a geometric rate); a cycle that refits to U alone repeats the first."""
+    ch = grid_walk(33)
+    o = ob.Opts(coarse_max=25, ridge=1e-12)
+    x, st = ob.mle_solve(ch.to_scipy(), 6, 30, 1e-8, o, grid=ch.grid, max_cycles=30)
+    h = np.array(st["history"])
+    assert st["converged"]
+    assert np.all(h[1:] < h[:-1])
+    assert st["cycles"] <= 12  # Table 1 prints 9 MLE iterations at N = 33
+
+
+def test_mle_solve_reaches_the_closed_form():
+    """The MLE used as a stand-alone solver (Section 4.1) converges to x proportional to the
+    degree (the closed form of the uniform network) within its tolerance's reach."""
+    ch = grid_walk(17)
+    o = ob.Opts(ridge=1e-12, coarse_max=25)
+    x, st = ob.mle_solve(ch.to_scipy(), 6, 30, 1e-12, o, grid=ch.grid, max_cycles=60, norm="l1")
+    assert st["converged"]
+    assert _rel(x, exact.exact_stationary(ch)) < 1e-8
+
+
+def test_w_cycle_mle_needs_fewer_cycles_than_v_cycle():
+    ch = tandem_queue(32)
+    counts = {}
+    for mu in (1, 2):
+        o = ob.Opts(coarse_max=25, ridge=1e-12, mu=mu)
+        _, st = ob.mle_solve(ch.to_scipy(), 6, 30, 1e-8, o, grid=ch.grid, max_cycles=40)
+        assert st["converged"]
+        counts[mu] = st["cycles"]
+    assert counts[2] < counts[1]
+
+
+# ------------------------------------------------------------------ MLE restart (R32)
+def test_mle_restart_with_the_exact_vector_makes_it_the_null_vector_of_every_level():
+    """With the exact stationary vector x* as the state-vector test vector (its residual
+    is ~0, so it dominates every LS fit), the rebuilt P_l reproduce its injections and
+    B_{l+1} (R_l ... R_0 x*) = Q_l B_l x* ~ 0 on every level, and B_L^+ is recomputed
+    from the rebuilt B_L.  Not injecting x* down, or not replacing column 0, fails."""
+    ch = grid_walk(33)
+    o = ob.Opts(ridge=1e-12)
+    H = ob.setup(ch.to_scipy(), 6, 10, o, grid=ch.grid)
+    xe = exact.exact_stationary(ch)
+    before = [np.abs(lv.B @ lv.V[:, 0]).sum() / np.abs(lv.V[:, 0]).sum() for lv in H.levels[1:]]
+    ob.mle_restart(H, xe)
+    v = xe.copy()
+    for l, lv in enumerate(H.levels[:-1]):
+        c2f = np.flatnonzero(lv.cf)[np.argsort(lv.cidx[lv.cf], kind="stable")]
+        v = v[c2f]
+        Bc = H.levels[l + 1].B
+        ratio = np.abs(Bc @ v).sum() / (abs(Bc).sum(axis=0).A1 @ np.abs(v))
+        assert ratio < 1e-9, (l, ratio, before[l])
+    assert np.allclose(H.pinv, ob.pinv_truncated(H.levels[-1].B.toarray()), atol=0)
+
+
+def test_solve_with_mle_restarts_reaches_the_closed_form():
+    """Short restart cycles force several MLE restarts; the restarted solve still reaches
+    the exact vector, and counts one MLE restart per failed cycle."""
+    ch = grid_walk(33)
+    o = ob.Opts(gmres_m=3, max_it=200, tv_lo=0.0, tv_hi=1.0)
+    H = ob.setup(ch.to_scipy(), 6, 10, o, grid=ch.grid)
+    x, st = ob.solve(H, 1e-12)
+    assert st["converged"] and st["mle_restarts"] >= 1
+    assert st["mle_restarts"] == st["restarts"]
+    assert _rel(x, exact.exact_stationary(ch)) < 1e-8
+
+
+# ------------------------------------------------------------------ pArnoldi (Section 4.3)
+def test_ritz_value_closest_to_zero_of_a_known_spectrum():
+    rng = np.random.default_rng(3)
+    lam = np.array([0.9, -0.013, 1.7, 0.4 + 0.0j, 2.5])
+    S = rng.standard_normal((5, 5))
+    Hk = S @ np.diag(lam.real) @ np.linalg.inv(S)
+    theta, eta = ob.ritz_closest_to_zero(Hk)
+    assert abs(theta + 0.013) < 1e-12
+    v = S[:, 1] / np.linalg.norm(S[:, 1])
+    v = v if v[np.argmax(np.abs(v))] > 0 else -v
+    assert np.allclose(eta, v, atol=1e-10)
+
+
+def _dense_vcycle(H):
+    n = H.levels[0].B.shape[0]
+    return np.column_stack([ob.vcycle(H, e) for e in np.eye(n)])
+
+
+def test_parnoldi_is_rayleigh_ritz_on_the_krylov_space_of_CB():
+    """After k steps the Ritz vector equals the Rayleigh-Ritz vector of C B on
+    span{y, CBy, ..., (CB)^(k-1) y}, built here from the dense operator and a QR basis.
+    Using B C instead of C B, a wrong Hessenberg entry or the wrong Ritz value fails."""
+    ch = grid_walk(9)
+    o = ob.Opts(tv_lo=0.0, tv_hi=1.0)
+    H = ob.setup(ch.to_scipy(), 6, 5, o, grid=ch.grid)
+    C = _dense_vcycle(H)
+    B = H.levels[0].B.toarray()
+    M = C @ B
+    y = H.x_init
+    for k in (2, 3, 4):
+        K = np.column_stack([np.linalg.matrix_power(M, i) @ y for i in range(k)])
+        Qk, _ = np.linalg.qr(K)
+        theta, eta = ob.ritz_closest_to_zero(Qk.T @ M @ Qk)
+        xr = Qk @ eta
+        xr = xr / xr.sum()
+        x, st = ob.parnoldi(H, 0.0, m=k, max_it=k)
+        assert st["iterations"] == k
+        assert _rel(x, xr) < 1e-9
+
+
+def test_parnoldi_reaches_the_closed_form():
+    ch = grid_walk(17)
+    o = ob.Opts(tv_lo=0.0, tv_hi=1.0)
+    H = ob.setup(ch.to_scipy(), 6, 10, o, grid=ch.grid)
+    x, st = ob.parnoldi(H, 1e-12)
+    assert st["converged"]
+    assert _rel(x, exact.exact_stationary(ch)) < 1e-9
+    assert st["iterations"] <= 15
