@@ -35,6 +35,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 STREAM_TV = 0  # stream k: test vector k
 STREAM_CR = 1 << 22  # + (level << 8) + round: CR start vectors
 STREAM_MIS = 1 << 23  # + (level << 8) + call: independent-set priorities
+STREAM_COLOUR = 1 << 21  # + (level << 8) + colour: priorities of the smoother's colouring
 
 
 def splitmix64_output(state: np.ndarray) -> np.ndarray:
@@ -105,6 +106,7 @@ class Opts:
     mu: int = 1  # Algorithm 3's loop count: 1 = V-cycle setup, 2 = W-cycle setup
     setup_cycles: int = 1  # MLE cycles before the final rebuild (R33; the tables' V^2 = 2)
     mle_restart: bool = True  # R32: an MLE restart after every pGMRES cycle that fails
+    smoother: str = "jacobi"  # V-cycle smoother: "jacobi" (omega-Jacobi) or "mcgs" (R34)
 
 
 # ---------------------------------------------------------------------------------
@@ -257,6 +259,32 @@ def coarsen_cr(B, level: int, opts: Opts):
         cf = cf | independent_set(S, slow, opts.seed, STREAM_MIS + (level << 8) + rounds)
     cidx = np.where(cf, np.cumsum(cf) - 1, -1).astype(np.int64)
     return cf, cidx, rounds
+
+
+def multicolour(B, level: int, seed: int) -> list:
+    """R34, the colour classes of the multicolour Gauss-Seidel smoother (Section 3 names
+    Gauss-Seidel beside Jacobi): colour c is a maximal independent set (R18's rule, own
+    priority stream per level and colour) of the states the earlier colours left, in
+    the symmetrised graph of B, so no two states of a colour share an entry of B.
+    Returns the states of each colour, ascending."""
+    S = _sym_adjacency(B)
+    left = np.ones(B.shape[0], dtype=bool)
+    colours = []
+    while left.any():
+        ind = independent_set(S, left, seed, STREAM_COLOUR + (level << 8) + len(colours))
+        colours.append(np.flatnonzero(ind))
+        left &= ~ind
+    return colours
+
+
+def gs_sweep(B, dinv: np.ndarray, b: np.ndarray, x: np.ndarray, colours: list, reverse: bool) -> np.ndarray:
+    """One multicolour Gauss-Seidel sweep on B x = b: colour by colour (ascending, or
+    descending with reverse), x_i <- x_i + (b_i - (B x)_i) / b_ii for the states i of the
+    colour, with the x of the earlier colours already updated (R34)."""
+    x = np.array(x, dtype=np.float64, copy=True)
+    for rows in (colours[::-1] if reverse else colours):
+        x[rows] = x[rows] + dinv[rows] * (b[rows] - B[rows] @ x)
+    return x
 
 
 # ---------------------------------------------------------------------------------
@@ -529,6 +557,7 @@ class Level:
     cgrid: tuple | None = None  # grid of level l+1 (full coarsening)
     coarsest: bool = False
     kinds: np.ndarray | None = None  # coarsest level: 0 real, 1 Re, 2 Im of a complex pair
+    colours: list | None = None  # multicolour Gauss-Seidel classes (R34)
 
 
 @dataclass
@@ -692,8 +721,12 @@ def rebuild(lvs: list, opts: Opts):
 
 
 def _finish(H: "Hierarchy"):
-    """B_L^+ of the rebuilt coarsest matrix and the initial guess V_0[:, 0] / 1^T V_0[:, 0]."""
+    """B_L^+ of the rebuilt coarsest matrix and the initial guess V_0[:, 0] / 1^T V_0[:, 0];
+    with the multicolour smoother, the colour classes of every rebuilt B_l (R34)."""
     H.pinv = pinv_truncated(H.levels[-1].B.toarray())
+    if H.opts.smoother == "mcgs":
+        for l, lv in enumerate(H.levels[:-1]):
+            lv.colours = multicolour(lv.B, l, H.opts.seed)
     x0 = H.levels[0].V[:, 0].copy()
     H.x_init = x0 / x0.sum()
 
@@ -782,6 +815,9 @@ def mle_restart(H: Hierarchy, x: np.ndarray):
         if lvs[l + 1].sel is not None:
             lvs[l + 1].sel[0] = True
     H.pinv = pinv_truncated(lvs[-1].B.toarray())
+    if H.opts.smoother == "mcgs":
+        for l, lv in enumerate(lvs[:-1]):
+            lv.colours = multicolour(lv.B, l, H.opts.seed)
     H.stats["mle_restarts"] = H.stats.get("mle_restarts", 0) + 1
 
 
@@ -791,20 +827,22 @@ def mle_restart(H: Hierarchy, x: np.ndarray):
 def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
     """z = C_l b with error propagator I - C_l B_l = S^nu2 (I - P_l C_{l+1} Q_l B_l) S^nu1,
     S = I - omega D^{-1} B_l (Eq. (4.4)), zero initial guess, and C_L = B_L^+ on the
-    coarsest level."""
+    coarsest level.  With smoother "mcgs" (R34) S is a multicolour Gauss-Seidel sweep,
+    colours ascending before the coarse correction and descending after it."""
     o = H.opts
     if l == H.L:
         return H.pinv @ b
     lv = H.levels[l]
     dinv = 1.0 / diag_of(lv.B)
     x = np.zeros_like(b)
+    gs = o.smoother == "mcgs"
     for _ in range(o.nu_pre):
-        x = x + o.omega * dinv * (b - lv.B @ x)
+        x = gs_sweep(lv.B, dinv, b, x, lv.colours, False) if gs else x + o.omega * dinv * (b - lv.B @ x)
     r = b - lv.B @ x
     ec = vcycle(H, lv.Q @ r, l + 1)
     x = x + lv.P @ ec
     for _ in range(o.nu_post):
-        x = x + o.omega * dinv * (b - lv.B @ x)
+        x = gs_sweep(lv.B, dinv, b, x, lv.colours, True) if gs else x + o.omega * dinv * (b - lv.B @ x)
     return x
 
 

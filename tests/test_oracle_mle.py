@@ -257,3 +257,88 @@ def test_parnoldi_reaches_the_closed_form():
     assert st["converged"]
     assert _rel(x, exact.exact_stationary(ch)) < 1e-9
     assert st["iterations"] <= 15
+
+
+# ------------------------------------------------------------------ multicolour Gauss-Seidel (R34)
+def test_multicolour_classes_are_a_greedy_independent_set_colouring():
+    """Every state gets one colour; no entry of B joins two states of a colour; and colour c
+    is maximal among the states the earlier colours left (each later state has a neighbour
+    in it).  A colouring that skips the maximality step or the symmetrisation fails."""
+    ch = delaunay_walk(500, 2)
+    B = ob.system_matrix(ch.to_scipy())
+    cols = ob.multicolour(B, 0, 0)
+    n = B.shape[0]
+    colour = np.full(n, -1)
+    for c, rows in enumerate(cols):
+        assert np.all(colour[rows] == -1)
+        colour[rows] = c
+        assert np.array_equal(rows, np.sort(rows))
+    assert np.all(colour >= 0)
+    S = ob._sym_adjacency(B).tocoo()
+    assert np.all(colour[S.row] != colour[S.col])
+    Sc = S.tocsr()
+    for i in range(n):
+        nb = Sc.indices[Sc.indptr[i]:Sc.indptr[i + 1]]
+        for c in range(colour[i]):
+            assert np.any(colour[nb] == c), (i, c)
+
+
+def test_gs_sweep_is_sequential_gauss_seidel_in_colour_order():
+    """Within a colour no state reads another's value, so the colour-wise update equals a
+    plain Gauss-Seidel sweep state by state in colour order (ascending, or descending for
+    reverse); using the values from before the sweep (Jacobi) differs."""
+    ch = tandem_queue(12)
+    B = ob.system_matrix(ch.to_scipy()).tocsr()
+    cols = ob.multicolour(B, 1, 5)
+    d = B.diagonal()
+    rng = np.random.default_rng(0)
+    b, x0 = rng.standard_normal(ch.n), rng.standard_normal(ch.n)
+    for reverse in (False, True):
+        got = ob.gs_sweep(B, 1.0 / d, b, x0, cols, reverse)
+        x = x0.copy()
+        for rows in (cols[::-1] if reverse else cols):
+            for i in rows:
+                s = sum(B.data[p] * x[B.indices[p]] for p in range(B.indptr[i], B.indptr[i + 1]))
+                x[i] += (b[i] - s) / d[i]
+        assert np.allclose(got, x, rtol=0, atol=1e-13)
+    jac = x0 + (b - B @ x0) / d
+    assert not np.allclose(ob.gs_sweep(B, 1.0 / d, b, x0, cols, False), jac)
+
+
+def test_mcgs_vcycle_matches_its_error_propagator():
+    """Eq. (4.4) with the Gauss-Seidel sweeps: I - C_l B_l = S_post^nu2 (I - P C_{l+1} Q B) S_pre^nu1
+    with S_pre = (I - E_K D^-1 B) ... (I - E_1 D^-1 B) (colours 1..K ascending; E_c the
+    diagonal indicator of colour c) and S_post the same product in the other order."""
+    ch = grid_walk(13)
+    o = ob.Opts(smoother="mcgs", coarse_max=10)
+    H = ob.setup(ch.to_scipy(), 6, 10, o, grid=ch.grid)
+    assert H.L >= 2
+    C_next = H.pinv
+    for l in range(H.L - 1, -1, -1):
+        lv = H.levels[l]
+        n = lv.B.shape[0]
+        Bd = lv.B.toarray()
+        Dinv = np.diag(1.0 / np.diag(Bd))
+        steps = []
+        for rows in lv.colours:
+            E = np.zeros((n, n))
+            E[rows, rows] = 1.0
+            steps.append(np.eye(n) - E @ Dinv @ Bd)
+        S_pre = np.eye(n)
+        for M in steps:
+            S_pre = M @ S_pre
+        S_post = np.eye(n)
+        for M in steps[::-1]:
+            S_post = M @ S_post
+        Cl = np.column_stack([ob.vcycle(H, e, l) for e in np.eye(n)])
+        E_ = np.linalg.matrix_power(S_post, o.nu_post) @ (np.eye(n) - lv.P.toarray() @ C_next @ lv.Q.toarray() @ Bd) \
+            @ np.linalg.matrix_power(S_pre, o.nu_pre)
+        assert np.allclose(np.eye(n) - Cl @ Bd, E_, atol=1e-12)
+        C_next = Cl
+
+
+def test_mcgs_solve_reaches_the_closed_form():
+    ch = delaunay_walk(800, 4)
+    o = ob.Opts(smoother="mcgs", coarsen="cr", tv_lo=0.0, tv_hi=1.0)
+    x, H, st = ob.stationary(ch.to_scipy(), 8, 10, 1e-13, o, grid=None)
+    assert st["converged"] and _rel(x, exact.exact_stationary(ch)) < 1e-9
