@@ -82,7 +82,7 @@ typedef struct {
     int32_t mmax;       /* candidates kept per fine point, closest first (<= 16) */
     int32_t k_ev;       /* coarsest-level eigenvectors carried up (Section 5.1: 6) */
     int32_t coarse_max; /* stop coarsening at n_l <= coarse_max (<= 64) */
-    int32_t gmres_m;    /* FGMRES restart length (<= 64) */
+    int32_t gmres_m;    /* FGMRES restart length (<= 256) */
     int32_t max_it;     /* total FGMRES iteration cap */
     int32_t precision;  /* BAMG_PREC_FP64 or BAMG_PREC_MIXED (FP32 setup + V-cycle) */
     int32_t coarsen;    /* BAMG_COARSEN_GRID (needs grid_nx, grid_ny) or BAMG_COARSEN_CR */
@@ -107,7 +107,22 @@ typedef struct {
     int32_t device_loop;    /* 1 (default): between true-residual checks the Arnoldi steps run in a
                                device-side loop (a CUDA graph WHILE node, one host wait per check);
                                0: one graph launch and one host wait per step.  Same iterates. */
+    /* setup cycling and restarts (Section 4.1; Section 5.1) */
+    int32_t mle_restart;    /* 1 (default): after every FGMRES restart cycle that ends above tol, an MLE
+                               restart: the iterate becomes the state-vector test vector of every level
+                               (injected downwards) and all P_l, B_l, T_l and B_L^+ are rebuilt before
+                               the next cycle ("alternate several times between the MLE and AMG-GMRES
+                               iterations", Section 4.1); 0: plain restarts */
+    int32_t setup_cycles;   /* MLE cycles in the setup before the final rebuild (1; the tables' V^2 = 2) */
+    int32_t mu;             /* Algorithm 3's loop count: 1 = V-cycle setup, 2 = W-cycle setup */
+    int32_t smoother;       /* V-cycle smoother: BAMG_SMOOTH_JACOBI (omega-Jacobi, Section 3; default) or
+                               BAMG_SMOOTH_MCGS (multicolour Gauss-Seidel, Section 3's other relaxation:
+                               colour c is an independent set of the states the earlier colours left in
+                               the symmetrised graph of B_l; colours ascending before the coarse
+                               correction, descending after it; the setup's relaxations stay Jacobi) */
 } bamg_opts;
+
+enum { BAMG_SMOOTH_JACOBI = 0, BAMG_SMOOTH_MCGS = 1 };
 
 enum { BAMG_INTERP_LS = 0, BAMG_INTERP_LEARNED = 1 };
 
@@ -121,6 +136,7 @@ typedef struct {
     double solve_ms;      /* wall time of this bamg_solve */
     int32_t host_waits;   /* host synchronisations on Arnoldi steps: one per step, or one per
                              estimate-triggered check where the steps loop on the device */
+    int32_t mle_restarts; /* MLE restarts between restart cycles (bamg_opts.mle_restart) */
 } bamg_stats;
 
 typedef struct bamg_handle bamg_handle;
@@ -135,12 +151,14 @@ int bamg_default_opts(bamg_opts* o);
  * Errors: EINVAL (sizes, r, options, grid dims), ENOTSTOCH, ENOMEM, ECUDA, ENUMERIC. */
 int bamg_setup(const bamg_csr* A, int r, int levels, const bamg_opts* o, bamg_handle** h);
 
-enum { BAMG_X_GUESS = 1, BAMG_X_HOST = 2 };
+enum { BAMG_X_GUESS = 1, BAMG_X_HOST = 2, BAMG_NORM_L2 = 4 };
 /* Preconditioned flexible GMRES on B x = 0 (Section 4.2) until
  * ||B x||_1 / ||x||_1 <= tol, then x is scaled to 1^T x = 1.
  * x: n doubles, device memory unless flags has BAMG_X_HOST.  With BAMG_X_GUESS the
  * incoming x is the initial guess, otherwise the setup's state-vector approximation
- * (Section 4.1) is used.  st may be NULL.  Errors: ENOCONV (x holds the last iterate),
+ * (Section 4.1) is used.  With BAMG_NORM_L2 the stopping test is ||B x||_2 / ||x||_2 <= tol
+ * (Section 5.1's criterion; st->residual_l1 still reports the l1 ratio).
+ * st may be NULL.  Errors: ENOCONV (x holds the last iterate),
  * ENUMERIC, ECUDA. */
 int bamg_solve(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st);
 
@@ -158,6 +176,34 @@ int bamg_solve(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st)
  * message in bamg_last_error); the other chains are still solved. */
 int bamg_solve_batch(int nchains, const bamg_csr* As, const int* r, const int* levels, const bamg_opts* opts,
                      double* const* xs, int flags, double tol, int nworkers, bamg_stats* st);
+
+/* The MLE as a stand-alone solver (Section 4.1; the "MLE" rows of Tables 1, 2 and 4):
+ * MLE cycles (Algorithm 3 with loop count o->mu) from the random test vectors until the
+ * state-vector approximation x = V_0[:, 0] meets ||B x||_1 / ||x||_1 <= tol (with
+ * BAMG_NORM_L2 in flags: ||B x||_2 / ||x||_2 <= tol, Section 5.1's criterion) or
+ * max_cycles cycles ran.  Algorithm 3 empties V_l at the start of a call; that is read as
+ * holding on the first visit of level l only, so every later cycle relaxes V_l (nu_ev
+ * shifted sweeps) on the way down and fits P_l to U_l and the selected V_l, and U_l is
+ * relaxed on the first visit only.  x: n doubles (device memory, or host with
+ * BAMG_X_HOST) receiving the last approximation with 1^T x = 1 (may be NULL).
+ * st->iterations = cycles, st->residual_l1 = its l1 ratio.  h (may be NULL) receives the
+ * hierarchy, rebuilt from the final test sets, for bamg_solve / bamg_parnoldi (the
+ * "alternate MLE and AMG-GMRES" use); it is returned with ENOCONV too.
+ * Errors: as bamg_setup, plus ENOCONV when max_cycles cycles did not reach tol. */
+int bamg_mle_solve(const bamg_csr* A, int r, int levels, const bamg_opts* o, double tol, int max_cycles, int flags,
+                   double* x, bamg_stats* st, bamg_handle** h);
+
+/* Multigrid-preconditioned Arnoldi (Section 4.3): orthonormal v_1, v_2, ... of the Krylov
+ * space of C B (C = the V(nu_pre, nu_post) cycle, left preconditioning) from y = the
+ * setup's state-vector approximation (or x with BAMG_X_GUESS); the eigenvector eta of
+ * H_k = V_k^T C B V_k for its eigenvalue closest to 0 (inverse iteration with shift 0 on
+ * H_k: it converges when that eigenvalue is real and simple, as the eigenvalue 0 of C B
+ * is); the Ritz vector V_k eta, whose true residual is tested after every step (l1 ratio,
+ * or the 2-norm ratio with BAMG_NORM_L2).  The Gram-Schmidt process is the FGMRES one
+ * (FP64, one reorthogonalisation); after min(gmres_m, 64) steps the process restarts from
+ * the Ritz vector.  x receives the result with 1^T x = 1.  Errors: ENOCONV (x holds the
+ * last Ritz vector), ENUMERIC, ECUDA. */
+int bamg_parnoldi(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st);
 
 /* Frees the handle and its device memory.  NULL is allowed. */
 void bamg_free(bamg_handle* h);

@@ -67,6 +67,8 @@ def default_opts(**kw) -> capi.Opts:
     if "model" in kw:
         m = kw.pop("model")
         kw["model"] = m._h.value if m is not None else None
+    if "smoother" in kw and isinstance(kw["smoother"], str):
+        kw["smoother"] = {"jacobi": 0, "mcgs": 1}[kw["smoother"]]
     if "learned_refit" in kw:
         kw["learned_refit"] = int(bool(kw["learned_refit"]))
     if "grid" in kw:
@@ -109,9 +111,9 @@ class Solver:
         self._h, self.n, self.opts, self._keep = h, n, o, None
         return self
 
-    def solve(self, tol: float, x0=None, out=None, host: bool = False):
-        """Returns (x, stats).  x0: optional initial guess (same device as out)."""
-        flags = 0
+    def _out(self, out, host, x0, norm):
+        flags = capi.NORM_L2 if norm == "l2" else 0
+        assert norm in ("l1", "l2")
         if host:
             flags |= capi.X_HOST
             x = out if out is not None else torch.empty(self.n, dtype=torch.float64, pin_memory=True)
@@ -120,8 +122,26 @@ class Solver:
         if x0 is not None:
             x.copy_(x0)
             flags |= capi.X_GUESS
+        return x, flags
+
+    def solve(self, tol: float, x0=None, out=None, host: bool = False, norm: str = "l1"):
+        """Returns (x, stats).  x0: optional initial guess (same device as out).  norm:
+        "l1" (||Bx||_1/||x||_1 <= tol) or "l2" (the 2-norm ratio of the paper's tables)."""
+        x, flags = self._out(out, host, x0, norm)
         st = capi.Stats()
         code = _lib().bamg_solve(self._h, _p(x), flags, float(tol), C.byref(st))
+        stats = {f[0]: getattr(st, f[0]) for f in capi.Stats._fields_}
+        if code != capi.BAMG_OK:
+            err = BamgError(code, _lib().bamg_last_error().decode())
+            err.stats = stats
+            raise err
+        return x, stats
+
+    def parnoldi(self, tol: float, x0=None, out=None, host: bool = False, norm: str = "l1"):
+        """Multigrid-preconditioned Arnoldi (bamg_parnoldi).  Returns (x, stats)."""
+        x, flags = self._out(out, host, x0, norm)
+        st = capi.Stats()
+        code = _lib().bamg_parnoldi(self._h, _p(x), flags, float(tol), C.byref(st))
         stats = {f[0]: getattr(st, f[0]) for f in capi.Stats._fields_}
         if code != capi.BAMG_OK:
             err = BamgError(code, _lib().bamg_last_error().decode())
@@ -250,6 +270,7 @@ def solve_batch(chains, r, levels, tol: float, opts=None, workers: int = 0, host
     if code != capi.BAMG_OK:
         err = BamgError(code, _lib().bamg_last_error().decode())
         err.stats = stats
+        err.xs = outs  # every chain's result (the failed ones hold their last iterate)
         raise err
     return outs, stats
 
@@ -419,6 +440,33 @@ def autotune_report():
     capi.check(min(k, 0))
     names = ("elem_bytes", "shift", "entry_batch", "chunks_per_row", "log2_n", "chunks_per_thread", "blocks_per_sm")
     return [dict(zip(names, rows[7 * r:7 * r + 7])) for r in range(k)]
+
+
+def mle_solve(row_ptr, col, val, r: int, levels: int, tol: float, max_cycles: int = 50, norm: str = "l1",
+              keep: bool = False, **opts):
+    """The MLE as a stand-alone solver (bamg_mle_solve): returns (x, stats, solver or None).
+    With keep=True the rebuilt hierarchy comes back as a Solver (also when the MLE did not
+    converge; stats["status"] then says so) for a following solve() or parnoldi()."""
+    o = default_opts(**opts)
+    o.stream = _stream().value
+    n = int(row_ptr.numel() - 1)
+    A = capi.Csr(n, int(col.numel()), _p(_i32(row_ptr)).value, _p(_i32(col)).value, _p(val).value, 0)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    st = capi.Stats()
+    h = C.c_void_p(0)
+    flags = capi.NORM_L2 if norm == "l2" else 0
+    code = _lib().bamg_mle_solve(C.byref(A), r, levels, C.byref(o), float(tol), int(max_cycles), flags, _p(x),
+                                 C.byref(st), C.byref(h) if keep else None)
+    stats = {f[0]: getattr(st, f[0]) for f in capi.Stats._fields_}
+    solver = Solver._from_handle(h, n, o) if keep and h.value else None
+    if code not in (capi.BAMG_OK, capi.BAMG_ENOCONV) or (code != capi.BAMG_OK and not keep):
+        if solver is not None:
+            solver.close()
+        err = BamgError(code, _lib().bamg_last_error().decode())
+        err.stats = stats
+        raise err
+    stats["status"] = code
+    return x, stats, solver
 
 
 def relax_noalloc(B, X: torch.Tensor, ncols: int, col0: int, omega: float, nu: int, T_val=None, lam=None):

@@ -14,7 +14,7 @@ BAMG_OK, BAMG_EINVAL, BAMG_ENOTSTOCH, BAMG_ECUDA, BAMG_ENOMEM, BAMG_ENOCONV, BAM
 F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 COARSEN_GRID, COARSEN_CR = 0, 1
-X_GUESS, X_HOST = 1, 2
+X_GUESS, X_HOST, NORM_L2 = 1, 2, 4
 INTERP_LS, INTERP_LEARNED = 0, 1
 MLP_F, MLP_H, MLP_S = 112, 128, 16
 EXPORT_B, EXPORT_T, EXPORT_P, EXPORT_CF, EXPORT_X, EXPORT_PINV, EXPORT_XINIT, EXPORT_LAMBDA = range(8)
@@ -43,13 +43,14 @@ class Opts(C.Structure):
                 ("cr_theta", C.c_double), ("cr_nu", C.c_int32), ("cr_max_rounds", C.c_int32),
                 ("cr_omega", C.c_double), ("stream", C.c_void_p), ("interp", C.c_int32), ("learned_refit", C.c_int32),
                 ("model", C.c_void_p), ("learned_rho_max", C.c_double),
-                ("device_loop", C.c_int32)]
+                ("device_loop", C.c_int32), ("mle_restart", C.c_int32), ("setup_cycles", C.c_int32),
+                ("mu", C.c_int32), ("smoother", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("restarts", C.c_int32),
                 ("true_checks", C.c_int32), ("residual_l1", C.c_double), ("setup_ms", C.c_double),
-                ("solve_ms", C.c_double), ("host_waits", C.c_int32)]
+                ("solve_ms", C.c_double), ("host_waits", C.c_int32), ("mle_restarts", C.c_int32)]
 
 
 class LevelIn(C.Structure):
@@ -66,6 +67,8 @@ SIGNATURES = {
     "bamg_default_opts": (_I, [C.POINTER(Opts)]),
     "bamg_setup": (_I, [C.POINTER(Csr), _I, _I, C.POINTER(Opts), C.POINTER(_P)]),
     "bamg_solve": (_I, [_P, _P, _I, _D, C.POINTER(Stats)]),
+    "bamg_mle_solve": (_I, [C.POINTER(Csr), _I, _I, C.POINTER(Opts), _D, _I, _I, _P, C.POINTER(Stats), C.POINTER(_P)]),
+    "bamg_parnoldi": (_I, [_P, _P, _I, _D, C.POINTER(Stats)]),
     "bamg_free": (None, [_P]),
     "bamg_solve_batch": (_I, [_I, C.POINTER(Csr), C.POINTER(_I), C.POINTER(_I), C.POINTER(Opts), C.POINTER(_P), _I,
                               _D, _I, C.POINTER(Stats)]),

@@ -250,6 +250,7 @@ __device__ __forceinline__ double counter_uniform(uint64_t seed, uint64_t stream
 constexpr uint64_t STREAM_TV = 0;
 constexpr uint64_t STREAM_CR = 1ull << 22;
 constexpr uint64_t STREAM_MIS = 1ull << 23;
+constexpr uint64_t STREAM_COLOUR = 1ull << 21;  // + (level << 8) + colour: the smoother's colouring
 
 // 16-byte vector of T: 2 doubles or 4 floats.
 template <typename T>

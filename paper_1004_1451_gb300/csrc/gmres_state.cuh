@@ -5,7 +5,7 @@
 
 namespace bamg {
 
-constexpr int GMRES_MMAX = 64;
+constexpr int GMRES_MMAX = 256;
 
 struct GmresLayout {
     int h1, h2, R, cs, sn, g, y, nrm2, est, hn, total;

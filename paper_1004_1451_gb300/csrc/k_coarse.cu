@@ -678,8 +678,12 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
         }
     __shared__ int srcp[CN];
     if (tid == 0) lu_row_sources(n, perm, srcp);
+    // start vector in [1, 2) drawn per column (SplitMix64, stream = the column): for a
+    // multiple eigenvalue (the symmetric pairs of grid walks) each column converges to
+    // the projection of its own start onto the eigenspace, so the columns span it
+    // instead of repeating one vector
     if (tid < n) {
-        vr[tid] = F(1) + (F)tid / (F)n;
+        vr[tid] = (F)(1.0 + counter_uniform(0x243F6A8885A308D3ull, (uint64_t)blockIdx.x, (uint64_t)tid));
         vi[tid] = F(0);
     }
     __syncthreads();

@@ -268,6 +268,68 @@ int coarsen_cr(const MatView<T>& B, int level, uint64_t seed, double theta, int 
     return rounds;
 }
 
+// ---------------------------------------------------------------- colouring of the smoother
+// Colour c = an independent set (the rule above, priority stream STREAM_COLOUR + (level <<
+// 8) + c) of the states the earlier colours left, in the symmetrised graph of B, until
+// every state has a colour.  The classes go out as one row list sorted by (colour, state)
+// with host offsets ptr[0..ncol].
+__global__ void k_colour_take(int n, const uint8_t* __restrict__ chosen, int c, int32_t* __restrict__ colour,
+                              uint8_t* __restrict__ left, int* __restrict__ remaining) {
+    pdl_begin();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (chosen[i]) {
+        colour[i] = c;
+        left[i] = 0;
+    } else if (left[i]) {
+        atomicAdd(remaining, 1);
+    }
+}
+
+constexpr int MAX_COLOURS = 255;  // the stream encoding leaves 8 bits for the colour
+
+void colour_classes(int n, int nnz, const int32_t* rp, const int32_t* ci, int level, uint64_t seed,
+                    std::vector<int>& ptr, DevBuf<int32_t>& rows, cudaStream_t s) {
+    const unsigned g = blocks_for(n, 256);
+    TmpBuf<int32_t> cnt(n, s), rpT(n + 1, s), cursor(n, s);
+    BAMG_CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * n, s));
+    BAMG_CK(cudaMemsetAsync(cursor.get(), 0, sizeof(int32_t) * n, s));
+    BAMG_LAUNCH(k_tcount, g, 256, 0, s, n, rp, ci, cnt.get());
+    exclusive_scan(cnt.get(), rpT.get(), n, s);
+    TmpBuf<int32_t> ciT(nnz > 0 ? nnz : 1, s);
+    BAMG_LAUNCH(k_tfill, g, 256, 0, s, n, rp, ci, rpT.get(), cursor.get(), ciT.get());
+    TmpBuf<uint8_t> left(n, s), und(n, s), chosen(n, s);
+    TmpBuf<int32_t> colour(n, s);
+    TmpBuf<int> rem(1, s);
+    BAMG_CK(cudaMemsetAsync(left.get(), 1, n, s));
+    int ncol = 0;
+    for (int c = 0; c < MAX_COLOURS; ++c) {
+        BAMG_CK(cudaMemcpyAsync(und.get(), left.get(), n, cudaMemcpyDeviceToDevice, s));
+        BAMG_CK(cudaMemsetAsync(chosen.get(), 0, n, s));
+        independent_set(n, rp, ci, rpT.get(), ciT.get(), und.get(), chosen.get(), seed,
+                        STREAM_COLOUR + ((uint64_t)level << 8) + (uint64_t)c, s);
+        BAMG_CK(cudaMemsetAsync(rem.get(), 0, sizeof(int), s));
+        BAMG_LAUNCH(k_colour_take, g, 256, 0, s, n, (const uint8_t*)chosen.get(), c, colour.get(), left.get(),
+                    rem.get());
+        if (read_int(rem.get(), s) == 0) {
+            ncol = c + 1;
+            break;
+        }
+    }
+    BAMG_REQUIRE(ncol > 0, BAMG_ETIMEOUT, "colouring: more than 255 colours");
+    std::vector<int32_t> hc(n), hr(n);
+    BAMG_CK(cudaMemcpyAsync(hc.data(), colour.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    BAMG_CK(cudaStreamSynchronize(s));
+    ptr.assign(ncol + 1, 0);
+    for (int i = 0; i < n; ++i) ptr[hc[i] + 1]++;
+    for (int c = 0; c < ncol; ++c) ptr[c + 1] += ptr[c];
+    std::vector<int> at(ptr.begin(), ptr.end() - 1);
+    for (int i = 0; i < n; ++i) hr[at[hc[i]]++] = i;  // ascending states within a colour
+    rows.alloc(n);
+    BAMG_CK(cudaMemcpyAsync(rows.get(), hr.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    BAMG_CK(cudaStreamSynchronize(s));
+}
+
 template int coarsen_cr<float>(const MatView<float>&, int, uint64_t, double, int, double, int, uint8_t*, int32_t*,
                                int*, cudaStream_t);
 template int coarsen_cr<double>(const MatView<double>&, int, uint64_t, double, int, double, int, uint8_t*, int32_t*,

@@ -427,9 +427,71 @@ static T* final_x(const VLevel<T>& v, int nu_pre, int nu_post, bool coarsest) {
     return x;
 }
 
+// One multicolour Gauss-Seidel colour: x_i <- x_i + (b_i - (B x)_i) / b_ii for the cnt states
+// rows[0..cnt) of one colour, in place (no state of a colour reads another's value).
+template <typename T>
+__global__ void k_gs_colour(int cnt, const int32_t* __restrict__ rows, const int32_t* __restrict__ rp,
+                            const int32_t* __restrict__ ci, const T* __restrict__ bv, const T* __restrict__ dinv,
+                            const T* __restrict__ b, T* x) {
+    pdl_begin();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    const int i = rows[k];
+    const T bx = row_sum<T>(rp[i], rp[i + 1], ci, bv, [&](int j) { return x[j]; });
+    x[i] = x[i] + dinv[i] * (b[i] - bx);
+}
+
+template <typename T>
+static void gs_sweep(const VLevel<T>& v, bool reverse, cudaStream_t s) {
+    for (int q = 0; q < v.gs_ncol; ++q) {
+        const int c = reverse ? v.gs_ncol - 1 - q : q;
+        const int a = v.gs_ptr[c], cnt = v.gs_ptr[c + 1] - a;
+        if (cnt > 0)
+            BAMG_LAUNCH_PDL(k_gs_colour<T>, blocks_for(cnt, 256), 256, 0, s, cnt, v.gs_rows + a, v.B.rp, v.B.ci,
+                            v.B.v, v.dinv, (const T*)v.b, v.x);
+    }
+}
+
+// The V-cycle with the multicolour Gauss-Seidel smoother: zero guess, nu_pre sweeps with
+// the colours ascending, residual, restriction, recursion, B_L^+ on the coarsest level,
+// prolongation, nu_post sweeps with the colours descending.  One launch per colour.
+template <typename T>
+static void vcycle_gs(const std::vector<VLevel<T>>& lv, const T* pinv, int nu_pre, int nu_post, cudaStream_t s, T* Z,
+                      const int* dj) {
+    const int L = (int)lv.size() - 1;
+    for (int l = 0; l < L; ++l) {
+        const VLevel<T>& v = lv[l];
+        const int n = v.B.n;
+        BAMG_CK(cudaMemsetAsync(v.x, 0, sizeof(T) * n, s));
+        for (int k = 0; k < nu_pre; ++k) gs_sweep(v, false, s);
+        BAMG_LAUNCH_PDL(k_resid<T>, blocks_for(n, 256), 256, 0, s, n, v.B.rp, v.B.ci, v.B.v, (const T*)v.b,
+                        (const T*)v.x, v.r);
+        const int nc = lv[l + 1].B.n;
+        BAMG_LAUNCH_PDL(k_restrict<T>, blocks_for(nc, 256), 256, 0, s, nc, v.qrp, v.qci, v.qv, (const T*)v.r,
+                        lv[l + 1].b);
+    }
+    const int nL = lv[L].B.n;
+    BAMG_LAUNCH_PDL(k_dense_mv<T>, blocks_for(nL, 4), 128, 0, s, nL, pinv, (const T*)lv[L].b, lv[L].x);
+    for (int l = L - 1; l >= 0; --l) {
+        const VLevel<T>& v = lv[l];
+        const int n = v.B.n;
+        BAMG_LAUNCH_PDL(k_prolong_add<T>, blocks_for(n, 256), 256, 0, s, n, v.P.c, v.P.pcol, v.P.pval, v.P.pcnt,
+                        (const T*)lv[l + 1].x, v.x);
+        for (int k = 0; k < nu_post; ++k) gs_sweep(v, true, s);
+    }
+    if (Z) {
+        const int n = lv[0].B.n;
+        BAMG_LAUNCH_PDL(k_copy<T>, blocks_for(n, 256), 256, 0, s, n, (const T*)lv[0].x, lv[0].x, Z, dj);
+    }
+}
+
 template <typename T>
 void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int nu_pre, int nu_post, cudaStream_t s,
             T* Z, const int* dj) {
+    if (lv.size() > 1 && lv[0].gs_ncol > 0) {
+        vcycle_gs<T>(lv, pinv, nu_pre, nu_post, s, Z, dj);
+        return;
+    }
     const int L = (int)lv.size() - 1;
     const T omega = (T)omega_d;
     // the levels from l0 on (small enough for one block) run in k_vcycle_tail
@@ -645,44 +707,40 @@ void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const dou
     BAMG_LAUNCH(k_form_x<TZ>, blocks_for(n, 256), 256, 0, s, n, x0, Z, ldz, nz, d_y, x);
 }
 
-// sums of |Bx|, (Bx)^2, |x| and x over rows: per-block partials then a fixed-order sum.
+// sums of |Bx|, (Bx)^2, |x|, x and x^2 over rows: per-block partials then a fixed-order sum.
 __global__ void __launch_bounds__(256) k_resnorm_partial(int n, const int32_t* __restrict__ rp,
                                                          const int32_t* __restrict__ ci, const double* __restrict__ bv,
                                                          const double* __restrict__ x, double* __restrict__ partial) {
     pdl_begin();
-    __shared__ double sh[4][8];
+    __shared__ double sh[RESNORM_SUMS][8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double a = 0.0, b2 = 0.0, c = 0.0, d = 0.0;
+    double v[RESNORM_SUMS] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (i < n) {
         double s = 0.0;
         for (int p = rp[i]; p < rp[i + 1]; ++p) s += bv[p] * x[ci[p]];
-        a = fabs(s);
-        b2 = s * s;
-        c = fabs(x[i]);
-        d = x[i];
+        v[0] = fabs(s);
+        v[1] = s * s;
+        v[2] = fabs(x[i]);
+        v[3] = x[i];
+        v[4] = x[i] * x[i];
     }
-    a = warp_sum(a);
-    b2 = warp_sum(b2);
-    c = warp_sum(c);
-    d = warp_sum(d);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        sh[0][wid] = a;
-        sh[1][wid] = b2;
-        sh[2][wid] = c;
-        sh[3][wid] = d;
+#pragma unroll
+    for (int q = 0; q < RESNORM_SUMS; ++q) {
+        const double t = warp_sum(v[q]);
+        if (lane == 0) sh[q][wid] = t;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < RESNORM_SUMS) {
         double t = 0.0;
         for (int w = 0; w < 8; ++w) t += sh[threadIdx.x][w];
-        partial[(int64_t)blockIdx.x * 4 + threadIdx.x] = t;
+        partial[(int64_t)blockIdx.x * RESNORM_SUMS + threadIdx.x] = t;
     }
 }
 void residual_norms(const MatView<double>& B, const double* x, double* d_out, double* d_partial, cudaStream_t s) {
     const int nb = (int)blocks_for(B.n, 256);
     BAMG_LAUNCH(k_resnorm_partial, nb, 256, 0, s, B.n, B.rp, B.ci, B.v, x, d_partial);
-    BAMG_LAUNCH(k_reduce_cols, 1, 128, 0, s, nb, 4, d_partial, d_out);
+    BAMG_LAUNCH(k_reduce_cols, blocks_for(RESNORM_SUMS, 4), 128, 0, s, nb, RESNORM_SUMS, d_partial, d_out);  // a warp per sum
 }
 
 // y = x * num or x / num with num = d_num[num_idx] (a device scalar).
@@ -698,41 +756,6 @@ void scale_vec(int n, double* x, const double* d_num, int num_idx, bool reciproc
     BAMG_LAUNCH(k_scale_vec, blocks_for(n, 256), 256, 0, s, n, x, d_num, num_idx, reciprocal ? 1 : 0, y);
 }
 
-// Givens update of column j (Saad, Iterative Methods for Sparse Linear Systems, Alg. 6.9
-// as a rotation sequence): h = h1 + h2 from the two Gram-Schmidt passes, h_{j+1,j} =
-// sqrt(nrm2); previous rotations are applied, a new one annihilates h_{j+1,j}, and
-// |g_{j+1}| is the residual norm of the least-squares problem.
-__global__ void k_givens(double* __restrict__ st, int j, int m) {
-    pdl_begin();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    GmresLayout L(m);
-    double col[GMRES_MMAX + 1];
-    for (int i = 0; i <= j; ++i) col[i] = st[L.h1 + i] + st[L.h2 + i];
-    const double hn = sqrt(st[L.nrm2]);
-    col[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-        const double c = st[L.cs + i], s = st[L.sn + i];
-        const double a = col[i], b = col[i + 1];
-        col[i] = c * a + s * b;
-        col[i + 1] = -s * a + c * b;
-    }
-    const double a = col[j], b = col[j + 1];
-    const double den = hypot(a, b);
-    const double c = den == 0.0 ? 1.0 : a / den, s = den == 0.0 ? 0.0 : b / den;
-    st[L.cs + j] = c;
-    st[L.sn + j] = s;
-    col[j] = c * a + s * b;
-    const double gj = st[L.g + j];
-    st[L.g + j + 1] = -s * gj;
-    st[L.g + j] = c * gj;
-    for (int i = 0; i <= j; ++i) st[L.R + i + (int64_t)j * m] = col[i];
-    st[L.est] = fabs(st[L.g + j + 1]);
-    st[L.hn] = hn;
-}
-void gmres_arnoldi_step(double* d_state, int j, int m, cudaStream_t s) {
-    BAMG_LAUNCH(k_givens, 1, 32, 0, s, d_state, j, m);
-}
-
 // Start of a cycle: beta = ||r0||_2 from nrm2, g = beta e_1; hn = beta scales v_1.
 __global__ void k_gmres_init(double* __restrict__ st, int m) {
     pdl_begin();
@@ -746,24 +769,23 @@ __global__ void k_gmres_init(double* __restrict__ st, int m) {
 }
 void gmres_init(double* d_state, int m, cudaStream_t s) { BAMG_LAUNCH(k_gmres_init, 1, 32, 0, s, d_state, m); }
 
-// y = R^{-1} g for the leading (j+1) x (j+1) block: R and g staged in shared memory,
-// column-oriented back substitution by one warp.
+// y = R^{-1} g for the leading (j+1) x (j+1) block: column-oriented back substitution by
+// one warp, R read from the state in global memory (column-major, consecutive lanes read
+// consecutive rows of a column), y in shared memory.
 __global__ void k_solve_y(double* __restrict__ st, int j, int m) {
     pdl_begin();
-    __shared__ double R[GMRES_MMAX * GMRES_MMAX], y[GMRES_MMAX];
+    __shared__ double y[GMRES_MMAX];
     GmresLayout L(m);
     const int lane = threadIdx.x;
-    for (int idx = lane; idx < (j + 1) * (j + 1); idx += 32) {
-        const int r = idx % (j + 1), c = idx / (j + 1);
-        R[r * GMRES_MMAX + c] = st[L.R + r + (int64_t)c * m];
-    }
+    const double* R = st + L.R;
     for (int r = lane; r <= j; r += 32) y[r] = st[L.g + r];
     __syncwarp();
     for (int q = j; q >= 0; --q) {
-        if (lane == 0) y[q] /= R[q * GMRES_MMAX + q];
+        const double* col = R + (int64_t)q * m;
+        if (lane == 0) y[q] /= col[q];
         __syncwarp();
         const double yq = y[q];
-        for (int r = lane; r < q; r += 32) y[r] -= R[r * GMRES_MMAX + q] * yq;
+        for (int r = lane; r < q; r += 32) y[r] -= col[r] * yq;
         __syncwarp();
     }
     for (int r = lane; r <= j; r += 32) st[L.y + r] = y[r];
@@ -979,6 +1001,181 @@ template void arnoldi_step_graphable<double>(int, const MatView<double>&, double
                                              double*, int, double*, const std::vector<VLevel<double>>&,
                                              const double*, double, int, int, double*, const double*,
                                              cudaGraphConditionalHandle, cudaStream_t);
+
+// ---------------------------------------------------------------- preconditioned Arnoldi
+// Section 4.3: Arnoldi on the left-preconditioned matrix C B.  One step: vin = B v_j in
+// FP64 rounded to the V-cycle's arithmetic, z = C vin (one V-cycle), w = V[j+1] = z in
+// FP64 with its per-tile dots against V[0..j]; the two Gram-Schmidt passes and the
+// scaling are the FGMRES kernels'; the raw Hessenberg column is kept in H.
+template <typename T>
+__global__ void k_parn_bv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ bv, const double* __restrict__ V, const int* __restrict__ dj,
+                          T* __restrict__ vin) {
+    pdl_begin();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* v = V + (int64_t)(*dj) * n;
+    vin[i] = (T)row_sum<double>(rp[i], rp[i + 1], ci, bv, [&](int c) { return v[c]; });
+}
+
+template <typename TX>
+__global__ void __launch_bounds__(256) k_parn_store_dots(int n, int tile, const TX* __restrict__ z,
+                                                         const int* __restrict__ dj, double* __restrict__ V,
+                                                         double* __restrict__ Pout, int stride) {
+    pdl_begin();
+    const int j = *dj;
+    const int r0 = blockIdx.x * tile, cnt = min(tile, n - r0);
+    double* w = V + (int64_t)(j + 1) * n;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) w[r0 + e] = (double)z[r0 + e];
+    __syncthreads();
+    arn_tile_dots(V, n, j, r0, cnt, w, 0, Pout, stride);
+}
+
+// H[0..j, j] = h1 + h2 (the two Gram-Schmidt passes), H[j+1, j] = ||w||; column-major, ld ldh
+__global__ void k_parn_hess(const double* __restrict__ st, int m, const int* __restrict__ dj, double* __restrict__ H,
+                            int ldh) {
+    pdl_begin();
+    const GmresLayout L(m);
+    const int j = *dj;
+    for (int r = threadIdx.x; r <= j; r += blockDim.x) H[r + (int64_t)j * ldh] = st[L.h1 + r] + st[L.h2 + r];
+    if (threadIdx.x == 0) H[j + 1 + (int64_t)j * ldh] = sqrt(st[L.nrm2]);
+}
+
+// Eigenvector of the k x k upper Hessenberg H_k for its eigenvalue closest to 0 (Section 4.3),
+// by inverse iteration with shift 0: H_k = L U by Gaussian elimination with partial
+// pivoting between neighbouring rows (a Hessenberg column has one sub-diagonal entry),
+// then up to PARN_INV_ITERS solves from the all-ones vector, each normalised to unit
+// 2-norm with its largest-modulus entry positive, until two iterates agree to 1e-15.  A
+// zero pivot is replaced by 2^-52 times the largest entry of H_k (the matrix is singular
+// to working precision exactly when the Ritz value is 0).  One block, k <= PARN_MMAX.
+constexpr int PARN_INV_ITERS = 50;
+__global__ void __launch_bounds__(128) k_ritz_hess(const double* __restrict__ H, int ldh, int k,
+                                                   double* __restrict__ eta) {
+    pdl_begin();
+    __shared__ double A[PARN_MMAX][PARN_MMAX + 1];
+    __shared__ double mult[PARN_MMAX], y[PARN_MMAX], prev[PARN_MMAX];
+    __shared__ int swp[PARN_MMAX];
+    __shared__ double s_scale, s_norm;
+    __shared__ int s_done;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int e = tid; e < k * k; e += blockDim.x) {
+        const int r = e % k, c = e / k;
+        A[r][c] = H[r + (int64_t)c * ldh];
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double mx = 0.0;
+        for (int e = lane; e < k * k; e += 32) mx = fmax(mx, fabs(A[e % k][e / k]));
+        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_scale = mx > 0.0 ? mx * 0x1p-52 : 0x1p-1022;
+    }
+    __syncthreads();
+    for (int c = 0; c + 1 < k; ++c) {
+        if (tid == 0) swp[c] = fabs(A[c + 1][c]) > fabs(A[c][c]) ? 1 : 0;
+        __syncthreads();
+        if (swp[c])
+            for (int q = c + tid; q < k; q += blockDim.x) {
+                const double t = A[c][q];
+                A[c][q] = A[c + 1][q];
+                A[c + 1][q] = t;
+            }
+        __syncthreads();
+        if (tid == 0) {
+            if (A[c][c] == 0.0) A[c][c] = s_scale;
+            mult[c] = A[c + 1][c] / A[c][c];
+        }
+        __syncthreads();
+        for (int q = c + 1 + tid; q < k; q += blockDim.x) A[c + 1][q] -= mult[c] * A[c][q];
+        __syncthreads();
+    }
+    if (tid == 0 && A[k - 1][k - 1] == 0.0) A[k - 1][k - 1] = s_scale;
+    for (int r = tid; r < k; r += blockDim.x) {
+        y[r] = 1.0 / sqrt((double)k);
+        prev[r] = y[r];
+    }
+    if (tid == 0) s_done = 0;
+    __syncthreads();
+    for (int t = 0; t < PARN_INV_ITERS && !s_done; ++t) {
+        if (wid == 0) {
+            if (lane == 0)  // the row operations of the factorisation on the right-hand side
+                for (int c = 0; c + 1 < k; ++c) {
+                    if (swp[c]) {
+                        const double q = y[c];
+                        y[c] = y[c + 1];
+                        y[c + 1] = q;
+                    }
+                    y[c + 1] -= mult[c] * y[c];
+                }
+            __syncwarp();
+            for (int q = k - 1; q >= 0; --q) {  // U y = y, column by column
+                if (lane == 0) y[q] /= A[q][q];
+                __syncwarp();
+                const double yq = y[q];
+                for (int r = lane; r < q; r += 32) y[r] -= A[r][q] * yq;
+                __syncwarp();
+            }
+            double ss = 0.0, big = 0.0;
+            int at = 0;
+            for (int r = lane; r < k; r += 32) {
+                ss += y[r] * y[r];
+                if (fabs(y[r]) > big) big = fabs(y[r]), at = r;
+            }
+            for (int o = 16; o; o >>= 1) {
+                ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                const double ob = __shfl_xor_sync(0xffffffffu, big, o);
+                const int oa = __shfl_xor_sync(0xffffffffu, at, o);
+                if (ob > big || (ob == big && oa < at)) big = ob, at = oa;
+            }
+            const double sc = (y[at] < 0.0 ? -1.0 : 1.0) / sqrt(ss);
+            double dif = 0.0;
+            for (int r = lane; r < k; r += 32) {
+                y[r] *= sc;
+                dif = fmax(dif, fabs(y[r] - prev[r]));
+                prev[r] = y[r];
+            }
+            for (int o = 16; o; o >>= 1) dif = fmax(dif, __shfl_xor_sync(0xffffffffu, dif, o));
+            if (lane == 0) {
+                s_norm = ss;
+                s_done = (t > 0 && dif <= 1e-15) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+    }
+    for (int r = tid; r < k; r += blockDim.x) eta[r] = y[r];
+}
+
+template <typename T>
+void parnoldi_step(int n, const MatView<double>& B, double* V, T* vin, T* zout, int* dj, double* st, int m,
+                   double* H, int ldh, double* partial, const std::vector<VLevel<T>>& lv, const T* pinv, double omega,
+                   int nu_pre, int nu_post, cudaStream_t s) {
+    GmresLayout L(m);
+    const unsigned g = blocks_for(n, 256);
+    const int stride = m + 1;
+    BAMG_LAUNCH_PDL(k_parn_bv<T>, g, 256, 0, s, n, B.rp, B.ci, B.v, (const double*)V, (const int*)dj, vin);
+    vcycle<T>(lv, pinv, omega, nu_pre, nu_post, s, (T*)nullptr, (const int*)nullptr);
+    const int tile = arn_tile_rows(n), nt = arn_tiles(n);
+    double* Pa = partial;
+    double* Pb = partial + (size_t)nt * stride;
+    BAMG_LAUNCH_PDL(k_parn_store_dots<T>, nt, 256, 0, s, n, tile, (const T*)zout, (const int*)dj, V, Pa, stride);
+    BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pa, nt, st + L.h1,
+                    Pb, stride, 0);
+    BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pb, nt, st + L.h2,
+                    Pa, stride, 1);
+    BAMG_LAUNCH_PDL(k_givens_scale_j, g, 256, 0, s, n, V, (const int*)dj, st, m, (const double*)Pa, nt, stride);
+    BAMG_LAUNCH_PDL(k_parn_hess, 1, 64, 0, s, (const double*)st, m, (const int*)dj, H, ldh);
+    BAMG_LAUNCH_PDL(k_inc_j, 1, 32, 0, s, dj);
+}
+template void parnoldi_step<float>(int, const MatView<double>&, double*, float*, float*, int*, double*, int, double*,
+                                   int, double*, const std::vector<VLevel<float>>&, const float*, double, int, int,
+                                   cudaStream_t);
+template void parnoldi_step<double>(int, const MatView<double>&, double*, double*, double*, int*, double*, int,
+                                    double*, int, double*, const std::vector<VLevel<double>>&, const double*, double,
+                                    int, int, cudaStream_t);
+
+void ritz_closest_to_zero(const double* H, int ldh, int k, double* eta, cudaStream_t s) {
+    BAMG_REQUIRE(k >= 1 && k <= PARN_MMAX, BAMG_EINVAL, "pArnoldi: Hessenberg order out of range");
+    BAMG_LAUNCH(k_ritz_hess, 1, 128, 0, s, H, ldh, k, eta);
+}
 
 // `sweeps` sweeps of the smoother S of Eq. (4.4) on one level, ping-ponging between x and
 // y; the result ends in x (one copy when sweeps is odd).

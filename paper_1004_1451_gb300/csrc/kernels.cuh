@@ -150,6 +150,12 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
 // computed in FP32 arithmetic when fp32 is set, else in FP64.
 int coarse_pinv(int n, const double* dB, double* dP, bool fp32, cudaStream_t s);
 
+// Colour classes of the multicolour Gauss-Seidel smoother for the pattern (n, rp, ci):
+// repeated independent sets of the uncoloured states; rows sorted by (colour, state), host
+// offsets ptr[0..ncolours].
+void colour_classes(int n, int nnz, const int32_t* rp, const int32_t* ci, int level, uint64_t seed,
+                    std::vector<int>& ptr, DevBuf<int32_t>& rows, cudaStream_t s);
+
 // ------------------------------------------------------------------ k_solve.cu
 template <typename T>
 struct VLevel {  // one level of the V-cycle
@@ -161,6 +167,11 @@ struct VLevel {  // one level of the V-cycle
     const T* qv = nullptr;
     int qnnz = 0;                  // entries of Q
     T *b = nullptr, *x = nullptr, *r = nullptr;  // work vectors of n entries
+    // multicolour Gauss-Seidel smoother (gs_ncol > 0): rows sorted by colour (device) and
+    // the colour offsets gs_ptr[0..gs_ncol] (host memory owned by the hierarchy)
+    const int32_t* gs_rows = nullptr;
+    const int* gs_ptr = nullptr;
+    int gs_ncol = 0;
 };
 // One V-cycle: lv[0].b -> lv[0].x.  With Z != null the result is also stored at
 // Z + (*dj) * n_0.
@@ -182,6 +193,18 @@ void update_minus(int n, const double* V, int64_t ldv, int nv, const double* d_h
 template <typename TZ>
 void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const double* d_y, double* x, cudaStream_t s);
 // sum |B x|, sum (B x)^2, sum |x|, sum x into d_out[4] (deterministic).
+// Section 4.3 (preconditioned Arnoldi): one step on C B with the index j in *dj (raw
+// Hessenberg column into H, ld ldh), and the eigenvector of H_k for the eigenvalue closest
+// to 0 (inverse iteration with shift 0; k <= PARN_MMAX).
+constexpr int PARN_MMAX = 64;
+template <typename T>
+void parnoldi_step(int n, const MatView<double>& B, double* V, T* vin, T* zout, int* dj, double* st, int m,
+                   double* H, int ldh, double* partial, const std::vector<VLevel<T>>& lv, const T* pinv, double omega,
+                   int nu_pre, int nu_post, cudaStream_t s);
+void ritz_closest_to_zero(const double* H, int ldh, int k, double* eta, cudaStream_t s);
+// d_out[0..4] = sum |Bx|, sum (Bx)^2, sum |x|, sum x, sum x^2 (FP64, fixed order);
+// d_partial: blocks_for(n, 256) * RESNORM_SUMS doubles
+constexpr int RESNORM_SUMS = 5;
 void residual_norms(const MatView<double>& B, const double* x, double* d_out, double* d_partial, cudaStream_t s);
 void scale_vec(int n, double* x, const double* d_num, int num_idx, bool reciprocal, double* y, cudaStream_t s);
 void gmres_init(double* d_state, int m, cudaStream_t s);
@@ -196,7 +219,6 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
                             int m, double* partial, const std::vector<VLevel<T>>& lv, const T* pinv, double omega,
                             int nu_pre, int nu_post, double* h_est, const double* ctl,
                             cudaGraphConditionalHandle cond, cudaStream_t s);
-void gmres_arnoldi_step(double* d_state, int j, int m, cudaStream_t s);
 void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s);
 
 }  // namespace bamg

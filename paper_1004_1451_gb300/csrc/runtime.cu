@@ -84,6 +84,16 @@ __global__ void k_vf_axpy(int n, double* __restrict__ r, const double* __restric
     if (i < n) r[i] -= t[i];
 }
 
+// X[i * ld + col] = x_i / sqrt(nrm2[0]) (the MLE restart's state-vector column)
+template <typename T>
+__global__ void k_state_col(int n, const double* __restrict__ x, const double* __restrict__ nrm2, T* __restrict__ X,
+                            int ld, int col) {
+    pdl_begin();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double s = nrm2[0] > 0.0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
+    if (i < n) X[(int64_t)i * ld + col] = (T)(x[i] * s);
+}
+
 // active[k] = 1 for the random vectors, sel[q] for eigenvector column ldU + q, else 0.
 __global__ void k_active_mask(int r, int ldU, int nvec, int ld, const uint8_t* __restrict__ sel,
                               uint8_t* __restrict__ active) {
@@ -114,6 +124,8 @@ struct LevelT {
     DevBuf<double> w, lam;
     DevBuf<uint8_t> sel;
     DevBuf<T> vb, vx, vr;
+    DevBuf<int32_t> gs_rows;  // multicolour Gauss-Seidel classes (rows by colour)
+    std::vector<int> gs_ptr;
     MatView<T> B() const { return MatView<T>{n, nnz, rp.get(), ci.get(), bv.get()}; }
     EllView<T> P(int c) const { return EllView<T>{n, c, pcol.get(), pval.get(), pcnt.get()}; }
     void diagonals(cudaStream_t s) {
@@ -159,7 +171,22 @@ struct PhaseTrace {
     }
 };
 
+// The solve's private stream and its two fence events.  Held by the base class so that it
+// is destroyed after every device buffer of the derived solver: buffers (re)allocated
+// during a solve (the MLE restart's rebuilt levels) are released on this stream.
+struct PrivateStream {
+    cudaStream_t ps = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    ~PrivateStream() {
+        if (ps) cudaStreamSynchronize(ps);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (ps) cudaStreamDestroy(ps);
+    }
+};
+
 struct SolverBase {
+    PrivateStream priv;  // first member: destroyed last
     bamg_opts o{};
     cudaStream_t s = nullptr;
     double setup_ms = 0.0;
@@ -167,6 +194,9 @@ struct SolverBase {
     virtual int nlevels() const = 0;
     virtual void level_size(int l, int64_t* n, int64_t* nnz) const = 0;
     virtual void solve(double* x, int flags, double tol, bamg_stats* st) = 0;
+    virtual void parnoldi(double* x, int flags, double tol, bamg_stats* st) = 0;
+    virtual void mle_setup(const bamg_csr* A, int r, int levels, double tol, int max_cycles, bool l2, double* x,
+                           bool x_host, bamg_stats* st) = 0;
     virtual void vcycle_apply(const double* v, double* z) = 0;
     virtual void smooth_apply(int level, int sweeps, const void* b, void* x, void* work) = 0;
     virtual int precision() const = 0;
@@ -197,9 +227,10 @@ struct Solver : SolverBase {
     DevBuf<T> Z, vin, zout;
     DevBuf<int> dj;
     double* h_pin = nullptr;
-    // one Arnoldi step captured as a CUDA graph, replayed on a private stream
-    cudaStream_t ps = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // one Arnoldi step captured as a CUDA graph, replayed on the private stream
+    cudaStream_t& ps = priv.ps;
+    cudaEvent_t& ev_in = priv.ev_in;
+    cudaEvent_t& ev_out = priv.ev_out;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_kernels = 0;  // kernels of one step
@@ -211,10 +242,8 @@ struct Solver : SolverBase {
         if (ps) cudaStreamSynchronize(ps);
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
-        if (ev_in) cudaEventDestroy(ev_in);
-        if (ev_out) cudaEventDestroy(ev_out);
-        if (ps) cudaStreamDestroy(ps);
         if (h_pin) cudaFreeHost(h_pin);
+        // the private stream itself is destroyed by SolverBase::priv after the buffers
     }
     int nlevels() const override { return (int)lv.size(); }
     void level_size(int l, int64_t* n, int64_t* nnz) const override {
@@ -247,6 +276,11 @@ struct Solver : SolverBase {
             v[l].b = L.vb.get();
             v[l].x = L.vx.get();
             v[l].r = L.vr.get();
+            if (o.smoother == BAMG_SMOOTH_MCGS && l + 1 < lv.size() && !L.gs_ptr.empty()) {
+                v[l].gs_rows = L.gs_rows.get();
+                v[l].gs_ptr = L.gs_ptr.data();
+                v[l].gs_ncol = (int)L.gs_ptr.size() - 1;
+            }
         }
         v[0].b = const_cast<T*>(b0);
         v[0].x = x0v;
@@ -329,20 +363,171 @@ struct Solver : SolverBase {
     }
 
     // --------------------------------------------------------------- setup
-    void setup(const bamg_csr* A, int r_, int levels) {
-        auto t0 = std::chrono::steady_clock::now();
-        AllocStream as_(s);
-        if (!arena || arena->s != s) arena = std::make_unique<StackArena>(s);
-        ArenaScope ar_(*arena);
-        PhaseTrace tr(s);
-        trace = tr.on ? &tr : nullptr;
-        struct Untrace {
-            PhaseTrace*& p;
-            ~Untrace() { p = nullptr; }
-        } untrace_{trace};
+    // Algorithm 3 as a recursion over the levels (the same steps in the same order as the
+    // CPU restatement): first visit (relax U_l, split), interpolation step (P_l, Q_l,
+    // B_{l+1}, T_{l+1}; U_{l+1} = R U_l on the first descent), recursive call, upward step
+    // (V_l = P_l V_{l+1}, shifted sweeps, lambda update, selection).
+    int levels_max = 0;
+    int L_idx = -1;  // index of the coarsest level once the first descent reached it
+
+    bool first_visit(int l) {
+        LevelT<T>& c = *lv[l];
+        if (l == levels_max || c.n <= o.coarse_max) {
+            L_idx = l;
+            return true;
+        }
+        {
+            TmpBuf<T> work((size_t)c.n * ld, s);
+            relax<T>(c.B(), nullptr, c.dB.get(), c.dinv.get(), nullptr, nullptr, r, ld, 0, (T)o.omega, o.nu_tv,
+                     c.X.get(), work.get(), s);
+        }
+        if (trace) trace->mark("relax", l);
+        split(l);
+        if (trace) trace->mark("split", l);
+        return false;
+    }
+
+    void interp_step(int l, bool with_v) {
+        const bool create = (int)lv.size() == l + 1;
+        if (create) {
+            auto nl = std::make_unique<LevelT<T>>();
+            nl->nx = (lv[l]->nx + 1) / 2;
+            nl->ny = (lv[l]->ny + 1) / 2;
+            lv.push_back(std::move(nl));
+        }
+        if (with_v) {
+            TmpBuf<uint8_t> active(32, s);
+            BAMG_LAUNCH(k_active_mask, 1, 32, 0, s, r, ldU, nvec, ld, lv[l]->sel.get(), active.get());
+            build_level_operators(l, active.get(), ld);
+        } else {
+            build_level_operators(l, nullptr, r);
+        }
+        if (create) {
+            LevelT<T>& cc = *lv[l];
+            LevelT<T>& nn = *lv[l + 1];
+            nn.X.alloc((size_t)nn.n * ld);
+            BAMG_CK(cudaMemsetAsync(nn.X.get(), 0, sizeof(T) * nn.n * ld, s));
+            inject_cols<T>(nn.n, cc.c2f.get(), cc.X.get(), nn.X.get(), ld, 0, r, s);
+        }
+        if (trace) trace->mark(with_v ? "rebuild" : "operators", l);
+    }
+
+    void coarsest_eigs(int l) {
+        LevelT<T>& Lc = *lv[l];
+        nL = Lc.n;
+        BAMG_REQUIRE(nL <= 64, BAMG_EINVAL, "coarsest level has more than 64 states: raise `levels` or lower coarse_max");
+        TmpBuf<double> Bd((size_t)nL * nL, s), Td((size_t)nL * nL, s), Vd((size_t)nL * (o.k_ev + 1), s);
+        TmpBuf<int32_t> kinds(o.k_ev + 1, s);
+        csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.bv.get(), Bd.get(), s);
+        csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.tv.get(), Td.get(), s);
+        Lc.lam.ensure(ldV);
+        BAMG_CK(cudaMemsetAsync(Lc.lam.get(), 0, sizeof(double) * ldV, s));
+        const int nv = coarse_eig(nL, Bd.get(), Td.get(), o.k_ev, Lc.lam.get(), Vd.get(), kinds.get(),
+                                  std::is_same<T, float>::value, s);
+        BAMG_REQUIRE(nv > 0, BAMG_ENUMERIC, "coarsest eigensolve did not converge");
+        nvec = nv;
+        launch_vecs_to_strided<double, T>(nL, nvec, Vd.get(), Lc.X.get(), ld, ldU, s);
+        ++coarse_solves;
+        if (trace) trace->mark("coarse_eig");
+    }
+
+    void up_step(int l) {
+        LevelT<T>& c = *lv[l];
+        LevelT<T>& ch = *lv[l + 1];
+        prolong_cols<T>(c.P(o.caliber), ch.X.get(), c.X.get(), ld, ldU, nvec, s);
+        c.lam.ensure(ldV);
+        BAMG_CK(cudaMemcpyAsync(c.lam.get(), ch.lam.get(), sizeof(double) * ldV, cudaMemcpyDeviceToDevice, s));
+        relax_v(l);
+        c.sel.ensure(ldV);
+        rayleigh_update<T>(c.B(), c.tv.get(), c.X.get(), nvec, ld, ldU, o.ev_change_tol, c.lam.get(), c.sel.get(), s);
+        if (trace) trace->mark("up", l);
+    }
+
+    // nu_ev sweeps on (B_l - lambda_i T_l) x^(i) = 0 over the eigenvector columns
+    void relax_v(int l) {
+        LevelT<T>& c = *lv[l];
+        TmpBuf<T> work((size_t)c.n * ld, s);
+        relax<T>(c.B(), c.tv.get(), c.dB.get(), c.dinv.get(), c.dT.get(), c.lam.get(), nvec, ld, ldU, (T)o.omega,
+                 o.nu_ev, c.X.get(), work.get(), s);
+    }
+
+    // bootamg_mle (Algorithm 3) with loop count o.mu.  V_l = {} only on the first visit of
+    // level l; later visits relax V_l on the way down and fit P_l to U_l and V_l (the
+    // reading of the CPU restatement); U_l is relaxed on the first visit only.
+    void mle(int l, bool first) {
+        if (first) {
+            if (first_visit(l)) {
+                coarsest_eigs(l);
+                return;
+            }
+        } else if (l == L_idx) {
+            coarsest_eigs(l);
+            return;
+        } else {
+            relax_v(l);
+        }
+        for (int it = 0; it < o.mu; ++it) {
+            const bool fresh = first && it == 0;
+            interp_step(l, !fresh);
+            mle(l + 1, fresh);
+            up_step(l);
+        }
+    }
+
+    // Section 1: all P_l, B_l, T_l recalculated top-down from U_l and the selected V_l
+    void rebuild() {
+        for (int l = 0; l < L_idx; ++l) interp_step(l, true);
+    }
+
+    // minimal-norm inverse of the coarsest B_L (Section 4.2)
+    void coarse_pinv_now() {
+        LevelT<T>& Lc = *lv[L_idx];
+        TmpBuf<double> Bd((size_t)nL * nL, s);
+        csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.bv.get(), Bd.get(), s);
+        pinv64.ensure((size_t)nL * nL);
+        BAMG_REQUIRE(coarse_pinv(nL, Bd.get(), pinv64.get(), std::is_same<T, float>::value, s) == 0, BAMG_ENUMERIC,
+                     "singular coarsest factor");
+        pinvT.ensure((size_t)nL * nL);
+        if constexpr (std::is_same<T, double>::value)
+            BAMG_CK(cudaMemcpyAsync(pinvT.get(), pinv64.get(), sizeof(double) * nL * nL, cudaMemcpyDeviceToDevice, s));
+        else
+            launch_convert<double, float>((int64_t)nL * nL, pinv64.get(), pinvT.get(), s);
+        if (trace) trace->mark("pinv");
+    }
+
+    // colour classes of every level but the coarsest for the multicolour Gauss-Seidel
+    // smoother, on the final B_l
+    void build_colours() {
+        if (o.smoother != BAMG_SMOOTH_MCGS) return;
+        for (size_t l = 0; l + 1 < lv.size(); ++l) {
+            LevelT<T>& c = *lv[l];
+            colour_classes(c.n, c.nnz, c.rp.get(), c.ci.get(), (int)l, o.seed, c.gs_ptr, c.gs_rows, s);
+        }
+        if (trace) trace->mark("colours");
+    }
+
+    // the state-vector approximation V_0[:, 0] in FP64 into y, scaled to 1^T y = 1; the
+    // l1 ratio ||B y||_1 / ||y||_1 and the 2-norm ratio into h_ratio[0..1] when given
+    void state_vector(double* y, double* h_ratio) {
+        const int n = lv[0]->n;
+        launch_strided_to_vec<T, double>(n, lv[0]->X.get(), ld, ldU, y, s);
+        TmpBuf<double> sums(8, s), part((size_t)blocks_for(n, 256) * RESNORM_SUMS, s);
+        residual_norms(B64(), y, sums.get(), part.get(), s);
+        scale_vec(n, y, sums.get(), 3, true, y, s);
+        if (h_ratio) {  // the ratios are scale invariant: read them off the same sums
+            double h[RESNORM_SUMS];
+            BAMG_CK(cudaMemcpyAsync(h, sums.get(), sizeof h, cudaMemcpyDeviceToHost, s));
+            BAMG_CK(cudaStreamSynchronize(s));
+            h_ratio[0] = h[2] > 0.0 ? h[0] / h[2] : INFINITY;
+            h_ratio[1] = h[4] > 0.0 ? std::sqrt(h[1] / h[4]) : INFINITY;
+        }
+    }
+
+    int coarse_solves = 0;
+
+    void read_input(const bamg_csr* A, int r_) {
         const int n = A->n;
         r = r_;
-        // inputs on the device
         const int32_t *rpA = A->row_ptr, *ciA = A->col;
         const double* vA = A->val;
         DevBuf<int32_t> hrp, hci;
@@ -396,108 +581,95 @@ struct Solver : SolverBase {
         launch_tv_init<T>(n, r, ld, 0, o.seed, o.tv_lo, o.tv_hi, L0->X.get(), s);
         lv.clear();
         lv.push_back(std::move(L0));
-        const T omega = (T)o.omega;
-        tr.mark("input");
-        // ---- first pass, down (Algorithm 3: relax U_l, P_l, Q_l, B_{l+1}, T_{l+1}, U_{l+1} = R U_l)
-        for (int l = 0; l < levels; ++l) {
-            LevelT<T>& c = *lv.back();
-            if (c.n <= o.coarse_max) break;
-            {
-                TmpBuf<T> work((size_t)c.n * ld, s);
-                relax<T>(c.B(), nullptr, c.dB.get(), c.dinv.get(), nullptr, nullptr, r, ld, 0, omega, o.nu_tv,
-                         c.X.get(), work.get(), s);
-            }
-            tr.mark("relax", l);
-            split(l);
-            tr.mark("split", l);
-            auto nl = std::make_unique<LevelT<T>>();
-            nl->nx = (c.nx + 1) / 2;
-            nl->ny = (c.ny + 1) / 2;
-            lv.push_back(std::move(nl));
-            build_level_operators(l, nullptr, r);
-            LevelT<T>& cc = *lv[l];
-            LevelT<T>& nn = *lv[l + 1];
-            nn.X.alloc((size_t)nn.n * ld);
-            BAMG_CK(cudaMemsetAsync(nn.X.get(), 0, sizeof(T) * nn.n * ld, s));
-            inject_cols<T>(nn.n, cc.c2f.get(), cc.X.get(), nn.X.get(), ld, 0, r, s);
-            tr.mark("operators", l);
-        }
-        const int L = (int)lv.size() - 1;
-        LevelT<T>& Lc = *lv[L];
-        nL = Lc.n;
-        BAMG_REQUIRE(nL <= 64, BAMG_EINVAL,
-                     "coarsest level has more than 64 states: raise `levels` or lower coarse_max");
-        // ---- coarsest eigenpairs
-        {
-            TmpBuf<double> Bd((size_t)nL * nL, s), Td((size_t)nL * nL, s), Vd((size_t)nL * (o.k_ev + 1), s);
-            TmpBuf<int32_t> kinds(o.k_ev + 1, s);
-            csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.bv.get(), Bd.get(), s);
-            csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.tv.get(), Td.get(), s);
-            Lc.lam.alloc(ldV);
-            BAMG_CK(cudaMemsetAsync(Lc.lam.get(), 0, sizeof(double) * ldV, s));
-            const int nv = coarse_eig(nL, Bd.get(), Td.get(), o.k_ev, Lc.lam.get(), Vd.get(), kinds.get(),
-                                      std::is_same<T, float>::value, s);
-            BAMG_REQUIRE(nv > 0, BAMG_ENUMERIC, "coarsest eigensolve did not converge");
-            nvec = nv;
-            launch_vecs_to_strided<double, T>(nL, nvec, Vd.get(), Lc.X.get(), ld, ldU, s);
-        }
-        tr.mark("coarse_eig");
-        // ---- up (Algorithm 3: V_l = P_l V_{l+1}, relax (B_l - lambda_i T_l) x = 0, Rayleigh update)
-        for (int l = L - 1; l >= 0; --l) {
-            LevelT<T>& c = *lv[l];
-            LevelT<T>& ch = *lv[l + 1];
-            prolong_cols<T>(c.P(o.caliber), ch.X.get(), c.X.get(), ld, ldU, nvec, s);
-            c.lam.alloc(ldV);
-            BAMG_CK(cudaMemcpyAsync(c.lam.get(), ch.lam.get(), sizeof(double) * ldV, cudaMemcpyDeviceToDevice, s));
-            {
-                TmpBuf<T> work((size_t)c.n * ld, s);
-                relax<T>(c.B(), c.tv.get(), c.dB.get(), c.dinv.get(), c.dT.get(), c.lam.get(), nvec, ld, ldU, omega,
-                         o.nu_ev, c.X.get(), work.get(), s);
-            }
-            c.sel.alloc(ldV);
-            rayleigh_update<T>(c.B(), c.tv.get(), c.X.get(), nvec, ld, ldU, o.ev_change_tol, c.lam.get(), c.sel.get(),
-                               s);
-            tr.mark("up", l);
-        }
-        // ---- rebuild all P_l, B_{l+1}, T_{l+1} from U_l and the selected V_l, top-down
-        {
-            TmpBuf<uint8_t> active(32, s);
-            for (int l = 0; l < L; ++l) {
-                BAMG_LAUNCH(k_active_mask, 1, 32, 0, s, r, ldU, nvec, ld, lv[l]->sel.get(), active.get());
-                build_level_operators(l, active.get(), ld);
-                tr.mark("rebuild", l);
-            }
-        }
-        // ---- coarsest minimal-norm inverse of the rebuilt B_L
-        {
-            TmpBuf<double> Bd((size_t)nL * nL, s);
-            csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.bv.get(), Bd.get(), s);
-            pinv64.alloc((size_t)nL * nL);
-            BAMG_REQUIRE(coarse_pinv(nL, Bd.get(), pinv64.get(), std::is_same<T, float>::value, s) == 0, BAMG_ENUMERIC,
-                         "singular coarsest factor");
-            pinvT.alloc((size_t)nL * nL);
-            if constexpr (std::is_same<T, double>::value)
-                BAMG_CK(cudaMemcpyAsync(pinvT.get(), pinv64.get(), sizeof(double) * nL * nL, cudaMemcpyDeviceToDevice, s));
-            else
-                launch_convert<double, float>((int64_t)nL * nL, pinv64.get(), pinvT.get(), s);
-        }
-        tr.mark("pinv");
-        // ---- initial guess: the state-vector approximation, 1^T x = 1
-        x_init.alloc(n);
-        launch_strided_to_vec<T, double>(n, lv[0]->X.get(), ld, ldU, x_init.get(), s);
-        {
-            TmpBuf<double> sums(4, s), part((size_t)blocks_for(n, 256) * 4, s);
-            residual_norms(B64(), x_init.get(), sums.get(), part.get(), s);
-            scale_vec(n, x_init.get(), sums.get(), 3, true, x_init.get(), s);
-        }
-        alloc_vcycle_work();
+        nvec = 0;
+        coarse_solves = 0;
+        L_idx = -1;
+    }
+
+    void check_search_overflow() {
         int h_err = 0;
         BAMG_CK(cudaMemcpyAsync(&h_err, ls_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
         BAMG_CK(cudaStreamSynchronize(s));
         BAMG_REQUIRE(h_err == 0, BAMG_EOVERFLOW, "neighbourhood search: a fine point needs more than 2048 recorded states");
+    }
+
+    // Bootstrap setup: o.setup_cycles MLE cycles, then the rebuild, B_L^+ and the initial
+    // guess.  With `mle_tol` > 0 (the stand-alone MLE of Section 4.1) the cycles go on
+    // until the state vector approximation meets the tolerance (2-norm ratio when
+    // mle_l2, else the l1 ratio) or `max_cycles` cycles ran; *h_cycles / h_ratio report.
+    void setup(const bamg_csr* A, int r_, int levels, double mle_tol = 0.0, int max_cycles = 0, bool mle_l2 = false,
+               int* h_cycles = nullptr, double* h_ratio = nullptr) {
+        auto t0 = std::chrono::steady_clock::now();
+        AllocStream as_(s);
+        if (!arena || arena->s != s) arena = std::make_unique<StackArena>(s);
+        ArenaScope ar_(*arena);
+        PhaseTrace tr(s);
+        trace = tr.on ? &tr : nullptr;
+        struct Untrace {
+            PhaseTrace*& p;
+            ~Untrace() { p = nullptr; }
+        } untrace_{trace};
+        levels_max = levels;
+        read_input(A, r_);
+        const int n = A->n;
+        tr.mark("input");
+        x_init.alloc(n);
+        if (mle_tol > 0.0) {
+            int cycles = 0;
+            double rat[2] = {INFINITY, INFINITY};
+            while (true) {
+                mle(0, cycles == 0);
+                ++cycles;
+                state_vector(x_init.get(), rat);
+                if (rat[mle_l2 ? 1 : 0] <= mle_tol || cycles >= max_cycles) break;
+            }
+            if (h_cycles) *h_cycles = cycles;
+            if (h_ratio) h_ratio[0] = rat[0], h_ratio[1] = rat[1];
+        } else {
+            mle(0, true);
+            for (int c = 1; c < o.setup_cycles; ++c) mle(0, false);
+        }
+        BAMG_REQUIRE(L_idx >= 0, BAMG_ECUDA, "setup did not reach a coarsest level");
+        rebuild();
+        coarse_pinv_now();
+        build_colours();
+        if (mle_tol <= 0.0) state_vector(x_init.get(), nullptr);
+        alloc_vcycle_work();
+        check_search_overflow();
         tr.mark("guess");
         setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
+
+    // MLE restart (the reading of Section 5.1's "restarting the MLE iterations"): the
+    // iterate x becomes the state-vector test vector of every level (x / ||x||_2 on level 0,
+    // injected on the coarser ones), all P_l, B_l, T_l are rebuilt and B_L^+ recomputed.
+    // Runs on the solve's stream after a host synchronisation (the old operators are no
+    // longer in use); the captured Arnoldi step is dropped, its pointers being stale.
+    void mle_restart(const double* x) {
+        BAMG_CK(cudaStreamSynchronize(s));
+        AllocStream as_(s);
+        const int n = lv[0]->n;
+        {
+            TmpBuf<double> nrm(2, s), part((size_t)dots_partial_blocks(n) + 64, s);
+            dots(n, x, n, 1, x, nrm.get(), part.get(), s);
+            BAMG_LAUNCH(k_state_col<T>, blocks_for(n, 256), 256, 0, s, n, x, (const double*)nrm.get(), lv[0]->X.get(), ld,
+                        ldU);
+        }
+        for (int l = 0; l < L_idx; ++l) {
+            BAMG_CK(cudaMemsetAsync(lv[l]->sel.get(), 1, 1, s));
+            interp_step(l, true);
+            inject_cols<T>(lv[l + 1]->n, lv[l]->c2f.get(), lv[l]->X.get(), lv[l + 1]->X.get(), ld, ldU, 1, s);
+        }
+        coarse_pinv_now();
+        build_colours();
+        check_search_overflow();
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        ++mle_restarts;
+    }
+    int mle_restarts = 0;
 
     // --------------------------------------------------------------- import
     void import(int nlev, const bamg_level_in* in, const double* h_pinv, const double* h_x_init) {
@@ -555,6 +727,7 @@ struct Solver : SolverBase {
         launch_convert<double, T>((int64_t)nL * nL, pinv64.get(), pinvT.get(), s);
         x_init.alloc(lv[0]->n);
         BAMG_CK(cudaMemcpyAsync(x_init.get(), h_x_init, sizeof(double) * lv[0]->n, cudaMemcpyHostToDevice, s));
+        build_colours();
         alloc_vcycle_work();
         BAMG_CK(cudaStreamSynchronize(s));
     }
@@ -705,36 +878,24 @@ struct Solver : SolverBase {
         return true;
     }
 
-    void solve(double* x_user, int flags, double tol, bamg_stats* st) override {
-        AllocStream as_(s);
-        const int n = lv[0]->n;
-        m = std::min(std::max(o.gmres_m, 1), GMRES_MMAX);
-        GmresLayout GL(m);
-        V.ensure((size_t)n * (m + 1));
-        Z.ensure((size_t)n * m);
-        state.ensure(GL.total);
-        const int pb = std::max({dots_partial_blocks(n) * (m + 1), (int)blocks_for(n, 256) * 4,
-                                 2 * arn_tiles(n) * (m + 1)});
-        partial.ensure(pb);
-        x0.ensure(n);
-        xw.ensure(n);
-        rn.ensure(8);
-        vin.ensure(n);
-        zout.ensure(n);
-        dj.ensure(1);
+    void ensure_private_stream() {
         if (!h_pin) BAMG_CK(cudaMallocHost(&h_pin, 16 * sizeof(double)));
         if (!ps) {
             BAMG_CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
             BAMG_CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
             BAMG_CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
         }
-        // all work of the solve runs on the private stream, fenced against the caller's
+    }
+    // runs f with s = the private stream, fenced against the caller's stream on both sides
+    template <typename F>
+    void on_private_stream(F&& f) {
+        ensure_private_stream();
         cudaStream_t su = s;
         BAMG_CK(cudaEventRecord(ev_in, su));
         BAMG_CK(cudaStreamWaitEvent(ps, ev_in, 0));
         s = ps;
         try {
-            solve_on_private_stream(x_user, flags, tol, st);
+            f();
         } catch (...) {
             cudaEventRecord(ev_out, ps);
             cudaStreamWaitEvent(su, ev_out, 0);
@@ -744,6 +905,156 @@ struct Solver : SolverBase {
         BAMG_CK(cudaEventRecord(ev_out, ps));
         BAMG_CK(cudaStreamWaitEvent(su, ev_out, 0));
         s = su;
+    }
+
+    void solve(double* x_user, int flags, double tol, bamg_stats* st) override {
+        AllocStream as_(s);
+        const int n = lv[0]->n;
+        m = std::min(std::max(o.gmres_m, 1), GMRES_MMAX);
+        GmresLayout GL(m);
+        V.ensure((size_t)n * (m + 1));
+        Z.ensure((size_t)n * m);
+        state.ensure(GL.total);
+        const int pb = std::max({dots_partial_blocks(n) * (m + 1), (int)blocks_for(n, 256) * RESNORM_SUMS,
+                                 2 * arn_tiles(n) * (m + 1)});
+        partial.ensure(pb);
+        x0.ensure(n);
+        xw.ensure(n);
+        rn.ensure(8);
+        vin.ensure(n);
+        zout.ensure(n);
+        dj.ensure(1);
+        // all work of the solve runs on the private stream, fenced against the caller's
+        on_private_stream([&] { solve_on_private_stream(x_user, flags, tol, st); });
+    }
+
+    // --------------------------------------------------------------- pArnoldi (Section 4.3)
+    DevBuf<double> Hh, eta, zero;
+    void parnoldi(double* x_user, int flags, double tol, bamg_stats* st) override {
+        AllocStream as_(s);
+        const int n = lv[0]->n;
+        const int mp = std::min(std::max(o.gmres_m, 1), PARN_MMAX);
+        GmresLayout GL(mp);
+        V.ensure((size_t)n * (mp + 1));
+        state.ensure(GL.total);
+        partial.ensure(std::max({dots_partial_blocks(n) * (mp + 1), (int)blocks_for(n, 256) * RESNORM_SUMS,
+                                 2 * arn_tiles(n) * (mp + 1)}));
+        x0.ensure(n);
+        xw.ensure(n);
+        rn.ensure(8);
+        vin.ensure(n);
+        zout.ensure(n);
+        dj.ensure(1);
+        Hh.ensure((size_t)(mp + 1) * mp);
+        eta.ensure(mp);
+        if (zero.n < (size_t)n) {
+            zero.ensure(n);
+            BAMG_CK(cudaMemsetAsync(zero.get(), 0, sizeof(double) * n, s));
+        }
+        on_private_stream([&] { parnoldi_on_private_stream(mp, x_user, flags, tol, st); });
+    }
+
+    // Arnoldi on C B from y = the setup's state-vector approximation (or the guess); after
+    // every step the Ritz vector x = V_k eta of the eigenvalue of H_k closest to 0 and its
+    // true residual; after mp steps a restart from the Ritz vector.
+    void parnoldi_on_private_stream(int mp, double* x_user, int flags, double tol, bamg_stats* st) {
+        auto t0 = std::chrono::steady_clock::now();
+        const int n = lv[0]->n;
+        GmresLayout GL(mp);
+        const MatView<double> B = B64();
+        const bool l2 = (flags & BAMG_NORM_L2) != 0;
+        if (flags & BAMG_X_GUESS)
+            BAMG_CK(cudaMemcpyAsync(x0.get(), x_user, sizeof(double) * n,
+                                    (flags & BAMG_X_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+        else
+            BAMG_CK(cudaMemcpyAsync(x0.get(), x_init.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        std::vector<VLevel<T>> vl = vlevels(vin.get(), zout.get());
+        int it = 0, restarts = 0, checks = 0, status = BAMG_ENOCONV;
+        residual_norms(B, x0.get(), rn.get(), partial.get(), s);
+        read_n(rn.get(), RESNORM_SUMS);
+        double ratio1 = h_pin[0] / h_pin[2];
+        double ratio = l2 ? std::sqrt(h_pin[1] / h_pin[4]) : ratio1, xsum = h_pin[3];
+        double* xfinal = x0.get();
+        if (ratio <= tol) status = BAMG_OK;
+        while (status != BAMG_OK && it < o.max_it) {
+            double* V0 = V.get();
+            dots(n, x0.get(), n, 1, x0.get(), state.get() + GL.nrm2, partial.get(), s);
+            gmres_init(state.get(), mp, s);
+            scale_vec(n, x0.get(), state.get(), GL.hn, true, V0, s);
+            BAMG_CK(cudaMemsetAsync(dj.get(), 0, sizeof(int), s));
+            bool stop = false;
+            for (int j = 0; j < mp && it < o.max_it; ++j) {
+                parnoldi_step<T>(n, B, V.get(), vin.get(), zout.get(), dj.get(), state.get(), mp, Hh.get(), mp + 1,
+                                 partial.get(), vl, pinvT.get(), o.omega, o.nu_pre, o.nu_post, s);
+                ++it;
+                ritz_closest_to_zero(Hh.get(), mp + 1, j + 1, eta.get(), s);
+                form_x<double>(n, zero.get(), V.get(), n, j + 1, eta.get(), xw.get(), s);
+                residual_norms(B, xw.get(), rn.get(), partial.get(), s);
+                BAMG_CK(cudaMemcpyAsync(h_pin + 8, state.get() + GL.hn, sizeof(double), cudaMemcpyDeviceToHost, s));
+                read_n(rn.get(), RESNORM_SUMS);
+                ++checks;
+                xfinal = xw.get();
+                ratio1 = h_pin[0] / h_pin[2];
+                ratio = l2 ? std::sqrt(h_pin[1] / h_pin[4]) : ratio1;
+                xsum = h_pin[3];
+                if (!(ratio == ratio)) throw Error(BAMG_ENUMERIC, "NaN in the Arnoldi iteration");
+                if (ratio <= tol) {
+                    status = BAMG_OK;
+                    stop = true;
+                    break;
+                }
+                if (h_pin[8] == 0.0) {  // invariant subspace: the Ritz vector is final
+                    stop = true;
+                    break;
+                }
+            }
+            if (stop) break;
+            BAMG_CK(cudaMemcpyAsync(x0.get(), xw.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            xfinal = x0.get();
+            ++restarts;
+        }
+        TmpBuf<double> out(n, s);
+        h_pin[9] = xsum;
+        BAMG_CK(cudaMemcpyAsync(rn.get() + 5, h_pin + 9, sizeof(double), cudaMemcpyHostToDevice, s));
+        scale_vec(n, xfinal, rn.get(), 5, true, out.get(), s);
+        BAMG_CK(cudaMemcpyAsync(x_user, out.get(), sizeof(double) * n,
+                                (flags & BAMG_X_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+        BAMG_CK(cudaStreamSynchronize(s));
+        if (st) {
+            std::memset(st, 0, sizeof(*st));
+            st->status = status;
+            st->iterations = it;
+            st->restarts = restarts;
+            st->true_checks = checks;
+            st->host_waits = checks;
+            st->residual_l1 = ratio1;
+            st->setup_ms = setup_ms;
+            st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        if (status != BAMG_OK) throw Error(status, "pArnoldi did not reach the tolerance within max_it iterations");
+    }
+
+    // --------------------------------------------------------------- stand-alone MLE (Section 4.1)
+    void mle_setup(const bamg_csr* A, int r_, int levels, double tol, int max_cycles, bool l2, double* x, bool x_host,
+                   bamg_stats* st) override {
+        int cycles = 0;
+        double rat[2] = {INFINITY, INFINITY};
+        setup(A, r_, levels, tol, max_cycles, l2, &cycles, rat);
+        const int n = lv[0]->n;
+        if (x) {  // the last cycle's state vector approximation, 1^T x = 1 (x_init)
+            BAMG_CK(cudaMemcpyAsync(x, x_init.get(), sizeof(double) * n,
+                                    x_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+            BAMG_CK(cudaStreamSynchronize(s));
+        }
+        const double ratio = rat[l2 ? 1 : 0];
+        if (st) {
+            std::memset(st, 0, sizeof(*st));
+            st->status = ratio <= tol ? BAMG_OK : BAMG_ENOCONV;
+            st->iterations = cycles;
+            st->residual_l1 = rat[0];
+            st->setup_ms = setup_ms;
+        }
+        if (!(ratio <= tol)) throw Error(BAMG_ENOCONV, "MLE did not reach the tolerance within max_cycles cycles");
     }
 
     void solve_on_private_stream(double* x_user, int flags, double tol, bamg_stats* st) {
@@ -757,16 +1068,21 @@ struct Solver : SolverBase {
         } else {
             BAMG_CK(cudaMemcpyAsync(x0.get(), x_init.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         }
-        if (!gexec) capture_step(n);
         int it = 0, restarts = 0, checks = 0, waits = 0, status = BAMG_ENOCONV;
+        const int restarts0 = mle_restarts;
+        // stopping test: ||B x||_1 / ||x||_1 <= tol, or with BAMG_NORM_L2 the 2-norm ratio
+        // (the criterion of the paper's tables); ratio1 is always the l1 ratio
+        const bool l2 = (flags & BAMG_NORM_L2) != 0;
         residual_norms(B, x0.get(), rn.get(), partial.get(), s);
-        read_n(rn.get(), 4);
-        double ratio = h_pin[0] / h_pin[2];
-        double x1 = h_pin[2], xsum = h_pin[3], last_x1 = x1;
+        read_n(rn.get(), RESNORM_SUMS);
+        double ratio1 = h_pin[0] / h_pin[2];
+        double ratio = l2 ? std::sqrt(h_pin[1] / h_pin[4]) : ratio1;
+        double x1 = l2 ? std::sqrt(h_pin[4]) : h_pin[2], xsum = h_pin[3], last_x1 = x1;
         double kappa = 1.0;
         bool have_xw = false;
         if (ratio <= tol) status = BAMG_OK;
         while (status != BAMG_OK && it < o.max_it) {
+            if (!gexec) capture_step(n);
             double* V0 = V.get();
             spmv_f64(B, x0.get(), V0, -1.0, s);
             dots(n, V0, n, 1, V0, state.get() + GL.nrm2, partial.get(), s);
@@ -803,14 +1119,15 @@ struct Solver : SolverBase {
                     gmres_solve_y(state.get(), j, m, s);
                     form_x<T>(n, x0.get(), Z.get(), n, j + 1, state.get() + GL.y, xw.get(), s);
                     residual_norms(B, xw.get(), rn.get(), partial.get(), s);
-                    read_n(rn.get(), 4);
+                    read_n(rn.get(), RESNORM_SUMS);
                     ++checks;
                     have_xw = true;
                     const double r1 = h_pin[0], r2 = std::sqrt(h_pin[1]);
-                    ratio = r1 / h_pin[2];
-                    last_x1 = h_pin[2];
+                    ratio1 = r1 / h_pin[2];
+                    ratio = l2 ? r2 / std::sqrt(h_pin[4]) : ratio1;
+                    last_x1 = l2 ? std::sqrt(h_pin[4]) : h_pin[2];
                     xsum = h_pin[3];
-                    if (r2 > 0.0) kappa = std::max(1.0, r1 / r2);
+                    if (r2 > 0.0 && !l2) kappa = std::max(1.0, r1 / r2);
                     if (!(ratio == ratio)) throw Error(BAMG_ENUMERIC, "NaN in the Krylov iteration");
                     if (ratio <= tol) {
                         status = BAMG_OK;
@@ -825,6 +1142,8 @@ struct Solver : SolverBase {
                 x1 = last_x1;
             }
             ++restarts;
+            // an imported hierarchy carries no test vectors: plain restarts there
+            if (o.mle_restart && it < o.max_it && L_idx >= 0 && nvec > 0) mle_restart(x0.get());
         }
         double* xfinal = have_xw ? xw.get() : x0.get();
         // normalise 1^T x = 1
@@ -843,7 +1162,8 @@ struct Solver : SolverBase {
             st->restarts = restarts;
             st->true_checks = checks;
             st->host_waits = waits;
-            st->residual_l1 = ratio;
+            st->mle_restarts = mle_restarts - restarts0;
+            st->residual_l1 = ratio1;
             st->setup_ms = setup_ms;
             st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         }
@@ -972,6 +1292,10 @@ int bamg_default_opts(bamg_opts* o) {
     o->model = nullptr;
     o->learned_rho_max = 0.0;
     o->device_loop = 1;
+    o->mle_restart = 1;
+    o->setup_cycles = 1;
+    o->mu = 1;
+    o->smoother = BAMG_SMOOTH_JACOBI;
     return BAMG_OK;
 }
 
@@ -982,7 +1306,7 @@ static void check_opts(const bamg_opts& o) {
     BAMG_REQUIRE(o.k_ev >= 1 && o.k_ev <= 15, BAMG_EINVAL, "k_ev must be 1..15");
     BAMG_REQUIRE(o.coarse_max >= 1 && o.coarse_max <= 64, BAMG_EINVAL, "coarse_max must be 1..64");
     BAMG_REQUIRE(o.nu_pre >= 0 && o.nu_post >= 0 && o.nu_tv >= 0 && o.nu_ev >= 0, BAMG_EINVAL, "negative sweep count");
-    BAMG_REQUIRE(o.gmres_m >= 1 && o.gmres_m <= GMRES_MMAX, BAMG_EINVAL, "gmres_m must be 1..64");
+    BAMG_REQUIRE(o.gmres_m >= 1 && o.gmres_m <= GMRES_MMAX, BAMG_EINVAL, "gmres_m must be 1..256");
     BAMG_REQUIRE(o.max_it >= 1, BAMG_EINVAL, "max_it must be >= 1");
     BAMG_REQUIRE(o.precision == BAMG_PREC_FP64 || o.precision == BAMG_PREC_MIXED, BAMG_EINVAL, "bad precision");
     BAMG_REQUIRE(o.coarsen == BAMG_COARSEN_GRID || o.coarsen == BAMG_COARSEN_CR, BAMG_EINVAL, "bad coarsening");
@@ -990,6 +1314,9 @@ static void check_opts(const bamg_opts& o) {
     BAMG_REQUIRE(o.interp == BAMG_INTERP_LS || o.interp == BAMG_INTERP_LEARNED, BAMG_EINVAL, "bad interp");
     BAMG_REQUIRE(o.interp == BAMG_INTERP_LS || (o.model && o.model->impl), BAMG_EINVAL,
                  "BAMG_INTERP_LEARNED needs a model");
+    BAMG_REQUIRE(o.mu == 1 || o.mu == 2, BAMG_EINVAL, "mu must be 1 (V-cycle setup) or 2 (W-cycle setup)");
+    BAMG_REQUIRE(o.setup_cycles >= 1 && o.setup_cycles <= 64, BAMG_EINVAL, "setup_cycles must be 1..64");
+    BAMG_REQUIRE(o.smoother == BAMG_SMOOTH_JACOBI || o.smoother == BAMG_SMOOTH_MCGS, BAMG_EINVAL, "bad smoother");
 }
 
 static void check_setup_args(const bamg_csr* A, int r, int levels, const bamg_opts& o) {
@@ -1051,6 +1378,50 @@ int bamg_setup(const bamg_csr* A, int r, int levels, const bamg_opts* opts, bamg
         auto hh = std::make_unique<bamg_handle>();
         hh->impl = make_solver(A, r, levels, o);
         *h = hh.release();
+    });
+}
+
+int bamg_mle_solve(const bamg_csr* A, int r, int levels, const bamg_opts* opts, double tol, int max_cycles,
+                   int flags, double* x, bamg_stats* st, bamg_handle** h) {
+    return guarded([&] {
+        BAMG_REQUIRE(A, BAMG_EINVAL, "null argument");
+        if (h) *h = nullptr;
+        BAMG_REQUIRE(tol > 0.0 && max_cycles >= 1, BAMG_EINVAL, "tol must be > 0 and max_cycles >= 1");
+        BAMG_REQUIRE(!(flags & BAMG_X_GUESS), BAMG_EINVAL, "the MLE takes no initial guess");
+        bamg_opts o;
+        if (opts) o = *opts;
+        else bamg_default_opts(&o);
+        check_setup_args(A, r, levels, o);
+        std::unique_ptr<SolverBase> sv;
+        if (o.precision == BAMG_PREC_FP64) sv = std::make_unique<Solver<double>>();
+        else sv = std::make_unique<Solver<float>>();
+        sv->o = o;
+        sv->s = (cudaStream_t)o.stream;
+        sv->interp_used = o.interp;
+        int code = BAMG_OK;
+        std::string msg;
+        try {
+            sv->mle_setup(A, r, levels, tol, max_cycles, (flags & BAMG_NORM_L2) != 0, x, (flags & BAMG_X_HOST) != 0,
+                          st);
+        } catch (const Error& e) {
+            if (e.code != BAMG_ENOCONV) throw;
+            code = e.code;
+            msg = e.what();
+        }
+        if (h) {
+            auto hh = std::make_unique<bamg_handle>();
+            hh->impl = std::move(sv);
+            *h = hh.release();
+        }
+        if (code != BAMG_OK) throw Error(code, msg);
+    });
+}
+
+int bamg_parnoldi(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st) {
+    return guarded([&] {
+        BAMG_REQUIRE(h && h->impl && x, BAMG_EINVAL, "null argument");
+        BAMG_REQUIRE(tol >= 0.0, BAMG_EINVAL, "tol must be >= 0");
+        h->impl->parnoldi(x, flags, tol, st);
     });
 }
 
