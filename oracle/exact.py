@@ -40,7 +40,8 @@ def birth_death_ambiguity(birth: np.ndarray, death: np.ndarray, tol: float):
     dx = x* * (M_R [k <= m] - M_L [k > m]), the move of mass across the edge.  Then
     1^T dx = 0, ||dx||_1 = 2 M_L M_R, and by detailed balance (b_m x*_m = d_{m+1} x*_{m+1})
     B dx is nonzero only at m and m+1, with ||B dx||_1 = 2 b_m x*_m.  Hence
-      kappa_lb = max_m M_L M_R / (b_m x*_m)  <=  ||B^#||_1  (B^# B dx = dx), and
+      kappa_lb = max_m M_L M_R / (b_m x*_m) <= max ||B^# r||_1 / ||r||_1 over 1^T r = 0
+      (B^# B dx = dx), and
       eps(tol) = max_m 2 M_L M_R min(1, tol / (2 b_m x*_m)):
     x* + s dx (s <= 1) is non-negative, has 1^T x = 1, meets the tolerance and lies eps
     away from x* in relative l1.  Evaluated in log space.  Returns (log10 kappa_lb, eps)."""
@@ -61,6 +62,36 @@ def birth_death_ambiguity(birth: np.ndarray, death: np.ndarray, tol: float):
     log_kappa = float((mass - flux).max()) / np.log(10.0)
     eps = float((2.0 * np.exp(mass + np.minimum(0.0, np.log(tol) - np.log(2.0) - flux))).max())
     return log_kappa, eps
+
+
+def birth_death_condition(birth: np.ndarray, death: np.ndarray) -> float:
+    """An upper bound K on ||B^#||_1 for a birth-death chain (log10 K is returned), so that
+    any x with 1^T x = 1 lies within K ||B x||_1 of x* in l1.
+
+    With u = x / x* (componentwise) and the net flux J_i = sum_{k<=i} (B x)_k across the
+    edge i -> i+1 (B x = J_i - J_{i-1} row by row), detailed balance gives
+    u_{i+1} - u_i = -J_i w_i, w_i = 1 / (b_i x*_i), and |J_i| <= ||B x||_1 / 2.  The mean
+    absolute deviation of u (weights x*) about its mean is at most twice that about the
+    value at the weighted median m, so
+      ||x - x*||_1 <= ||B x||_1 sum_i w_i (M_L(i) for i < m, M_R(i) for i >= m),
+    M_L(i) = sum_{k<=i} x*_k, M_R = 1 - M_L: K bounds max ||B^# r||_1 / ||r||_1 over the
+    residuals with 1^T r = 0 (every B x has that).  Evaluated in log space."""
+    birth = np.asarray(birth, dtype=np.float64)
+    death = np.asarray(death, dtype=np.float64)
+    n = len(birth)
+    if n < 2:
+        return 0.0
+    logx = np.zeros(n)
+    logx[1:] = np.cumsum(np.log(birth[:-1]) - np.log(death[1:]))
+    logx -= logx.max()
+    logx -= np.log(np.exp(logx).sum())
+    ML = np.cumsum(np.exp(logx))[:-1]
+    m = int(np.searchsorted(ML, 0.5))
+    side = np.where(np.arange(n - 1) < m, ML, 1.0 - ML)
+    ok = side > 0
+    terms = np.log(side[ok]) - np.log(birth[:-1][ok]) - logx[:-1][ok]
+    top = terms.max()
+    return float((top + np.log(np.exp(terms - top).sum())) / np.log(10.0))
 
 
 def dense_nullspace(A_dense: np.ndarray) -> np.ndarray:

@@ -852,14 +852,18 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
                bool fp32_vectors, cudaStream_t s) {
     BAMG_REQUIRE(n >= 1 && n <= CN, BAMG_EINVAL, "coarse_eig: coarsest order must be 1..64");
     BAMG_REQUIRE(k_ev >= 1 && k_ev <= 16, BAMG_EINVAL, "coarse_eig: 1 <= k_ev <= 16");
-    static std::atomic<bool> attr{false};  // idempotent; several host threads may get here
+    // the attribute is per device (idempotent; several host threads may get here)
+    static std::atomic<bool> attr[256] = {};
+    int dev = 0;
+    BAMG_CK(cudaGetDevice(&dev));
+    BAMG_REQUIRE(dev >= 0 && dev < 256, BAMG_EINVAL, "device ordinal out of range");
     const size_t smem64 = 4 * CN * LDP * sizeof(double), smem32 = 4 * CN * LDP * sizeof(float);
-    if (!attr) {
+    if (!attr[dev]) {
         BAMG_CK(cudaFuncSetAttribute(k_coarse_eigvec<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem64));
         BAMG_CK(cudaFuncSetAttribute(k_coarse_eigvec<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem32));
-        attr = true;
+        attr[dev] = true;
     }
     TmpBuf<double> sel(3 * (k_ev + 1), s);
     TmpBuf<int> info(8, s);

@@ -1286,13 +1286,16 @@ void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int
         return (size_t)GAL_HSLOTS * (sizeof(unsigned long long) + 2 * tb + sizeof(int)) + GAL_STAGE * (2 * tb + sizeof(int));
     };
     const size_t smem_l = large_smem(sizeof(T));
-    static std::atomic<bool> attr{false};  // idempotent; several host threads may get here
-    if (!attr) {
+    static std::atomic<bool> attr[256] = {};  // per device; idempotent across host threads
+    int dev = 0;
+    BAMG_CK(cudaGetDevice(&dev));
+    BAMG_REQUIRE(dev >= 0 && dev < 256, BAMG_EINVAL, "device ordinal out of range");
+    if (!attr[dev]) {
         BAMG_CK(cudaFuncSetAttribute(k_gal_large<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)large_smem(sizeof(float))));
         BAMG_CK(cudaFuncSetAttribute(k_gal_large<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)large_smem(sizeof(double))));
-        attr = true;
+        attr[dev] = true;
     }
     BAMG_LAUNCH(k_gal_large<T>, GAL_BLOCKS_L, 32, smem_l, s, ga, (const int32_t*)list.get(), (const int*)nlist.get());
     out.rp.alloc(nc + 1);

@@ -121,3 +121,67 @@ def test_batch_results_agree_with_oracle_residual():
         assert abs(x.sum() - 1.0) < 1e-12
         if c.kind != "birth_death":  # well conditioned: the residual bound keeps x >= 0
             assert np.all(x >= -1e-12 * x.max())
+
+
+# The options the 512-chain workload runs with: birth-death chains in FP64 (their
+# stationary vectors span more decades than FP32's exponent range), restart length 256
+# and MLE restarts; grid walks in mixed precision.
+BD_BATCH = dict(ridge=1e-10, gmres_m=256, max_it=3000, precision="fp64")
+
+
+def _batch_opts(chains):
+    return [dict(grid=c.grid, **(BD_BATCH if c.kind == "birth_death" else dict(precision="mixed"))) for c in chains]
+
+
+def test_workload_draw_with_large_birth_death_chains():
+    """The first 64 chains of the 512-chain workload (12 birth-death chains with n >= 16k).
+    Grid walks: x proportional to degree within 1e-6 (mixed).  Birth-death chains: the
+    residual of every converged x, recomputed in FP64 on the host, meets 1e-10, and every x
+    lies within the rigorous bound K ||B x||_1 of the product form (K from detailed balance:
+    the bound holds at any size but says little where K is astronomically large, which is
+    what the next test is for); at most one in ten may stop at max_it."""
+    import paper_1004_1451_gb300 as bamg
+
+    chains = batched_mixture(0)[:64]
+    assert sum(c.kind == "birth_death" and c.n >= 16384 for c in chains) >= 10
+    try:
+        xs, stats = bamg.solve_batch(_dev(chains), 8, 30, 1e-10, opts=_batch_opts(chains), workers=8)
+    except bamg.BamgError as e:
+        xs, stats = e.xs, e.stats
+    nbd = conv = 0
+    for c, x, st in zip(chains, xs, stats):
+        x = x.cpu().numpy()
+        xe = exact.exact_stationary(c)
+        if c.kind != "birth_death":
+            assert st["status"] == 0
+            assert rel(x, xe) < 1e-6
+            continue
+        nbd += 1
+        if st["status"] != 0:  # stopped at max_it: x holds the last iterate
+            assert st["status"] == bamg._capi.BAMG_ENOCONV, (c.n, st)
+            continue
+        conv += 1
+        assert abs(x.sum() - 1.0) < 1e-12
+        r1 = float(np.abs(ob.system_matrix(c.to_scipy()) @ x).sum())
+        assert r1 / np.abs(x).sum() <= 1e-10 * 1.01
+        K = 10 ** exact.birth_death_condition(c.meta["birth"], c.meta["death"])
+        assert np.abs(x - xe).sum() <= K * r1 * (1 + 1e-6) + 1e-14
+    assert conv >= 0.9 * nbd, (conv, nbd)
+
+
+def test_best_conditioned_birth_death_chains_at_parity_tolerance():
+    """The four birth-death chains of the 512-chain workload with the smallest bound K
+    (about 1e6-1e6.4) solved to 1e-13 (the parity tolerance), where K ||B x||_1 <= 1e-6:
+    each x is within 1e-6 of the product form."""
+    import paper_1004_1451_gb300 as bamg
+
+    mix = batched_mixture(0)
+    chains = [mix[i] for i in (340, 504, 20, 108)]
+    xs, stats = bamg.solve_batch(_dev(chains), 8, 30, 1e-13, opts=_batch_opts(chains), workers=4)
+    for c, x, st in zip(chains, xs, stats):
+        x = x.cpu().numpy()
+        K = 10 ** exact.birth_death_condition(c.meta["birth"], c.meta["death"])
+        r1 = float(np.abs(ob.system_matrix(c.to_scipy()) @ x).sum())
+        err = np.abs(x - exact.exact_stationary(c)).sum()
+        assert K * r1 <= 1e-6 and err <= K * r1 * (1 + 1e-6) + 1e-14, (c.n, K, r1, err)
+        assert err < 1e-6

@@ -38,16 +38,24 @@ def test_tandem_three_routes():
     assert np.all(xd > 0)
 
 
+def _error_per_residual(G):
+    """max ||G r||_1 / ||r||_1 over residuals with 1^T r = 0 (every B x has that): the
+    extreme points of that set are (e_i - e_j) / 2."""
+    D = np.abs(G[:, :, None] - G[:, None, :]).sum(axis=0)
+    return D.max() / 2.0
+
+
 def test_birth_death_ambiguity_bounds_the_group_inverse():
-    """kappa_lb is a lower bound on ||B^#||_1 (dense group inverse (B + x* 1^T)^-1 - x* 1^T),
-    and the explicit mass move it is built on has exactly the stated residual and error."""
+    """kappa_lb is a lower bound on the error per residual of the dense group inverse
+    (B + x* 1^T)^-1 - x* 1^T, and the explicit mass move it is built on has exactly the
+    stated residual and error."""
     for n, seed in [(50, 1), (120, 5), (200, 7)]:
         ch = random_birth_death(n, seed)
         b, d = ch.meta["birth"], ch.meta["death"]
         x = exact.birth_death(b, d)
         B = np.eye(n) - ch.dense()
         G = np.linalg.inv(B + np.outer(x, np.ones(n))) - np.outer(x, np.ones(n))
-        kappa = np.abs(G).sum(axis=0).max()
+        kappa = _error_per_residual(G)
         lk, _ = exact.birth_death_ambiguity(b, d, 1e-10)
         assert 10 ** lk <= kappa * (1 + 1e-9)
         assert 10 ** lk >= 0.01 * kappa  # not a vacuous bound on these chains
@@ -68,3 +76,32 @@ def test_birth_death_ambiguity_of_a_uniform_chain_is_small():
     lk, eps = exact.birth_death_ambiguity(ch.meta["birth"], ch.meta["death"], 1e-10)
     assert np.isclose(10 ** lk, n / (4 * b), rtol=1e-9)
     assert np.isclose(eps, 2 * 0.25 * 1e-10 / (2 * b / n), rtol=1e-9)
+
+
+def test_birth_death_condition_bounds_the_group_inverse_from_above():
+    """K bounds the dense group inverse's error per residual from above on chains across
+    five orders of conditioning, and is not vacuous (within 10x)."""
+    for n, seed in [(50, 1), (120, 5), (200, 7), (150, 3)]:
+        ch = random_birth_death(n, seed)
+        b, d = ch.meta["birth"], ch.meta["death"]
+        x = exact.birth_death(b, d)
+        B = np.eye(n) - ch.dense()
+        G = np.linalg.inv(B + np.outer(x, np.ones(n))) - np.outer(x, np.ones(n))
+        kappa = _error_per_residual(G)
+        K = 10 ** exact.birth_death_condition(b, d)
+        assert kappa <= K * (1 + 1e-9), (kappa, K)
+        assert K <= 10 * kappa, (kappa, K)
+        lk, _ = exact.birth_death_ambiguity(b, d, 1e-10)
+        assert 10 ** lk <= K
+
+
+def test_birth_death_condition_uniform_closed_form():
+    """Equal rates b: x* = 1/n, w_i = n/b, M_L(i) = (i+1)/n; the median m = n/2 - 1 for even
+    n, K = (n/b) (sum_{i<m} (i+1)/n + sum_{i>=m} (n-1-i)/n)."""
+    n, b = 100, 0.3
+    ch = birth_death(np.full(n, b), np.full(n, b))
+    K = 10 ** exact.birth_death_condition(ch.meta["birth"], ch.meta["death"])
+    ML = np.arange(1, n) / n
+    m = int(np.searchsorted(ML, 0.5))
+    want = (n / b) * (ML[:m].sum() + (1 - ML[m:]).sum())
+    assert np.isclose(K, want, rtol=1e-9)
