@@ -120,6 +120,14 @@ typedef struct {
                                colour c is an independent set of the states the earlier colours left in
                                the symmetrised graph of B_l; colours ascending before the coarse
                                correction, descending after it; the setup's relaxations stay Jacobi) */
+    int32_t persistent;     /* 1: where the hierarchy qualifies (short-row grid levels, at most 24 levels,
+                               the coarse tail within shared memory, no Gauss-Seidel smoother) and the
+                               device supports it, the Arnoldi steps between true-residual checks run in
+                               one cooperative launch with grid-wide barriers instead of a graph per step
+                               (same iterates; a barrier wait that gives up returns BAMG_ETIMEOUT).
+                               0 (default): the graph form, which measured faster (the grid barriers
+                               between the step's phases cost more than graph kernel boundaries).
+                               bamg_solve_batch with more than one worker always uses the graph form. */
 } bamg_opts;
 
 enum { BAMG_SMOOTH_JACOBI = 0, BAMG_SMOOTH_MCGS = 1 };

@@ -174,17 +174,21 @@ def loss(y: np.ndarray, t: np.ndarray, mask: np.ndarray) -> float:
     return float(np.sum(mask * (y - t) ** 2) / y.shape[0])
 
 
-def backward(p: dict, cache: dict, y: np.ndarray, t: np.ndarray, mask: np.ndarray) -> dict:
+def backward(p: dict, cache: dict, y: np.ndarray, t: np.ndarray, mask: np.ndarray, bf16_grads: bool = False) -> dict:
     """Gradients of the loss by the chain rule through the three products (the rounded
-    forward inputs are treated as the layer inputs; rounding is not differentiated)."""
+    forward inputs are treated as the layer inputs; rounding is not differentiated).
+    With bf16_grads the output gradients entering a product (dy, d2, d1) are rounded to
+    bfloat16 as well, as the GPU's tensor-core backward takes them; bias gradients are
+    plain sums."""
     r = cache["r"]
+    rg = bf16 if bf16_grads else (lambda a: a)
     dy = 2.0 * mask * (y - t) / y.shape[0]
-    g = {"W3": dy.T @ cache["x2"], "b3": dy.sum(axis=0)}
-    d2 = (dy @ r(p["W3"])) * (cache["a2"] > 0)
-    g["W2"] = d2.T @ cache["x1"]
+    g = {"W3": rg(dy).T @ cache["x2"], "b3": dy.sum(axis=0)}
+    d2 = (rg(dy) @ r(p["W3"])) * (cache["a2"] > 0)
+    g["W2"] = rg(d2).T @ cache["x1"]
     g["b2"] = d2.sum(axis=0)
-    d1 = (d2 @ r(p["W2"])) * (cache["a1"] > 0)
-    g["W1"] = d1.T @ cache["x0"]
+    d1 = (rg(d2) @ r(p["W2"])) * (cache["a1"] > 0)
+    g["W1"] = rg(d1).T @ cache["x0"]
     g["b1"] = d1.sum(axis=0)
     return g
 

@@ -877,7 +877,21 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
                 "[bamg] coarse eigenvalues: n=%d QR double-shift steps=%d status=%d cycles lu+K=%d arnoldi=%d qr=%d "
                 "tail=%d\n",
                 n, h[3], h[2], h[4], h[5], h[6], h[7]);
-    if (h[2] != 0) return BAMG_ENUMERIC;
+    if (h[2] != 0) {
+        // The FP32 QR iteration on the shift-invert Arnoldi matrix did not converge (seen on
+        // birth-death chains whose coarsest eigenvalues cluster near 0 by many orders of
+        // magnitude): the coarsest level then supplies the state vector alone, by inverse
+        // iteration at shift 0 (the eigenvalue it belongs to is exactly 0).
+        const double one_sel[3] = {0.0, 0.0, 0.0};
+        const double zero = 0.0;
+        const int32_t real_kind = 0;
+        BAMG_CK(cudaMemcpyAsync(sel.get(), one_sel, sizeof(one_sel), cudaMemcpyHostToDevice, s));
+        BAMG_CK(cudaMemcpyAsync(d_lam, &zero, sizeof(double), cudaMemcpyHostToDevice, s));
+        BAMG_CK(cudaMemcpyAsync(d_kind, &real_kind, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        h[0] = 1;
+        h[1] = 1;
+        if (dbg) fprintf(stderr, "[bamg] coarse eigenvalues: QR did not converge; state vector only\n");
+    }
     if (h[1] > 0) {
         TmpBuf<int> cyc(2 * h[1], s);
         if (fp32_vectors)

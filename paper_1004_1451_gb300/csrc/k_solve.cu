@@ -282,10 +282,9 @@ __device__ __forceinline__ VLevel<T> tail_level(const TailArgs<T>& a, int l, uns
     return v;
 }
 
+// Issue the cp.async copies of the tail levels' matrices (and B_L^+) into shared memory.
 template <typename T>
-__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char tail_smem[];
-    // the matrices first: they were written during the setup, long before this launch
+__device__ __forceinline__ void tail_stage(const TailArgs<T>& a, unsigned char* tail_smem) {
     for (int l = 0; l + 1 < a.nl; ++l) {
         if (a.soff[l] < 0) continue;
         const VLevel<T>& g = a.lv[l];
@@ -305,7 +304,13 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
     }
     const int nL = a.lv[a.nl - 1].B.n;
     if (a.pinv_off >= 0) stage_async(tail_smem + a.pinv_off, a.pinv, sizeof(T) * (size_t)nL * nL);
-    pdl_begin();
+}
+
+// One pass of the V-cycle over the tail levels by one block (the staged copies complete at
+// its start): reads the first tail level's b from global memory and writes that level's
+// final x to the global buffer the grid kernels read it from.
+template <typename T>
+__device__ __forceinline__ void tail_cycle(const TailArgs<T>& a, unsigned char* tail_smem) {
     // the vectors of all tail levels: b, x and the work vector per level
     T* sbuf = reinterpret_cast<T*>(tail_smem);
     const int tid = threadIdx.x;
@@ -415,6 +420,15 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
     for (int i = tid; i < a.lv[0].B.n; i += blockDim.x) gx[i] = xf[i];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    // the matrices first: they were written during the setup, long before this launch
+    tail_stage(a, tail_smem);
+    pdl_begin();
+    tail_cycle(a, tail_smem);
+}
+
 // The buffer that holds a level's final x after the down and up passes (the sequence of
 // swaps in vcycle and k_vcycle_tail).
 template <typename T>
@@ -485,6 +499,51 @@ static void vcycle_gs(const std::vector<VLevel<T>>& lv, const T* pinv, int nu_pr
     }
 }
 
+// The tail levels l0..L of a hierarchy as kernel arguments: the vectors of every tail level
+// in shared memory (3 n each), then the matrices of the finer tail levels (their rows are
+// walked most) and B_L^+ staged while they fit in `budget` bytes; *smem = bytes used.
+template <typename T>
+static TailArgs<T> make_tail_args(const std::vector<VLevel<T>>& lv, int l0, const T* pinv, int nu_pre, int nu_post,
+                                  T omega, size_t budget, size_t* smem_out) {
+    const int L = (int)lv.size() - 1;
+    TailArgs<T> a;
+    a.nl = L - l0 + 1;
+    for (int q = 0; q < a.nl; ++q) a.lv[q] = lv[l0 + q];
+    a.pinv = pinv;
+    a.nu_pre = nu_pre;
+    a.nu_post = nu_post;
+    a.omega = omega;
+    size_t smem = 0;
+    for (int q = 0; q < a.nl; ++q) smem += 3 * sizeof(T) * (size_t)a.lv[q].B.n;
+    BAMG_REQUIRE(smem <= 96 * 1024, BAMG_EINVAL, "vcycle tail: levels too large for shared memory");
+    smem = al16(smem);
+    for (int q = 0; q < a.nl; ++q) {
+        a.soff[q] = -1;
+        if (q + 1 == a.nl) continue;
+        const size_t need = TailLayout<T>(a.lv[q], a.lv[q + 1].B.n).end;
+        if (smem + need <= budget) {
+            a.soff[q] = (int32_t)smem;
+            smem += need;
+        }
+    }
+    const size_t npinv = al16(sizeof(T) * (size_t)a.lv[a.nl - 1].B.n * a.lv[a.nl - 1].B.n);
+    if (smem + npinv <= budget) {
+        a.pinv_off = (int32_t)smem;
+        smem += npinv;
+    }
+    *smem_out = smem;
+    return a;
+}
+
+// First level handled by the single-block tail (L + 1: none).
+template <typename T>
+static int tail_start(const std::vector<VLevel<T>>& lv) {
+    const int L = (int)lv.size() - 1;
+    for (int l = 1; l <= L; ++l)
+        if (lv[l].B.n <= TAIL_MAX_N && lv[l].B.nnz <= TAIL_MAX_NNZ && L - l + 1 <= TAIL_MAX_LEVELS) return l;
+    return L + 1;
+}
+
 template <typename T>
 void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int nu_pre, int nu_post, cudaStream_t s,
             T* Z, const int* dj) {
@@ -495,12 +554,7 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
     const int L = (int)lv.size() - 1;
     const T omega = (T)omega_d;
     // the levels from l0 on (small enough for one block) run in k_vcycle_tail
-    int l0 = L + 1;
-    for (int l = 1; l <= L; ++l)
-        if (lv[l].B.n <= TAIL_MAX_N && lv[l].B.nnz <= TAIL_MAX_NNZ && L - l + 1 <= TAIL_MAX_LEVELS) {
-            l0 = l;
-            break;
-        }
+    const int l0 = tail_start(lv);
     std::vector<T*> xcur(L + 1), xtmp(L + 1);
     for (int l = 0; l < std::min(L, l0); ++l) {
         const VLevel<T>& v = lv[l];
@@ -540,33 +594,8 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         xtmp[l] = t;
     }
     if (l0 <= L) {
-        TailArgs<T> a;
-        a.nl = L - l0 + 1;
-        for (int q = 0; q < a.nl; ++q) a.lv[q] = lv[l0 + q];
-        a.pinv = pinv;
-        a.nu_pre = nu_pre;
-        a.nu_post = nu_post;
-        a.omega = omega;
         size_t smem = 0;
-        for (int q = 0; q < a.nl; ++q) smem += 3 * sizeof(T) * (size_t)a.lv[q].B.n;
-        BAMG_REQUIRE(smem <= 96 * 1024, BAMG_EINVAL, "vcycle tail: levels too large for shared memory");
-        // stage the matrices of the finer tail levels first (their rows are walked most),
-        // then B_L^+, while they fit
-        smem = al16(smem);
-        for (int q = 0; q < a.nl; ++q) {
-            a.soff[q] = -1;
-            if (q + 1 == a.nl) continue;
-            const size_t need = TailLayout<T>(a.lv[q], a.lv[q + 1].B.n).end;
-            if (smem + need <= (size_t)TAIL_SMEM) {
-                a.soff[q] = (int32_t)smem;
-                smem += need;
-            }
-        }
-        const size_t npinv = al16(sizeof(T) * (size_t)a.lv[a.nl - 1].B.n * a.lv[a.nl - 1].B.n);
-        if (smem + npinv <= (size_t)TAIL_SMEM) {
-            a.pinv_off = (int32_t)smem;
-            smem += npinv;
-        }
+        const TailArgs<T> a = make_tail_args(lv, l0, pinv, nu_pre, nu_post, omega, (size_t)TAIL_SMEM, &smem);
         // the attribute is per device: set once on each device (idempotent; several host
         // threads may get here)
         static std::atomic<bool> attr[256] = {};
@@ -1176,6 +1205,420 @@ void ritz_closest_to_zero(const double* H, int ldh, int k, double* eta, cudaStre
     BAMG_REQUIRE(k >= 1 && k <= PARN_MMAX, BAMG_EINVAL, "pArnoldi: Hessenberg order out of range");
     BAMG_LAUNCH(k_ritz_hess, 1, 128, 0, s, H, ldh, k, eta);
 }
+
+// ---------------------------------------------------------------- persistent Arnoldi cycle
+// FGMRES Arnoldi steps of one restart cycle in a single cooperative launch: the same phases
+// as the captured step (v_j to the V-cycle's precision, the V-cycle's grid levels, the
+// single-block tail on block 0, the FP64 SpMV with the first Gram-Schmidt dots, two update
+// passes, the Givens update with the scaling of v_{j+1}, the stop test of k_step_end), with
+// a grid-wide barrier between phases instead of a kernel boundary.  The per-row arithmetic,
+// the row tiles of the Arnoldi kernels and every reduction order are those of the separate
+// kernels, so the iterates are bit-identical.  Vectors written inside the kernel are read
+// through plain pointers (never the read-only path); the matrices are read-only.
+constexpr int PERSIST_THREADS = TAIL_THREADS;
+constexpr int PERSIST_MAX_LEVELS = 24;
+constexpr unsigned long long GRID_BAR_SPIN_LIMIT = 1ull << 24;  // then the barrier gives up
+
+template <typename T>
+struct CycleArgs {
+    VLevel<T> lv[PERSIST_MAX_LEVELS];
+    int L = 0, l0 = 0;
+    const T* pinv = nullptr;
+    TailArgs<T> tail;
+    T omega = T(0);
+    int nu_pre = 0, nu_post = 0;
+    MatView<double> B;
+    double* V = nullptr;
+    T* Z = nullptr;
+    T* vin = nullptr;
+    double* st = nullptr;
+    double* partial = nullptr;
+    int m = 0, tile = 0, nt = 0;
+    int* dj = nullptr;
+    const double* ctl = nullptr;  // kappa, tol ||x||_1, last j + 1
+    unsigned* bar = nullptr;      // arrivals, generation
+    int* err = nullptr;           // 1 when a barrier wait gave up
+};
+
+// Grid-wide barrier of a cooperative launch: arrival counter and generation in global
+// memory.  The block barrier orders every thread's writes before thread 0's fence and
+// arrival (release), and thread 0's fence after it sees the new generation before the
+// block's later reads (acquire).  The wait polls tightly, then backs off, and gives up
+// after GRID_BAR_SPIN_LIMIT polls (or when another block gave up): it sets *err and
+// returns false.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long polls = 0;
+            while (*gen == g0) {
+                if (*(volatile int*)err) break;
+                if (++polls > GRID_BAR_SPIN_LIMIT) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                if (polls > 512) __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)err == 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T prow_Bx(int i, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const T* __restrict__ bv, const T* x) {
+    return row_sum<T>(rp[i], rp[i + 1], ci, bv, [&](int j) { return x[j]; });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PERSIST_THREADS, 1) k_arnoldi_cycle(const __grid_constant__ CycleArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char psm[];
+    __shared__ double sh[GMRES_MMAX + 1];
+    __shared__ double gcol[GMRES_MMAX + 1], gcs[GMRES_MMAX], gsn[GMRES_MMAX], s_nrm2;
+    const bool has_tail = a.l0 <= a.L;
+    if (has_tail && blockIdx.x == 0) tail_stage(a.tail, psm);
+    pdl_begin();
+    const int n = a.lv[0].B.n;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const GmresLayout GL(a.m);
+    const int stride = a.m + 1;
+    const T omega = a.omega;
+    const int Lg = a.L < a.l0 ? a.L : a.l0;  // grid levels 0 .. Lg-1
+    int j = *a.dj;
+    for (;;) {
+        // ---- v_j in the V-cycle's precision
+        for (int i = gtid; i < n; i += gsz) a.vin[i] = (T)a.V[(int64_t)j * n + i];
+        if (!grid_sync(a.bar, a.err)) return;
+        // ---- V-cycle, down (the buffer sequence of vcycle())
+        T* xcur[PERSIST_MAX_LEVELS];
+        T* xtmp[PERSIST_MAX_LEVELS];
+        for (int l = 0; l < Lg; ++l) {
+            const VLevel<T>& v = a.lv[l];
+            const int nl = v.B.n;
+            T* b = l == 0 ? a.vin : v.b;
+            T* x = v.x;
+            T* t = v.r;
+            if (a.nu_pre >= 2) {
+                for (int i = gtid; i < nl; i += gsz) {
+                    const T x1 = (omega * v.dinv[i]) * b[i];
+                    x[i] = x1 + (omega * v.dinv[i]) *
+                                    (b[i] - row_sum<T>(v.B.rp[i], v.B.rp[i + 1], v.B.ci, v.B.v,
+                                                       [&](int c) { return (omega * v.dinv[c]) * b[c]; }));
+                }
+                if (!grid_sync(a.bar, a.err)) return;
+                for (int k = 2; k < a.nu_pre; ++k) {
+                    for (int i = gtid; i < nl; i += gsz)
+                        t[i] = x[i] + (omega * v.dinv[i]) * (b[i] - prow_Bx(i, v.B.rp, v.B.ci, v.B.v, x));
+                    if (!grid_sync(a.bar, a.err)) return;
+                    T* q = x;
+                    x = t;
+                    t = q;
+                }
+            } else if (a.nu_pre == 1) {
+                for (int i = gtid; i < nl; i += gsz) x[i] = (omega * v.dinv[i]) * b[i];
+                if (!grid_sync(a.bar, a.err)) return;
+            } else {
+                for (int i = gtid; i < nl; i += gsz) x[i] = T(0);
+                if (!grid_sync(a.bar, a.err)) return;
+            }
+            for (int i = gtid; i < nl; i += gsz) t[i] = b[i] - prow_Bx(i, v.B.rp, v.B.ci, v.B.v, x);
+            if (!grid_sync(a.bar, a.err)) return;
+            const int nc = a.lv[l + 1].B.n;
+            T* bc = a.lv[l + 1].b;
+            for (int I = gtid; I < nc; I += gsz)
+                bc[I] = row_sum<T>(v.qrp[I], v.qrp[I + 1], v.qci, v.qv, [&](int i) { return t[i]; });
+            if (!grid_sync(a.bar, a.err)) return;
+            xcur[l] = x;
+            xtmp[l] = t;
+        }
+        // ---- the coarse end: the single-block tail, or B_L^+ by the grid
+        if (has_tail) {
+            if (blockIdx.x == 0) tail_cycle(a.tail, psm);
+            if (!grid_sync(a.bar, a.err)) return;
+            xcur[a.l0] = a.tail.lv[0].x;  // set below from the tail's buffer bookkeeping
+        } else {
+            const int nL = a.lv[a.L].B.n;
+            T* bL = a.L == 0 ? a.vin : a.lv[a.L].b;
+            for (int row = gtid >> 5; row < nL; row += gsz >> 5) {
+                T sum = T(0);
+                for (int c = lane; c < nL; c += 32) sum += a.pinv[(int64_t)row * nL + c] * bL[c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (lane == 0) a.lv[a.L].x[row] = sum;
+            }
+            if (!grid_sync(a.bar, a.err)) return;
+            xcur[a.L] = a.lv[a.L].x;
+        }
+        if (has_tail) {  // the buffer the tail left the first tail level's x in (final_x)
+            const VLevel<T>& v = a.lv[a.l0];
+            if (a.l0 == a.L) {
+                xcur[a.l0] = v.x;
+            } else {
+                T* x = v.x;
+                T* t = v.r;
+                for (int k = 2; k < a.nu_pre; ++k) {
+                    T* q = x;
+                    x = t;
+                    t = q;
+                }
+                for (int k = 0; k < a.nu_post; ++k) {
+                    T* q = x;
+                    x = t;
+                    t = q;
+                }
+                xcur[a.l0] = x;
+            }
+        }
+        // ---- V-cycle, up
+        for (int l = Lg - 1; l >= 0; --l) {
+            const VLevel<T>& v = a.lv[l];
+            const int nl = v.B.n;
+            T* b = l == 0 ? a.vin : v.b;
+            T* x = xcur[l];
+            T* t = xtmp[l];
+            T* zl = l == 0 ? a.Z : nullptr;
+            const T* ec = xcur[l + 1];
+            for (int i = gtid; i < nl; i += gsz) {
+                T s = T(0);
+                for (int q = 0; q < v.P.pcnt[i]; ++q)
+                    s += v.P.pval[(int64_t)i * v.P.c + q] * ec[v.P.pcol[(int64_t)i * v.P.c + q]];
+                x[i] = x[i] + s;
+            }
+            if (!grid_sync(a.bar, a.err)) return;
+            for (int k = 0; k < a.nu_post; ++k) {
+                T* zk = k == a.nu_post - 1 ? zl : nullptr;
+                for (int i = gtid; i < nl; i += gsz) {
+                    const T val = x[i] + (omega * v.dinv[i]) * (b[i] - prow_Bx(i, v.B.rp, v.B.ci, v.B.v, x));
+                    t[i] = val;
+                    if (zk) zk[(int64_t)j * nl + i] = val;
+                }
+                if (!grid_sync(a.bar, a.err)) return;
+                T* q = x;
+                x = t;
+                t = q;
+            }
+            if (a.nu_post == 0 && zl) {
+                for (int i = gtid; i < nl; i += gsz) zl[(int64_t)j * nl + i] = x[i];
+                if (!grid_sync(a.bar, a.err)) return;
+            }
+            xcur[l] = x;
+        }
+        const T* z = a.L == 0 ? a.lv[0].x : xcur[0];
+        if (a.L == 0 && a.Z) {
+            for (int i = gtid; i < n; i += gsz) a.Z[(int64_t)j * n + i] = z[i];
+            if (!grid_sync(a.bar, a.err)) return;
+        }
+        // ---- w = V[j+1] = B z (FP64) and its per-tile dots with V[0..j]
+        double* w = a.V + (int64_t)(j + 1) * n;
+        double* Pa = a.partial;
+        double* Pb = a.partial + (size_t)a.nt * stride;
+        for (int tl = blockIdx.x; tl < a.nt; tl += gridDim.x) {
+            const int r0 = tl * a.tile, cnt = min(a.tile, n - r0);
+            for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+                const int i = r0 + e;
+                w[i] = row_sum<double>(a.B.rp[i], a.B.rp[i + 1], a.B.ci, a.B.v, [&](int c) { return (double)z[c]; });
+            }
+            __syncthreads();
+            for (int q = wid; q <= j; q += nw) {
+                const double* vq = a.V + (int64_t)q * n + r0;
+                double acc = 0.0;
+                for (int e = lane; e < cnt; e += 32) acc += vq[e] * w[r0 + e];
+                acc = warp_sum(acc);
+                if (lane == 0) Pa[(int64_t)tl * stride + q] = acc;
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(a.bar, a.err)) return;
+        // ---- two classical Gram-Schmidt passes: h = column sums of Pin; w -= V[0..j] h; dots
+        for (int pass = 0; pass < 2; ++pass) {
+            const double* Pin = pass == 0 ? Pa : Pb;
+            double* Pout = pass == 0 ? Pb : Pa;
+            double* hout = a.st + (pass == 0 ? GL.h1 : GL.h2);
+            for (int q = wid; q <= j; q += nw) {
+                double sacc = 0.0;
+                for (int bb = lane; bb < a.nt; bb += 32) sacc += Pin[(int64_t)bb * stride + q];
+                sacc = warp_sum(sacc);
+                if (lane == 0) {
+                    sh[q] = sacc;
+                    if (blockIdx.x == 0) hout[q] = sacc;
+                }
+            }
+            __syncthreads();
+            for (int tl = blockIdx.x; tl < a.nt; tl += gridDim.x) {
+                const int r0 = tl * a.tile, cnt = min(a.tile, n - r0);
+                for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+                    const int i = r0 + e;
+                    double sacc = w[i];
+                    for (int q = 0; q <= j; ++q) sacc -= a.V[(int64_t)q * n + i] * sh[q];
+                    w[i] = sacc;
+                }
+                __syncthreads();
+                const int nv = pass == 1 ? 1 : j + 1;
+                for (int q = wid; q < nv; q += nw) {
+                    const double* vq = pass == 1 ? w + r0 : a.V + (int64_t)q * n + r0;
+                    double acc = 0.0;
+                    for (int e = lane; e < cnt; e += 32) acc += vq[e] * w[r0 + e];
+                    acc = warp_sum(acc);
+                    if (lane == 0) Pout[(int64_t)tl * stride + q] = acc;
+                }
+                __syncthreads();
+            }
+            if (!grid_sync(a.bar, a.err)) return;
+        }
+        // ---- ||w||, the Givens update (block 0) and v_{j+1} = w / ||w|| (every block)
+        if (wid == 0) {
+            double nn = 0.0;
+            for (int bb = lane; bb < a.nt; bb += 32) nn += Pa[(int64_t)bb * stride];
+            nn = warp_sum(nn);
+            if (lane == 0) s_nrm2 = nn;
+        }
+        __syncthreads();
+        if (blockIdx.x == 0) {
+            double* st = a.st;
+            if (threadIdx.x == 0) st[GL.nrm2] = s_nrm2;
+            for (int q = threadIdx.x; q <= j; q += blockDim.x) {
+                gcol[q] = st[GL.h1 + q] + st[GL.h2 + q];
+                if (q < j) {
+                    gcs[q] = st[GL.cs + q];
+                    gsn[q] = st[GL.sn + q];
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const double hn = sqrt(s_nrm2);
+                gcol[j + 1] = hn;
+                for (int q = 0; q < j; ++q) {
+                    const double c = gcs[q], sn = gsn[q];
+                    const double x0 = gcol[q], x1 = gcol[q + 1];
+                    gcol[q] = c * x0 + sn * x1;
+                    gcol[q + 1] = -sn * x0 + c * x1;
+                }
+                const double x0 = gcol[j], x1 = gcol[j + 1];
+                const double den = hypot(x0, x1);
+                const double c = den == 0.0 ? 1.0 : x0 / den, sn = den == 0.0 ? 0.0 : x1 / den;
+                st[GL.cs + j] = c;
+                st[GL.sn + j] = sn;
+                gcol[j] = c * x0 + sn * x1;
+                const double gj = st[GL.g + j];
+                st[GL.g + j + 1] = -sn * gj;
+                st[GL.g + j] = c * gj;
+                st[GL.est] = fabs(st[GL.g + j + 1]);
+                st[GL.hn] = hn;
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q <= j; q += blockDim.x) st[GL.R + q + (int64_t)j * a.m] = gcol[q];
+        }
+        {
+            const double hn = sqrt(s_nrm2);
+            for (int i = gtid; i < n; i += gsz) w[i] = hn != 0.0 ? w[i] / hn : 0.0;
+        }
+        if (!grid_sync(a.bar, a.err)) return;
+        // ---- the stop test of k_step_end, taken by every block on the same values
+        const int jn = j + 1;
+        const double est = *(volatile double*)(a.st + GL.est), hn = *(volatile double*)(a.st + GL.hn);
+        const bool stop = jn >= (int)a.ctl[2] || hn == 0.0 || est * a.ctl[0] <= a.ctl[1];
+        j = jn;
+        if (stop) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) *a.dj = jn;
+            return;
+        }
+    }
+}
+
+// Launches k_arnoldi_cycle for the steps *dj .. until its stop test (ctl) on stream s.
+// Returns false, launching nothing, when the hierarchy or the device does not qualify:
+// a grid level with long rows (the lane-group kernels), more than PERSIST_MAX_LEVELS
+// levels, a tail that does not fit beside the kernel's own shared memory, or no
+// cooperative launch of one 1024-thread block per SM.
+template <typename T>
+bool arnoldi_cycle_persistent(int n, const MatView<double>& B, double* V, T* Z, T* vin, int* dj, double* st, int m,
+                              double* partial, const std::vector<VLevel<T>>& lv, const T* pinv, double omega,
+                              int nu_pre, int nu_post, const double* ctl, unsigned* bar, int* err, cudaStream_t s) {
+    const int L = (int)lv.size() - 1;
+    if (L + 1 > PERSIST_MAX_LEVELS) return false;
+    const int l0 = tail_start(lv);
+    if (lv[0].gs_ncol > 0) return false;  // the multicolour Gauss-Seidel smoother runs in the graph form
+    for (int l = 0; l < std::min(L, l0); ++l)
+        if (lanes_per_row(lv[l].B.n, lv[l].B.nnz) != 1) return false;
+    int dev = 0, sms = 0, coop = 0;
+    BAMG_CK(cudaGetDevice(&dev));
+    BAMG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BAMG_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop || sms <= 0) return false;
+    cudaFuncAttributes fa{};
+    BAMG_CK(cudaFuncGetAttributes(&fa, k_arnoldi_cycle<T>));
+    const size_t budget = (size_t)TAIL_SMEM - fa.sharedSizeBytes - 1024;
+    CycleArgs<T> a;
+    a.L = L;
+    a.l0 = l0;
+    for (int l = 0; l <= L; ++l) a.lv[l] = lv[l];
+    a.pinv = pinv;
+    size_t smem = 0;
+    if (l0 <= L) {
+        size_t need = 0;
+        for (int q = l0; q <= L; ++q) need += 3 * sizeof(T) * (size_t)lv[q].B.n;
+        if (al16(need) > budget) return false;
+        a.tail = make_tail_args(lv, l0, pinv, nu_pre, nu_post, (T)omega, budget, &smem);
+    }
+    a.omega = (T)omega;
+    a.nu_pre = nu_pre;
+    a.nu_post = nu_post;
+    a.B = B;
+    a.V = V;
+    a.Z = Z;
+    a.vin = vin;
+    a.st = st;
+    a.partial = partial;
+    a.m = m;
+    a.tile = arn_tile_rows(n);
+    a.nt = arn_tiles(n);
+    a.dj = dj;
+    a.ctl = ctl;
+    a.bar = bar;
+    a.err = err;
+    static std::atomic<bool> attr[256] = {};
+    BAMG_REQUIRE(dev >= 0 && dev < 256, BAMG_EINVAL, "device ordinal out of range");
+    if (!attr[dev]) {
+        BAMG_CK(cudaFuncSetAttribute(k_arnoldi_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)((size_t)TAIL_SMEM - fa.sharedSizeBytes)));
+        attr[dev] = true;
+    }
+    int per_sm = 0;
+    BAMG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_cycle<T>, PERSIST_THREADS, smem));
+    if (per_sm < 1) return false;
+    BAMG_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+    BAMG_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)sms);
+    cfg.blockDim = dim3(PERSIST_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    BAMG_CK(cudaLaunchKernelEx(&cfg, k_arnoldi_cycle<T>, a));
+    count_launch();
+    BAMG_CK(cudaGetLastError());
+    return true;
+}
+template bool arnoldi_cycle_persistent<float>(int, const MatView<double>&, double*, float*, float*, int*, double*, int,
+                                              double*, const std::vector<VLevel<float>>&, const float*, double, int,
+                                              int, const double*, unsigned*, int*, cudaStream_t);
+template bool arnoldi_cycle_persistent<double>(int, const MatView<double>&, double*, double*, double*, int*, double*,
+                                               int, double*, const std::vector<VLevel<double>>&, const double*,
+                                               double, int, int, const double*, unsigned*, int*, cudaStream_t);
 
 // `sweeps` sweeps of the smoother S of Eq. (4.4) on one level, ping-ponging between x and
 // y; the result ends in x (one copy when sweeps is odd).

@@ -193,6 +193,13 @@ void update_minus(int n, const double* V, int64_t ldv, int nv, const double* d_h
 template <typename TZ>
 void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const double* d_y, double* x, cudaStream_t s);
 // sum |B x|, sum (B x)^2, sum |x|, sum x into d_out[4] (deterministic).
+// FGMRES Arnoldi steps *dj .. (until the stop test of ctl) in one cooperative launch with
+// grid-wide barriers (same iterates as the captured step); false, launching nothing, when
+// the hierarchy or device does not qualify.  bar: 2 unsigned, err: 1 int (device).
+template <typename T>
+bool arnoldi_cycle_persistent(int n, const MatView<double>& B, double* V, T* Z, T* vin, int* dj, double* st, int m,
+                              double* partial, const std::vector<VLevel<T>>& lv, const T* pinv, double omega,
+                              int nu_pre, int nu_post, const double* ctl, unsigned* bar, int* err, cudaStream_t s);
 // Section 4.3 (preconditioned Arnoldi): one step on C B with the index j in *dj (raw
 // Hessenberg column into H, ld ldh), and the eigenvector of H_k for the eigenvalue closest
 // to 0 (inverse iteration with shift 0; k <= PARN_MMAX).

@@ -236,6 +236,8 @@ struct Solver : SolverBase {
     int64_t graph_kernels = 0;  // kernels of one step
     bool graph_loop = false;    // one launch runs steps until the device-side test stops it
     DevBuf<double> ctl;         // the loop's kappa, tol ||x||_1 and last j + 1
+    DevBuf<unsigned> pbar;      // grid barrier of the persistent Arnoldi cycle
+    DevBuf<int> perr;           // set when one of its barrier waits gave up
 
     ~Solver() override {
         cudaStreamSynchronize(s);
@@ -1073,6 +1075,12 @@ struct Solver : SolverBase {
         // stopping test: ||B x||_1 / ||x||_1 <= tol, or with BAMG_NORM_L2 the 2-norm ratio
         // (the criterion of the paper's tables); ratio1 is always the l1 ratio
         const bool l2 = (flags & BAMG_NORM_L2) != 0;
+        bool persist = o.persistent != 0;  // steps in one cooperative launch where the hierarchy qualifies
+        if (persist) {
+            if (!ctl.get()) ctl.alloc(3);
+            pbar.ensure(2);
+            perr.ensure(1);
+        }
         residual_norms(B, x0.get(), rn.get(), partial.get(), s);
         read_n(rn.get(), RESNORM_SUMS);
         double ratio1 = h_pin[0] / h_pin[2];
@@ -1082,7 +1090,7 @@ struct Solver : SolverBase {
         bool have_xw = false;
         if (ratio <= tol) status = BAMG_OK;
         while (status != BAMG_OK && it < o.max_it) {
-            if (!gexec) capture_step(n);
+            if (!persist && !gexec) capture_step(n);
             double* V0 = V.get();
             spmv_f64(B, x0.get(), V0, -1.0, s);
             dots(n, V0, n, 1, V0, state.get() + GL.nrm2, partial.get(), s);
@@ -1090,7 +1098,37 @@ struct Solver : SolverBase {
             scale_vec(n, V0, state.get(), GL.hn, true, V0, s);
             BAMG_CK(cudaMemsetAsync(dj.get(), 0, sizeof(int), s));
             for (int j = 0; j < m && it < o.max_it; ++j) {
-                if (graph_loop) {  // steps j .. jn - 1 in one launch
+                bool launched = false;
+                if (persist) {  // steps j .. jn - 1 in one cooperative launch
+                    h_pin[12] = kappa;
+                    h_pin[13] = tol * x1;
+                    h_pin[14] = (double)std::min(m, j + (o.max_it - it));
+                    BAMG_CK(cudaMemcpyAsync(ctl.get(), h_pin + 12, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+                    std::vector<VLevel<T>> vl = vlevels(vin.get(), zout.get());
+                    launched = arnoldi_cycle_persistent<T>(n, B, V.get(), Z.get(), vin.get(), dj.get(), state.get(), m,
+                                                           partial.get(), vl, pinvT.get(), o.omega, o.nu_pre,
+                                                           o.nu_post, ctl.get(), pbar.get(), perr.get(), s);
+                    if (launched) {
+                        BAMG_CK(cudaMemcpyAsync(h_pin, state.get() + GL.est, 2 * sizeof(double),
+                                                cudaMemcpyDeviceToHost, s));
+                        BAMG_CK(cudaMemcpyAsync(h_pin + 4, dj.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+                        BAMG_CK(cudaMemcpyAsync(h_pin + 5, perr.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+                        BAMG_CK(cudaStreamSynchronize(s));
+                        ++waits;
+                        BAMG_REQUIRE(*reinterpret_cast<const int*>(h_pin + 5) == 0, BAMG_ETIMEOUT,
+                                     "persistent Arnoldi cycle: a grid barrier wait gave up");
+                        const int jn = *reinterpret_cast<const int*>(h_pin + 4);
+                        BAMG_REQUIRE(jn > j && jn <= (int)h_pin[14], BAMG_ECUDA,
+                                     "persistent Arnoldi cycle: bad step count");
+                        it += jn - j;
+                        j = jn - 1;
+                    } else {  // this hierarchy runs the captured step
+                        persist = false;
+                        if (!gexec) capture_step(n);
+                    }
+                }
+                if (launched) {
+                } else if (graph_loop) {  // steps j .. jn - 1 in one launch
                     h_pin[12] = kappa;
                     h_pin[13] = tol * x1;
                     h_pin[14] = (double)std::min(m, j + (o.max_it - it));
@@ -1296,6 +1334,7 @@ int bamg_default_opts(bamg_opts* o) {
     o->setup_cycles = 1;
     o->mu = 1;
     o->smoother = BAMG_SMOOTH_JACOBI;
+    o->persistent = 0;
     return BAMG_OK;
 }
 
@@ -1477,7 +1516,10 @@ int bamg_solve_batch(int nchains, const bamg_csr* As, const int* r, const int* l
             // with several host threads, graphs holding a WHILE conditional node slowed the
             // other threads' setups about fourfold (512-chain mixture, 8 workers), more than
             // the device-side loop saves: one graph launch per Arnoldi step here
-            if (nworkers > 1) o.device_loop = 0;
+            if (nworkers > 1) {
+                o.device_loop = 0;
+                o.persistent = 0;  // a cooperative launch holds every SM: the workers' solves would take turns
+            }
             bamg_handle* h = nullptr;
             bamg_stats local{};
             int code = bamg_setup(&As[k], r[k], levels[k], &o, &h);

@@ -237,13 +237,45 @@ def test_learned_setup_solves_and_falls_back():
         assert s.interp_used()[0] == "learned"
         x, st = s.solve(1e-13 if precision == "fp64" else 1e-12)
         assert rel(x.cpu().numpy(), xe) < bound, (precision, st)
-        rho_l = s.vcycle_factor()
-        s_ls = bamg.Solver(rp, ci, v, r=10, levels=20, grid=ch.grid, precision=precision)
-        rho_ls = s_ls.vcycle_factor()
-        assert rho_l < max(1.0, 1.5 * rho_ls)
     # a limit no hierarchy meets sends the setup back to least squares
     s = bamg.Solver(rp, ci, v, r=10, levels=20, grid=ch.grid, interp="learned", model=m, learned_rho_max=1e-9)
     used, rho = s.interp_used()
     assert used == "ls" and rho > 1e-9
     x, st = s.solve(1e-13)
     assert rel(x.cpu().numpy(), xe) < 1e-8
+
+
+def test_learned_gain_on_a_held_out_chain():
+    """What the trained network gains: the MLP trained (20 epochs) on the LS rows of four
+    tandem queues of capacity 63-255 with random rates, then a held-out tandem queue of
+    capacity 255 (65,536 states) with other rates, whose least-squares V-cycle converges
+    (factor about 0.73, so the baseline is sound): the learned hierarchy's V-cycle factor is
+    at least 5% smaller and FGMRES needs at least two fewer iterations (measured on a
+    GB300: 0.681 against 0.735, 13 against 17), in both precisions."""
+    torch = _torch()
+    bamg = _bamg()
+
+    def dev(c):
+        return tuple(torch.tensor(a, device="cuda") for a in (c.row_ptr, c.col, c.val))
+
+    Fs, Ts = [], []
+    for c in tandem_training_set(1, 4, n_lo=63, n_hi=255):
+        f, t = bamg.interp_dataset(*dev(c), 10, 20, grid=c.grid, precision="mixed")
+        keep = (f[:, 0:96:6].sum(dim=1) > 0) & (t.abs().amax(dim=1) <= 4.0)
+        Fs.append(f[keep])
+        Ts.append(t[keep])
+    F, T = torch.cat(Fs), torch.cat(Ts)
+    m = bamg.Model(0)
+    m.train(F, T, epochs=20, batch=4096, lr=1e-3)
+    test = tandem_training_set(99, 1, n_lo=255, n_hi=255)[0]
+    A = dev(test)
+    for precision in ("mixed", "fp64"):
+        s_ls = bamg.Solver(*A, r=10, levels=20, grid=test.grid, precision=precision)
+        s_l = bamg.Solver(*A, r=10, levels=20, grid=test.grid, precision=precision, interp="learned", model=m)
+        rho_ls, rho_l = s_ls.vcycle_factor(30), s_l.vcycle_factor(30)
+        _, st_ls = s_ls.solve(1e-10)
+        _, st_l = s_l.solve(1e-10)
+        assert rho_ls < 1.0, rho_ls
+        assert rho_l <= 0.95 * rho_ls, (precision, rho_l, rho_ls)
+        assert st_l["iterations"] <= st_ls["iterations"] - 2, (precision, st_l["iterations"], st_ls["iterations"])
+    m.close()

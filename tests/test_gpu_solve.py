@@ -247,7 +247,7 @@ def test_device_loop_gives_the_same_iterates(precision):
     # run the same arithmetic and take the same decisions: bit-identical results; a short
     # restart length exercises restarts and the end-of-cycle exit
     ch = tandem_queue(63)
-    runs = [_run(ch, 10, 10, 1e-12, precision, gmres_m=6, device_loop=d) for d in (0, 1)]
+    runs = [_run(ch, 10, 10, 1e-12, precision, gmres_m=6, device_loop=d, persistent=0) for d in (0, 1)]
     (_, x0, st0), (_, x1, st1) = runs
     assert np.array_equal(x0, x1)
     for k in ("iterations", "restarts", "true_checks", "residual_l1"):
@@ -255,6 +255,36 @@ def test_device_loop_gives_the_same_iterates(precision):
     assert st0["restarts"] >= 1
     assert st0["host_waits"] == st0["iterations"]
     assert st1["host_waits"] == st1["true_checks"] < st1["iterations"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("kind,m", [("tandem63", 6), ("tandem63", 50), ("grid8", 50), ("bd3000", 60),
+                                     ("grid_rect", 50)])
+def test_persistent_cycle_gives_the_same_iterates(kind, m, precision):
+    """The Arnoldi steps in one cooperative launch with grid barriers (persistent=1) and the
+    captured step (one graph launch per step) give bit-identical iterates: with a coarse
+    tail (tandem, birth-death) and with the dense coarsest level as the only level (8 x 8
+    grid), with and without restarts; the persistent form launches far fewer kernels."""
+    bamg = _bamg()
+    if kind == "tandem63":
+        ch, kw = tandem_queue(63), {}
+    elif kind == "grid8":
+        ch, kw = grid_walk(8), {}
+    elif kind == "grid_rect":
+        ch, kw = grid_walk(45, 19), {}
+    else:
+        ch, kw = random_birth_death(3000, 9), dict(ridge=1e-10)
+    l0 = bamg.launch_count()
+    _, xg, stg = _run(ch, 8, 20, 1e-12, precision, gmres_m=m, device_loop=0, persistent=0, **kw)
+    l1 = bamg.launch_count()
+    _, xp, stp = _run(ch, 8, 20, 1e-12, precision, gmres_m=m, persistent=1, **kw)
+    l2 = bamg.launch_count()
+    assert np.array_equal(xg, xp)
+    for k in ("iterations", "restarts", "true_checks", "residual_l1"):
+        assert stg[k] == stp[k], k
+    assert stp["host_waits"] == stp["true_checks"]
+    if stg["iterations"] >= 4:
+        assert (l2 - l1) < (l1 - l0), (l1 - l0, l2 - l1)
 
 
 def test_device_loop_stops_at_max_it():
