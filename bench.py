@@ -148,7 +148,8 @@ def run_ours(args):
 
     def step(precision="mixed"):
         s = bamg.Solver(rp, ci, v, r=R, levels=20, grid=ch.grid, precision=precision,
-                        device_loop=args.device_loop, persistent=args.persistent)
+                        device_loop=args.device_loop, persistent=args.persistent,
+                        coarse_tail=args.coarse_tail)
         _, st = s.solve(TOL, out=x)
         return s, st
 
@@ -775,6 +776,9 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 2^20-point Delaunay line")
     ap.add_argument("--persistent", type=int, default=0,
                     help="1: Arnoldi steps in one cooperative launch where the hierarchy qualifies; 0: graph form")
+    ap.add_argument("--coarse-tail", type=int, default=0, choices=[0, 1],
+                    help="coarse end of the V-cycle: 0 on a thread-block cluster (from the first level with at "
+                         "most 4096 rows), 1 in one block (from 1024 rows)")
     ap.add_argument("--no-variants", action="store_true", help="skip the variants line (smoother, setup cycling, "
                                                                  "pArnoldi)")
     ap.add_argument("--large-only", action="store_true", help="run only the 2^20-point Delaunay line")

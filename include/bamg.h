@@ -128,6 +128,16 @@ typedef struct {
                                0 (default): the graph form, which measured faster (the grid barriers
                                between the step's phases cost more than graph kernel boundaries).
                                bamg_solve_batch with more than one worker always uses the graph form. */
+    int32_t coarse_tail;    /* the coarse end of the V-cycle (Eq. (4.4) on the small levels) in one
+                               launch per cycle: 0 (default) = every level from the first one with at
+                               most 4096 rows on one cluster of 8 thread blocks (each block owns a slice
+                               of every level's rows and sends its values to the others through
+                               distributed shared memory; cluster barriers between the phases), where
+                               the device supports clusters; 1 = every level from the first one with at
+                               most 1024 rows in a single thread block.  One thread per row in the grid
+                               kernels' order of operations: on hierarchies whose levels have fewer than
+                               12 entries per row on average the iterates are the same bit for bit,
+                               otherwise equal up to rounding. */
 } bamg_opts;
 
 enum { BAMG_SMOOTH_JACOBI = 0, BAMG_SMOOTH_MCGS = 1 };

@@ -44,7 +44,8 @@ class Opts(C.Structure):
                 ("cr_omega", C.c_double), ("stream", C.c_void_p), ("interp", C.c_int32), ("learned_refit", C.c_int32),
                 ("model", C.c_void_p), ("learned_rho_max", C.c_double),
                 ("device_loop", C.c_int32), ("mle_restart", C.c_int32), ("setup_cycles", C.c_int32),
-                ("mu", C.c_int32), ("smoother", C.c_int32), ("persistent", C.c_int32)]
+                ("mu", C.c_int32), ("smoother", C.c_int32), ("persistent", C.c_int32),
+                ("coarse_tail", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -212,6 +212,7 @@ struct TailArgs {
     VLevel<T> lv[TAIL_MAX_LEVELS];
     int32_t soff[TAIL_MAX_LEVELS];  // byte offset of the level's staged matrices, -1: read from global
     int32_t pinv_off = -1;          // byte offset of the staged B_L^+, -1: read from global
+    int32_t voff[TAIL_MAX_LEVELS];  // element offset of the level's vectors b, x, t in shared memory
     int nl = 0;  // levels in the tail; the last one is the coarsest
     const T* pinv = nullptr;
     int nu_pre = 0, nu_post = 0;
@@ -311,35 +312,26 @@ __device__ __forceinline__ void tail_stage(const TailArgs<T>& a, unsigned char* 
 // final x to the global buffer the grid kernels read it from.
 template <typename T>
 __device__ __forceinline__ void tail_cycle(const TailArgs<T>& a, unsigned char* tail_smem) {
-    // the vectors of all tail levels: b, x and the work vector per level
+    // the vectors of all tail levels: b, x and the work vector t of level l at
+    // sbuf + voff[l] + {0, n, 2n}.  Which of x and t holds the iterate after the pre- (and the
+    // post-) smoothing sweeps follows from the sweep counts, so the buffers are addressed from
+    // the kernel parameters alone: a per-thread pointer table indexed by level would live in
+    // local memory, which the large shared-memory carve-out leaves to L2.
     T* sbuf = reinterpret_cast<T*>(tail_smem);
     const int tid = threadIdx.x;
-    T* sb[TAIL_MAX_LEVELS];
-    T* sx[TAIL_MAX_LEVELS];
-    T* sr[TAIL_MAX_LEVELS];
-    {
-        size_t off = 0;
-        for (int l = 0; l < a.nl; ++l) {
-            const int n = a.lv[l].B.n;
-            sb[l] = sbuf + off;
-            sx[l] = sbuf + off + n;
-            sr[l] = sbuf + off + 2 * (size_t)n;
-            off += 3 * (size_t)n;
-        }
-    }
-    for (int i = tid; i < a.lv[0].B.n; i += blockDim.x) sb[0][i] = a.lv[0].b[i];
+    const bool pre_sw = a.nu_pre >= 2 && ((a.nu_pre - 2) & 1);  // iterate in t after the down sweeps
+    const bool post_sw = (a.nu_post & 1) != 0;                   // the up sweeps swap once more each
+    for (int i = tid; i < a.lv[0].B.n; i += blockDim.x) sbuf[a.voff[0] + i] = a.lv[0].b[i];
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    T* xcur[TAIL_MAX_LEVELS];
-    T* xtmp[TAIL_MAX_LEVELS];
     T* gx = a.lv[0].x;  // global buffer that receives the first tail level's result
     T* gt = a.lv[0].r;
     for (int l = 0; l + 1 < a.nl; ++l) {
         const VLevel<T> v = tail_level(a, l, tail_smem);
         const int n = v.B.n;
-        T* b = sb[l];
-        T* x = sx[l];
-        T* t = sr[l];
+        T* b = sbuf + a.voff[l];
+        T* x = b + n;
+        T* t = b + 2 * n;
         if (a.nu_pre >= 2) {
             for (int i = tid; i < n; i += blockDim.x) {
                 const T x1 = (a.omega * v.dinv[i]) * b[i];
@@ -369,35 +361,36 @@ __device__ __forceinline__ void tail_cycle(const TailArgs<T>& a, unsigned char* 
         for (int i = tid; i < n; i += blockDim.x) t[i] = b[i] - row_Bx(i, v.B.rp, v.B.ci, v.B.v, x);
         __syncthreads();
         const int nc = a.lv[l + 1].B.n;
-        T* bc = sb[l + 1];
+        T* bc = sbuf + a.voff[l + 1];
         for (int I = tid; I < nc; I += blockDim.x)
             bc[I] = row_sum<T>(v.qrp[I], v.qrp[I + 1], v.qci, v.qv, [&](int i) { return t[i]; });
         __syncthreads();
-        xcur[l] = x;
-        xtmp[l] = t;
     }
+    const int L = a.nl - 1;
     {  // coarsest: x = B_L^+ b, one warp per row as in the grid kernel
-        const int L = a.nl - 1;
         const int n = a.lv[L].B.n;
         const int lane = tid & 31;
         const T* pinv = a.pinv_off >= 0 ? reinterpret_cast<const T*>(tail_smem + a.pinv_off) : a.pinv;
+        const T* bL = sbuf + a.voff[L];
+        T* xL = sbuf + a.voff[L] + n;
         for (int row = tid >> 5; row < n; row += blockDim.x >> 5) {
             T sum = T(0);
-            for (int c = lane; c < n; c += 32) sum += pinv[(int64_t)row * n + c] * sb[L][c];
+            for (int c = lane; c < n; c += 32) sum += pinv[(int64_t)row * n + c] * bL[c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if (lane == 0) sx[L][row] = sum;
+            if (lane == 0) xL[row] = sum;
         }
         __syncthreads();
-        xcur[L] = sx[L];
     }
-    for (int l = a.nl - 2; l >= 0; --l) {
+    for (int l = L - 1; l >= 0; --l) {
         const VLevel<T> v = tail_level(a, l, tail_smem);
         const int n = v.B.n;
-        T* b = sb[l];
-        T* x = xcur[l];
-        T* t = xtmp[l];
-        const T* ec = xcur[l + 1];
+        T* b = sbuf + a.voff[l];
+        T* x = b + (pre_sw ? 2 : 1) * n;  // the down pass's iterate
+        T* t = b + (pre_sw ? 1 : 2) * n;
+        // the coarse correction: level l + 1's final iterate
+        const int nc = a.lv[l + 1].B.n;
+        const T* ec = sbuf + a.voff[l + 1] + (l + 1 == L ? 1 : ((pre_sw != post_sw) ? 2 : 1)) * nc;
         for (int i = tid; i < n; i += blockDim.x) x[i] = row_prolonged(i, v.P.c, v.P.pcol, v.P.pval, v.P.pcnt, ec, x);
         __syncthreads();
         for (int k = 0; k < a.nu_post; ++k) {
@@ -413,20 +406,32 @@ __device__ __forceinline__ void tail_cycle(const TailArgs<T>& a, unsigned char* 
                 gt = g;
             }
         }
-        xcur[l] = x;
     }
     // the first tail level's x to the global buffer the grid kernels read it from
-    const T* xf = xcur[0];
-    for (int i = tid; i < a.lv[0].B.n; i += blockDim.x) gx[i] = xf[i];
+    const int n0 = a.lv[0].B.n;
+    const T* xf = sbuf + a.voff[0] + ((a.nl > 1 && pre_sw != post_sw) ? 2 : 1) * n0;
+    for (int i = tid; i < n0; i += blockDim.x) gx[i] = xf[i];
 }
 
+// Static shared memory of k_vcycle_tail: a copy of its arguments (the phases index them by
+// level; from shared memory such reads are cheap).
+constexpr int TAIL_STATIC = 4096;
+static_assert(sizeof(TailArgs<double>) <= TAIL_STATIC && sizeof(TailArgs<double>) % 4 == 0, "tail arguments");
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<T> a) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
+    __shared__ __align__(16) unsigned char sa_raw[sizeof(TailArgs<T>)];
+    {
+        const int* src = reinterpret_cast<const int*>(&a);
+        int* dst = reinterpret_cast<int*>(sa_raw);
+        for (int k = threadIdx.x; k < (int)(sizeof(TailArgs<T>) / 4); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const TailArgs<T>& sa = *reinterpret_cast<const TailArgs<T>*>(sa_raw);
     // the matrices first: they were written during the setup, long before this launch
-    tail_stage(a, tail_smem);
+    tail_stage(sa, tail_smem);
     pdl_begin();
-    tail_cycle(a, tail_smem);
+    tail_cycle(sa, tail_smem);
 }
 
 // The buffer that holds a level's final x after the down and up passes (the sequence of
@@ -514,7 +519,10 @@ static TailArgs<T> make_tail_args(const std::vector<VLevel<T>>& lv, int l0, cons
     a.nu_post = nu_post;
     a.omega = omega;
     size_t smem = 0;
-    for (int q = 0; q < a.nl; ++q) smem += 3 * sizeof(T) * (size_t)a.lv[q].B.n;
+    for (int q = 0; q < a.nl; ++q) {
+        a.voff[q] = (int32_t)(smem / sizeof(T));
+        smem += 3 * sizeof(T) * (size_t)a.lv[q].B.n;
+    }
     BAMG_REQUIRE(smem <= 96 * 1024, BAMG_EINVAL, "vcycle tail: levels too large for shared memory");
     smem = al16(smem);
     for (int q = 0; q < a.nl; ++q) {
@@ -535,6 +543,418 @@ static TailArgs<T> make_tail_args(const std::vector<VLevel<T>>& lv, int l0, cons
     return a;
 }
 
+// ---------------------------------------------------------------- the coarse end on a cluster
+// The tail levels spread over one cluster of CTAIL_CS blocks, one per SM.  Block q owns the
+// rows [n q / CS, n (q + 1) / CS) of every tail level (for Q: the same split of the coarse
+// rows).  Every block keeps a full copy of each tail level's vectors b, x and t.  A phase
+// computes the block's own rows with the per-row arithmetic of the grid kernels (one thread
+// per row, the same order of operations, so the result is identical) and stores each value
+// into the copies of all blocks of the cluster (distributed shared memory).  A cluster
+// barrier with release / acquire semantics then ends the phase, so every block reads the
+// whole vector in the next one.  Each block stages only its own rows of B, P, Q and B_L^+,
+// plus all of D^{-1}, which the first sweep reads at neighbouring rows.  The finest tail
+// level may have CS times the rows of the single-block tail.
+constexpr int CTAIL_CS = 8;  // blocks per cluster (the portable maximum)
+constexpr int CTAIL_THREADS = 512;
+constexpr int CTAIL_MAX_N = CTAIL_CS * CTAIL_THREADS;  // at most one row per thread on every level
+constexpr size_t CTAIL_VEC_MAX = 96 * 1024;            // the replicated vectors of all tail levels
+constexpr int CTAIL_STATIC = 12 * 1024;                // static shared memory (arguments, slices, copy list)
+constexpr int CTAIL_JOBS = 10 * TAIL_MAX_LEVELS;       // staged arrays per block
+
+template <typename T>
+struct CTailArgs {
+    VLevel<T> lv[TAIL_MAX_LEVELS];
+    int32_t voff[TAIL_MAX_LEVELS];  // element offset of level l's b, x, t in the replicated region
+    int32_t vec_bytes = 0;          // bytes of the replicated region (a multiple of 16)
+    int32_t smem_bytes = 0;         // dynamic shared memory of each block
+    int nl = 0;                     // levels in the tail; the last one is the coarsest
+    const T* pinv = nullptr;
+    int nu_pre = 0, nu_post = 0;
+    T omega = T(0);
+};
+
+// One block's rows [lo, hi) of one tail level.  Every pointer addresses the element of the
+// first own row (or entry), staged in shared memory or in global memory: rp[i - lo],
+// ci[p - nz0], pcol[(i - lo) c + t], qrp[I - clo], qci[q - qz0], pinv[(i - lo) n + c];
+// dinv covers all rows.
+template <typename T>
+struct CSlice {
+    int lo, hi, nz0, qz0;
+    const int32_t* rp;
+    const int32_t* ci;
+    const T* v;
+    const T* dinv;
+    const int32_t* pcol;
+    const T* pval;
+    const int32_t* pcnt;
+    const int32_t* qrp;
+    const int32_t* qci;
+    const T* qv;
+    const T* pinv;
+};
+struct CopyJob {
+    const unsigned char* src;
+    unsigned char* dst;
+    int bytes;
+};
+static_assert(sizeof(CTailArgs<double>) + sizeof(CSlice<double>) * TAIL_MAX_LEVELS + sizeof(CopyJob) * CTAIL_JOBS +
+                      sizeof(int) * (4 * TAIL_MAX_LEVELS + 1) + 64 <=
+                  CTAIL_STATIC,
+              "static shared memory of the cluster tail");
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// every thread of every block of the cluster (the non-aligned form: the row loops before it
+// may leave a warp's threads apart); stores before it are visible to all blocks after it
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// value v into element p of the same shared array in every block of the cluster
+__device__ __forceinline__ void push_all(float* p, float v) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+#pragma unroll
+    for (int r = 0; r < CTAIL_CS; ++r) {
+        uint32_t ra;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
+        asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
+    }
+}
+__device__ __forceinline__ void push_all(double* p, double v) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+#pragma unroll
+    for (int r = 0; r < CTAIL_CS; ++r) {
+        uint32_t ra;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
+        asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+    }
+}
+
+// Room for `bytes` copied from src into a 16-byte aligned region: the copy starts at the
+// region's start plus (src mod 16), so source and destination agree modulo 16.
+__host__ __device__ constexpr size_t stage_room(size_t bytes) { return al16(bytes + 16); }
+// Copy job list: the block's threads copy [src, src + bytes) to dst, 16 bytes at a time
+// where both are on a 16-byte boundary, 4 bytes at a time for the ragged ends.
+__device__ __forceinline__ void run_copy(const CopyJob& j) {
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(j.src);
+    const int head = (int)(((16 - (s0 & 15)) & 15) < (uintptr_t)j.bytes ? ((16 - (s0 & 15)) & 15) : j.bytes);
+    const int n16 = (j.bytes - head) >> 4;
+    const int tail0 = head + (n16 << 4);
+    for (int k = threadIdx.x; k < (head >> 2); k += blockDim.x) cp_async4(j.dst + 4 * k, j.src + 4 * k);
+    for (int k = threadIdx.x; k < n16; k += blockDim.x) cp_async16(j.dst + head + 16 * k, j.src + head + 16 * k);
+    for (int k = threadIdx.x; k < ((j.bytes - tail0) >> 2); k += blockDim.x)
+        cp_async4(j.dst + tail0 + 4 * k, j.src + tail0 + 4 * k);
+}
+
+template <typename T>
+__global__ void __cluster_dims__(CTAIL_CS, 1, 1) __launch_bounds__(CTAIL_THREADS)
+    k_vcycle_tail_cluster(const __grid_constant__ CTailArgs<T> ga) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ __align__(16) unsigned char sa_raw[sizeof(CTailArgs<T>)];
+    __shared__ CSlice<T> sl[TAIL_MAX_LEVELS];
+    __shared__ CopyJob jobs[CTAIL_JOBS];
+    __shared__ int bnd[TAIL_MAX_LEVELS][4];  // rp[lo], rp[hi], qrp[clo], qrp[chi]
+    __shared__ int njobs;
+    const int tid = threadIdx.x;
+    {
+        const int* src = reinterpret_cast<const int*>(&ga);
+        int* dst = reinterpret_cast<int*>(sa_raw);
+        for (int k = tid; k < (int)(sizeof(CTailArgs<T>) / 4); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const CTailArgs<T>& a = *reinterpret_cast<const CTailArgs<T>*>(sa_raw);
+    const int q = (int)cluster_rank(), L = a.nl - 1;
+    auto row_lo = [&](int l, int r) { return (int)(((int64_t)a.lv[l].B.n * r) / CTAIL_CS); };
+    // ---- own rows and their entry ranges.  The matrices were written during the setup, long
+    // before this launch, so they are read before the wait on the preceding kernel.
+    if (tid < a.nl) {
+        const int l = tid, lo = row_lo(l, q), hi = row_lo(l, q + 1);
+        if (l < L) {
+            const int clo = row_lo(l + 1, q), chi = row_lo(l + 1, q + 1);
+            bnd[l][0] = a.lv[l].B.rp[lo];
+            bnd[l][1] = a.lv[l].B.rp[hi];
+            bnd[l][2] = a.lv[l].qrp[clo];
+            bnd[l][3] = a.lv[l].qrp[chi];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {  // the staging plan: levels in order while the budget lasts, global memory beyond
+        size_t off = (size_t)a.vec_bytes;
+        const size_t budget = (size_t)a.smem_bytes;
+        int nj = 0;
+        for (int l = 0; l <= L; ++l) {
+            const VLevel<T>& g = a.lv[l];
+            const int lo = row_lo(l, q), hi = row_lo(l, q + 1), rows = hi - lo, n = g.B.n;
+            CSlice<T> c;
+            c.lo = lo;
+            c.hi = hi;
+            c.nz0 = c.qz0 = 0;
+            c.rp = c.ci = c.pcol = c.pcnt = c.qrp = c.qci = nullptr;
+            c.v = c.dinv = c.pval = c.qv = c.pinv = nullptr;
+            const unsigned char* src[10];
+            size_t bytes[10];
+            int na = 0;
+            if (l < L) {
+                const int nz0 = bnd[l][0], nz1 = bnd[l][1], qz0 = bnd[l][2], qz1 = bnd[l][3];
+                const int clo = row_lo(l + 1, q), chi = row_lo(l + 1, q + 1), pc = g.P.c;
+                c.nz0 = nz0;
+                c.qz0 = qz0;
+                c.rp = g.B.rp + lo;
+                c.ci = g.B.ci + nz0;
+                c.v = g.B.v + nz0;
+                c.dinv = g.dinv;
+                c.pcol = g.P.pcol + (int64_t)lo * pc;
+                c.pval = g.P.pval + (int64_t)lo * pc;
+                c.pcnt = g.P.pcnt + lo;
+                c.qrp = g.qrp + clo;
+                c.qci = g.qci + qz0;
+                c.qv = g.qv + qz0;
+                const unsigned char* s_[10] = {(const unsigned char*)c.rp,   (const unsigned char*)c.ci,
+                                               (const unsigned char*)c.v,    (const unsigned char*)c.dinv,
+                                               (const unsigned char*)c.pcol, (const unsigned char*)c.pval,
+                                               (const unsigned char*)c.pcnt, (const unsigned char*)c.qrp,
+                                               (const unsigned char*)c.qci,  (const unsigned char*)c.qv};
+                const size_t b_[10] = {4 * (size_t)(rows + 1),        4 * (size_t)(nz1 - nz0),
+                                       sizeof(T) * (size_t)(nz1 - nz0), sizeof(T) * (size_t)n,
+                                       4 * (size_t)rows * pc,          sizeof(T) * (size_t)rows * pc,
+                                       4 * (size_t)rows,               4 * (size_t)(chi - clo + 1),
+                                       4 * (size_t)(qz1 - qz0),        sizeof(T) * (size_t)(qz1 - qz0)};
+                for (int k = 0; k < 10; ++k) {
+                    src[k] = s_[k];
+                    bytes[k] = b_[k];
+                }
+                na = 10;
+            } else if (a.pinv) {
+                c.pinv = a.pinv + (int64_t)lo * n;
+                src[0] = (const unsigned char*)c.pinv;
+                bytes[0] = sizeof(T) * (size_t)rows * n;
+                na = 1;
+            }
+            size_t need = 0;
+            for (int k = 0; k < na; ++k) need += stage_room(bytes[k]);
+            if (na > 0 && off + need <= budget && nj + na <= CTAIL_JOBS) {
+                unsigned char* d[10];
+                for (int k = 0; k < na; ++k) {
+                    d[k] = sm + off + (reinterpret_cast<uintptr_t>(src[k]) & 15);
+                    off += stage_room(bytes[k]);
+                    if (bytes[k] > 0) jobs[nj++] = CopyJob{src[k], d[k], (int)bytes[k]};
+                }
+                if (l < L) {
+                    c.rp = reinterpret_cast<const int32_t*>(d[0]);
+                    c.ci = reinterpret_cast<const int32_t*>(d[1]);
+                    c.v = reinterpret_cast<const T*>(d[2]);
+                    c.dinv = reinterpret_cast<const T*>(d[3]);
+                    c.pcol = reinterpret_cast<const int32_t*>(d[4]);
+                    c.pval = reinterpret_cast<const T*>(d[5]);
+                    c.pcnt = reinterpret_cast<const int32_t*>(d[6]);
+                    c.qrp = reinterpret_cast<const int32_t*>(d[7]);
+                    c.qci = reinterpret_cast<const int32_t*>(d[8]);
+                    c.qv = reinterpret_cast<const T*>(d[9]);
+                } else {
+                    c.pinv = reinterpret_cast<const T*>(d[0]);
+                }
+            }
+            sl[l] = c;
+        }
+        njobs = nj;
+    }
+    __syncthreads();
+    for (int k = 0; k < njobs; ++k) run_copy(jobs[k]);
+    pdl_begin();
+    // ---- the first tail level's right-hand side (written by the preceding kernel)
+    T* sbuf = reinterpret_cast<T*>(sm);
+    for (int i = tid; i < a.lv[0].B.n; i += blockDim.x) sbuf[a.voff[0] + i] = a.lv[0].b[i];
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    cluster_barrier();  // every block of the cluster runs before the first remote store
+    const bool pre_sw = a.nu_pre >= 2 && ((a.nu_pre - 2) & 1);
+    const bool post_sw = (a.nu_post & 1) != 0;
+    const T omega = a.omega;
+    T* gx = a.lv[0].x;  // global buffer that receives the first tail level's result
+    T* gt = a.lv[0].r;
+    for (int l = 0; l < L; ++l) {
+        const CSlice<T>& c = sl[l];
+        const int n = a.lv[l].B.n;
+        T* b = sbuf + a.voff[l];
+        T* x = b + n;
+        T* t = b + 2 * n;
+        auto Bx = [&](int i, const T* y) {
+            return row_sum<T>(c.rp[i - c.lo] - c.nz0, c.rp[i - c.lo + 1] - c.nz0, c.ci, c.v,
+                              [&](int j) { return y[j]; });
+        };
+        if (a.nu_pre >= 2) {
+            for (int i = c.lo + tid; i < c.hi; i += blockDim.x) {
+                const T x1 = (omega * c.dinv[i]) * b[i];
+                const T bx1 = row_sum<T>(c.rp[i - c.lo] - c.nz0, c.rp[i - c.lo + 1] - c.nz0, c.ci, c.v,
+                                         [&](int j) { return (omega * c.dinv[j]) * b[j]; });
+                push_all(x + i, x1 + (omega * c.dinv[i]) * (b[i] - bx1));
+            }
+            cluster_barrier();
+            for (int k = 2; k < a.nu_pre; ++k) {
+                for (int i = c.lo + tid; i < c.hi; i += blockDim.x)
+                    push_all(t + i, x[i] + (omega * c.dinv[i]) * (b[i] - Bx(i, x)));
+                cluster_barrier();
+                T* sw = x;
+                x = t;
+                t = sw;
+                if (l == 0) {
+                    T* g = gx;
+                    gx = gt;
+                    gt = g;
+                }
+            }
+        } else if (a.nu_pre == 1) {
+            for (int i = c.lo + tid; i < c.hi; i += blockDim.x) push_all(x + i, (omega * c.dinv[i]) * b[i]);
+            cluster_barrier();
+        } else {
+            for (int i = tid; i < n; i += blockDim.x) x[i] = T(0);  // every block clears its own copy
+            __syncthreads();
+        }
+        for (int i = c.lo + tid; i < c.hi; i += blockDim.x) push_all(t + i, b[i] - Bx(i, x));
+        cluster_barrier();
+        const CSlice<T>& cc = sl[l + 1];
+        T* bc = sbuf + a.voff[l + 1];
+        for (int I = cc.lo + tid; I < cc.hi; I += blockDim.x)
+            push_all(bc + I, row_sum<T>(c.qrp[I - cc.lo] - c.qz0, c.qrp[I - cc.lo + 1] - c.qz0, c.qci, c.qv,
+                                        [&](int i) { return t[i]; }));
+        cluster_barrier();
+    }
+    {  // coarsest: x = B_L^+ b, one warp per row as in the grid kernel
+        const CSlice<T>& c = sl[L];
+        const int n = a.lv[L].B.n, lane = tid & 31;
+        const T* bL = sbuf + a.voff[L];
+        T* xL = sbuf + a.voff[L] + n;
+        for (int row = c.lo + (tid >> 5); row < c.hi; row += blockDim.x >> 5) {
+            T sum = T(0);
+            for (int col = lane; col < n; col += 32) sum += c.pinv[(int64_t)(row - c.lo) * n + col] * bL[col];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) {
+                if (L == 0)
+                    gx[row] = sum;
+                else
+                    push_all(xL + row, sum);
+            }
+        }
+        if (L == 0) return;
+        cluster_barrier();
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        const CSlice<T>& c = sl[l];
+        const int n = a.lv[l].B.n, nc = a.lv[l + 1].B.n, pc = a.lv[l].P.c;
+        T* b = sbuf + a.voff[l];
+        T* x = b + (pre_sw ? 2 : 1) * n;  // the down pass's iterate
+        T* t = b + (pre_sw ? 1 : 2) * n;
+        const T* ec = sbuf + a.voff[l + 1] + (l + 1 == L ? 1 : ((pre_sw != post_sw) ? 2 : 1)) * nc;
+        const bool last = (l == 0 && a.nu_post == 0);
+        for (int i = c.lo + tid; i < c.hi; i += blockDim.x) {
+            const int r = i - c.lo;
+            T s = T(0);
+            for (int k = 0; k < c.pcnt[r]; ++k) s += c.pval[(int64_t)r * pc + k] * ec[c.pcol[(int64_t)r * pc + k]];
+            if (last)
+                gx[i] = x[i] + s;
+            else
+                push_all(x + i, x[i] + s);
+        }
+        if (last) return;
+        cluster_barrier();
+        for (int k = 0; k < a.nu_post; ++k) {
+            const bool fin = (l == 0 && k + 1 == a.nu_post);
+            for (int i = c.lo + tid; i < c.hi; i += blockDim.x) {
+                const T y = x[i] + (omega * c.dinv[i]) * (b[i] - row_sum<T>(c.rp[i - c.lo] - c.nz0,
+                                                                            c.rp[i - c.lo + 1] - c.nz0, c.ci, c.v,
+                                                                            [&](int j) { return x[j]; }));
+                if (fin)
+                    gt[i] = y;  // the buffer the swap below makes gx
+                else
+                    push_all(t + i, y);
+            }
+            if (fin) return;
+            cluster_barrier();
+            T* sw = x;
+            x = t;
+            t = sw;
+            if (l == 0) {
+                T* g = gx;
+                gx = gt;
+                gt = g;
+            }
+        }
+    }
+}
+
+// The tail levels l0..L as arguments of the cluster kernel (the replicated vectors first;
+// each block plans its own staging in the rest of `smem_bytes`).
+template <typename T>
+static CTailArgs<T> make_ctail_args(const std::vector<VLevel<T>>& lv, int l0, const T* pinv, int nu_pre, int nu_post,
+                                    T omega, size_t smem_bytes) {
+    const int L = (int)lv.size() - 1;
+    CTailArgs<T> a;
+    a.nl = L - l0 + 1;
+    for (int q = 0; q < a.nl; ++q) a.lv[q] = lv[l0 + q];
+    a.pinv = pinv;
+    a.nu_pre = nu_pre;
+    a.nu_post = nu_post;
+    a.omega = omega;
+    size_t vec = 0;
+    for (int q = 0; q < a.nl; ++q) {
+        a.voff[q] = (int32_t)(vec / sizeof(T));
+        vec += 3 * sizeof(T) * (size_t)a.lv[q].B.n;
+    }
+    a.vec_bytes = (int32_t)al16(vec);
+    a.smem_bytes = (int32_t)smem_bytes;
+    BAMG_REQUIRE((size_t)a.vec_bytes <= smem_bytes, BAMG_EINVAL, "vcycle tail: vectors exceed shared memory");
+    return a;
+}
+
+// First level of the cluster tail (L + 1: none): the finest level from which on every level
+// has at most CTAIL_MAX_N rows and the replicated vectors fit.
+template <typename T>
+static int ctail_start(const std::vector<VLevel<T>>& lv) {
+    const int L = (int)lv.size() - 1;
+    for (int l = 1; l <= L; ++l) {
+        if (L - l + 1 > TAIL_MAX_LEVELS || lv[l].B.n > CTAIL_MAX_N) continue;
+        size_t vec = 0;
+        for (int q = l; q <= L; ++q) vec += 3 * sizeof(T) * (size_t)lv[q].B.n;
+        if (vec <= CTAIL_VEC_MAX) return l;
+    }
+    return L + 1;
+}
+
+// Whether this device runs the cluster kernel at its shared-memory size (checked once per
+// device; the attribute is per device and idempotent).
+template <typename T>
+static bool ctail_available() {
+    static std::atomic<int> state[256] = {};  // 0 unknown, 1 yes, 2 no
+    int dev = 0;
+    BAMG_CK(cudaGetDevice(&dev));
+    BAMG_REQUIRE(dev >= 0 && dev < 256, BAMG_EINVAL, "device ordinal out of range");
+    int st = state[dev].load();
+    if (st == 0) {
+        int cl = 0;
+        BAMG_CK(cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, dev));
+        bool ok = cl != 0;
+        if (ok)
+            ok = cudaFuncSetAttribute(k_vcycle_tail_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TAIL_SMEM - CTAIL_STATIC) == cudaSuccess;
+        if (ok) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(CTAIL_CS);
+            cfg.blockDim = dim3(CTAIL_THREADS);
+            cfg.dynamicSmemBytes = TAIL_SMEM - CTAIL_STATIC;
+            int nclusters = 0;
+            ok = cudaOccupancyMaxActiveClusters(&nclusters, k_vcycle_tail_cluster<T>, &cfg) == cudaSuccess &&
+                 nclusters >= 1;
+        }
+        cudaGetLastError();  // a refusal above is an answer, not an error of later calls
+        st = ok ? 1 : 2;
+        state[dev].store(st);
+    }
+    return st == 1;
+}
+
 // First level handled by the single-block tail (L + 1: none).
 template <typename T>
 static int tail_start(const std::vector<VLevel<T>>& lv) {
@@ -553,8 +973,12 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
     }
     const int L = (int)lv.size() - 1;
     const T omega = (T)omega_d;
-    // the levels from l0 on (small enough for one block) run in k_vcycle_tail
-    const int l0 = tail_start(lv);
+    // the levels from l0 on run in one launch: every level from the first one with at most
+    // CTAIL_MAX_N rows on a thread-block cluster (k_vcycle_tail_cluster) where the device has
+    // clusters, else those from the first one with at most TAIL_MAX_N rows in one block
+    // (k_vcycle_tail)
+    const bool on_cluster = lv[0].tail_form == 0 && L >= 1 && ctail_available<T>();
+    const int l0 = on_cluster ? ctail_start(lv) : tail_start(lv);
     std::vector<T*> xcur(L + 1), xtmp(L + 1);
     for (int l = 0; l < std::min(L, l0); ++l) {
         const VLevel<T>& v = lv[l];
@@ -593,9 +1017,14 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         xcur[l] = x;
         xtmp[l] = t;
     }
-    if (l0 <= L) {
+    if (l0 <= L && on_cluster) {
+        const CTailArgs<T> a = make_ctail_args(lv, l0, pinv, nu_pre, nu_post, omega, (size_t)(TAIL_SMEM - CTAIL_STATIC));
+        BAMG_LAUNCH_PDL(k_vcycle_tail_cluster<T>, CTAIL_CS, CTAIL_THREADS, TAIL_SMEM - CTAIL_STATIC, s, a);
+        xcur[l0] = final_x(lv[l0], nu_pre, nu_post, l0 == L);
+    } else if (l0 <= L) {
         size_t smem = 0;
-        const TailArgs<T> a = make_tail_args(lv, l0, pinv, nu_pre, nu_post, omega, (size_t)TAIL_SMEM, &smem);
+        const TailArgs<T> a =
+            make_tail_args(lv, l0, pinv, nu_pre, nu_post, omega, (size_t)(TAIL_SMEM - TAIL_STATIC), &smem);
         // the attribute is per device: set once on each device (idempotent; several host
         // threads may get here)
         static std::atomic<bool> attr[256] = {};
@@ -603,7 +1032,8 @@ void vcycle(const std::vector<VLevel<T>>& lv, const T* pinv, double omega_d, int
         BAMG_CK(cudaGetDevice(&dev));
         BAMG_REQUIRE(dev >= 0 && dev < 256, BAMG_EINVAL, "device ordinal out of range");
         if (!attr[dev]) {
-            BAMG_CK(cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM));
+            BAMG_CK(cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TAIL_SMEM - TAIL_STATIC));
             attr[dev] = true;
         }
         BAMG_LAUNCH_PDL(k_vcycle_tail<T>, 1, TAIL_THREADS, smem, s, a);

@@ -172,6 +172,10 @@ struct VLevel {  // one level of the V-cycle
     const int32_t* gs_rows = nullptr;
     const int* gs_ptr = nullptr;
     int gs_ncol = 0;
+    // read on lv[0] only: the form of the coarse end of the V-cycle, 0 = the levels from the
+    // first one with at most 4096 rows on a thread-block cluster (where the device has
+    // clusters), 1 = the levels from the first one with at most 1024 rows in one block
+    int tail_form = 0;
 };
 // One V-cycle: lv[0].b -> lv[0].x.  With Z != null the result is also stored at
 // Z + (*dj) * n_0.

@@ -286,6 +286,7 @@ struct Solver : SolverBase {
         }
         v[0].b = const_cast<T*>(b0);
         v[0].x = x0v;
+        v[0].tail_form = o.coarse_tail;
         return v;
     }
 
@@ -1335,6 +1336,7 @@ int bamg_default_opts(bamg_opts* o) {
     o->mu = 1;
     o->smoother = BAMG_SMOOTH_JACOBI;
     o->persistent = 0;
+    o->coarse_tail = 0;
     return BAMG_OK;
 }
 
@@ -1356,6 +1358,7 @@ static void check_opts(const bamg_opts& o) {
     BAMG_REQUIRE(o.mu == 1 || o.mu == 2, BAMG_EINVAL, "mu must be 1 (V-cycle setup) or 2 (W-cycle setup)");
     BAMG_REQUIRE(o.setup_cycles >= 1 && o.setup_cycles <= 64, BAMG_EINVAL, "setup_cycles must be 1..64");
     BAMG_REQUIRE(o.smoother == BAMG_SMOOTH_JACOBI || o.smoother == BAMG_SMOOTH_MCGS, BAMG_EINVAL, "bad smoother");
+    BAMG_REQUIRE(o.coarse_tail == 0 || o.coarse_tail == 1, BAMG_EINVAL, "coarse_tail must be 0 or 1");
 }
 
 static void check_setup_args(const bamg_csr* A, int r, int levels, const bamg_opts& o) {

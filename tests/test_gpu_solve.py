@@ -287,6 +287,36 @@ def test_persistent_cycle_gives_the_same_iterates(kind, m, precision):
         assert (l2 - l1) < (l1 - l0), (l1 - l0, l2 - l1)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("kind", ["tandem127", "grid97", "bd3000", "tandem383"])
+def test_cluster_tail_gives_the_same_iterates(kind, precision):
+    """The coarse end of the V-cycle on a cluster of 8 thread blocks (coarse_tail=0: every
+    level from the first one with at most 4096 rows in one launch; each block owns a slice
+    of every level's rows and sends its values to the others through distributed shared
+    memory) and in one block (coarse_tail=1: from the first level with at most 1024 rows,
+    the levels above on the grid kernels) give bit-identical iterates and V-cycle outputs:
+    one thread per row in the grid kernels' order of operations, on these short-row
+    hierarchies.  The grid walk's levels (2401, 625, 169, 49 states) and the birth-death
+    chain's split unevenly over the blocks; the 384 x 384 tandem queue (147,456 states)
+    has two grid levels above the cluster."""
+    torch = _torch()
+    if kind == "tandem127":
+        ch, kw = tandem_queue(127), {}
+    elif kind == "tandem383":
+        ch, kw = tandem_queue(383), {}
+    elif kind == "grid97":
+        ch, kw = grid_walk(97), {}
+    else:
+        ch, kw = random_birth_death(3000, 9), dict(ridge=1e-10)
+    s1, x1, st1 = _run(ch, 8, 20, 1e-12, precision, coarse_tail=1, **kw)
+    s0, x0, st0 = _run(ch, 8, 20, 1e-12, precision, coarse_tail=0, **kw)
+    assert np.array_equal(x0, x1)
+    for k in ("iterations", "restarts", "true_checks", "residual_l1"):
+        assert st0[k] == st1[k], k
+    v = torch.tensor(np.random.default_rng(3).standard_normal(ch.n), device="cuda")
+    assert torch.equal(s0.vcycle(v), s1.vcycle(v))
+
+
 def test_device_loop_stops_at_max_it():
     bamg = _bamg()
     ch = grid_walk(40)
