@@ -208,9 +208,11 @@ def adam_step(p: dict, g: dict, st: dict, lr: float, b1: float = 0.9, b2: float 
         p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
 
 
-def train(p: dict, feats: np.ndarray, targets: np.ndarray, epochs: int, batch: int, lr: float, use_bf16=True):
+def train(p: dict, feats: np.ndarray, targets: np.ndarray, epochs: int, batch: int, lr: float, use_bf16=True,
+          bf16_grads: bool = False):
     """Adam over contiguous batches of the rows in their given order; returns the mean
-    loss of each epoch."""
+    loss of each epoch.  bf16_grads: the backward's product inputs rounded as in
+    backward()."""
     st = adam_init(p)
     hist = []
     mask = slot_mask(feats)
@@ -221,7 +223,7 @@ def train(p: dict, feats: np.ndarray, targets: np.ndarray, epochs: int, batch: i
             y, cache = forward(p, f, use_bf16)
             tot += loss(y, t, mk)
             nb += 1
-            adam_step(p, backward(p, cache, y, t, mk), st, lr)
+            adam_step(p, backward(p, cache, y, t, mk, bf16_grads), st, lr)
         hist.append(tot / max(nb, 1))
     return hist
 

@@ -7,8 +7,9 @@
 //
 // Forward products run on the tensor cores (mma.sync m16n8k16, bf16 in, FP32 accumulate):
 // one warp computes 16 rows x N outputs, the weights staged once per block in shared
-// memory with a padded row stride.  The training backward products (weight gradients
-// summed over the batch, input gradients) are small FP32-accumulating SIMT tiles.
+// memory with a padded row stride.  The training backward's products (input gradients
+// through the ReLU masks, weight gradients summed over the batch) use the same instruction
+// with the incoming gradient rounded to bf16; bias gradients and Adam stay in FP32.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(FWD_WARPS * 32)
     }
 }
 
-// ------------------------------------------------------------------ backward (SIMT)
+// ------------------------------------------------------------------ backward
 // dY = (2 / rows_in_batch) mask (Y - T), mask = the features' slot-valid flags; the batch
 // loss sum mask (Y - T)^2 / rows_in_batch is added to *loss.
 __global__ void k_mlp_loss(int64_t M, int64_t Mtot, const float* __restrict__ Y, const float* __restrict__ Tg,
@@ -180,86 +181,143 @@ __global__ void k_mlp_loss(int64_t M, int64_t Mtot, const float* __restrict__ Y,
     if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l);
 }
 
-// G[n][k] += sum_m D[m][n] X[m][k] (D: M x N FP32, X: M x K bf16 or FP32 rounded to bf16)
-// for rows [blockIdx.z * 128, +128); 32 x 32 output tile per block, 2 x 2 per thread.
-template <typename TX>
-__global__ void __launch_bounds__(256) k_gemm_tn(int64_t M, int N, int K, const float* __restrict__ D,
-                                                 const TX* __restrict__ X, float* __restrict__ G) {
+// The backward products on the tensor cores as well (mma.sync m16n8k16, bf16 in, FP32
+// accumulate): the gradient entering a product is rounded to bf16 like the forward's inputs;
+// the bias gradients are FP32 sums of the unrounded gradients (k_colsum).
+
+// Dout[m][n] = (sum_k bf16(Din[m][k]) W[k][n]) * (H[m][n] > 0): the gradient at a layer's
+// input (W: K x N bf16, the layer's out x in weights) through the ReLU of the layer below
+// (H: that layer's bf16 output).  As the forward tile: 4 warps x 16 rows per block, W^T
+// staged once per block with a padded stride.  K a multiple of 16, N of 8.
+template <int N, int K>
+__global__ void __launch_bounds__(FWD_WARPS * 32)
+    k_mlp_dgrad(int64_t M, const float* __restrict__ Din, const __nv_bfloat16* __restrict__ W,
+                const __nv_bfloat16* __restrict__ Hm, float* __restrict__ Dout) {
     pdl_begin();
-    __shared__ float sD[32][33], sX[32][33];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int n0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
-    const int64_t m_begin = (int64_t)blockIdx.z * 128, m_end = min(M, m_begin + 128);
-    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-    for (int64_t m0 = m_begin; m0 < m_end; m0 += 32) {
-        for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
-            const int mm = idx >> 5, cc = idx & 31;
-            const int64_t m = m0 + mm;
-            sD[mm][cc] = (m < m_end && n0 + cc < N) ? D[m * N + n0 + cc] : 0.f;
-            float xv = 0.f;
-            if (m < m_end && k0 + cc < K) {
-                if constexpr (sizeof(TX) == 2)
-                    xv = __bfloat162float(X[m * K + k0 + cc]);
-                else
-                    xv = __bfloat162float(__float2bfloat16_rn(X[m * K + k0 + cc]));
-            }
-            sX[mm][cc] = xv;
+    constexpr int LDW = K + 8;
+    __shared__ __align__(16) __nv_bfloat16 sWT[N * LDW];  // sWT[n][k] = W[k][n]
+    for (int idx = threadIdx.x; idx < N * K; idx += blockDim.x) {
+        const int k = idx / N, n = idx - k * N;
+        sWT[n * LDW + k] = W[(int64_t)k * N + n];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t r0 = ((int64_t)blockIdx.x * FWD_WARPS + warp) * 16;
+    if (r0 >= M) return;
+    const int64_t ra = r0 + g, rb = r0 + g + 8;
+    const bool va = ra < M, vb = rb < M;
+    float acc[N / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < N / 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < K; kk += 16) {
+        const uint32_t a0 = va ? load_pair<float>(Din + ra * K + kk + 2 * t) : 0u;
+        const uint32_t a1 = vb ? load_pair<float>(Din + rb * K + kk + 2 * t) : 0u;
+        const uint32_t a2 = va ? load_pair<float>(Din + ra * K + kk + 2 * t + 8) : 0u;
+        const uint32_t a3 = vb ? load_pair<float>(Din + rb * K + kk + 2 * t + 8) : 0u;
+#pragma unroll
+        for (int nt = 0; nt < N / 8; ++nt) {
+            const __nv_bfloat16* wr = sWT + (nt * 8 + g) * LDW + kk + 2 * t;
+            mma_bf16(acc[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t*>(wr),
+                     *reinterpret_cast<const uint32_t*>(wr + 8));
         }
-        __syncthreads();
-#pragma unroll 8
-        for (int mm = 0; mm < 32; ++mm) {
-            const float d0 = sD[mm][ty], d1 = sD[mm][ty + 16];
-            const float x0 = sX[mm][tx], x1 = sX[mm][tx + 16];
-            acc[0][0] += d0 * x0, acc[0][1] += d0 * x1, acc[1][0] += d1 * x0, acc[1][1] += d1 * x1;
-        }
-        __syncthreads();
     }
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int n = n0 + ty + 16 * a, k = k0 + tx + 16 * b;
-            if (n < N && k < K) atomicAdd(&G[(int64_t)n * K + k], acc[a][b]);
+    for (int nt = 0; nt < N / 8; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        if (va) {
+            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(Hm + ra * N + c);
+            *reinterpret_cast<float2*>(Dout + ra * N + c) =
+                make_float2(__low2float(h) > 0.f ? acc[nt][0] : 0.f, __high2float(h) > 0.f ? acc[nt][1] : 0.f);
         }
+        if (vb) {
+            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(Hm + rb * N + c);
+            *reinterpret_cast<float2*>(Dout + rb * N + c) =
+                make_float2(__low2float(h) > 0.f ? acc[nt][2] : 0.f, __high2float(h) > 0.f ? acc[nt][3] : 0.f);
+        }
+    }
 }
 
-// O[m][k] = (sum_n D[m][n] W[n][k]) * (H[m][k] > 0): D FP32 M x N, W bf16 N x K, H bf16.
-__global__ void __launch_bounds__(256) k_gemm_nn_relu(int64_t M, int N, int K, const float* __restrict__ D,
-                                                      const __nv_bfloat16* __restrict__ W,
-                                                      const __nv_bfloat16* __restrict__ Hm, float* __restrict__ O) {
+// G[n][k] += sum_m bf16(D[m][n]) X[m][k]: a layer's weight gradient from the gradient at its
+// output (D: M x N FP32) and its input (X: M x K, bf16 activations or the FP32 features,
+// rounded to bf16).  Block (x, y): rows [x WG_ROWS, +WG_ROWS) and the output rows
+// n in [16 y, 16 y + 16).  Rows in chunks of WG_MC; both operands staged transposed in shared
+// memory (row index m contiguous, so each fragment register is one aligned pair), padded
+// so that the fragment loads are free of bank conflicts; the 16 x 8 output tiles of the slab
+// spread over the warps; the block's partial sums go to G with atomics.
+constexpr int WG_MC = 64, WG_WARPS = 4, WG_ROWS = 256;
+template <typename TX, int N, int K>
+__global__ void __launch_bounds__(WG_WARPS * 32)
+    k_mlp_wgrad(int64_t M, const float* __restrict__ D, const TX* __restrict__ X, float* __restrict__ G) {
     pdl_begin();
-    __shared__ float sD[32][33], sW[32][33];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t m0 = (int64_t)blockIdx.y * 32;
-    const int k0 = blockIdx.x * 32;
-    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-    for (int n0 = 0; n0 < N; n0 += 32) {
-        for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
-            const int a = idx >> 5, b = idx & 31;
-            const int64_t m = m0 + a;
-            sD[a][b] = (m < M && n0 + b < N) ? D[m * N + n0 + b] : 0.f;
-            sW[a][b] = (n0 + a < N && k0 + b < K) ? __bfloat162float(W[(int64_t)(n0 + a) * K + k0 + b]) : 0.f;
+    static_assert(N % 16 == 0 && K % 8 == 0, "tile sizes");
+    constexpr int LDM = WG_MC + 8;                                  // padded row stride (bf16 elements)
+    constexpr int TK = K / 8, TPW = (TK + WG_WARPS - 1) / WG_WARPS;  // output tiles per warp
+    __shared__ __align__(16) __nv_bfloat16 sDT[16 * LDM];           // sDT[n - n0][m - m0]
+    __shared__ __align__(16) __nv_bfloat16 sXT[K * LDM];            // sXT[k][m - m0]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int n0 = blockIdx.y * 16;
+    const int64_t m_begin = (int64_t)blockIdx.x * WG_ROWS;
+    const int64_t m_end = m_begin + WG_ROWS < M ? m_begin + WG_ROWS : M;
+    float acc[TPW][4];
+#pragma unroll
+    for (int q = 0; q < TPW; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
+    for (int64_t m0 = m_begin; m0 < m_end; m0 += WG_MC) {
+        // rows m0 + 2i, m0 + 2i + 1 of D (slab columns) and X, as bf16 pairs along m
+        for (int idx = threadIdx.x; idx < (WG_MC / 2) * 16; idx += blockDim.x) {
+            const int i = idx >> 4, n = idx & 15;
+            const int64_t m = m0 + 2 * i;
+            const float d0 = m < m_end ? D[m * N + n0 + n] : 0.f;
+            const float d1 = m + 1 < m_end ? D[(m + 1) * N + n0 + n] : 0.f;
+            *reinterpret_cast<uint32_t*>(&sDT[n * LDM + 2 * i]) = pack_bf16(d0, d1);
+        }
+        for (int idx = threadIdx.x; idx < (WG_MC / 2) * K; idx += blockDim.x) {
+            const int i = idx / K, k = idx - i * K;
+            const int64_t m = m0 + 2 * i;
+            float x0 = 0.f, x1 = 0.f;
+            if constexpr (sizeof(TX) == 2) {
+                if (m < m_end) x0 = __bfloat162float(X[m * K + k]);
+                if (m + 1 < m_end) x1 = __bfloat162float(X[(m + 1) * K + k]);
+            } else {
+                if (m < m_end) x0 = X[m * K + k];
+                if (m + 1 < m_end) x1 = X[(m + 1) * K + k];
+            }
+            *reinterpret_cast<uint32_t*>(&sXT[k * LDM + 2 * i]) = pack_bf16(x0, x1);
         }
         __syncthreads();
-#pragma unroll 8
-        for (int nn = 0; nn < 32; ++nn) {
-            const float d0 = sD[ty][nn], d1 = sD[ty + 16][nn];
-            const float w0 = sW[nn][tx], w1 = sW[nn][tx + 16];
-            acc[0][0] += d0 * w0, acc[0][1] += d0 * w1, acc[1][0] += d1 * w0, acc[1][1] += d1 * w1;
+#pragma unroll
+        for (int q = 0; q < TPW; ++q) {
+            const int tk = warp + q * WG_WARPS;
+            if (tk < TK) {
+#pragma unroll
+                for (int kk = 0; kk < WG_MC; kk += 16) {
+                    const __nv_bfloat16* ar = sDT + g * LDM + kk + 2 * t;
+                    const __nv_bfloat16* br = sXT + (tk * 8 + g) * LDM + kk + 2 * t;
+                    mma_bf16(acc[q], *reinterpret_cast<const uint32_t*>(ar),
+                             *reinterpret_cast<const uint32_t*>(ar + 8 * LDM), *reinterpret_cast<const uint32_t*>(ar + 8),
+                             *reinterpret_cast<const uint32_t*>(ar + 8 * LDM + 8), *reinterpret_cast<const uint32_t*>(br),
+                             *reinterpret_cast<const uint32_t*>(br + 8));
+                }
+            }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int64_t m = m0 + ty + 16 * a;
-            const int k = k0 + tx + 16 * b;
-            if (m < M && k < K) {
-                const float h = __bfloat162float(Hm[m * K + k]);
-                O[m * K + k] = h > 0.f ? acc[a][b] : 0.f;
-            }
+    for (int q = 0; q < TPW; ++q) {
+        const int tk = warp + q * WG_WARPS;
+        if (tk < TK) {
+            const int k = tk * 8 + 2 * t;
+            float* gr = G + (int64_t)(n0 + g) * K + k;
+            atomicAdd(gr, acc[q][0]);
+            atomicAdd(gr + 1, acc[q][1]);
+            atomicAdd(gr + 8 * K, acc[q][2]);
+            atomicAdd(gr + 8 * K + 1, acc[q][3]);
         }
+    }
 }
 
 // g[n] += sum_m D[m][n]
@@ -378,22 +436,22 @@ static void gradients(Model* m, int64_t rows, const float* feat, const float* ta
     BAMG_CK(cudaMemsetAsync(G, 0, sizeof(float) * NPARAM, s));
     BAMG_LAUNCH(k_mlp_loss, blocks_for(rows * MLP_S, 256), 256, 0, s, rows, rows, w.Y.get(), target, feat, w.dY.get(),
                 w.loss.get());
-    const unsigned zb = (unsigned)((rows + 127) / 128);
+    const unsigned zb = (unsigned)((rows + WG_ROWS - 1) / WG_ROWS), gd = blocks_for(rows, FWD_WARPS * 16);
     // layer 3
-    BAMG_LAUNCH(k_gemm_tn<__nv_bfloat16>, dim3(MLP_H / 32, 1, zb), 256, 0, s, rows, MLP_S, MLP_H,
+    BAMG_LAUNCH((k_mlp_wgrad<__nv_bfloat16, MLP_S, MLP_H>), dim3(zb, MLP_S / 16), WG_WARPS * 32, 0, s, rows,
                 (const float*)w.dY.get(), (const __nv_bfloat16*)w.H2.get(), G + OFF_W3);
     BAMG_LAUNCH(k_colsum, MLP_S, 256, 0, s, rows, MLP_S, (const float*)w.dY.get(), G + OFF_B3);
-    BAMG_LAUNCH(k_gemm_nn_relu, dim3(MLP_H / 32, blocks_for(rows, 32)), 256, 0, s, rows, MLP_S, MLP_H,
-                (const float*)w.dY.get(), Wb + BOFF_W3, (const __nv_bfloat16*)w.H2.get(), w.D2.get());
+    BAMG_LAUNCH((k_mlp_dgrad<MLP_H, MLP_S>), gd, FWD_WARPS * 32, 0, s, rows, (const float*)w.dY.get(),
+                Wb + BOFF_W3, (const __nv_bfloat16*)w.H2.get(), w.D2.get());
     // layer 2
-    BAMG_LAUNCH(k_gemm_tn<__nv_bfloat16>, dim3(MLP_H / 32, MLP_H / 32, zb), 256, 0, s, rows, MLP_H, MLP_H,
+    BAMG_LAUNCH((k_mlp_wgrad<__nv_bfloat16, MLP_H, MLP_H>), dim3(zb, MLP_H / 16), WG_WARPS * 32, 0, s, rows,
                 (const float*)w.D2.get(), (const __nv_bfloat16*)w.H1.get(), G + OFF_W2);
     BAMG_LAUNCH(k_colsum, MLP_H, 256, 0, s, rows, MLP_H, (const float*)w.D2.get(), G + OFF_B2);
-    BAMG_LAUNCH(k_gemm_nn_relu, dim3(MLP_H / 32, blocks_for(rows, 32)), 256, 0, s, rows, MLP_H, MLP_H,
-                (const float*)w.D2.get(), Wb + BOFF_W2, (const __nv_bfloat16*)w.H1.get(), w.D1.get());
+    BAMG_LAUNCH((k_mlp_dgrad<MLP_H, MLP_H>), gd, FWD_WARPS * 32, 0, s, rows, (const float*)w.D2.get(),
+                Wb + BOFF_W2, (const __nv_bfloat16*)w.H1.get(), w.D1.get());
     // layer 1
-    BAMG_LAUNCH(k_gemm_tn<float>, dim3(MLP_F / 32 + (MLP_F % 32 ? 1 : 0), MLP_H / 32, zb), 256, 0, s, rows, MLP_H,
-                MLP_F, (const float*)w.D1.get(), feat, G + OFF_W1);
+    BAMG_LAUNCH((k_mlp_wgrad<float, MLP_H, MLP_F>), dim3(zb, MLP_H / 16), WG_WARPS * 32, 0, s, rows,
+                (const float*)w.D1.get(), feat, G + OFF_W1);
     BAMG_LAUNCH(k_colsum, MLP_H, 256, 0, s, rows, MLP_H, (const float*)w.D1.get(), G + OFF_B1);
 }
 
