@@ -36,7 +36,7 @@ def birth_death(birth: np.ndarray, death: np.ndarray) -> np.ndarray:
 def birth_death_ambiguity(birth: np.ndarray, death: np.ndarray, tol: float):
     """How far the residual test ||B x||_1 / ||x||_1 <= tol pins a birth-death chain's x.
 
-    For x* (1^T x* = 1) and an edge m -> m+1 let M_L = sum_{k<=m} x*_k, M_R = 1 - M_L and
+    For x* (1^T x* = 1) and an edge m -> m+1 let M_L = sum_{k<=m} x*_k, M_R = sum_{k>m} x*_k and
     dx = x* * (M_R [k <= m] - M_L [k > m]), the move of mass across the edge.  Then
     1^T dx = 0, ||dx||_1 = 2 M_L M_R, and by detailed balance (b_m x*_m = d_{m+1} x*_{m+1})
     B dx is nonzero only at m and m+1, with ||B dx||_1 = 2 b_m x*_m.  Hence
@@ -53,12 +53,10 @@ def birth_death_ambiguity(birth: np.ndarray, death: np.ndarray, tol: float):
     logx = np.zeros(n)
     logx[1:] = np.cumsum(np.log(birth[:-1]) - np.log(death[1:]))
     logx -= logx.max()
-    logx -= np.log(np.exp(logx).sum())
-    ML = np.cumsum(np.exp(logx))[:-1]
-    MR = np.maximum(1.0 - ML, 0.0)
-    ok = (ML > 0) & (MR > 0)
-    mass = np.log(ML[ok]) + np.log(MR[ok])
-    flux = np.log(birth[:-1][ok]) + logx[:-1][ok]  # log(b_m x*_m)
+    logx -= np.logaddexp.reduce(logx)
+    # both masses accumulated from their own end (1 - M_L cancels where M_R is tiny)
+    mass = np.logaddexp.accumulate(logx)[:-1] + np.logaddexp.accumulate(logx[::-1])[::-1][1:]
+    flux = np.log(birth[:-1]) + logx[:-1]  # log(b_m x*_m)
     log_kappa = float((mass - flux).max()) / np.log(10.0)
     eps = float((2.0 * np.exp(mass + np.minimum(0.0, np.log(tol) - np.log(2.0) - flux))).max())
     return log_kappa, eps
@@ -74,8 +72,11 @@ def birth_death_condition(birth: np.ndarray, death: np.ndarray) -> float:
     absolute deviation of u (weights x*) about its mean is at most twice that about the
     value at the weighted median m, so
       ||x - x*||_1 <= ||B x||_1 sum_i w_i (M_L(i) for i < m, M_R(i) for i >= m),
-    M_L(i) = sum_{k<=i} x*_k, M_R = 1 - M_L: K bounds max ||B^# r||_1 / ||r||_1 over the
-    residuals with 1^T r = 0 (every B x has that).  Evaluated in log space."""
+    M_L(i) = sum_{k<=i} x*_k, M_R(i) = sum_{k>i} x*_k: K bounds max ||B^# r||_1 / ||r||_1
+    over the residuals with 1^T r = 0 (every B x has that).  Evaluated in log space, both
+    masses accumulated from their own end: where log x* has a deep valley followed by a
+    smaller bump (random rates make log x* a random walk), M_R past the valley is far
+    below the rounding of 1 - M_L while w there is huge, and those terms dominate K."""
     birth = np.asarray(birth, dtype=np.float64)
     death = np.asarray(death, dtype=np.float64)
     n = len(birth)
@@ -84,12 +85,12 @@ def birth_death_condition(birth: np.ndarray, death: np.ndarray) -> float:
     logx = np.zeros(n)
     logx[1:] = np.cumsum(np.log(birth[:-1]) - np.log(death[1:]))
     logx -= logx.max()
-    logx -= np.log(np.exp(logx).sum())
-    ML = np.cumsum(np.exp(logx))[:-1]
-    m = int(np.searchsorted(ML, 0.5))
-    side = np.where(np.arange(n - 1) < m, ML, 1.0 - ML)
-    ok = side > 0
-    terms = np.log(side[ok]) - np.log(birth[:-1][ok]) - logx[:-1][ok]
+    logx -= np.logaddexp.reduce(logx)
+    logML = np.logaddexp.accumulate(logx)[:-1]  # log M_L(i), i < n - 1
+    logMR = np.logaddexp.accumulate(logx[::-1])[::-1][1:]  # log M_R(i) = log sum_{k>i} x*_k
+    m = int(np.searchsorted(np.exp(logML), 0.5))
+    side = np.where(np.arange(n - 1) < m, logML, logMR)
+    terms = side - np.log(birth[:-1]) - logx[:-1]
     top = terms.max()
     return float((top + np.log(np.exp(terms - top).sum())) / np.log(10.0))
 

@@ -95,6 +95,58 @@ def test_birth_death_condition_bounds_the_group_inverse_from_above():
         assert 10 ** lk <= K
 
 
+def _valley_chain():
+    """60 states: x* falls by 9x per step for 30 steps (a valley about 1e-29 deep), rises by
+    9x for 11 steps (a bump about 1e-18 high), then stays flat: the mass past the valley,
+    about 1e-17, is below the rounding of 1 - M_L, while 1 / (b x*) at the valley is about
+    1e29."""
+    n = 60
+    birth, death = np.full(n, 0.3), np.full(n, 0.3)
+    for k in range(n - 1):  # edge k -> k + 1: x*_{k+1} / x*_k = birth[k] / death[k + 1]
+        if k < 30:
+            birth[k], death[k + 1] = 0.05, 0.45
+        elif k < 41:
+            birth[k], death[k + 1] = 0.45, 0.05
+    return birth_death(birth, death)
+
+
+def _worst_pair_error(b, d):
+    """max ||e||_1 over the residuals (e_j - e_k) / 2 (the extreme points of the unit l1 ball
+    with 1^T r = 0), e solving B e = r, 1^T e = 0, by the flux recursion of detailed balance:
+    the residual's partial sums R_i = +-1/2 between j and k give u_{i+1} = u_i - R_i / (b_i x*_i)
+    with e = x* u, and 1^T e = 0 fixes the constant."""
+    x = exact.birth_death(b, d)
+    n = len(x)
+    w = 1.0 / (b[:-1] * x[:-1])
+    best = 0.0
+    for j in range(n):
+        for k in range(j + 1, n):
+            R = np.zeros(n - 1)
+            R[j:k] = 0.5
+            u = np.concatenate([[0.0], -np.cumsum(w * R)])
+            u -= (x * u).sum()
+            best = max(best, float(np.abs(x * u).sum()))
+    return best
+
+
+def test_birth_death_condition_counts_the_mass_past_a_deep_valley():
+    """On a chain whose x* has a deep valley followed by a small bump, K still bounds the
+    worst error per residual from above and stays within 10x of it.  Fails if M_R is taken
+    as 1 - M_L, which rounds to 0 past the valley and drops the dominant terms (K then comes
+    out near 40 against a worst case near 3e12); kappa_lb stays a lower bound."""
+    ch = _valley_chain()
+    b, d = ch.meta["birth"], ch.meta["death"]
+    x = exact.birth_death(b, d)
+    assert x[30] < 1e-28 and 1e-19 < x[-1] < 1e-17 and x[41:].sum() < 1e-16
+    worst = _worst_pair_error(b, d)
+    K = 10 ** exact.birth_death_condition(b, d)
+    assert worst <= K * (1 + 1e-9), (worst, K)
+    assert K <= 10 * worst, (worst, K)
+    lk, _ = exact.birth_death_ambiguity(b, d, 1e-10)
+    assert 10 ** lk <= worst * (1 + 1e-9)
+    assert 10 ** lk >= 1e-3 * worst
+
+
 def test_birth_death_condition_uniform_closed_form():
     """Equal rates b: x* = 1/n, w_i = n/b, M_L(i) = (i+1)/n; the median m = n/2 - 1 for even
     n, K = (n/b) (sum_{i<m} (i+1)/n + sum_{i>=m} (n-1-i)/n)."""
