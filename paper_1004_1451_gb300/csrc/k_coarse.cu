@@ -7,9 +7,10 @@
 // small Hessenberg matrix (Golub & Van Loan, Matrix Computations, Sec. 7.5).
 // Eigenvectors, one block per selected eigenvalue: inverse iteration in complex
 // arithmetic on the pencil (B - sigma T) and a Rayleigh-type quotient, in FP64 (or in
-// FP32 for the mixed-precision setup).  B^+: a bordered FP64 LU solve, the right-hand
-// sides split over several blocks.  Factorisations use the whole block; triangular
-// solves run in single warps (registers and shuffles, no block barriers).
+// FP32 for the mixed-precision setup).  B^+: one LU of the bordered matrix B + z z^T
+// (z = 1/sqrt(n)), the right-hand sides split over several blocks.  Factorisations use the
+// whole block (rows in place, the pivot found by a warp reduction); triangular solves run
+// in single warps (shuffles, no block barriers).
 #include <cfloat>
 #include <cstdio>
 #include <cstdlib>
@@ -30,106 +31,205 @@ __device__ __forceinline__ F absv(F x) {
     return x < F(0) ? -x : x;
 }
 
-// ---------------------------------------------------------------- block-parallel real LU
-// In-place LU with partial pivoting of the n x n row-major A (shared, stride LDP);
-// perm[k] = pivot row of step k; pivots smaller than floorv in magnitude become
-// +-floorv.  On return the strict lower part holds L (unit diagonal), dinv[k] = 1 / u_kk,
-// and the strict upper part holds the rows of U scaled by dinv (a unit upper factor),
-// so that a solve needs no division.  Rank-one updates use a 16 x 16 thread grid.
+// ---------------------------------------------------------------- block LU, rows in place
+// Partial pivoting with the rows left where they are: step k takes as pivot the not yet
+// pivoted row of largest magnitude in column k and records it as src[k]; the other
+// unpivoted rows get their multiplier in column k and update their columns > k.  On return
+// row src[i] of A holds pivot row i: multipliers left of column i, the upper factor times
+// dinv[i] (= 1 / u_ii) right of it, so a solve reads equation i from row src[i] (and its
+// right-hand side entry b[src[i]]).  n <= 64, A in shared memory with row stride LDP = 65.
+//
+// Per step: warp 0 finds the pivot with one warp reduction over a 32-bit key (the
+// magnitude's float bits with the low 6 mantissa bits replaced by 63 - row: magnitudes
+// within 2^-17 count as equal and the lowest row wins; a NaN counts as infinite, so a valid
+// row is always taken and the NaN reaches the factors, where the callers' finiteness checks
+// see it); then all CT threads update, 4 per row, consecutive threads on consecutive rows
+// (a column's rows sit on distinct banks).  The multipliers of a step are parked in `mult`
+// and written to their column by warp 0 in the next step, when no thread reads that column.
+// Every thread of the block calls it (block barriers inside).
+__device__ __forceinline__ unsigned pivot_key(float mag, int row) {
+    const unsigned bits = mag == mag ? __float_as_uint(mag) : 0x7f800000u;
+    return (bits & ~63u) | (unsigned)(63 - row);
+}
+
+// Real A (F = float or double); pivots below floorv in magnitude become +-floorv.
 template <typename F>
-__device__ void blu_factor(F* A, int n, int* perm, F* dinv, F floorv) {
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+__device__ void block_lu_factor(F* A, int n, int* src, F* dinv, F floorv) {
+    __shared__ int step_of[CN];  // pivot step of each row, -1 while unpivoted
+    __shared__ F mult[CN];
+    const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+    const int r = tid & (CN - 1), q = tid >> 6;  // this thread's row and its column phase (CT = 4 CN)
+    if (tid < CN) step_of[tid] = tid < n ? -1 : CN;
+    __syncthreads();
     for (int k = 0; k < n; ++k) {
-        if (tid < 32) {  // pivot search; one thread forms the (floored) pivot's reciprocal
-            F best = F(-1);
-            int br = k;
-            for (int r = k + tid; r < n; r += 32) {
-                const F v = absv(A[r * LDP + k]);
-                if (v > best) {
-                    best = v;
-                    br = r;
-                }
+        if (wid == 0) {
+            const bool ua = step_of[lane] < 0, ub = step_of[lane + 32] < 0;
+            if (k > 0) {  // the previous step's multipliers into column k - 1
+                if (ua) A[lane * LDP + k - 1] = mult[lane];
+                if (ub) A[(lane + 32) * LDP + k - 1] = mult[lane + 32];
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const F ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-                if (ob > best || (ob == best && orr < br)) {
-                    best = ob;
-                    br = orr;
-                }
-            }
-            if (tid == 0) {
-                perm[k] = br;
-                F p = A[br * LDP + k];
-                if (absv(p) < floorv) p = p >= F(0) ? floorv : -floorv;
-                dinv[k] = F(1) / p;
-                A[br * LDP + k] = p;  // lands on the diagonal with the row swap
+            const unsigned ka = ua ? pivot_key((float)absv(A[lane * LDP + k]), lane) : 0u;
+            const unsigned kb = ub ? pivot_key((float)absv(A[(lane + 32) * LDP + k]), lane + 32) : 0u;
+            const unsigned best = __reduce_max_sync(0xffffffffu, ka > kb ? ka : kb);
+            if (lane == 0) {
+                const int pr = 63 - (int)(best & 63u);
+                F pv = A[pr * LDP + k];
+                if (absv(pv) < floorv) pv = pv >= F(0) ? floorv : -floorv;
+                A[pr * LDP + k] = pv;
+                src[k] = pr;
+                dinv[k] = F(1) / pv;
+                step_of[pr] = k;
             }
         }
         __syncthreads();
-        const int br = perm[k];
-        if (br != k) {
-            for (int c = tid; c < n; c += CT) {
-                const F t = A[k * LDP + c];
-                A[k * LDP + c] = A[br * LDP + c];
-                A[br * LDP + c] = t;
-            }
-            __syncthreads();
-        }
-        const F inv = dinv[k];
-        // rank-one update, a 4 x 4 register tile per thread (n <= 64)
-        F u[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = k + 1 + tx + 16 * j;
-            u[j] = c < n ? A[k * LDP + c] : F(0);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = k + 1 + ty + 16 * i;
-            if (r < n) {
-                const F l = A[r * LDP + k] * inv;
-                F a[4];
+        if (step_of[r] < 0) {
+            const F l = A[r * LDP + k] * dinv[k];
+            if (q == 0) mult[r] = l;
+            const F* prow = A + src[k] * LDP;
+            F* row = A + r * LDP;
+            int c = k + 1 + q;
+            for (; c + 12 < n; c += 16) {  // 4 columns at once, loads before stores
+                F pc[4], x[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int c = k + 1 + tx + 16 * j;
-                    a[j] = c < n ? A[r * LDP + c] : F(0);
+                    pc[j] = prow[c + 4 * j];
+                    x[j] = row[c + 4 * j];
                 }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = k + 1 + tx + 16 * j;
-                    if (c < n) A[r * LDP + c] = a[j] - l * u[j];
-                }
+                for (int j = 0; j < 4; ++j) row[c + 4 * j] = x[j] - l * pc[j];
             }
+            for (; c < n; c += 4) row[c] -= l * prow[c];
         }
         __syncthreads();
-        for (int r = k + 1 + tid; r < n; r += CT) A[r * LDP + k] *= inv;
+    }
+    // unit upper factor: the part of row src[i] right of column i times dinv[i]
+    const int sr = step_of[r];
+    if (sr < n) {
+        const F d = dinv[sr];
+        for (int c = sr + 1 + ((q - sr - 1) & 3); c < n; c += 4) A[r * LDP + c] *= d;
     }
     __syncthreads();
-    for (int r = ty; r < n; r += 16)
-        for (int c = r + 1 + tx; c < n; c += 16) A[r * LDP + c] *= dinv[r];
+}
+
+// 1 / (pr + i pi) without squaring (Smith's method: no overflow or underflow in FP32)
+template <typename F>
+__device__ __forceinline__ void cplx_recip(F pr, F pi, F& dr, F& di) {
+    if (absv(pr) >= absv(pi)) {
+        const F t = pi / pr, d = F(1) / (pr + pi * t);
+        dr = d;
+        di = -t * d;
+    } else {
+        const F t = pr / pi, d = F(1) / (pr * t + pi);
+        dr = t * d;
+        di = -d;
+    }
+}
+
+// Complex A = Ar + i Ai, pivoting on |Re| + |Im|; pivots below floorv become floorv; dr + i di
+// = 1 / u_ii.  Same layout and contract as block_lu_factor.
+template <typename F>
+__device__ void block_lu_factor_cplx(F* Ar, F* Ai, int n, int* src, F* dr, F* di, F floorv) {
+    __shared__ int step_of[CN];
+    __shared__ F mr[CN], mi[CN];
+    const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+    const int r = tid & (CN - 1), q = tid >> 6;
+    if (tid < CN) step_of[tid] = tid < n ? -1 : CN;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (wid == 0) {
+            const bool ua = step_of[lane] < 0, ub = step_of[lane + 32] < 0;
+            if (k > 0) {
+                if (ua) {
+                    Ar[lane * LDP + k - 1] = mr[lane];
+                    Ai[lane * LDP + k - 1] = mi[lane];
+                }
+                if (ub) {
+                    Ar[(lane + 32) * LDP + k - 1] = mr[lane + 32];
+                    Ai[(lane + 32) * LDP + k - 1] = mi[lane + 32];
+                }
+            }
+            const int ia = lane * LDP + k, ib = (lane + 32) * LDP + k;
+            const unsigned ka = ua ? pivot_key((float)(absv(Ar[ia]) + absv(Ai[ia])), lane) : 0u;
+            const unsigned kb = ub ? pivot_key((float)(absv(Ar[ib]) + absv(Ai[ib])), lane + 32) : 0u;
+            const unsigned best = __reduce_max_sync(0xffffffffu, ka > kb ? ka : kb);
+            if (lane == 0) {
+                const int pr = 63 - (int)(best & 63u);
+                F ppr = Ar[pr * LDP + k], ppi = Ai[pr * LDP + k];
+                if (absv(ppr) + absv(ppi) < floorv) {
+                    ppr = floorv;
+                    ppi = F(0);
+                }
+                Ar[pr * LDP + k] = ppr;
+                Ai[pr * LDP + k] = ppi;
+                F qr, qi;
+                cplx_recip(ppr, ppi, qr, qi);
+                src[k] = pr;
+                dr[k] = qr;
+                di[k] = qi;
+                step_of[pr] = k;
+            }
+        }
+        __syncthreads();
+        if (step_of[r] < 0) {
+            const F ar = Ar[r * LDP + k], ai = Ai[r * LDP + k], qr = dr[k], qi = di[k];
+            const F lr = ar * qr - ai * qi, li = ar * qi + ai * qr;
+            if (q == 0) {
+                mr[r] = lr;
+                mi[r] = li;
+            }
+            const F* pur = Ar + src[k] * LDP;
+            const F* pui = Ai + src[k] * LDP;
+            F* xr_ = Ar + r * LDP;
+            F* xi_ = Ai + r * LDP;
+            int c = k + 1 + q;
+            for (; c + 4 < n; c += 8) {  // 2 columns at once, loads before stores
+                const F ur0 = pur[c], ui0 = pui[c], ur1 = pur[c + 4], ui1 = pui[c + 4];
+                const F x0 = xr_[c], y0 = xi_[c], x1 = xr_[c + 4], y1 = xi_[c + 4];
+                xr_[c] = x0 - (lr * ur0 - li * ui0);
+                xi_[c] = y0 - (lr * ui0 + li * ur0);
+                xr_[c + 4] = x1 - (lr * ur1 - li * ui1);
+                xi_[c + 4] = y1 - (lr * ui1 + li * ur1);
+            }
+            for (; c < n; c += 4) {
+                const F ur = pur[c], ui = pui[c], x = xr_[c], y = xi_[c];
+                xr_[c] = x - (lr * ur - li * ui);
+                xi_[c] = y - (lr * ui + li * ur);
+            }
+        }
+        __syncthreads();
+    }
+    const int sr = step_of[r];
+    if (sr < n) {
+        const F qr = dr[sr], qi = di[sr];
+        for (int c = sr + 1 + ((q - sr - 1) & 3); c < n; c += 4) {
+            const F ur = Ar[r * LDP + c], ui = Ai[r * LDP + c];
+            Ar[r * LDP + c] = ur * qr - ui * qi;
+            Ai[r * LDP + c] = ur * qi + ui * qr;
+        }
+    }
     __syncthreads();
 }
 
 // One warp solves A X = R for the NC columns c0 .. c0 + NC - 1 (those < m) of the
-// row-major R (row stride ldr) at once: the independent columns hide the latency of the
-// shuffles.  Row interchanges, then forward and back substitution eliminating one column
-// of L (of U) at a time, as in the plain algorithm.
+// row-major R (row stride ldr) at once, with the factors of block_lu_factor (equation i in
+// row src[i] of A and of R): the independent columns hide the latency of the shuffles.
+// Forward and back substitution eliminate one column of L (of U) at a time, as in the
+// plain algorithm; lane l holds the unknowns l and l + 32.
 template <typename F, int NC>
 __device__ void warp_lu_solve_cols(const F* A, int n, const int* src, const F* dinv, F* R, int ldr, int c0, int m) {
     const int lane = lane_id();
+    const int r0 = lane < n ? src[lane] : 0, r1 = lane + 32 < n ? src[lane + 32] : 0;
     F x0[NC], x1[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         const bool cj = c0 + j < m;
-        x0[j] = lane < n && cj ? R[src[lane] * ldr + c0 + j] : F(0);
-        x1[j] = lane + 32 < n && cj ? R[src[lane + 32] * ldr + c0 + j] : F(0);
+        x0[j] = lane < n && cj ? R[r0 * ldr + c0 + j] : F(0);
+        x1[j] = lane + 32 < n && cj ? R[r1 * ldr + c0 + j] : F(0);
     }
     __syncwarp();
     for (int q = 0; q + 1 < n; ++q) {  // unit lower
         const bool a0 = lane > q && lane < n, a1 = lane + 32 > q && lane + 32 < n;
-        const F l0 = a0 ? A[lane * LDP + q] : F(0), l1 = a1 ? A[(lane + 32) * LDP + q] : F(0);
+        const F l0 = a0 ? A[r0 * LDP + q] : F(0), l1 = a1 ? A[r1 * LDP + q] : F(0);
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             const F y = __shfl_sync(0xffffffffu, q < 32 ? x0[j] : x1[j], q & 31);
@@ -145,7 +245,7 @@ __device__ void warp_lu_solve_cols(const F* A, int n, const int* src, const F* d
     }
     for (int q = n - 1; q > 0; --q) {  // unit upper
         const bool a0 = lane < q, a1 = lane + 32 < q;
-        const F u0 = a0 ? A[lane * LDP + q] : F(0), u1 = a1 ? A[(lane + 32) * LDP + q] : F(0);
+        const F u0 = a0 ? A[r0 * LDP + q] : F(0), u1 = a1 ? A[r1 * LDP + q] : F(0);
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             const F y = __shfl_sync(0xffffffffu, q < 32 ? x0[j] : x1[j], q & 31);
@@ -163,39 +263,11 @@ __device__ void warp_lu_solve_cols(const F* A, int n, const int* src, const F* d
     __syncwarp();
 }
 
-// One warp solves A x = b for one right-hand side b (stride ldb) with the factor of
-// blu_factor; src[i] is the row of b that the interchanges bring to row i
-// (lu_row_sources).  Lane l holds x_l and x_{l+32}; the eliminations run one column of
-// L (of U) at a time, as in the plain algorithm.  The warp's lanes must all call it.
-__device__ void lu_row_sources(int n, const int* perm, int* src) {  // one thread
-    for (int i = 0; i < n; ++i) src[i] = i;
-    for (int k = 0; k < n; ++k) {
-        const int pk = perm[k], t = src[k];
-        src[k] = src[pk];
-        src[pk] = t;
-    }
-}
+// One warp solves A x = b for one right-hand side b (stride ldb), in place, with the factors
+// of block_lu_factor.  The warp's lanes must all call it.
 template <typename F>
 __device__ void warp_lu_solve(const F* A, int n, const int* src, const F* dinv, F* b, int ldb) {
-    const int lane = lane_id();
-    F x0 = lane < n ? b[src[lane] * ldb] : F(0);
-    F x1 = lane + 32 < n ? b[src[lane + 32] * ldb] : F(0);
-    __syncwarp();
-    for (int q = 0; q + 1 < n; ++q) {  // unit lower
-        const F y = __shfl_sync(0xffffffffu, q < 32 ? x0 : x1, q & 31);
-        if (lane > q && lane < n) x0 = x0 - A[lane * LDP + q] * y;
-        if (lane + 32 > q && lane + 32 < n) x1 = x1 - A[(lane + 32) * LDP + q] * y;
-    }
-    if (lane < n) x0 *= dinv[lane];
-    if (lane + 32 < n) x1 *= dinv[lane + 32];
-    for (int q = n - 1; q > 0; --q) {  // unit upper
-        const F y = __shfl_sync(0xffffffffu, q < 32 ? x0 : x1, q & 31);
-        if (lane < q) x0 = x0 - A[lane * LDP + q] * y;
-        if (lane + 32 < q) x1 = x1 - A[(lane + 32) * LDP + q] * y;
-    }
-    if (lane < n) b[lane * ldb] = x0;
-    if (lane + 32 < n) b[(lane + 32) * ldb] = x1;
-    __syncwarp();
+    warp_lu_solve_cols<F, 1>(A, n, src, dinv, b, ldb, 0, 1);
 }
 
 // ---------------------------------------------------------------- FP32 Hessenberg + QR
@@ -333,9 +405,9 @@ __device__ int hqr_f32(float* H, int n, float* wr, float* wi, int* steps) {
 // Kernel 1: estimates of the eigenvalues of B x = lambda T x closest to zero, in FP32
 // (they serve only as shifts).  sigma = -1e-4 max|B|; K = (B - sigma T)^{-1} T is formed
 // explicitly (its dominant eigenvalues theta = 1 / (lambda - sigma) belong to the lambda
-// of smallest modulus); KRY Arnoldi steps on K with classical Gram-Schmidt applied twice
-// (whole block: 4 threads per row for K v, one warp per basis vector for the inner
-// products); the eigenvalues of the Hessenberg matrix by the Francis QR iteration (one
+// of smallest modulus); min(n, max(20, 2 k_ev + 6), KRY) Arnoldi steps on K with classical
+// Gram-Schmidt applied twice (whole block: 4 threads per row for K v, one warp per basis
+// vector for the inner products); the eigenvalues of the Hessenberg matrix by the Francis QR iteration (one
 // warp); lambda = sigma + 1 / theta.  Selection: eigenvalues with Im >= 0 (a complex pair
 // is represented by its member with positive imaginary part) in order of |lambda|; a real
 // one takes one vector column, a pair two (Re v, Im v), until k_ev columns are filled.
@@ -353,7 +425,6 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __re
     __shared__ float part[4 * CN];
     __shared__ float w[CN], hq[KRY + 1], hcol[KRY + 1], dinv[CN];
     __shared__ float wr[CN], wi[CN], red[CT / 32], s_nn;
-    __shared__ int perm[CN];
     const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
     const long long c_start = clock64();
     // sigma from the largest entry of B
@@ -373,16 +444,18 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __re
         A[r * LDP + c] = (float)Bg[idx] - sigma * t;
     }
     __syncthreads();
-    blu_factor<float>(A, n, perm, dinv, 1e-30f);
-    {  // Km = (B - sigma T)^{-1} T, one column at a time per warp
+    {  // Km = (B - sigma T)^{-1} T: the LU by the block, then several columns per warp
         __shared__ int src[CN];
-        if (tid == 0) lu_row_sources(n, perm, src);
+        block_lu_factor<float>(A, n, src, dinv, 1e-30f);
         __syncthreads();
         warp_lu_solve_cols<float, CN / (CT / 32)>(A, n, src, dinv, Km, LDP, wid * (CN / (CT / 32)), n);
         __syncthreads();
     }
     const long long c_lu = clock64();
-    const int kd = n < KRY ? n : KRY;
+    // Krylov dimension: the wanted eigenvalues are the dominant ones of K, so 2 k_ev + 6 steps
+    // (at least 20, at most KRY) give them to shift accuracy; the QR work grows with its square
+    const int kwant = 2 * k_ev + 6 > 20 ? 2 * k_ev + 6 : 20;
+    const int kd = min(n, min(KRY, kwant));
     if (tid < n) {  // v_0: fixed generic start
         Vk[tid] = 1.f + (float)tid / (float)n;
     }
@@ -541,9 +614,8 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
     F* Tm = Bm + CN * LDP;
     __shared__ F vr[CN], vi[CN], tr[CN], ti[CN], dr[CN], di[CN], pre[4 * CN], pim[4 * CN];
     __shared__ double red[4 * (CT / 32)];
-    __shared__ int perm[CN];
     const long long c_start = clock64();
-    const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5, ty = tid >> 4, tx = tid & 15;
+    const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
     const F sr = (F)sel[3 * blockIdx.x], si = (F)sel[3 * blockIdx.x + 1];
     const int col = (int)sel[3 * blockIdx.x + 2];
     for (int idx = tid; idx < n * n; idx += CT) {
@@ -576,108 +648,10 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
     for (int q = 0; q < CT / 32; ++q) amax = amax > pre[q] ? amax : pre[q];
     const F pfloor = (sizeof(F) == 8 ? F(1e-15) : F(1e-7)) * (amax > F(0) ? amax : F(1));
     __syncthreads();
-    // complex LU with partial pivoting on |Re| + |Im|; dr + i di = 1 / u_kk
-    for (int k = 0; k < n; ++k) {
-        if (tid < 32) {
-            F best = F(-1);
-            int br = k;
-            for (int r = k + tid; r < n; r += 32) {
-                const F m = absv(Ar[r * LDP + k]) + absv(Ai[r * LDP + k]);
-                if (m > best) {
-                    best = m;
-                    br = r;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const F ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-                if (ob > best || (ob == best && orr < br)) {
-                    best = ob;
-                    br = orr;
-                }
-            }
-            if (tid == 0) {  // the pivot's reciprocal, formed once
-                perm[k] = br;
-                F pr = Ar[br * LDP + k], pi = Ai[br * LDP + k];
-                if (absv(pr) + absv(pi) < pfloor) {
-                    pr = pfloor;
-                    pi = F(0);
-                    Ar[br * LDP + k] = pr;
-                    Ai[br * LDP + k] = pi;
-                }
-                // 1 / (pr + i pi) without squaring (Smith's method: no underflow in FP32)
-                if (absv(pr) >= absv(pi)) {
-                    const F t = pi / pr, d = F(1) / (pr + pi * t);
-                    dr[k] = d;
-                    di[k] = -t * d;
-                } else {
-                    const F t = pr / pi, d = F(1) / (pr * t + pi);
-                    dr[k] = t * d;
-                    di[k] = -d;
-                }
-            }
-        }
-        __syncthreads();
-        const int br = perm[k];
-        if (br != k) {
-            for (int c = tid; c < n; c += CT) {
-                F t = Ar[k * LDP + c];
-                Ar[k * LDP + c] = Ar[br * LDP + c];
-                Ar[br * LDP + c] = t;
-                t = Ai[k * LDP + c];
-                Ai[k * LDP + c] = Ai[br * LDP + c];
-                Ai[br * LDP + c] = t;
-            }
-            __syncthreads();
-        }
-        const F qr_ = dr[k], qi_ = di[k];  // 1 / pivot
-        F ur[4], ui[4];  // rank-one update, a 4 x 4 register tile per thread
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = k + 1 + tx + 16 * j;
-            ur[j] = c < n ? Ar[k * LDP + c] : F(0);
-            ui[j] = c < n ? Ai[k * LDP + c] : F(0);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = k + 1 + ty + 16 * i;
-            if (r < n) {
-                const F ar = Ar[r * LDP + k], ai = Ai[r * LDP + k];
-                const F lr = ar * qr_ - ai * qi_, li = ar * qi_ + ai * qr_;
-                F xr[4], xi[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = k + 1 + tx + 16 * j;
-                    xr[j] = c < n ? Ar[r * LDP + c] : F(0);
-                    xi[j] = c < n ? Ai[r * LDP + c] : F(0);
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = k + 1 + tx + 16 * j;
-                    if (c < n) {
-                        Ar[r * LDP + c] = xr[j] - (lr * ur[j] - li * ui[j]);
-                        Ai[r * LDP + c] = xi[j] - (lr * ui[j] + li * ur[j]);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        for (int r = k + 1 + tid; r < n; r += CT) {
-            const F ar = Ar[r * LDP + k], ai = Ai[r * LDP + k];
-            Ar[r * LDP + k] = ar * qr_ - ai * qi_;
-            Ai[r * LDP + k] = ar * qi_ + ai * qr_;
-        }
-    }
-    __syncthreads();
-    for (int r = ty; r < n; r += 16)  // rows of U times 1 / u_rr: a unit upper factor
-        for (int c = r + 1 + tx; c < n; c += 16) {
-            const F ur = Ar[r * LDP + c], ui = Ai[r * LDP + c];
-            Ar[r * LDP + c] = ur * dr[r] - ui * di[r];
-            Ai[r * LDP + c] = ur * di[r] + ui * dr[r];
-        }
+    // complex LU with partial pivoting on |Re| + |Im|, rows in place: row srcp[i] holds
+    // pivot row i, dr + i di = 1 / u_ii
     __shared__ int srcp[CN];
-    if (tid == 0) lu_row_sources(n, perm, srcp);
+    block_lu_factor_cplx<F>(Ar, Ai, n, srcp, dr, di, pfloor);
     // start vector in [1, 2) drawn per column (SplitMix64, stream = the column): for a
     // multiple eigenvalue (the symmetric pairs of grid walks) each column converges to
     // the projection of its own start onto the eigenspace, so the columns span it
@@ -716,9 +690,11 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
             }
             __syncwarp();
             F xr[2], xi[2];
+            int fr[2];  // the rows of A holding this lane's equations
 #pragma unroll
             for (int h = 0; h < 2; ++h) {  // row interchanges
                 const int r = lane + 32 * h;
+                fr[h] = r < n ? srcp[r] : 0;
                 xr[h] = r < n ? tr[srcp[r]] : F(0);
                 xi[h] = r < n ? ti[srcp[r]] : F(0);
             }
@@ -729,7 +705,7 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
                 for (int h = 0; h < 2; ++h) {
                     const int r = lane + 32 * h;
                     if (r > q && r < n) {
-                        const F lr = Ar[r * LDP + q], li = Ai[r * LDP + q];
+                        const F lr = Ar[fr[h] * LDP + q], li = Ai[fr[h] * LDP + q];
                         xr[h] -= lr * yr - li * yi;
                         xi[h] -= lr * yi + li * yr;
                     }
@@ -751,7 +727,7 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
                 for (int h = 0; h < 2; ++h) {
                     const int r = lane + 32 * h;
                     if (r < q) {
-                        const F ur = Ar[r * LDP + q], ui = Ai[r * LDP + q];
+                        const F ur = Ar[fr[h] * LDP + q], ui = Ai[fr[h] * LDP + q];
                         xr[h] -= ur * yr - ui * yi;
                         xi[h] -= ur * yi + ui * yr;
                     }
@@ -910,13 +886,13 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
 }
 
 // ---------------------------------------------------------------- minimal-norm inverse
-// B has rank n-1 with left null vector 1.  y = its right null vector (two steps of
-// inverse iteration on the LU of B with a pivot floor); with z = 1/sqrt(n) the bordered
-// matrix M = B + z y^T is nonsingular and B^+ = M^{-1} (I - z z^T): M w = (I - z z^T) b
-// forces y^T w = 0, so w is the solution of B w = (I - z z^T) b orthogonal to null(B).
-// Every block factors B and M (the factorisations are identical) and solves its own
-// PINV_COLS columns of (I - z z^T).  Arithmetic F: FP64, or FP32 for the mixed-precision
-// V-cycle, which applies B^+ in FP32.
+// B has rank n-1 and left null vector 1 (1^T B = 0).  With z = 1/sqrt(n), M = B + z z^T is
+// nonsingular, and one factorisation of M gives B^+: M y = z yields the right null vector
+// (z^T B = 0 forces z^T y = 1, hence B y = 0), and M w = (I - z z^T) b forces z^T w = 0,
+// hence B w = (I - z z^T) b; the minimal-norm solution is w minus its component along y, so
+// B^+ b = (I - y y^T / y^T y) M^{-1} (I - z z^T) b.  Every block factors M (identically) and
+// solves y and its own PINV_COLS columns, one per warp.  Arithmetic F: FP64,
+// or FP32 for the mixed-precision V-cycle, which applies B^+ in FP32.
 constexpr int PINV_COLS = 8;
 template <typename F>
 __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restrict__ Bg, double* __restrict__ Pg,
@@ -924,62 +900,42 @@ __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restr
     pdl_begin();
     __shared__ F A[CN * LDP];
     __shared__ F R[CN * PINV_COLS];
-    __shared__ F y[CN], dinv[CN], red[CT / 32];
-    __shared__ int perm[CN];
+    __shared__ F y[CN], dinv[CN];
+    __shared__ int src[CN];
     const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
     const long long c_start = clock64();
     const int c0 = blockIdx.x * PINV_COLS, mc = min(PINV_COLS, n - c0);
-    F mx = F(0);
+    const F ninv = (F)(1.0 / (double)n);
     for (int idx = tid; idx < n * n; idx += CT) {
         const int r = idx / n, c = idx - r * n;
-        const F b = (F)Bg[idx];
-        A[r * LDP + c] = b;
-        mx = mx > absv(b) ? mx : absv(b);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const F t = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = mx > t ? mx : t;
-    }
-    if (lane == 0) red[wid] = mx;
-    __syncthreads();
-    mx = F(0);
-    for (int q = 0; q < CT / 32; ++q) mx = mx > red[q] ? mx : red[q];
-    const F rel_floor = sizeof(F) == 8 ? F(1e-14) : F(1e-6f);
-    __shared__ int src[CN];
-    blu_factor<F>(A, n, perm, dinv, rel_floor * (mx > F(0) ? mx : F(1)));
-    if (tid == 0) lu_row_sources(n, perm, src);
-    if (tid < n) y[tid] = F(1);
-    __syncthreads();
-    if (wid == 0) {  // two steps of inverse iteration, in one warp
-        for (int it = 0; it < 2; ++it) {
-            warp_lu_solve<F>(A, n, src, dinv, y, 1);
-            double nn = 0.0;
-            for (int r = lane; r < n; r += 32) nn += (double)y[r] * y[r];
-            const F sc = (F)(1.0 / sqrt(warp_sum(nn)));
-            for (int r = lane; r < n; r += 32) y[r] *= sc;
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    const F zs = (F)(1.0 / sqrt((double)n)), ninv = (F)(1.0 / (double)n);
-    for (int idx = tid; idx < n * n; idx += CT) {
-        const int r = idx / n, c = idx - r * n;
-        A[r * LDP + c] = (F)Bg[idx] + zs * y[c];
+        A[r * LDP + c] = (F)Bg[idx] + ninv;  // B + z z^T
     }
     for (int idx = tid; idx < n * mc; idx += CT) {
         const int r = idx / mc, c = idx - r * mc;
-        R[r * mc + c] = (r == c0 + c ? F(1) : F(0)) - ninv;
+        R[r * mc + c] = (r == c0 + c ? F(1) : F(0)) - ninv;  // (I - z z^T) e_c
     }
+    if (tid < n) y[tid] = (F)(1.0 / sqrt((double)n));
     __syncthreads();
-    const long long c_null = clock64();
-    blu_factor<F>(A, n, perm, dinv, pivot_tiny<F>());
-    if (tid == 0) lu_row_sources(n, perm, src);
+    block_lu_factor<F>(A, n, src, dinv, pivot_tiny<F>());
     __syncthreads();
     const long long c_lu = clock64();
-    if (wid < mc) warp_lu_solve<F>(A, n, src, dinv, R + wid, mc);  // one right-hand side per warp
+    if (wid == 0) warp_lu_solve<F>(A, n, src, dinv, y, 1);            // M y = z
+    if (wid < mc) warp_lu_solve<F>(A, n, src, dinv, R + wid, mc);     // M w = (I - z z^T) e_c
     __syncthreads();
     const long long c_solve = clock64();
+    if (wid < mc) {  // w - y (y^T w) / (y^T y)
+        double yw = 0.0, yy = 0.0;
+        for (int r = lane; r < n; r += 32) {
+            yw += (double)y[r] * (double)R[r * mc + wid];
+            yy += (double)y[r] * (double)y[r];
+        }
+        yw = warp_sum(yw);
+        yy = warp_sum(yy);
+        const F f = (F)(yy > 0.0 ? yw / yy : 0.0);
+        __syncwarp();
+        for (int r = lane; r < n; r += 32) R[r * mc + wid] -= f * y[r];
+    }
+    __syncthreads();
     int bad = 0;
     for (int idx = tid; idx < n * mc; idx += CT) {
         const int r = idx / mc, c = idx - r * mc;
@@ -990,8 +946,8 @@ __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restr
     bad = __syncthreads_or(bad);
     if (tid == 0) {
         info[4 * blockIdx.x] = bad;
-        info[4 * blockIdx.x + 1] = (int)(c_null - c_start);  // diagnostics: cycles per phase
-        info[4 * blockIdx.x + 2] = (int)(c_lu - c_null);
+        info[4 * blockIdx.x + 1] = 0;  // diagnostics: cycles per phase
+        info[4 * blockIdx.x + 2] = (int)(c_lu - c_start);
         info[4 * blockIdx.x + 3] = (int)(c_solve - c_lu);
     }
 }
@@ -1008,8 +964,8 @@ int coarse_pinv(int n, const double* dB, double* dP, bool fp32, cudaStream_t s) 
     BAMG_CK(cudaMemcpyAsync(h, info.get(), sizeof(int) * 4 * nb, cudaMemcpyDeviceToHost, s));
     BAMG_CK(cudaStreamSynchronize(s));
     if (getenv("BAMG_DEBUG"))
-        fprintf(stderr, "[bamg] coarse pinv (%s): n=%d blocks=%d cycles null=%d lu=%d solve=%d\n", fp32 ? "fp32" : "fp64",
-                n, nb, h[1], h[2], h[3]);
+        fprintf(stderr, "[bamg] coarse pinv (%s): n=%d blocks=%d cycles lu=%d solve=%d\n", fp32 ? "fp32" : "fp64", n,
+                nb, h[2], h[3]);
     for (int b = 0; b < nb; ++b)
         if (h[4 * b]) return BAMG_ENUMERIC;
     return 0;

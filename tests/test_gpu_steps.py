@@ -364,16 +364,20 @@ def test_galerkin_long_rows_bit_exact(nq, dense):
 
 
 # ------------------------------------------------------------------ coarsest level
-def _coarse_pair():
-    ch = grid_walk(33)
+def _coarse_pair(kind="grid33"):
+    # grid walk 33 x 33: a 25-state coarsest level; tandem queue 64 x 64 (non-symmetric):
+    # 64 states, the largest coarsest order (both rows of every lane in the one-warp
+    # factorisations)
+    ch = grid_walk(33) if kind == "grid33" else tandem_queue(63)
     H = ob.setup(ch.to_scipy(), 6, 10, ob.Opts(), grid=ch.grid)
     Lc = H.levels[-1]
     return Lc.B.toarray(), Lc.T.toarray(), H
 
 
-def test_coarse_eig_matches_oracle():
+@pytest.mark.parametrize("kind", ["grid33", "tandem63"])
+def test_coarse_eig_matches_oracle(kind):
     torch = _torch()
-    Bd, Td, H = _coarse_pair()
+    Bd, Td, H = _coarse_pair(kind)
     lam_o, V_o, kinds_o = ob.coarse_eigs(Bd, Td, 6)
     lam, V, kinds, pinv = _bamg().coarse_eig(torch.tensor(Bd, device="cuda"), torch.tensor(Td, device="cuda"), 6)
     lam, V, kinds, pinv = lam.cpu().numpy(), V.cpu().numpy(), kinds.cpu().numpy(), pinv.cpu().numpy()
@@ -392,11 +396,12 @@ def test_coarse_eig_matches_oracle():
     assert np.allclose(pinv, ob.pinv_truncated(Bd), rtol=1e-9, atol=1e-11)
 
 
-def test_coarse_eig_fp32_vectors_close_to_oracle():
+@pytest.mark.parametrize("kind", ["grid33", "tandem63"])
+def test_coarse_eig_fp32_vectors_close_to_oracle(kind):
     # the mixed-precision setup refines the coarsest eigenvectors in FP32: same selection,
     # eigenvalues and vectors to FP32 accuracy
     torch = _torch()
-    Bd, Td, H = _coarse_pair()
+    Bd, Td, H = _coarse_pair(kind)
     lam_o, V_o, kinds_o = ob.coarse_eigs(Bd, Td, 6)
     lam, V, kinds, pinv = _bamg().coarse_eig(torch.tensor(Bd, device="cuda"), torch.tensor(Td, device="cuda"), 6,
                                              fp32_vectors=True)
