@@ -7,7 +7,7 @@
 // small Hessenberg matrix (Golub & Van Loan, Matrix Computations, Sec. 7.5).
 // Eigenvectors, one block per selected eigenvalue: inverse iteration in complex
 // arithmetic on the pencil (B - sigma T) and a Rayleigh-type quotient, in FP64 (or in
-// FP32 for the mixed-precision setup).  B^+: one LU of the bordered matrix B + z z^T
+// FP32 for the mixed-precision setup, through the explicit (B - sigma T)^{-1} T).  B^+: one LU of the bordered matrix B + z z^T
 // (z = 1/sqrt(n)), the right-hand sides split over several blocks.  Factorisations use the
 // whole block (rows in place, the pivot found by a warp reduction); triangular solves run
 // in single warps (shuffles, no block barriers).
@@ -16,6 +16,7 @@
 #include <cstdlib>
 
 #include <atomic>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -268,6 +269,80 @@ __device__ void warp_lu_solve_cols(const F* A, int n, const int* src, const F* d
 template <typename F>
 __device__ void warp_lu_solve(const F* A, int n, const int* src, const F* dinv, F* b, int ldb) {
     warp_lu_solve_cols<F, 1>(A, n, src, dinv, b, ldb, 0, 1);
+}
+
+// One warp solves (Ar + i Ai) X = R for the NC real right-hand sides c0 .. c0 + NC - 1 (those
+// < n) of R (row-major, stride LDP), with the factors of block_lu_factor_cplx (equation i in
+// row src[i]); X = Xr + i Xi (stride LDP).  The NC independent columns share each step's
+// shuffle latency.  Entries of L (U) beyond a lane's range are taken as zero, which leaves
+// its unknowns exactly unchanged.
+template <typename F, int NC>
+__device__ void warp_lu_solve_cols_cplx(const F* Ar, const F* Ai, int n, const int* src, const F* dr, const F* di,
+                                        const F* R, F* Xr, F* Xi, int c0) {
+    const int lane = lane_id();
+    const bool v0 = lane < n, v1 = lane + 32 < n;
+    const int r0 = v0 ? src[lane] : 0, r1 = v1 ? src[lane + 32] : 0;
+    F ar[NC], ai[NC], br[NC], bi[NC];  // the unknowns lane (a) and lane + 32 (b) of each column
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const bool cj = c0 + j < n;
+        ar[j] = v0 && cj ? R[r0 * LDP + c0 + j] : F(0);
+        br[j] = v1 && cj ? R[r1 * LDP + c0 + j] : F(0);
+        ai[j] = bi[j] = F(0);
+    }
+    __syncwarp();
+    for (int q = 0; q + 1 < n; ++q) {  // unit lower
+        const bool a0 = v0 && lane > q, a1 = v1 && lane + 32 > q;
+        const F l0r = a0 ? Ar[r0 * LDP + q] : F(0), l0i = a0 ? Ai[r0 * LDP + q] : F(0);
+        const F l1r = a1 ? Ar[r1 * LDP + q] : F(0), l1i = a1 ? Ai[r1 * LDP + q] : F(0);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const F yr = __shfl_sync(0xffffffffu, q < 32 ? ar[j] : br[j], q & 31);
+            const F yi = __shfl_sync(0xffffffffu, q < 32 ? ai[j] : bi[j], q & 31);
+            ar[j] -= l0r * yr - l0i * yi;
+            ai[j] -= l0r * yi + l0i * yr;
+            br[j] -= l1r * yr - l1i * yi;
+            bi[j] -= l1r * yi + l1i * yr;
+        }
+    }
+    {
+        const F d0r = v0 ? dr[lane] : F(0), d0i = v0 ? di[lane] : F(0);
+        const F d1r = v1 ? dr[lane + 32] : F(0), d1i = v1 ? di[lane + 32] : F(0);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const F a = ar[j], b = ai[j], c = br[j], d = bi[j];
+            ar[j] = a * d0r - b * d0i;
+            ai[j] = a * d0i + b * d0r;
+            br[j] = c * d1r - d * d1i;
+            bi[j] = c * d1i + d * d1r;
+        }
+    }
+    for (int q = n - 1; q > 0; --q) {  // unit upper
+        const bool a0 = v0 && lane < q, a1 = v1 && lane + 32 < q;
+        const F u0r = a0 ? Ar[r0 * LDP + q] : F(0), u0i = a0 ? Ai[r0 * LDP + q] : F(0);
+        const F u1r = a1 ? Ar[r1 * LDP + q] : F(0), u1i = a1 ? Ai[r1 * LDP + q] : F(0);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const F yr = __shfl_sync(0xffffffffu, q < 32 ? ar[j] : br[j], q & 31);
+            const F yi = __shfl_sync(0xffffffffu, q < 32 ? ai[j] : bi[j], q & 31);
+            ar[j] -= u0r * yr - u0i * yi;
+            ai[j] -= u0r * yi + u0i * yr;
+            br[j] -= u1r * yr - u1i * yi;
+            bi[j] -= u1r * yi + u1i * yr;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        if (c0 + j >= n) continue;
+        if (v0) {
+            Xr[lane * LDP + c0 + j] = ar[j];
+            Xi[lane * LDP + c0 + j] = ai[j];
+        }
+        if (v1) {
+            Xr[(lane + 32) * LDP + c0 + j] = br[j];
+            Xi[(lane + 32) * LDP + c0 + j] = bi[j];
+        }
+    }
 }
 
 // ---------------------------------------------------------------- FP32 Hessenberg + QR
@@ -590,9 +665,11 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __re
 // Kernel 2, one block per selected eigenvalue, in arithmetic F (double, or float for the
 // mixed-precision setup): LU of the pencil (B - sigma T) in complex arithmetic with sigma
 // the FP32 estimate; four steps of inverse iteration v <- (B - sigma T)^{-1} T v from a
-// fixed positive start; the Rayleigh-type quotient lambda = v^H B v / v^H T v (Algorithm
-// 3's update, in complex form, accumulated in FP64); and the phase that makes <w, v> real
-// and positive (w_i = i + 1) with unit 2-norm.
+// start drawn per column (FP64: two triangular solves per step in one warp; FP32: the
+// matrix K = (B - sigma T)^{-1} T formed once by all warps, eight right-hand sides each,
+// then products with K); the Rayleigh-type quotient lambda = v^H B v / v^H T v (Algorithm
+// 3's update, in complex form, accumulated in F); and the phase that makes <w, v> real and
+// positive (w_i = i + 1) with unit 2-norm.
 template <typename F>
 __device__ __forceinline__ F pivot_tiny() {
     if constexpr (sizeof(F) == 8)
@@ -613,7 +690,7 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
     F* Bm = Ai + CN * LDP;
     F* Tm = Bm + CN * LDP;
     __shared__ F vr[CN], vi[CN], tr[CN], ti[CN], dr[CN], di[CN], pre[4 * CN], pim[4 * CN];
-    __shared__ double red[4 * (CT / 32)];
+    __shared__ typename std::conditional<sizeof(F) == 4, float, double>::type red[4 * (CT / 32)];
     const long long c_start = clock64();
     const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
     const F sr = (F)sel[3 * blockIdx.x], si = (F)sel[3 * blockIdx.x + 1];
@@ -666,6 +743,50 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
     // interchanges and the two triangular solves in warp 0 (registers and shuffles; lane l
     // holds rows l and l + 32), in the order of operations of the plain solve
     const int row = tid & (CN - 1), quarter = tid >> 6;
+    if constexpr (sizeof(F) == 4) {
+        // FP32: K = (B - sigma T)^{-1} T once (each warp solves 8 of its columns), then the four
+        // steps as products v <- K v by the block (4 threads per row); the normalisation in FP32
+        F* Kr = Tm + CN * LDP;
+        F* Ki = Kr + CN * LDP;
+        warp_lu_solve_cols_cplx<F, CN / (CT / 32)>(Ar, Ai, n, srcp, dr, di, Tm, Kr, Ki, wid * (CN / (CT / 32)));
+        __syncthreads();
+        for (int it = 0; it < 4; ++it) {
+            if (row < n) {
+                F a = F(0), b = F(0);
+                const int c1 = min(n, 16 * quarter + 16);
+                for (int c = 16 * quarter; c < c1; ++c) {
+                    const F kr = Kr[row * LDP + c], ki = Ki[row * LDP + c];
+                    a += kr * vr[c] - ki * vi[c];
+                    b += kr * vi[c] + ki * vr[c];
+                }
+                pre[quarter * CN + row] = a;
+                pim[quarter * CN + row] = b;
+            }
+            __syncthreads();
+            if (wid == 0) {
+                F xr[2], xi[2], nn = F(0);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = lane + 32 * h;
+                    xr[h] = r < n ? (pre[r] + pre[CN + r]) + (pre[2 * CN + r] + pre[3 * CN + r]) : F(0);
+                    xi[h] = r < n ? (pim[r] + pim[CN + r]) + (pim[2 * CN + r] + pim[3 * CN + r]) : F(0);
+                    nn += xr[h] * xr[h] + xi[h] * xi[h];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+                const F sc = rsqrtf(nn);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = lane + 32 * h;
+                    if (r < n) {
+                        vr[r] = xr[h] * sc;
+                        vi[r] = xi[h] * sc;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    } else {
     for (int it = 0; it < 4; ++it) {
         if (row < n) {
             F a = F(0), b = F(0);
@@ -749,9 +870,17 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
         }
         __syncthreads();
     }
-    // lambda = v^H B v / v^H T v: (B v)_r and (T v)_r with 4 threads per row
+    }
+    // lambda = v^H B v / v^H T v: (B v)_r and (T v)_r with 4 threads per row, the sums in
+    // FP64 (FP32 for the FP32 vectors)
+    using Acc = typename std::conditional<sizeof(F) == 4, float, double>::type;
+    auto wsum = [](Acc v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
     {
-        double br_ = 0.0, bi_ = 0.0, tr_ = 0.0, ti_ = 0.0;
+        Acc br_ = Acc(0), bi_ = Acc(0), tr_ = Acc(0), ti_ = Acc(0);
         if (row < n) {
             F wbr = F(0), wbi = F(0), wtr = F(0), wti = F(0);
             const int c1 = min(n, 16 * quarter + 16);
@@ -762,16 +891,16 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
                 wtr += t * vr[c];
                 wti += t * vi[c];
             }
-            const double xr = vr[row], xi = vi[row];
+            const Acc xr = vr[row], xi = vi[row];
             br_ = xr * wbr + xi * wbi;
             bi_ = xr * wbi - xi * wbr;
             tr_ = xr * wtr + xi * wti;
             ti_ = xr * wti - xi * wtr;
         }
-        br_ = warp_sum(br_);
-        bi_ = warp_sum(bi_);
-        tr_ = warp_sum(tr_);
-        ti_ = warp_sum(ti_);
+        br_ = wsum(br_);
+        bi_ = wsum(bi_);
+        tr_ = wsum(tr_);
+        ti_ = wsum(ti_);
         if (lane == 0) {
             red[4 * wid] = br_;
             red[4 * wid + 1] = bi_;
@@ -781,33 +910,33 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
     }
     __syncthreads();
     if (tid >= 32) return;
-    double sr2 = 0.0, si2 = 0.0;
+    Acc sr2 = Acc(0), si2 = Acc(0);
     for (int r = lane; r < n; r += 32) {
-        sr2 += (double)(r + 1) * vr[r];
-        si2 += (double)(r + 1) * vi[r];
+        sr2 += (Acc)(r + 1) * vr[r];
+        si2 += (Acc)(r + 1) * vi[r];
     }
-    sr2 = warp_sum(sr2);
-    si2 = warp_sum(si2);
-    const double sa = hypot(sr2, si2);
-    const double cr = sa > 0.0 ? sr2 / sa : 1.0, ci = sa > 0.0 ? -si2 / sa : 0.0;  // conj(s)/|s|
-    double nn = 0.0;
-    double ar[2], ai[2];
+    sr2 = wsum(sr2);
+    si2 = wsum(si2);
+    const Acc sa = hypot(sr2, si2);
+    const Acc cr = sa > Acc(0) ? sr2 / sa : Acc(1), ci = sa > Acc(0) ? -si2 / sa : Acc(0);  // conj(s)/|s|
+    Acc nn = Acc(0);
+    Acc ar[2], ai[2];
     for (int q = 0, r = lane; q < 2; ++q, r += 32) {
-        ar[q] = ai[q] = 0.0;
+        ar[q] = ai[q] = Acc(0);
         if (r < n) {
-            ar[q] = (double)vr[r] * cr - (double)vi[r] * ci;
-            ai[q] = (double)vr[r] * ci + (double)vi[r] * cr;
+            ar[q] = (Acc)vr[r] * cr - (Acc)vi[r] * ci;
+            ai[q] = (Acc)vr[r] * ci + (Acc)vi[r] * cr;
             nn += ar[q] * ar[q] + ai[q] * ai[q];
         }
     }
-    nn = 1.0 / sqrt(warp_sum(nn));
+    nn = Acc(1) / sqrt(wsum(nn));
     for (int q = 0, r = lane; q < 2; ++q, r += 32)
         if (r < n) {
-            V[(int64_t)col * n + r] = ar[q] * nn;
-            if (si != F(0)) V[(int64_t)(col + 1) * n + r] = ai[q] * nn;
+            V[(int64_t)col * n + r] = (double)(ar[q] * nn);
+            if (si != F(0)) V[(int64_t)(col + 1) * n + r] = (double)(ai[q] * nn);
         }
     if (lane == 0) {
-        double nbr = 0.0, nbi = 0.0, ntr = 0.0, nti = 0.0;
+        Acc nbr = Acc(0), nbi = Acc(0), ntr = Acc(0), nti = Acc(0);
         for (int q = 0; q < CT / 32; ++q) {
             nbr += red[4 * q];
             nbi += red[4 * q + 1];
@@ -815,7 +944,7 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __res
             nti += red[4 * q + 3];
         }
         // Re of (nbr + i nbi) / (ntr + i nti)
-        double lre = (nbr * ntr + nbi * nti) / (ntr * ntr + nti * nti);
+        double lre = (double)((nbr * ntr + nbi * nti) / (ntr * ntr + nti * nti));
         if (col == 0) lre = 0.0;  // the state vector's eigenvalue is exactly zero
         lam[col] = lre;
         if (si != F(0)) lam[col + 1] = lre;
@@ -833,7 +962,7 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
     int dev = 0;
     BAMG_CK(cudaGetDevice(&dev));
     BAMG_REQUIRE(dev >= 0 && dev < 256, BAMG_EINVAL, "device ordinal out of range");
-    const size_t smem64 = 4 * CN * LDP * sizeof(double), smem32 = 4 * CN * LDP * sizeof(float);
+    const size_t smem64 = 4 * CN * LDP * sizeof(double), smem32 = 6 * CN * LDP * sizeof(float);
     if (!attr[dev]) {
         BAMG_CK(cudaFuncSetAttribute(k_coarse_eigvec<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem64));
