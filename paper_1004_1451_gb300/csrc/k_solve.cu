@@ -1366,12 +1366,12 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(int n, int tile, const 
     arn_tile_dots(V, n, j, r0, cnt, w, next_self, Pout, stride);
 }
 
-// Givens update (one thread) fused with v_{j+1} = w / ||w||: every thread forms
-// ||w|| = sqrt(nrm2) itself, so the scaling does not wait for the rotation.
+// Givens update (one thread) fused with v_{j+1} = w / ||w||: every block forms ||w|| from the
+// partial sums itself (once, not per thread), so the scaling does not wait for the rotation.
 __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __restrict__ dj, double* __restrict__ st,
                                  int m, const double* __restrict__ Pn, int nb, int stride) {
     pdl_begin();
-    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX], s_nrm2;
+    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX], s_nrm2, s_hn;
     GmresLayout L(m);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = *dj;
@@ -1379,6 +1379,7 @@ __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __res
         const double nn = arn_colsum(Pn, nb, stride, 0, threadIdx.x);
         if (threadIdx.x == 0) {
             s_nrm2 = nn;
+            s_hn = sqrt(nn);
             if (blockIdx.x == 0) st[L.nrm2] = nn;
         }
     }
@@ -1417,10 +1418,9 @@ __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __res
         __syncthreads();
         for (int q = threadIdx.x; q <= j; q += blockDim.x) st[L.R + q + (int64_t)j * m] = col[q];
     }
-    if (i < n) {
-        const double hn = sqrt(s_nrm2);
+    if (i < n) {  // w / ||w|| with the block's one square root (the division as in the plain algorithm)
         double* w = V + (int64_t)(j + 1) * n;
-        w[i] = hn != 0.0 ? w[i] / hn : 0.0;
+        w[i] = s_hn != 0.0 ? w[i] / s_hn : 0.0;
     }
 }
 
@@ -1948,7 +1948,9 @@ __global__ void __launch_bounds__(PERSIST_THREADS, 1) k_arnoldi_cycle(const __gr
             __syncthreads();
             for (int q = threadIdx.x; q <= j; q += blockDim.x) st[GL.R + q + (int64_t)j * a.m] = gcol[q];
         }
-        {
+        {  // w / ||w||, the square root formed once per thread (an FP64 square root is a long
+           // instruction sequence at GB300's FP64 rate); the division stays, as in the plain
+           // algorithm's w / h_{j+1,j}
             const double hn = sqrt(s_nrm2);
             for (int i = gtid; i < n; i += gsz) w[i] = hn != 0.0 ? w[i] / hn : 0.0;
         }
