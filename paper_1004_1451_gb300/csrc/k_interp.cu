@@ -840,13 +840,46 @@ __global__ void k_q_fill(int n, int c, const int32_t* __restrict__ pcol, const i
 }
 // Sort each row by fine index (the fill order above is arbitrary) and set the
 // averaging weights 1/|J_i| (Section 4: identical entries per column, 1^T Q = 1^T).
+// Rows of up to Q_SORT_REG entries are sorted in registers (one load and one store per
+// entry), longer ones in place; 1 / |J_i| comes from constants where |J_i| <= 4 (every
+// caliber the setup allows), the same values as the division.
+constexpr int Q_SORT_REG = 16;
 template <typename T>
 __global__ void k_q_sort(int nc, const int32_t* __restrict__ qrp, int32_t* __restrict__ qci, T* __restrict__ qv,
                          const int32_t* __restrict__ pcnt) {
     pdl_begin();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
+    auto inv = [](int p) {  // 1 / p, from constants for the common p <= 4
+        switch (p) {
+            case 1: return (T)(1.0 / 1.0);
+            case 2: return (T)(1.0 / 2.0);
+            case 3: return (T)(1.0 / 3.0);
+            case 4: return (T)(1.0 / 4.0);
+            default: return (T)(1.0 / (double)p);
+        }
+    };
     const int a = qrp[I], b = qrp[I + 1];
+    if (b - a <= Q_SORT_REG) {
+        int v[Q_SORT_REG];
+#pragma unroll
+        for (int k = 0; k < Q_SORT_REG; ++k) v[k] = a + k < b ? qci[a + k] : 0x7fffffff;
+#pragma unroll
+        for (int k = 1; k < Q_SORT_REG; ++k)  // insertion sort, unrolled: indices stay constant
+#pragma unroll
+            for (int q = k; q > 0; --q) {
+                const int lo = min(v[q - 1], v[q]), hi = max(v[q - 1], v[q]);
+                v[q - 1] = lo;
+                v[q] = hi;
+            }
+#pragma unroll
+        for (int k = 0; k < Q_SORT_REG; ++k)
+            if (a + k < b) {
+                qci[a + k] = v[k];
+                qv[a + k] = inv(pcnt[v[k]]);
+            }
+        return;
+    }
     for (int p = a + 1; p < b; ++p) {
         const int v = qci[p];
         int q = p;
@@ -856,7 +889,7 @@ __global__ void k_q_sort(int nc, const int32_t* __restrict__ qrp, int32_t* __res
         }
         qci[q] = v;
     }
-    for (int p = a; p < b; ++p) qv[p] = (T)(1.0 / (double)pcnt[qci[p]]);
+    for (int p = a; p < b; ++p) qv[p] = inv(pcnt[qci[p]]);
 }
 
 template <typename T>

@@ -503,7 +503,9 @@ static int colstats_blocks(int n, int ncols, int* width) {
     int ny = 1;
     while (ny * 2 * nvec <= 256) ny *= 2;
     int nb = (int)blocks_for(n, ny);
-    if (nb > 512) nb = 512;
+    // the consumers sum the partials in FP64 on one SM, where GB300's FP64 rate makes every
+    // partial count: 128 blocks still cover the level
+    if (nb > 128) nb = 128;
     *width = nvec * 2 * W;
     return nb;
 }
@@ -535,6 +537,7 @@ __device__ void colsum_partials(int nblocks, int width, const double* __restrict
 }
 
 // ---------------------------------------------------------------- LS weights
+// nrm[k] = ||x_k||_2 and nrm[32 + k] = 1 / nrm[k] (used by FP32 test vectors)
 __global__ void __launch_bounds__(COLSUM_T) k_weights(int ncols, int W, int nblocks, const double* __restrict__ partial,
                                                         const uint8_t* __restrict__ active, double floor,
                                                         double* __restrict__ w, double* __restrict__ nrm) {
@@ -559,6 +562,7 @@ __global__ void __launch_bounds__(COLSUM_T) k_weights(int ncols, int W, int nblo
     if (k < ncols) {
         w[k] = mx > 0.0 ? m / mx : 0.0;
         nrm[k] = nk;
+        nrm[32 + k] = 1.0 / nk;
     }
 }
 
@@ -572,7 +576,10 @@ __global__ void k_scale_cols(int n, T* __restrict__ X, int ld, int col0, int nco
     const double d = nrm[k];
     if (d != 1.0) {
         T* p = X + (int64_t)row * ld + col0 + k;
-        *p = (T)((double)*p / d);
+        if constexpr (sizeof(T) == 4)  // the FP64 product rounds to the same FP32 value as the quotient
+            *p = (T)((double)*p * nrm[32 + k]);  // (but for double rounding); an FP64 division per element is slow
+        else
+            *p = (T)((double)*p / d);
     }
 }
 
@@ -584,7 +591,7 @@ void tv_weights(const MatView<T>& B, int ncols, int ld, int col0, const uint8_t*
     int width = 0;
     const int nb = colstats_blocks<T>(B.n, ncols, &width);
     TmpBuf<double> partial((size_t)nb * width, s);
-    TmpBuf<double> nrm(32, s);
+    TmpBuf<double> nrm(64, s);
     colstats<T, 0>(B, nullptr, X, ld, col0, ncols, partial.get(), s);
     BAMG_LAUNCH(k_weights, 1, COLSUM_T, 0, s, ncols, W, nb, (const double*)partial.get(), d_active, floor, d_w,
                 nrm.get());
