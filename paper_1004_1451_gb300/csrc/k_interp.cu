@@ -408,6 +408,7 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
                 const int ka = __shfl_sync(0xffffffffu, ra, k);
                 const int kx = __shfl_sync(0xffffffffu, incl - rlen, k);
                 const int v = e < total ? ci[ka + e - kx] : -1;
+                const bool vc = v >= 0 && cf[v] != 0;  // loaded with v: the count below reads it from dist
                 const bool isnew = v >= 0 && !vis_contains(hs, HS, v);
                 const int key = isnew ? v : -1 - lane;
                 const unsigned grp = __match_any_sync(0xffffffffu, key);
@@ -416,13 +417,13 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
                 unsigned bal = __ballot_sync(0xffffffffu, leader);
                 if (fonly || nvis + __popc(bal) > CAP) {  // list full: keep the coarse nodes only
                     fonly = true;
-                    bal = __ballot_sync(0xffffffffu, leader && cf[v] != 0);
+                    bal = __ballot_sync(0xffffffffu, leader && vc);
                 }
                 const bool rec = (bal >> lane) & 1u;
                 const int pos = nvis + __popc(bal & lt);
                 if (rec && pos < CAP) {
                     vis[pos] = v;
-                    dist[pos] = (uint8_t)d;
+                    dist[pos] = (uint8_t)(d | (vc ? 0x80 : 0));  // depth, and the C flag in bit 7
                     vis_insert(hs, HS, v);
                 }
                 int added = __popc(bal);
@@ -436,7 +437,7 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
         }
         for (int q0 = fe; q0 < nvis; q0 += 32) {  // coarse points recorded at this depth
             const int q = q0 + lane;
-            ncvis += __popc(__ballot_sync(0xffffffffu, q < nvis && cf[vis[q]] != 0));
+            ncvis += __popc(__ballot_sync(0xffffffffu, q < nvis && (dist[q] & 0x80) != 0));
         }
         // a truncated depth (fine nodes not recorded) is exact only if the search ends here
         if (fonly) {
@@ -458,8 +459,8 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
         unsigned long long kq = 0;
         if (q < nvis) {
             v = vis[q];
-            isc = cf[v] != 0;
-            if (isc) kq = ((unsigned long long)dist[q] << 32) | (unsigned)cidx[v];
+            isc = (dist[q] & 0x80) != 0;
+            if (isc) kq = ((unsigned long long)(dist[q] & 0x7f) << 32) | (unsigned)cidx[v];
         }
         const unsigned bal = __ballot_sync(0xffffffffu, isc);
         __syncwarp();  // every lane has read vis[q] before the compacted writes below
@@ -629,7 +630,7 @@ __device__ bool ls_point(int i, const int32_t* __restrict__ rp, const int32_t* _
 // CAP-entry list is appended to ovf_list (or flags err when ovf_list is null).  Second
 // pass (list != nullptr): persistent warps over the *list_count points of list.
 template <typename T, int CAP, int WARPS, bool EXTRA>
-__global__ void __launch_bounds__(WARPS * 32, (WARPS > 1 && sizeof(T) == 4) ? 6 : 1)  // FP32: 6 blocks/SM
+__global__ void __launch_bounds__(WARPS * 32, (WARPS > 1 && sizeof(T) == 4) ? 8 : 1)  // FP32: 8 blocks/SM
     k_ls_fit(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ bv,
              const uint8_t* __restrict__ cf, const int32_t* __restrict__ cidx, const T* __restrict__ X, int ncols,
              int ld, const double* __restrict__ w, int z, int mmax, int c, double ridge, int32_t* __restrict__ pcol,

@@ -504,8 +504,10 @@ static int colstats_blocks(int n, int ncols, int* width) {
     while (ny * 2 * nvec <= 256) ny *= 2;
     int nb = (int)blocks_for(n, ny);
     // the consumers sum the partials in FP64 on one SM, where GB300's FP64 rate makes every
-    // partial count: 128 blocks still cover the level
-    if (nb > 128) nb = 128;
+    // partial count: 128 blocks cover levels up to 2^18 rows; larger ones stream enough
+    // test-vector bytes to need up to 512
+    const int cap = n <= (1 << 18) ? 128 : (n >= (1 << 20) ? 512 : n >> 11);
+    if (nb > cap) nb = cap;
     *width = nvec * 2 * W;
     return nb;
 }
