@@ -914,18 +914,47 @@ void build_restriction(const EllView<T>& P, int nc, DevBuf<int32_t>& qrp, DevBuf
 // coarse row I, rounded as ((q * m) * p); the products of one (I, J) are then summed in
 // that order.  This is the order of the plain definition, so a CPU evaluation of the
 // same sum in the same order gives the same bits.
-__global__ void k_gal_count(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
-                            const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                            const int32_t* __restrict__ pcnt, int32_t* __restrict__ np) {
+// Products of coarse row I: sum over its Q entries i and the entries (i, j) of B of |P row j|.
+// One warp per coarse row: the lanes take the Q entries, then the (i, j) pairs, 32 at a time.
+constexpr int GAL_COUNT_WARPS = 4;
+__global__ void __launch_bounds__(GAL_COUNT_WARPS * 32)
+    k_gal_count(int nc, const int32_t* __restrict__ qrp, const int32_t* __restrict__ qci,
+                const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const int32_t* __restrict__ pcnt,
+                int32_t* __restrict__ np) {
     pdl_begin();
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int I = blockIdx.x * GAL_COUNT_WARPS + (threadIdx.x >> 5);
     if (I >= nc) return;
+    const int q0 = qrp[I], q1 = qrp[I + 1];
     int s = 0;
-    for (int q = qrp[I]; q < qrp[I + 1]; ++q) {
-        const int i = qci[q];
-        for (int p = rp[i]; p < rp[i + 1]; ++p) s += pcnt[ci[p]];
+    for (int qc = q0; qc < q1; qc += 32) {
+        const int qq = qc + lane;
+        const int ii = qq < q1 ? qci[qq] : 0;
+        const int rb = qq < q1 ? rp[ii] : 0;
+        const int rl = qq < q1 ? rp[ii + 1] - rb : 0;
+        int rinc = rl;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, rinc, d);
+            if (lane >= d) rinc += v;
+        }
+        const int npairs = __shfl_sync(0xffffffffu, rinc, 31);
+        for (int f0 = 0; f0 < npairs; f0 += 32) {
+            const int f = f0 + lane;
+            int k = 0;
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int ic = __shfl_sync(0xffffffffu, rinc, k + st - 1);
+                if (ic <= f) k += st;
+            }
+            k = min(k, 31);
+            const int p = __shfl_sync(0xffffffffu, rb, k) + f - __shfl_sync(0xffffffffu, rinc - rl, k);
+            if (f < npairs) s += pcnt[ci[p]];
+        }
     }
-    np[I] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) np[I] = s;
 }
 
 template <typename T>
@@ -934,10 +963,11 @@ __global__ void k_gal_compact(int nc, const int32_t* __restrict__ poff, const in
                               const T* __restrict__ utv, int32_t* __restrict__ ci, T* __restrict__ bv,
                               T* __restrict__ tv) {
     pdl_begin();
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int I = blockIdx.x * GAL_COUNT_WARPS + (threadIdx.x >> 5);  // one warp per coarse row
     if (I >= nc) return;
-    const int o = poff[I], d = rpc[I];
-    for (int u = 0; u < ucnt[I]; ++u) {
+    const int o = poff[I], d = rpc[I], cnt = ucnt[I];
+    for (int u = lane; u < cnt; u += 32) {
         ci[d + u] = uJ[o + u];
         bv[d + u] = ubv[o + u];
         tv[d + u] = utv[o + u];
@@ -983,52 +1013,62 @@ __device__ void gal_row(const GalArgs<T>& a, int I, bool local, unsigned long lo
     const unsigned lt = (1u << lane) - 1u;
     const int o = a.poff[I], np = a.poff[I + 1] - o;
     const int q0 = a.qrp[I], q1 = a.qrp[I + 1];
-    int npairs = 0;
-    for (int q = q0; q < q1; ++q) npairs += a.rp[a.qci[q] + 1] - a.rp[a.qci[q]];
     int base = 0;
-    for (int f0 = 0; f0 < npairs; f0 += 32) {
-        const int f = f0 + lane;
-        int q = q0, acc = 0, i = -1, p = -1;
-        if (f < npairs) {
-            for (; q < q1; ++q) {
-                const int ii = a.qci[q], len = a.rp[ii + 1] - a.rp[ii];
-                if (f < acc + len) {
-                    i = ii;
-                    p = a.rp[ii] + (f - acc);
-                    break;
-                }
-                acc += len;
-            }
-        }
-        const int j = f < npairs ? a.ci[p] : 0;
-        const int cnt = f < npairs ? a.pcnt[j] : 0;
-        int incl = cnt;  // inclusive warp prefix sum of the product counts
+    for (int qc = q0; qc < q1; qc += 32) {  // the Q row's entries in chunks of 32
+        // each lane one entry (fine row i, its B row's start and length), prefix of the lengths
+        const int qq = qc + lane;
+        const int ii = qq < q1 ? a.qci[qq] : 0;
+        const int rb = qq < q1 ? a.rp[ii] : 0;
+        const int rl = qq < q1 ? a.rp[ii + 1] - rb : 0;
+        int rinc = rl;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += v;
+            const int v = __shfl_up_sync(0xffffffffu, rinc, d);
+            if (lane >= d) rinc += v;
         }
-        const int pos0 = base + incl - cnt;
-        if (f < npairs) {
-            const T qq = a.qv[q];
-            const T qb = mul_rn(qq, a.bv[p]);
-            const T qt = a.tv ? mul_rn(qq, a.tv[p]) : (j == i ? qq : T(0));
-            for (int sl = 0; sl < cnt; ++sl) {
-                const T pv = a.pval[(int64_t)j * a.c + sl];
-                const int J = a.pcol[(int64_t)j * a.c + sl];
-                const int e = pos0 + sl;
-                if (local) {
-                    keys[e] = ((unsigned long long)(unsigned)J << 32) | (unsigned)e;
-                    svb[e] = mul_rn(qb, pv);
-                    svt[e] = mul_rn(qt, pv);
-                } else {
-                    a.pJ[o + e] = J;
-                    a.pvb[o + e] = mul_rn(qb, pv);
-                    a.pvt[o + e] = mul_rn(qt, pv);
+        const int npairs = __shfl_sync(0xffffffffu, rinc, 31);
+        for (int f0 = 0; f0 < npairs; f0 += 32) {
+            const int f = f0 + lane;
+            int k = 0;  // the chunk entry holding pair f: the first with rinc > f
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int ic = __shfl_sync(0xffffffffu, rinc, k + st - 1);
+                if (ic <= f) k += st;
+            }
+            k = min(k, 31);
+            const int i = __shfl_sync(0xffffffffu, ii, k);
+            const int p = __shfl_sync(0xffffffffu, rb, k) + f - __shfl_sync(0xffffffffu, rinc - rl, k);
+            const int q = qc + k;
+            const int j = f < npairs ? a.ci[p] : 0;
+            const int cnt = f < npairs ? a.pcnt[j] : 0;
+            int incl = cnt;  // inclusive warp prefix sum of the product counts
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += v;
+            }
+            const int pos0 = base + incl - cnt;
+            if (f < npairs) {
+                const T qq_ = a.qv[q];
+                const T qb = mul_rn(qq_, a.bv[p]);
+                const T qt = a.tv ? mul_rn(qq_, a.tv[p]) : (j == i ? qq_ : T(0));
+                for (int sl = 0; sl < cnt; ++sl) {
+                    const T pv = a.pval[(int64_t)j * a.c + sl];
+                    const int J = a.pcol[(int64_t)j * a.c + sl];
+                    const int e = pos0 + sl;
+                    if (local) {
+                        keys[e] = ((unsigned long long)(unsigned)J << 32) | (unsigned)e;
+                        svb[e] = mul_rn(qb, pv);
+                        svt[e] = mul_rn(qt, pv);
+                    } else {
+                        a.pJ[o + e] = J;
+                        a.pvb[o + e] = mul_rn(qb, pv);
+                        a.pvt[o + e] = mul_rn(qt, pv);
+                    }
                 }
             }
+            base += __shfl_sync(0xffffffffu, incl, 31);
         }
-        base += __shfl_sync(0xffffffffu, incl, 31);
     }
     __syncwarp();
     if (local) {
@@ -1300,7 +1340,8 @@ template <typename T>
 void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int32_t* qci, const T* qv,
               const EllView<T>& P, int nc, GalerkinOut<T>& out, cudaStream_t s) {
     TmpBuf<int32_t> np(nc, s), poff(nc + 1, s);
-    BAMG_LAUNCH(k_gal_count, blocks_for(nc, 128), 128, 0, s, nc, qrp, qci, B.rp, B.ci, P.pcnt, np.get());
+    BAMG_LAUNCH(k_gal_count, blocks_for(nc, GAL_COUNT_WARPS), GAL_COUNT_WARPS * 32, 0, s, nc, qrp, qci, B.rp, B.ci,
+                P.pcnt, np.get());
     exclusive_scan(np.get(), poff.get(), nc, s);
     // bound on the product count: each entry b_ij meets at most c columns of Q and c rows of P
     const size_t bound = (size_t)B.nnz * P.c * P.c;
@@ -1339,7 +1380,8 @@ void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int
     out.ci.alloc(nz);
     out.bv.alloc(nz);
     out.tv.alloc(nz);
-    BAMG_LAUNCH(k_gal_compact<T>, blocks_for(nc, 128), 128, 0, s, nc, poff.get(), ucnt.get(), out.rp.get(), uJ.get(),
+    BAMG_LAUNCH(k_gal_compact<T>, blocks_for(nc, GAL_COUNT_WARPS), GAL_COUNT_WARPS * 32, 0, s, nc, poff.get(),
+                ucnt.get(), out.rp.get(), uJ.get(),
                 ubv.get(), utv.get(), out.ci.get(), out.bv.get(), out.tv.get());
 }
 
