@@ -1286,15 +1286,14 @@ __global__ void k_step_end(int* dj, const double* __restrict__ st, int m, const 
 // Fused Arnoldi kernels over row tiles (one block each).  The column sums of the per-tile
 // dot products are formed again by every block that needs them (warp per column, lanes
 // strided over the tiles, the same order in every block), so the reductions need no kernel
-// of their own; the tile grows with n so that there are at most ARN_MAX_TILES of them.  Every
-// consumer block sums all the partials in FP64, so their count is kept at one tile per SM of
-// GB300 (152): enough blocks for the FP64 update, and 40% fewer FP64 additions per block than
-// 256 tiles (the FP64 rate, not memory, bounds these kernels).
+// of their own; the tile grows with n so that there are at most ARN_MAX_TILES of them.  (One
+// tile per SM, which cuts the partials every block sums by 40%, measured 60 us per bench step
+// slower than 256 tiles: the update's latency wants the blocks.)
 constexpr int ARN_MIN_TILE = 256;
-constexpr int ARN_MAX_TILES = 152;
+constexpr int ARN_MAX_TILES = 256;
 int arn_tile_rows(int n) {
     const int64_t t = ((int64_t)n + ARN_MAX_TILES - 1) / ARN_MAX_TILES;
-    return (int)std::max<int64_t>(ARN_MIN_TILE, (t + 31) / 32 * 32);
+    return (int)std::max<int64_t>(ARN_MIN_TILE, (t + ARN_MIN_TILE - 1) / ARN_MIN_TILE * ARN_MIN_TILE);
 }
 int arn_tiles(int n) { return (int)blocks_for(n, arn_tile_rows(n)); }
 
