@@ -977,13 +977,18 @@ __global__ void k_gal_compact(int nc, const int32_t* __restrict__ poff, const in
 // Expansion, ordering and summation of one coarse row in one warp, in shared memory: the
 // lanes enumerate the row's (Q entry, B entry) pairs in order, each writing the products of
 // its pair at their position in the definition order (a warp prefix sum over the pairs'
-// product counts); the (J, position) keys are sorted by a bitonic network and every run of
-// equal J is summed in position order.  Rows are handled by a first kernel with room for
+// product counts).  The products are then taken in chunks of 32 in that order: the lanes
+// of a chunk that share a J are summed by the lowest one, in lane order, onto J's running
+// sum (a slot in order of first appearance, found through a small open-addressing table),
+// so every J sums its products in definition order; the slots are finally ranked by J.
+// Rows are handled by a first kernel with room for
 // GAL_CAP_S products per warp (most rows); longer rows go to a list that a second kernel
 // accumulates in a hash table (below), and beyond its capacity through global memory
 // with a quadratic scan.
 constexpr int GAL_WARPS_S = 4;
-constexpr int GAL_CAP_S = 256;
+constexpr int GAL_CAP_S = 256;  // a power of two: also the slots of the row's J table
+constexpr int GAL_CAP_LOG = 8;
+static_assert((1 << GAL_CAP_LOG) == GAL_CAP_S, "J table size");
 constexpr int GAL_BLOCKS_L = 608;
 
 template <typename T>
@@ -1005,10 +1010,12 @@ struct GalArgs {
     uint8_t* head;
 };
 
-// One coarse row I in one warp.  local: keys/svb/svt in shared memory (np <= capacity),
-// else the products go to the global product space.
+// One coarse row I in one warp.  local: sJ/svb/svt (products, then the row's slots), hkey
+// and hval (the J table) in shared memory, GAL_CAP_S entries each (np <= GAL_CAP_S); else
+// the products go to the global product space.
 template <typename T>
-__device__ void gal_row(const GalArgs<T>& a, int I, bool local, unsigned long long* keys, T* svb, T* svt) {
+__device__ void gal_row(const GalArgs<T>& a, int I, bool local, int* sJ, T* svb, T* svt, int* hkey,
+                        unsigned char* hval) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int o = a.poff[I], np = a.poff[I + 1] - o;
@@ -1057,7 +1064,7 @@ __device__ void gal_row(const GalArgs<T>& a, int I, bool local, unsigned long lo
                     const int J = a.pcol[(int64_t)j * a.c + sl];
                     const int e = pos0 + sl;
                     if (local) {
-                        keys[e] = ((unsigned long long)(unsigned)J << 32) | (unsigned)e;
+                        sJ[e] = J;
                         svb[e] = mul_rn(qb, pv);
                         svt[e] = mul_rn(qt, pv);
                     } else {
@@ -1072,48 +1079,68 @@ __device__ void gal_row(const GalArgs<T>& a, int I, bool local, unsigned long lo
     }
     __syncwarp();
     if (local) {
-        int N = 32;
-        while (N < np) N <<= 1;
-        for (int e = np + lane; e < N; e += 32) keys[e] = ~0ull;
+        for (int e = lane; e < GAL_CAP_S; e += 32) hkey[e] = 0;  // key J + 1; 0 = free
         __syncwarp();
-        for (int k = 2; k <= N; k <<= 1) {
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int e = lane; e < N; e += 32) {
-                    const int pe = e ^ jj;
-                    if (pe > e) {
-                        const unsigned long long x = keys[e], y = keys[pe];
-                        const bool up = (e & k) == 0;
-                        if ((x > y) == up) {
-                            keys[e] = y;
-                            keys[pe] = x;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        int ub = 0;
+        int U = 0;  // slots so far (U <= e0: each slot took at least one earlier product)
         for (int e0 = 0; e0 < np; e0 += 32) {
             const int e = e0 + lane;
-            const unsigned Je = e < np ? (unsigned)(keys[e] >> 32) : 0u;
-            const bool hd = e < np && (e == 0 || (unsigned)(keys[e - 1] >> 32) != Je);
-            const unsigned bal = __ballot_sync(0xffffffffu, hd);
-            if (hd) {
-                const int rank = ub + __popc(bal & lt);
-                const int ps = (int)(keys[e] & 0xffffffffu);
-                T sb = svb[ps], st = svt[ps];
-                for (int e2 = e + 1; e2 < np && (unsigned)(keys[e2] >> 32) == Je; ++e2) {
-                    const int pos = (int)(keys[e2] & 0xffffffffu);
+            const int J = e < np ? sJ[e] : -1 - lane;
+            const unsigned grp = __match_any_sync(0xffffffffu, J);
+            const bool leader = e < np && (grp & lt) == 0u;
+            bool claimed = false;
+            unsigned h = 0;
+            T sb = T(0), st = T(0);
+            if (leader) {
+                h = ((unsigned)J * 2654435761u) >> (32 - GAL_CAP_LOG);
+                for (;;) {  // ends: the table has a free entry while U < GAL_CAP_S
+                    const int k = hkey[h];
+                    if (k == J + 1) break;
+                    if (k == 0 && atomicCAS(&hkey[h], 0, J + 1) == 0) {
+                        claimed = true;
+                        break;
+                    }
+                    h = (h + 1) & (GAL_CAP_S - 1);
+                }
+                if (claimed) {
+                    sb = svb[e];
+                    st = svt[e];
+                } else {  // J's slot from an earlier chunk (index < e0)
+                    const int u = hval[h];
+                    sb = add_rn(svb[u], svb[e]);
+                    st = add_rn(svt[u], svt[e]);
+                }
+                for (unsigned m = grp & (grp - 1u); m; m &= m - 1u) {
+                    const int pos = e0 + __ffs(m) - 1;
                     sb = add_rn(sb, svb[pos]);
                     st = add_rn(st, svt[pos]);
                 }
-                a.uJ[o + rank] = (int32_t)Je;
-                a.ubv[o + rank] = sb;
-                a.utv[o + rank] = st;
             }
-            ub += __popc(bal);
+            const unsigned cb = __ballot_sync(0xffffffffu, claimed);
+            __syncwarp();  // this chunk's products are read before slots overwrite them
+            if (leader) {
+                int u;
+                if (claimed) {
+                    u = U + __popc(cb & lt);  // < e0 + 32: a position already read
+                    hval[h] = (unsigned char)u;
+                    sJ[u] = J;
+                } else {
+                    u = hval[h];
+                }
+                svb[u] = sb;
+                svt[u] = st;
+            }
+            U += __popc(cb);
+            __syncwarp();
         }
-        if (lane == 0) a.ucnt[I] = ub;
+        for (int u = lane; u < U; u += 32) {  // slot u goes to position rank(J) of the row
+            const int Ju = sJ[u];
+            int rank = 0;
+            for (int v = 0; v < U; ++v) rank += sJ[v] < Ju;
+            a.uJ[o + rank] = (int32_t)Ju;
+            a.ubv[o + rank] = svb[u];
+            a.utv[o + rank] = svt[u];
+        }
+        if (lane == 0) a.ucnt[I] = U;
         __syncwarp();
         return;
     }
@@ -1157,8 +1184,9 @@ template <typename T>
 __global__ void __launch_bounds__(GAL_WARPS_S * 32)
     k_gal_small(const __grid_constant__ GalArgs<T> a, int32_t* __restrict__ list, int* __restrict__ nlist) {
     pdl_begin();
-    __shared__ unsigned long long keys[GAL_WARPS_S][GAL_CAP_S];
+    __shared__ int sJ[GAL_WARPS_S][GAL_CAP_S], hkey[GAL_WARPS_S][GAL_CAP_S];
     __shared__ T svb[GAL_WARPS_S][GAL_CAP_S], svt[GAL_WARPS_S][GAL_CAP_S];
+    __shared__ unsigned char hval[GAL_WARPS_S][GAL_CAP_S];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int I = blockIdx.x * GAL_WARPS_S + wid;
     if (I >= a.nc) return;
@@ -1167,7 +1195,7 @@ __global__ void __launch_bounds__(GAL_WARPS_S * 32)
         if (lane == 0) list[atomicAdd(nlist, 1)] = I;
         return;
     }
-    gal_row<T>(a, I, true, keys[wid], svb[wid], svt[wid]);
+    gal_row<T>(a, I, true, sJ[wid], svb[wid], svt[wid], hkey[wid], hval[wid]);
 }
 
 // Long rows by accumulation instead of sorting: the products of each batch of 32 (Q, B)
@@ -1332,7 +1360,7 @@ __global__ void __launch_bounds__(32) k_gal_large(const __grid_constant__ GalArg
     const int cnt = *nlist;
     for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
         const int I = list[k];
-        if (!gal_row_hash<T>(a, I, hkey, hvb, hvt, sJ, sb_, st_, skeys)) gal_row<T>(a, I, false, nullptr, nullptr, nullptr);
+        if (!gal_row_hash<T>(a, I, hkey, hvb, hvt, sJ, sb_, st_, skeys)) gal_row<T>(a, I, false, nullptr, nullptr, nullptr, nullptr, nullptr);
     }
 }
 
