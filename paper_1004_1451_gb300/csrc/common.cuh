@@ -295,6 +295,18 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
+// w / h rounded to nearest, given r = 1 / h rounded to nearest: q0 = w r lies within an ulp
+// of the quotient, the remainder w - q0 h is exact in one fma, and q0 + rem r rounded once is
+// the correctly rounded quotient (Markstein's theorem: P. Markstein, IBM J. Res. Dev. 34(1),
+// 1990).  Three FP64 operations instead of a full division, for the many quotients by one
+// divisor; it holds for quotients in the normal range.  A zero remainder keeps q0, and with
+// it the sign of a zero quotient.
+__device__ __forceinline__ double div_by_recip(double w, double h, double r) {
+    const double q0 = __dmul_rn(w, r);
+    const double rem = __fma_rn(-q0, h, w);
+    return rem == 0.0 ? q0 : __fma_rn(rem, r, q0);
+}
+
 // ------------------------------------------------------------------ host helpers
 void exclusive_scan(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s);  // d_out has n+1 entries
 int32_t read_int(const int32_t* d_p, cudaStream_t s);

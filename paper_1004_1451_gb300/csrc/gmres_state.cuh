@@ -8,7 +8,7 @@ namespace bamg {
 constexpr int GMRES_MMAX = 256;
 
 struct GmresLayout {
-    int h1, h2, R, cs, sn, g, y, nrm2, est, hn, total;
+    int h1, h2, R, cs, sn, g, y, nrm2, est, hn, rhn, total;  // est, hn adjacent (read together)
     __host__ __device__ explicit GmresLayout(int m) {
         int o = 0;
         h1 = o;
@@ -28,6 +28,7 @@ struct GmresLayout {
         nrm2 = o++;
         est = o++;
         hn = o++;
+        rhn = o++;  // 1 / hn
         total = o;
     }
 };

@@ -1202,14 +1202,18 @@ void residual_norms(const MatView<double>& B, const double* x, double* d_out, do
     BAMG_LAUNCH(k_reduce_cols, blocks_for(RESNORM_SUMS, 4), 128, 0, s, nb, RESNORM_SUMS, d_partial, d_out);  // a warp per sum
 }
 
-// y = x * num or x / num with num = d_num[num_idx] (a device scalar).
+// y = x * num or x / num with num = d_num[num_idx] (a device scalar); the quotients are
+// correctly rounded from one reciprocal per block.
 __global__ void k_scale_vec(int n, const double* __restrict__ x, const double* __restrict__ d_num, int num_idx,
                             int reciprocal, double* __restrict__ y) {
     pdl_begin();
+    __shared__ double s_r;
+    const double a = d_num[num_idx];
+    if (reciprocal && threadIdx.x == 0) s_r = a != 0.0 ? 1.0 / a : 0.0;
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double a = d_num[num_idx];
-    y[i] = reciprocal ? (a != 0.0 ? x[i] / a : 0.0) : x[i] * a;
+    y[i] = reciprocal ? (a != 0.0 ? div_by_recip(x[i], a, s_r) : 0.0) : x[i] * a;
 }
 void scale_vec(int n, double* x, const double* d_num, int num_idx, bool reciprocal, double* y, cudaStream_t s) {
     BAMG_LAUNCH(k_scale_vec, blocks_for(n, 256), 256, 0, s, n, x, d_num, num_idx, reciprocal ? 1 : 0, y);
@@ -1224,6 +1228,7 @@ __global__ void k_gmres_init(double* __restrict__ st, int m) {
     for (int i = 0; i <= m; ++i) st[L.g + i] = 0.0;
     st[L.g] = beta;
     st[L.hn] = beta;
+    st[L.rhn] = beta != 0.0 ? 1.0 / beta : 0.0;
     st[L.est] = beta;
 }
 void gmres_init(double* d_state, int m, cudaStream_t s) { BAMG_LAUNCH(k_gmres_init, 1, 32, 0, s, d_state, m); }
@@ -1254,35 +1259,30 @@ void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s) { BAMG_LAUNCH(
 
 // ---------------------------------------------------------------- graph-replayable Arnoldi step
 // The kernels below read the Arnoldi index j from device memory (*dj), so one captured
-// graph serves every iteration of a cycle: v_j -> V-cycle input, z_j <- V-cycle output,
-// w = V[j+1] = B z_j, two classical Gram-Schmidt passes, ||w||, the Givens update,
-// v_{j+1} = w / ||w||, and j <- j + 1.
+// graph serves every iteration of a cycle: v_j = w_{j-1} / ||w_{j-1}|| -> V-cycle input,
+// z_j <- V-cycle output, w = V[j+1] = B z_j, two classical Gram-Schmidt passes, ||w||, the
+// Givens update and j <- j + 1 (w stays in V[j+1] unscaled until the next step scales it,
+// so the step's last kernel is one block).
 template <typename T>
-__global__ void k_v_to_in(int n, const double* __restrict__ V, const int* __restrict__ dj, T* __restrict__ vin) {
+__global__ void k_v_to_in(int n, double* __restrict__ V, const int* __restrict__ dj, const double* __restrict__ hr,
+                          T* __restrict__ vin) {
     pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) vin[i] = (T)V[(int64_t)(*dj) * n + i];
+    const int j = *dj;
+    if (i >= n) return;
+    double* v = V + (int64_t)j * n;
+    double vi = v[i];
+    if (j > 0) {  // v_0 arrives scaled from the start of the cycle; hr = (||w||, 1 / ||w||)
+        const double h = hr[0];
+        vi = h != 0.0 ? div_by_recip(vi, h, hr[1]) : 0.0;  // the correctly rounded quotient
+        v[i] = vi;
+    }
+    vin[i] = (T)vi;
 }
 __global__ void k_inc_j(int* dj) {
     pdl_begin();
     if (threadIdx.x == 0 && blockIdx.x == 0) *dj += 1;
 }
-// j += 1 at the end of a step of the device-side loop, and the loop's condition: go on
-// while j < ctl[2], h_{j+1,j} != 0 and estimate * kappa > tol ||x||_1 (the host's test
-// for a true residual check, with the same operands).
-__global__ void k_step_end(int* dj, const double* __restrict__ st, int m, const double* __restrict__ ctl,
-                           cudaGraphConditionalHandle cond) {
-    pdl_begin();
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        const GmresLayout L(m);
-        const int jn = *dj + 1;
-        *dj = jn;
-        const double est = st[L.est], hn = st[L.hn];
-        const bool stop = jn >= (int)ctl[2] || hn == 0.0 || est * ctl[0] <= ctl[1];
-        cudaGraphSetConditional(cond, stop ? 0u : 1u);
-    }
-}
-
 // Fused Arnoldi kernels over row tiles (one block each).  The column sums of the per-tile
 // dot products are formed again by every block that needs them (warp per column, lanes
 // strided over the tiles, the same order in every block), so the reductions need no kernel
@@ -1373,7 +1373,7 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(int n, int tile, const 
 __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __restrict__ dj, double* __restrict__ st,
                                  int m, const double* __restrict__ Pn, int nb, int stride) {
     pdl_begin();
-    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX], s_nrm2, s_hn;
+    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX], s_nrm2, s_hn, s_rhn;
     GmresLayout L(m);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = *dj;
@@ -1382,6 +1382,7 @@ __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __res
         if (threadIdx.x == 0) {
             s_nrm2 = nn;
             s_hn = sqrt(nn);
+            s_rhn = s_hn != 0.0 ? 1.0 / s_hn : 0.0;
             if (blockIdx.x == 0) st[L.nrm2] = nn;
         }
     }
@@ -1420,10 +1421,65 @@ __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __res
         __syncthreads();
         for (int q = threadIdx.x; q <= j; q += blockDim.x) st[L.R + q + (int64_t)j * m] = col[q];
     }
-    if (i < n) {  // w / ||w|| with the block's one square root (the division as in the plain algorithm)
+    if (i < n) {  // w / ||w|| with the block's one square root and reciprocal (correctly rounded quotients)
         double* w = V + (int64_t)(j + 1) * n;
-        w[i] = s_hn != 0.0 ? w[i] / s_hn : 0.0;
+        w[i] = s_hn != 0.0 ? div_by_recip(w[i], s_hn, s_rhn) : 0.0;
     }
+}
+
+// Givens update of Hessenberg column j (one block) with ||w||^2 from the per-tile partial
+// sums, then j += 1; with a conditional handle also the device-side loop's condition: go
+// on while j < ctl[2], h_{j+1,j} != 0 and estimate * kappa > tol ||x||_1 (the host's test
+// for a true residual check, with the same operands).
+__global__ void k_givens_end(int* __restrict__ dj, double* __restrict__ st, int m, const double* __restrict__ Pn,
+                             int nb, int stride, const double* __restrict__ ctl, cudaGraphConditionalHandle cond) {
+    pdl_begin();
+    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX], s_nrm2;
+    GmresLayout L(m);
+    const int j = *dj;
+    if (threadIdx.x < 32) {
+        const double nn = arn_colsum(Pn, nb, stride, 0, threadIdx.x);
+        if (threadIdx.x == 0) s_nrm2 = nn;
+    }
+    for (int q = threadIdx.x; q <= j; q += blockDim.x) {
+        col[q] = st[L.h1 + q] + st[L.h2 + q];
+        if (q < j) {
+            cs[q] = st[L.cs + q];
+            sn[q] = st[L.sn + q];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double nn = s_nrm2, hn = sqrt(nn);
+        st[L.nrm2] = nn;
+        col[j + 1] = hn;
+        for (int q = 0; q < j; ++q) {
+            const double c = cs[q], s = sn[q];
+            const double a = col[q], b = col[q + 1];
+            col[q] = c * a + s * b;
+            col[q + 1] = -s * a + c * b;
+        }
+        const double a = col[j], b = col[j + 1];
+        const double den = hypot(a, b);
+        const double c = den == 0.0 ? 1.0 : a / den, s = den == 0.0 ? 0.0 : b / den;
+        st[L.cs + j] = c;
+        st[L.sn + j] = s;
+        col[j] = c * a + s * b;
+        const double gj = st[L.g + j];
+        st[L.g + j + 1] = -s * gj;
+        st[L.g + j] = c * gj;
+        const double est = fabs(st[L.g + j + 1]);
+        st[L.est] = est;
+        st[L.hn] = hn;
+        st[L.rhn] = hn != 0.0 ? 1.0 / hn : 0.0;
+        *dj = j + 1;
+        if (cond) {
+            const bool stop = j + 1 >= (int)ctl[2] || hn == 0.0 || est * ctl[0] <= ctl[1];
+            cudaGraphSetConditional(cond, stop ? 0u : 1u);
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q <= j; q += blockDim.x) st[L.R + q + (int64_t)j * m] = col[q];
 }
 
 template <typename T>
@@ -1434,7 +1490,7 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
     GmresLayout L(m);
     const unsigned g = blocks_for(n, 256);
     const int stride = m + 1;
-    BAMG_LAUNCH_PDL(k_v_to_in<T>, g, 256, 0, s, n, V, dj, vin);
+    BAMG_LAUNCH_PDL(k_v_to_in<T>, g, 256, 0, s, n, V, (const int*)dj, (const double*)(st + L.hn), vin);
     vcycle<T>(lv, pinv, omega, nu_pre, nu_post, s, Z, dj);
     const int tile = arn_tile_rows(n), nt = arn_tiles(n);
     double* Pa = partial;
@@ -1445,13 +1501,8 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
                     Pb, stride, 0);
     BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pb, nt, st + L.h2,
                     Pa, stride, 1);
-    BAMG_LAUNCH_PDL(k_givens_scale_j, g, 256, 0, s, n, V, (const int*)dj, st, m, (const double*)Pa, nt, stride);
-    if (cond) {
-        BAMG_LAUNCH_PDL(k_step_end, 1, 32, 0, s, dj, (const double*)st, m, ctl, cond);
-    } else {
-        BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        BAMG_LAUNCH_PDL(k_inc_j, 1, 32, 0, s, dj);
-    }
+    BAMG_LAUNCH_PDL(k_givens_end, 1, 64, 0, s, dj, st, m, (const double*)Pa, nt, stride, ctl, cond);
+    if (!cond) BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
 template void arnoldi_step_graphable<float>(int, const MatView<double>&, double*, float*, float*, float*, int*,
@@ -1642,7 +1693,7 @@ void ritz_closest_to_zero(const double* H, int ldh, int k, double* eta, cudaStre
 // FGMRES Arnoldi steps of one restart cycle in a single cooperative launch: the same phases
 // as the captured step (v_j to the V-cycle's precision, the V-cycle's grid levels, the
 // single-block tail on block 0, the FP64 SpMV with the first Gram-Schmidt dots, two update
-// passes, the Givens update with the scaling of v_{j+1}, the stop test of k_step_end), with
+// passes, the Givens update with the scaling of v_{j+1}, the stop test of k_givens_end), with
 // a grid-wide barrier between phases instead of a kernel boundary.  The per-row arithmetic,
 // the row tiles of the Arnoldi kernels and every reduction order are those of the separate
 // kernels, so the iterates are bit-identical.  Vectors written inside the kernel are read
@@ -1946,18 +1997,19 @@ __global__ void __launch_bounds__(PERSIST_THREADS, 1) k_arnoldi_cycle(const __gr
                 st[GL.g + j] = c * gj;
                 st[GL.est] = fabs(st[GL.g + j + 1]);
                 st[GL.hn] = hn;
+                st[GL.rhn] = hn != 0.0 ? 1.0 / hn : 0.0;
             }
             __syncthreads();
             for (int q = threadIdx.x; q <= j; q += blockDim.x) st[GL.R + q + (int64_t)j * a.m] = gcol[q];
         }
-        {  // w / ||w||, the square root formed once per thread (an FP64 square root is a long
-           // instruction sequence at GB300's FP64 rate); the division stays, as in the plain
-           // algorithm's w / h_{j+1,j}
-            const double hn = sqrt(s_nrm2);
-            for (int i = gtid; i < n; i += gsz) w[i] = hn != 0.0 ? w[i] / hn : 0.0;
+        {  // w / ||w||, the square root and the reciprocal formed once per thread (both are long
+           // instruction sequences at GB300's FP64 rate); the quotients correctly rounded, as
+           // the plain algorithm's w / h_{j+1,j}
+            const double hn = sqrt(s_nrm2), rhn = hn != 0.0 ? 1.0 / hn : 0.0;
+            for (int i = gtid; i < n; i += gsz) w[i] = hn != 0.0 ? div_by_recip(w[i], hn, rhn) : 0.0;
         }
         if (!grid_sync(a.bar, a.err)) return;
-        // ---- the stop test of k_step_end, taken by every block on the same values
+        // ---- the stop test of k_givens_end, taken by every block on the same values
         const int jn = j + 1;
         const double est = *(volatile double*)(a.st + GL.est), hn = *(volatile double*)(a.st + GL.hn);
         const bool stop = jn >= (int)a.ctl[2] || hn == 0.0 || est * a.ctl[0] <= a.ctl[1];
