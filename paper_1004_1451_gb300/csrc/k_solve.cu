@@ -559,7 +559,8 @@ constexpr int CTAIL_THREADS = 512;
 constexpr int CTAIL_MAX_N = CTAIL_CS * CTAIL_THREADS;  // at most one row per thread on every level
 constexpr size_t CTAIL_VEC_MAX = 96 * 1024;            // the replicated vectors of all tail levels
 constexpr int CTAIL_STATIC = 12 * 1024;                // static shared memory (arguments, slices, copy list)
-constexpr int CTAIL_JOBS = 10 * TAIL_MAX_LEVELS;       // staged arrays per block
+constexpr int CTAIL_JOBS = 16 * TAIL_MAX_LEVELS;       // copy jobs per block
+constexpr int CTAIL_SUBJOB = 8192;                     // bytes per copy job at most (a multiple of 16)
 
 template <typename T>
 struct CTailArgs {
@@ -635,17 +636,18 @@ __device__ __forceinline__ void push_all(double* p, double v) {
 // Room for `bytes` copied from src into a 16-byte aligned region: the copy starts at the
 // region's start plus (src mod 16), so source and destination agree modulo 16.
 __host__ __device__ constexpr size_t stage_room(size_t bytes) { return al16(bytes + 16); }
-// Copy job list: the block's threads copy [src, src + bytes) to dst, 16 bytes at a time
-// where both are on a 16-byte boundary, 4 bytes at a time for the ragged ends.
-__device__ __forceinline__ void run_copy(const CopyJob& j) {
+// Copy job by the 32 lanes of one warp: [src, src + bytes) to dst, 16 bytes at a time where
+// both are on a 16-byte boundary, 4 bytes at a time for the ragged ends.  (The block's warps
+// take whole jobs, so issuing a job costs no block-wide pass; a staged array becomes jobs of
+// at most CTAIL_SUBJOB bytes, so a long one still spreads over the warps.)
+__device__ __forceinline__ void run_copy_warp(const CopyJob& j, int lane) {
     const uintptr_t s0 = reinterpret_cast<uintptr_t>(j.src);
     const int head = (int)(((16 - (s0 & 15)) & 15) < (uintptr_t)j.bytes ? ((16 - (s0 & 15)) & 15) : j.bytes);
     const int n16 = (j.bytes - head) >> 4;
     const int tail0 = head + (n16 << 4);
-    for (int k = threadIdx.x; k < (head >> 2); k += blockDim.x) cp_async4(j.dst + 4 * k, j.src + 4 * k);
-    for (int k = threadIdx.x; k < n16; k += blockDim.x) cp_async16(j.dst + head + 16 * k, j.src + head + 16 * k);
-    for (int k = threadIdx.x; k < ((j.bytes - tail0) >> 2); k += blockDim.x)
-        cp_async4(j.dst + tail0 + 4 * k, j.src + tail0 + 4 * k);
+    for (int k = lane; k < (head >> 2); k += 32) cp_async4(j.dst + 4 * k, j.src + 4 * k);
+    for (int k = lane; k < n16; k += 32) cp_async16(j.dst + head + 16 * k, j.src + head + 16 * k);
+    for (int k = lane; k < ((j.bytes - tail0) >> 2); k += 32) cp_async4(j.dst + tail0 + 4 * k, j.src + tail0 + 4 * k);
 }
 
 template <typename T>
@@ -655,7 +657,7 @@ __global__ void __cluster_dims__(CTAIL_CS, 1, 1) __launch_bounds__(CTAIL_THREADS
     __shared__ __align__(16) unsigned char sa_raw[sizeof(CTailArgs<T>)];
     __shared__ CSlice<T> sl[TAIL_MAX_LEVELS];
     __shared__ CopyJob jobs[CTAIL_JOBS];
-    __shared__ int bnd[TAIL_MAX_LEVELS][4];  // rp[lo], rp[hi], qrp[clo], qrp[chi]
+    __shared__ int plan[TAIL_MAX_LEVELS][4];  // per level: bytes to stage, arrays, offset (-1: not staged), job
     __shared__ int njobs;
     const int tid = threadIdx.x;
     {
@@ -667,101 +669,122 @@ __global__ void __cluster_dims__(CTAIL_CS, 1, 1) __launch_bounds__(CTAIL_THREADS
     const CTailArgs<T>& a = *reinterpret_cast<const CTailArgs<T>*>(sa_raw);
     const int q = (int)cluster_rank(), L = a.nl - 1;
     auto row_lo = [&](int l, int r) { return (int)(((int64_t)a.lv[l].B.n * r) / CTAIL_CS); };
-    // ---- own rows and their entry ranges.  The matrices were written during the setup, long
-    // before this launch, so they are read before the wait on the preceding kernel.
+    // ---- the staging plan, one thread per level (the matrices were written during the setup,
+    // long before this launch, so they are read before the wait on the preceding kernel): the
+    // level's own rows, their entry ranges and the arrays to stage; then thread 0 places the
+    // levels in order while the budget lasts (global memory beyond); then each level's thread
+    // fills in its copy jobs and shared-memory pointers.
+    CSlice<T> c;
+    const unsigned char* src[10];
+    size_t bytes[10];
+    int na = 0;
     if (tid < a.nl) {
-        const int l = tid, lo = row_lo(l, q), hi = row_lo(l, q + 1);
+        const int l = tid;
+        const VLevel<T>& g = a.lv[l];
+        const int lo = row_lo(l, q), hi = row_lo(l, q + 1), rows = hi - lo, n = g.B.n;
+        c.lo = lo;
+        c.hi = hi;
+        c.nz0 = c.qz0 = 0;
+        c.rp = c.ci = c.pcol = c.pcnt = c.qrp = c.qci = nullptr;
+        c.v = c.dinv = c.pval = c.qv = c.pinv = nullptr;
         if (l < L) {
-            const int clo = row_lo(l + 1, q), chi = row_lo(l + 1, q + 1);
-            bnd[l][0] = a.lv[l].B.rp[lo];
-            bnd[l][1] = a.lv[l].B.rp[hi];
-            bnd[l][2] = a.lv[l].qrp[clo];
-            bnd[l][3] = a.lv[l].qrp[chi];
+            const int clo = row_lo(l + 1, q), chi = row_lo(l + 1, q + 1), pc = g.P.c;
+            const int nz0 = g.B.rp[lo], nz1 = g.B.rp[hi], qz0 = g.qrp[clo], qz1 = g.qrp[chi];
+            c.nz0 = nz0;
+            c.qz0 = qz0;
+            c.rp = g.B.rp + lo;
+            c.ci = g.B.ci + nz0;
+            c.v = g.B.v + nz0;
+            c.dinv = g.dinv;
+            c.pcol = g.P.pcol + (int64_t)lo * pc;
+            c.pval = g.P.pval + (int64_t)lo * pc;
+            c.pcnt = g.P.pcnt + lo;
+            c.qrp = g.qrp + clo;
+            c.qci = g.qci + qz0;
+            c.qv = g.qv + qz0;
+            const unsigned char* s_[10] = {(const unsigned char*)c.rp,   (const unsigned char*)c.ci,
+                                           (const unsigned char*)c.v,    (const unsigned char*)c.dinv,
+                                           (const unsigned char*)c.pcol, (const unsigned char*)c.pval,
+                                           (const unsigned char*)c.pcnt, (const unsigned char*)c.qrp,
+                                           (const unsigned char*)c.qci,  (const unsigned char*)c.qv};
+            const size_t b_[10] = {4 * (size_t)(rows + 1),        4 * (size_t)(nz1 - nz0),
+                                   sizeof(T) * (size_t)(nz1 - nz0), sizeof(T) * (size_t)n,
+                                   4 * (size_t)rows * pc,          sizeof(T) * (size_t)rows * pc,
+                                   4 * (size_t)rows,               4 * (size_t)(chi - clo + 1),
+                                   4 * (size_t)(qz1 - qz0),        sizeof(T) * (size_t)(qz1 - qz0)};
+            for (int k = 0; k < 10; ++k) {
+                src[k] = s_[k];
+                bytes[k] = b_[k];
+            }
+            na = 10;
+        } else if (a.pinv) {
+            c.pinv = a.pinv + (int64_t)lo * n;
+            src[0] = (const unsigned char*)c.pinv;
+            bytes[0] = sizeof(T) * (size_t)rows * n;
+            na = 1;
         }
+        size_t need = 0;
+        int nz = 0;
+        for (int k = 0; k < na; ++k) {
+            need += stage_room(bytes[k]);
+            nz += (int)((bytes[k] + CTAIL_SUBJOB - 1) / CTAIL_SUBJOB);
+        }
+        plan[l][0] = na > 0 ? (int)need : -1;
+        plan[l][1] = nz;
     }
     __syncthreads();
-    if (tid == 0) {  // the staging plan: levels in order while the budget lasts, global memory beyond
+    if (tid == 0) {
         size_t off = (size_t)a.vec_bytes;
         const size_t budget = (size_t)a.smem_bytes;
         int nj = 0;
         for (int l = 0; l <= L; ++l) {
-            const VLevel<T>& g = a.lv[l];
-            const int lo = row_lo(l, q), hi = row_lo(l, q + 1), rows = hi - lo, n = g.B.n;
-            CSlice<T> c;
-            c.lo = lo;
-            c.hi = hi;
-            c.nz0 = c.qz0 = 0;
-            c.rp = c.ci = c.pcol = c.pcnt = c.qrp = c.qci = nullptr;
-            c.v = c.dinv = c.pval = c.qv = c.pinv = nullptr;
-            const unsigned char* src[10];
-            size_t bytes[10];
-            int na = 0;
-            if (l < L) {
-                const int nz0 = bnd[l][0], nz1 = bnd[l][1], qz0 = bnd[l][2], qz1 = bnd[l][3];
-                const int clo = row_lo(l + 1, q), chi = row_lo(l + 1, q + 1), pc = g.P.c;
-                c.nz0 = nz0;
-                c.qz0 = qz0;
-                c.rp = g.B.rp + lo;
-                c.ci = g.B.ci + nz0;
-                c.v = g.B.v + nz0;
-                c.dinv = g.dinv;
-                c.pcol = g.P.pcol + (int64_t)lo * pc;
-                c.pval = g.P.pval + (int64_t)lo * pc;
-                c.pcnt = g.P.pcnt + lo;
-                c.qrp = g.qrp + clo;
-                c.qci = g.qci + qz0;
-                c.qv = g.qv + qz0;
-                const unsigned char* s_[10] = {(const unsigned char*)c.rp,   (const unsigned char*)c.ci,
-                                               (const unsigned char*)c.v,    (const unsigned char*)c.dinv,
-                                               (const unsigned char*)c.pcol, (const unsigned char*)c.pval,
-                                               (const unsigned char*)c.pcnt, (const unsigned char*)c.qrp,
-                                               (const unsigned char*)c.qci,  (const unsigned char*)c.qv};
-                const size_t b_[10] = {4 * (size_t)(rows + 1),        4 * (size_t)(nz1 - nz0),
-                                       sizeof(T) * (size_t)(nz1 - nz0), sizeof(T) * (size_t)n,
-                                       4 * (size_t)rows * pc,          sizeof(T) * (size_t)rows * pc,
-                                       4 * (size_t)rows,               4 * (size_t)(chi - clo + 1),
-                                       4 * (size_t)(qz1 - qz0),        sizeof(T) * (size_t)(qz1 - qz0)};
-                for (int k = 0; k < 10; ++k) {
-                    src[k] = s_[k];
-                    bytes[k] = b_[k];
-                }
-                na = 10;
-            } else if (a.pinv) {
-                c.pinv = a.pinv + (int64_t)lo * n;
-                src[0] = (const unsigned char*)c.pinv;
-                bytes[0] = sizeof(T) * (size_t)rows * n;
-                na = 1;
+            const int need = plan[l][0], nz = plan[l][1];
+            if (need >= 0 && off + (size_t)need <= budget && nj + nz <= CTAIL_JOBS) {
+                plan[l][2] = (int)off;
+                plan[l][3] = nj;
+                off += (size_t)need;
+                nj += nz;
+            } else {
+                plan[l][2] = -1;
             }
-            size_t need = 0;
-            for (int k = 0; k < na; ++k) need += stage_room(bytes[k]);
-            if (na > 0 && off + need <= budget && nj + na <= CTAIL_JOBS) {
-                unsigned char* d[10];
-                for (int k = 0; k < na; ++k) {
-                    d[k] = sm + off + (reinterpret_cast<uintptr_t>(src[k]) & 15);
-                    off += stage_room(bytes[k]);
-                    if (bytes[k] > 0) jobs[nj++] = CopyJob{src[k], d[k], (int)bytes[k]};
-                }
-                if (l < L) {
-                    c.rp = reinterpret_cast<const int32_t*>(d[0]);
-                    c.ci = reinterpret_cast<const int32_t*>(d[1]);
-                    c.v = reinterpret_cast<const T*>(d[2]);
-                    c.dinv = reinterpret_cast<const T*>(d[3]);
-                    c.pcol = reinterpret_cast<const int32_t*>(d[4]);
-                    c.pval = reinterpret_cast<const T*>(d[5]);
-                    c.pcnt = reinterpret_cast<const int32_t*>(d[6]);
-                    c.qrp = reinterpret_cast<const int32_t*>(d[7]);
-                    c.qci = reinterpret_cast<const int32_t*>(d[8]);
-                    c.qv = reinterpret_cast<const T*>(d[9]);
-                } else {
-                    c.pinv = reinterpret_cast<const T*>(d[0]);
-                }
-            }
-            sl[l] = c;
         }
         njobs = nj;
     }
     __syncthreads();
-    for (int k = 0; k < njobs; ++k) run_copy(jobs[k]);
+    if (tid < a.nl) {
+        const int l = tid;
+        if (plan[l][2] >= 0) {
+            size_t off = (size_t)plan[l][2];
+            int nj = plan[l][3];
+            unsigned char* d[10];
+            for (int k = 0; k < na; ++k) {
+                d[k] = sm + off + (reinterpret_cast<uintptr_t>(src[k]) & 15);
+                off += stage_room(bytes[k]);
+                for (size_t o = 0; o < bytes[k]; o += CTAIL_SUBJOB)  // o keeps src and dst congruent mod 16
+                    jobs[nj++] = CopyJob{src[k] + o, d[k] + o, (int)min((size_t)CTAIL_SUBJOB, bytes[k] - o)};
+            }
+            if (l < L) {
+                c.rp = reinterpret_cast<const int32_t*>(d[0]);
+                c.ci = reinterpret_cast<const int32_t*>(d[1]);
+                c.v = reinterpret_cast<const T*>(d[2]);
+                c.dinv = reinterpret_cast<const T*>(d[3]);
+                c.pcol = reinterpret_cast<const int32_t*>(d[4]);
+                c.pval = reinterpret_cast<const T*>(d[5]);
+                c.pcnt = reinterpret_cast<const int32_t*>(d[6]);
+                c.qrp = reinterpret_cast<const int32_t*>(d[7]);
+                c.qci = reinterpret_cast<const int32_t*>(d[8]);
+                c.qv = reinterpret_cast<const T*>(d[9]);
+            } else {
+                c.pinv = reinterpret_cast<const T*>(d[0]);
+            }
+        }
+        sl[l] = c;
+    }
+    __syncthreads();
+    {
+        const int wid = tid >> 5, nw = blockDim.x >> 5, lane = tid & 31;
+        for (int k = wid; k < njobs; k += nw) run_copy_warp(jobs[k], lane);
+    }
     pdl_begin();
     // ---- the first tail level's right-hand side (written by the preceding kernel)
     T* sbuf = reinterpret_cast<T*>(sm);
