@@ -1325,8 +1325,31 @@ __device__ __forceinline__ double arn_colsum(const double* __restrict__ P, int n
     for (int b = lane; b < nb; b += 32) s += P[(int64_t)b * stride + q];
     return warp_sum(s);
 }
+// The column sums of the per-tile partials (nb rows of `stride`), q < ncol, formed once by the
+// block of the grid that finishes last, in arn_colsum's order (so the totals are those every
+// block formed for itself before): every block counts itself on *cnt after its partials are
+// written and fenced; the last one sums and resets the count for the next kernel.  Every
+// thread of the block calls it.
+__device__ __forceinline__ void arn_last_block_sums(const double* P, int nb, int stride, int ncol,
+                                                    unsigned* __restrict__ cnt, double* __restrict__ tot) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(cnt, 1u) == (unsigned)gridDim.x - 1u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = wid; q < ncol; q += nw) {
+        double s = 0.0;
+        for (int b = lane; b < nb; b += 32) s += __ldcg(P + (int64_t)b * stride + q);
+        s = warp_sum(s);
+        if (lane == 0) tot[q] = s;
+    }
+    if (threadIdx.x == 0) *cnt = 0u;
+}
 // per-tile dots of the tile's rows of w with V[0..j] (self = 0) or with itself; the block
-// has just written w, so these reads hit the caches
+// has just written w, so these reads hit the caches.  Each writing lane fences after its last
+// partial (arn_last_block_sums reads them from another block).
 __device__ __forceinline__ void arn_tile_dots(const double* __restrict__ V, int n, int j, int r0, int cnt,
                                               const double* w, int self, double* __restrict__ Pout, int stride) {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1340,6 +1363,7 @@ __device__ __forceinline__ void arn_tile_dots(const double* __restrict__ V, int 
         acc = warp_sum(acc);
         if (lane == 0) Pout[(int64_t)blockIdx.x * stride + q] = acc;
     }
+    if (lane == 0 && wid < nv) __threadfence();  // once, after the warp's last partial
 }
 
 // w = V[j+1] = B z_j (FP64) and its per-tile dots with V[0..j]
@@ -1347,7 +1371,8 @@ template <typename TX>
 __global__ void __launch_bounds__(256) k_arn_spmv_dots(int n, int tile, const int32_t* __restrict__ rp,
                                                        const int32_t* __restrict__ ci, const double* __restrict__ bv,
                                                        const TX* __restrict__ z, const int* __restrict__ dj,
-                                                       double* __restrict__ V, double* __restrict__ Pout, int stride) {
+                                                       double* __restrict__ V, double* __restrict__ Pout, int stride,
+                                                       unsigned* __restrict__ ticket, double* __restrict__ tot) {
     pdl_begin();
     const int j = *dj;
     const int r0 = blockIdx.x * tile, cnt = min(tile, n - r0);
@@ -1358,23 +1383,31 @@ __global__ void __launch_bounds__(256) k_arn_spmv_dots(int n, int tile, const in
     }
     __syncthreads();
     arn_tile_dots(V, n, j, r0, cnt, w, 0, Pout, stride);
+    if (ticket) arn_last_block_sums(Pout, gridDim.x, stride, j + 1, ticket, tot);
 }
 
-// h = column sums of Pin (block 0 stores them at hout); w -= V[0..j] h; then the per-tile
-// dots of the new w with V[0..j] (next_self = 0) or with itself (next_self = 1)
+// h = column sums of Pin (block 0 stores them at hout), or with ticket the totals at hout that
+// the preceding kernel's last block formed; w -= V[0..j] h; then the per-tile dots of the new
+// w with V[0..j] (next_self = 0) or with itself (next_self = 1), with ticket summed by this
+// kernel's last block into tot
 __global__ void __launch_bounds__(256) k_arn_update_dots(int n, int tile, const int* __restrict__ dj,
                                                          double* __restrict__ V, const double* __restrict__ Pin,
                                                          int nb, double* __restrict__ hout, double* __restrict__ Pout,
-                                                         int stride, int next_self) {
+                                                         int stride, int next_self, unsigned* __restrict__ ticket,
+                                                         double* __restrict__ tot) {
     pdl_begin();
     __shared__ double sh[GMRES_MMAX + 1];
     const int j = *dj;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int q = wid; q <= j; q += nw) {
-        const double hq = arn_colsum(Pin, nb, stride, q, lane);
-        if (lane == 0) {
-            sh[q] = hq;
-            if (blockIdx.x == 0) hout[q] = hq;
+    if (ticket) {
+        for (int q = threadIdx.x; q <= j; q += blockDim.x) sh[q] = hout[q];
+    } else {
+        for (int q = wid; q <= j; q += nw) {
+            const double hq = arn_colsum(Pin, nb, stride, q, lane);
+            if (lane == 0) {
+                sh[q] = hq;
+                if (blockIdx.x == 0) hout[q] = hq;
+            }
         }
     }
     __syncthreads();
@@ -1389,6 +1422,7 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(int n, int tile, const 
     }
     __syncthreads();
     arn_tile_dots(V, n, j, r0, cnt, w, next_self, Pout, stride);
+    if (ticket) arn_last_block_sums(Pout, gridDim.x, stride, next_self ? 1 : j + 1, ticket, tot);
 }
 
 // Givens update (one thread) fused with v_{j+1} = w / ||w||: every block forms ||w|| from the
@@ -1450,20 +1484,16 @@ __global__ void k_givens_scale_j(int n, double* __restrict__ V, const int* __res
     }
 }
 
-// Givens update of Hessenberg column j (one block) with ||w||^2 from the per-tile partial
-// sums, then j += 1; with a conditional handle also the device-side loop's condition: go
-// on while j < ctl[2], h_{j+1,j} != 0 and estimate * kappa > tol ||x||_1 (the host's test
-// for a true residual check, with the same operands).
-__global__ void k_givens_end(int* __restrict__ dj, double* __restrict__ st, int m, const double* __restrict__ Pn,
-                             int nb, int stride, const double* __restrict__ ctl, cudaGraphConditionalHandle cond) {
+// Givens update of Hessenberg column j (one block) with ||w||^2 at st[nrm2] (summed by the
+// preceding kernel), then j += 1; with a conditional handle also the device-side loop's
+// condition: go on while j < ctl[2], h_{j+1,j} != 0 and estimate * kappa > tol ||x||_1 (the
+// host's test for a true residual check, with the same operands).
+__global__ void k_givens_end(int* __restrict__ dj, double* __restrict__ st, int m, const double* __restrict__ ctl,
+                             cudaGraphConditionalHandle cond) {
     pdl_begin();
-    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX], s_nrm2;
+    __shared__ double col[GMRES_MMAX + 1], cs[GMRES_MMAX], sn[GMRES_MMAX];
     GmresLayout L(m);
     const int j = *dj;
-    if (threadIdx.x < 32) {
-        const double nn = arn_colsum(Pn, nb, stride, 0, threadIdx.x);
-        if (threadIdx.x == 0) s_nrm2 = nn;
-    }
     for (int q = threadIdx.x; q <= j; q += blockDim.x) {
         col[q] = st[L.h1 + q] + st[L.h2 + q];
         if (q < j) {
@@ -1473,8 +1503,7 @@ __global__ void k_givens_end(int* __restrict__ dj, double* __restrict__ st, int 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double nn = s_nrm2, hn = sqrt(nn);
-        st[L.nrm2] = nn;
+        const double nn = st[L.nrm2], hn = sqrt(nn);
         col[j + 1] = hn;
         for (int q = 0; q < j; ++q) {
             const double c = cs[q], s = sn[q];
@@ -1518,13 +1547,15 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
     const int tile = arn_tile_rows(n), nt = arn_tiles(n);
     double* Pa = partial;
     double* Pb = partial + (size_t)nt * stride;
+    // each kernel's last block sums the per-tile partials for the next (ticket = dj + 1)
+    unsigned* ticket = reinterpret_cast<unsigned*>(dj + 1);
     BAMG_LAUNCH_PDL(k_arn_spmv_dots<T>, nt, 256, 0, s, n, tile, B.rp, B.ci, B.v, (const T*)zout, (const int*)dj, V,
-                    Pa, stride);
+                    Pa, stride, ticket, st + L.h1);
     BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pa, nt, st + L.h1,
-                    Pb, stride, 0);
+                    Pb, stride, 0, ticket, st + L.h2);
     BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pb, nt, st + L.h2,
-                    Pa, stride, 1);
-    BAMG_LAUNCH_PDL(k_givens_end, 1, 64, 0, s, dj, st, m, (const double*)Pa, nt, stride, ctl, cond);
+                    Pa, stride, 1, ticket, st + L.nrm2);
+    BAMG_LAUNCH_PDL(k_givens_end, 1, 64, 0, s, dj, st, m, ctl, cond);
     if (!cond) BAMG_CK(cudaMemcpyAsync(h_est, st + L.est, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
@@ -1693,9 +1724,9 @@ void parnoldi_step(int n, const MatView<double>& B, double* V, T* vin, T* zout, 
     double* Pb = partial + (size_t)nt * stride;
     BAMG_LAUNCH_PDL(k_parn_store_dots<T>, nt, 256, 0, s, n, tile, (const T*)zout, (const int*)dj, V, Pa, stride);
     BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pa, nt, st + L.h1,
-                    Pb, stride, 0);
+                    Pb, stride, 0, (unsigned*)nullptr, (double*)nullptr);
     BAMG_LAUNCH_PDL(k_arn_update_dots, nt, 256, 0, s, n, tile, (const int*)dj, V, (const double*)Pb, nt, st + L.h2,
-                    Pa, stride, 1);
+                    Pa, stride, 1, (unsigned*)nullptr, (double*)nullptr);
     BAMG_LAUNCH_PDL(k_givens_scale_j, g, 256, 0, s, n, V, (const int*)dj, st, m, (const double*)Pa, nt, stride);
     BAMG_LAUNCH_PDL(k_parn_hess, 1, 64, 0, s, (const double*)st, m, (const int*)dj, H, ldh);
     BAMG_LAUNCH_PDL(k_inc_j, 1, 32, 0, s, dj);

@@ -926,7 +926,7 @@ struct Solver : SolverBase {
         rn.ensure(8);
         vin.ensure(n);
         zout.ensure(n);
-        dj.ensure(1);
+        dj.ensure(2);  // j and the Arnoldi kernels' last-block ticket
         // all work of the solve runs on the private stream, fenced against the caller's
         on_private_stream([&] { solve_on_private_stream(x_user, flags, tol, st); });
     }
@@ -947,7 +947,7 @@ struct Solver : SolverBase {
         rn.ensure(8);
         vin.ensure(n);
         zout.ensure(n);
-        dj.ensure(1);
+        dj.ensure(2);  // j and the Arnoldi kernels' last-block ticket
         Hh.ensure((size_t)(mp + 1) * mp);
         eta.ensure(mp);
         if (zero.n < (size_t)n) {
@@ -984,7 +984,7 @@ struct Solver : SolverBase {
             dots(n, x0.get(), n, 1, x0.get(), state.get() + GL.nrm2, partial.get(), s);
             gmres_init(state.get(), mp, s);
             scale_vec(n, x0.get(), state.get(), GL.hn, true, V0, s);
-            BAMG_CK(cudaMemsetAsync(dj.get(), 0, sizeof(int), s));
+            BAMG_CK(cudaMemsetAsync(dj.get(), 0, 2 * sizeof(int), s));
             bool stop = false;
             for (int j = 0; j < mp && it < o.max_it; ++j) {
                 parnoldi_step<T>(n, B, V.get(), vin.get(), zout.get(), dj.get(), state.get(), mp, Hh.get(), mp + 1,
@@ -1097,7 +1097,7 @@ struct Solver : SolverBase {
             dots(n, V0, n, 1, V0, state.get() + GL.nrm2, partial.get(), s);
             gmres_init(state.get(), m, s);
             scale_vec(n, V0, state.get(), GL.hn, true, V0, s);
-            BAMG_CK(cudaMemsetAsync(dj.get(), 0, sizeof(int), s));
+            BAMG_CK(cudaMemsetAsync(dj.get(), 0, 2 * sizeof(int), s));
             for (int j = 0; j < m && it < o.max_it; ++j) {
                 bool launched = false;
                 if (persist) {  // steps j .. jn - 1 in one cooperative launch
