@@ -308,7 +308,10 @@ __device__ __forceinline__ double div_by_recip(double w, double h, double r) {
 }
 
 // ------------------------------------------------------------------ host helpers
-void exclusive_scan(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s);  // d_out has n+1 entries
-int32_t read_int(const int32_t* d_p, cudaStream_t s);
+// d_out has n + 1 entries; with h_total (the device address of mapped host memory) the total
+// is also stored there
+void exclusive_scan(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s, int32_t* h_total = nullptr);
+int32_t exclusive_scan_total(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s);  // the total, to the host
+int32_t read_int(const int32_t* d_p, cudaStream_t s);  // a device int, to the host (after s's earlier work)
 
 }  // namespace bamg

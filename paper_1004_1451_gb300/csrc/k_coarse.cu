@@ -650,6 +650,16 @@ __global__ void __launch_bounds__(CT) k_coarse_eigvals(int n, const double* __re
             }
         }
         if (col > 0) lam[0] = 0.0;
+        if (st != 0) {
+            // The FP32 QR iteration on the shift-invert Arnoldi matrix did not converge (seen
+            // on birth-death chains whose coarsest eigenvalues cluster near 0 by many orders of
+            // magnitude): the coarsest level then supplies the state vector alone, by inverse
+            // iteration at shift 0 (the eigenvalue it belongs to is exactly 0).
+            sel[0] = sel[1] = sel[2] = 0.0;
+            lam[0] = 0.0;
+            kind[0] = 0;
+            col = ns = 1;
+        }
         info[0] = col;
         info[1] = ns;
         info[2] = st;
@@ -682,8 +692,9 @@ template <typename F>
 __global__ void __launch_bounds__(CT) k_coarse_eigvec(int n, const double* __restrict__ Bg,
                                                       const double* __restrict__ Tg, const double* __restrict__ sel,
                                                       double* __restrict__ V, double* __restrict__ lam,
-                                                      int* __restrict__ cycles) {
+                                                      int* __restrict__ cycles, const int* __restrict__ info) {
     pdl_begin();
+    if ((int)blockIdx.x >= info[1]) return;  // past the selected eigenvalues (uniform per block)
     extern __shared__ __align__(16) unsigned char smraw[];
     F* Ar = reinterpret_cast<F*>(smraw);
     F* Ai = Ar + CN * LDP;
@@ -973,43 +984,30 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
     TmpBuf<double> sel(3 * (k_ev + 1), s);
     TmpBuf<int> info(8, s);
     BAMG_LAUNCH(k_coarse_eigvals, 1, CT, 0, s, n, dB, dT, k_ev, sel.get(), d_lam, d_kind, info.get());
+    // one block per selected eigenvalue: k_ev blocks, those past the selection (info[1])
+    // return at once, so the launch needs no read of the selection by the host; the columns
+    // filled (info[0]) are read while the blocks run
+    TmpBuf<int> cyc(2 * k_ev, s);
+    if (fp32_vectors)
+        BAMG_LAUNCH(k_coarse_eigvec<float>, k_ev, CT, smem32, s, n, dB, dT, sel.get(), d_V, d_lam, cyc.get(),
+                    (const int*)info.get());
+    else
+        BAMG_LAUNCH(k_coarse_eigvec<double>, k_ev, CT, smem64, s, n, dB, dT, sel.get(), d_V, d_lam, cyc.get(),
+                    (const int*)info.get());
     int h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     BAMG_CK(cudaMemcpyAsync(h, info.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
     BAMG_CK(cudaStreamSynchronize(s));
-    const bool dbg = getenv("BAMG_DEBUG") != nullptr;
-    if (dbg)
+    if (getenv("BAMG_DEBUG")) {
         fprintf(stderr,
                 "[bamg] coarse eigenvalues: n=%d QR double-shift steps=%d status=%d cycles lu+K=%d arnoldi=%d qr=%d "
                 "tail=%d\n",
                 n, h[3], h[2], h[4], h[5], h[6], h[7]);
-    if (h[2] != 0) {
-        // The FP32 QR iteration on the shift-invert Arnoldi matrix did not converge (seen on
-        // birth-death chains whose coarsest eigenvalues cluster near 0 by many orders of
-        // magnitude): the coarsest level then supplies the state vector alone, by inverse
-        // iteration at shift 0 (the eigenvalue it belongs to is exactly 0).
-        const double one_sel[3] = {0.0, 0.0, 0.0};
-        const double zero = 0.0;
-        const int32_t real_kind = 0;
-        BAMG_CK(cudaMemcpyAsync(sel.get(), one_sel, sizeof(one_sel), cudaMemcpyHostToDevice, s));
-        BAMG_CK(cudaMemcpyAsync(d_lam, &zero, sizeof(double), cudaMemcpyHostToDevice, s));
-        BAMG_CK(cudaMemcpyAsync(d_kind, &real_kind, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        h[0] = 1;
-        h[1] = 1;
-        if (dbg) fprintf(stderr, "[bamg] coarse eigenvalues: QR did not converge; state vector only\n");
-    }
-    if (h[1] > 0) {
-        TmpBuf<int> cyc(2 * h[1], s);
-        if (fp32_vectors)
-            BAMG_LAUNCH(k_coarse_eigvec<float>, h[1], CT, smem32, s, n, dB, dT, sel.get(), d_V, d_lam, cyc.get());
-        else
-            BAMG_LAUNCH(k_coarse_eigvec<double>, h[1], CT, smem64, s, n, dB, dT, sel.get(), d_V, d_lam, cyc.get());
-        if (dbg) {
-            int hc[64] = {0};
-            BAMG_CK(cudaMemcpyAsync(hc, cyc.get(), sizeof(int) * 2 * h[1], cudaMemcpyDeviceToHost, s));
-            BAMG_CK(cudaStreamSynchronize(s));
-            fprintf(stderr, "[bamg] coarse eigenvectors (%s): %d blocks, cycles lu=%d iterate=%d\n",
-                    fp32_vectors ? "fp32" : "fp64", h[1], hc[0], hc[1]);
-        }
+        if (h[2] != 0) fprintf(stderr, "[bamg] coarse eigenvalues: QR did not converge; state vector only\n");
+        int hc[64] = {0};
+        BAMG_CK(cudaMemcpyAsync(hc, cyc.get(), sizeof(int) * 2 * k_ev, cudaMemcpyDeviceToHost, s));
+        BAMG_CK(cudaStreamSynchronize(s));
+        fprintf(stderr, "[bamg] coarse eigenvectors (%s): %d blocks, cycles lu=%d iterate=%d\n",
+                fp32_vectors ? "fp32" : "fp64", h[1], hc[0], hc[1]);
     }
     return h[0];
 }
@@ -1025,7 +1023,7 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
 constexpr int PINV_COLS = 8;
 template <typename F>
 __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restrict__ Bg, double* __restrict__ Pg,
-                                                    int* __restrict__ info) {
+                                                    int* __restrict__ info, int* __restrict__ fail) {
     pdl_begin();
     __shared__ F A[CN * LDP];
     __shared__ F R[CN * PINV_COLS];
@@ -1075,20 +1073,22 @@ __global__ void __launch_bounds__(CT) k_coarse_pinv(int n, const double* __restr
     bad = __syncthreads_or(bad);
     if (tid == 0) {
         info[4 * blockIdx.x] = bad;
+        if (fail && bad) atomicOr(fail, 2);
         info[4 * blockIdx.x + 1] = 0;  // diagnostics: cycles per phase
         info[4 * blockIdx.x + 2] = (int)(c_lu - c_start);
         info[4 * blockIdx.x + 3] = (int)(c_solve - c_lu);
     }
 }
 
-int coarse_pinv(int n, const double* dB, double* dP, bool fp32, cudaStream_t s) {
+int coarse_pinv(int n, const double* dB, double* dP, bool fp32, cudaStream_t s, int* d_fail) {
     BAMG_REQUIRE(n >= 1 && n <= CN, BAMG_EINVAL, "coarse_pinv: coarsest order must be 1..64");
     const int nb = (n + PINV_COLS - 1) / PINV_COLS;
     TmpBuf<int> info(4 * nb, s);
     if (fp32)
-        BAMG_LAUNCH(k_coarse_pinv<float>, nb, CT, 0, s, n, dB, dP, info.get());
+        BAMG_LAUNCH(k_coarse_pinv<float>, nb, CT, 0, s, n, dB, dP, info.get(), d_fail);
     else
-        BAMG_LAUNCH(k_coarse_pinv<double>, nb, CT, 0, s, n, dB, dP, info.get());
+        BAMG_LAUNCH(k_coarse_pinv<double>, nb, CT, 0, s, n, dB, dP, info.get(), d_fail);
+    if (d_fail && !getenv("BAMG_DEBUG")) return 0;  // the caller reads the flag later
     int h[4 * (CN / PINV_COLS)] = {0};
     BAMG_CK(cudaMemcpyAsync(h, info.get(), sizeof(int) * 4 * nb, cudaMemcpyDeviceToHost, s));
     BAMG_CK(cudaStreamSynchronize(s));

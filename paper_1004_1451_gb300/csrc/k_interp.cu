@@ -5,6 +5,7 @@
 #include <cfloat>
 
 #include <atomic>
+#include <chrono>
 
 #include "kernels.cuh"
 
@@ -54,7 +55,8 @@ __global__ void k_scan_local(const int32_t* __restrict__ in, int32_t* __restrict
     }
 }
 
-__global__ void k_scan_sums(int32_t* __restrict__ bsum, int nb, int32_t* __restrict__ total) {
+__global__ void k_scan_sums(int32_t* __restrict__ bsum, int nb, int32_t* __restrict__ total,
+                            int32_t* __restrict__ h_total) {
     pdl_begin();
     __shared__ int32_t wsum[32];
     __shared__ int32_t carry;
@@ -89,7 +91,13 @@ __global__ void k_scan_sums(int32_t* __restrict__ bsum, int nb, int32_t* __restr
         if (threadIdx.x == blockDim.x - 1) carry = excl + v;
         __syncthreads();
     }
-    if (threadIdx.x == 0) *total = carry;
+    if (threadIdx.x == 0) {
+        *total = carry;
+        if (h_total) {
+            *(volatile int32_t*)h_total = carry;
+            __threadfence_system();
+        }
+    }
 }
 
 __global__ void k_scan_add(int32_t* __restrict__ out, int n, const int32_t* __restrict__ bsum) {
@@ -101,7 +109,8 @@ __global__ void k_scan_add(int32_t* __restrict__ out, int n, const int32_t* __re
 // Arrays of up to SCAN_ONE_MAX entries: one block walks the tiles in order with a running
 // carry (one launch instead of three).  out[n] = total; out may alias in.
 constexpr int SCAN_ONE_T = 1024, SCAN_ONE_MAX = 32768;
-__global__ void __launch_bounds__(SCAN_ONE_T) k_scan_one(const int32_t* in, int32_t* out, int n) {
+__global__ void __launch_bounds__(SCAN_ONE_T) k_scan_one(const int32_t* in, int32_t* out, int n,
+                                                         int32_t* __restrict__ h_total) {
     pdl_begin();
     __shared__ int32_t wsum[SCAN_ONE_T / 32];
     __shared__ int32_t carry;
@@ -145,30 +154,90 @@ __global__ void __launch_bounds__(SCAN_ONE_T) k_scan_one(const int32_t* in, int3
         if (threadIdx.x == SCAN_ONE_T - 1) carry = run;
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[n] = carry;
+    if (threadIdx.x == 0) {
+        out[n] = carry;
+        if (h_total) {
+            *(volatile int32_t*)h_total = carry;
+            __threadfence_system();
+        }
+    }
 }
 
-void exclusive_scan(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s) {
+// ---------------------------------------------------------------- counts read by the host
+// A word of mapped pinned host memory per host thread and device: a kernel stores a count
+// there and the host polls it, instead of a device-to-host copy and a stream synchronisation
+// (whose completion path left the GPU idle for about 20 us per read in the setup).
+struct HostWord {
+    int32_t* h = nullptr;
+    int32_t* d = nullptr;
+};
+static HostWord& host_word() {
+    thread_local HostWord w[64];
+    int dev = 0;
+    BAMG_CK(cudaGetDevice(&dev));
+    BAMG_REQUIRE(dev >= 0 && dev < 64, BAMG_EINVAL, "device ordinal out of range");
+    HostWord& hw = w[dev];
+    if (!hw.h) {
+        BAMG_CK(cudaHostAlloc((void**)&hw.h, 64, cudaHostAllocMapped | cudaHostAllocPortable));
+        BAMG_CK(cudaHostGetDevicePointer((void**)&hw.d, hw.h, 0));
+    }
+    return hw;
+}
+constexpr int32_t HOST_WORD_EMPTY = INT32_MIN;
+// The count a kernel queued on s stores in the word: polled, with the stream's state checked
+// now and then so that an error or a stream that finished without storing is reported; a
+// bounded wait (BAMG_ETIMEOUT after 60 s).
+static int32_t host_word_wait(const HostWord& hw, cudaStream_t s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (uint64_t k = 0;; ++k) {
+        const int32_t v = *(volatile int32_t*)hw.h;
+        if (v != HOST_WORD_EMPTY) return v;
+        if ((k & 1023) == 1023) {
+            const cudaError_t e = cudaStreamQuery(s);
+            if (e != cudaSuccess && e != cudaErrorNotReady) BAMG_CK(e);
+            if (e == cudaSuccess && *(volatile int32_t*)hw.h == HOST_WORD_EMPTY)
+                throw Error(BAMG_ECUDA, "a count the host waits for was not stored");
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+                throw Error(BAMG_ETIMEOUT, "waiting for a count from the device");
+        }
+    }
+}
+__global__ void k_word_copy(const int32_t* __restrict__ d_p, int32_t* __restrict__ h) {
+    pdl_begin();
+    *(volatile int32_t*)h = *d_p;
+    __threadfence_system();
+}
+
+void exclusive_scan(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s, int32_t* h_total) {
     if (n <= 0) {
         BAMG_CK(cudaMemsetAsync(d_out, 0, sizeof(int32_t), s));
+        if (h_total) BAMG_LAUNCH(k_word_copy, 1, 1, 0, s, (const int32_t*)d_out, h_total);
         return;
     }
     if (n <= SCAN_ONE_MAX) {
-        BAMG_LAUNCH(k_scan_one, 1, SCAN_ONE_T, 0, s, d_in, d_out, n);
+        BAMG_LAUNCH(k_scan_one, 1, SCAN_ONE_T, 0, s, d_in, d_out, n, h_total);
         return;
     }
     const int nb = (int)blocks_for(n, SCAN_B);
     TmpBuf<int32_t> bsum(nb, s);
     BAMG_LAUNCH(k_scan_local, nb, SCAN_T, 0, s, d_in, d_out, n, bsum.get());
-    BAMG_LAUNCH(k_scan_sums, 1, 1024, 0, s, bsum.get(), nb, d_out + n);
+    BAMG_LAUNCH(k_scan_sums, 1, 1024, 0, s, bsum.get(), nb, d_out + n, h_total);
     BAMG_LAUNCH(k_scan_add, blocks_for(n, 256), 256, 0, s, d_out, n, bsum.get());
 }
 
+// exclusive scan of n counts into d_out (n + 1 entries), returning the total to the host
+int32_t exclusive_scan_total(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s) {
+    HostWord& hw = host_word();
+    *(volatile int32_t*)hw.h = HOST_WORD_EMPTY;
+    exclusive_scan(d_in, d_out, n, s, hw.d);
+    return host_word_wait(hw, s);
+}
+
 int32_t read_int(const int32_t* d_p, cudaStream_t s) {
-    int32_t v = 0;
-    BAMG_CK(cudaMemcpyAsync(&v, d_p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    BAMG_CK(cudaStreamSynchronize(s));
-    return v;
+    HostWord& hw = host_word();
+    *(volatile int32_t*)hw.h = HOST_WORD_EMPTY;
+    BAMG_LAUNCH(k_word_copy, 1, 1, 0, s, d_p, hw.d);
+    return host_word_wait(hw, s);
 }
 
 // ================================================================ coarsening
@@ -1402,8 +1471,7 @@ void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int
     }
     BAMG_LAUNCH(k_gal_large<T>, GAL_BLOCKS_L, 32, smem_l, s, ga, (const int32_t*)list.get(), (const int*)nlist.get());
     out.rp.alloc(nc + 1);
-    exclusive_scan(ucnt.get(), out.rp.get(), nc, s);
-    out.nnz = read_int(out.rp.get() + nc, s);
+    out.nnz = exclusive_scan_total(ucnt.get(), out.rp.get(), nc, s);
     const size_t nz = out.nnz > 0 ? (size_t)out.nnz : 1;
     out.ci.alloc(nz);
     out.bv.alloc(nz);

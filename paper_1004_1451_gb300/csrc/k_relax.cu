@@ -794,13 +794,10 @@ int build_system_matrix(int n, int nnzA, const int32_t* rpA, const int32_t* ciA,
     BAMG_CK(cudaMemsetAsync(flags.get(), 0, sizeof(int), s));
     BAMG_LAUNCH(k_count_B, blocks_for(n, 256), 256, 0, s, n, rpA, ciA, vA, cnt.get(), flags.get(), colsum.get());
     BAMG_LAUNCH(k_check_colsum, blocks_for(n, 256), 256, 0, s, n, colsum.get(), flags.get());
-    int h_flags = 0;
-    BAMG_CK(cudaMemcpyAsync(&h_flags, flags.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
-    BAMG_CK(cudaStreamSynchronize(s));
+    const int h_flags = read_int(flags.get(), s);
     if (h_flags) return h_flags;
     rpB.alloc(n + 1);
-    exclusive_scan(cnt.get(), rpB.get(), n, s);
-    const int nnzB = read_int(rpB.get() + n, s);
+    const int nnzB = exclusive_scan_total(cnt.get(), rpB.get(), n, s);
     ciB.alloc(nnzB);
     vB.alloc(nnzB);
     BAMG_LAUNCH(k_fill_B, blocks_for(n, 256), 256, 0, s, n, rpA, ciA, vA, rpB.get(), ciB.get(), vB.get());

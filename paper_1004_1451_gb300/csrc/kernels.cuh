@@ -148,7 +148,9 @@ int coarse_eig(int n, const double* dB, const double* dT, int k_ev, double* d_la
                bool fp32_vectors, cudaStream_t s);
 // Minimal-norm inverse of the rank n-1 matrix B (dense FP64 in and out, row-major),
 // computed in FP32 arithmetic when fp32 is set, else in FP64.
-int coarse_pinv(int n, const double* dB, double* dP, bool fp32, cudaStream_t s);
+// with d_fail: a failed factorisation sets bit 2 of *d_fail and the call returns 0 without
+// waiting for the device; else it returns BAMG_ENUMERIC after reading the blocks' status
+int coarse_pinv(int n, const double* dB, double* dP, bool fp32, cudaStream_t s, int* d_fail = nullptr);
 
 // Colour classes of the multicolour Gauss-Seidel smoother for the pattern (n, rp, ci):
 // repeated independent sets of the uncoloured states; rows sorted by (colour, state), host

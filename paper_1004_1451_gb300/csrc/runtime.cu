@@ -290,7 +290,7 @@ struct Solver : SolverBase {
         return v;
     }
 
-    DevBuf<int> ls_err;  // overflow flag of the neighbourhood searches, read once per setup
+    DevBuf<int> ls_err;  // bit 1: a neighbourhood search overflowed; bit 2: B_L^+ failed (read once per setup)
     std::unique_ptr<StackArena> arena;  // the setup's temporaries
     PhaseTrace* trace = nullptr;  // set during a traced setup
 
@@ -488,8 +488,7 @@ struct Solver : SolverBase {
         TmpBuf<double> Bd((size_t)nL * nL, s);
         csr_to_dense<T>(nL, Lc.rp.get(), Lc.ci.get(), Lc.bv.get(), Bd.get(), s);
         pinv64.ensure((size_t)nL * nL);
-        BAMG_REQUIRE(coarse_pinv(nL, Bd.get(), pinv64.get(), std::is_same<T, float>::value, s) == 0, BAMG_ENUMERIC,
-                     "singular coarsest factor");
+        coarse_pinv(nL, Bd.get(), pinv64.get(), std::is_same<T, float>::value, s, ls_err.get());
         pinvT.ensure((size_t)nL * nL);
         if constexpr (std::is_same<T, double>::value)
             BAMG_CK(cudaMemcpyAsync(pinvT.get(), pinv64.get(), sizeof(double) * nL * nL, cudaMemcpyDeviceToDevice, s));
@@ -590,10 +589,9 @@ struct Solver : SolverBase {
     }
 
     void check_search_overflow() {
-        int h_err = 0;
-        BAMG_CK(cudaMemcpyAsync(&h_err, ls_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
-        BAMG_CK(cudaStreamSynchronize(s));
-        BAMG_REQUIRE(h_err == 0, BAMG_EOVERFLOW, "neighbourhood search: a fine point needs more than 2048 recorded states");
+        const int h_err = read_int(ls_err.get(), s);
+        BAMG_REQUIRE(!(h_err & 2), BAMG_ENUMERIC, "singular coarsest factor");
+        BAMG_REQUIRE(!(h_err & 1), BAMG_EOVERFLOW, "neighbourhood search: a fine point needs more than 2048 recorded states");
     }
 
     // Bootstrap setup: o.setup_cycles MLE cycles, then the rebuild, B_L^+ and the initial
