@@ -232,6 +232,13 @@ int32_t exclusive_scan_total(const int32_t* d_in, int32_t* d_out, int n, cudaStr
     exclusive_scan(d_in, d_out, n, s, hw.d);
     return host_word_wait(hw, s);
 }
+// the same scan with the total left on its way to the host word (scan_total_wait collects it)
+static void exclusive_scan_total_begin(const int32_t* d_in, int32_t* d_out, int n, cudaStream_t s) {
+    HostWord& hw = host_word();
+    *(volatile int32_t*)hw.h = HOST_WORD_EMPTY;
+    exclusive_scan(d_in, d_out, n, s, hw.d);
+}
+static int32_t scan_total_wait(cudaStream_t s) { return host_word_wait(host_word(), s); }
 
 int32_t read_int(const int32_t* d_p, cudaStream_t s) {
     HostWord& hw = host_word();
@@ -1435,7 +1442,7 @@ __global__ void __launch_bounds__(32) k_gal_large(const __grid_constant__ GalArg
 
 template <typename T>
 void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int32_t* qci, const T* qv,
-              const EllView<T>& P, int nc, GalerkinOut<T>& out, cudaStream_t s) {
+              const EllView<T>& P, int nc, GalerkinOut<T>& out, cudaStream_t s, bool defer) {
     TmpBuf<int32_t> np(nc, s), poff(nc + 1, s);
     BAMG_LAUNCH(k_gal_count, blocks_for(nc, GAL_COUNT_WARPS), GAL_COUNT_WARPS * 32, 0, s, nc, qrp, qci, B.rp, B.ci,
                 P.pcnt, np.get());
@@ -1471,14 +1478,27 @@ void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int
     }
     BAMG_LAUNCH(k_gal_large<T>, GAL_BLOCKS_L, 32, smem_l, s, ga, (const int32_t*)list.get(), (const int*)nlist.get());
     out.rp.alloc(nc + 1);
-    out.nnz = exclusive_scan_total(ucnt.get(), out.rp.get(), nc, s);
-    const size_t nz = out.nnz > 0 ? (size_t)out.nnz : 1;
+    size_t nz = tot;  // with defer: room for the bound, the count still on its way
+    // (only while the bound's arrays stay small: large ones cost more to allocate than the wait)
+    if (defer && tot * (sizeof(int32_t) + 2 * sizeof(T)) > ((size_t)64 << 20)) defer = false;
+    if (defer) {
+        exclusive_scan_total_begin(ucnt.get(), out.rp.get(), nc, s);
+        out.nnz = -1;
+    } else {
+        out.nnz = exclusive_scan_total(ucnt.get(), out.rp.get(), nc, s);
+        nz = out.nnz > 0 ? (size_t)out.nnz : 1;
+    }
     out.ci.alloc(nz);
     out.bv.alloc(nz);
     out.tv.alloc(nz);
     BAMG_LAUNCH(k_gal_compact<T>, blocks_for(nc, GAL_COUNT_WARPS), GAL_COUNT_WARPS * 32, 0, s, nc, poff.get(),
                 ucnt.get(), out.rp.get(), uJ.get(),
                 ubv.get(), utv.get(), out.ci.get(), out.bv.get(), out.tv.get());
+}
+
+template <typename T>
+void galerkin_nnz(GalerkinOut<T>& out, cudaStream_t s) {
+    if (out.nnz < 0) out.nnz = scan_total_wait(s);
 }
 
 template <typename T>
@@ -1505,7 +1525,8 @@ void csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const T* v, doubl
     template void build_restriction<T>(const EllView<T>&, int, DevBuf<int32_t>&, DevBuf<int32_t>&, DevBuf<T>&,      \
                                        cudaStream_t);                                                               \
     template void galerkin<T>(const MatView<T>&, const T*, const int32_t*, const int32_t*, const T*,                \
-                              const EllView<T>&, int, GalerkinOut<T>&, cudaStream_t);                               \
+                              const EllView<T>&, int, GalerkinOut<T>&, cudaStream_t, bool);                         \
+    template void galerkin_nnz<T>(GalerkinOut<T>&, cudaStream_t);                                                   \
     template void csr_to_dense<T>(int, const int32_t*, const int32_t*, const T*, double*, cudaStream_t);
 INST(float)
 INST(double)

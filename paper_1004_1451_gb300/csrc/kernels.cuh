@@ -126,11 +126,17 @@ template <typename T>
 struct GalerkinOut {
     DevBuf<int32_t> rp, ci;
     DevBuf<T> bv, tv;
-    int nnz = 0;
+    int nnz = 0;  // -1 while the count is on its way to the host (galerkin with defer)
 };
+// With defer (taken while the bound's arrays stay within 64 MB) the coarse arrays get room for
+// the product count's bound and the compaction is queued without waiting for the entry count;
+// galerkin_nnz(out, s) then waits for it (no other count may be read on this host thread in
+// between).
 template <typename T>
 void galerkin(const MatView<T>& B, const T* T_val, const int32_t* qrp, const int32_t* qci, const T* qv,
-              const EllView<T>& P, int nc, GalerkinOut<T>& out, cudaStream_t s);
+              const EllView<T>& P, int nc, GalerkinOut<T>& out, cudaStream_t s, bool defer = false);
+template <typename T>
+void galerkin_nnz(GalerkinOut<T>& out, cudaStream_t s);
 template <typename T>
 void csr_to_dense(int n, const int32_t* rp, const int32_t* ci, const T* v, double* D, cudaStream_t s);
 

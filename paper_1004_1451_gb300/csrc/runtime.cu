@@ -336,15 +336,18 @@ struct Solver : SolverBase {
         build_restriction<T>(c.P(o.caliber), c.nc, c.qrp, c.qci, c.qv, s);
         if (trace) trace->mark(" q", l);
         GalerkinOut<T> go;
-        galerkin<T>(c.B(), c.tv.get(), c.qrp.get(), c.qci.get(), c.qv.get(), c.P(o.caliber), c.nc, go, s);
-        if (trace) trace->mark(" gal", l);
+        // the entry count reaches the host while the compaction and the diagonals run (the
+        // coarse arrays have room for the product count's bound)
+        galerkin<T>(c.B(), c.tv.get(), c.qrp.get(), c.qci.get(), c.qv.get(), c.P(o.caliber), c.nc, go, s, true);
         nx.n = c.nc;
-        nx.nnz = go.nnz;
         nx.rp = std::move(go.rp);
         nx.ci = std::move(go.ci);
         nx.bv = std::move(go.bv);
         nx.tv = std::move(go.tv);
         nx.diagonals(s);
+        galerkin_nnz<T>(go, s);
+        nx.nnz = go.nnz;
+        if (trace) trace->mark(" gal", l);
     }
 
     void split(int l) {
