@@ -1084,6 +1084,21 @@ struct Solver : SolverBase {
             perr.ensure(1);
         }
         residual_norms(B, x0.get(), rn.get(), partial.get(), s);
+        // a restart cycle's start: v_1 = r_0 / ||r_0||, g = beta e_1, j = 0
+        auto cycle_start = [&] {
+            double* V0 = V.get();
+            spmv_f64(B, x0.get(), V0, -1.0, s);
+            dots(n, V0, n, 1, V0, state.get() + GL.nrm2, partial.get(), s);
+            gmres_init(state.get(), m, s);
+            scale_vec(n, V0, state.get(), GL.hn, true, V0, s);
+            BAMG_CK(cudaMemsetAsync(dj.get(), 0, 2 * sizeof(int), s));
+        };
+        // the first cycle's start is queued before the residual is read and the step is
+        // captured meanwhile, so the device works while the host captures (the start goes
+        // unused when x_0 already meets the tolerance)
+        cycle_start();
+        bool started = true;
+        if (!persist && !gexec) capture_step(n);
         read_n(rn.get(), RESNORM_SUMS);
         double ratio1 = h_pin[0] / h_pin[2];
         double ratio = l2 ? std::sqrt(h_pin[1] / h_pin[4]) : ratio1;
@@ -1093,12 +1108,8 @@ struct Solver : SolverBase {
         if (ratio <= tol) status = BAMG_OK;
         while (status != BAMG_OK && it < o.max_it) {
             if (!persist && !gexec) capture_step(n);
-            double* V0 = V.get();
-            spmv_f64(B, x0.get(), V0, -1.0, s);
-            dots(n, V0, n, 1, V0, state.get() + GL.nrm2, partial.get(), s);
-            gmres_init(state.get(), m, s);
-            scale_vec(n, V0, state.get(), GL.hn, true, V0, s);
-            BAMG_CK(cudaMemsetAsync(dj.get(), 0, 2 * sizeof(int), s));
+            if (!started) cycle_start();
+            started = false;
             for (int j = 0; j < m && it < o.max_it; ++j) {
                 bool launched = false;
                 if (persist) {  // steps j .. jn - 1 in one cooperative launch
