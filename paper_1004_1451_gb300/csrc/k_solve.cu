@@ -1173,8 +1173,9 @@ void update_minus(int n, const double* V, int64_t ldv, int nv, const double* d_h
 
 template <typename TZ>
 __global__ void k_form_x(int n, const double* __restrict__ x0, const TZ* __restrict__ Z, int64_t ldz, int nz,
-                         const double* __restrict__ y, double* __restrict__ x) {
+                         const double* __restrict__ y, double* __restrict__ x, const int* __restrict__ dnz) {
     pdl_begin();
+    if (dnz) nz = *dnz;  // the column count from device memory
     __shared__ double sy[GMRES_MMAX];
     for (int q = threadIdx.x; q < nz; q += blockDim.x) sy[q] = y[q];
     __syncthreads();
@@ -1185,8 +1186,9 @@ __global__ void k_form_x(int n, const double* __restrict__ x0, const TZ* __restr
     x[i] = x0[i] + s;
 }
 template <typename TZ>
-void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const double* d_y, double* x, cudaStream_t s) {
-    BAMG_LAUNCH(k_form_x<TZ>, blocks_for(n, 256), 256, 0, s, n, x0, Z, ldz, nz, d_y, x);
+void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const double* d_y, double* x, cudaStream_t s,
+            const int* dnz) {
+    BAMG_LAUNCH(k_form_x<TZ>, blocks_for(n, 256), 256, 0, s, n, x0, Z, ldz, nz, d_y, x, dnz);
 }
 
 // sums of |Bx|, (Bx)^2, |x|, x and x^2 over rows: per-block partials then a fixed-order sum.
@@ -1259,8 +1261,9 @@ void gmres_init(double* d_state, int m, cudaStream_t s) { BAMG_LAUNCH(k_gmres_in
 // y = R^{-1} g for the leading (j+1) x (j+1) block: column-oriented back substitution by
 // one warp, R read from the state in global memory (column-major, consecutive lanes read
 // consecutive rows of a column), y in shared memory.
-__global__ void k_solve_y(double* __restrict__ st, int j, int m) {
+__global__ void k_solve_y(double* __restrict__ st, int j, int m, const int* __restrict__ dj) {
     pdl_begin();
+    if (dj) j = *dj - 1;  // the last column from device memory
     __shared__ double y[GMRES_MMAX];
     GmresLayout L(m);
     const int lane = threadIdx.x;
@@ -1277,7 +1280,9 @@ __global__ void k_solve_y(double* __restrict__ st, int j, int m) {
     }
     for (int r = lane; r <= j; r += 32) st[L.y + r] = y[r];
 }
-void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s) { BAMG_LAUNCH(k_solve_y, 1, 32, 0, s, d_state, j, m); }
+void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s, const int* dj) {
+    BAMG_LAUNCH(k_solve_y, 1, 32, 0, s, d_state, j, m, dj);
+}
 
 
 // ---------------------------------------------------------------- graph-replayable Arnoldi step
@@ -2185,7 +2190,9 @@ template void vcycle<float>(const std::vector<VLevel<float>>&, const float*, dou
                             const int*);
 template void vcycle<double>(const std::vector<VLevel<double>>&, const double*, double, int, int, cudaStream_t,
                              double*, const int*);
-template void form_x<float>(int, const double*, const float*, int64_t, int, const double*, double*, cudaStream_t);
-template void form_x<double>(int, const double*, const double*, int64_t, int, const double*, double*, cudaStream_t);
+template void form_x<float>(int, const double*, const float*, int64_t, int, const double*, double*, cudaStream_t,
+                             const int*);
+template void form_x<double>(int, const double*, const double*, int64_t, int, const double*, double*, cudaStream_t,
+                              const int*);
 
 }  // namespace bamg

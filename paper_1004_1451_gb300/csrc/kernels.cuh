@@ -203,7 +203,8 @@ int dots_partial_blocks(int n);
 int arn_tiles(int n);  // row tiles of the fused Arnoldi kernels
 void update_minus(int n, const double* V, int64_t ldv, int nv, const double* d_h, double* w, cudaStream_t s);
 template <typename TZ>
-void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const double* d_y, double* x, cudaStream_t s);
+void form_x(int n, const double* x0, const TZ* Z, int64_t ldz, int nz, const double* d_y, double* x, cudaStream_t s,
+            const int* dnz = nullptr);  // with dnz the column count is *dnz (device memory)
 // sum |B x|, sum (B x)^2, sum |x|, sum x into d_out[4] (deterministic).
 // FGMRES Arnoldi steps *dj .. (until the stop test of ctl) in one cooperative launch with
 // grid-wide barriers (same iterates as the captured step); false, launching nothing, when
@@ -238,7 +239,7 @@ void arnoldi_step_graphable(int n, const MatView<double>& B, double* V, T* Z, T*
                             int m, double* partial, const std::vector<VLevel<T>>& lv, const T* pinv, double omega,
                             int nu_pre, int nu_post, double* h_est, const double* ctl,
                             cudaGraphConditionalHandle cond, cudaStream_t s);
-void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s);
+void gmres_solve_y(double* d_state, int j, int m, cudaStream_t s, const int* dj = nullptr);  // with dj: j = *dj - 1
 
 }  // namespace bamg
 

@@ -234,6 +234,7 @@ struct Solver : SolverBase {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_kernels = 0;  // kernels of one step
+    int64_t graph_post = 0;     // kernels of the check after the device-side loop (one per launch)
     bool graph_loop = false;    // one launch runs steps until the device-side test stops it
     DevBuf<double> ctl;         // the loop's kappa, tol ||x||_1 and last j + 1
     DevBuf<unsigned> pbar;      // grid barrier of the persistent Arnoldi cycle
@@ -754,7 +755,7 @@ struct Solver : SolverBase {
         const int n = lv[0]->n;
         const MatView<double> B = B64();
         TmpBuf<double> x(n, s), r(n, s), z(n, s), t(n, s), mom(2, s);
-        if (!h_pin) BAMG_CK(cudaMallocHost(&h_pin, 16 * sizeof(double)));
+        if (!h_pin) BAMG_CK(cudaMallocHost(&h_pin, 32 * sizeof(double)));
         BAMG_LAUNCH(k_vf_start, blocks_for(n, 256), 256, 0, s, n, x.get());
         spmv_f64(B, x.get(), r.get(), 1.0, s);
         auto normalise = [&]() {  // r <- (r - mean) / ||r - mean||; returns the norm
@@ -825,6 +826,7 @@ struct Solver : SolverBase {
         const uint64_t c0 = t_launches;  // other threads may launch meanwhile
         cudaGraph_t g = nullptr;
         cudaGraphConditionalHandle cond = 0;
+        cudaGraphNode_t cnode = nullptr;
         if (loop) {
             BAMG_CK(cudaGraphCreate(&g, 0));
             bool ok = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
@@ -834,8 +836,7 @@ struct Solver : SolverBase {
                 p.conditional.handle = cond;
                 p.conditional.type = cudaGraphCondTypeWhile;
                 p.conditional.size = 1;
-                cudaGraphNode_t node = nullptr;
-                ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p) == cudaSuccess;
+                ok = cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &p) == cudaSuccess;
             }
             if (ok)
                 ok = cudaStreamBeginCaptureToGraph(s, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
@@ -868,6 +869,29 @@ struct Solver : SolverBase {
         if (!loop) g = c;
         const int64_t kernels = (int64_t)(t_launches - c0);
         count_launches(-kernels);  // counted again at every executed step
+        int64_t post = 0;
+        if (loop) {
+            // after the loop: the true residual check that every stop of the loop calls for
+            // (y from R and g, x = x_0 + Z y, the residual sums), on the device, so that the
+            // host reads the stop and the check together
+            const uint64_t c1 = t_launches;
+            GmresLayout GL(m);
+            BAMG_CK(cudaStreamBeginCaptureToGraph(s, g, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+            try {
+                gmres_solve_y(state.get(), 0, m, s, dj.get());
+                form_x<T>(n, x0.get(), Z.get(), n, 0, state.get() + GL.y, xw.get(), s, dj.get());
+                residual_norms(B64(), xw.get(), rn.get(), partial.get(), s);
+            } catch (...) {
+                cudaGraph_t c2 = nullptr;
+                cudaStreamEndCapture(s, &c2);
+                cudaGraphDestroy(g);
+                throw;
+            }
+            cudaGraph_t c2 = nullptr;
+            BAMG_CK(cudaStreamEndCapture(s, &c2));
+            post = (int64_t)(t_launches - c1);
+            count_launches(-post);
+        }
         cudaGraphExec_t ex = nullptr;
         if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
             cudaGetLastError();
@@ -878,12 +902,13 @@ struct Solver : SolverBase {
         graph = g;
         gexec = ex;
         graph_kernels = kernels;
+        graph_post = post;
         graph_loop = loop;
         return true;
     }
 
     void ensure_private_stream() {
-        if (!h_pin) BAMG_CK(cudaMallocHost(&h_pin, 16 * sizeof(double)));
+        if (!h_pin) BAMG_CK(cudaMallocHost(&h_pin, 32 * sizeof(double)));
         if (!ps) {
             BAMG_CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
             BAMG_CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
@@ -1111,7 +1136,7 @@ struct Solver : SolverBase {
             if (!started) cycle_start();
             started = false;
             for (int j = 0; j < m && it < o.max_it; ++j) {
-                bool launched = false;
+                bool launched = false, checked = false;  // checked: the graph formed the check's sums
                 if (persist) {  // steps j .. jn - 1 in one cooperative launch
                     h_pin[12] = kappa;
                     h_pin[13] = tol * x1;
@@ -1150,11 +1175,14 @@ struct Solver : SolverBase {
                     BAMG_CK(cudaMemcpyAsync(h_pin, state.get() + GL.est, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                             s));
                     BAMG_CK(cudaMemcpyAsync(h_pin + 4, dj.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+                    BAMG_CK(cudaMemcpyAsync(h_pin + 16, rn.get(), RESNORM_SUMS * sizeof(double), cudaMemcpyDeviceToHost,
+                                            s));
                     BAMG_CK(cudaStreamSynchronize(s));
                     ++waits;
                     const int jn = *reinterpret_cast<const int*>(h_pin + 4);
                     BAMG_REQUIRE(jn > j && jn <= (int)h_pin[14], BAMG_ECUDA, "device-side Arnoldi loop: bad step count");
-                    count_launches(graph_kernels * (jn - j));
+                    count_launches(graph_kernels * (jn - j) + graph_post);
+                    checked = true;
                     it += jn - j;
                     j = jn - 1;
                 } else {
@@ -1167,10 +1195,14 @@ struct Solver : SolverBase {
                 const double est = h_pin[0], hn = h_pin[1];
                 const bool last = (j == m - 1) || it >= o.max_it || hn == 0.0;
                 if (est * kappa <= tol * x1 || last) {
-                    gmres_solve_y(state.get(), j, m, s);
-                    form_x<T>(n, x0.get(), Z.get(), n, j + 1, state.get() + GL.y, xw.get(), s);
-                    residual_norms(B, xw.get(), rn.get(), partial.get(), s);
-                    read_n(rn.get(), RESNORM_SUMS);
+                    if (checked) {  // formed by the graph after its loop, read with the stop
+                        for (int k = 0; k < RESNORM_SUMS; ++k) h_pin[k] = h_pin[16 + k];
+                    } else {
+                        gmres_solve_y(state.get(), j, m, s);
+                        form_x<T>(n, x0.get(), Z.get(), n, j + 1, state.get() + GL.y, xw.get(), s);
+                        residual_norms(B, xw.get(), rn.get(), partial.get(), s);
+                        read_n(rn.get(), RESNORM_SUMS);
+                    }
                     ++checks;
                     have_xw = true;
                     const double r1 = h_pin[0], r2 = std::sqrt(h_pin[1]);
