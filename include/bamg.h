@@ -166,7 +166,11 @@ int bamg_default_opts(bamg_opts* o);
  * A: the transition matrix (copied; the caller may free it on return).
  * r: number of random test vectors (1..24).  levels: maximum number of coarsenings.
  * On success *h owns all device memory of the hierarchy until bamg_free(*h).
- * Errors: EINVAL (sizes, r, options, grid dims), ENOTSTOCH, ENOMEM, ECUDA, ENUMERIC. */
+ * Errors: EINVAL (sizes, r, options, grid dims), ENOTSTOCH, ENOMEM, ECUDA, ENUMERIC.
+ * The setup returns without waiting for its last kernels: two errors found on the device
+ * at its end, a neighbourhood search that overflowed (EOVERFLOW) and a singular coarsest
+ * factor (ENUMERIC), are returned by the next call that uses the handle (bamg_solve,
+ * bamg_parnoldi, bamg_vcycle_apply, the smoother and export calls). */
 int bamg_setup(const bamg_csr* A, int r, int levels, const bamg_opts* o, bamg_handle** h);
 
 enum { BAMG_X_GUESS = 1, BAMG_X_HOST = 2, BAMG_NORM_L2 = 4 };
@@ -177,7 +181,7 @@ enum { BAMG_X_GUESS = 1, BAMG_X_HOST = 2, BAMG_NORM_L2 = 4 };
  * (Section 4.1) is used.  With BAMG_NORM_L2 the stopping test is ||B x||_2 / ||x||_2 <= tol
  * (Section 5.1's criterion; st->residual_l1 still reports the l1 ratio).
  * st may be NULL.  Errors: ENOCONV (x holds the last iterate),
- * ENUMERIC, ECUDA. */
+ * ENUMERIC, ECUDA; and EOVERFLOW or ENUMERIC left by bamg_setup (see there). */
 int bamg_solve(bamg_handle* h, double* x, int flags, double tol, bamg_stats* st);
 
 /* Batched form: sets up and solves nchains independent chains to ||B x||_1/||x||_1 <= tol

@@ -592,6 +592,27 @@ struct Solver : SolverBase {
         L_idx = -1;
     }
 
+    // The setup's device-side error flags (ls_err) reach the host without the setup waiting for
+    // the device: the copy is queued into the pinned block (double slot 30) and read by the
+    // next call that uses the hierarchy, which waits for the device in any case (bamg_solve
+    // after its first residual read, at no cost).
+    bool setup_flags_pending = false;
+    void queue_setup_flags() {
+        ensure_private_stream();
+        int* hf = reinterpret_cast<int*>(h_pin + 30);
+        *hf = 0;
+        BAMG_CK(cudaMemcpyAsync(hf, ls_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        setup_flags_pending = true;
+    }
+    // synced: the queued copy is known to have completed (a later wait covered it)
+    void check_setup_flags(bool synced) {
+        if (!setup_flags_pending) return;
+        if (!synced) BAMG_CK(cudaStreamSynchronize(s));
+        setup_flags_pending = false;
+        const int h_err = *reinterpret_cast<const int*>(h_pin + 30);
+        BAMG_REQUIRE(!(h_err & 2), BAMG_ENUMERIC, "singular coarsest factor");
+        BAMG_REQUIRE(!(h_err & 1), BAMG_EOVERFLOW, "neighbourhood search: a fine point needs more than 2048 recorded states");
+    }
     void check_search_overflow() {
         const int h_err = read_int(ls_err.get(), s);
         BAMG_REQUIRE(!(h_err & 2), BAMG_ENUMERIC, "singular coarsest factor");
@@ -640,7 +661,11 @@ struct Solver : SolverBase {
         build_colours();
         if (mle_tol <= 0.0) state_vector(x_init.get(), nullptr);
         alloc_vcycle_work();
-        check_search_overflow();
+        setup_flags_pending = false;
+        if (mle_tol > 0.0)
+            check_search_overflow();
+        else
+            queue_setup_flags();
         tr.mark("guess");
         setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
@@ -741,6 +766,7 @@ struct Solver : SolverBase {
     int precision() const override { return std::is_same<T, float>::value ? BAMG_F32 : BAMG_F64; }
 
     void smooth_apply(int level, int sweeps, const void* b, void* x, void* work) override {
+        check_setup_flags(false);
         BAMG_REQUIRE(level >= 0 && level < (int)lv.size(), BAMG_EINVAL, "smooth_apply: no such level");
         BAMG_REQUIRE(sweeps >= 0, BAMG_EINVAL, "smooth_apply: sweeps < 0");
         VLevel<T> v;
@@ -751,6 +777,7 @@ struct Solver : SolverBase {
 
     // power iteration on the residual propagator I - B C (see bamg_vcycle_factor)
     double vcycle_factor(int iters) override {
+        check_setup_flags(false);
         AllocStream as_(s);
         const int n = lv[0]->n;
         const MatView<double> B = B64();
@@ -786,6 +813,7 @@ struct Solver : SolverBase {
     }
 
     void vcycle_apply(const double* v, double* z) override {
+        check_setup_flags(false);
         AllocStream as_(s);
         const int n = lv[0]->n;
         if constexpr (std::is_same<T, double>::value) {
@@ -960,6 +988,7 @@ struct Solver : SolverBase {
     // --------------------------------------------------------------- pArnoldi (Section 4.3)
     DevBuf<double> Hh, eta, zero;
     void parnoldi(double* x_user, int flags, double tol, bamg_stats* st) override {
+        check_setup_flags(false);
         AllocStream as_(s);
         const int n = lv[0]->n;
         const int mp = std::min(std::max(o.gmres_m, 1), PARN_MMAX);
@@ -1125,6 +1154,7 @@ struct Solver : SolverBase {
         bool started = true;
         if (!persist && !gexec) capture_step(n);
         read_n(rn.get(), RESNORM_SUMS);
+        check_setup_flags(true);  // the setup's copy preceded this wait on the caller's stream
         double ratio1 = h_pin[0] / h_pin[2];
         double ratio = l2 ? std::sqrt(h_pin[1] / h_pin[4]) : ratio1;
         double x1 = l2 ? std::sqrt(h_pin[4]) : h_pin[2], xsum = h_pin[3], last_x1 = x1;
@@ -1262,6 +1292,7 @@ struct Solver : SolverBase {
         for (size_t i = 0; i < cnt; ++i) h[i] = (double)tmp[i];
     }
     void export_obj(int l, int what, void* h_dst, int64_t cap, int64_t* bytes) override {
+        check_setup_flags(false);
         BAMG_REQUIRE(l >= 0 && l < (int)lv.size(), BAMG_EINVAL, "export: level out of range");
         LevelT<T>& L = *lv[l];
         int64_t need = 0;
